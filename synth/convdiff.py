@@ -1,0 +1,182 @@
+"""Seeded convection-diffusion test matrices on regular 2D/3D grids.
+
+This module builds INPUTS only: a sparse matrix A in CSR form, right-hand
+sides, and the grid description.  It holds none of the factorisation's
+arithmetic and is shared, unchanged, by the CPU oracle, the tests and the
+benchmark.
+
+Problem (the paper's benchmark family, Section 4): -div(a grad u) + v . grad u = f
+on the unit square/cube with u = 0 on the boundary, n points per side,
+h = 1/(n+1), lexicographic numbering with x fastest.
+
+Discretisation (ours; the paper's own generator is not available):
+  * diffusion: 5-/7-point stencil; the coefficient of the face between two
+    cells is the harmonic mean of the cells' a; a boundary face uses the
+    cell's own a;
+  * convection: first-order upwind in advective form, per cell:
+    v_d > 0 adds v_d/h to the diagonal and -v_d/h to the (c, c-e_d) entry,
+    v_d < 0 adds |v_d|/h to the diagonal and -|v_d|/h to the (c, c+e_d) entry;
+    entries that would couple to a boundary node are dropped.
+The result is a non-singular M-matrix, weakly row diagonally dominant (strictly
+on rows next to the boundary).
+
+Random streams: numpy Generator(PCG64(seed)); draws in the order
+coefficient field a, then the velocity angle field, then right-hand sides.
+"""
+import numpy as np
+
+__all__ = ["Problem", "convdiff", "config_problem", "rhs"]
+
+
+class Problem:
+    """A CSR matrix plus the grid it lives on.
+
+    rowptr: int64[n+1], colind: int32[nnz] (sorted within a row),
+    val: float64[nnz], dims: tuple of grid sides (x fastest).
+    """
+
+    def __init__(self, dims, rowptr, colind, val, seed=None, name=""):
+        self.dims = tuple(int(d) for d in dims)
+        self.rowptr = rowptr
+        self.colind = colind
+        self.val = val
+        self.seed = seed
+        self.name = name
+
+    @property
+    def n(self):
+        return int(self.rowptr.shape[0] - 1)
+
+    @property
+    def nnz(self):
+        return int(self.colind.shape[0])
+
+    def to_dense(self):
+        A = np.zeros((self.n, self.n))
+        for r in range(self.n):
+            for e in range(self.rowptr[r], self.rowptr[r + 1]):
+                A[r, self.colind[e]] += self.val[e]
+        return A
+
+    def matvec(self, x):
+        """y = A x for x of shape (n,) or (n, k) (float64)."""
+        x = np.asarray(x, dtype=np.float64)
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        prod = self.val[:, None] * x.reshape(self.n, -1)[self.colind]
+        y = np.zeros((self.n, prod.shape[1]))
+        np.add.at(y, rows, prod)
+        return y.reshape(x.shape)
+
+
+def convdiff(dims, a, v):
+    """Assemble the upwinded convection-diffusion matrix.
+
+    dims: (nx, ny) or (nx, ny, nz); a: cell diffusion, shape dims[::-1]
+    flattened to (N,) in x-fastest order; v: velocity per cell, shape (N, d).
+    """
+    dims = tuple(int(d) for d in dims)
+    d = len(dims)
+    N = int(np.prod(dims))
+    n = dims[0]
+    assert all(s == n for s in dims), "cubic grids only"
+    h = 1.0 / (n + 1)
+    a = np.asarray(a, dtype=np.float64).reshape(N)
+    v = np.asarray(v, dtype=np.float64).reshape(N, d)
+    strides = [1]
+    for k in range(1, d):
+        strides.append(strides[-1] * dims[k - 1])
+    idx = np.arange(N)
+    coords = [(idx // strides[k]) % dims[k] for k in range(d)]
+    diag = np.zeros(N)
+    offd = {}  # (k, sign) -> coefficient array per row for neighbour c + sign*e_k
+    for k in range(d):
+        for sgn in (-1, 1):
+            offd[(k, sgn)] = np.zeros(N)
+    for k in range(d):
+        for sgn in (-1, 1):
+            inside = (coords[k] + sgn >= 0) & (coords[k] + sgn < dims[k])
+            nb = np.where(inside, idx + sgn * strides[k], idx)
+            an = a[nb]
+            face = np.where(inside, 2.0 * a * an / (a + an), a)
+            diag += face / (h * h)
+            offd[(k, sgn)] -= np.where(inside, face / (h * h), 0.0)
+        vk = v[:, k]
+        up = np.abs(vk) / h
+        diag += up
+        # v > 0: couple to c - e_k ; v < 0: couple to c + e_k
+        has_m = (vk > 0) & (coords[k] - 1 >= 0)
+        has_p = (vk < 0) & (coords[k] + 1 < dims[k])
+        offd[(k, -1)] -= np.where(has_m, up, 0.0)
+        offd[(k, 1)] -= np.where(has_p, up, 0.0)
+    rows, cols, vals = [idx], [idx], [diag]
+    for k in range(d):
+        for sgn in (-1, 1):
+            inside = (coords[k] + sgn >= 0) & (coords[k] + sgn < dims[k])
+            rows.append(idx[inside])
+            cols.append(idx[inside] + sgn * strides[k])
+            vals.append(offd[(k, sgn)][inside])
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int64)
+    return rowptr, cols.astype(np.int32), vals.astype(np.float64)
+
+
+def _uniform_a(rng, N):
+    return rng.uniform(0.1, 10.0, size=N)
+
+
+def config_problem(kind, n=None, seed=None):
+    """Build one of the named synthetic workloads.
+
+    kind:
+      "2d_uniform_a"  : a ~ U[0.1,10] per cell, v = (10, 10)   (64x64 default)
+      "2d_lognormal"  : a = exp(g), g ~ N(0,1); v = 50 (cos t, sin t),
+                        t ~ U[0, 2 pi) per cell                 (256x256 default)
+      "3d_uniform_a"  : a ~ U[0.1,10], v = 20 (1, 1, 1)         (32^3 default)
+    """
+    if kind == "2d_uniform_a":
+        n = 64 if n is None else n
+        seed = 1000 if seed is None else seed
+        rng = np.random.Generator(np.random.PCG64(seed))
+        N = n * n
+        a = _uniform_a(rng, N)
+        v = np.tile([10.0, 10.0], (N, 1))
+        dims = (n, n)
+    elif kind == "2d_lognormal":
+        n = 256 if n is None else n
+        seed = 2000 if seed is None else seed
+        rng = np.random.Generator(np.random.PCG64(seed))
+        N = n * n
+        a = np.exp(rng.standard_normal(N))
+        t = rng.uniform(0.0, 2.0 * np.pi, size=N)
+        v = 50.0 * np.stack([np.cos(t), np.sin(t)], axis=1)
+        dims = (n, n)
+    elif kind == "3d_uniform_a":
+        n = 32 if n is None else n
+        seed = 3000 if seed is None else seed
+        rng = np.random.Generator(np.random.PCG64(seed))
+        N = n ** 3
+        a = _uniform_a(rng, N)
+        v = np.tile([20.0, 20.0, 20.0], (N, 1))
+        dims = (n, n, n)
+    else:
+        raise ValueError(kind)
+    rowptr, colind, val = convdiff(dims, a, v)
+    p = Problem(dims, rowptr, colind, val, seed=seed, name=f"{kind}_{n}")
+    p.rng = rng
+    return p
+
+
+def rhs(problem, nrhs=1, seed=None):
+    """Right-hand sides, iid N(0,1), shape (n, nrhs) column-major in memory."""
+    if seed is None:
+        rng = problem.rng
+    else:
+        rng = np.random.Generator(np.random.PCG64(seed))
+    b = rng.standard_normal((nrhs, problem.n))
+    return np.asfortranarray(b.T)
