@@ -1,0 +1,202 @@
+/*
+ * spaqr.h — C ABI of the GB300 spaQR library (sparsified QR preconditioner).
+ *
+ * Method: Gnanasekaran & Darve, "Hierarchical Orthogonal Factorization:
+ * Sparse Square Matrices" (arXiv 2010.06807).  The library solves A x = b for a
+ * sparse, unsymmetric, full-rank A in R^{N x N} (Section 1) by
+ *   1. a geometric modified nested-dissection ordering (Section 2.3),
+ *   2. the spaQR factorisation Q^T A W^{-1} ~ I (Algorithm 2, Section 2.7):
+ *      block Householder QR of every separator (Section 2.4), block-diagonal
+ *      scaling (Section 2.5, "Scaling of Interfaces") and sparsification of
+ *      every interface by a column-pivoted QR truncated at eps (Sections 2.2,
+ *      2.5; rank rule of Section 4), merging interfaces level by level
+ *      (Section 2.6),
+ *   3. the application x = W^{-1} Q^T b of the stored factor sequence
+ *      (Section 2.7), used as a right preconditioner inside GMRES that stops at
+ *      ||b - A x||_2 / ||b||_2 <= tol (Section 4).
+ *
+ * Conventions (all entry points):
+ *   - Return value 0 is SPAQR_OK; errors are negative SPAQR_ERR_* codes.  No
+ *     C++ exception crosses this boundary.  spaqr_last_error() gives a
+ *     thread-local message for the last failure.
+ *   - Handles are opaque and owned by the library; the caller frees them with
+ *     the matching *_destroy function.  Input arrays are borrowed, never freed.
+ *   - Dense vectors / right-hand sides are column-major with a leading
+ *     dimension; they may live in host or device memory (detected with
+ *     cudaPointerGetAttributes).  Host buffers are copied through the device.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Calls return after the work on `stream` has
+ *     completed unless stated otherwise.
+ *   - Every numeric step runs in the library's CUDA kernels on the current
+ *     device; there is no CPU fallback.  The ordering is integer host work.
+ */
+#ifndef SPAQR_H
+#define SPAQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SPAQR_OK                 0
+#define SPAQR_ERR_INVALID_ARG   -1   /* bad pointer, size, stride or option */
+#define SPAQR_ERR_UNSUPPORTED   -2   /* e.g. no grid (hypergraph ordering is not built), scaling off */
+#define SPAQR_ERR_OOM           -3   /* device allocation failed */
+#define SPAQR_ERR_SINGULAR      -4   /* zero diagonal in an R_ss or R_pp factor */
+#define SPAQR_ERR_NOT_CONVERGED -5   /* GMRES hit maxit; X holds the last iterate */
+#define SPAQR_ERR_TIMEOUT       -6   /* reserved: a bounded device wait ran out */
+#define SPAQR_ERR_CUDA          -7   /* a CUDA runtime call failed */
+#define SPAQR_ERR_NO_DEVICE     -8   /* no CUDA device is visible */
+
+/* precision of the factorisation (GMRES and rank decisions are always FP64) */
+#define SPAQR_FP64 0
+
+/* Sparse matrix in CSR form, rows sorted, N x N.  rowptr has n+1 entries,
+ * colind/val have nnz entries.  If on_device != 0 the three arrays are device
+ * pointers, otherwise host pointers.  Borrowed for the duration of a call. */
+typedef struct {
+    int64_t n, nnz;
+    const int64_t* rowptr;
+    const int32_t* colind;
+    const double*  val;
+    int on_device;
+} spaqr_csr;
+
+/* Regular grid the matrix lives on (lexicographic numbering, x fastest).
+ * dim = 2 uses nx, ny; dim = 3 uses nx, ny, nz.  n must equal the product. */
+typedef struct {
+    int dim;
+    int nx, ny, nz;
+} spaqr_grid;
+
+/* Factorisation options.  eps: truncation tolerance of the rank-revealing QR
+ * (|R_ii| >= eps |R_11| is kept, Section 4), eps = 0 keeps everything.
+ * nlevels: 0 chooses ceil(log2(N/64)) (Section 4).  skip: number of levels
+ * (from the leaves) factored before scaling/sparsification starts.
+ * scaling must be 1 (the unscaled variant is not built).  precision: SPAQR_FP64.
+ * col_normalize: scale columns of A to unit 2-norm first (Section 2.7). */
+typedef struct {
+    double eps;
+    int nlevels;
+    int skip;
+    int scaling;
+    int precision;
+    int col_normalize;
+    void* stream;
+} spaqr_opts;
+
+/* Default options: eps 1e-2, nlevels 0, skip 2, scaling 1, FP64, normalise. */
+void spaqr_opts_default(spaqr_opts* o);
+
+typedef struct spaqr_ordering spaqr_ordering;
+typedef struct spaqr_factor_s spaqr_factor_t;
+
+/* Ordering summary (spaqr_ordering_info). */
+typedef struct {
+    int64_t n;          /* matrix size */
+    int64_t nnz;        /* nonzeros of the pattern */
+    int32_t nlevels;    /* L */
+    int32_t n_atoms;    /* finest interface clusters (incl. leaves) */
+    int32_t n_nodes;    /* nodes of the nested-dissection tree */
+    int64_t plan_len;   /* int32 entries of the encoded symbolic plan */
+} spaqr_ordering_info_t;
+
+/* Factor summary (spaqr_factor_info). */
+typedef struct {
+    int64_t n;
+    int32_t nlevels;
+    int32_t skip;
+    double  eps;
+    int64_t factor_bytes;      /* device bytes held by the factor */
+    int64_t solve_bytes;       /* algorithmic bytes one application reads (nrhs = 1) */
+    double  factor_flops;      /* algorithmic FP64 flops of the factorisation */
+    double  solve_flops;       /* algorithmic flops of one application per RHS */
+    int32_t n_interfaces_sparsified;
+    int64_t rank_sum;          /* sum of kept ranks over all sparsified interfaces */
+    int64_t size_sum;          /* sum of interface sizes before sparsification */
+    double  phase_ms[4];       /* factorize / scale / sparsify / merge, CUDA events */
+    int32_t top_size;          /* size of the root separator when it was factored */
+} spaqr_info;
+
+/* Last error message of the calling thread (never NULL). */
+const char* spaqr_last_error(void);
+
+/* Geometric modified nested dissection of the matrix pattern on grid g
+ * (Sections 2.1, 2.3): separators two grid planes thick (a vertex separator of
+ * G(A^T A) for 5/7-point stencils), interfaces from the cuts of descendant
+ * subdomains, cluster hierarchy, row order = column order.  Host-only integer
+ * work (a device pattern is copied to the host).  nlevels = 0 picks
+ * ceil(log2(N/64)).  g == NULL returns SPAQR_ERR_UNSUPPORTED (hypergraph
+ * ordering for general matrices is not built).  Also builds the symbolic plan:
+ * per level the active clusters, the block pattern with fill, the fronts and
+ * their processing order.  *out is owned by the caller
+ * (spaqr_ordering_destroy). */
+int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out);
+
+/* Sizes of the ordering's arrays. */
+int spaqr_ordering_info(const spaqr_ordering* ord, spaqr_ordering_info_t* info);
+
+/* Copy the ordering out: perm[new] = old index (n entries), atom_ptr
+ * (n_atoms+1 entries), atom_node (n_atoms entries, preorder id of the atom's
+ * nested-dissection node), node_level (n_nodes entries, 1 = root) and the
+ * encoded symbolic plan (plan_len int32).  Any pointer may be NULL to skip it.
+ * Plan encoding, per level k = 1..L:
+ *   level, n_clusters, cluster first-atom ids...,
+ *   n_fronts, then per front in processing order:
+ *     front id, colour, |R|, R ids..., |C|, C ids... */
+int spaqr_ordering_get(const spaqr_ordering* ord, int64_t* perm, int64_t* atom_ptr,
+                       int32_t* atom_node, int32_t* node_level, int32_t* plan);
+
+void spaqr_ordering_destroy(spaqr_ordering* ord);
+
+/* Numeric spaQR factorisation (Algorithm 2) of A with the ordering `ord`
+ * (same pattern).  A may be on host or device.  Runs on opts->stream and
+ * returns after the factor is complete.  The factor lives in device memory of
+ * the current device and is immutable afterwards, so concurrent
+ * spaqr_solve / spaqr_gmres calls on different streams may share it.
+ * Errors: INVALID_ARG, UNSUPPORTED (scaling = 0, precision != FP64), OOM,
+ * CUDA, NO_DEVICE. */
+int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts* opts,
+                 spaqr_factor_t** out);
+
+/* One application of the preconditioner, X = W^{-1} Q^T B (Section 2.7, in
+ * the original unknowns, column scaling undone).  B: n x nrhs with leading
+ * dimension ldb >= n; X: n x nrhs with ldx >= n.  B and X may alias only if
+ * they are the same pointer with the same leading dimension.  Host or device
+ * pointers (both on the same side).  Synchronous on `stream`.
+ * Errors: INVALID_ARG, SINGULAR, OOM, CUDA. */
+int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb,
+                double* X, int64_t ldx, void* stream);
+
+/* Right-preconditioned GMRES (Section 4) for the nrhs columns of B, each with
+ * its own Krylov space, using F as preconditioner and A (CSR, host or device)
+ * for products.  X on entry is the initial guess, on exit the solution.
+ * Converged when the explicitly recomputed ||b - A x||_2 / ||b||_2 <= tol.
+ * iters[c] and relres[c] (host arrays of nrhs entries, may be NULL) receive
+ * per-column iteration counts and final relative residuals.  maxit bounds the
+ * Krylov dimension (no restart).  Returns NOT_CONVERGED if any column missed
+ * tol (X holds the last iterate).  Synchronous on `stream`. */
+int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B,
+                int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
+                double* relres, void* stream);
+
+/* Summary and timings of a factor. */
+int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out);
+
+/* Per-level interface ranks: for level index k (0 = leaves) writes up to cap
+ * pairs (size before, kept rank) of the interfaces sparsified at that level,
+ * in ascending cluster order, and the count in *count.  Also the CPQR pivot
+ * norms |R_rr| (first rejected or last kept) and |R_11| per interface into
+ * margins[2*i], margins[2*i+1] if margins != NULL. */
+int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, double* margins,
+                       int cap, int* count);
+
+void spaqr_factor_destroy(spaqr_factor_t* F);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAQR_H */

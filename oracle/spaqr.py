@@ -21,7 +21,8 @@ Readings where the paper is silent (also in the design notes):
       subtrees; Theorem 2.1).  A front of separator s has rows
       R(s) = {i : block (i, s) exists} and columns C(s) = {j related to s :
       block (i, j) exists for some i in R(s)}; H_s^T is applied to those
-      columns only.
+      columns only.  R(s) and C(s) of every front of a level are taken from
+      the block pattern at the start of that level.
   F2  Fronts of one level that share a row cluster are ordered: colour the
       fronts greedily in ascending id (two fronts conflict when they share a
       row cluster), then process them by (colour, id).

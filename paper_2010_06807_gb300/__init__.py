@@ -1,0 +1,357 @@
+"""Python binding of libspaqr (GB300 spaQR): argument marshalling only.
+
+Every call goes through the C ABI declared in include/spaqr.h; every numeric
+step runs in the library's CUDA kernels.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA).  Dense right-hand sides are column-major
+(n x nrhs with unit row stride), e.g. ``torch.empty(nrhs, n).T`` or
+``np.asfortranarray``.
+
+The library is loaded on first use; if it is missing this raises, there is no
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "SpaqrError", "load_library", "spaqr_order", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
+    "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspaqr.so")
+
+SPAQR_OK = 0
+_ERRNAMES = {
+    -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED",
+    -6: "TIMEOUT", -7: "CUDA", -8: "NO_DEVICE",
+}
+
+
+class SpaqrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"spaqr error {code} ({_ERRNAMES.get(code, '?')}): {msg}")
+        self.code = code
+        self.name = _ERRNAMES.get(code, "?")
+
+
+class _CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("nlevels", ctypes.c_int), ("skip", ctypes.c_int),
+                ("scaling", ctypes.c_int), ("precision", ctypes.c_int), ("col_normalize", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class _OrdInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nlevels", ctypes.c_int32),
+                ("n_atoms", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("plan_len", ctypes.c_int64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nlevels", ctypes.c_int32), ("skip", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
+                ("solve_bytes", ctypes.c_int64), ("factor_flops", ctypes.c_double),
+                ("solve_flops", ctypes.c_double), ("n_interfaces_sparsified", ctypes.c_int32),
+                ("rank_sum", ctypes.c_int64), ("size_sum", ctypes.c_int64),
+                ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32)]
+
+
+_lib = None
+
+# every symbol include/spaqr.h declares
+EXPORTS = [
+    "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_ordering_info",
+    "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy",
+]
+
+
+def load_library(path=None):
+    """Load libspaqr.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libspaqr.so not built ({p}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.spaqr_last_error.restype = ctypes.c_char_p
+    lib.spaqr_opts_default.argtypes = [ctypes.POINTER(_Opts)]
+    lib.spaqr_opts_default.restype = None
+    lib.spaqr_order.argtypes = [ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), i32, ctypes.POINTER(vp)]
+    lib.spaqr_ordering_info.argtypes = [vp, ctypes.POINTER(_OrdInfo)]
+    lib.spaqr_ordering_get.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.spaqr_ordering_destroy.argtypes = [vp]
+    lib.spaqr_ordering_destroy.restype = None
+    if hasattr(lib, "spaqr_factor"):
+        lib.spaqr_factor.argtypes = [vp, ctypes.POINTER(_CSR), ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+        lib.spaqr_solve.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+        lib.spaqr_gmres.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
+        lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
+        lib.spaqr_factor_destroy.argtypes = [vp]
+        lib.spaqr_factor_destroy.restype = None
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SPAQR_OK:
+        raise SpaqrError(rc, _lib.spaqr_last_error().decode(errors="replace"))
+
+
+def num_levels(n):
+    """ceil(log2(N/64)), at least 1 (Section 4)."""
+    import math
+    if n <= 64:
+        return 1
+    return max(1, int(math.ceil(math.log2(n / 64.0) - 1e-12)))
+
+
+# ---------------------------------------------------------------------------
+# array marshalling
+# ---------------------------------------------------------------------------
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive, on_device) for a numpy array or torch tensor of dtype."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        if x.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x, bool(x.is_cuda)
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a, False
+
+
+def _make_csr(rowptr, colind, val=None):
+    rp, k1, d1 = _ptr(rowptr, np.int64)
+    ci, k2, d2 = _ptr(colind, np.int32)
+    keep = [k1, k2]
+    vv, d3 = None, d1
+    if val is not None:
+        vv, k3, d3 = _ptr(val, np.float64)
+        keep.append(k3)
+    if not (d1 == d2 == d3):
+        raise ValueError("CSR arrays must all be on the host or all on the device")
+    n = int(rowptr.shape[0]) - 1
+    nnz = int(colind.shape[0])
+    c = _CSR(n, nnz, rp, ci, vv, 1 if d1 else 0)
+    return c, keep
+
+
+def _dense_colmajor(x, n, name):
+    """(ptr, ld, nrhs, keepalive, on_device) for an n x nrhs column-major operand."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64")
+        if x.dim() == 1:
+            if x.stride(0) != 1:
+                raise ValueError(f"{name} must have unit stride")
+            return x.data_ptr(), n, 1, x, bool(x.is_cuda)
+        if x.shape[0] != n or x.stride(0) != 1:
+            raise ValueError(f"{name} must be n x nrhs column-major (stride(0) == 1)")
+        ld = x.stride(1) if x.shape[1] > 1 else n
+        return x.data_ptr(), ld, int(x.shape[1]), x, bool(x.is_cuda)
+    a = np.asarray(x)
+    if a.dtype != np.float64:
+        raise TypeError(f"{name} must be float64")
+    if a.ndim == 1:
+        a = a.reshape(n, 1)
+    if a.shape[0] != n or not a.flags.f_contiguous:
+        raise ValueError(f"{name} must be a Fortran-ordered n x nrhs float64 array")
+    return a.ctypes.data, n, int(a.shape[1]), a, False
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# ordering
+# ---------------------------------------------------------------------------
+
+class Ordering:
+    """Owns a spaqr_ordering handle."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        info = _OrdInfo()
+        _check(_lib.spaqr_ordering_info(self._h, ctypes.byref(info)))
+        self.n = info.n
+        self.nnz = info.nnz
+        self.L = info.nlevels
+        self.n_atoms = info.n_atoms
+        self.n_nodes = info.n_nodes
+        self.plan_len = info.plan_len
+
+    def arrays(self):
+        perm = np.zeros(self.n, dtype=np.int64)
+        atom_ptr = np.zeros(self.n_atoms + 1, dtype=np.int64)
+        atom_node = np.zeros(self.n_atoms, dtype=np.int32)
+        node_level = np.zeros(self.n_nodes, dtype=np.int32)
+        plan = np.zeros(self.plan_len, dtype=np.int32)
+        _check(_lib.spaqr_ordering_get(self._h, perm.ctypes.data, atom_ptr.ctypes.data,
+                                       atom_node.ctypes.data, node_level.ctypes.data, plan.ctypes.data))
+        return dict(perm=perm, atom_ptr=atom_ptr, atom_node=atom_node, node_level=node_level, plan=plan)
+
+    def plan(self):
+        """Decode the symbolic plan: list of per-level dicts."""
+        code = self.arrays()["plan"].tolist()
+        out = []
+        i = 0
+        while i < len(code):
+            lev = code[i]; ncl = code[i + 1]; i += 2
+            cl = code[i:i + ncl]; i += ncl
+            nf = code[i]; i += 1
+            fronts = []
+            for _ in range(nf):
+                s, col, nr = code[i], code[i + 1], code[i + 2]; i += 3
+                R = code[i:i + nr]; i += nr
+                nc = code[i]; i += 1
+                C = code[i:i + nc]; i += nc
+                fronts.append(dict(id=s, colour=col, R=R, C=C))
+            out.append(dict(level=lev, clusters=cl, fronts=fronts))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.spaqr_ordering_destroy(h)
+            self._h = None
+
+
+def spaqr_order(rowptr, colind, dims, nlevels=0):
+    """Geometric modified nested dissection + symbolic plan (spaqr_order)."""
+    load_library()
+    csr, keep = _make_csr(rowptr, colind)
+    dims = tuple(int(d) for d in dims)
+    g = _Grid(len(dims), dims[0], dims[1], dims[2] if len(dims) > 2 else 1)
+    h = ctypes.c_void_p()
+    _check(_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), int(nlevels), ctypes.byref(h)))
+    return Ordering(h.value)
+
+
+# ---------------------------------------------------------------------------
+# factor / solve / gmres
+# ---------------------------------------------------------------------------
+
+class Factor:
+    """Owns a spaqr_factor_t handle."""
+
+    def __init__(self, handle, n):
+        self._h = ctypes.c_void_p(handle)
+        self.n = n
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.spaqr_factor_destroy(h)
+            self._h = None
+
+
+def spaqr_factor(ordering, rowptr, colind, val, eps=1e-2, nlevels=0, skip=2, scaling=1,
+                 col_normalize=1, stream=None):
+    """Numeric spaQR factorisation (Algorithm 2) on the current CUDA device."""
+    load_library()
+    csr, keep = _make_csr(rowptr, colind, val)
+    o = _Opts()
+    _lib.spaqr_opts_default(ctypes.byref(o))
+    o.eps = float(eps)
+    o.nlevels = int(nlevels)
+    o.skip = int(skip)
+    o.scaling = int(scaling)
+    o.col_normalize = int(col_normalize)
+    o.stream = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    _check(_lib.spaqr_factor(ordering._h, ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))
+    return Factor(h.value, csr.n)
+
+
+def spaqr_solve(F, B, X=None, stream=None):
+    """X = M^{-1} B (one application of the factor).  Returns X."""
+    load_library()
+    bp, ldb, nrhs, kb, bdev = _dense_colmajor(B, F.n, "B")
+    if X is None:
+        if bdev:
+            import torch
+            X = torch.empty(nrhs, F.n, dtype=torch.float64, device=B.device).T
+            if B.dim() == 1:
+                X = X[:, 0]
+        else:
+            X = np.zeros((F.n, nrhs), order="F")
+            if np.asarray(B).ndim == 1:
+                X = X[:, 0]
+    xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
+    if nrx != nrhs or xdev != bdev:
+        raise ValueError("X must match B in shape and memory space")
+    _check(_lib.spaqr_solve(F._h, nrhs, bp, ldb, xp, ldx, _stream_ptr(stream)))
+    return X
+
+
+def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=None):
+    """Right-preconditioned GMRES; returns (X, iters[nrhs], relres[nrhs]).
+
+    Raises SpaqrError(NOT_CONVERGED) if a column misses tol.
+    """
+    load_library()
+    csr, keep = _make_csr(rowptr, colind, val)
+    bp, ldb, nrhs, kb, bdev = _dense_colmajor(B, F.n, "B")
+    if X is None:
+        if bdev:
+            import torch
+            X = torch.zeros(nrhs, F.n, dtype=torch.float64, device=B.device).T
+            if B.dim() == 1:
+                X = X[:, 0]
+        else:
+            X = np.zeros((F.n, nrhs), order="F")
+            if np.asarray(B).ndim == 1:
+                X = X[:, 0]
+    xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs, dtype=np.float64)
+    _check(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
+                            iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)))
+    return X, iters, relres
+
+
+def spaqr_factor_info(F):
+    load_library()
+    info = _Info()
+    _check(_lib.spaqr_factor_info(F._h, ctypes.byref(info)))
+    return {f: (list(getattr(info, f)) if f == "phase_ms" else getattr(info, f)) for f, _ in _Info._fields_}
+
+
+def spaqr_factor_ranks(F, level):
+    """[(size_before, rank)], margins [(|R_rr| first rejected or last kept, |R_11|)] of a level."""
+    load_library()
+    cnt = ctypes.c_int(0)
+    _check(_lib.spaqr_factor_ranks(F._h, int(level), None, None, 0, ctypes.byref(cnt)))
+    n = cnt.value
+    pairs = np.zeros(2 * max(n, 1), dtype=np.int32)
+    margins = np.zeros(2 * max(n, 1), dtype=np.float64)
+    _check(_lib.spaqr_factor_ranks(F._h, int(level), pairs.ctypes.data, margins.ctypes.data, n,
+                                   ctypes.byref(cnt)))
+    return pairs[:2 * n].reshape(n, 2), margins[:2 * n].reshape(n, 2)

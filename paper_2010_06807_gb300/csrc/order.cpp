@@ -1,0 +1,514 @@
+// Geometric modified nested dissection and the symbolic spaQR plan (host).
+//
+// Paper: Section 2.1 (nested dissection on G(A^T A) gives the column
+// partition), Section 2.3 (modified nested dissection: the recursion on
+// interior + boundary splits separators into interfaces; rows ordered like
+// columns for diagonally dominant matrices), Section 2.6 (merge along the
+// cluster hierarchy), Section 4 (L = ceil(log2(N/64))).
+//
+// Readings where the paper is silent:
+//  * a separator of G(A^T A) for 5/7-point stencils is two grid planes thick;
+//  * cut the longest extent (ties x, y, z) at m = lo + max(0, (ext-2)/2);
+//    separator planes [m, m+2), children [lo, m) and [m+2, hi);
+//  * the cut of a non-leaf descendant box D splits separator S of box B when D
+//    touches S along B's cut dimension and D cuts a tangent dimension; it
+//    applies to the nodes of S that, in the remaining tangent dimension(s), lie
+//    within D's extent widened by two planes; it classifies them as below,
+//    inside or above D's slab;
+//  * interfaces after eliminating level l are the classes under cuts of depth
+//    <= l-1, the merge after level l removes depth l-1 cuts;
+//  * order: nodes by level (leaves first), then preorder; inside a separator
+//    atoms in hierarchical order (coarser classes first, classes by their
+//    smallest grid index); inside an atom by grid index.
+//  * blocks exist only between clusters whose nodes are equal or ancestor /
+//    descendant (Section 2.1, Theorem 2.1); a front's rows R(s) are the
+//    clusters with a block in column s, its columns C(s) the related clusters
+//    with a block in a row of R(s), both taken at the start of the level;
+//    fronts sharing a row cluster are ordered by a greedy colouring.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+#include <unordered_map>
+
+#include "spaqr_internal.h"
+
+namespace spaqr {
+
+int num_levels(int64_t n) {
+    if (n <= 64) return 1;
+    double v = std::log2((double)n / 64.0);
+    int L = (int)std::ceil(v - 1e-12);
+    return L < 1 ? 1 : L;
+}
+
+int StepPlan::find(int i, int j) const {
+    auto b = rowidx.begin() + colptr[j], e = rowidx.begin() + colptr[j + 1];
+    auto it = std::lower_bound(b, e, i);
+    if (it == e || *it != i) return -1;
+    return (int)(it - rowidx.begin());
+}
+
+namespace {
+
+struct Builder {
+    int dim;
+    int dims[3];
+    int L;
+    std::vector<NDNode> nodes;
+
+    int build(const int* lo, const int* hi, int depth, int parent) {
+        int id = (int)nodes.size();
+        nodes.push_back(NDNode());
+        {
+            NDNode& nd = nodes[id];
+            nd.id = id;
+            nd.depth = depth;
+            nd.parent = parent;
+            for (int k = 0; k < 3; k++) { nd.lo[k] = lo[k]; nd.hi[k] = hi[k]; }
+        }
+        if (depth < L - 1) {
+            int ext[3];
+            for (int k = 0; k < 3; k++) ext[k] = hi[k] - lo[k];
+            int c = 0;
+            for (int k = 1; k < dim; k++)
+                if (ext[k] > ext[c]) c = k;
+            int m = lo[c] + (ext[c] >= 2 ? (ext[c] - 2) / 2 : 0);
+            int llo[3], lhi[3], rlo[3], rhi[3];
+            for (int k = 0; k < 3; k++) { llo[k] = lo[k]; lhi[k] = hi[k]; rlo[k] = lo[k]; rhi[k] = hi[k]; }
+            lhi[c] = m;
+            rlo[c] = std::min(m + 2, hi[c]);
+            int l = build(llo, lhi, depth + 1, id);
+            int r = build(rlo, rhi, depth + 1, id);
+            NDNode& nd = nodes[id];
+            nd.cut_dim = c;
+            nd.cut_m = m;
+            nd.left = l;
+            nd.right = r;
+            nd.size = 1 + nodes[l].size + nodes[r].size;
+        }
+        return id;
+    }
+};
+
+struct Key {
+    int depth, node, k;
+    bool operator==(const Key& o) const { return depth == o.depth && node == o.node && k == o.k; }
+    bool operator!=(const Key& o) const { return !(*this == o); }
+};
+
+bool prefix_equal(const std::vector<Key>& a, const std::vector<Key>& b, int stage) {
+    size_t i = 0, j = 0;
+    while (true) {
+        while (i < a.size() && a[i].depth > stage) i++;
+        while (j < b.size() && b[j].depth > stage) j++;
+        if (i == a.size() || j == b.size()) return i == a.size() && j == b.size();
+        if (a[i] != b[j]) return false;
+        i++;
+        j++;
+    }
+}
+
+}  // namespace
+
+int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz, int dim,
+                   const int* dims, int nlevels, Ordering& o) {
+    if (dim != 2 && dim != 3) { set_error("grid dim must be 2 or 3"); return SPAQR_ERR_INVALID_ARG; }
+    int64_t N = 1;
+    for (int k = 0; k < dim; k++) {
+        if (dims[k] < 1) { set_error("grid sides must be >= 1"); return SPAQR_ERR_INVALID_ARG; }
+        N *= dims[k];
+    }
+    if (N != n) { set_error("grid size does not match matrix size"); return SPAQR_ERR_INVALID_ARG; }
+    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+    o.dim = dim;
+    for (int k = 0; k < 3; k++) o.dims[k] = k < dim ? dims[k] : 1;
+    o.n = n;
+    o.nnz = nnz;
+    o.L = nlevels > 0 ? nlevels : num_levels(n);
+    const int L = o.L;
+
+    Builder b;
+    b.dim = dim;
+    for (int k = 0; k < 3; k++) b.dims[k] = o.dims[k];
+    b.L = L;
+    int lo0[3] = {0, 0, 0}, hi0[3] = {o.dims[0], o.dims[1], o.dims[2]};
+    b.build(lo0, hi0, 0, -1);
+    o.nodes = b.nodes;
+    const std::vector<NDNode>& nodes = o.nodes;
+    const int nn = (int)nodes.size();
+    const int64_t stride[3] = {1, o.dims[0], (int64_t)o.dims[0] * o.dims[1]};
+
+    // ---- atoms of every node -------------------------------------------
+    struct Atom { std::vector<int64_t> pts; std::vector<Key> key; };
+    std::vector<std::vector<Atom>> node_atoms(nn);
+    for (int id = 0; id < nn; id++) {
+        const NDNode& nd = nodes[id];
+        int lo[3], hi[3];
+        for (int k = 0; k < 3; k++) { lo[k] = nd.lo[k]; hi[k] = nd.hi[k]; }
+        if (nd.cut_dim >= 0) {
+            lo[nd.cut_dim] = nd.cut_m;
+            hi[nd.cut_dim] = std::min(nd.cut_m + 2, nd.hi[nd.cut_dim]);
+        }
+        bool empty = false;
+        for (int k = 0; k < 3; k++) if (hi[k] <= lo[k]) empty = true;
+        if (empty) continue;
+        // points in index order (x fastest)
+        std::vector<std::array<int, 3>> pts;
+        for (int z = lo[2]; z < hi[2]; z++)
+            for (int y = lo[1]; y < hi[1]; y++)
+                for (int x = lo[0]; x < hi[0]; x++) pts.push_back({x, y, z});
+        const size_t np = pts.size();
+        std::vector<int64_t> gidx(np);
+        for (size_t i = 0; i < np; i++)
+            gidx[i] = pts[i][0] * stride[0] + pts[i][1] * stride[1] + pts[i][2] * stride[2];
+        if (nd.cut_dim < 0) {
+            Atom a;
+            a.pts = gidx;
+            node_atoms[id].push_back(std::move(a));
+            continue;
+        }
+        const int c = nd.cut_dim;
+        const int left_hi = nodes[nd.left].hi[c];
+        const int right_lo = nodes[nd.right].lo[c];
+        std::vector<int> cuts;
+        for (int d = id + 1; d < id + nd.size; d++) {
+            const NDNode& D = nodes[d];
+            if (D.cut_dim < 0 || D.cut_dim == c) continue;
+            bool dempty = false;
+            for (int k = 0; k < 3; k++) if (D.hi[k] <= D.lo[k]) dempty = true;
+            if (dempty) continue;
+            if (!(D.hi[c] == left_hi || D.lo[c] == right_lo)) continue;
+            cuts.push_back(d);
+        }
+        std::sort(cuts.begin(), cuts.end(), [&](int a, int bb) {
+            if (nodes[a].depth != nodes[bb].depth) return nodes[a].depth < nodes[bb].depth;
+            return a < bb;
+        });
+        std::vector<std::vector<Key>> keys(np);
+        for (int d : cuts) {
+            const NDNode& D = nodes[d];
+            const int cd = D.cut_dim;
+            for (size_t i = 0; i < np; i++) {
+                bool ok = true;
+                for (int e = 0; e < dim; e++) {
+                    if (e == c || e == cd) continue;
+                    if (pts[i][e] < D.lo[e] - 2 || pts[i][e] >= D.hi[e] + 2) { ok = false; break; }
+                }
+                if (!ok) continue;
+                int v = pts[i][cd];
+                int kv = v < D.cut_m ? 0 : (v < D.cut_m + 2 ? 1 : 2);
+                keys[i].push_back(Key{D.depth, d, kv});
+            }
+        }
+        // hierarchical order: per stage depth, the smallest grid index of the class
+        std::vector<int> depths;
+        for (int d : cuts) depths.push_back(nodes[d].depth);
+        std::sort(depths.begin(), depths.end());
+        depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
+        std::vector<std::vector<int64_t>> scol(depths.size(), std::vector<int64_t>(np));
+        for (size_t si = 0; si < depths.size(); si++) {
+            int s = depths[si];
+            std::map<std::vector<std::tuple<int, int, int>>, int64_t> minidx;
+            std::vector<std::vector<std::tuple<int, int, int>>> cls(np);
+            for (size_t i = 0; i < np; i++) {
+                for (const Key& kk : keys[i])
+                    if (kk.depth <= s) cls[i].push_back(std::make_tuple(kk.depth, kk.node, kk.k));
+                auto it = minidx.find(cls[i]);
+                if (it == minidx.end() || gidx[i] < it->second) minidx[cls[i]] = gidx[i];
+            }
+            for (size_t i = 0; i < np; i++) scol[si][i] = minidx[cls[i]];
+        }
+        std::vector<size_t> ord(np);
+        for (size_t i = 0; i < np; i++) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t bb) {
+            for (size_t si = 0; si < depths.size(); si++)
+                if (scol[si][a] != scol[si][bb]) return scol[si][a] < scol[si][bb];
+            return gidx[a] < gidx[bb];
+        });
+        for (size_t t = 0; t < np; t++) {
+            size_t i = ord[t];
+            if (node_atoms[id].empty() || node_atoms[id].back().key != keys[i]) {
+                Atom a;
+                a.key = keys[i];
+                node_atoms[id].push_back(std::move(a));
+            }
+            node_atoms[id].back().pts.push_back(gidx[i]);
+        }
+    }
+
+    // ---- global order ----------------------------------------------------
+    std::vector<int> norder(nn);
+    for (int i = 0; i < nn; i++) norder[i] = i;
+    std::sort(norder.begin(), norder.end(), [&](int a, int bb) {
+        if (nodes[a].depth != nodes[bb].depth) return nodes[a].depth > nodes[bb].depth;
+        return a < bb;
+    });
+    o.perm.clear();
+    o.atom_ptr.assign(1, 0);
+    o.atom_node.clear();
+    std::vector<std::vector<Key>> atom_keys;
+    for (int id : norder) {
+        for (Atom& a : node_atoms[id]) {
+            for (int64_t g : a.pts) o.perm.push_back(g);
+            o.atom_ptr.push_back((int64_t)o.perm.size());
+            o.atom_node.push_back(id);
+            atom_keys.push_back(a.key);
+        }
+    }
+    if ((int64_t)o.perm.size() != n) { set_error("ordering lost points"); return SPAQR_ERR_INVALID_ARG; }
+    const int na = (int)o.atom_node.size();
+    o.iperm.assign(n, 0);
+    for (int64_t i = 0; i < n; i++) o.iperm[o.perm[i]] = i;
+    o.atom_of.assign(n, 0);
+    for (int a = 0; a < na; a++)
+        for (int64_t i = o.atom_ptr[a]; i < o.atom_ptr[a + 1]; i++) o.atom_of[i] = a;
+
+    auto stage_first = [&](int stage) {
+        std::vector<int> f(na);
+        for (int a = 0; a < na; a++) {
+            if (a > 0 && o.atom_node[a] == o.atom_node[a - 1] &&
+                prefix_equal(atom_keys[a], atom_keys[a - 1], stage))
+                f[a] = f[a - 1];
+            else
+                f[a] = a;
+        }
+        return f;
+    };
+
+    // ---- pattern copies, CSC traversal ------------------------------------
+    o.rowptr.assign(rowptr, rowptr + n + 1);
+    o.colind.assign(colind, colind + nnz);
+    for (int64_t e = 0; e < nnz; e++)
+        if (colind[e] < 0 || colind[e] >= n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    o.csc_ptr.assign(n + 1, 0);
+    for (int64_t e = 0; e < nnz; e++) o.csc_ptr[colind[e] + 1]++;
+    for (int64_t i = 0; i < n; i++) o.csc_ptr[i + 1] += o.csc_ptr[i];
+    o.csc_entry.assign(nnz, 0);
+    {
+        std::vector<int64_t> fill(o.csc_ptr.begin(), o.csc_ptr.end() - 1);
+        for (int64_t r = 0; r < n; r++)
+            for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) o.csc_entry[fill[colind[e]]++] = e;
+    }
+
+    // ---- symbolic plan -------------------------------------------------
+    std::set<std::pair<int, int>> P;  // (row cluster, col cluster) by first atom
+    for (int64_t r = 0; r < n; r++) {
+        int ar = o.atom_of[o.iperm[r]];
+        for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
+            int ac = o.atom_of[o.iperm[colind[e]]];
+            if (!o.related(o.atom_node[ar], o.atom_node[ac])) {
+                set_error("matrix pattern couples separated subdomains (not a 5/7-point stencil on this grid?)");
+                return SPAQR_ERR_UNSUPPORTED;
+            }
+            P.insert({ar, ac});
+        }
+    }
+    std::vector<int> active(na);
+    std::vector<int> cnode(na), cend(na);
+    for (int a = 0; a < na; a++) { active[a] = a; cnode[a] = o.atom_node[a]; cend[a] = a + 1; }
+    o.steps.clear();
+    o.plan_code.clear();
+    for (int k = 1; k <= L; k++) {
+        const int lev = L - k + 1;
+        StepPlan sp;
+        sp.level = lev;
+        sp.cl = active;  // sorted
+        const int ncl = (int)active.size();
+        std::unordered_map<int, int> idx;
+        for (int i = 0; i < ncl; i++) idx[active[i]] = i;
+        sp.cl_node.resize(ncl);
+        sp.is_front.assign(ncl, 0);
+        for (int i = 0; i < ncl; i++) {
+            sp.cl_node[i] = cnode[active[i]];
+            if (nodes[sp.cl_node[i]].depth + 1 == lev) sp.is_front[i] = 1;
+        }
+        std::vector<std::vector<int>> col_rows(ncl), row_cols(ncl);
+        for (auto& pr : P) {
+            int i = idx.at(pr.first), j = idx.at(pr.second);
+            col_rows[j].push_back(i);
+            row_cols[i].push_back(j);
+        }
+        std::vector<int> fr;
+        for (int i = 0; i < ncl; i++) if (sp.is_front[i]) fr.push_back(i);
+        {
+            std::set<int> seen;
+            for (int f : fr) {
+                if (seen.count(sp.cl_node[f])) { set_error("separator not merged at its level"); return SPAQR_ERR_INVALID_ARG; }
+                seen.insert(sp.cl_node[f]);
+            }
+        }
+        std::vector<std::vector<int>> Rf(fr.size()), Cf(fr.size());
+        for (size_t t = 0; t < fr.size(); t++) {
+            int s = fr[t];
+            Rf[t] = col_rows[s];  // ascending (set order)
+            std::set<int> cs;
+            for (int i : Rf[t])
+                for (int j : row_cols[i])
+                    if (o.related(sp.cl_node[j], sp.cl_node[s])) cs.insert(j);
+            Cf[t].assign(cs.begin(), cs.end());
+            if (Rf[t].empty() || Rf[t][0] != s || Cf[t][0] != s) {
+                set_error("front without its diagonal block");
+                return SPAQR_ERR_SINGULAR;
+            }
+        }
+        // greedy colouring in ascending id: conflict = a shared row cluster
+        std::vector<int> col(fr.size(), 0);
+        for (size_t t = 0; t < fr.size(); t++) {
+            std::set<int> used;
+            std::vector<char> mine(ncl, 0);
+            for (int i : Rf[t]) mine[i] = 1;
+            for (size_t u = 0; u < t; u++) {
+                bool share = false;
+                for (int i : Rf[u]) if (mine[i]) { share = true; break; }
+                if (share) used.insert(col[u]);
+            }
+            int c = 0;
+            while (used.count(c)) c++;
+            col[t] = c;
+        }
+        std::vector<size_t> seq(fr.size());
+        for (size_t t = 0; t < fr.size(); t++) seq[t] = t;
+        std::stable_sort(seq.begin(), seq.end(), [&](size_t a, size_t bb) {
+            if (col[a] != col[bb]) return col[a] < col[bb];
+            return fr[a] < fr[bb];
+        });
+        for (size_t t : seq) {
+            sp.fronts.push_back(fr[t]);
+            sp.colour.push_back(col[t]);
+            sp.R.push_back(Rf[t]);
+            sp.C.push_back(Cf[t]);
+        }
+        // fill of this level
+        for (size_t t = 0; t < fr.size(); t++)
+            for (int i : Rf[t])
+                for (int j : Cf[t]) P.insert({active[i], active[j]});
+        // CSC of the pattern with fill
+        sp.colptr.assign(ncl + 1, 0);
+        for (auto& pr : P) sp.colptr[idx.at(pr.second) + 1]++;
+        for (int j = 0; j < ncl; j++) sp.colptr[j + 1] += sp.colptr[j];
+        sp.rowidx.assign(sp.colptr[ncl], 0);
+        {
+            std::vector<int> fillp(sp.colptr.begin(), sp.colptr.end() - 1);
+            // P iterates by row then column; rows ascending within each column
+            for (auto& pr : P) sp.rowidx[fillp[idx.at(pr.second)]++] = idx.at(pr.first);
+        }
+        // encode
+        o.plan_code.push_back(lev);
+        o.plan_code.push_back(ncl);
+        for (int i = 0; i < ncl; i++) o.plan_code.push_back(active[i]);
+        o.plan_code.push_back((int)sp.fronts.size());
+        for (size_t t = 0; t < sp.fronts.size(); t++) {
+            o.plan_code.push_back(active[sp.fronts[t]]);
+            o.plan_code.push_back(sp.colour[t]);
+            o.plan_code.push_back((int)sp.R[t].size());
+            for (int i : sp.R[t]) o.plan_code.push_back(active[i]);
+            o.plan_code.push_back((int)sp.C[t].size());
+            for (int j : sp.C[t]) o.plan_code.push_back(active[j]);
+        }
+        // eliminate the fronts
+        for (auto it = P.begin(); it != P.end();) {
+            if (sp.is_front[idx.at(it->first)] || sp.is_front[idx.at(it->second)]) it = P.erase(it);
+            else ++it;
+        }
+        std::vector<int> rest;
+        for (int i = 0; i < ncl; i++) if (!sp.is_front[i]) rest.push_back(active[i]);
+        sp.parent.assign(ncl, -1);
+        if (k < L && !rest.empty()) {
+            std::vector<int> f = stage_first(L - k - 1);
+            std::map<int, int> newid;  // parent first atom -> new end
+            for (int c : rest) {
+                int g = f[c];
+                if (f[cend[c] - 1] != g) { set_error("merge hierarchy not nested"); return SPAQR_ERR_INVALID_ARG; }
+                auto it = newid.find(g);
+                if (it == newid.end()) newid[g] = cend[c];
+                else it->second = std::max(it->second, cend[c]);
+            }
+            std::vector<int> nxt;
+            for (auto& kv : newid) nxt.push_back(kv.first);
+            std::unordered_map<int, int> nidx;
+            for (size_t i = 0; i < nxt.size(); i++) nidx[nxt[i]] = (int)i;
+            for (int i = 0; i < ncl; i++)
+                if (!sp.is_front[i]) sp.parent[i] = nidx.at(f[active[i]]);
+            sp.n_next = (int)nxt.size();
+            std::set<std::pair<int, int>> P2;
+            for (auto& pr : P) P2.insert({f[pr.first], f[pr.second]});
+            P.swap(P2);
+            for (int g : nxt) {
+                cnode[g] = o.atom_node[g];
+                cend[g] = newid[g];
+            }
+            active = nxt;
+        } else {
+            active = rest;
+        }
+        o.steps.push_back(std::move(sp));
+    }
+    if (!active.empty() || !P.empty()) { set_error("plan left active clusters"); return SPAQR_ERR_INVALID_ARG; }
+
+    // ---- gather map into the level-1 arena --------------------------------
+    {
+        const StepPlan& s1 = o.steps[0];
+        const int ncl = (int)s1.cl.size();  // == na
+        std::vector<int64_t> H(ncl, 0), poff(ncl + 1, 0), rowoff(s1.rowidx.size());
+        for (int j = 0; j < ncl; j++) {
+            int64_t h = 0;
+            for (int e = s1.colptr[j]; e < s1.colptr[j + 1]; e++) {
+                rowoff[e] = h;
+                int i = s1.rowidx[e];
+                h += o.atom_ptr[i + 1] - o.atom_ptr[i];
+            }
+            H[j] = h;
+            poff[j + 1] = poff[j] + h * (o.atom_ptr[j + 1] - o.atom_ptr[j]);
+        }
+        o.arena1_size = poff[ncl];
+        o.gather_off.assign(nnz, 0);
+        for (int64_t r = 0; r < n; r++) {
+            int64_t nr = o.iperm[r];
+            int ar = o.atom_of[nr];
+            for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
+                int64_t nc = o.iperm[colind[e]];
+                int ac = o.atom_of[nc];
+                int pos = s1.find(ar, ac);
+                o.gather_off[e] = poff[ac] + rowoff[pos] + (nr - o.atom_ptr[ar]) +
+                                  (nc - o.atom_ptr[ac]) * H[ac];
+            }
+        }
+    }
+    return SPAQR_OK;
+}
+
+}  // namespace spaqr
+
+// ---------------------------------------------------------------------------
+// C ABI: ordering
+// ---------------------------------------------------------------------------
+
+extern "C" int spaqr_ordering_info(const spaqr_ordering* ord, spaqr_ordering_info_t* info) {
+    if (!ord || !info) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    info->n = ord->o.n;
+    info->nnz = ord->o.nnz;
+    info->nlevels = ord->o.L;
+    info->n_atoms = (int32_t)ord->o.atom_node.size();
+    info->n_nodes = (int32_t)ord->o.nodes.size();
+    info->plan_len = (int64_t)ord->o.plan_code.size();
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_ordering_get(const spaqr_ordering* ord, int64_t* perm, int64_t* atom_ptr,
+                                  int32_t* atom_node, int32_t* node_level, int32_t* plan) {
+    if (!ord) { spaqr::set_error("null ordering"); return SPAQR_ERR_INVALID_ARG; }
+    const spaqr::Ordering& o = ord->o;
+    if (perm) std::memcpy(perm, o.perm.data(), sizeof(int64_t) * o.perm.size());
+    if (atom_ptr) std::memcpy(atom_ptr, o.atom_ptr.data(), sizeof(int64_t) * o.atom_ptr.size());
+    if (atom_node) std::memcpy(atom_node, o.atom_node.data(), sizeof(int32_t) * o.atom_node.size());
+    if (node_level)
+        for (size_t i = 0; i < o.nodes.size(); i++) node_level[i] = o.nodes[i].depth + 1;
+    if (plan) std::memcpy(plan, o.plan_code.data(), sizeof(int32_t) * o.plan_code.size());
+    return SPAQR_OK;
+}
+
+extern "C" void spaqr_ordering_destroy(spaqr_ordering* ord) { delete ord; }

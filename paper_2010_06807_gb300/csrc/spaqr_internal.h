@@ -1,0 +1,83 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/spaqr.h"
+
+namespace spaqr {
+
+void set_error(const std::string& msg);
+
+// ---------------------------------------------------------------------------
+// Ordering and symbolic plan (host, integer).  Built once per pattern.
+// ---------------------------------------------------------------------------
+
+struct NDNode {
+    int id = 0, depth = 0, parent = -1, left = -1, right = -1;
+    int cut_dim = -1, cut_m = -1, size = 1;  // size = preorder subtree size
+    int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+};
+
+// One level of Algorithm 2 in symbolic form.  Cluster "indices" below are
+// positions in `cl` (the active clusters at the start of the level, ascending
+// by first atom).
+struct StepPlan {
+    int level = 0;
+    std::vector<int> cl;        // first atom of every active cluster
+    std::vector<int> cl_node;   // nested-dissection node of every cluster
+    std::vector<char> is_front; // factored at this level
+    // block pattern including this level's fill, CSC over cluster indices:
+    // column j holds rows rowidx[colptr[j] .. colptr[j+1]) (ascending)
+    std::vector<int> colptr, rowidx;
+    // fronts in processing order (colour, id)
+    std::vector<int> fronts, colour;
+    std::vector<std::vector<int>> R, C;   // per front (same order), cluster indices
+    // merge: for every non-front cluster, its parent index in the next level's
+    // cl (-1 when there is no next level)
+    std::vector<int> parent;
+    int n_next = 0;
+    // position of block (i, j) within the CSC arrays: lookup helper
+    int find(int i, int j) const;
+};
+
+struct Ordering {
+    int dim = 2;
+    int dims[3] = {1, 1, 1};
+    int64_t n = 0, nnz = 0;
+    int L = 1;
+    std::vector<NDNode> nodes;
+    std::vector<int64_t> perm;       // new -> old
+    std::vector<int64_t> iperm;      // old -> new
+    std::vector<int64_t> atom_ptr;
+    std::vector<int32_t> atom_node;
+    std::vector<int32_t> atom_of;    // new index -> atom
+    std::vector<StepPlan> steps;
+    // pattern copies for the numeric phase
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colind;
+    // CSC traversal of the CSR entries (deterministic column sums)
+    std::vector<int64_t> csc_ptr;    // n + 1
+    std::vector<int64_t> csc_entry;  // nnz: CSR entry index, rows ascending per column
+    // CSR entry -> offset in the level-1 block arena (column panels)
+    std::vector<int64_t> gather_off;
+    int64_t arena1_size = 0;
+    std::vector<int32_t> plan_code;  // encoded plan (spaqr_ordering_get)
+    bool related(int na, int nb) const {
+        if (na > nb) { int t = na; na = nb; nb = t; }
+        return nb < na + nodes[na].size;
+    }
+};
+
+int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
+                   int dim, const int* dims, int nlevels, Ordering& out);
+
+int num_levels(int64_t n);
+
+}  // namespace spaqr
+
+struct spaqr_ordering {
+    spaqr::Ordering o;
+};

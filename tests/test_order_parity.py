@@ -1,0 +1,59 @@
+"""The library's host ordering and symbolic plan match the oracle bit for bit.
+
+spaqr_order is integer host work, so this runs without a GPU.  The oracle
+(oracle/ordering.py, oracle/spaqr.py) is an independent implementation of the
+same readings of Section 2.3 / Algorithm 2.
+"""
+import numpy as np
+import pytest
+
+import paper_2010_06807_gb300 as sq
+from oracle import spaqr as osq
+from oracle.ordering import nd_order
+from synth.convdiff import config_problem, convdiff
+
+
+CASES = [
+    ("2d_uniform_a", 16, 3), ("2d_uniform_a", 24, 4), ("2d_uniform_a", 32, 0),
+    ("2d_uniform_a", 64, 0), ("2d_lognormal", 40, 5), ("3d_uniform_a", 8, 3),
+    ("3d_uniform_a", 12, 0), ("2d_uniform_a", 5, 4), ("2d_uniform_a", 4, 0),
+]
+
+
+@pytest.mark.parametrize("kind,n,L", CASES)
+def test_ordering_and_plan_bit_exact(spaqr_lib, kind, n, L):
+    p = config_problem(kind, n=n)
+    ordl = sq.spaqr_order(p.rowptr, p.colind, p.dims, L)
+    arr = ordl.arrays()
+    o = nd_order(p.dims, L if L > 0 else None)
+    assert ordl.L == o.L
+    np.testing.assert_array_equal(arr["perm"], o.perm)
+    np.testing.assert_array_equal(arr["atom_ptr"], o.atom_ptr)
+    np.testing.assert_array_equal(arr["atom_node"], o.atom_node)
+    np.testing.assert_array_equal(arr["node_level"], o.node_level)
+    # symbolic plan against the oracle's factorisation record (eps irrelevant)
+    F = osq.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-2, nlevels=o.L, skip=1, ordering=o)
+    plan = ordl.plan()
+    assert len(plan) == len(F.steps)
+    for st_l, st_o in zip(plan, F.steps):
+        assert st_l["level"] == st_o["level"]
+        assert st_l["clusters"] == sorted(st_o["sizes"].keys())
+        assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
+        for f in st_l["fronts"]:
+            s = f["id"]
+            assert f["colour"] == st_o["colour"][s]
+            assert f["R"] == list(st_o["R"][s])
+            assert f["C"] == list(st_o["C"][s])
+
+
+def test_order_rejects_bad_input(spaqr_lib):
+    p = config_problem("2d_uniform_a", n=8)
+    with pytest.raises(sq.SpaqrError) as e:
+        sq.spaqr_order(p.rowptr, p.colind, (8, 9))
+    assert e.value.name == "INVALID_ARG"
+    # a pattern that couples points two separators apart is not a stencil
+    rp = p.rowptr.copy()
+    ci = p.colind.copy()
+    ci[1] = 63 if ci[1] != 0 else ci[1]
+    with pytest.raises(sq.SpaqrError):
+        sq.spaqr_order(rp, np.sort(ci.reshape(-1)), (8, 8), 3)
