@@ -1,0 +1,1009 @@
+// Numeric spaQR factorisation on the GPU (Algorithm 2 of the paper).
+//
+// Per level (leaves first):
+//   (i)   every separator s of the level: Householder QR of its front (the
+//         column panel of s: rows R(s) stacked), then H_s^T applied to the
+//         columns C(s) of the front rows (Section 2.4);
+//   (ii)  block-diagonal scaling of every remaining interface p: A_pp = U R,
+//         rows p <- U^T, columns p <- R^{-1} (Section 2.5);
+//   (iii) sparsification: truncated column-pivoted QR of
+//         M_p = [A_np^T | A_pn] (rank rule of Section 4), then
+//         A_ij <- Q_i^T A_ij Q_j keeping the coarse rows/columns (Sections
+//         2.2, 2.5); all Q_p of a level are computed before any is applied;
+//   (iv)  merge of interfaces along the cluster hierarchy (Section 2.6),
+//         fused into (iii): every coarse block is written at its place in the
+//         merged blocks of the next level.
+// Storage: per level one arena of column panels (panel j = all blocks of
+// column j stacked, rows ascending), column-major.  The arena of a level is
+// kept: it holds the front reflectors, R_ss, the R_sj rows and the scaled
+// diagonal blocks the solve needs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dense.cuh"
+#include "spaqr_internal.h"
+#include "tasks.h"
+
+namespace spaqr {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// d_j = 1 / ||A(:, j)||_2 (Section 2.7); sums in ascending row order.
+__global__ void k_colscale(int64_t n, const int64_t* __restrict__ csc_ptr,
+                           const int64_t* __restrict__ csc_entry, const double* __restrict__ val,
+                           int normalize, double* __restrict__ d, int* __restrict__ bad) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (!normalize) { d[j] = 1.0; return; }
+    double s = 0.0;
+    for (int64_t e = csc_ptr[j]; e < csc_ptr[j + 1]; e++) {
+        const double v = val[csc_entry[e]];
+        s += v * v;
+    }
+    if (s == 0.0) { *bad = 1; d[j] = 0.0; return; }
+    d[j] = 1.0 / sqrt(s);
+}
+
+// Level-1 arena <- A D scattered into column panels.
+__global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int32_t* __restrict__ colind,
+                         const double* __restrict__ val, const double* __restrict__ d,
+                         double* __restrict__ arena) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    arena[off[e]] = val[e] * d[colind[e]];
+}
+
+__global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks) {
+    extern __shared__ double sm[];
+    const QRTask t = tasks[blockIdx.x];
+    const int tt = t.m < t.n ? t.m : t.n;
+    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask* __restrict__ tasks,
+                                                    const ApplyFront* __restrict__ fronts,
+                                                    const Seg* __restrict__ segs, int wdoubles) {
+    extern __shared__ double sm[];
+    double* W = sm;
+    int* rmap = reinterpret_cast<int*>(sm + wdoubles);
+    const ApplyTask t = tasks[blockIdx.x];
+    for (int f = 0; f < t.nfr; f++) {
+        const ApplyFront F = fronts[t.fr_begin + f];
+        int pos = 0;
+        for (int s = 0; s < F.nseg; s++) {
+            const Seg g = segs[F.seg_begin + s];
+            for (int r = threadIdx.x; r < g.len; r += NT) rmap[pos + r] = (int)(g.off + r);
+            pos += g.len;
+        }
+        __syncthreads();
+        RowMapped B{t.B, t.ldb, rmap};
+        cta_apply_wy(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask* __restrict__ tasks, int* singular) {
+    extern __shared__ double sm[];
+    const ScaleTask t = tasks[blockIdx.x];
+    for (int c0 = 0; c0 < t.nj; c0 += t.q) {
+        const int q = min(t.q, t.nj - c0);
+        RowMapped B{t.A + (int64_t)c0 * t.lda, t.lda, nullptr};
+        cta_apply_wy(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, B, q, true, sm);
+    }
+    cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, singular);
+}
+
+// Truncated CPQR with column norms recomputed from scratch at every step
+// (fused into the reflector update), pivot = largest norm, ties to the lowest
+// column index; stop at the first |R_kk| < eps |R_11|.
+__global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
+                                             const GatherSeg* __restrict__ gsegs, double eps) {
+    extern __shared__ double sm[];
+    double* red = sm;                               // NWARP
+    double* redv = sm + NWARP;                      // NWARP
+    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);   // NWARP ints (NWARP/2 doubles)
+    double* z = sm + 3 * NWARP;                     // kmax
+    const CPQRTask t = tasks[blockIdx.x];
+    const int m = t.np, c = t.ncols;
+    double* M = t.M;
+    // gather
+    for (int s = 0; s < t.nseg; s++) {
+        const GatherSeg g = gsegs[t.seg_begin + s];
+        if (g.transpose) {
+            // M[r, col_off + cc] = src[cc + r * ld], r < cols (= n_p), cc < rows
+            const int64_t tot = (int64_t)g.rows * g.cols;
+            for (int64_t o = threadIdx.x; o < tot; o += NT) {
+                const int cc = (int)(o % g.rows), r = (int)(o / g.rows);
+                M[r + (int64_t)(g.col_off + cc) * m] = g.src[cc + (int64_t)r * g.ld];
+            }
+        } else {
+            const int64_t tot = (int64_t)g.rows * g.cols;
+            for (int64_t o = threadIdx.x; o < tot; o += NT) {
+                const int r = (int)(o % g.rows), cc = (int)(o / g.rows);
+                M[r + (int64_t)(g.col_off + cc) * m] = g.src[r + (int64_t)cc * g.ld];
+            }
+        }
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int j = w; j < c; j += NWARP) {
+        const double* cj = M + (int64_t)j * m;
+        double s = 0.0;
+        for (int r = l; r < m; r += 32) s += cj[r] * cj[r];
+        s = warp_sum(s);
+        if (l == 0) t.norms[j] = s;
+    }
+    __syncthreads();
+    const int tmax = m < c ? m : c;
+    int rank = 0;
+    double R11 = 0.0;
+    for (int k = 0; k < tmax; k++) {
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int j = k + threadIdx.x; j < c; j += NT) {
+            const double v = t.norms[j];
+            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+        }
+        double gv;
+        int gi;
+        block_argmax(bv, bi, redv, redi, gv, gi);
+        const double pn = sqrt(gv);
+        if (threadIdx.x == 0) t.rdiag[k] = pn;
+        if (k == 0) R11 = pn;
+        if (R11 == 0.0) break;
+        if (pn < eps * R11) break;
+        if (gi != k) {
+            double* a = M + (int64_t)k * m;
+            double* b = M + (int64_t)gi * m;
+            for (int r = threadIdx.x; r < m; r += NT) {
+                const double x = a[r];
+                a[r] = b[r];
+                b[r] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
+        }
+        __syncthreads();
+        double* col = M + (int64_t)k * m;
+        const double tk = cta_house(col, k, m, red);
+        if (threadIdx.x == 0) t.tau[k] = tk;
+        // reflect the remaining columns and recompute their norms (rows k+1..)
+        for (int j = k + 1 + w; j < c; j += NWARP) {
+            double* cj = M + (int64_t)j * m;
+            if (tk != 0.0) {
+                const double ck = cj[k];
+                double d = 0.0;
+                for (int r = k + 1 + l; r < m; r += 32) d += col[r] * cj[r];
+                d = warp_sum(d) + ck;
+                const double f = tk * d;
+                if (l == 0) cj[k] = ck - f;
+                for (int r = k + 1 + l; r < m; r += 32) cj[r] -= f * col[r];
+            }
+            double s = 0.0;
+            for (int r = k + 1 + l; r < m; r += 32) s += cj[r] * cj[r];
+            s = warp_sum(s);
+            if (l == 0) t.norms[j] = s;
+        }
+        __syncthreads();
+        rank = k + 1;
+    }
+    // explicit reflectors V (n_p x rank), unit diagonal, zeros above
+    for (int64_t o = threadIdx.x; o < (int64_t)m * rank; o += NT) {
+        const int r = (int)(o % m), i = (int)(o / m);
+        double v = r < i ? 0.0 : (r == i ? 1.0 : M[r + (int64_t)i * m]);
+        t.V[r + (int64_t)i * m] = v;
+    }
+    if (threadIdx.x == 0) *t.rank = rank;
+    __syncthreads();
+    cta_form_t(t.V, m, m, rank, t.tau, t.T, t.kmax, z);
+}
+
+// Coarse block [Q_i^T A Q_j](0:r_i, 0:r_j) into the merged block of the next
+// level; identity for diagonal blocks; plain copy when not sparsified.
+__global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask* __restrict__ tasks) {
+    const SparsifyTask t = tasks[blockIdx.x];
+    if (t.mode == 2) {
+        const int64_t tot = (int64_t)t.mi * t.nj;
+        for (int64_t o = threadIdx.x; o < tot; o += NT) {
+            const int r = (int)(o % t.mi), c = (int)(o / t.mi);
+            t.D[r + (int64_t)c * t.ldd] = t.A[r + (int64_t)c * t.lda];
+        }
+        return;
+    }
+    if (t.mode == 1) {
+        for (int i = threadIdx.x; i < t.ri; i += NT) t.D[i + (int64_t)i * t.ldd] = 1.0;
+        return;
+    }
+    const int mi = t.mi, nj = t.nj, ri = t.ri, rj = t.rj;
+    double* B1 = t.scratch;                        // ri x nj
+    double* B2 = B1 + (int64_t)ri * nj;            // ri x nj
+    double* Z1 = B2 + (int64_t)ri * nj;            // ri x rj
+    double* Z2 = Z1 + (int64_t)ri * rj;            // ri x rj
+    // B1 = V_i^T A
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
+        const int p = (int)(o % ri), c = (int)(o / ri);
+        const double* vp = t.Vi + (int64_t)p * mi;
+        const double* ac = t.A + (int64_t)c * t.lda;
+        double s = 0.0;
+        for (int r = p; r < mi; r++) s += vp[r] * ac[r];
+        B1[o] = s;
+    }
+    __syncthreads();
+    // B2 = T_i^T B1
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
+        const int p = (int)(o % ri), c = (int)(o / ri);
+        double s = 0.0;
+        for (int u = 0; u <= p; u++) s += t.Ti[u + (int64_t)p * t.ldti] * B1[u + (int64_t)c * ri];
+        B2[o] = s;
+    }
+    __syncthreads();
+    // X = (Q_i^T A)(0:ri, :) = A(0:ri, :) - V_i(0:ri, :) B2   -> B1
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
+        const int p = (int)(o % ri), c = (int)(o / ri);
+        double s = 0.0;
+        for (int q = 0; q <= p; q++) s += t.Vi[p + (int64_t)q * mi] * B2[q + (int64_t)c * ri];
+        B1[o] = t.A[p + (int64_t)c * t.lda] - s;
+    }
+    __syncthreads();
+    const double* X = B1;
+    // Z1 = X V_j (ri x rj)
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
+        const int p = (int)(o % ri), q = (int)(o / ri);
+        const double* vq = t.Vj + (int64_t)q * nj;
+        double s = 0.0;
+        for (int c = q; c < nj; c++) s += X[p + (int64_t)c * ri] * vq[c];
+        Z1[o] = s;
+    }
+    __syncthreads();
+    // Z2 = Z1 T_j
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
+        const int p = (int)(o % ri), q = (int)(o / ri);
+        double s = 0.0;
+        for (int u = 0; u <= q; u++) s += Z1[p + (int64_t)u * ri] * t.Tj[u + (int64_t)q * t.ldtj];
+        Z2[o] = s;
+    }
+    __syncthreads();
+    // D = (X Q_j)(:, 0:rj) = X(:, 0:rj) - Z2 V_j(0:rj, :)^T
+    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
+        const int p = (int)(o % ri), q = (int)(o / ri);
+        double s = 0.0;
+        for (int u = 0; u <= q; u++) s += Z2[p + (int64_t)u * ri] * t.Vj[q + (int64_t)u * nj];
+        t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * ri] - s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Ctx {
+    spaqr_factor_s* F;
+    cudaStream_t st;
+    std::vector<void*> temps;
+    int rc = SPAQR_OK;
+
+    template <class T>
+    T* alloc(int64_t count, bool keep) {
+        if (rc != SPAQR_OK) return nullptr;
+        void* p = nullptr;
+        size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+            rc = SPAQR_ERR_OOM;
+            return nullptr;
+        }
+        if (keep) {
+            F->allocs.push_back(p);
+            F->bytes += (int64_t)bytes;
+        } else {
+            temps.push_back(p);
+        }
+        return (T*)p;
+    }
+    template <class T>
+    T* upload(const std::vector<T>& h, bool keep) {
+        T* d = alloc<T>((int64_t)h.size(), keep);
+        if (d && !h.empty()) cuda(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+        return d;
+    }
+    void cuda(cudaError_t e) {
+        if (e != cudaSuccess && rc == SPAQR_OK) {
+            set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+            rc = SPAQR_ERR_CUDA;
+        }
+    }
+    void launched() { cuda(cudaGetLastError()); }
+    void free_temps() {
+        for (void* p : temps) cudaFreeAsync(p, st);
+        temps.clear();
+    }
+};
+
+struct LevelLayout {
+    std::vector<int64_t> H, poff, rowoff, voff;
+    int64_t total = 0, rows = 0;
+};
+
+void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& L) {
+    const int ncl = (int)sp.cl.size();
+    L.H.assign(ncl, 0);
+    L.poff.assign(ncl + 1, 0);
+    L.rowoff.assign(sp.rowidx.size(), 0);
+    L.voff.assign(ncl + 1, 0);
+    for (int j = 0; j < ncl; j++) {
+        int64_t h = 0;
+        for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+            L.rowoff[e] = h;
+            h += sz[sp.rowidx[e]];
+        }
+        L.H[j] = h;
+        L.poff[j + 1] = L.poff[j] + h * sz[j];
+        L.voff[j + 1] = L.voff[j] + sz[j];
+    }
+    L.total = L.poff[ncl];
+    L.rows = L.voff[ncl];
+}
+
+const int kSmemMax = 200 * 1024;
+
+int chunk_width(int64_t n, int64_t budget_doubles) {
+    int64_t q = budget_doubles / (2 * std::max<int64_t>(n, 1));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(32, q));
+}
+
+bool g_attr_set = false;
+
+}  // namespace
+
+int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spaqr_factor_s* F) {
+    Ctx C;
+    C.F = F;
+    C.st = (cudaStream_t)opt->stream;
+    cudaStream_t st = C.st;
+    const int64_t n = o.n, nnz = o.nnz;
+    const int L = o.L;
+    F->n = n;
+    F->L = L;
+    F->skip = opt->skip;
+    F->eps = opt->eps;
+    if (!g_attr_set) {
+        C.cuda(cudaFuncSetAttribute(k_front_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_scale_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        if (C.rc != SPAQR_OK) return C.rc;
+        g_attr_set = true;
+    }
+    // phase timers: (start, end, phase) event triples
+    struct Timer { cudaEvent_t a, b; int ph; };
+    std::vector<Timer> timers;
+    auto tstart = [&]() {
+        Timer t;
+        t.ph = -1;
+        C.cuda(cudaEventCreate(&t.a));
+        C.cuda(cudaEventCreate(&t.b));
+        C.cuda(cudaEventRecord(t.a, st));
+        timers.push_back(t);
+    };
+    auto tstop = [&](int ph) {
+        timers.back().ph = ph;
+        C.cuda(cudaEventRecord(timers.back().b, st));
+    };
+
+    // ---- inputs on the device ----
+    const double* dval = A->val;
+    const int32_t* dcol = A->colind;
+    if (!A->on_device) {
+        double* v = C.alloc<double>(nnz, false);
+        int32_t* ci = C.alloc<int32_t>(nnz, false);
+        if (C.rc) return C.rc;
+        C.cuda(cudaMemcpyAsync(v, A->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, st));
+        C.cuda(cudaMemcpyAsync(ci, A->colind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+        dval = v;
+        dcol = ci;
+    }
+    int64_t* d_cscp = C.upload(o.csc_ptr, false);
+    int64_t* d_csce = C.upload(o.csc_entry, false);
+    int64_t* d_goff = C.upload(o.gather_off, false);
+    F->d_perm = C.upload(o.perm, true);
+    F->d_scale = C.alloc<double>(n, true);
+    int* d_flags = C.alloc<int>(4, true);
+    if (C.rc) return C.rc;
+    C.cuda(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
+    tstart();
+    k_colscale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_cscp, d_csce, dval, opt->col_normalize,
+                                                             F->d_scale, d_flags);
+    C.launched();
+
+    std::vector<int64_t> sz(o.steps[0].cl.size());
+    for (size_t a = 0; a < sz.size(); a++) sz[a] = o.atom_ptr[a + 1] - o.atom_ptr[a];
+    LevelLayout lay;
+    layout_of(o.steps[0], sz, lay);
+    if (lay.total != o.arena1_size) { set_error("arena layout mismatch"); return SPAQR_ERR_INVALID_ARG; }
+    double* arena = C.alloc<double>(lay.total, true);
+    if (C.rc) return C.rc;
+    C.cuda(cudaMemsetAsync(arena, 0, sizeof(double) * lay.total, st));
+    k_gather<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, d_goff, dcol, dval, F->d_scale, arena);
+    C.launched();
+    tstop(3);
+
+    // solve-plan host arrays
+    std::vector<SolveFront> sfronts;
+    std::vector<Seg> ssegs;
+    std::vector<SolveRsj> srsj;
+    std::vector<SolveSS> sss;
+    F->lv.assign(L, SolveLevelHost());
+    int64_t ws = 0;
+    double flops = 0.0, sflops = 0.0;
+    int64_t sbytes = 0;
+    F->ranks.assign(L, {});
+    F->margins.assign(L, {});
+
+    for (int k = 0; k < L; k++) {
+        const StepPlan& sp = o.steps[k];
+        const int ncl = (int)sp.cl.size();
+        SolveLevelHost& LV = F->lv[k];
+        LV.rows = lay.rows;
+        LV.ws_off = ws;
+        ws += lay.rows;
+        auto blk = [&](int e, int j) { return arena + lay.poff[j] + lay.rowoff[e]; };
+
+        // ---------------- (i) factor the fronts ----------------
+        std::vector<QRTask> qr;
+        std::vector<double*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr);
+        int64_t aux = 0;
+        for (size_t f = 0; f < sp.fronts.size(); f++) {
+            const int s = sp.fronts[f];
+            aux += sz[s] + sz[s] * sz[s];
+        }
+        double* faux = C.alloc<double>(aux, true);
+        if (C.rc) return C.rc;
+        int tmax = 1;
+        {
+            int64_t a = 0;
+            for (size_t f = 0; f < sp.fronts.size(); f++) {
+                const int s = sp.fronts[f];
+                ftau[f] = faux + a;
+                a += sz[s];
+                fT[f] = faux + a;
+                a += sz[s] * sz[s];
+                if (sz[s] == 0) continue;
+                qr.push_back(QRTask{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f]});
+                tmax = std::max<int>(tmax, (int)sz[s]);
+                flops += 2.0 * lay.H[s] * sz[s] * sz[s] - 2.0 / 3.0 * sz[s] * sz[s] * sz[s];
+                if (k == L - 1) F->top_size = (int)sz[s];
+            }
+        }
+        // apply: per column j, the fronts containing it (processing order)
+        std::vector<std::vector<int>> fronts_of(ncl);
+        for (size_t f = 0; f < sp.fronts.size(); f++) {
+            if (sz[sp.fronts[f]] == 0) continue;
+            for (size_t t = 1; t < sp.C[f].size(); t++) fronts_of[sp.C[f][t]].push_back((int)f);
+        }
+        std::vector<ApplyTask> at;
+        std::vector<ApplyFront> af;
+        std::vector<Seg> asg;
+        size_t smem_apply = 0;
+        for (int j = 0; j < ncl; j++) {
+            if (fronts_of[j].empty() || sz[j] == 0) continue;
+            const int fb = (int)af.size();
+            int nmax = 1, mmax = 1;
+            for (int f : fronts_of[j]) {
+                const int s = sp.fronts[f];
+                ApplyFront A1;
+                A1.V = arena + lay.poff[s];
+                A1.T = fT[f];
+                A1.ldv = lay.H[s];
+                A1.m = (int)lay.H[s];
+                A1.n = (int)sz[s];
+                A1.seg_begin = (int)asg.size();
+                for (int i : sp.R[f]) {
+                    const int e = sp.find(i, j);
+                    if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
+                    if (sz[i] > 0) asg.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
+                }
+                A1.nseg = (int)asg.size() - A1.seg_begin;
+                af.push_back(A1);
+                nmax = std::max(nmax, A1.n);
+                mmax = std::max(mmax, A1.m);
+                flops += (4.0 * A1.m * A1.n - 2.0 * A1.n * A1.n) * sz[j];
+            }
+            const int q = chunk_width(nmax, 6144);
+            for (int64_t c0 = 0; c0 < sz[j]; c0 += q) {
+                ApplyTask T1;
+                T1.B = arena + lay.poff[j] + c0 * lay.H[j];
+                T1.ldb = lay.H[j];
+                T1.q = (int)std::min<int64_t>(q, sz[j] - c0);
+                T1.fr_begin = fb;
+                T1.nfr = (int)fronts_of[j].size();
+                T1.m_max = mmax;
+                at.push_back(T1);
+            }
+            smem_apply = std::max(smem_apply, (size_t)(2 * nmax * q) * 8 + (size_t)mmax * 4 + 16);
+        }
+        // the apply kernel uses one W size for all tasks
+        int wd = 0;
+        {
+            size_t maxw = 0, maxm = 0;
+            for (const ApplyTask& T1 : at) {
+                int nmax = 1;
+                for (int f = 0; f < T1.nfr; f++) nmax = std::max(nmax, af[T1.fr_begin + f].n);
+                maxw = std::max(maxw, (size_t)(2 * nmax * T1.q));
+                maxm = std::max(maxm, (size_t)T1.m_max);
+            }
+            wd = (int)maxw;
+            smem_apply = maxw * 8 + maxm * 4 + 16;
+        }
+        if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
+        tstart();
+        if (!qr.empty()) {
+            QRTask* d = C.upload(qr, false);
+            if (C.rc) return C.rc;
+            k_qr<<<(unsigned)qr.size(), NT, (size_t)(NWARP + tmax) * 8, st>>>(d);
+            C.launched();
+        }
+        if (!at.empty()) {
+            ApplyTask* d1 = C.upload(at, false);
+            ApplyFront* d2 = C.upload(af, false);
+            Seg* d3 = C.upload(asg, false);
+            if (C.rc) return C.rc;
+            k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, wd);
+            C.launched();
+        }
+        tstop(0);
+
+        // solve record of the fronts, grouped by colour
+        LV.front_begin = (int)sfronts.size();
+        LV.colour_ptr.assign(1, 0);
+        {
+            int cur = 0;
+            for (size_t f = 0; f < sp.fronts.size(); f++) {
+                while (sp.colour[f] > cur) {
+                    LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
+                    cur++;
+                }
+                const int s = sp.fronts[f];
+                if (sz[s] == 0) continue;
+                SolveFront sf;
+                sf.V = arena + lay.poff[s];
+                sf.T = fT[f];
+                sf.ldv = lay.H[s];
+                sf.m = (int)lay.H[s];
+                sf.n = (int)sz[s];
+                sf.seg_begin = (int)ssegs.size();
+                for (int i : sp.R[f])
+                    if (sz[i] > 0) ssegs.push_back(Seg{lay.voff[i], (int)sz[i], 0});
+                sf.nseg = (int)ssegs.size() - sf.seg_begin;
+                sf.rsj_begin = (int)srsj.size();
+                for (size_t t = 1; t < sp.C[f].size(); t++) {
+                    const int j = sp.C[f][t];
+                    if (sz[j] == 0) continue;
+                    const int e = sp.find(s, j);
+                    srsj.push_back(SolveRsj{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
+                    sflops += 2.0 * sz[s] * sz[j];
+                    sbytes += 8 * sz[s] * sz[j];
+                }
+                sf.nrsj = (int)srsj.size() - sf.rsj_begin;
+                sfronts.push_back(sf);
+                LV.max_front_m = std::max(LV.max_front_m, sf.m);
+                LV.max_front_n = std::max(LV.max_front_n, sf.n);
+                sflops += 4.0 * sf.m * sf.n - 2.0 * sf.n * sf.n + 1.0 * sf.n * sf.n;
+                sbytes += 8 * (int64_t)sf.m * sf.n + 8 * (int64_t)sf.n * sf.n;
+            }
+            LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
+            LV.nfront = (int)sfronts.size() - LV.front_begin;
+        }
+
+        // ---------------- (ii)/(iii) scale and sparsify ----------------
+        std::vector<int> rest;
+        for (int i = 0; i < ncl; i++)
+            if (!sp.is_front[i]) rest.push_back(i);
+        const bool sparsify = (k + 1 > opt->skip) && !rest.empty();
+        std::vector<int64_t> newsz(ncl, 0);
+        std::vector<double*> uT(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
+        std::vector<int> kmax(ncl, 0);
+        if (sparsify) {
+            // scaling QR of every diagonal block
+            int64_t ua = 0;
+            for (int p : rest) ua += sz[p] + sz[p] * sz[p];
+            double* uaux = C.alloc<double>(ua, true);
+            if (C.rc) return C.rc;
+            std::vector<QRTask> sq;
+            int tm = 1;
+            int64_t a = 0;
+            for (int p : rest) {
+                double* tau = uaux + a;
+                a += sz[p];
+                uT[p] = uaux + a;
+                a += sz[p] * sz[p];
+                if (sz[p] == 0) continue;
+                const int e = sp.find(p, p);
+                if (e < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
+                sq.push_back(QRTask{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p]});
+                tm = std::max<int>(tm, (int)sz[p]);
+                flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
+            }
+            // scaling of the off-diagonal blocks
+            std::vector<ScaleTask> sc;
+            size_t smem_sc = 16;
+            for (int j : rest) {
+                if (sz[j] == 0) continue;
+                const int ej = sp.find(j, j);
+                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                    const int i = sp.rowidx[e];
+                    if (i == j || sp.is_front[i] || sz[i] == 0) continue;
+                    const int ei = sp.find(i, i);
+                    ScaleTask t;
+                    t.A = blk(e, j);
+                    t.lda = lay.H[j];
+                    t.mi = (int)sz[i];
+                    t.nj = (int)sz[j];
+                    t.Vi = blk(ei, i);
+                    t.ldvi = lay.H[i];
+                    t.Ti = uT[i];
+                    t.Rj = blk(ej, j);
+                    t.ldrj = lay.H[j];
+                    t.q = chunk_width(sz[i], 6144);
+                    smem_sc = std::max(smem_sc, (size_t)(2 * sz[i] * t.q) * 8);
+                    sc.push_back(t);
+                    flops += 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
+                }
+            }
+            tstart();
+            if (!sq.empty()) {
+                QRTask* d = C.upload(sq, false);
+                if (C.rc) return C.rc;
+                k_qr<<<(unsigned)sq.size(), NT, (size_t)(NWARP + tm) * 8, st>>>(d);
+                C.launched();
+            }
+            if (!sc.empty()) {
+                ScaleTask* d = C.upload(sc, false);
+                if (C.rc) return C.rc;
+                k_scale_apply<<<(unsigned)sc.size(), NT, smem_sc, st>>>(d, d_flags + 1);
+                C.launched();
+            }
+            tstop(1);
+            tstart();
+            // CPQR of M_p
+            std::vector<std::vector<std::pair<int, int>>> rowlist(ncl);   // row i -> (col j, entry)
+            for (int j = 0; j < ncl; j++)
+                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) rowlist[sp.rowidx[e]].push_back({j, e});
+            std::vector<CPQRTask> cp;
+            std::vector<GatherSeg> gs;
+            std::vector<int> cp_of(ncl, -1);
+            int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0;
+            std::vector<int> ncols(ncl, 0);
+            for (int p : rest) {
+                if (sz[p] == 0) continue;
+                int nc = 0;
+                for (int e = sp.colptr[p]; e < sp.colptr[p + 1]; e++) {
+                    const int i = sp.rowidx[e];
+                    if (i != p && !sp.is_front[i]) nc += (int)sz[i];
+                }
+                for (auto& je : rowlist[p]) {
+                    const int j = je.first;
+                    if (j != p && !sp.is_front[j]) nc += (int)sz[j];
+                }
+                ncols[p] = nc;
+                kmax[p] = (int)std::min<int64_t>(sz[p], nc);
+                mtot += sz[p] * nc;
+                ntot += nc;
+                vtot += sz[p] * kmax[p];
+                ttot += (int64_t)kmax[p] * kmax[p] + kmax[p];
+                rtot += kmax[p] + 1;
+            }
+            double* Mbuf = C.alloc<double>(mtot, false);
+            double* Nbuf = C.alloc<double>(ntot, false);
+            double* Vbuf = C.alloc<double>(vtot, true);
+            double* Tbuf = C.alloc<double>(ttot, true);
+            double* Rdg = C.alloc<double>(rtot, false);
+            int* Rk = C.alloc<int>(ncl, false);
+            if (C.rc) return C.rc;
+            C.cuda(cudaMemsetAsync(Rk, 0, sizeof(int) * ncl, st));
+            int64_t mo = 0, no = 0, vo = 0, to = 0, ro = 0;
+            int kmx = 1;
+            std::vector<int64_t> rdg_off(ncl, 0);
+            for (int p : rest) {
+                if (sz[p] == 0) continue;
+                CPQRTask t;
+                t.M = Mbuf + mo;
+                t.norms = Nbuf + no;
+                t.np = (int)sz[p];
+                t.ncols = ncols[p];
+                t.seg_begin = (int)gs.size();
+                int co = 0;
+                for (int e = sp.colptr[p]; e < sp.colptr[p + 1]; e++) {
+                    const int i = sp.rowidx[e];
+                    if (i == p || sp.is_front[i] || sz[i] == 0) continue;
+                    gs.push_back(GatherSeg{blk(e, p), lay.H[p], (int)sz[i], (int)sz[p], 1, co});
+                    co += (int)sz[i];
+                }
+                for (auto& je : rowlist[p]) {
+                    const int j = je.first;
+                    if (j == p || sp.is_front[j] || sz[j] == 0) continue;
+                    gs.push_back(GatherSeg{blk(je.second, j), lay.H[j], (int)sz[p], (int)sz[j], 0, co});
+                    co += (int)sz[j];
+                }
+                t.nseg = (int)gs.size() - t.seg_begin;
+                t.V = Vbuf + vo;
+                t.kmax = kmax[p];
+                t.tau = Tbuf + to;
+                t.T = Tbuf + to + kmax[p];
+                t.rdiag = Rdg + ro;
+                t.rank = Rk + p;
+                qV[p] = t.V;
+                qT[p] = t.T;
+                rdg_off[p] = ro;
+                mo += sz[p] * ncols[p];
+                no += ncols[p];
+                vo += sz[p] * kmax[p];
+                to += (int64_t)kmax[p] * kmax[p] + kmax[p];
+                ro += kmax[p] + 1;
+                kmx = std::max(kmx, kmax[p]);
+                cp_of[p] = (int)cp.size();
+                cp.push_back(t);
+            }
+            if (!cp.empty()) {
+                CPQRTask* d1 = C.upload(cp, false);
+                GatherSeg* d2 = C.upload(gs, false);
+                if (C.rc) return C.rc;
+                k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(4 * NWARP + kmx) * 8, st>>>(d1, d2, opt->eps);
+                C.launched();
+            }
+            // ranks back to the host (the only device->host sync of a level)
+            std::vector<int> rk(ncl, 0);
+            std::vector<double> rdg(std::max<int64_t>(rtot, 1), 0.0);
+            C.cuda(cudaMemcpyAsync(rk.data(), Rk, sizeof(int) * ncl, cudaMemcpyDeviceToHost, st));
+            if (rtot > 0) C.cuda(cudaMemcpyAsync(rdg.data(), Rdg, sizeof(double) * rtot, cudaMemcpyDeviceToHost, st));
+            tstop(2);
+            C.cuda(cudaStreamSynchronize(st));
+            if (C.rc) return C.rc;
+            for (int p : rest) {
+                newsz[p] = sz[p] == 0 ? 0 : rk[p];
+                if (sz[p] == 0) continue;
+                F->ranks[k].push_back({(int)sz[p], rk[p]});
+                const double* rd = rdg.data() + rdg_off[p];
+                const int r = rk[p];
+                const double rr = r < kmax[p] ? rd[r] : (r > 0 ? rd[r - 1] : 0.0);
+                F->margins[k].push_back({rr, rd[0]});
+                flops += 4.0 * sz[p] * ncols[p] * r + 2.0 * sz[p] * ncols[p] * r;
+            }
+        } else {
+            for (int p : rest) newsz[p] = sz[p];
+        }
+
+        // ---------------- (iv) merge into the next level ----------------
+        if (k < L - 1) {
+            const StepPlan& sn = o.steps[k + 1];
+            const int nn = (int)sn.cl.size();
+            std::vector<int64_t> nsz(nn, 0), coff(ncl, 0);
+            for (int p : rest) {
+                const int J = sp.parent[p];
+                coff[p] = nsz[J];
+                nsz[J] += newsz[p];
+            }
+            LevelLayout nl;
+            layout_of(sn, nsz, nl);
+            double* narena = C.alloc<double>(nl.total, true);
+            if (C.rc) return C.rc;
+            tstart();
+            C.cuda(cudaMemsetAsync(narena, 0, sizeof(double) * nl.total, st));
+            std::vector<SparsifyTask> sk;
+            int64_t scr = 0;
+            for (int j : rest) {
+                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                    const int i = sp.rowidx[e];
+                    if (sp.is_front[i]) continue;
+                    const int I = sp.parent[i], J = sp.parent[j];
+                    const int e2 = sn.find(I, J);
+                    if (e2 < 0) { set_error("merged block missing"); return SPAQR_ERR_INVALID_ARG; }
+                    SparsifyTask t;
+                    std::memset(&t, 0, sizeof(t));
+                    t.A = blk(e, j);
+                    t.lda = lay.H[j];
+                    t.mi = (int)sz[i];
+                    t.nj = (int)sz[j];
+                    t.D = narena + nl.poff[J] + nl.rowoff[e2] + coff[i] + coff[j] * nl.H[J];
+                    t.ldd = nl.H[J];
+                    if (!sparsify) {
+                        if (sz[i] == 0 || sz[j] == 0) continue;
+                        t.mode = 2;
+                    } else if (i == j) {
+                        if (newsz[i] == 0) continue;
+                        t.mode = 1;
+                        t.ri = (int)newsz[i];
+                    } else {
+                        if (newsz[i] == 0 || newsz[j] == 0) continue;
+                        t.mode = 0;
+                        t.Vi = qV[i];
+                        t.Ti = qT[i];
+                        t.ri = (int)newsz[i];
+                        t.ldti = kmax[i];
+                        t.Vj = qV[j];
+                        t.Tj = qT[j];
+                        t.rj = (int)newsz[j];
+                        t.ldtj = kmax[j];
+                        t.scratch = (double*)(intptr_t)scr;  // offset, fixed below
+                        scr += 2 * (int64_t)t.ri * t.nj + 2 * (int64_t)t.ri * t.rj;
+                        flops += 4.0 * t.ri * t.mi * t.nj + 4.0 * t.ri * t.nj * t.rj;
+                    }
+                    sk.push_back(t);
+                }
+            }
+            if (!sk.empty()) {
+                double* sbuf = C.alloc<double>(scr, false);
+                if (C.rc) return C.rc;
+                for (SparsifyTask& t : sk)
+                    if (t.mode == 0) t.scratch = sbuf + (int64_t)(intptr_t)t.scratch;
+                SparsifyTask* d = C.upload(sk, false);
+                if (C.rc) return C.rc;
+                k_sparsify<<<(unsigned)sk.size(), NT, 0, st>>>(d);
+                C.launched();
+            }
+            tstop(3);
+            // solve record of the surviving clusters
+            LV.ss_begin = (int)sss.size();
+            for (int p : rest) {
+                SolveSS s;
+                std::memset(&s, 0, sizeof(s));
+                s.off = lay.voff[p];
+                s.noff = nl.voff[sp.parent[p]] + coff[p];
+                s.np = (int)sz[p];
+                s.r = (int)newsz[p];
+                if (sparsify && sz[p] > 0) {
+                    const int e = sp.find(p, p);
+                    s.UV = blk(e, p);
+                    s.lduv = lay.H[p];
+                    s.UT = uT[p];
+                    s.QV = qV[p];
+                    s.QT = qT[p];
+                    s.ldqt = std::max(kmax[p], 1);
+                    sflops += 2.0 * (4.0 * sz[p] * sz[p] + 4.0 * sz[p] * newsz[p]);
+                    sbytes += 8 * (2 * sz[p] * sz[p] + sz[p] * newsz[p]);
+                }
+                sss.push_back(s);
+                LV.max_ss_n = std::max(LV.max_ss_n, s.np);
+                LV.max_ss_r = std::max(LV.max_ss_r, s.r);
+            }
+            LV.nss = (int)sss.size() - LV.ss_begin;
+            C.free_temps();
+            sz = nsz;
+            lay = nl;
+            arena = narena;
+        } else {
+            LV.ss_begin = (int)sss.size();
+            LV.nss = 0;
+            C.free_temps();
+        }
+    }
+    // upload the solve plan
+    F->d_fronts = C.upload(sfronts, true);
+    F->d_segs = C.upload(ssegs, true);
+    F->d_rsj = C.upload(srsj, true);
+    F->d_ss = C.upload(sss, true);
+    F->ws_rows = ws;
+    F->flops = flops;
+    F->solve_flops = sflops;
+    F->solve_bytes = sbytes;
+    int flags[4] = {0, 0, 0, 0};
+    C.cuda(cudaMemcpyAsync(flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    C.cuda(cudaStreamSynchronize(st));
+    C.free_temps();
+    C.cuda(cudaStreamSynchronize(st));
+    if (C.rc) return C.rc;
+    for (Timer& t : timers) {
+        float ms = 0.0f;
+        if (t.ph >= 0 && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) F->phase_ms[t.ph] += ms;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    if (flags[0]) { set_error("matrix has a zero column"); return SPAQR_ERR_SINGULAR; }
+    if (flags[1]) { set_error("zero diagonal in a scaling factor R_pp"); return SPAQR_ERR_SINGULAR; }
+    return SPAQR_OK;
+}
+
+}  // namespace spaqr
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts* opts,
+                            spaqr_factor_t** out) {
+    using namespace spaqr;
+    if (!out) { set_error("out is NULL"); return SPAQR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!ord || !A || !opts) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (A->n != ord->o.n || A->nnz != ord->o.nnz || !A->val) {
+        set_error("matrix does not match the ordering's pattern");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (!(opts->eps >= 0.0) || opts->skip < 0) { set_error("eps must be >= 0 and skip >= 0"); return SPAQR_ERR_INVALID_ARG; }
+    if (opts->nlevels != 0 && opts->nlevels != ord->o.L) {
+        set_error("opts.nlevels differs from the ordering's level count");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (opts->scaling != 1) { set_error("only the scaled variant is built (scaling = 1)"); return SPAQR_ERR_UNSUPPORTED; }
+    if (opts->precision != SPAQR_FP64) { set_error("only FP64 factorisation is built"); return SPAQR_ERR_UNSUPPORTED; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return SPAQR_ERR_NO_DEVICE;
+    }
+    spaqr_factor_s* F = new (std::nothrow) spaqr_factor_s();
+    if (!F) { set_error("host allocation failed"); return SPAQR_ERR_OOM; }
+    cudaGetDevice(&F->device);
+    int rc;
+    try {
+        rc = run_factor(ord->o, A, opts, F);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        rc = SPAQR_ERR_OOM;
+    }
+    if (rc != SPAQR_OK) {
+        cudaStreamSynchronize((cudaStream_t)opts->stream);
+        spaqr_factor_destroy(F);
+        return rc;
+    }
+    *out = F;
+    return SPAQR_OK;
+}
+
+extern "C" void spaqr_factor_destroy(spaqr_factor_t* F) {
+    if (!F) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(F->device);
+    cudaDeviceSynchronize();
+    for (void* p : F->allocs) cudaFree(p);
+    cudaSetDevice(cur);
+    delete F;
+}
+
+extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
+    if (!F || !out) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    std::memset(out, 0, sizeof(*out));
+    out->n = F->n;
+    out->nlevels = F->L;
+    out->skip = F->skip;
+    out->eps = F->eps;
+    out->factor_bytes = F->bytes;
+    out->solve_bytes = F->solve_bytes + 16 * F->n;
+    out->factor_flops = F->flops;
+    out->solve_flops = F->solve_flops;
+    for (auto& lvl : F->ranks)
+        for (auto& pr : lvl) {
+            out->n_interfaces_sparsified++;
+            out->rank_sum += pr.second;
+            out->size_sum += pr.first;
+        }
+    for (int i = 0; i < 4; i++) out->phase_ms[i] = F->phase_ms[i];
+    out->top_size = F->top_size;
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, double* margins,
+                                  int cap, int* count) {
+    if (!F || !count) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (level < 0 || level >= (int)F->ranks.size()) { spaqr::set_error("level out of range"); return SPAQR_ERR_INVALID_ARG; }
+    const auto& R = F->ranks[level];
+    *count = (int)R.size();
+    const int m = std::min<int>(cap, (int)R.size());
+    for (int i = 0; i < m; i++) {
+        if (pairs) { pairs[2 * i] = R[i].first; pairs[2 * i + 1] = R[i].second; }
+        if (margins) { margins[2 * i] = F->margins[level][i].first; margins[2 * i + 1] = F->margins[level][i].second; }
+    }
+    return SPAQR_OK;
+}

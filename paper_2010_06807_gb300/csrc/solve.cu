@@ -1,0 +1,660 @@
+// Application of the spaQR factor (Section 2.7) and right-preconditioned
+// GMRES (Section 4) on the GPU.
+//
+// With left operations L_1..L_K (H_s^T on front rows, U_p^T, Q_p^T) and right
+// operations C_1..C_K (R_s^{-1}, R_p^{-1}, Q_p) recorded in factor order,
+// L_K ... L_1 A D C_1 ... C_K ~ I, so x = D C_1 (C_2 (... C_K (L_K ... L_1 b))).
+//   forward  (leaves -> root): fronts (by colour), then per surviving cluster
+//            y_p <- Q_p^T U_p^T y_p; the coarse part moves into the merged
+//            cluster of the next level, the fine part stays (its block is I);
+//   backward (root -> leaves): coarse part back, x_p <- R_p^{-1} Q_p [x_c; x_f],
+//            then x_s <- R_ss^{-1} (z_s - sum_j R_sj x_j) for every front.
+// Each level has its own vector (rows = sizes of its clusters), all in one
+// workspace, column-major with one column per right-hand side.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dense.cuh"
+#include "spaqr_internal.h"
+#include "tasks.h"
+
+namespace spaqr {
+
+__global__ void k_perm_in(int64_t n, int nrhs, const int64_t* __restrict__ perm, const double* __restrict__ B,
+                          int64_t ldb, double* __restrict__ Y, int64_t ldy) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = perm[i];
+    for (int c = 0; c < nrhs; c++) Y[i + c * ldy] = B[g + c * ldb];
+}
+
+__global__ void k_perm_out(int64_t n, int nrhs, const int64_t* __restrict__ perm, const double* __restrict__ d,
+                           const double* __restrict__ Y, int64_t ldy, double* __restrict__ X, int64_t ldx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = perm[i];
+    const double s = d[g];
+    for (int c = 0; c < nrhs; c++) X[g + c * ldx] = s * Y[i + c * ldy];
+}
+
+__global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
+                                                   double* Y, int64_t ldy, int nrhs, int q, int wdoubles) {
+    extern __shared__ double sm[];
+    double* W = sm;
+    int* rmap = reinterpret_cast<int*>(sm + wdoubles);
+    const SolveFront F = fr[blockIdx.x];
+    int pos = 0;
+    for (int s = 0; s < F.nseg; s++) {
+        const Seg g = segs[F.seg_begin + s];
+        for (int r = threadIdx.x; r < g.len; r += NT) rmap[pos + r] = (int)(g.off + r);
+        pos += g.len;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < nrhs; c0 += q) {
+        RowMapped B{Y + (int64_t)c0 * ldy, ldy, rmap};
+        cta_apply_wy(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, min(q, nrhs - c0), true, W);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy, double* Yn,
+                                                int64_t ldyn, int nrhs, int q) {
+    extern __shared__ double sm[];
+    const SolveSS S = ss[blockIdx.x];
+    double* y = Y + S.off;
+    for (int c0 = 0; c0 < nrhs; c0 += q) {
+        const int qq = min(q, nrhs - c0);
+        RowMapped B{y + (int64_t)c0 * ldy, ldy, nullptr};
+        if (S.UV) cta_apply_wy(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qq, true, sm);
+        if (S.QV && S.r > 0) cta_apply_wy(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qq, true, sm);
+    }
+    for (int64_t o = threadIdx.x; o < (int64_t)S.r * nrhs; o += NT) {
+        const int r = (int)(o % S.r), c = (int)(o / S.r);
+        Yn[S.noff + r + c * ldyn] = y[r + c * ldy];
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy,
+                                                const double* Yn, int64_t ldyn, int nrhs, int q, int* singular) {
+    extern __shared__ double sm[];
+    const SolveSS S = ss[blockIdx.x];
+    double* y = Y + S.off;
+    for (int64_t o = threadIdx.x; o < (int64_t)S.r * nrhs; o += NT) {
+        const int r = (int)(o % S.r), c = (int)(o / S.r);
+        y[r + c * ldy] = Yn[S.noff + r + c * ldyn];
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < nrhs; c0 += q) {
+        const int qq = min(q, nrhs - c0);
+        RowMapped B{y + (int64_t)c0 * ldy, ldy, nullptr};
+        if (S.QV && S.r > 0) cta_apply_wy(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qq, false, sm);
+    }
+    if (S.UV) {
+        RowMapped B{y, ldy, nullptr};
+        cta_trsv_upper(S.UV, S.lduv, S.np, B, nrhs, singular);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
+                                                   const SolveRsj* __restrict__ rsj, double* Y, int64_t ldy,
+                                                   int nrhs, int* singular) {
+    const SolveFront F = fr[blockIdx.x];
+    const Seg s0 = segs[F.seg_begin];  // the front's own rows
+    double* xs = Y + s0.off;
+    const int n = F.n;
+    // rhs = z_s - sum_j R_sj x_j
+    for (int64_t o = threadIdx.x; o < (int64_t)n * nrhs; o += NT) {
+        const int r = (int)(o % n), c = (int)(o / n);
+        double acc = 0.0;
+        for (int b = 0; b < F.nrsj; b++) {
+            const SolveRsj R = rsj[F.rsj_begin + b];
+            const double* xj = Y + R.xoff + (int64_t)c * ldy;
+            const double* row = R.R + r;
+            for (int u = 0; u < R.nj; u++) acc += row[(int64_t)u * R.ldr] * xj[u];
+        }
+        xs[r + (int64_t)c * ldy] -= acc;
+    }
+    __syncthreads();
+    RowMapped X{xs, ldy, nullptr};
+    cta_trsv_upper(F.V, F.ldv, n, X, nrhs, singular);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES kernels (FP64)
+// ---------------------------------------------------------------------------
+
+// Y = A X (CSR, nrhs columns)
+__global__ void k_spmv(int64_t n, int nrhs, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                       const double* __restrict__ val, const double* __restrict__ X, int64_t ldx,
+                       double* __restrict__ Y, int64_t ldy) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    double s = 0.0;
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) s += val[e] * X[colind[e] + c * ldx];
+    Y[r + c * ldy] = s;
+}
+
+// R = B - A X
+__global__ void k_residual(int64_t n, int nrhs, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                           const double* __restrict__ val, const double* __restrict__ X, int64_t ldx,
+                           const double* __restrict__ B, int64_t ldb, double* __restrict__ R) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    double s = 0.0;
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) s += val[e] * X[colind[e] + c * ldx];
+    R[r + c * n] = B[r + c * ldb] - s;
+}
+
+// out[i + c * nout] = dot(U_i[:, c], W[:, c]) for i < nvec; U_i = U + i * n * nrhs.
+// One CTA per (i, c); fixed reduction order.
+__global__ void __launch_bounds__(NT) k_dots(int64_t n, int nrhs, const double* __restrict__ U, int nvec,
+                                             const double* __restrict__ W, double* __restrict__ out, int nout) {
+    __shared__ double red[NWARP];
+    const int i = blockIdx.x % nvec, c = blockIdx.x / nvec;
+    const double* u = U + ((int64_t)i * nrhs + c) * n;
+    const double* w = W + (int64_t)c * n;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += NT) s += u[r] * w[r];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[i + c * nout] = s;
+}
+
+// W[:, c] -= sum_i U_i[:, c] h[i, c] ; H[:, j] += h  (only active columns)
+__global__ void k_orth_update(int64_t n, int nrhs, const double* __restrict__ U, int nvec,
+                              const double* __restrict__ h, int nh, double* __restrict__ W,
+                              const int* __restrict__ active) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    if (!active[c]) return;
+    double s = 0.0;
+    for (int i = 0; i < nvec; i++) s += U[((int64_t)i * nrhs + c) * n + r] * h[i + c * nh];
+    W[r + c * n] -= s;
+}
+
+// U_{j+1}[:, c] = W[:, c] / hn[c] (zero for inactive columns or hn = 0)
+__global__ void k_normalize(int64_t n, int nrhs, const double* __restrict__ W, const double* __restrict__ hn,
+                            double* __restrict__ Unext, const int* __restrict__ active) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int c = (int)(o / n);
+    const double h = hn[c];
+    Unext[o] = (active[c] && h != 0.0) ? W[o] / h : 0.0;
+}
+
+// Givens update of column j of every active Hessenberg matrix (one thread per
+// RHS).  H_c is (ldh x maxit) column-major; cs/sn/g per column.
+__global__ void k_givens(int nrhs, int j, double* H, int ldh, int64_t hstride, const double* h1,
+                         const double* h2, const double* hn, double* cs, double* sn, double* g, int ldg,
+                         const double* bnorm, double* est, const int* active) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    double* Hc = H + c * hstride;
+    double* col = Hc + (int64_t)j * ldh;
+    double* csc = cs + (int64_t)c * ldg;
+    double* snc = sn + (int64_t)c * ldg;
+    double* gc = g + (int64_t)c * ldg;
+    if (!active[c]) { est[c] = 0.0; return; }
+    for (int i = 0; i <= j; i++) col[i] = h1[i + c * ldh] + h2[i + c * ldh];
+    col[j + 1] = hn[c];
+    for (int i = 0; i < j; i++) {
+        const double t = csc[i] * col[i] + snc[i] * col[i + 1];
+        col[i + 1] = -snc[i] * col[i] + csc[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    double cj = 1.0, sj = 0.0;
+    if (den != 0.0) { cj = col[j] / den; sj = col[j + 1] / den; }
+    csc[j] = cj;
+    snc[j] = sj;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    gc[j + 1] = -sj * gc[j];
+    gc[j] = cj * gc[j];
+    est[c] = fabs(gc[j + 1]) / bnorm[c];
+}
+
+// y_c = H_c(0:j+1, 0:j+1)^{-1} g_c(0:j+1) for columns with want[c]; U = sum_i V_i y_i.
+__global__ void k_hsolve(int nrhs, int j, const double* H, int ldh, int64_t hstride, const double* g, int ldg,
+                         double* y, const int* want) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    double* yc = y + (int64_t)c * ldg;
+    if (!want[c]) {
+        for (int i = 0; i <= j; i++) yc[i] = 0.0;
+        return;
+    }
+    const double* Hc = H + c * hstride;
+    for (int i = j; i >= 0; i--) {
+        double s = g[(int64_t)c * ldg + i];
+        for (int k = i + 1; k <= j; k++) s -= Hc[i + (int64_t)k * ldh] * yc[k];
+        const double d = Hc[i + (int64_t)i * ldh];
+        yc[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+__global__ void k_combine(int64_t n, int nrhs, const double* __restrict__ U, int nvec, const double* __restrict__ y,
+                          int ldy, double* __restrict__ out) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    double s = 0.0;
+    for (int i = 0; i < nvec; i++) s += U[((int64_t)i * nrhs + c) * n + r] * y[i + (int64_t)c * ldy];
+    out[r + c * n] = s;
+}
+
+// X[:, c] = X0[:, c] + Z[:, c] for accepted columns
+__global__ void k_accept(int64_t n, int nrhs, const double* __restrict__ X0, int64_t ldx0, const double* __restrict__ Z,
+                         double* __restrict__ X, int64_t ldx, const int* __restrict__ take) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    if (!take[c]) return;
+    X[r + c * ldx] = X0[r + c * ldx0] + Z[r + c * n];
+}
+
+__global__ void k_copy_cols(int64_t n, int nrhs, const double* __restrict__ S, int64_t lds, double* __restrict__ D,
+                            int64_t ldd) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int64_t r = o % n;
+    const int c = (int)(o / n);
+    D[r + c * ldd] = S[r + c * lds];
+}
+
+__global__ void k_sqrtv(int nrhs, double* v) {
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) v[c] = sqrt(v[c]);
+}
+
+__global__ void k_scale_cols(int64_t n, int nrhs, double* __restrict__ U, const double* __restrict__ s) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const int c = (int)(o / n);
+    const double v = s[c];
+    U[o] = v != 0.0 ? U[o] / v : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+const int kSmemMax = 200 * 1024;
+bool g_solve_attr = false;
+
+struct SCtx {
+    cudaStream_t st;
+    std::vector<void*> temps;
+    int rc = SPAQR_OK;
+    template <class T>
+    T* alloc(int64_t count) {
+        if (rc != SPAQR_OK) return nullptr;
+        void* p = nullptr;
+        size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("device allocation failed");
+            rc = SPAQR_ERR_OOM;
+            return nullptr;
+        }
+        temps.push_back(p);
+        return (T*)p;
+    }
+    void cuda(cudaError_t e) {
+        if (e != cudaSuccess && rc == SPAQR_OK) {
+            set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+            rc = SPAQR_ERR_CUDA;
+        }
+    }
+    void launched() { cuda(cudaGetLastError()); }
+    void release(void* p) {
+        for (auto it = temps.begin(); it != temps.end(); ++it)
+            if (*it == p) { cudaFreeAsync(p, st); temps.erase(it); return; }
+    }
+    ~SCtx() {
+        for (void* p : temps) cudaFreeAsync(p, st);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int qwidth(int n, int nrhs) {
+    int q = (int)std::max<int64_t>(1, std::min<int64_t>(32, 6144 / (2 * (int64_t)std::max(n, 1))));
+    return std::min(q, std::max(nrhs, 1));
+}
+
+void set_solve_attrs() {
+    if (g_solve_attr) return;
+    cudaFuncSetAttribute(k_sfront_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    cudaFuncSetAttribute(k_sss_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    cudaFuncSetAttribute(k_sss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    g_solve_attr = true;
+}
+
+}  // namespace
+
+// X = M^{-1} B with B, X device pointers (n x nrhs, leading dims).  `singular`
+// is a device int (may be null).  Stream-ordered, no synchronisation.
+int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                 cudaStream_t st, double* ws, int* singular) {
+    set_solve_attrs();
+    const int64_t n = F->n;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    double* Y0 = ws + F->lv[0].ws_off * nrhs;
+    k_perm_in<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows);
+    const int L = F->L;
+    for (int k = 0; k < L; k++) {
+        const SolveLevelHost& LV = F->lv[k];
+        double* Y = ws + LV.ws_off * nrhs;
+        const int64_t ldy = LV.rows;
+        if (LV.nfront > 0) {
+            const int q = qwidth(LV.max_front_n, nrhs);
+            const int wd = 2 * LV.max_front_n * q;
+            const size_t smem = (size_t)wd * 8 + (size_t)LV.max_front_m * 4 + 16;
+            for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
+                const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
+                if (b > a)
+                    k_sfront_fwd<<<b - a, NT, smem, st>>>(F->d_fronts + LV.front_begin + a, F->d_segs, Y, ldy, nrhs,
+                                                          q, wd);
+            }
+        }
+        if (LV.nss > 0) {
+            const SolveLevelHost& LN = F->lv[k + 1];
+            const int q = qwidth(LV.max_ss_n, nrhs);
+            const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
+            k_sss_fwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, q);
+        }
+    }
+    for (int k = L - 1; k >= 0; k--) {
+        const SolveLevelHost& LV = F->lv[k];
+        double* Y = ws + LV.ws_off * nrhs;
+        const int64_t ldy = LV.rows;
+        if (LV.nss > 0) {
+            const SolveLevelHost& LN = F->lv[k + 1];
+            const int q = qwidth(LV.max_ss_n, nrhs);
+            const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
+            k_sss_bwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, q,
+                                                singular);
+        }
+        if (LV.nfront > 0)
+            k_sfront_bwd<<<LV.nfront, NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs, F->d_rsj, Y, ldy, nrhs,
+                                                   singular);
+    }
+    k_perm_out<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx);
+    return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
+}
+
+}  // namespace spaqr
+
+using namespace spaqr;
+
+extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                           void* stream) {
+    if (!F || !B || !X) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (nrhs < 0 || ldb < F->n || ldx < F->n) { set_error("bad nrhs or leading dimension"); return SPAQR_ERR_INVALID_ARG; }
+    if (nrhs == 0) return SPAQR_OK;
+    if (B != X) {
+        const char* b0 = (const char*)B;
+        const char* b1 = (const char*)(B + (ldb * (nrhs - 1) + F->n));
+        const char* x0 = (const char*)X;
+        const char* x1 = (const char*)(X + (ldx * (nrhs - 1) + F->n));
+        if (b0 < x1 && x0 < b1) { set_error("B and X overlap"); return SPAQR_ERR_INVALID_ARG; }
+    } else if (ldb != ldx) {
+        set_error("aliased B and X need the same leading dimension");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != F->device) cudaSetDevice(F->device);
+    SCtx C;
+    C.st = (cudaStream_t)stream;
+    const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
+    if (bdev != xdev) { set_error("B and X must both be host or both be device memory"); return SPAQR_ERR_INVALID_ARG; }
+    const int64_t n = F->n;
+    const double* dB = B;
+    double* dX = X;
+    int64_t lb = ldb, lx = ldx;
+    if (!bdev) {
+        double* t = C.alloc<double>(n * nrhs);
+        if (C.rc) return C.rc;
+        C.cuda(cudaMemcpy2DAsync(t, n * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyHostToDevice, C.st));
+        dB = t;
+        dX = t;
+        lb = lx = n;
+    }
+    double* ws = C.alloc<double>(F->ws_rows * nrhs);
+    int* flag = C.alloc<int>(1);
+    if (C.rc) return C.rc;
+    C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), C.st));
+    C.cuda((cudaError_t)0);
+    int rc = apply_device(F, nrhs, dB, lb, dX, lx, C.st, ws, flag);
+    if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); return C.rc ? C.rc : rc; }
+    if (!bdev) C.cuda(cudaMemcpy2DAsync(X, ldx * 8, dX, n * 8, n * 8, nrhs, cudaMemcpyDeviceToHost, C.st));
+    int hflag = 0;
+    C.cuda(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, C.st));
+    C.cuda(cudaStreamSynchronize(C.st));
+    if (cur != F->device) cudaSetDevice(cur);
+    if (C.rc) return C.rc;
+    if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B, int64_t ldb,
+                           double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres, void* stream) {
+    if (!F || !A || !B || !X) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (A->n != F->n || nrhs < 0 || ldb < F->n || ldx < F->n || maxit < 1 || !(tol >= 0.0)) {
+        set_error("bad size, leading dimension, tol or maxit");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (nrhs == 0) return SPAQR_OK;
+    SCtx C;
+    C.st = (cudaStream_t)stream;
+    cudaStream_t st = C.st;
+    const int64_t n = F->n, nnz = A->nnz;
+    const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
+    if (bdev != xdev) { set_error("B and X must both be host or both be device memory"); return SPAQR_ERR_INVALID_ARG; }
+    // matrix on the device
+    const int64_t* rp = A->rowptr;
+    const int32_t* ci = A->colind;
+    const double* va = A->val;
+    if (!A->on_device) {
+        int64_t* a = C.alloc<int64_t>(n + 1);
+        int32_t* b = C.alloc<int32_t>(nnz);
+        double* v = C.alloc<double>(nnz);
+        if (C.rc) return C.rc;
+        C.cuda(cudaMemcpyAsync(a, A->rowptr, 8 * (n + 1), cudaMemcpyHostToDevice, st));
+        C.cuda(cudaMemcpyAsync(b, A->colind, 4 * nnz, cudaMemcpyHostToDevice, st));
+        C.cuda(cudaMemcpyAsync(v, A->val, 8 * nnz, cudaMemcpyHostToDevice, st));
+        rp = a;
+        ci = b;
+        va = v;
+    }
+    // B, X on the device (column-major n x nrhs, ld n for temporaries)
+    const double* dB = B;
+    double* dX = X;
+    int64_t lb = ldb, lx = ldx;
+    if (!bdev) {
+        double* tb = C.alloc<double>(n * nrhs);
+        double* tx = C.alloc<double>(n * nrhs);
+        if (C.rc) return C.rc;
+        C.cuda(cudaMemcpy2DAsync(tb, n * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyHostToDevice, st));
+        C.cuda(cudaMemcpy2DAsync(tx, n * 8, X, ldx * 8, n * 8, nrhs, cudaMemcpyHostToDevice, st));
+        dB = tb;
+        dX = tx;
+        lb = lx = n;
+    }
+    const unsigned nbl = (unsigned)((n * nrhs + 255) / 256);
+    const int ldh = maxit + 1;
+    const int64_t hstride = (int64_t)ldh * maxit;
+    double* X0 = C.alloc<double>(n * nrhs);
+    double* Wv = C.alloc<double>(n * nrhs);
+    double* Zv = C.alloc<double>(n * nrhs);
+    double* ws = C.alloc<double>(F->ws_rows * nrhs);
+    double* H = C.alloc<double>(hstride * nrhs);
+    double* h1 = C.alloc<double>((int64_t)ldh * nrhs);
+    double* h2 = C.alloc<double>((int64_t)ldh * nrhs);
+    double* hn = C.alloc<double>(nrhs);
+    double* cs = C.alloc<double>((int64_t)ldh * nrhs);
+    double* sn = C.alloc<double>((int64_t)ldh * nrhs);
+    double* g = C.alloc<double>((int64_t)ldh * nrhs);
+    double* ycoef = C.alloc<double>((int64_t)ldh * nrhs);
+    double* bn = C.alloc<double>(nrhs);
+    double* est = C.alloc<double>(nrhs);
+    double* rn = C.alloc<double>(nrhs);
+    int* active = C.alloc<int>(nrhs);
+    int* want = C.alloc<int>(nrhs);
+    int* flag = C.alloc<int>(1);
+    if (C.rc) return C.rc;
+    int cap = std::min(maxit, 48) + 1;
+    double* Vb = C.alloc<double>((int64_t)cap * n * nrhs);
+    if (C.rc) return C.rc;
+    C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nrhs, st));
+    C.cuda(cudaMemsetAsync(g, 0, sizeof(double) * ldh * nrhs, st));
+    // X0 = X; r0 = B - A X0 (into V_0); beta = ||r0||; ||b||
+    k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dX, lx, X0, n);
+    k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb);
+    k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n);
+    k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1);  // ||b||^2 (nvec = 1, U = W)
+    k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1);  // ||r0||^2
+    C.launched();
+    std::vector<double> hb(nrhs), hr(nrhs), hest(nrhs), hres(nrhs, 1.0);
+    std::vector<int> hact(nrhs, 1), hit(nrhs, 0), hwant(nrhs, 0);
+    C.cuda(cudaMemcpyAsync(hb.data(), bn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+    C.cuda(cudaMemcpyAsync(hr.data(), hn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+    C.cuda(cudaStreamSynchronize(st));
+    if (C.rc) return C.rc;
+    std::vector<double> hg(ldh * nrhs, 0.0);
+    for (int c = 0; c < nrhs; c++) {
+        hb[c] = std::sqrt(hb[c]);
+        hr[c] = std::sqrt(hr[c]);
+        if (hb[c] == 0.0) {
+            // b = 0: x = 0
+            hact[c] = 0;
+            hres[c] = 0.0;
+            C.cuda(cudaMemsetAsync(dX + c * lx, 0, 8 * n, st));
+        } else if (hr[c] / hb[c] <= tol) {
+            hact[c] = 0;  // the initial guess already satisfies tol
+            hres[c] = hr[c] / hb[c];
+        }
+        hg[(int64_t)c * ldh] = hr[c];
+    }
+    C.cuda(cudaMemcpyAsync(bn, hb.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(g, hg.data(), 8 * ldh * nrhs, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(hn, hr.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
+    k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn);  // V_0 = r0 / beta
+    C.launched();
+    int nact = 0;
+    for (int c = 0; c < nrhs; c++) nact += hact[c];
+    int j = 0;
+    for (; j < maxit && nact > 0 && C.rc == SPAQR_OK; j++) {
+        if (j + 1 >= cap) {
+            const int ncap = std::min(maxit, 2 * cap) + 1;
+            double* nv = C.alloc<double>((int64_t)ncap * n * nrhs);
+            if (C.rc) break;
+            C.cuda(cudaMemcpyAsync(nv, Vb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            C.release(Vb);
+            Vb = nv;
+            cap = ncap;
+        }
+        double* Vj = Vb + (int64_t)j * n * nrhs;
+        // z = M^{-1} v_j ; w = A z
+        int rc = apply_device(F, nrhs, Vj, n, Zv, n, st, ws, flag);
+        if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
+        k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zv, n, Wv, n);
+        // classical Gram-Schmidt, twice
+        k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h1, ldh);
+        k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h1, ldh, Wv, active);
+        k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h2, ldh);
+        k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h2, ldh, Wv, active);
+        k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, hn, 1);
+        k_sqrtv<<<1, 32, 0, st>>>(nrhs, hn);
+        C.launched();
+        std::vector<double> hnv(nrhs);
+        k_normalize<<<nbl, 256, 0, st>>>(n, nrhs, Wv, hn, Vb + (int64_t)(j + 1) * n * nrhs, active);
+        k_givens<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, h1, h2, hn, cs, sn, g, ldh, bn, est,
+                                                  active);
+        C.launched();
+        C.cuda(cudaMemcpyAsync(hest.data(), est, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaMemcpyAsync(hnv.data(), hn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaStreamSynchronize(st));
+        if (C.rc) break;
+        bool anyw = false;
+        for (int c = 0; c < nrhs; c++) {
+            hwant[c] = 0;
+            if (!hact[c]) continue;
+            hit[c] = j + 1;
+            if (hest[c] <= tol || hnv[c] == 0.0 || j == maxit - 1) { hwant[c] = 1; anyw = true; }
+        }
+        if (!anyw) continue;
+        // candidate x = x0 + M^{-1} (V y) for the wanted columns; keep it if the
+        // recomputed residual meets tol
+        C.cuda(cudaMemcpyAsync(want, hwant.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
+        k_hsolve<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, g, ldh, ycoef, want);
+        k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, ycoef, ldh, Wv);
+        rc = apply_device(F, nrhs, Wv, n, Zv, n, st, ws, flag);
+        if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
+        // trial X into Wv: Wv = X0 + Zv (all columns), residual into Zv
+        k_accept<<<nbl, 256, 0, st>>>(n, nrhs, X0, n, Zv, Wv, n, want);
+        k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv);
+        k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Zv, 1, Zv, rn, 1);
+        C.launched();
+        std::vector<double> hrn(nrhs);
+        C.cuda(cudaMemcpyAsync(hrn.data(), rn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaStreamSynchronize(st));
+        if (C.rc) break;
+        std::vector<int> take(nrhs, 0);
+        bool anyt = false;
+        for (int c = 0; c < nrhs; c++) {
+            if (!hwant[c]) continue;
+            const double rr = std::sqrt(hrn[c]) / hb[c];
+            hres[c] = rr;
+            if (rr <= tol || hnv[c] == 0.0 || j == maxit - 1) {
+                take[c] = 1;
+                anyt = true;
+                hact[c] = 0;
+                nact--;
+            }
+        }
+        if (anyt) {
+            // dX[:, c] = Wv[:, c] for accepted columns
+            for (int c = 0; c < nrhs; c++)
+                if (take[c]) C.cuda(cudaMemcpyAsync(dX + c * lx, Wv + c * n, 8 * n, cudaMemcpyDeviceToDevice, st));
+            C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
+        }
+    }
+    if (!bdev) C.cuda(cudaMemcpy2DAsync(X, ldx * 8, dX, n * 8, n * 8, nrhs, cudaMemcpyDeviceToHost, st));
+    int hflag = 0;
+    C.cuda(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    C.cuda(cudaStreamSynchronize(st));
+    if (C.rc) return C.rc;
+    if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
+    bool ok = true;
+    for (int c = 0; c < nrhs; c++) {
+        if (iters) iters[c] = hit[c];
+        if (relres) relres[c] = hres[c];
+        if (!(hres[c] <= tol)) ok = false;
+    }
+    if (!ok) { set_error("GMRES did not reach tol within maxit"); return SPAQR_ERR_NOT_CONVERGED; }
+    return SPAQR_OK;
+}

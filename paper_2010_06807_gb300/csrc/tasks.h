@@ -1,0 +1,180 @@
+// Task descriptors handed from the host orchestration to the kernels, and the
+// factor object.  Plain structs (device arrays of them are uploaded per launch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "spaqr_internal.h"
+
+namespace spaqr {
+
+// Householder QR of an m x n block in place (front of a separator, Section
+// 2.4, or diagonal block of an interface, Section 2.5).
+struct QRTask {
+    double* A;
+    int64_t lda;
+    int m, n;
+    double* tau;   // min(m, n)
+    double* T;     // t x t compact-WY factor, ld = t
+};
+
+// Rows of a front inside another column panel (or inside a solve vector).
+struct Seg {
+    int64_t off;   // first row
+    int len;
+    int pad;
+};
+
+// One front applied to one column panel (Section 2.4: H_s^T on the columns
+// C(s) restricted to the rows R(s)).
+struct ApplyFront {
+    const double* V;   // front panel (reflectors below the diagonal)
+    const double* T;
+    int64_t ldv;
+    int m, n;          // front rows, reflectors
+    int seg_begin, nseg;
+};
+
+// A chunk of columns of panel j, with the fronts to apply in order.
+struct ApplyTask {
+    double* B;         // first column of the chunk
+    int64_t ldb;
+    int q;             // chunk width
+    int fr_begin, nfr;
+    int m_max;         // largest front in the list (row map size)
+};
+
+// Block (i, j) <- U_i^T A_ij R_j^{-1} (Section 2.5).
+struct ScaleTask {
+    double* A;
+    int64_t lda;
+    int mi, nj;
+    const double* Vi;   // diagonal block i after its QR (reflectors below the diagonal)
+    int64_t ldvi;
+    const double* Ti;   // n_i x n_i, ld n_i
+    const double* Rj;   // diagonal block j (R on and above the diagonal)
+    int64_t ldrj;
+    int q;              // column chunk for the U^T product
+};
+
+// Column segment of M_p = [A_{k p}^T ... | A_{p j} ...] (Section 2.5).
+struct GatherSeg {
+    const double* src;
+    int64_t ld;
+    int rows, cols;     // of the source block
+    int transpose;      // 1: src is A_{k p} (n_k x n_p) and enters as its transpose
+    int col_off;        // first column in M_p
+};
+
+// Truncated column-pivoted QR of M_p (rank rule of Section 4).
+struct CPQRTask {
+    double* M;          // scratch n_p x ncols, ld n_p
+    double* norms;      // scratch ncols
+    int np, ncols;
+    int seg_begin, nseg;
+    double* V;          // out: n_p x kmax explicit reflectors, ld n_p
+    double* tau;        // out: kmax
+    double* T;          // out: r x r compact-WY, ld kmax
+    double* rdiag;      // out: pivot norms, kmax + 1 entries
+    int* rank;          // out
+    int kmax;           // min(n_p, ncols)
+};
+
+// New block (r_i x r_j) = [Q_i^T A_ij Q_j] (coarse rows/cols, Sections 2.5),
+// written at its place in the merged block of the next level (Section 2.6);
+// or a plain copy when the level is not sparsified.
+struct SparsifyTask {
+    const double* A;
+    int64_t lda;
+    int mi, nj;
+    const double* Vi;   // n_i x r_i explicit, ld n_i
+    const double* Ti;   // ld kmax_i
+    int ri, ldti;
+    const double* Vj;
+    const double* Tj;
+    int rj, ldtj;
+    double* D;
+    int64_t ldd;
+    double* scratch;    // 2 * r_i * n_j + 2 * r_i * r_j doubles
+    int mode;           // 0 sparsify, 1 identity r_i, 2 copy
+};
+
+// ---------------------------------------------------------------------------
+// solve descriptors
+// ---------------------------------------------------------------------------
+
+struct SolveFront {
+    const double* V;   // front panel: reflectors below the diagonal, R_ss on top
+    const double* T;
+    int64_t ldv;
+    int m, n;
+    int seg_begin, nseg;   // rows R(s) in the level vector (first segment = s)
+    int rsj_begin, nrsj;
+};
+
+struct SolveRsj {
+    const double* R;   // n_s x n_j block of row s in column j
+    int64_t ldr;
+    int nj;
+    int pad;
+    int64_t xoff;      // rows of j in the level vector
+};
+
+// Scaling + sparsification (or plain carry-over) of one cluster that survives
+// a level.
+struct SolveSS {
+    int64_t off;       // rows in this level's vector
+    int64_t noff;      // rows of its coarse part in the next level's vector
+    int np, r;
+    const double* UV;  // diagonal block after the scaling QR (null: not scaled)
+    int64_t lduv;
+    const double* UT;  // n_p x n_p
+    const double* QV;  // n_p x r explicit
+    const double* QT;  // ld kmax
+    int ldqt;
+    int pad;
+};
+
+}  // namespace spaqr
+
+// ---------------------------------------------------------------------------
+// factor object
+// ---------------------------------------------------------------------------
+
+struct SolveLevelHost {
+    int64_t rows = 0;         // length of the level vector
+    int64_t ws_off = 0;       // offset (in doubles, per RHS column) in the solve workspace
+    std::vector<int> colour_ptr;   // fronts grouped by colour: [colour_ptr[c], colour_ptr[c+1])
+    int front_begin = 0, nfront = 0;  // into the device SolveFront array
+    int ss_begin = 0, nss = 0;        // into the device SolveSS array
+    int max_front_m = 0, max_front_n = 0, max_ss_n = 0, max_ss_r = 0;
+};
+
+struct spaqr_factor_s {
+    int device = 0;
+    int64_t n = 0;
+    int L = 0, skip = 0;
+    double eps = 0.0;
+    std::vector<void*> allocs;     // device allocations owned by the factor
+    int64_t bytes = 0;
+    double* d_scale = nullptr;     // column scaling D (n)
+    int64_t* d_perm = nullptr;     // new -> old
+    // solve plan
+    std::vector<SolveLevelHost> lv;
+    spaqr::SolveFront* d_fronts = nullptr;
+    spaqr::Seg* d_segs = nullptr;
+    spaqr::SolveRsj* d_rsj = nullptr;
+    spaqr::SolveSS* d_ss = nullptr;
+    int64_t ws_rows = 0;           // total rows of all level vectors
+    // diagnostics
+    std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
+    std::vector<std::vector<std::pair<double, double>>> margins;
+    double phase_ms[4] = {0, 0, 0, 0};
+    double flops = 0.0;
+    double solve_flops = 0.0;
+    int64_t solve_bytes = 0;
+    int top_size = 0;
+};
