@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 spaQR hot path.
+
+Workload (one step = the whole hot path on one batch):
+  2D convection-diffusion, 5-point upwind FD on 256 x 256 (N = 65536),
+  a = exp(g), g ~ N(0,1) per cell, velocity 50 (cos t, sin t), t ~ U[0, 2 pi)
+  per cell, FP64, L = 10 levels, eps = 1e-2, 16 right-hand sides ~ N(0,1).
+  step = spaqr_factor (column scaling, gather, per level: front QR + apply,
+  block-diagonal scaling, truncated CPQR sparsification, merge) followed by
+  spaqr_gmres for the 16 right-hand sides to ||b - A x|| / ||b|| <= 1e-12
+  (every GMRES iteration applies the factor).  The nested-dissection ordering
+  is integer host work done once per sparsity pattern; it is timed separately
+  (order_ms) and is not part of a step.
+
+Metric: right-hand sides solved to 1e-12 per second over whole steps
+(factor + GMRES), with factor time and GMRES time per step as p50/p99.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica (the path does not shard);
+value = all ranks' right-hand sides / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "factor s + solves/s to rel.resid 1e-12 (mixed/batched vs plain FP64); p50/p99"
+UNIT = "solves/s"
+KIND, NSIDE, NRHS, EPS, TOL, MAXIT = "2d_lognormal", 256, 16, 1e-2, 1e-12, 300
+WORKLOAD = "convdiff2d_256x256_lognormal_a_pe50_randangle_fp64_eps1e-2_16rhs"
+# FP64 peak on GB300: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2070 MHz (nominal
+# 1.25 TFLOP/s); a DFMA microbenchmark measured 1.19 TFLOP/s at ~1990 MHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = max(0, min(len(v) - 1, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
+
+
+# ---------------------------------------------------------------------------
+# oracle runs (CPU baseline / reference arm): a separate single-threaded process
+# ---------------------------------------------------------------------------
+
+_ORACLE_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from synth.convdiff import config_problem, rhs
+from oracle import spaqr as osq
+p = config_problem(%(kind)r, n=%(n)d)
+b = rhs(p, %(nrhs)d)
+mode = %(mode)r
+t0 = time.perf_counter()
+F = osq.factor(p.n, p.rowptr, p.colind, p.val, p.dims, %(eps)r)
+tf = time.perf_counter() - t0
+out = {"factor_s": tf, "gmres_s": [], "iters": []}
+cols = list(range(%(ncols)d))
+for c in cols:
+    t0 = time.perf_counter()
+    x, it, rr, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, c % b.shape[1]],
+                             lambda v: osq.solve(F, v), tol=%(tol)r, maxit=%(maxit)d)
+    out["gmres_s"].append(time.perf_counter() - t0)
+    out["iters"].append(int(it))
+    out["relres_max"] = max(out.get("relres_max", 0.0), float(rr))
+print(json.dumps(out))
+"""
+
+
+def run_oracle(ncols, mode="baseline"):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = _ORACLE_SCRIPT % dict(root=ROOT, kind=KIND, n=NSIDE, nrhs=NRHS, mode=mode, eps=EPS, tol=TOL,
+                                 maxit=MAXIT, ncols=ncols)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands
+# ---------------------------------------------------------------------------
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # one oracle process: the factorisation once, then W + K single-RHS GMRES solves
+    r = run_oracle(a.warmup + a.steps, mode="reference")
+    factor_s = r["factor_s"]
+    # a step of the reference: one right-hand side of the 16, i.e. its GMRES plus
+    # 1/16 of one factorisation (the factor is shared by the 16 right-hand sides)
+    steps_t = [factor_s / NRHS + g for g in r["gmres_s"][a.warmup:]]
+    mean = sum(steps_t) / len(steps_t)
+    value = 1.0 / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nrhs": NRHS, "eps": EPS, "tol": TOL, "n": NSIDE * NSIDE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": (f"oracle factorisation of the full 256x256 matrix once ({factor_s:.1f} s), "
+                                    "then per step the oracle GMRES of one RHS to 1e-12 plus 1/16 of the "
+                                    f"factorisation; iters {r['iters'][:3]}")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2010_06807_gb300 as sq
+    from synth.convdiff import config_problem, rhs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    sq.load_library()
+
+    p = config_problem(KIND, n=NSIDE)
+    b = rhs(p, NRHS)
+    rp = torch.from_numpy(p.rowptr).to(dev)
+    ci = torch.from_numpy(p.colind).to(dev)
+    va = torch.from_numpy(p.val).to(dev)
+    Bd = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T          # n x 16, column-major
+    Xd = torch.zeros(NRHS, p.n, dtype=torch.float64, device=dev).T
+    st = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # > L2 (126 MB)
+
+    t0 = time.perf_counter()
+    ordl = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+    order_ms = (time.perf_counter() - t0) * 1e3
+
+    def step():
+        F = sq.spaqr_factor(ordl, rp, ci, va, eps=EPS, stream=st)
+        ev_mid.record(st)
+        Xd.zero_()
+        X, it, rr = sq.spaqr_gmres(F, rp, ci, va, Bd, X=Xd, tol=TOL, maxit=MAXIT, stream=st)
+        return F, it, rr
+
+    with torch.cuda.stream(st):
+        for _ in range(a.warmup):
+            ev_mid = torch.cuda.Event(enable_timing=True)
+            F, it, rr = step()
+            del F
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        sq.spaqr_stats_reset()
+        sq.spaqr_profile(True)
+        fac_ms, gm_ms, step_ms, iters, relres = [], [], [], [], []
+        for _ in range(a.steps):
+            flush.zero_()                                   # evict L2 between steps
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev_mid = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+            F, it, rr = step()
+            ev1.record(st)
+            ev1.synchronize()
+            fac_ms.append(ev0.elapsed_time(ev_mid))
+            gm_ms.append(ev_mid.elapsed_time(ev1))
+            step_ms.append(ev0.elapsed_time(ev1))
+            iters.append(it.tolist())
+            relres.append(float(rr.max()))
+            info = sq.spaqr_factor_info(F)
+            del F
+        torch.cuda.synchronize(dev)
+        sq.spaqr_profile(False)
+        launches, kstats = sq.spaqr_stats()
+        clk = clocks.stop()
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = NRHS * a.steps * world / total_s
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----
+    rph = torch.from_numpy(p.rowptr).pin_memory()
+    cih = torch.from_numpy(p.colind).pin_memory()
+    vah = torch.from_numpy(p.val).pin_memory()
+    Bh = torch.from_numpy(np.ascontiguousarray(b.T)).pin_memory().T
+    Xh = torch.zeros(NRHS, p.n, dtype=torch.float64).pin_memory().T
+    e2e_t = []
+    for i in range(a.warmup + a.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        F = sq.spaqr_factor(ordl, rph, cih, vah, eps=EPS, stream=st)
+        Xh.zero_()
+        X, it, rr = sq.spaqr_gmres(F, rph, cih, vah, Bh, X=Xh, tol=TOL, maxit=MAXIT, stream=st)
+        t1 = time.perf_counter()
+        del F
+        if i >= a.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_total = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    nnz, n = p.nnz, p.n
+    h2d = (8 * nnz + 4 * nnz) + (8 * (n + 1) + 4 * nnz + 8 * nnz) + 2 * 8 * n * NRHS
+    d2h = 8 * n * NRHS
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ----
+    dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    dname, d = dom
+    per_launch_ms = d["total_ms"] / max(d["launches"], 1)
+    peaks = _peaks()
+    solve_kinds = {"solve_perm", "solve_front_fwd", "solve_ss_fwd", "solve_ss_bwd", "solve_front_bwd", "spmv",
+                   "gmres_orth", "gmres_small"}
+    if dname in solve_kinds:
+        ach = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": dname}
+    else:
+        ach = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dname,
+                "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz (derived)"}
+    roof["launches"] = d["launches"]
+    roof["avg_launch_ms"] = per_launch_ms
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_s * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "nrhs": NRHS, "eps": EPS, "tol": TOL,
+                   "levels": info["nlevels"], "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MiB memset outside the timed region)"},
+        "factor_ms_p50": _pct(fac_ms, 50), "factor_ms_p99": _pct(fac_ms, 99),
+        "gmres_ms_p50": _pct(gm_ms, 50), "gmres_ms_p99": _pct(gm_ms, 99),
+        "step_ms_p50": _pct(step_ms, 50), "step_ms_p99": _pct(step_ms, 99),
+        "order_ms": order_ms,
+        "gmres_iters": iters[-1], "relres_max": max(relres),
+        "factor_gflop": info["factor_flops"] / 1e9, "factor_mbytes": info["factor_bytes"] / 2 ** 20,
+        "rank_sum": info["rank_sum"], "size_sum": info["size_sum"], "top_separator": info["top_size"],
+        "phase_ms": dict(zip(["factorize", "scale", "sparsify", "merge"], info["phase_ms"])),
+        "e2e": {"value": NRHS * a.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kstats.items()
+                    if v["launches"]},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        try:
+            r = run_oracle(1)
+            cv = NRHS / (r["factor_s"] + NRHS * r["gmres_s"][0])
+            line["cpu_baseline"] = {
+                "value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"oracle factorisation of the full 256x256 matrix ({r['factor_s']:.1f} s) + oracle "
+                           f"GMRES of 1 of the 16 RHS ({r['gmres_s'][0]:.1f} s, {r['iters'][0]} iters); "
+                           "value = 16 / (factor + 16 x gmres)")}
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {e}"}
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return reference_arm(a)
+    return ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -195,6 +195,31 @@ int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, doubl
 
 void spaqr_factor_destroy(spaqr_factor_t* F);
 
+/* Kernel launch statistics (process wide).  The paper reports the runtime of
+ * every level split into factorize / scale / sparsify / merge (Section 4,
+ * "runtime per level" figure); these counters refine that split per kernel.
+ * launches counts every kernel the library enqueues; with profiling on
+ * (spaqr_profile(1)) each launch is also bracketed by CUDA events on its
+ * stream and total_ms sums their durations.  flops / bytes are the
+ * algorithmic FP64 flops and bytes of the counted launches (from block sizes,
+ * not from hardware counters). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+    double flops;
+    double bytes;
+} spaqr_kernel_stat;
+
+/* Zero all counters and drop pending event records. */
+void spaqr_stats_reset(void);
+/* on != 0: record CUDA events around every launch from now on. */
+void spaqr_profile(int on);
+/* Copy up to cap per-kernel records into out (cap may be 0), set *count to
+ * the number of kernel kinds and *total_launches to the launch count since the
+ * last reset.  Waits for pending events.  Errors: INVALID_ARG, CUDA. */
+int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t* total_launches);
+
 #ifdef __cplusplus
 }
 #endif

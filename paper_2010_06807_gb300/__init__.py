@@ -17,6 +17,7 @@ import numpy as np
 __all__ = [
     "SpaqrError", "load_library", "spaqr_order", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
     "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
+    "spaqr_stats_reset", "spaqr_profile", "spaqr_stats",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -65,13 +66,19 @@ class _Info(ctypes.Structure):
                 ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32)]
 
 
+class _KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 # every symbol include/spaqr.h declares
 EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
-    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
+    "spaqr_profile", "spaqr_stats",
 ]
 
 
@@ -101,6 +108,13 @@ def load_library(path=None):
         lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_factor_destroy.argtypes = [vp]
         lib.spaqr_factor_destroy.restype = None
+    if hasattr(lib, "spaqr_stats"):
+        lib.spaqr_stats_reset.argtypes = []
+        lib.spaqr_stats_reset.restype = None
+        lib.spaqr_profile.argtypes = [i32]
+        lib.spaqr_profile.restype = None
+        lib.spaqr_stats.argtypes = [ctypes.POINTER(_KStat), i32, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64)]
     if path is None:
         _lib = lib
     return lib
@@ -355,3 +369,30 @@ def spaqr_factor_ranks(F, level):
     _check(_lib.spaqr_factor_ranks(F._h, int(level), pairs.ctypes.data, margins.ctypes.data, n,
                                    ctypes.byref(cnt)))
     return pairs[:2 * n].reshape(n, 2), margins[:2 * n].reshape(n, 2)
+
+
+def spaqr_stats_reset():
+    """Zero the library's launch counters."""
+    load_library()
+    _lib.spaqr_stats_reset()
+
+
+def spaqr_profile(on=True):
+    """Bracket every library launch with CUDA events (for per-kernel timing)."""
+    load_library()
+    _lib.spaqr_profile(1 if on else 0)
+
+
+def spaqr_stats():
+    """(total launches, {kernel: dict(launches, total_ms, flops, bytes)}) since the last reset."""
+    load_library()
+    cnt = ctypes.c_int(0)
+    tot = ctypes.c_int64(0)
+    _check(_lib.spaqr_stats(None, 0, ctypes.byref(cnt), ctypes.byref(tot)))
+    arr = (_KStat * cnt.value)()
+    _check(_lib.spaqr_stats(arr, cnt.value, ctypes.byref(cnt), ctypes.byref(tot)))
+    out = {}
+    for k in arr:
+        out[k.name.decode()] = dict(launches=int(k.launches), total_ms=float(k.total_ms),
+                                    flops=float(k.flops), bytes=float(k.bytes))
+    return int(tot.value), out

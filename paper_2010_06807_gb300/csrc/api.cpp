@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -69,5 +70,113 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
     }
     if (rc != SPAQR_OK) { delete ord; return rc; }
     *out = ord;
+    return SPAQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting
+// ---------------------------------------------------------------------------
+namespace spaqr {
+namespace {
+const char* kKindNames[KK_COUNT] = {
+    "colscale", "gather", "front_qr", "front_apply", "scale_qr", "scale_apply", "cpqr",
+    "sparsify_merge", "solve_perm", "solve_front_fwd", "solve_ss_fwd", "solve_ss_bwd",
+    "solve_front_bwd", "spmv", "gmres_orth", "gmres_small"};
+struct Rec { int kind; cudaEvent_t a, b; };
+std::mutex g_mu;
+bool g_prof = false;
+int64_t g_launches = 0;
+int64_t g_count[KK_COUNT];
+double g_ms[KK_COUNT], g_flops[KK_COUNT], g_bytes[KK_COUNT];
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t get_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+}  // namespace
+
+int prof_begin(void* stream, int kind, double flops, double bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_launches++;
+    g_count[kind]++;
+    g_flops[kind] += flops;
+    g_bytes[kind] += bytes;
+    if (!g_prof) return -1;
+    Rec r;
+    r.kind = kind;
+    r.a = get_event();
+    r.b = get_event();
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, (cudaStream_t)stream);
+    g_recs.push_back(r);
+    return (int)g_recs.size() - 1;
+}
+
+void prof_end(void* stream, int rec) {
+    if (rec < 0) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (rec < (int)g_recs.size()) cudaEventRecord(g_recs[rec].b, (cudaStream_t)stream);
+}
+
+void prof_add(int rec, int kind, double flops, double bytes) {
+    (void)rec;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_flops[kind] += flops;
+    g_bytes[kind] += bytes;
+}
+}  // namespace spaqr
+
+extern "C" void spaqr_stats_reset(void) {
+    using namespace spaqr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (Rec& r : g_recs) {
+        cudaEventSynchronize(r.b);
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    g_launches = 0;
+    for (int k = 0; k < KK_COUNT; k++) { g_count[k] = 0; g_ms[k] = g_flops[k] = g_bytes[k] = 0.0; }
+}
+
+extern "C" void spaqr_profile(int on) {
+    std::lock_guard<std::mutex> lk(spaqr::g_mu);
+    spaqr::g_prof = on != 0;
+}
+
+extern "C" int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t* total_launches) {
+    using namespace spaqr;
+    if ((cap > 0 && !out) || !count) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (Rec& r : g_recs) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("event timing failed");
+            return SPAQR_ERR_CUDA;
+        }
+        g_ms[r.kind] += ms;
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    *count = KK_COUNT;
+    if (total_launches) *total_launches = g_launches;
+    for (int k = 0; k < KK_COUNT && k < cap; k++) {
+        std::memset(out[k].name, 0, sizeof(out[k].name));
+        std::strncpy(out[k].name, kKindNames[k], sizeof(out[k].name) - 1);
+        out[k].launches = g_count[k];
+        out[k].total_ms = g_ms[k];
+        out[k].flops = g_flops[k];
+        out[k].bytes = g_bytes[k];
+    }
     return SPAQR_OK;
 }

@@ -30,6 +30,13 @@
 #include "spaqr_internal.h"
 #include "tasks.h"
 
+#define SPAQR_LAUNCH(kind, flops, bytes, stream, ...)                            \
+    do {                                                                         \
+        const int rec_ = prof_begin((void*)(stream), (kind), (flops), (bytes)); \
+        __VA_ARGS__;                                                             \
+        prof_end((void*)(stream), rec_);                                         \
+    } while (0)
+
 namespace spaqr {
 
 // ---------------------------------------------------------------------------
@@ -422,8 +429,9 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
     tstart();
-    k_colscale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_cscp, d_csce, dval, opt->col_normalize,
-                                                             F->d_scale, d_flags);
+    SPAQR_LAUNCH(KK_COLSCALE, 2.0 * nnz, 24.0 * nnz + 16.0 * n, st,
+                 k_colscale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_cscp, d_csce, dval,
+                                                                          opt->col_normalize, F->d_scale, d_flags));
     C.launched();
 
     std::vector<int64_t> sz(o.steps[0].cl.size());
@@ -434,7 +442,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     double* arena = C.alloc<double>(lay.total, true);
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(arena, 0, sizeof(double) * lay.total, st));
-    k_gather<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, d_goff, dcol, dval, F->d_scale, arena);
+    SPAQR_LAUNCH(KK_GATHER, 1.0 * nnz, 36.0 * nnz, st,
+                 k_gather<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, d_goff, dcol, dval, F->d_scale, arena));
     C.launched();
     tstop(3);
 
@@ -460,6 +469,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         auto blk = [&](int e, int j) { return arena + lay.poff[j] + lay.rowoff[e]; };
 
         // ---------------- (i) factor the fronts ----------------
+        double fl_qr = 0, by_qr = 0, fl_ap = 0, by_ap = 0;
         std::vector<QRTask> qr;
         std::vector<double*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr);
         int64_t aux = 0;
@@ -481,7 +491,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 if (sz[s] == 0) continue;
                 qr.push_back(QRTask{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f]});
                 tmax = std::max<int>(tmax, (int)sz[s]);
-                flops += 2.0 * lay.H[s] * sz[s] * sz[s] - 2.0 / 3.0 * sz[s] * sz[s] * sz[s];
+                const double fq = 2.0 * lay.H[s] * sz[s] * sz[s] - 2.0 / 3.0 * sz[s] * sz[s] * sz[s];
+                flops += fq;
+                fl_qr += fq;
+                by_qr += 16.0 * lay.H[s] * sz[s] + 8.0 * sz[s] * sz[s];
                 if (k == L - 1) F->top_size = (int)sz[s];
             }
         }
@@ -517,7 +530,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 af.push_back(A1);
                 nmax = std::max(nmax, A1.n);
                 mmax = std::max(mmax, A1.m);
-                flops += (4.0 * A1.m * A1.n - 2.0 * A1.n * A1.n) * sz[j];
+                const double fa = (4.0 * A1.m * A1.n - 2.0 * A1.n * A1.n) * sz[j];
+                flops += fa;
+                fl_ap += fa;
+                by_ap += 16.0 * A1.m * sz[j] + 8.0 * A1.m * A1.n;
             }
             const int q = chunk_width(nmax, 6144);
             for (int64_t c0 = 0; c0 < sz[j]; c0 += q) {
@@ -550,7 +566,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         if (!qr.empty()) {
             QRTask* d = C.upload(qr, false);
             if (C.rc) return C.rc;
-            k_qr<<<(unsigned)qr.size(), NT, (size_t)(NWARP + tmax) * 8, st>>>(d);
+            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st, k_qr<<<(unsigned)qr.size(), NT, (size_t)(NWARP + tmax) * 8, st>>>(d));
             C.launched();
         }
         if (!at.empty()) {
@@ -558,7 +574,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             ApplyFront* d2 = C.upload(af, false);
             Seg* d3 = C.upload(asg, false);
             if (C.rc) return C.rc;
-            k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, wd);
+            SPAQR_LAUNCH(KK_FRONT_APPLY, fl_ap, by_ap, st,
+                         k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, wd));
             C.launched();
         }
         tstop(0);
@@ -568,9 +585,15 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         LV.colour_ptr.assign(1, 0);
         {
             int cur = 0;
+            LV.ff_flops.assign(1, 0.0);
+            LV.ff_fixed.assign(1, 0.0);
+            LV.ff_vec.assign(1, 0.0);
             for (size_t f = 0; f < sp.fronts.size(); f++) {
                 while (sp.colour[f] > cur) {
                     LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
+                    LV.ff_flops.push_back(0.0);
+                    LV.ff_fixed.push_back(0.0);
+                    LV.ff_vec.push_back(0.0);
                     cur++;
                 }
                 const int s = sp.fronts[f];
@@ -595,6 +618,17 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     sbytes += 8 * sz[s] * sz[j];
                 }
                 sf.nrsj = (int)srsj.size() - sf.rsj_begin;
+                {
+                    double snj = 0;
+                    for (int b = sf.rsj_begin; b < (int)srsj.size(); b++) snj += srsj[b].nj;
+                    const double m_ = sf.m, n_ = sf.n;
+                    LV.ff_flops.back() += 4.0 * m_ * n_ + n_ * n_;
+                    LV.ff_fixed.back() += 8.0 * (m_ * n_ + n_ * n_);
+                    LV.ff_vec.back() += 16.0 * m_;
+                    LV.fb_flops += 2.0 * n_ * snj + n_ * n_;
+                    LV.fb_fixed += 8.0 * (n_ * n_ + n_ * snj);
+                    LV.fb_vec += 16.0 * n_ + 8.0 * snj;
+                }
                 sfronts.push_back(sf);
                 LV.max_front_m = std::max(LV.max_front_m, sf.m);
                 LV.max_front_n = std::max(LV.max_front_n, sf.n);
@@ -620,6 +654,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             double* uaux = C.alloc<double>(ua, true);
             if (C.rc) return C.rc;
             std::vector<QRTask> sq;
+            double fl_sq = 0, by_sq = 0, fl_sc = 0, by_sc = 0;
             int tm = 1;
             int64_t a = 0;
             for (int p : rest) {
@@ -633,6 +668,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 sq.push_back(QRTask{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p]});
                 tm = std::max<int>(tm, (int)sz[p]);
                 flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
+                fl_sq += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
+                by_sq += 24.0 * sz[p] * sz[p];
             }
             // scaling of the off-diagonal blocks
             std::vector<ScaleTask> sc;
@@ -657,20 +694,24 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     t.q = chunk_width(sz[i], 6144);
                     smem_sc = std::max(smem_sc, (size_t)(2 * sz[i] * t.q) * 8);
                     sc.push_back(t);
-                    flops += 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
+                    const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
+                    flops += fs;
+                    fl_sc += fs;
+                    by_sc += 16.0 * sz[i] * sz[j] + 8.0 * sz[i] * sz[i] + 8.0 * sz[j] * sz[j];
                 }
             }
             tstart();
             if (!sq.empty()) {
                 QRTask* d = C.upload(sq, false);
                 if (C.rc) return C.rc;
-                k_qr<<<(unsigned)sq.size(), NT, (size_t)(NWARP + tm) * 8, st>>>(d);
+                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st, k_qr<<<(unsigned)sq.size(), NT, (size_t)(NWARP + tm) * 8, st>>>(d));
                 C.launched();
             }
             if (!sc.empty()) {
                 ScaleTask* d = C.upload(sc, false);
                 if (C.rc) return C.rc;
-                k_scale_apply<<<(unsigned)sc.size(), NT, smem_sc, st>>>(d, d_flags + 1);
+                SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
+                             k_scale_apply<<<(unsigned)sc.size(), NT, smem_sc, st>>>(d, d_flags + 1));
                 C.launched();
             }
             tstop(1);
@@ -712,6 +753,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (C.rc) return C.rc;
             C.cuda(cudaMemsetAsync(Rk, 0, sizeof(int) * ncl, st));
             int64_t mo = 0, no = 0, vo = 0, to = 0, ro = 0;
+            double by_cp = 16.0 * mtot;
             int kmx = 1;
             std::vector<int64_t> rdg_off(ncl, 0);
             for (int p : rest) {
@@ -758,7 +800,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 CPQRTask* d1 = C.upload(cp, false);
                 GatherSeg* d2 = C.upload(gs, false);
                 if (C.rc) return C.rc;
-                k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(4 * NWARP + kmx) * 8, st>>>(d1, d2, opt->eps);
+                SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
+                             k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(4 * NWARP + kmx) * 8, st>>>(d1, d2, opt->eps));
                 C.launched();
             }
             // ranks back to the host (the only device->host sync of a level)
@@ -777,7 +820,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 const int r = rk[p];
                 const double rr = r < kmax[p] ? rd[r] : (r > 0 ? rd[r - 1] : 0.0);
                 F->margins[k].push_back({rr, rd[0]});
-                flops += 4.0 * sz[p] * ncols[p] * r + 2.0 * sz[p] * ncols[p] * r;
+                // r steps of reflection (4 (m-k)(c-k)) and norm recomputation (2 (m-k)(c-k))
+                double fc = 0.0;
+                for (int kk = 0; kk < r; kk++) fc += 6.0 * (double)(sz[p] - kk) * (double)(ncols[p] - kk);
+                flops += fc;
+                prof_add(-1, KK_CPQR, fc, 0.0);
             }
         } else {
             for (int p : rest) newsz[p] = sz[p];
@@ -801,6 +848,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             C.cuda(cudaMemsetAsync(narena, 0, sizeof(double) * nl.total, st));
             std::vector<SparsifyTask> sk;
             int64_t scr = 0;
+            double fl_sp = 0, by_sp = 0;
             for (int j : rest) {
                 for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
                     const int i = sp.rowidx[e];
@@ -836,8 +884,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         t.ldtj = kmax[j];
                         t.scratch = (double*)(intptr_t)scr;  // offset, fixed below
                         scr += 2 * (int64_t)t.ri * t.nj + 2 * (int64_t)t.ri * t.rj;
-                        flops += 4.0 * t.ri * t.mi * t.nj + 4.0 * t.ri * t.nj * t.rj;
+                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.ri * t.nj * t.rj;
+                        flops += fp;
+                        fl_sp += fp;
                     }
+                    by_sp += 8.0 * t.mi * t.nj + 8.0 * std::max(t.ri, 1) * std::max(t.rj, 1);
                     sk.push_back(t);
                 }
             }
@@ -848,7 +899,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     if (t.mode == 0) t.scratch = sbuf + (int64_t)(intptr_t)t.scratch;
                 SparsifyTask* d = C.upload(sk, false);
                 if (C.rc) return C.rc;
-                k_sparsify<<<(unsigned)sk.size(), NT, 0, st>>>(d);
+                SPAQR_LAUNCH(KK_SPARSIFY, fl_sp, by_sp, st, k_sparsify<<<(unsigned)sk.size(), NT, 0, st>>>(d));
                 C.launched();
             }
             tstop(3);
@@ -871,7 +922,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     s.ldqt = std::max(kmax[p], 1);
                     sflops += 2.0 * (4.0 * sz[p] * sz[p] + 4.0 * sz[p] * newsz[p]);
                     sbytes += 8 * (2 * sz[p] * sz[p] + sz[p] * newsz[p]);
+                    const double n_ = (double)sz[p], r_ = (double)newsz[p];
+                    LV.ssf_flops += 5.0 * n_ * n_ + 4.0 * n_ * r_ + r_ * r_;
+                    LV.ssf_fixed += 8.0 * (2.0 * n_ * n_ + n_ * r_ + r_ * r_);
+                    LV.ssb_flops += 4.0 * n_ * r_ + r_ * r_ + n_ * n_;
+                    LV.ssb_fixed += 8.0 * (n_ * n_ + n_ * r_ + r_ * r_);
                 }
+                LV.ssf_vec += 16.0 * sz[p] + 8.0 * newsz[p];
+                LV.ssb_vec += 16.0 * sz[p] + 8.0 * newsz[p];
                 sss.push_back(s);
                 LV.max_ss_n = std::max(LV.max_ss_n, s.np);
                 LV.max_ss_r = std::max(LV.max_ss_r, s.r);

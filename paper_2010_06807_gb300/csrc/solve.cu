@@ -23,6 +23,13 @@
 #include "spaqr_internal.h"
 #include "tasks.h"
 
+#define SPAQR_LAUNCH(kind, flops, bytes, stream, ...)                            \
+    do {                                                                         \
+        const int rec_ = prof_begin((void*)(stream), (kind), (flops), (bytes)); \
+        __VA_ARGS__;                                                             \
+        prof_end((void*)(stream), rec_);                                         \
+    } while (0)
+
 namespace spaqr {
 
 __global__ void k_perm_in(int64_t n, int nrhs, const int64_t* __restrict__ perm, const double* __restrict__ B,
@@ -360,7 +367,8 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
     const int64_t n = F->n;
     const unsigned nb = (unsigned)((n + 255) / 256);
     double* Y0 = ws + F->lv[0].ws_off * nrhs;
-    k_perm_in<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows);
+    SPAQR_LAUNCH(KK_SOLVE_PERM, 0.0, 8.0 * n + 16.0 * n * nrhs, st,
+                 k_perm_in<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows));
     const int L = F->L;
     for (int k = 0; k < L; k++) {
         const SolveLevelHost& LV = F->lv[k];
@@ -373,15 +381,18 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
             for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
                 const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
                 if (b > a)
-                    k_sfront_fwd<<<b - a, NT, smem, st>>>(F->d_fronts + LV.front_begin + a, F->d_segs, Y, ldy, nrhs,
-                                                          q, wd);
+                    SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] + LV.ff_vec[c] * nrhs, st,
+                                 k_sfront_fwd<<<b - a, NT, smem, st>>>(F->d_fronts + LV.front_begin + a, F->d_segs, Y,
+                                                                       ldy, nrhs, q, wd));
             }
         }
         if (LV.nss > 0) {
             const SolveLevelHost& LN = F->lv[k + 1];
             const int q = qwidth(LV.max_ss_n, nrhs);
             const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
-            k_sss_fwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, q);
+            SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed + LV.ssf_vec * nrhs, st,
+                         k_sss_fwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs,
+                                                             LN.rows, nrhs, q));
         }
     }
     for (int k = L - 1; k >= 0; k--) {
@@ -392,14 +403,17 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
             const SolveLevelHost& LN = F->lv[k + 1];
             const int q = qwidth(LV.max_ss_n, nrhs);
             const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
-            k_sss_bwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, q,
-                                                singular);
+            SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed + LV.ssb_vec * nrhs, st,
+                         k_sss_bwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs,
+                                                             LN.rows, nrhs, q, singular));
         }
         if (LV.nfront > 0)
-            k_sfront_bwd<<<LV.nfront, NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs, F->d_rsj, Y, ldy, nrhs,
-                                                   singular);
+            SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed + LV.fb_vec * nrhs, st,
+                         k_sfront_bwd<<<LV.nfront, NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs, F->d_rsj, Y,
+                                                                ldy, nrhs, singular));
     }
-    k_perm_out<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx);
+    SPAQR_LAUNCH(KK_SOLVE_PERM, 1.0 * n * nrhs, 16.0 * n + 16.0 * n * nrhs, st,
+                 k_perm_out<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
     return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
 }
 
@@ -531,12 +545,10 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nrhs, st));
     C.cuda(cudaMemsetAsync(g, 0, sizeof(double) * ldh * nrhs, st));
     // X0 = X; r0 = B - A X0 (into V_0); beta = ||r0||; ||b||
-    k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dX, lx, X0, n);
-    k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb);
-    k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n);
-    k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1);  // ||b||^2 (nvec = 1, U = W)
-    k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1);  // ||r0||^2
-    C.launched();
+    SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dX, lx, X0, n));
+    SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb));
+    SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n));
+    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1));  // ||b||^2 (nvec = 1, U = W) k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1);  // ||r0||^2 C.launched();
     std::vector<double> hb(nrhs), hr(nrhs), hest(nrhs), hres(nrhs, 1.0);
     std::vector<int> hact(nrhs, 1), hit(nrhs, 0), hwant(nrhs, 0);
     C.cuda(cudaMemcpyAsync(hb.data(), bn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
@@ -562,8 +574,7 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     C.cuda(cudaMemcpyAsync(g, hg.data(), 8 * ldh * nrhs, cudaMemcpyHostToDevice, st));
     C.cuda(cudaMemcpyAsync(hn, hr.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
     C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
-    k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn);  // V_0 = r0 / beta
-    C.launched();
+    SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn));  // V_0 = r0 / beta C.launched();
     int nact = 0;
     for (int c = 0; c < nrhs; c++) nact += hact[c];
     int j = 0;
@@ -581,19 +592,18 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         // z = M^{-1} v_j ; w = A z
         int rc = apply_device(F, nrhs, Vj, n, Zv, n, st, ws, flag);
         if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
-        k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zv, n, Wv, n);
+        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st, k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zv, n, Wv, n));
         // classical Gram-Schmidt, twice
-        k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h1, ldh);
-        k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h1, ldh, Wv, active);
-        k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h2, ldh);
-        k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h2, ldh, Wv, active);
-        k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, hn, 1);
-        k_sqrtv<<<1, 32, 0, st>>>(nrhs, hn);
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * ((j + 1) + 1) * nrhs, st, k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h1, ldh));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 3) * nrhs, st, k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h1, ldh, Wv, active));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * ((j + 1) + 1) * nrhs, st, k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h2, ldh));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 3) * nrhs, st, k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h2, ldh, Wv, active));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, hn, 1));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * nrhs, 16.0 * nrhs, st, k_sqrtv<<<1, 32, 0, st>>>(nrhs, hn));
         C.launched();
         std::vector<double> hnv(nrhs);
-        k_normalize<<<nbl, 256, 0, st>>>(n, nrhs, Wv, hn, Vb + (int64_t)(j + 1) * n * nrhs, active);
-        k_givens<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, h1, h2, hn, cs, sn, g, ldh, bn, est,
-                                                  active);
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_normalize<<<nbl, 256, 0, st>>>(n, nrhs, Wv, hn, Vb + (int64_t)(j + 1) * n * nrhs, active));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 6.0 * (j + 1) * nrhs, 16.0 * (j + 2) * nrhs, st, k_givens<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, h1, h2, hn, cs, sn, g, ldh, bn, est, active));
         C.launched();
         C.cuda(cudaMemcpyAsync(hest.data(), est, 8 * nrhs, cudaMemcpyDeviceToHost, st));
         C.cuda(cudaMemcpyAsync(hnv.data(), hn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
@@ -610,14 +620,14 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         // candidate x = x0 + M^{-1} (V y) for the wanted columns; keep it if the
         // recomputed residual meets tol
         C.cuda(cudaMemcpyAsync(want, hwant.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
-        k_hsolve<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, g, ldh, ycoef, want);
-        k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, ycoef, ldh, Wv);
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * (j + 1) * (j + 1) * nrhs, 8.0 * (j + 1) * (j + 1) * nrhs, st, k_hsolve<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, g, ldh, ycoef, want));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 2) * nrhs, st, k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, ycoef, ldh, Wv));
         rc = apply_device(F, nrhs, Wv, n, Zv, n, st, ws, flag);
         if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
         // trial X into Wv: Wv = X0 + Zv (all columns), residual into Zv
-        k_accept<<<nbl, 256, 0, st>>>(n, nrhs, X0, n, Zv, Wv, n, want);
-        k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv);
-        k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Zv, 1, Zv, rn, 1);
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 24.0 * n * nrhs, st, k_accept<<<nbl, 256, 0, st>>>(n, nrhs, X0, n, Zv, Wv, n, want));
+        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Zv, 1, Zv, rn, 1));
         C.launched();
         std::vector<double> hrn(nrhs);
         C.cuda(cudaMemcpyAsync(hrn.data(), rn, 8 * nrhs, cudaMemcpyDeviceToHost, st));

@@ -151,6 +151,12 @@ struct SolveLevelHost {
     int front_begin = 0, nfront = 0;  // into the device SolveFront array
     int ss_begin = 0, nss = 0;        // into the device SolveSS array
     int max_front_m = 0, max_front_n = 0, max_ss_n = 0, max_ss_r = 0;
+    // algorithmic work of the level's solve launches: flops per RHS, bytes of
+    // factor data read once plus vector bytes per RHS
+    std::vector<double> ff_flops, ff_fixed, ff_vec;   // forward fronts, per colour
+    double ssf_flops = 0, ssf_fixed = 0, ssf_vec = 0; // forward scale/sparsify
+    double ssb_flops = 0, ssb_fixed = 0, ssb_vec = 0; // backward scale/sparsify
+    double fb_flops = 0, fb_fixed = 0, fb_vec = 0;    // backward fronts
 };
 
 struct spaqr_factor_s {
