@@ -86,7 +86,7 @@ out = {"factor_s": tf, "gmres_s": [], "iters": []}
 cols = list(range(%(ncols)d))
 for c in cols:
     t0 = time.perf_counter()
-    x, it, rr, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, c % b.shape[1]],
+    x, it, rr, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, c %% b.shape[1]],
                              lambda v: osq.solve(F, v), tol=%(tol)r, maxit=%(maxit)d)
     out["gmres_s"].append(time.perf_counter() - t0)
     out["iters"].append(int(it))

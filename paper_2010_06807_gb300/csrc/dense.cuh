@@ -6,8 +6,20 @@
 // beta = -sign(alpha) sqrt(alpha^2 + x.x) with sign(0) = +1,
 // tau = (beta - alpha) / beta, v = (1, x / (alpha - beta)).  A factored
 // matrix keeps v below the diagonal (unit diagonal implied) and R on and
-// above it.  Block reflector (compact WY): H_0 ... H_{t-1} = I - V T V^T with
-// T upper triangular.
+// above it.
+//
+// Blocked reflectors: reflectors are grouped in panels of NB consecutive
+// ones; panel b (reflectors p0 .. p0+pb-1) is I - V_b T_b V_b^T with T_b upper
+// triangular, stored as the diagonal block T[p0:p0+pb, p0:p0+pb] of an array
+// with leading dimension ldt (the off-diagonal blocks are unused).
+// Q = H_0 H_1 ... = Q_0 Q_1 ... so Q^T B applies panels 0, 1, ... with T_b^T
+// and Q B applies them in reverse order with T_b.
+//
+// GB300 executes FP64 at ~2 DFMA per clock per SM, and a warp shuffle
+// reduction costs one DADD per step on that same pipe.  The routines therefore
+// compute every dot product as one thread's sequential DFMA chain (thread per
+// output) and only reduce across threads where a result is needed once per
+// column (norms, Householder scalars).
 //
 // Every routine is called by all NT threads of a CTA and synchronises
 // internally; operands may be in global or shared memory.
@@ -19,6 +31,7 @@ namespace spaqr {
 
 constexpr int NT = 256;          // threads per CTA of every kernel
 constexpr int NWARP = NT / 32;
+constexpr int NB = 16;           // reflectors per panel
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -41,35 +54,51 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Largest value over the CTA, ties to the smallest index; every thread gets it.
-__device__ __forceinline__ void block_argmax(double v, int idx, double* redv, int* redi, double& bv,
-                                             int& bi) {
+// Values are non-negative, so their IEEE bit patterns order like the values and
+// the comparison runs on the integer pipe.
+__device__ __forceinline__ void block_argmax(double v, int idx, long long* redv, int* redi, double& bv, int& bi) {
+    long long key = __double_as_longlong(v);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; }
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
-    if (l == 0) { redv[w] = v; redi[w] = idx; }
+    if (l == 0) { redv[w] = key; redi[w] = idx; }
     __syncthreads();
-    bv = redv[0];
+    long long bk = redv[0];
     bi = redi[0];
     for (int i = 1; i < NWARP; i++) {
-        if (redv[i] > bv || (redv[i] == bv && redi[i] < bi)) { bv = redv[i]; bi = redi[i]; }
+        if (redv[i] > bk || (redv[i] == bk && redi[i] < bi)) { bk = redv[i]; bi = redi[i]; }
     }
+    bv = __longlong_as_double(bk);
 }
 
-// Householder vector of column `col` (rows k..m-1) in place: col[k] <- beta,
-// col[k+1..] <- v (below the unit).  Returns tau.  All threads get tau.
-__device__ __forceinline__ double cta_house(double* col, int k, int m, double* red) {
+// Strided view of a matrix: element (r, c) is base[row(r) * rs + c * cs] with
+// row(r) = rmap ? rmap[r] : r.
+struct Mat {
+    double* base;
+    int64_t rs, cs;
+    const int* rmap;
+    __device__ __forceinline__ double& at(int r, int c) const {
+        const int64_t rr = rmap ? (int64_t)rmap[r] : (int64_t)r;
+        return base[rr * rs + (int64_t)c * cs];
+    }
+    __device__ __forceinline__ Mat cols(int c0) const { return Mat{base + (int64_t)c0 * cs, rs, cs, rmap}; }
+};
+
+// Householder vector of column `col` (rows k..m-1, element stride `stride`)
+// in place: col[k] <- beta, col[k+1..] <- v.  Returns tau to every thread.
+__device__ __forceinline__ double cta_house(double* col, int64_t stride, int k, int m, double* red) {
     double part = 0.0;
     for (int r = k + 1 + threadIdx.x; r < m; r += NT) {
-        double x = col[r];
+        const double x = col[(int64_t)r * stride];
         part += x * x;
     }
     const double xn2 = block_sum(part, red);
-    const double alpha = col[k];
+    const double alpha = col[(int64_t)k * stride];
     double tk = 0.0, beta = alpha, denom = 1.0;
     if (xn2 != 0.0) {
         const double s = sqrt(alpha * alpha + xn2);
@@ -78,164 +107,309 @@ __device__ __forceinline__ double cta_house(double* col, int k, int m, double* r
         denom = alpha - beta;
     }
     __syncthreads();
-    if (threadIdx.x == 0) col[k] = beta;
+    if (threadIdx.x == 0) col[(int64_t)k * stride] = beta;
     if (tk != 0.0)
-        for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[r] = col[r] / denom;
+        for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] = col[(int64_t)r * stride] / denom;
     __syncthreads();
     return tk;
 }
 
-// Apply H_k = I - tau v v^T (v = e_k + col[k+1..m-1]) to columns j0..j1-1 of A.
-// One warp per column.
-__device__ __forceinline__ void cta_reflect_cols(const double* col, double tk, int k, int m, double* A,
-                                                 int64_t lda, int j0, int j1) {
-    if (tk == 0.0) return;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j = j0 + w; j < j1; j += NWARP) {
-        double* cj = A + (int64_t)j * lda;
-        const double ck = cj[k];
-        double d = 0.0;
-        for (int r = k + 1 + l; r < m; r += 32) d += col[r] * cj[r];
-        d = warp_sum(d) + ck;
-        const double f = tk * d;
-        if (l == 0) cj[k] = ck - f;
-        for (int r = k + 1 + l; r < m; r += 32) cj[r] -= f * col[r];
-    }
-}
-
-// T factor (forward, columnwise) of the t reflectors stored in A (m rows).
-// T is t x t upper triangular, leading dimension ldt.  `z` holds t doubles of
-// shared memory.
-static __device__ void cta_form_t(const double* A, int64_t lda, int m, int t, const double* tau, double* T,
-                           int ldt, double* z) {
-    for (int k = 0; k < t; k++) {
-        const double tk = tau[k];
-        // z_i = V(:,i)^T v_k for i < k
-        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        for (int i = w; i < k; i += NWARP) {
-            const double* vi = A + (int64_t)i * lda;
-            const double* vk = A + (int64_t)k * lda;
-            double d = 0.0;
-            for (int r = k + 1 + l; r < m; r += 32) d += vi[r] * vk[r];
-            d = warp_sum(d) + vi[k];
-            if (l == 0) z[i] = d;
+// Diagonal T blocks of the t reflectors in V (m rows, column-major, ldv); the
+// diagonal/upper part of V is not read (unit diagonal implied).  `G` holds
+// NB * NB doubles of shared memory.
+static __device__ void cta_form_tblocks(const double* V, int64_t ldv, int m, int t, const double* tau, double* T,
+                                        int ldt, double* G) {
+    for (int p0 = 0; p0 < t; p0 += NB) {
+        const int pb = t - p0 < NB ? t - p0 : NB;
+        // G(i, k) = V(:, p0+i)^T V(:, p0+k), i < k
+        for (int o = threadIdx.x; o < pb * pb; o += NT) {
+            const int i = o % pb, k = o / pb;
+            if (i >= k) continue;
+            const double* vi = V + (int64_t)(p0 + i) * ldv;
+            const double* vk = V + (int64_t)(p0 + k) * ldv;
+            double s = vi[p0 + k];
+            for (int r = p0 + k + 1; r < m; r++) s += vi[r] * vk[r];
+            G[i + k * NB] = s;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < k; i += NT) {
-            double s = 0.0;
-            for (int p = i; p < k; p++) s += T[i + (int64_t)p * ldt] * z[p];
-            T[i + (int64_t)k * ldt] = -tk * s;
+        for (int k = 0; k < pb; k++) {
+            const double tk = tau[p0 + k];
+            for (int i = threadIdx.x; i < k; i += NT) {
+                double s = 0.0;
+                for (int u = i; u < k; u++) s += T[(p0 + i) + (int64_t)(p0 + u) * ldt] * G[u + k * NB];
+                T[(p0 + i) + (int64_t)(p0 + k) * ldt] = -tk * s;
+            }
+            if (threadIdx.x == 0) T[(p0 + k) + (int64_t)(p0 + k) * ldt] = tk;
+            for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[(p0 + i) + (int64_t)(p0 + k) * ldt] = 0.0;
+            __syncthreads();
         }
-        if (threadIdx.x == 0) T[k + (int64_t)k * ldt] = tk;
-        // zero the strictly lower part of column k for clean storage
-        for (int i = k + 1 + threadIdx.x; i < t; i += NT) T[i + (int64_t)k * ldt] = 0.0;
-        __syncthreads();
     }
 }
 
-// In-place Householder QR of A (m x n, lda); tau gets min(m, n) entries; if T
-// is non-null the compact-WY T (t x t, ldt) is formed.  `smem` holds
-// NWARP + t doubles.
-static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau, double* T, int ldt,
-                       double* smem) {
-    double* red = smem;
-    const int t = m < n ? m : n;
-    for (int k = 0; k < t; k++) {
-        double* col = A + (int64_t)k * lda;
-        const double tk = cta_house(col, k, m, red);
-        if (threadIdx.x == 0) tau[k] = tk;
-        cta_reflect_cols(col, tk, k, m, A, lda, k + 1, n);
-        __syncthreads();
-    }
-    if (T != nullptr) cta_form_t(A, lda, m, t, tau, T, ldt, smem + NWARP);
+// Number of row groups that split each dot product so that nout outputs keep
+// all NT threads busy (a power of two, 1 when nout >= NT / 2).
+__device__ __forceinline__ int row_groups(int nout) {
+    int g = 1;
+    while (g < 16 && nout * g * 2 <= NT) g *= 2;
+    return g;
 }
 
-// Element (r, c) of an m x q operand addressed through an optional row map:
-// row r lives at base[(rmap ? rmap[r] : r) + c * ld].
-struct RowMapped {
-    double* base;
-    int64_t ld;
-    const int* rmap;
-    __device__ __forceinline__ double& at(int r, int c) const {
-        return base[(rmap ? (int64_t)rmap[r] : (int64_t)r) + (int64_t)c * ld];
+// W1(i, c) = sum over the rows of Vcol_i(r) * Bv(r, c) for the pb x q outputs;
+// `dot(i, c, r0, step)` returns a partial sum over rows r0, r0 + step, ...
+// P holds NT doubles.
+template <class Dot>
+__device__ __forceinline__ void cta_small_gemv(int pb, int q, double* W1, double* P, Dot dot) {
+    const int nout = pb * q;
+    const int G = row_groups(nout);
+    if (G == 1) {
+        for (int o = threadIdx.x; o < nout; o += NT) W1[o] = dot(o % pb, o / pb, 0, 1);
+        __syncthreads();
+        return;
     }
-};
-
-// B <- (I - V T V^T)^T B  (trans = true, i.e. Q^T B)  or  (I - V T V^T) B.
-// V: m x n unit lower trapezoidal stored in place (v below the diagonal,
-// diagonal/upper part ignored) unless `explicit_v` (then read as is).
-// B: m x q through a row map.  W: 2 * n * q doubles of shared memory.
-static __device__ void cta_apply_wy(const double* V, int64_t ldv, int m, int n, const double* T, int ldt,
-                             bool explicit_v, RowMapped B, int q, bool trans, double* W) {
-    if (n == 0 || q == 0) return;
-    double* W1 = W;
-    double* W2 = W + (int64_t)n * q;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    // W1 = V^T B (n x q)
-    for (int o = w; o < n * q; o += NWARP) {
-        const int i = o % n, c = o / n;
-        const double* vi = V + (int64_t)i * ldv;
-        double d = 0.0;
-        for (int r = i + 1 + l; r < m; r += 32) d += vi[r] * B.at(r, c);
-        d = warp_sum(d);
-        if (l == 0) W1[o] = d + (explicit_v ? vi[i] : 1.0) * B.at(i, c);
+    if (threadIdx.x < nout * G) {
+        const int o = threadIdx.x % nout, g = threadIdx.x / nout;
+        P[threadIdx.x] = dot(o % pb, o / pb, g, G);
     }
     __syncthreads();
-    // W2 = T^T W1 (trans) or T W1
-    for (int o = threadIdx.x; o < n * q; o += NT) {
-        const int i = o % n, c = o / n;
+    for (int o = threadIdx.x; o < nout; o += NT) {
+        double s = P[o];
+        for (int g = 1; g < G; g++) s += P[o + g * nout];
+        W1[o] = s;
+    }
+    __syncthreads();
+}
+
+// W2 = T_b^T W1 (trans) or T_b W1 for the diagonal T block at p0.
+__device__ __forceinline__ void cta_tblock_mul(const double* T, int ldt, int p0, int pb, int q, bool trans,
+                                               const double* W1, double* W2) {
+    for (int o = threadIdx.x; o < pb * q; o += NT) {
+        const int i = o % pb, c = o / pb;
         double s = 0.0;
         if (trans) {
-            for (int p = 0; p <= i; p++) s += T[p + (int64_t)i * ldt] * W1[p + c * n];
+            for (int u = 0; u <= i; u++) s += T[(p0 + u) + (int64_t)(p0 + i) * ldt] * W1[u + c * pb];
         } else {
-            for (int p = i; p < n; p++) s += T[i + (int64_t)p * ldt] * W1[p + c * n];
+            for (int u = i; u < pb; u++) s += T[(p0 + i) + (int64_t)(p0 + u) * ldt] * W1[u + c * pb];
         }
         W2[o] = s;
     }
     __syncthreads();
-    // B -= V W2
+}
+
+// B <- Q^T B (trans) or Q B for the t reflectors in V (m rows) with diagonal T
+// blocks; B is m x q, read and written in place (global or shared memory).
+// explicit_v: V holds its unit diagonal (and zeros above it) explicitly;
+// otherwise the diagonal is taken as 1 and the upper part is ignored.
+// W holds 2 * NB * q + NT doubles of shared memory.
+static __device__ void cta_apply_q(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
+                                   bool explicit_v, Mat B, int q, bool trans, double* W) {
+    if (t <= 0 || q <= 0) return;
+    double* W1 = W;
+    double* W2 = W + NB * q;
+    double* P = W + 2 * NB * q;
+    const int nbk = (t + NB - 1) / NB;
+    for (int bb = 0; bb < nbk; bb++) {
+        const int b = trans ? bb : nbk - 1 - bb;
+        const int p0 = b * NB;
+        const int pb = t - p0 < NB ? t - p0 : NB;
+        cta_small_gemv(pb, q, W1, P, [&](int i, int c, int g, int G) {
+            const int col = p0 + i;
+            const double* v = V + (int64_t)col * ldv;
+            double s = 0.0;
+            if (g == 0) s = (explicit_v ? v[col] : 1.0) * B.at(col, c);
+            for (int r = col + 1 + (g == 0 ? G - 1 : g - 1); r < m; r += G) s += v[r] * B.at(r, c);
+            return s;
+        });
+        cta_tblock_mul(T, ldt, p0, pb, q, trans, W1, W2);
+        // B(r, c) -= sum_{i <= r - p0} V(r, p0+i) W2(i, c), r >= p0
+        const int rows = m - p0;
+        for (int o = threadIdx.x; o < rows * q; o += NT) {
+            const int rr = o % rows, c = o / rows, r = p0 + rr;
+            const int top = rr < pb - 1 ? rr : pb - 1;   // last i with p0 + i <= r
+            double s = 0.0;
+            for (int i = 0; i < top; i++) s += V[r + (int64_t)(p0 + i) * ldv] * W2[i + c * pb];
+            const double vd = (rr == top) ? (explicit_v ? V[r + (int64_t)r * ldv] : 1.0)
+                                          : V[r + (int64_t)(p0 + top) * ldv];
+            s += vd * W2[top + c * pb];
+            B.at(r, c) -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// Shared memory (doubles) of cta_apply_q_staged for m rows and q columns.
+__host__ __device__ constexpr int64_t staged_smem_doubles(int m, int q) {
+    return (int64_t)(m | 1) * (q + NB) + 2 * NB * q + NT;
+}
+
+// Same as cta_apply_q, with B (m x q) staged into shared memory once and each
+// panel of V staged before use, so the inner loops read shared memory only.
+// smem: staged_smem_doubles(m, q).
+static __device__ void cta_apply_q_staged(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
+                                          bool explicit_v, Mat B, int q, bool trans, double* sm) {
+    if (t <= 0 || q <= 0) return;
+    const int ld = m | 1;
+    double* Bs = sm;
+    double* Vs = Bs + (int64_t)ld * q;
+    double* W1 = Vs + (int64_t)ld * NB;
+    double* W2 = W1 + NB * q;
+    double* P = W2 + NB * q;
     for (int o = threadIdx.x; o < m * q; o += NT) {
         const int r = o % m, c = o / m;
-        const int top = r < n ? r : n;  // strictly-lower part: columns i < min(r, n)
-        double s = 0.0;
-        for (int i = 0; i < top; i++) s += V[r + (int64_t)i * ldv] * W2[i + c * n];
-        if (r < n) s += (explicit_v ? V[r + (int64_t)r * ldv] : 1.0) * W2[r + c * n];
-        B.at(r, c) -= s;
+        Bs[r + c * ld] = B.at(r, c);
+    }
+    const int nbk = (t + NB - 1) / NB;
+    for (int bb = 0; bb < nbk; bb++) {
+        const int b = trans ? bb : nbk - 1 - bb;
+        const int p0 = b * NB;
+        const int pb = t - p0 < NB ? t - p0 : NB;
+        const int rows = m - p0;
+        // Vs(rr, i) = V(p0 + rr, p0 + i) with the unit diagonal and zeros above
+        for (int o = threadIdx.x; o < rows * pb; o += NT) {
+            const int rr = o % rows, i = o / rows;
+            const int r = p0 + rr, col = p0 + i;
+            double v = 0.0;
+            if (r > col) v = V[r + (int64_t)col * ldv];
+            else if (r == col) v = explicit_v ? V[r + (int64_t)col * ldv] : 1.0;
+            Vs[rr + i * ld] = v;
+        }
+        __syncthreads();
+        cta_small_gemv(pb, q, W1, P, [&](int i, int c, int g, int G) {
+            const double* vi = Vs + i * ld;
+            const double* bc = Bs + p0 + c * ld;
+            double s = 0.0;
+            for (int rr = i + g; rr < rows; rr += G) s += vi[rr] * bc[rr];
+            return s;
+        });
+        cta_tblock_mul(T, ldt, p0, pb, q, trans, W1, W2);
+        for (int o = threadIdx.x; o < rows * q; o += NT) {
+            const int rr = o % rows, c = o / rows;
+            const int top = rr < pb - 1 ? rr : pb - 1;
+            double s = 0.0;
+            for (int i = 0; i <= top; i++) s += Vs[rr + i * ld] * W2[i + c * pb];
+            Bs[p0 + rr + c * ld] -= s;
+        }
+        __syncthreads();
+    }
+    for (int o = threadIdx.x; o < m * q; o += NT) {
+        const int r = o % m, c = o / m;
+        B.at(r, c) = Bs[r + c * ld];
     }
     __syncthreads();
 }
 
+// cta_apply_q over q columns in chunks of qc (W: 2 * NB * qc + NT doubles).
+static __device__ void cta_apply_q_chunked(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
+                                           bool explicit_v, Mat B, int q, int qc, bool trans, double* W) {
+    for (int c0 = 0; c0 < q; c0 += qc) {
+        const int w = q - c0 < qc ? q - c0 : qc;
+        cta_apply_q(V, ldv, m, t, T, ldt, explicit_v, B.cols(c0), w, trans, W);
+    }
+}
+
+// Shared memory (doubles) needed by cta_qr with column chunk qc.
+__host__ __device__ constexpr int qr_smem_doubles(int qc) { return NWARP + NT + NB + NB * NB + 2 * NB * qc + NT; }
+
+// In-place blocked Householder QR of A (m x n, lda).  tau gets min(m, n)
+// entries and T the diagonal NB blocks (ldt).  smem: qr_smem_doubles(qc).
+static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau, double* T, int ldt, int qc,
+                              double* smem) {
+    double* red = smem;
+    double* P = red + NWARP;     // NT partial dots
+    double* Wk = P + NT;         // NB
+    double* G = Wk + NB;         // NB * NB
+    double* W = G + NB * NB;     // 2 * NB * qc + NT
+    const int t = m < n ? m : n;
+    for (int p0 = 0; p0 < t; p0 += NB) {
+        const int pe = (t - p0 < NB ? t : p0 + NB);   // panel columns [p0, pe)
+        for (int k = p0; k < pe; k++) {
+            double* col = A + (int64_t)k * lda;
+            const double tk = cta_house(col, 1, k, m, red);
+            if (threadIdx.x == 0) tau[k] = tk;
+            const int ncol = pe - k - 1;
+            if (ncol > 0 && tk != 0.0) {
+                // partial dots: NB column slots x (NT / NB) row groups
+                const int js = threadIdx.x % NB, g = threadIdx.x / NB;
+                double part = 0.0;
+                if (js < ncol) {
+                    const double* cj = A + (int64_t)(k + 1 + js) * lda;
+                    for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
+                }
+                P[threadIdx.x] = part;
+                __syncthreads();
+                if (threadIdx.x < ncol) {
+                    double s = A[k + (int64_t)(k + 1 + threadIdx.x) * lda];
+                    for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
+                    Wk[threadIdx.x] = tk * s;
+                }
+                __syncthreads();
+                const int rows = m - k;
+                for (int o = threadIdx.x; o < rows * ncol; o += NT) {
+                    const int rr = o % rows, jj = o / rows, r = k + rr;
+                    const double v = rr == 0 ? 1.0 : col[r];
+                    A[r + (int64_t)(k + 1 + jj) * lda] -= Wk[jj] * v;
+                }
+            }
+            __syncthreads();
+        }
+        // T block of the panel
+        cta_form_tblocks(A + p0 + (int64_t)p0 * lda, lda, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt,
+                         ldt, G);
+        // trailing update of the columns right of the panel
+        if (pe < n) {
+            Mat B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};
+            cta_apply_q_chunked(A + p0 + (int64_t)p0 * lda, lda, m - p0, pe - p0, T + p0 + (int64_t)p0 * ldt, ldt,
+                                false, B, n - pe, qc, true, W);
+        }
+    }
+}
+
 // B <- B R^{-1}: B is mi x nj (ldb), R upper triangular nj x nj (ldr).
-// Thread-per-row forward substitution; returns false (via flag) on a zero
-// diagonal.
-static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int nj, const double* R,
-                                     int64_t ldr, int* singular) {
+// Thread-per-row forward substitution; sets *singular on a zero diagonal.
+static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int nj, const double* R, int64_t ldr,
+                                            int* singular) {
     for (int r = threadIdx.x; r < mi; r += NT) {
         for (int c = 0; c < nj; c++) {
             double s = B[r + (int64_t)c * ldb];
             for (int p = 0; p < c; p++) s -= B[r + (int64_t)p * ldb] * R[p + (int64_t)c * ldr];
             const double d = R[c + (int64_t)c * ldr];
-            if (d == 0.0) { *singular = 1; s = 0.0; }
-            else s = s / d;
+            if (d == 0.0) {
+                *singular = 1;
+                s = 0.0;
+            } else {
+                s = s / d;
+            }
             B[r + (int64_t)c * ldb] = s;
         }
     }
     __syncthreads();
 }
 
-// X <- R^{-1} X for X n x q through a row map, R upper n x n (ldr).
-// Column-oriented back substitution.
-static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, RowMapped X, int q, int* singular) {
-    for (int i = n - 1; i >= 0; i--) {
-        const double d = R[i + (int64_t)i * ldr];
+// X <- R^{-1} X for X n x q, R upper n x n (ldr).  Back substitution by
+// diagonal blocks of NB rows: each block is solved by one thread per column,
+// then the rows above it are updated by all threads.
+static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, Mat X, int q, int* singular) {
+    for (int i1 = n; i1 > 0; i1 -= NB) {
+        const int i0 = i1 - NB > 0 ? i1 - NB : 0;
         for (int c = threadIdx.x; c < q; c += NT) {
-            if (d == 0.0) { *singular = 1; X.at(i, c) = 0.0; }
-            else X.at(i, c) = X.at(i, c) / d;
+            for (int i = i1 - 1; i >= i0; i--) {
+                double s = X.at(i, c);
+                for (int u = i + 1; u < i1; u++) s -= R[i + (int64_t)u * ldr] * X.at(u, c);
+                const double d = R[i + (int64_t)i * ldr];
+                if (d == 0.0) {
+                    *singular = 1;
+                    s = 0.0;
+                } else {
+                    s = s / d;
+                }
+                X.at(i, c) = s;
+            }
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < i * q; o += NT) {
-            const int r = o % i, c = o / i;
-            X.at(r, c) -= R[r + (int64_t)i * ldr] * X.at(i, c);
+        for (int o = threadIdx.x; o < i0 * q; o += NT) {
+            const int r = o % i0, c = o / i0;
+            double s = 0.0;
+            for (int u = i0; u < i1; u++) s += R[r + (int64_t)u * ldr] * X.at(u, c);
+            X.at(r, c) -= s;
         }
         __syncthreads();
     }

@@ -68,19 +68,24 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
     arena[off[e]] = val[e] * d[colind[e]];
 }
 
+constexpr int QC = 32;       // column chunk of the blocked updates
+constexpr int QAPPLY = 64;   // column chunk of one front-apply task
+
 __global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     const QRTask t = tasks[blockIdx.x];
     const int tt = t.m < t.n ? t.m : t.n;
-    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, sm);
+    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, sm);
 }
 
+// smem layout: rmap (rmap_doubles doubles) then the work area of the apply
+// (staged: staged_smem_doubles(m, q); otherwise 2 * NB * q + NT).
 __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask* __restrict__ tasks,
                                                     const ApplyFront* __restrict__ fronts,
-                                                    const Seg* __restrict__ segs, int wdoubles) {
+                                                    const Seg* __restrict__ segs, int rmap_doubles, int staged) {
     extern __shared__ double sm[];
-    double* W = sm;
-    int* rmap = reinterpret_cast<int*>(sm + wdoubles);
+    int* rmap = reinterpret_cast<int*>(sm);
+    double* W = sm + rmap_doubles;
     const ApplyTask t = tasks[blockIdx.x];
     for (int f = 0; f < t.nfr; f++) {
         const ApplyFront F = fronts[t.fr_begin + f];
@@ -91,61 +96,58 @@ __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask* __restrict_
             pos += g.len;
         }
         __syncthreads();
-        RowMapped B{t.B, t.ldb, rmap};
-        cta_apply_wy(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
+        const Mat B{t.B, 1, t.ldb, rmap};
+        if (staged) cta_apply_q_staged(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
+        else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
     }
 }
 
 __global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask* __restrict__ tasks, int* singular) {
     extern __shared__ double sm[];
     const ScaleTask t = tasks[blockIdx.x];
-    for (int c0 = 0; c0 < t.nj; c0 += t.q) {
-        const int q = min(t.q, t.nj - c0);
-        RowMapped B{t.A + (int64_t)c0 * t.lda, t.lda, nullptr};
-        cta_apply_wy(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, B, q, true, sm);
-    }
+    cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, Mat{t.A, 1, t.lda, nullptr}, t.nj, QC, true, sm);
     cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, singular);
 }
 
-// Truncated CPQR with column norms recomputed from scratch at every step
-// (fused into the reflector update), pivot = largest norm, ties to the lowest
-// column index; stop at the first |R_kk| < eps |R_11|.
+// Truncated CPQR of M_p (stored row-major) with column norms recomputed from
+// scratch at every step (fused into the reflector update, one thread per
+// column), pivot = largest norm, ties to the lowest column index; stops at the
+// first |R_kk| < eps |R_11|.
 __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
                                              const GatherSeg* __restrict__ gsegs, double eps) {
     extern __shared__ double sm[];
-    double* red = sm;                               // NWARP
-    double* redv = sm + NWARP;                      // NWARP
-    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);   // NWARP ints (NWARP/2 doubles)
-    double* z = sm + 3 * NWARP;                     // kmax
+    double* red = sm;                                            // NWARP
+    long long* redv = reinterpret_cast<long long*>(sm + NWARP);  // NWARP
+    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
+    double* G = sm + 3 * NWARP;                                  // NB * NB
+    double* vs = G + NB * NB;                                    // n_p
     const CPQRTask t = tasks[blockIdx.x];
     const int m = t.np, c = t.ncols;
-    double* M = t.M;
-    // gather
+    double* M = t.M;  // M(r, j) = M[r * c + j]
     for (int s = 0; s < t.nseg; s++) {
         const GatherSeg g = gsegs[t.seg_begin + s];
+        const int64_t tot = (int64_t)g.rows * g.cols;
         if (g.transpose) {
-            // M[r, col_off + cc] = src[cc + r * ld], r < cols (= n_p), cc < rows
-            const int64_t tot = (int64_t)g.rows * g.cols;
+            // M(r, col_off + cc) = src[cc + r * ld], r < n_p (= cols), cc < rows
             for (int64_t o = threadIdx.x; o < tot; o += NT) {
                 const int cc = (int)(o % g.rows), r = (int)(o / g.rows);
-                M[r + (int64_t)(g.col_off + cc) * m] = g.src[cc + (int64_t)r * g.ld];
+                M[(int64_t)r * c + g.col_off + cc] = g.src[cc + (int64_t)r * g.ld];
             }
         } else {
-            const int64_t tot = (int64_t)g.rows * g.cols;
             for (int64_t o = threadIdx.x; o < tot; o += NT) {
                 const int r = (int)(o % g.rows), cc = (int)(o / g.rows);
-                M[r + (int64_t)(g.col_off + cc) * m] = g.src[r + (int64_t)cc * g.ld];
+                M[(int64_t)r * c + g.col_off + cc] = g.src[r + (int64_t)cc * g.ld];
             }
         }
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j = w; j < c; j += NWARP) {
-        const double* cj = M + (int64_t)j * m;
+    for (int j = threadIdx.x; j < c; j += NT) {
         double s = 0.0;
-        for (int r = l; r < m; r += 32) s += cj[r] * cj[r];
-        s = warp_sum(s);
-        if (l == 0) t.norms[j] = s;
+        for (int r = 0; r < m; r++) {
+            const double x = M[(int64_t)r * c + j];
+            s += x * x;
+        }
+        t.norms[j] = s;
     }
     __syncthreads();
     const int tmax = m < c ? m : c;
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
             const double v = t.norms[j];
             if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
         }
+        if (bv < 0.0) bv = 0.0;
         double gv;
         int gi;
         block_argmax(bv, bi, redv, redi, gv, gi);
@@ -167,54 +170,50 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
         if (R11 == 0.0) break;
         if (pn < eps * R11) break;
         if (gi != k) {
-            double* a = M + (int64_t)k * m;
-            double* b = M + (int64_t)gi * m;
             for (int r = threadIdx.x; r < m; r += NT) {
-                const double x = a[r];
-                a[r] = b[r];
-                b[r] = x;
+                double* row = M + (int64_t)r * c;
+                const double x = row[k];
+                row[k] = row[gi];
+                row[gi] = x;
             }
             __syncthreads();
             if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
         }
         __syncthreads();
-        double* col = M + (int64_t)k * m;
-        const double tk = cta_house(col, k, m, red);
+        const double tk = cta_house(M + k, c, k, m, red);
         if (threadIdx.x == 0) t.tau[k] = tk;
-        // reflect the remaining columns and recompute their norms (rows k+1..)
-        for (int j = k + 1 + w; j < c; j += NWARP) {
-            double* cj = M + (int64_t)j * m;
-            if (tk != 0.0) {
-                const double ck = cj[k];
-                double d = 0.0;
-                for (int r = k + 1 + l; r < m; r += 32) d += col[r] * cj[r];
-                d = warp_sum(d) + ck;
-                const double f = tk * d;
-                if (l == 0) cj[k] = ck - f;
-                for (int r = k + 1 + l; r < m; r += 32) cj[r] -= f * col[r];
+        for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
+        __syncthreads();
+        for (int j = k + 1 + threadIdx.x; j < c; j += NT) {
+            double d = M[(int64_t)k * c + j];
+            for (int r = k + 1; r < m; r++) d += vs[r] * M[(int64_t)r * c + j];
+            const double f = tk * d;
+            M[(int64_t)k * c + j] -= f;
+            double nrm = 0.0;
+            for (int r = k + 1; r < m; r++) {
+                const double x = M[(int64_t)r * c + j] - f * vs[r];
+                M[(int64_t)r * c + j] = x;
+                nrm += x * x;
             }
-            double s = 0.0;
-            for (int r = k + 1 + l; r < m; r += 32) s += cj[r] * cj[r];
-            s = warp_sum(s);
-            if (l == 0) t.norms[j] = s;
+            t.norms[j] = nrm;
         }
         __syncthreads();
         rank = k + 1;
     }
-    // explicit reflectors V (n_p x rank), unit diagonal, zeros above
+    // explicit reflectors V (n_p x rank, column-major), unit diagonal, zeros above
     for (int64_t o = threadIdx.x; o < (int64_t)m * rank; o += NT) {
         const int r = (int)(o % m), i = (int)(o / m);
-        double v = r < i ? 0.0 : (r == i ? 1.0 : M[r + (int64_t)i * m]);
-        t.V[r + (int64_t)i * m] = v;
+        t.V[r + (int64_t)i * m] = r < i ? 0.0 : (r == i ? 1.0 : M[(int64_t)r * c + i]);
     }
     if (threadIdx.x == 0) *t.rank = rank;
     __syncthreads();
-    cta_form_t(t.V, m, m, rank, t.tau, t.T, t.kmax, z);
+    cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G);
 }
 
 // Coarse block [Q_i^T A Q_j](0:r_i, 0:r_j) into the merged block of the next
 // level; identity for diagonal blocks; plain copy when not sparsified.
 __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask* __restrict__ tasks) {
+    extern __shared__ double sm[];
     const SparsifyTask t = tasks[blockIdx.x];
     if (t.mode == 2) {
         const int64_t tot = (int64_t)t.mi * t.nj;
@@ -228,61 +227,20 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask* __restrict_
         for (int i = threadIdx.x; i < t.ri; i += NT) t.D[i + (int64_t)i * t.ldd] = 1.0;
         return;
     }
-    const int mi = t.mi, nj = t.nj, ri = t.ri, rj = t.rj;
-    double* B1 = t.scratch;                        // ri x nj
-    double* B2 = B1 + (int64_t)ri * nj;            // ri x nj
-    double* Z1 = B2 + (int64_t)ri * nj;            // ri x rj
-    double* Z2 = Z1 + (int64_t)ri * rj;            // ri x rj
-    // B1 = V_i^T A
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
-        const int p = (int)(o % ri), c = (int)(o / ri);
-        const double* vp = t.Vi + (int64_t)p * mi;
-        const double* ac = t.A + (int64_t)c * t.lda;
-        double s = 0.0;
-        for (int r = p; r < mi; r++) s += vp[r] * ac[r];
-        B1[o] = s;
+    const int mi = t.mi, nj = t.nj;
+    double* X = t.scratch;  // mi x nj, ld mi
+    for (int64_t o = threadIdx.x; o < (int64_t)mi * nj; o += NT) {
+        const int r = (int)(o % mi), c = (int)(o / mi);
+        X[o] = t.A[r + (int64_t)c * t.lda];
     }
     __syncthreads();
-    // B2 = T_i^T B1
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
-        const int p = (int)(o % ri), c = (int)(o / ri);
-        double s = 0.0;
-        for (int u = 0; u <= p; u++) s += t.Ti[u + (int64_t)p * t.ldti] * B1[u + (int64_t)c * ri];
-        B2[o] = s;
-    }
-    __syncthreads();
-    // X = (Q_i^T A)(0:ri, :) = A(0:ri, :) - V_i(0:ri, :) B2   -> B1
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * nj; o += NT) {
-        const int p = (int)(o % ri), c = (int)(o / ri);
-        double s = 0.0;
-        for (int q = 0; q <= p; q++) s += t.Vi[p + (int64_t)q * mi] * B2[q + (int64_t)c * ri];
-        B1[o] = t.A[p + (int64_t)c * t.lda] - s;
-    }
-    __syncthreads();
-    const double* X = B1;
-    // Z1 = X V_j (ri x rj)
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
-        const int p = (int)(o % ri), q = (int)(o / ri);
-        const double* vq = t.Vj + (int64_t)q * nj;
-        double s = 0.0;
-        for (int c = q; c < nj; c++) s += X[p + (int64_t)c * ri] * vq[c];
-        Z1[o] = s;
-    }
-    __syncthreads();
-    // Z2 = Z1 T_j
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
-        const int p = (int)(o % ri), q = (int)(o / ri);
-        double s = 0.0;
-        for (int u = 0; u <= q; u++) s += Z1[p + (int64_t)u * ri] * t.Tj[u + (int64_t)q * t.ldtj];
-        Z2[o] = s;
-    }
-    __syncthreads();
-    // D = (X Q_j)(:, 0:rj) = X(:, 0:rj) - Z2 V_j(0:rj, :)^T
-    for (int64_t o = threadIdx.x; o < (int64_t)ri * rj; o += NT) {
-        const int p = (int)(o % ri), q = (int)(o / ri);
-        double s = 0.0;
-        for (int u = 0; u <= q; u++) s += Z2[p + (int64_t)u * ri] * t.Vj[q + (int64_t)u * nj];
-        t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * ri] - s;
+    // X <- Q_i^T X
+    cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true, Mat{X, 1, mi, nullptr}, nj, QC, true, sm);
+    // X <- X Q_j, i.e. X^T <- Q_j^T X^T with X^T(r, c) = X[c + r * mi]
+    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat{X, mi, 1, nullptr}, mi, QC, true, sm);
+    for (int64_t o = threadIdx.x; o < (int64_t)t.ri * t.rj; o += NT) {
+        const int p = (int)(o % t.ri), q = (int)(o / t.ri);
+        t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * mi];
     }
 }
 
@@ -363,11 +321,6 @@ void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& 
 }
 
 const int kSmemMax = 200 * 1024;
-
-int chunk_width(int64_t n, int64_t budget_doubles) {
-    int64_t q = budget_doubles / (2 * std::max<int64_t>(n, 1));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(32, q));
-}
 
 bool g_attr_set = false;
 
@@ -508,6 +461,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         std::vector<ApplyFront> af;
         std::vector<Seg> asg;
         size_t smem_apply = 0;
+        // column chunk of a task: QAPPLY, halved while the staged work area of
+        // the tallest front would not fit
+        int qapply = QAPPLY;
+        {
+            int mm = 1;
+            for (size_t f = 0; f < sp.fronts.size(); f++) mm = std::max<int>(mm, (int)lay.H[sp.fronts[f]]);
+            while (qapply > 8 && ((mm + 1) / 2 + 1 + staged_smem_doubles(mm, qapply)) * 8 > kSmemMax) qapply /= 2;
+        }
         for (int j = 0; j < ncl; j++) {
             if (fronts_of[j].empty() || sz[j] == 0) continue;
             const int fb = (int)af.size();
@@ -535,7 +496,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 fl_ap += fa;
                 by_ap += 16.0 * A1.m * sz[j] + 8.0 * A1.m * A1.n;
             }
-            const int q = chunk_width(nmax, 6144);
+            const int q = qapply;
             for (int64_t c0 = 0; c0 < sz[j]; c0 += q) {
                 ApplyTask T1;
                 T1.B = arena + lay.poff[j] + c0 * lay.H[j];
@@ -546,27 +507,28 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 T1.m_max = mmax;
                 at.push_back(T1);
             }
-            smem_apply = std::max(smem_apply, (size_t)(2 * nmax * q) * 8 + (size_t)mmax * 4 + 16);
+            (void)nmax;
         }
-        // the apply kernel uses one W size for all tasks
-        int wd = 0;
+        // shared memory: row map + staged work area when it fits
+        int rmap_d = 0, staged = 0;
         {
-            size_t maxw = 0, maxm = 0;
-            for (const ApplyTask& T1 : at) {
-                int nmax = 1;
-                for (int f = 0; f < T1.nfr; f++) nmax = std::max(nmax, af[T1.fr_begin + f].n);
-                maxw = std::max(maxw, (size_t)(2 * nmax * T1.q));
-                maxm = std::max(maxm, (size_t)T1.m_max);
+            int maxm = 1;
+            for (const ApplyTask& T1 : at) maxm = std::max(maxm, T1.m_max);
+            rmap_d = (maxm + 1) / 2 + 1;
+            const int64_t need = rmap_d + staged_smem_doubles(maxm, qapply);
+            if (need * 8 <= kSmemMax) {
+                staged = 1;
+                smem_apply = (size_t)need * 8;
+            } else {
+                smem_apply = (size_t)(rmap_d + 2 * NB * qapply + NT) * 8;
             }
-            wd = (int)maxw;
-            smem_apply = maxw * 8 + maxm * 4 + 16;
         }
         if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
         tstart();
         if (!qr.empty()) {
             QRTask* d = C.upload(qr, false);
             if (C.rc) return C.rc;
-            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st, k_qr<<<(unsigned)qr.size(), NT, (size_t)(NWARP + tmax) * 8, st>>>(d));
+            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st, k_qr<<<(unsigned)qr.size(), NT, (size_t)qr_smem_doubles(QC) * 8, st>>>(d));
             C.launched();
         }
         if (!at.empty()) {
@@ -575,7 +537,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             Seg* d3 = C.upload(asg, false);
             if (C.rc) return C.rc;
             SPAQR_LAUNCH(KK_FRONT_APPLY, fl_ap, by_ap, st,
-                         k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, wd));
+                         k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, rmap_d, staged));
             C.launched();
         }
         tstop(0);
@@ -691,8 +653,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     t.Ti = uT[i];
                     t.Rj = blk(ej, j);
                     t.ldrj = lay.H[j];
-                    t.q = chunk_width(sz[i], 6144);
-                    smem_sc = std::max(smem_sc, (size_t)(2 * sz[i] * t.q) * 8);
+                    t.q = QC;
+                    smem_sc = (size_t)(2 * NB * QC + NT) * 8;
                     sc.push_back(t);
                     const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
                     flops += fs;
@@ -704,7 +666,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (!sq.empty()) {
                 QRTask* d = C.upload(sq, false);
                 if (C.rc) return C.rc;
-                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st, k_qr<<<(unsigned)sq.size(), NT, (size_t)(NWARP + tm) * 8, st>>>(d));
+                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st, k_qr<<<(unsigned)sq.size(), NT, (size_t)qr_smem_doubles(QC) * 8, st>>>(d));
                 C.launched();
             }
             if (!sc.empty()) {
@@ -754,7 +716,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             C.cuda(cudaMemsetAsync(Rk, 0, sizeof(int) * ncl, st));
             int64_t mo = 0, no = 0, vo = 0, to = 0, ro = 0;
             double by_cp = 16.0 * mtot;
-            int kmx = 1;
+            int kmx = 1, npmax = 1;
             std::vector<int64_t> rdg_off(ncl, 0);
             for (int p : rest) {
                 if (sz[p] == 0) continue;
@@ -793,6 +755,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 to += (int64_t)kmax[p] * kmax[p] + kmax[p];
                 ro += kmax[p] + 1;
                 kmx = std::max(kmx, kmax[p]);
+                npmax = std::max(npmax, (int)sz[p]);
                 cp_of[p] = (int)cp.size();
                 cp.push_back(t);
             }
@@ -801,7 +764,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 GatherSeg* d2 = C.upload(gs, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
-                             k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(4 * NWARP + kmx) * 8, st>>>(d1, d2, opt->eps));
+                             k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(3 * NWARP + NB * NB + npmax) * 8, st>>>(d1, d2, opt->eps));
                 C.launched();
             }
             // ranks back to the host (the only device->host sync of a level)
@@ -883,8 +846,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         t.rj = (int)newsz[j];
                         t.ldtj = kmax[j];
                         t.scratch = (double*)(intptr_t)scr;  // offset, fixed below
-                        scr += 2 * (int64_t)t.ri * t.nj + 2 * (int64_t)t.ri * t.rj;
-                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.ri * t.nj * t.rj;
+                        scr += (int64_t)t.mi * t.nj;
+                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.rj * t.nj * t.mi;
                         flops += fp;
                         fl_sp += fp;
                     }
@@ -899,7 +862,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     if (t.mode == 0) t.scratch = sbuf + (int64_t)(intptr_t)t.scratch;
                 SparsifyTask* d = C.upload(sk, false);
                 if (C.rc) return C.rc;
-                SPAQR_LAUNCH(KK_SPARSIFY, fl_sp, by_sp, st, k_sparsify<<<(unsigned)sk.size(), NT, 0, st>>>(d));
+                SPAQR_LAUNCH(KK_SPARSIFY, fl_sp, by_sp, st,
+                             k_sparsify<<<(unsigned)sk.size(), NT, (size_t)(2 * NB * QC + NT) * 8, st>>>(d));
                 C.launched();
             }
             tstop(3);

@@ -49,11 +49,22 @@ __global__ void k_perm_out(int64_t n, int nrhs, const int64_t* __restrict__ perm
     for (int c = 0; c < nrhs; c++) X[g + c * ldx] = s * Y[i + c * ldy];
 }
 
+// The right-hand sides of a launch are split into blockIdx.y chunks of qs
+// columns, so that levels with few fronts still occupy many SMs.
+__device__ __forceinline__ bool rhs_chunk(int nrhs, int qs, int& c0, int& qn) {
+    c0 = blockIdx.y * qs;
+    qn = nrhs - c0 < qs ? nrhs - c0 : qs;
+    return qn > 0;
+}
+
 __global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
-                                                   double* Y, int64_t ldy, int nrhs, int q, int wdoubles) {
+                                                   double* Y, int64_t ldy, int nrhs, int qs, int rmap_doubles,
+                                                   int staged) {
     extern __shared__ double sm[];
-    double* W = sm;
-    int* rmap = reinterpret_cast<int*>(sm + wdoubles);
+    int* rmap = reinterpret_cast<int*>(sm);
+    double* W = sm + rmap_doubles;
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveFront F = fr[blockIdx.x];
     int pos = 0;
     for (int s = 0; s < F.nseg; s++) {
@@ -62,72 +73,78 @@ __global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront* __restrict_
         pos += g.len;
     }
     __syncthreads();
-    for (int c0 = 0; c0 < nrhs; c0 += q) {
-        RowMapped B{Y + (int64_t)c0 * ldy, ldy, rmap};
-        cta_apply_wy(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, min(q, nrhs - c0), true, W);
-    }
+    const Mat B{Y + (int64_t)c0 * ldy, 1, ldy, rmap};
+    if (staged) cta_apply_q_staged(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, qn, true, W);
+    else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, qn, true, W);
 }
 
 __global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy, double* Yn,
-                                                int64_t ldyn, int nrhs, int q) {
+                                                int64_t ldyn, int nrhs, int qs, int staged) {
     extern __shared__ double sm[];
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveSS S = ss[blockIdx.x];
-    double* y = Y + S.off;
-    for (int c0 = 0; c0 < nrhs; c0 += q) {
-        const int qq = min(q, nrhs - c0);
-        RowMapped B{y + (int64_t)c0 * ldy, ldy, nullptr};
-        if (S.UV) cta_apply_wy(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qq, true, sm);
-        if (S.QV && S.r > 0) cta_apply_wy(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qq, true, sm);
+    double* y = Y + S.off + (int64_t)c0 * ldy;
+    const Mat B{y, 1, ldy, nullptr};
+    if (S.UV) {
+        if (staged) cta_apply_q_staged(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
+        else cta_apply_q(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
     }
-    for (int64_t o = threadIdx.x; o < (int64_t)S.r * nrhs; o += NT) {
+    if (S.QV && S.r > 0) {
+        if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, true, sm);
+        else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, true, sm);
+    }
+    for (int64_t o = threadIdx.x; o < (int64_t)S.r * qn; o += NT) {
         const int r = (int)(o % S.r), c = (int)(o / S.r);
-        Yn[S.noff + r + c * ldyn] = y[r + c * ldy];
+        Yn[S.noff + r + (c0 + c) * ldyn] = y[r + c * ldy];
     }
 }
 
 __global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy,
-                                                const double* Yn, int64_t ldyn, int nrhs, int q, int* singular) {
+                                                const double* Yn, int64_t ldyn, int nrhs, int qs, int staged,
+                                                int* singular) {
     extern __shared__ double sm[];
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveSS S = ss[blockIdx.x];
-    double* y = Y + S.off;
-    for (int64_t o = threadIdx.x; o < (int64_t)S.r * nrhs; o += NT) {
+    double* y = Y + S.off + (int64_t)c0 * ldy;
+    for (int64_t o = threadIdx.x; o < (int64_t)S.r * qn; o += NT) {
         const int r = (int)(o % S.r), c = (int)(o / S.r);
-        y[r + c * ldy] = Yn[S.noff + r + c * ldyn];
+        y[r + c * ldy] = Yn[S.noff + r + (c0 + c) * ldyn];
     }
     __syncthreads();
-    for (int c0 = 0; c0 < nrhs; c0 += q) {
-        const int qq = min(q, nrhs - c0);
-        RowMapped B{y + (int64_t)c0 * ldy, ldy, nullptr};
-        if (S.QV && S.r > 0) cta_apply_wy(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qq, false, sm);
+    const Mat B{y, 1, ldy, nullptr};
+    if (S.QV && S.r > 0) {
+        if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
+        else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
     }
-    if (S.UV) {
-        RowMapped B{y, ldy, nullptr};
-        cta_trsv_upper(S.UV, S.lduv, S.np, B, nrhs, singular);
-    }
+    if (S.UV) cta_trsv_upper(S.UV, S.lduv, S.np, B, qn, singular);
 }
 
 __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
                                                    const SolveRsj* __restrict__ rsj, double* Y, int64_t ldy,
-                                                   int nrhs, int* singular) {
+                                                   int nrhs, int qs, int* singular) {
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveFront F = fr[blockIdx.x];
     const Seg s0 = segs[F.seg_begin];  // the front's own rows
-    double* xs = Y + s0.off;
+    double* Yc = Y + (int64_t)c0 * ldy;
+    double* xs = Yc + s0.off;
     const int n = F.n;
     // rhs = z_s - sum_j R_sj x_j
-    for (int64_t o = threadIdx.x; o < (int64_t)n * nrhs; o += NT) {
+    for (int64_t o = threadIdx.x; o < (int64_t)n * qn; o += NT) {
         const int r = (int)(o % n), c = (int)(o / n);
         double acc = 0.0;
         for (int b = 0; b < F.nrsj; b++) {
             const SolveRsj R = rsj[F.rsj_begin + b];
-            const double* xj = Y + R.xoff + (int64_t)c * ldy;
+            const double* xj = Yc + R.xoff + (int64_t)c * ldy;
             const double* row = R.R + r;
             for (int u = 0; u < R.nj; u++) acc += row[(int64_t)u * R.ldr] * xj[u];
         }
         xs[r + (int64_t)c * ldy] -= acc;
     }
     __syncthreads();
-    RowMapped X{xs, ldy, nullptr};
-    cta_trsv_upper(F.V, F.ldv, n, X, nrhs, singular);
+    cta_trsv_upper(F.V, F.ldv, n, Mat{xs, 1, ldy, nullptr}, qn, singular);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,11 +361,6 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int qwidth(int n, int nrhs) {
-    int q = (int)std::max<int64_t>(1, std::min<int64_t>(32, 6144 / (2 * (int64_t)std::max(n, 1))));
-    return std::min(q, std::max(nrhs, 1));
-}
-
 void set_solve_attrs() {
     if (g_solve_attr) return;
     cudaFuncSetAttribute(k_sfront_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
@@ -361,6 +373,16 @@ void set_solve_attrs() {
 
 // X = M^{-1} B with B, X device pointers (n x nrhs, leading dims).  `singular`
 // is a device int (may be null).  Stream-ordered, no synchronisation.
+// RHS split of a launch with `blocks` CTAs: enough chunks to give every SM
+// about two CTAs, at most one column per chunk.
+static int rhs_split(int blocks, int nrhs) {
+    int split = (2 * 152 + blocks - 1) / std::max(blocks, 1);
+    split = std::max(1, std::min(split, nrhs));
+    return split;
+}
+
+static int64_t smem_limit_doubles() { return kSmemMax / 8; }
+
 int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
                  cudaStream_t st, double* ws, int* singular) {
     set_solve_attrs();
@@ -375,24 +397,32 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
         double* Y = ws + LV.ws_off * nrhs;
         const int64_t ldy = LV.rows;
         if (LV.nfront > 0) {
-            const int q = qwidth(LV.max_front_n, nrhs);
-            const int wd = 2 * LV.max_front_n * q;
-            const size_t smem = (size_t)wd * 8 + (size_t)LV.max_front_m * 4 + 16;
+            const int rmap_d = (LV.max_front_m + 1) / 2 + 1;
             for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
                 const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
-                if (b > a)
-                    SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] + LV.ff_vec[c] * nrhs, st,
-                                 k_sfront_fwd<<<b - a, NT, smem, st>>>(F->d_fronts + LV.front_begin + a, F->d_segs, Y,
-                                                                       ldy, nrhs, q, wd));
+                if (b <= a) continue;
+                const int split = rhs_split(b - a, nrhs);
+                const int qs = (nrhs + split - 1) / split;
+                const int staged = rmap_d + staged_smem_doubles(LV.max_front_m, qs) <= smem_limit_doubles();
+                const size_t smem = (size_t)(rmap_d + (staged ? staged_smem_doubles(LV.max_front_m, qs)
+                                                               : 2 * NB * qs + NT)) * 8;
+                SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs,
+                             st,
+                             k_sfront_fwd<<<dim3(b - a, split), NT, smem, st>>>(F->d_fronts + LV.front_begin + a,
+                                                                                F->d_segs, Y, ldy, nrhs, qs, rmap_d,
+                                                                                staged));
             }
         }
         if (LV.nss > 0) {
             const SolveLevelHost& LN = F->lv[k + 1];
-            const int q = qwidth(LV.max_ss_n, nrhs);
-            const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
-            SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed + LV.ssf_vec * nrhs, st,
-                         k_sss_fwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs,
-                                                             LN.rows, nrhs, q));
+            const int split = rhs_split(LV.nss, nrhs);
+            const int qs = (nrhs + split - 1) / split;
+            const int staged = staged_smem_doubles(LV.max_ss_n, qs) <= smem_limit_doubles();
+            const size_t smem = (size_t)(staged ? staged_smem_doubles(LV.max_ss_n, qs) : 2 * NB * qs + NT) * 8;
+            SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed * split + LV.ssf_vec * nrhs, st,
+                         k_sss_fwd<<<dim3(LV.nss, split), NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy,
+                                                                          ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
+                                                                          staged));
         }
     }
     for (int k = L - 1; k >= 0; k--) {
@@ -401,16 +431,22 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
         const int64_t ldy = LV.rows;
         if (LV.nss > 0) {
             const SolveLevelHost& LN = F->lv[k + 1];
-            const int q = qwidth(LV.max_ss_n, nrhs);
-            const size_t smem = (size_t)(2 * LV.max_ss_n * q) * 8 + 16;
-            SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed + LV.ssb_vec * nrhs, st,
-                         k_sss_bwd<<<LV.nss, NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs,
-                                                             LN.rows, nrhs, q, singular));
+            const int split = rhs_split(LV.nss, nrhs);
+            const int qs = (nrhs + split - 1) / split;
+            const int staged = staged_smem_doubles(LV.max_ss_n, qs) <= smem_limit_doubles();
+            const size_t smem = (size_t)(staged ? staged_smem_doubles(LV.max_ss_n, qs) : 2 * NB * qs + NT) * 8;
+            SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed * split + LV.ssb_vec * nrhs, st,
+                         k_sss_bwd<<<dim3(LV.nss, split), NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy,
+                                                                          ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
+                                                                          staged, singular));
         }
-        if (LV.nfront > 0)
-            SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed + LV.fb_vec * nrhs, st,
-                         k_sfront_bwd<<<LV.nfront, NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs, F->d_rsj, Y,
-                                                                ldy, nrhs, singular));
+        if (LV.nfront > 0) {
+            const int split = rhs_split(LV.nfront, nrhs);
+            const int qs = (nrhs + split - 1) / split;
+            SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed * split + LV.fb_vec * nrhs, st,
+                         k_sfront_bwd<<<dim3(LV.nfront, split), NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs,
+                                                                             F->d_rsj, Y, ldy, nrhs, qs, singular));
+        }
     }
     SPAQR_LAUNCH(KK_SOLVE_PERM, 1.0 * n * nrhs, 16.0 * n + 16.0 * n * nrhs, st,
                  k_perm_out<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
@@ -548,7 +584,10 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dX, lx, X0, n));
     SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb));
     SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n));
-    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1));  // ||b||^2 (nvec = 1, U = W) k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1);  // ||r0||^2 C.launched();
+    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1));  // ||b||^2
+    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
+                 k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1));  // ||r0||^2
+    C.launched();
     std::vector<double> hb(nrhs), hr(nrhs), hest(nrhs), hres(nrhs, 1.0);
     std::vector<int> hact(nrhs, 1), hit(nrhs, 0), hwant(nrhs, 0);
     C.cuda(cudaMemcpyAsync(hb.data(), bn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
@@ -574,7 +613,8 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     C.cuda(cudaMemcpyAsync(g, hg.data(), 8 * ldh * nrhs, cudaMemcpyHostToDevice, st));
     C.cuda(cudaMemcpyAsync(hn, hr.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
     C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
-    SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn));  // V_0 = r0 / beta C.launched();
+    SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn));  // V_0 = r0 / beta
+    C.launched();
     int nact = 0;
     for (int c = 0; c < nrhs; c++) nact += hact[c];
     int j = 0;
