@@ -39,6 +39,10 @@ WORKLOAD = "convdiff2d_256x256_lognormal_a_pe50_randangle_fp64_eps1e-2_16rhs"
 # FP64 peak on GB300: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2070 MHz (nominal
 # 1.25 TFLOP/s); a DFMA microbenchmark measured 1.19 TFLOP/s at ~1990 MHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernels on this workload (profiles/); None when
+# the kernel changed since the capture.
+TRAFFIC = {}
 
 
 def _args():
@@ -310,24 +314,19 @@ def ours(a):
         return 0
 
     # ---- roofline of the dominant kernel ----
+    # Every kernel of the path is bound by the FP64 pipe on GB300 (about 2 DFMA
+    # per clock per SM); even the 16-RHS solve kernels do ~4 flop per byte of
+    # factor data read, far above HBM's balance point.
     dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
     dname, d = dom
     per_launch_ms = d["total_ms"] / max(d["launches"], 1)
-    peaks = _peaks()
-    solve_kinds = {"solve_perm", "solve_front_fwd", "solve_ss_fwd", "solve_ss_bwd", "solve_front_bwd", "spmv",
-                   "gmres_orth", "gmres_small"}
-    if dname in solve_kinds:
-        ach = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": dname}
-    else:
-        ach = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dname,
-                "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz (derived)"}
-    roof["launches"] = d["launches"]
-    roof["avg_launch_ms"] = per_launch_ms
+    ach = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(dname), "kernel": dname,
+            "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz (derived; DFMA microbenchmark 1.19-1.20)",
+            "launches": d["launches"], "avg_launch_ms": per_launch_ms,
+            "algorithmic_gflop_per_launch": d["flops"] / d["launches"] / 1e9,
+            "algorithmic_mb_per_launch": d["bytes"] / d["launches"] / 2 ** 20}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,

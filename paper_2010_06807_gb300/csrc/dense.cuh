@@ -363,52 +363,95 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
     }
 }
 
-// B <- B R^{-1}: B is mi x nj (ldb), R upper triangular nj x nj (ldr).
-// Thread-per-row forward substitution; sets *singular on a zero diagonal.
-static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int nj, const double* R, int64_t ldr,
-                                            int* singular) {
-    for (int r = threadIdx.x; r < mi; r += NT) {
-        for (int c = 0; c < nj; c++) {
-            double s = B[r + (int64_t)c * ldb];
-            for (int p = 0; p < c; p++) s -= B[r + (int64_t)p * ldb] * R[p + (int64_t)c * ldr];
-            const double d = R[c + (int64_t)c * ldr];
+// Inverses of the diagonal NB x NB blocks of the upper triangular R (n x n,
+// ldr): block b (rows/columns [b NB, b NB + bs)) goes to Dinv rows
+// [b NB, b NB + bs), columns [0, bs) (ld n), upper triangular, zeros below.
+// One thread per column of a block (back substitution).  Sets *singular on a
+// zero diagonal entry (and writes zeros for it).
+static __device__ void cta_tri_inv_blocks(const double* R, int64_t ldr, int n, double* Dinv, int* singular) {
+    const int nbk = (n + NB - 1) / NB;
+    for (int o = threadIdx.x; o < nbk * NB; o += NT) {
+        const int b = o / NB, j = o % NB, b0 = b * NB;
+        const int bs = n - b0 < NB ? n - b0 : NB;
+        if (j >= bs) continue;
+        double* dj = Dinv + b0 + (int64_t)j * n;
+        for (int i = bs - 1; i > j; i--) dj[i] = 0.0;
+        for (int i = j; i >= 0; i--) {
+            double s = i == j ? 1.0 : 0.0;
+            for (int u = i + 1; u <= j; u++) s -= R[(b0 + i) + (int64_t)(b0 + u) * ldr] * dj[u];
+            const double d = R[(b0 + i) + (int64_t)(b0 + i) * ldr];
             if (d == 0.0) {
-                *singular = 1;
-                s = 0.0;
+                if (singular) *singular = 1;
+                dj[i] = 0.0;
             } else {
-                s = s / d;
+                dj[i] = s / d;
             }
-            B[r + (int64_t)c * ldb] = s;
         }
     }
     __syncthreads();
 }
 
-// X <- R^{-1} X for X n x q, R upper n x n (ldr).  Back substitution by
-// diagonal blocks of NB rows: each block is solved by one thread per column,
-// then the rows above it are updated by all threads.
-static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, Mat X, int q, int* singular) {
-    for (int i1 = n; i1 > 0; i1 -= NB) {
-        const int i0 = i1 - NB > 0 ? i1 - NB : 0;
-        for (int c = threadIdx.x; c < q; c += NT) {
-            for (int i = i1 - 1; i >= i0; i--) {
-                double s = X.at(i, c);
-                for (int u = i + 1; u < i1; u++) s -= R[i + (int64_t)u * ldr] * X.at(u, c);
-                const double d = R[i + (int64_t)i * ldr];
-                if (d == 0.0) {
-                    *singular = 1;
-                    s = 0.0;
-                } else {
-                    s = s / d;
+// B <- B R^{-1}: B is mi x nj (ldb), R upper triangular nj x nj (ldr) with
+// inverted diagonal blocks Dinv (ld nj).  Per block of NB columns (left to
+// right): the update by the solved columns runs one thread per entry, then
+// the block is multiplied by Dinv_b one thread per row.
+static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int nj, const double* R, int64_t ldr,
+                                            const double* Dinv) {
+    for (int b0 = 0; b0 < nj; b0 += NB) {
+        const int bs = nj - b0 < NB ? nj - b0 : NB;
+        if (b0 > 0) {
+            for (int o = threadIdx.x; o < mi * bs; o += NT) {
+                const int r = o % mi, j = o / mi;
+                const double* rc = R + (int64_t)(b0 + j) * ldr;
+                double s = B[r + (int64_t)(b0 + j) * ldb];
+                for (int u = 0; u < b0; u++) s -= B[r + (int64_t)u * ldb] * rc[u];
+                B[r + (int64_t)(b0 + j) * ldb] = s;
+            }
+            __syncthreads();
+        }
+        const double* D = Dinv + b0;
+        for (int r = threadIdx.x; r < mi; r += NT) {
+            double* br = B + r + (int64_t)b0 * ldb;
+            double t[NB];
+#pragma unroll
+            for (int j = 0; j < NB; j++) t[j] = j < bs ? br[(int64_t)j * ldb] : 0.0;
+#pragma unroll
+            for (int j = NB - 1; j >= 0; j--) {
+                if (j < bs) {
+                    double x = 0.0;
+#pragma unroll
+                    for (int l = 0; l <= j; l++) x += t[l] * D[l + (int64_t)j * nj];
+                    br[(int64_t)j * ldb] = x;
                 }
-                X.at(i, c) = s;
             }
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < i0 * q; o += NT) {
-            const int r = o % i0, c = o / i0;
+    }
+}
+
+// X <- R^{-1} X for X n x q, R upper n x n (ldr) with inverted diagonal
+// blocks Dinv (ld n).  Block back substitution: per block (bottom up)
+// x_b = Dinv_b y_b, then the rows above are updated.  tmp: NB * q doubles of
+// shared memory.
+static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, const double* Dinv, Mat X, int q,
+                                      double* tmp) {
+    const int nbk = (n + NB - 1) / NB;
+    for (int b = nbk - 1; b >= 0; b--) {
+        const int b0 = b * NB;
+        const int bs = n - b0 < NB ? n - b0 : NB;
+        for (int o = threadIdx.x; o < bs * q; o += NT) {
+            const int i = o % bs, c = o / bs;
             double s = 0.0;
-            for (int u = i0; u < i1; u++) s += R[r + (int64_t)u * ldr] * X.at(u, c);
+            for (int u = i; u < bs; u++) s += Dinv[(b0 + i) + (int64_t)u * n] * X.at(b0 + u, c);
+            tmp[o] = s;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < bs * q; o += NT) X.at(b0 + o % bs, o / bs) = tmp[o];
+        __syncthreads();
+        for (int o = threadIdx.x; o < b0 * q; o += NT) {
+            const int r = o % b0, c = o / b0;
+            double s = 0.0;
+            for (int u = 0; u < bs; u++) s += R[r + (int64_t)(b0 + u) * ldr] * X.at(b0 + u, c);
             X.at(r, c) -= s;
         }
         __syncthreads();

@@ -69,13 +69,14 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
 }
 
 constexpr int QC = 32;       // column chunk of the blocked updates
-constexpr int QAPPLY = 64;   // column chunk of one front-apply task
+constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 
 __global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     const QRTask t = tasks[blockIdx.x];
     const int tt = t.m < t.n ? t.m : t.n;
     cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, sm);
+    if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
 // smem layout: rmap (rmap_doubles doubles) then the work area of the apply
@@ -106,7 +107,8 @@ __global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask* __restrict_
     extern __shared__ double sm[];
     const ScaleTask t = tasks[blockIdx.x];
     cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, Mat{t.A, 1, t.lda, nullptr}, t.nj, QC, true, sm);
-    cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, singular);
+    cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, t.Dj);
+    (void)singular;
 }
 
 // Truncated CPQR of M_p (stored row-major) with column norms recomputed from
@@ -424,11 +426,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         // ---------------- (i) factor the fronts ----------------
         double fl_qr = 0, by_qr = 0, fl_ap = 0, by_ap = 0;
         std::vector<QRTask> qr;
-        std::vector<double*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr);
+        std::vector<double*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr),
+            fD(sp.fronts.size(), nullptr);
         int64_t aux = 0;
         for (size_t f = 0; f < sp.fronts.size(); f++) {
             const int s = sp.fronts[f];
-            aux += sz[s] + sz[s] * sz[s];
+            aux += sz[s] + sz[s] * sz[s] + sz[s] * NB;
         }
         double* faux = C.alloc<double>(aux, true);
         if (C.rc) return C.rc;
@@ -441,8 +444,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 a += sz[s];
                 fT[f] = faux + a;
                 a += sz[s] * sz[s];
+                fD[f] = faux + a;
+                a += sz[s] * NB;
                 if (sz[s] == 0) continue;
-                qr.push_back(QRTask{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f]});
+                qr.push_back(QRTask{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f], fD[f],
+                                    d_flags + 2});
                 tmax = std::max<int>(tmax, (int)sz[s]);
                 const double fq = 2.0 * lay.H[s] * sz[s] * sz[s] - 2.0 / 3.0 * sz[s] * sz[s] * sz[s];
                 flops += fq;
@@ -563,6 +569,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 SolveFront sf;
                 sf.V = arena + lay.poff[s];
                 sf.T = fT[f];
+                sf.Dinv = fD[f];
                 sf.ldv = lay.H[s];
                 sf.m = (int)lay.H[s];
                 sf.n = (int)sz[s];
@@ -607,12 +614,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (!sp.is_front[i]) rest.push_back(i);
         const bool sparsify = (k + 1 > opt->skip) && !rest.empty();
         std::vector<int64_t> newsz(ncl, 0);
-        std::vector<double*> uT(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
+        std::vector<double*> uT(ncl, nullptr), uD(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
         std::vector<int> kmax(ncl, 0);
         if (sparsify) {
             // scaling QR of every diagonal block
             int64_t ua = 0;
-            for (int p : rest) ua += sz[p] + sz[p] * sz[p];
+            for (int p : rest) ua += sz[p] + sz[p] * sz[p] + sz[p] * NB;
             double* uaux = C.alloc<double>(ua, true);
             if (C.rc) return C.rc;
             std::vector<QRTask> sq;
@@ -624,10 +631,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 a += sz[p];
                 uT[p] = uaux + a;
                 a += sz[p] * sz[p];
+                uD[p] = uaux + a;
+                a += sz[p] * NB;
                 if (sz[p] == 0) continue;
                 const int e = sp.find(p, p);
                 if (e < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
-                sq.push_back(QRTask{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p]});
+                sq.push_back(QRTask{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p], uD[p], d_flags + 1});
                 tm = std::max<int>(tm, (int)sz[p]);
                 flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
                 fl_sq += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
@@ -653,6 +662,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     t.Ti = uT[i];
                     t.Rj = blk(ej, j);
                     t.ldrj = lay.H[j];
+                    t.Dj = uD[j];
                     t.q = QC;
                     smem_sc = (size_t)(2 * NB * QC + NT) * 8;
                     sc.push_back(t);
@@ -881,6 +891,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     s.UV = blk(e, p);
                     s.lduv = lay.H[p];
                     s.UT = uT[p];
+                    s.UD = uD[p];
                     s.QV = qV[p];
                     s.QT = qT[p];
                     s.ldqt = std::max(kmax[p], 1);
@@ -932,6 +943,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     }
     if (flags[0]) { set_error("matrix has a zero column"); return SPAQR_ERR_SINGULAR; }
     if (flags[1]) { set_error("zero diagonal in a scaling factor R_pp"); return SPAQR_ERR_SINGULAR; }
+    if (flags[2]) { set_error("zero diagonal in a separator factor R_ss"); return SPAQR_ERR_SINGULAR; }
     return SPAQR_OK;
 }
 

@@ -118,12 +118,14 @@ __global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, 
         if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
         else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
     }
-    if (S.UV) cta_trsv_upper(S.UV, S.lduv, S.np, B, qn, singular);
+    if (S.UV) cta_trsv_upper(S.UV, S.lduv, S.np, S.UD, B, qn, sm);
+    (void)singular;
 }
 
 __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
                                                    const SolveRsj* __restrict__ rsj, double* Y, int64_t ldy,
                                                    int nrhs, int qs, int* singular) {
+    __shared__ double tmp[NB * 16];
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveFront F = fr[blockIdx.x];
@@ -144,7 +146,8 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict_
         xs[r + (int64_t)c * ldy] -= acc;
     }
     __syncthreads();
-    cta_trsv_upper(F.V, F.ldv, n, Mat{xs, 1, ldy, nullptr}, qn, singular);
+    cta_trsv_upper(F.V, F.ldv, n, F.Dinv, Mat{xs, 1, ldy, nullptr}, qn, tmp);
+    (void)singular;
 }
 
 // ---------------------------------------------------------------------------
@@ -374,10 +377,11 @@ void set_solve_attrs() {
 // X = M^{-1} B with B, X device pointers (n x nrhs, leading dims).  `singular`
 // is a device int (may be null).  Stream-ordered, no synchronisation.
 // RHS split of a launch with `blocks` CTAs: enough chunks to give every SM
-// about two CTAs, at most one column per chunk.
+// about two CTAs, between 1 and 16 columns per chunk.
 static int rhs_split(int blocks, int nrhs) {
     int split = (2 * 152 + blocks - 1) / std::max(blocks, 1);
     split = std::max(1, std::min(split, nrhs));
+    split = std::max(split, (nrhs + 15) / 16);   // at most 16 columns per CTA
     return split;
 }
 

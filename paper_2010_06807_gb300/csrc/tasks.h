@@ -18,7 +18,9 @@ struct QRTask {
     int64_t lda;
     int m, n;
     double* tau;   // min(m, n)
-    double* T;     // t x t compact-WY factor, ld = t
+    double* T;     // t x t block-diagonal T, ld = t
+    double* Dinv;  // inverted diagonal blocks of R (t x NB, ld t), or null
+    int* singular; // set on a zero diagonal of R
 };
 
 // Rows of a front inside another column panel (or inside a solve vector).
@@ -57,6 +59,7 @@ struct ScaleTask {
     const double* Ti;   // n_i x n_i, ld n_i
     const double* Rj;   // diagonal block j (R on and above the diagonal)
     int64_t ldrj;
+    const double* Dj;   // inverted diagonal NB blocks of R_j (n_j x NB, ld n_j)
     int q;              // column chunk for the U^T product
 };
 
@@ -109,6 +112,7 @@ struct SparsifyTask {
 struct SolveFront {
     const double* V;   // front panel: reflectors below the diagonal, R_ss on top
     const double* T;
+    const double* Dinv;  // inverted diagonal blocks of R_ss (n x NB, ld n)
     int64_t ldv;
     int m, n;
     int seg_begin, nseg;   // rows R(s) in the level vector (first segment = s)
@@ -132,6 +136,7 @@ struct SolveSS {
     const double* UV;  // diagonal block after the scaling QR (null: not scaled)
     int64_t lduv;
     const double* UT;  // n_p x n_p
+    const double* UD;  // inverted diagonal blocks of R_pp (n_p x NB, ld n_p)
     const double* QV;  // n_p x r explicit
     const double* QT;  // ld kmax
     int ldqt;
