@@ -306,23 +306,46 @@ static __device__ void cta_apply_q_chunked(const double* V, int64_t ldv, int m, 
     }
 }
 
-// Shared memory (doubles) needed by cta_qr with column chunk qc.
-__host__ __device__ constexpr int qr_smem_doubles(int qc) { return NWARP + NT + NB + NB * NB + 2 * NB * qc + NT; }
+// Shared memory (doubles) needed by cta_qr with column chunk qc and a staged
+// panel of up to prow rows (prow = 0: panels stay in global memory).
+__host__ __device__ constexpr int64_t qr_smem_doubles(int qc, int prow = 0) {
+    return NWARP + NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB;
+}
 
 // In-place blocked Householder QR of A (m x n, lda).  tau gets min(m, n)
-// entries and T the diagonal NB blocks (ldt).  smem: qr_smem_doubles(qc).
+// entries and T the diagonal NB blocks (ldt).  A panel of NB columns is
+// factored column by column (in shared memory when m <= prow), then applied
+// to the columns right of it as a block reflector.
+// smem: qr_smem_doubles(qc, prow).
 static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau, double* T, int ldt, int qc,
-                              double* smem) {
+                              int prow, double* smem) {
     double* red = smem;
     double* P = red + NWARP;     // NT partial dots
     double* Wk = P + NT;         // NB
     double* G = Wk + NB;         // NB * NB
     double* W = G + NB * NB;     // 2 * NB * qc + NT
+    double* Ps = W + 2 * NB * qc + NT;   // prow * NB
     const int t = m < n ? m : n;
+    const bool staged = m <= prow;
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pe = (t - p0 < NB ? t : p0 + NB);   // panel columns [p0, pe)
+        // panel view: column k, row r -> Pb[r + (k - p0) * ldp]
+        double* Pb;
+        int64_t ldp;
+        if (staged) {
+            ldp = m - p0;
+            Pb = Ps - p0;
+            for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
+                const int rr = o % (m - p0), j = o / (m - p0);
+                Ps[rr + (int64_t)j * ldp] = A[(p0 + rr) + (int64_t)(p0 + j) * lda];
+            }
+            __syncthreads();
+        } else {
+            ldp = lda;
+            Pb = A + (int64_t)p0 * lda;
+        }
         for (int k = p0; k < pe; k++) {
-            double* col = A + (int64_t)k * lda;
+            double* col = Pb + (int64_t)(k - p0) * ldp;
             const double tk = cta_house(col, 1, k, m, red);
             if (threadIdx.x == 0) tau[k] = tk;
             const int ncol = pe - k - 1;
@@ -331,13 +354,13 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
                 const int js = threadIdx.x % NB, g = threadIdx.x / NB;
                 double part = 0.0;
                 if (js < ncol) {
-                    const double* cj = A + (int64_t)(k + 1 + js) * lda;
+                    const double* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
                     for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
                 }
                 P[threadIdx.x] = part;
                 __syncthreads();
                 if (threadIdx.x < ncol) {
-                    double s = A[k + (int64_t)(k + 1 + threadIdx.x) * lda];
+                    double s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
                     for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
                     Wk[threadIdx.x] = tk * s;
                 }
@@ -346,20 +369,27 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
                 for (int o = threadIdx.x; o < rows * ncol; o += NT) {
                     const int rr = o % rows, jj = o / rows, r = k + rr;
                     const double v = rr == 0 ? 1.0 : col[r];
-                    A[r + (int64_t)(k + 1 + jj) * lda] -= Wk[jj] * v;
+                    Pb[r + (int64_t)(k + 1 + jj - p0) * ldp] -= Wk[jj] * v;
                 }
             }
             __syncthreads();
         }
-        // T block of the panel
-        cta_form_tblocks(A + p0 + (int64_t)p0 * lda, lda, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt,
-                         ldt, G);
+        if (staged) {
+            for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
+                const int rr = o % (m - p0), j = o / (m - p0);
+                A[(p0 + rr) + (int64_t)(p0 + j) * lda] = Ps[rr + (int64_t)j * ldp];
+            }
+        }
+        // T block of the panel (reflectors = panel rows p0.. of the panel view)
+        const double* Vp = Pb + p0;
+        cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G);
         // trailing update of the columns right of the panel
         if (pe < n) {
             Mat B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};
-            cta_apply_q_chunked(A + p0 + (int64_t)p0 * lda, lda, m - p0, pe - p0, T + p0 + (int64_t)p0 * ldt, ldt,
-                                false, B, n - pe, qc, true, W);
+            cta_apply_q_chunked(Vp, ldp, m - p0, pe - p0, T + p0 + (int64_t)p0 * ldt, ldt, false, B, n - pe, qc,
+                                true, W);
         }
+        __syncthreads();
     }
 }
 

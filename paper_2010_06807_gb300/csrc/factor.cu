@@ -71,11 +71,11 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
 constexpr int QC = 32;       // column chunk of the blocked updates
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 
-__global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks, int prow) {
     extern __shared__ double sm[];
     const QRTask t = tasks[blockIdx.x];
     const int tt = t.m < t.n ? t.m : t.n;
-    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, sm);
+    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, prow, sm);
     if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
@@ -323,6 +323,7 @@ void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& 
 }
 
 const int kSmemMax = 200 * 1024;
+const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
 bool g_attr_set = false;
 
@@ -468,12 +469,22 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         std::vector<Seg> asg;
         size_t smem_apply = 0;
         // column chunk of a task: QAPPLY, halved while the staged work area of
-        // the tallest front would not fit
+        // the tallest front would not fit or the level has too few tasks to
+        // give every SM two of them
         int qapply = QAPPLY;
         {
             int mm = 1;
+            int64_t cols = 0;
             for (size_t f = 0; f < sp.fronts.size(); f++) mm = std::max<int>(mm, (int)lay.H[sp.fronts[f]]);
+            {
+                std::vector<char> used(ncl, 0);
+                for (size_t f = 0; f < sp.fronts.size(); f++)
+                    for (size_t t = 1; t < sp.C[f].size(); t++) used[sp.C[f][t]] = 1;
+                for (int j = 0; j < ncl; j++)
+                    if (used[j]) cols += sz[j];
+            }
             while (qapply > 8 && ((mm + 1) / 2 + 1 + staged_smem_doubles(mm, qapply)) * 8 > kSmemMax) qapply /= 2;
+            while (qapply > 4 && cols / qapply < 2 * 152) qapply /= 2;
         }
         for (int j = 0; j < ncl; j++) {
             if (fronts_of[j].empty() || sz[j] == 0) continue;
@@ -534,7 +545,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         if (!qr.empty()) {
             QRTask* d = C.upload(qr, false);
             if (C.rc) return C.rc;
-            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st, k_qr<<<(unsigned)qr.size(), NT, (size_t)qr_smem_doubles(QC) * 8, st>>>(d));
+            int prow = 0;
+            for (const QRTask& q1 : qr) prow = std::max(prow, q1.m);
+            if (qr_smem_doubles(QC, prow) * 8 > kPanelSmem) prow = 0;
+            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st,
+                         k_qr<<<(unsigned)qr.size(), NT, (size_t)qr_smem_doubles(QC, prow) * 8, st>>>(d, prow));
             C.launched();
         }
         if (!at.empty()) {
@@ -676,7 +691,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (!sq.empty()) {
                 QRTask* d = C.upload(sq, false);
                 if (C.rc) return C.rc;
-                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st, k_qr<<<(unsigned)sq.size(), NT, (size_t)qr_smem_doubles(QC) * 8, st>>>(d));
+                int prow = 0;
+                for (const QRTask& q1 : sq) prow = std::max(prow, q1.m);
+                if (qr_smem_doubles(QC, prow) * 8 > kPanelSmem) prow = 0;
+                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st,
+                             k_qr<<<(unsigned)sq.size(), NT, (size_t)qr_smem_doubles(QC, prow) * 8, st>>>(d, prow));
                 C.launched();
             }
             if (!sc.empty()) {

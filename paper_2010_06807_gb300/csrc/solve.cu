@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, 
 __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
                                                    const SolveRsj* __restrict__ rsj, double* Y, int64_t ldy,
                                                    int nrhs, int qs, int* singular) {
+    __shared__ double P[NT];
     __shared__ double tmp[NB * 16];
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
@@ -133,17 +134,37 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict_
     double* Yc = Y + (int64_t)c0 * ldy;
     double* xs = Yc + s0.off;
     const int n = F.n;
-    // rhs = z_s - sum_j R_sj x_j
-    for (int64_t o = threadIdx.x; o < (int64_t)n * qn; o += NT) {
-        const int r = (int)(o % n), c = (int)(o / n);
+    // rhs = z_s - sum_j R_sj x_j; every output sum is split over G thread groups,
+    // group g taking the blocks b = g, g + G, ...
+    const int nout = n * qn;
+    int G = 1;
+    while (G < 16 && nout * G * 2 <= NT && G < F.nrsj) G *= 2;
+    for (int o0 = 0; o0 < nout; o0 += NT / G) {
+        const int tt = threadIdx.x;
+        const int o = o0 + tt % (NT / G), gg = tt / (NT / G);
         double acc = 0.0;
-        for (int b = 0; b < F.nrsj; b++) {
-            const SolveRsj R = rsj[F.rsj_begin + b];
-            const double* xj = Yc + R.xoff + (int64_t)c * ldy;
-            const double* row = R.R + r;
-            for (int u = 0; u < R.nj; u++) acc += row[(int64_t)u * R.ldr] * xj[u];
+        if (o < nout) {
+            const int r = o % n, c = o / n;
+            for (int b = gg; b < F.nrsj; b += G) {
+                const SolveRsj R = rsj[F.rsj_begin + b];
+                const double* xj = Yc + R.xoff + (int64_t)c * ldy;
+                const double* row = R.R + r;
+                for (int u = 0; u < R.nj; u++) acc += row[(int64_t)u * R.ldr] * xj[u];
+            }
         }
-        xs[r + (int64_t)c * ldy] -= acc;
+        if (G == 1) {
+            if (o < nout) xs[(o % n) + (int64_t)(o / n) * ldy] -= acc;
+        } else {
+            P[tt] = acc;
+            __syncthreads();
+            if (tt < NT / G && o0 + tt < nout) {
+                const int oo = o0 + tt;
+                double s = 0.0;
+                for (int k = 0; k < G; k++) s += P[tt + k * (NT / G)];
+                xs[(oo % n) + (int64_t)(oo / n) * ldy] -= s;
+            }
+            __syncthreads();
+        }
     }
     __syncthreads();
     cta_trsv_upper(F.V, F.ldv, n, F.Dinv, Mat{xs, 1, ldy, nullptr}, qn, tmp);
