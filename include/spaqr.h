@@ -170,6 +170,30 @@ int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts
 int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb,
                 double* X, int64_t ldx, void* stream);
 
+/* Allocation-free variant of spaqr_solve: X = M^{-1} B with the same kernels,
+ * for callers that cannot allocate device memory while they run -- for
+ * example code whose device memory is fully reserved by another allocator
+ * (a framework's caching pool), or a control loop that must not enter the CUDA
+ * allocator because cudaMalloc / cudaFree can synchronise the device and take
+ * an unbounded time.  The paper has no counterpart; it is an interface
+ * convenience.
+ * The scratch space (one vector per level, F's total level rows x nrhs
+ * doubles) lives in a fixed array of SPAQR_NOALLOC_SCRATCH_DOUBLES doubles
+ * (16 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  Calls needing more return SPAQR_ERR_INVALID_ARG
+ * (use fewer right-hand sides per call).  B and X must be device pointers
+ * (n x nrhs, leading dimensions ldb, ldx >= n; same aliasing rule as
+ * spaqr_solve).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array, so calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Nothing is allocated or freed (keep spaqr_profile off: profiling
+ * creates CUDA events).  Synchronous on `stream`.
+ * Errors: INVALID_ARG (size, host pointers), SINGULAR, CUDA. */
+#define SPAQR_NOALLOC_SCRATCH_DOUBLES (2 * 1024 * 1024)
+int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb,
+                        double* X, int64_t ldx, void* stream);
+
 /* Right-preconditioned GMRES (Section 4) for the nrhs columns of B, each with
  * its own Krylov space, using F as preconditioner and A (CSR, host or device)
  * for products.  X on entry is the initial guess, on exit the solution.

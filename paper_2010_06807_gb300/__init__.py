@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 __all__ = [
-    "SpaqrError", "load_library", "spaqr_order", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
+    "SpaqrError", "load_library", "spaqr_order", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
+    "spaqr_gmres",
     "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats",
 ]
@@ -76,7 +77,8 @@ _lib = None
 # every symbol include/spaqr.h declares
 EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_ordering_info",
-    "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_gmres",
+    "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
+    "spaqr_gmres",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats",
 ]
@@ -103,6 +105,8 @@ def load_library(path=None):
     if hasattr(lib, "spaqr_factor"):
         lib.spaqr_factor.argtypes = [vp, ctypes.POINTER(_CSR), ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
         lib.spaqr_solve.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+        if hasattr(lib, "spaqr_solve_noalloc"):
+            lib.spaqr_solve_noalloc.argtypes = [vp, i32, vp, i64, vp, i64, vp]
         lib.spaqr_gmres.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
         lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
         lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
@@ -322,6 +326,18 @@ def spaqr_solve(F, B, X=None, stream=None):
     if nrx != nrhs or xdev != bdev:
         raise ValueError("X must match B in shape and memory space")
     _check(_lib.spaqr_solve(F._h, nrhs, bp, ldb, xp, ldx, _stream_ptr(stream)))
+    return X
+
+
+def spaqr_solve_noalloc(F, B, X, stream=None):
+    """X = M^{-1} B through spaqr_solve_noalloc: device tensors only, nothing
+    allocated on the device (scratch is the library's fixed device array)."""
+    load_library()
+    bp, ldb, nrhs, kb, bdev = _dense_colmajor(B, F.n, "B")
+    xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
+    if nrx != nrhs:
+        raise ValueError("X must match B in shape")
+    _check(_lib.spaqr_solve_noalloc(F._h, nrhs, bp, ldb, xp, ldx, _stream_ptr(stream)))
     return X
 
 

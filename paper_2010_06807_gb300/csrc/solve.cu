@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -731,5 +732,90 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         if (!(hres[c] <= tol)) ok = false;
     }
     if (!ok) { set_error("GMRES did not reach tol within maxit"); return SPAQR_ERR_NOT_CONVERGED; }
+    return SPAQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.  The level vectors live in one file-scope device
+// array instead of a per-call cudaMallocAsync; its last 32 doubles hold the
+// singular flag.  Host code may not pass the symbol itself to a kernel (in
+// host code it names a host-side stand-in), so its device address is looked up
+// once per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) double g_noalloc_scratch[SPAQR_NOALLOC_SCRATCH_DOUBLES + 32];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {nullptr};
+}  // namespace
+
+extern "C" int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb, double* X,
+                                   int64_t ldx, void* stream) {
+    if (!F || !B || !X) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (nrhs < 0 || ldb < F->n || ldx < F->n) { set_error("bad nrhs or leading dimension"); return SPAQR_ERR_INVALID_ARG; }
+    if (nrhs == 0) return SPAQR_OK;
+    if (B != X) {
+        const char* b0 = (const char*)B;
+        const char* b1 = (const char*)(B + (ldb * (nrhs - 1) + F->n));
+        const char* x0 = (const char*)X;
+        const char* x1 = (const char*)(X + (ldx * (nrhs - 1) + F->n));
+        if (b0 < x1 && x0 < b1) { set_error("B and X overlap"); return SPAQR_ERR_INVALID_ARG; }
+    } else if (ldb != ldx) {
+        set_error("aliased B and X need the same leading dimension");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (F->ws_rows * (int64_t)nrhs > (int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) {
+        set_error("spaqr_solve_noalloc: needs " + std::to_string(F->ws_rows * (int64_t)nrhs) +
+                  " scratch doubles, the fixed array holds " + std::to_string((int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) +
+                  "; use fewer right-hand sides per call");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (!is_device_ptr(B) || !is_device_ptr(X)) {
+        set_error("spaqr_solve_noalloc takes device pointers only");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); set_error("cudaGetDevice failed"); return SPAQR_ERR_CUDA; }
+    if (cur != F->device && cudaSetDevice(F->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaSetDevice failed");
+        return SPAQR_ERR_CUDA;
+    }
+    const int dev = F->device;
+    double* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (dev < 0 || dev >= 128) { set_error("device index out of range"); return SPAQR_ERR_INVALID_ARG; }
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                if (cur != F->device) cudaSetDevice(cur);
+                set_error(std::string("cudaGetSymbolAddress of the solve scratch failed: ") + cudaGetErrorString(e));
+                return SPAQR_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        ws = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int* flag = reinterpret_cast<int*>(ws + SPAQR_NOALLOC_SCRATCH_DOUBLES);
+    int rc = SPAQR_OK;
+    // the flag must start at zero; the level vectors are written before read
+    if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) rc = SPAQR_ERR_CUDA;
+    if (rc == SPAQR_OK) rc = apply_device(F, nrhs, B, ldb, X, ldx, st, ws, flag);
+    int hflag = 0;
+    if (rc == SPAQR_OK && cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = SPAQR_ERR_CUDA;
+    if (rc == SPAQR_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPAQR_ERR_CUDA;
+    if (rc != SPAQR_OK) {
+        const cudaError_t e = cudaGetLastError();
+        set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+    }
+    if (cur != F->device) cudaSetDevice(cur);
+    if (rc != SPAQR_OK) return rc;
+    if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
     return SPAQR_OK;
 }
