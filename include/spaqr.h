@@ -50,8 +50,10 @@ extern "C" {
 #define SPAQR_ERR_CUDA          -7   /* a CUDA runtime call failed */
 #define SPAQR_ERR_NO_DEVICE     -8   /* no CUDA device is visible */
 
-/* precision of the factorisation (GMRES and rank decisions are always FP64) */
+/* precision of the factorisation and of its application; GMRES, the column
+ * scaling and the CPQR rank decisions are always FP64 */
 #define SPAQR_FP64 0
+#define SPAQR_FP32 1
 
 /* Sparse matrix in CSR form, rows sorted, N x N.  rowptr has n+1 entries,
  * colind/val have nnz entries.  If on_device != 0 the three arrays are device
@@ -75,7 +77,10 @@ typedef struct {
  * (|R_ii| >= eps |R_11| is kept, Section 4), eps = 0 keeps everything.
  * nlevels: 0 chooses ceil(log2(N/64)) (Section 4).  skip: number of levels
  * (from the leaves) factored before scaling/sparsification starts.
- * scaling must be 1 (the unscaled variant is not built).  precision: SPAQR_FP64.
+ * scaling must be 1 (the unscaled variant is not built).  precision:
+ * SPAQR_FP64 (plain form) or SPAQR_FP32 (mixed form: factor stored and
+ * applied in FP32, CPQR pivots from FP32 norms but each |R_kk| recomputed in
+ * FP64 for the rank decision; GMRES around it stays FP64).
  * col_normalize: scale columns of A to unit 2-norm first (Section 2.7). */
 typedef struct {
     double eps;
@@ -156,7 +161,7 @@ void spaqr_ordering_destroy(spaqr_ordering* ord);
  * returns after the factor is complete.  The factor lives in device memory of
  * the current device and is immutable afterwards, so concurrent
  * spaqr_solve / spaqr_gmres calls on different streams may share it.
- * Errors: INVALID_ARG, UNSUPPORTED (scaling = 0, precision != FP64), OOM,
+ * Errors: INVALID_ARG, UNSUPPORTED (scaling = 0, unknown precision), OOM,
  * CUDA, NO_DEVICE. */
 int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts* opts,
                  spaqr_factor_t** out);
@@ -196,7 +201,9 @@ int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const double* B, int6
 
 /* Right-preconditioned GMRES (Section 4) for the nrhs columns of B, each with
  * its own Krylov space, using F as preconditioner and A (CSR, host or device)
- * for products.  X on entry is the initial guess, on exit the solution.
+ * for products.  The flexible form is used (the preconditioned vectors
+ * Z_j = M^{-1} v_j are kept and x = x0 + Z y), so an FP32 factor, whose
+ * application is not exactly linear, still converges to FP64 accuracy.  X on entry is the initial guess, on exit the solution.
  * Converged when the explicitly recomputed ||b - A x||_2 / ||b||_2 <= tol.
  * iters[c] and relres[c] (host arrays of nrhs entries, may be NULL) receive
  * per-column iteration counts and final relative residuals.  maxit bounds the

@@ -290,13 +290,22 @@ class Factor:
             self._h = None
 
 
+SPAQR_FP64 = 0
+SPAQR_FP32 = 1
+
+
 def spaqr_factor(ordering, rowptr, colind, val, eps=1e-2, nlevels=0, skip=2, scaling=1,
-                 col_normalize=1, stream=None):
-    """Numeric spaQR factorisation (Algorithm 2) on the current CUDA device."""
+                 col_normalize=1, precision="fp64", stream=None):
+    """Numeric spaQR factorisation (Algorithm 2) on the current CUDA device.
+
+    precision: "fp64" (plain form) or "fp32" (mixed form: factor stored and
+    applied in FP32; rank decisions and GMRES stay FP64).
+    """
     load_library()
     csr, keep = _make_csr(rowptr, colind, val)
     o = _Opts()
     _lib.spaqr_opts_default(ctypes.byref(o))
+    o.precision = {"fp64": SPAQR_FP64, "fp32": SPAQR_FP32}[precision]
     o.eps = float(eps)
     o.nlevels = int(nlevels)
     o.skip = int(skip)

@@ -21,8 +21,11 @@
 // output) and only reduce across threads where a result is needed once per
 // column (norms, Householder scalars).
 //
-// Every routine is called by all NT threads of a CTA and synchronises
-// internally; operands may be in global or shared memory.
+// Every routine is templated on the storage/arithmetic type `real` (double
+// for the FP64 form, float for the mixed-precision form; Householder scalars
+// and pivot decisions stay FP64 in both), is called by all NT threads of a
+// CTA and synchronises internally; operands may be in global or shared
+// memory.
 #pragma once
 
 #include <cstdint>
@@ -78,11 +81,12 @@ __device__ __forceinline__ void block_argmax(double v, int idx, long long* redv,
 
 // Strided view of a matrix: element (r, c) is base[row(r) * rs + c * cs] with
 // row(r) = rmap ? rmap[r] : r.
+template <class real>
 struct Mat {
-    double* base;
+    real* base;
     int64_t rs, cs;
     const int* rmap;
-    __device__ __forceinline__ double& at(int r, int c) const {
+    __device__ __forceinline__ real& at(int r, int c) const {
         const int64_t rr = rmap ? (int64_t)rmap[r] : (int64_t)r;
         return base[rr * rs + (int64_t)c * cs];
     }
@@ -91,14 +95,17 @@ struct Mat {
 
 // Householder vector of column `col` (rows k..m-1, element stride `stride`)
 // in place: col[k] <- beta, col[k+1..] <- v.  Returns tau to every thread.
-__device__ __forceinline__ double cta_house(double* col, int64_t stride, int k, int m, double* red) {
-    double part = 0.0;
+// beta, tau and the scaling are computed in FP64 whatever the storage type;
+// the norm is accumulated in the storage type.
+template <class real>
+__device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, int m, double* red) {
+    real part = 0;
     for (int r = k + 1 + threadIdx.x; r < m; r += NT) {
-        const double x = col[(int64_t)r * stride];
+        const real x = col[(int64_t)r * stride];
         part += x * x;
     }
-    const double xn2 = block_sum(part, red);
-    const double alpha = col[(int64_t)k * stride];
+    const double xn2 = block_sum((double)part, red);
+    const double alpha = (double)col[(int64_t)k * stride];
     double tk = 0.0, beta = alpha, denom = 1.0;
     if (xn2 != 0.0) {
         const double s = sqrt(alpha * alpha + xn2);
@@ -107,9 +114,15 @@ __device__ __forceinline__ double cta_house(double* col, int64_t stride, int k, 
         denom = alpha - beta;
     }
     __syncthreads();
-    if (threadIdx.x == 0) col[(int64_t)k * stride] = beta;
-    if (tk != 0.0)
-        for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] = col[(int64_t)r * stride] / denom;
+    if (threadIdx.x == 0) col[(int64_t)k * stride] = (real)beta;
+    if (tk != 0.0) {
+        if constexpr (sizeof(real) == 8) {
+            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] = col[(int64_t)r * stride] / denom;
+        } else {
+            const real sc = (real)(1.0 / denom);
+            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] *= sc;
+        }
+    }
     __syncthreads();
     return tk;
 }
@@ -117,30 +130,31 @@ __device__ __forceinline__ double cta_house(double* col, int64_t stride, int k, 
 // Diagonal T blocks of the t reflectors in V (m rows, column-major, ldv); the
 // diagonal/upper part of V is not read (unit diagonal implied).  `G` holds
 // NB * NB doubles of shared memory.
-static __device__ void cta_form_tblocks(const double* V, int64_t ldv, int m, int t, const double* tau, double* T,
-                                        int ldt, double* G) {
+template <class real>
+static __device__ void cta_form_tblocks(const real* V, int64_t ldv, int m, int t, const real* tau, real* T, int ldt,
+                                        real* G) {
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pb = t - p0 < NB ? t - p0 : NB;
         // G(i, k) = V(:, p0+i)^T V(:, p0+k), i < k
         for (int o = threadIdx.x; o < pb * pb; o += NT) {
             const int i = o % pb, k = o / pb;
             if (i >= k) continue;
-            const double* vi = V + (int64_t)(p0 + i) * ldv;
-            const double* vk = V + (int64_t)(p0 + k) * ldv;
-            double s = vi[p0 + k];
+            const real* vi = V + (int64_t)(p0 + i) * ldv;
+            const real* vk = V + (int64_t)(p0 + k) * ldv;
+            real s = vi[p0 + k];
             for (int r = p0 + k + 1; r < m; r++) s += vi[r] * vk[r];
             G[i + k * NB] = s;
         }
         __syncthreads();
         for (int k = 0; k < pb; k++) {
-            const double tk = tau[p0 + k];
+            const real tk = tau[p0 + k];
             for (int i = threadIdx.x; i < k; i += NT) {
-                double s = 0.0;
+                real s = 0;
                 for (int u = i; u < k; u++) s += T[(p0 + i) + (int64_t)(p0 + u) * ldt] * G[u + k * NB];
                 T[(p0 + i) + (int64_t)(p0 + k) * ldt] = -tk * s;
             }
             if (threadIdx.x == 0) T[(p0 + k) + (int64_t)(p0 + k) * ldt] = tk;
-            for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[(p0 + i) + (int64_t)(p0 + k) * ldt] = 0.0;
+            for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[(p0 + i) + (int64_t)(p0 + k) * ldt] = 0;
             __syncthreads();
         }
     }
@@ -157,8 +171,8 @@ __device__ __forceinline__ int row_groups(int nout) {
 // W1(i, c) = sum over the rows of Vcol_i(r) * Bv(r, c) for the pb x q outputs;
 // `dot(i, c, r0, step)` returns a partial sum over rows r0, r0 + step, ...
 // P holds NT doubles.
-template <class Dot>
-__device__ __forceinline__ void cta_small_gemv(int pb, int q, double* W1, double* P, Dot dot) {
+template <class real, class Dot>
+__device__ __forceinline__ void cta_small_gemv(int pb, int q, real* W1, real* P, Dot dot) {
     const int nout = pb * q;
     const int G = row_groups(nout);
     if (G == 1) {
@@ -172,7 +186,7 @@ __device__ __forceinline__ void cta_small_gemv(int pb, int q, double* W1, double
     }
     __syncthreads();
     for (int o = threadIdx.x; o < nout; o += NT) {
-        double s = P[o];
+        real s = P[o];
         for (int g = 1; g < G; g++) s += P[o + g * nout];
         W1[o] = s;
     }
@@ -180,11 +194,12 @@ __device__ __forceinline__ void cta_small_gemv(int pb, int q, double* W1, double
 }
 
 // W2 = T_b^T W1 (trans) or T_b W1 for the diagonal T block at p0.
-__device__ __forceinline__ void cta_tblock_mul(const double* T, int ldt, int p0, int pb, int q, bool trans,
-                                               const double* W1, double* W2) {
+template <class real>
+__device__ __forceinline__ void cta_tblock_mul(const real* T, int ldt, int p0, int pb, int q, bool trans,
+                                               const real* W1, real* W2) {
     for (int o = threadIdx.x; o < pb * q; o += NT) {
         const int i = o % pb, c = o / pb;
-        double s = 0.0;
+        real s = 0;
         if (trans) {
             for (int u = 0; u <= i; u++) s += T[(p0 + u) + (int64_t)(p0 + i) * ldt] * W1[u + c * pb];
         } else {
@@ -200,12 +215,13 @@ __device__ __forceinline__ void cta_tblock_mul(const double* T, int ldt, int p0,
 // explicit_v: V holds its unit diagonal (and zeros above it) explicitly;
 // otherwise the diagonal is taken as 1 and the upper part is ignored.
 // W holds 2 * NB * q + NT doubles of shared memory.
-static __device__ void cta_apply_q(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
-                                   bool explicit_v, Mat B, int q, bool trans, double* W) {
+template <class real>
+static __device__ void cta_apply_q(const real* V, int64_t ldv, int m, int t, const real* T, int ldt,
+                                   bool explicit_v, Mat<real> B, int q, bool trans, real* W) {
     if (t <= 0 || q <= 0) return;
-    double* W1 = W;
-    double* W2 = W + NB * q;
-    double* P = W + 2 * NB * q;
+    real* W1 = W;
+    real* W2 = W + NB * q;
+    real* P = W + 2 * NB * q;
     const int nbk = (t + NB - 1) / NB;
     for (int bb = 0; bb < nbk; bb++) {
         const int b = trans ? bb : nbk - 1 - bb;
@@ -213,9 +229,9 @@ static __device__ void cta_apply_q(const double* V, int64_t ldv, int m, int t, c
         const int pb = t - p0 < NB ? t - p0 : NB;
         cta_small_gemv(pb, q, W1, P, [&](int i, int c, int g, int G) {
             const int col = p0 + i;
-            const double* v = V + (int64_t)col * ldv;
-            double s = 0.0;
-            if (g == 0) s = (explicit_v ? v[col] : 1.0) * B.at(col, c);
+            const real* v = V + (int64_t)col * ldv;
+            real s = 0;
+            if (g == 0) s = (explicit_v ? v[col] : (real)1) * B.at(col, c);
             for (int r = col + 1 + (g == 0 ? G - 1 : g - 1); r < m; r += G) s += v[r] * B.at(r, c);
             return s;
         });
@@ -225,10 +241,10 @@ static __device__ void cta_apply_q(const double* V, int64_t ldv, int m, int t, c
         for (int o = threadIdx.x; o < rows * q; o += NT) {
             const int rr = o % rows, c = o / rows, r = p0 + rr;
             const int top = rr < pb - 1 ? rr : pb - 1;   // last i with p0 + i <= r
-            double s = 0.0;
+            real s = 0;
             for (int i = 0; i < top; i++) s += V[r + (int64_t)(p0 + i) * ldv] * W2[i + c * pb];
-            const double vd = (rr == top) ? (explicit_v ? V[r + (int64_t)r * ldv] : 1.0)
-                                          : V[r + (int64_t)(p0 + top) * ldv];
+            const real vd = (rr == top) ? (explicit_v ? V[r + (int64_t)r * ldv] : (real)1)
+                                        : V[r + (int64_t)(p0 + top) * ldv];
             s += vd * W2[top + c * pb];
             B.at(r, c) -= s;
         }
@@ -236,23 +252,24 @@ static __device__ void cta_apply_q(const double* V, int64_t ldv, int m, int t, c
     }
 }
 
-// Shared memory (doubles) of cta_apply_q_staged for m rows and q columns.
-__host__ __device__ constexpr int64_t staged_smem_doubles(int m, int q) {
+// Shared memory (elements) of cta_apply_q_staged for m rows and q columns.
+__host__ __device__ constexpr int64_t staged_smem_elems(int m, int q) {
     return (int64_t)(m | 1) * (q + NB) + 2 * NB * q + NT;
 }
 
 // Same as cta_apply_q, with B (m x q) staged into shared memory once and each
 // panel of V staged before use, so the inner loops read shared memory only.
-// smem: staged_smem_doubles(m, q).
-static __device__ void cta_apply_q_staged(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
-                                          bool explicit_v, Mat B, int q, bool trans, double* sm) {
+// smem: staged_smem_elems(m, q) elements.
+template <class real>
+static __device__ void cta_apply_q_staged(const real* V, int64_t ldv, int m, int t, const real* T, int ldt,
+                                          bool explicit_v, Mat<real> B, int q, bool trans, real* sm) {
     if (t <= 0 || q <= 0) return;
     const int ld = m | 1;
-    double* Bs = sm;
-    double* Vs = Bs + (int64_t)ld * q;
-    double* W1 = Vs + (int64_t)ld * NB;
-    double* W2 = W1 + NB * q;
-    double* P = W2 + NB * q;
+    real* Bs = sm;
+    real* Vs = Bs + (int64_t)ld * q;
+    real* W1 = Vs + (int64_t)ld * NB;
+    real* W2 = W1 + NB * q;
+    real* P = W2 + NB * q;
     for (int o = threadIdx.x; o < m * q; o += NT) {
         const int r = o % m, c = o / m;
         Bs[r + c * ld] = B.at(r, c);
@@ -267,16 +284,16 @@ static __device__ void cta_apply_q_staged(const double* V, int64_t ldv, int m, i
         for (int o = threadIdx.x; o < rows * pb; o += NT) {
             const int rr = o % rows, i = o / rows;
             const int r = p0 + rr, col = p0 + i;
-            double v = 0.0;
+            real v = 0;
             if (r > col) v = V[r + (int64_t)col * ldv];
-            else if (r == col) v = explicit_v ? V[r + (int64_t)col * ldv] : 1.0;
+            else if (r == col) v = explicit_v ? V[r + (int64_t)col * ldv] : (real)1;
             Vs[rr + i * ld] = v;
         }
         __syncthreads();
         cta_small_gemv(pb, q, W1, P, [&](int i, int c, int g, int G) {
-            const double* vi = Vs + i * ld;
-            const double* bc = Bs + p0 + c * ld;
-            double s = 0.0;
+            const real* vi = Vs + i * ld;
+            const real* bc = Bs + p0 + c * ld;
+            real s = 0;
             for (int rr = i + g; rr < rows; rr += G) s += vi[rr] * bc[rr];
             return s;
         });
@@ -284,7 +301,7 @@ static __device__ void cta_apply_q_staged(const double* V, int64_t ldv, int m, i
         for (int o = threadIdx.x; o < rows * q; o += NT) {
             const int rr = o % rows, c = o / rows;
             const int top = rr < pb - 1 ? rr : pb - 1;
-            double s = 0.0;
+            real s = 0;
             for (int i = 0; i <= top; i++) s += Vs[rr + i * ld] * W2[i + c * pb];
             Bs[p0 + rr + c * ld] -= s;
         }
@@ -297,40 +314,42 @@ static __device__ void cta_apply_q_staged(const double* V, int64_t ldv, int m, i
     __syncthreads();
 }
 
-// cta_apply_q over q columns in chunks of qc (W: 2 * NB * qc + NT doubles).
-static __device__ void cta_apply_q_chunked(const double* V, int64_t ldv, int m, int t, const double* T, int ldt,
-                                           bool explicit_v, Mat B, int q, int qc, bool trans, double* W) {
+// cta_apply_q over q columns in chunks of qc (W: 2 * NB * qc + NT elements).
+template <class real>
+static __device__ void cta_apply_q_chunked(const real* V, int64_t ldv, int m, int t, const real* T, int ldt,
+                                           bool explicit_v, Mat<real> B, int q, int qc, bool trans, real* W) {
     for (int c0 = 0; c0 < q; c0 += qc) {
         const int w = q - c0 < qc ? q - c0 : qc;
         cta_apply_q(V, ldv, m, t, T, ldt, explicit_v, B.cols(c0), w, trans, W);
     }
 }
 
-// Shared memory (doubles) needed by cta_qr with column chunk qc and a staged
+// Shared memory (bytes) needed by cta_qr with column chunk qc and a staged
 // panel of up to prow rows (prow = 0: panels stay in global memory).
-__host__ __device__ constexpr int64_t qr_smem_doubles(int qc, int prow = 0) {
-    return NWARP + NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB;
+__host__ __device__ constexpr int64_t qr_smem_bytes(int esz, int qc, int prow = 0) {
+    return 8 * NWARP + (int64_t)esz * (NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB);
 }
 
 // In-place blocked Householder QR of A (m x n, lda).  tau gets min(m, n)
 // entries and T the diagonal NB blocks (ldt).  A panel of NB columns is
 // factored column by column (in shared memory when m <= prow), then applied
 // to the columns right of it as a block reflector.
-// smem: qr_smem_doubles(qc, prow).
-static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau, double* T, int ldt, int qc,
-                              int prow, double* smem) {
+// smem: qr_smem_bytes(sizeof(real), qc, prow).
+template <class real>
+static __device__ void cta_qr(real* A, int64_t lda, int m, int n, real* tau, real* T, int ldt, int qc, int prow,
+                              double* smem) {
     double* red = smem;
-    double* P = red + NWARP;     // NT partial dots
-    double* Wk = P + NT;         // NB
-    double* G = Wk + NB;         // NB * NB
-    double* W = G + NB * NB;     // 2 * NB * qc + NT
-    double* Ps = W + 2 * NB * qc + NT;   // prow * NB
+    real* P = reinterpret_cast<real*>(red + NWARP);   // NT partial dots
+    real* Wk = P + NT;         // NB
+    real* G = Wk + NB;         // NB * NB
+    real* W = G + NB * NB;     // 2 * NB * qc + NT
+    real* Ps = W + 2 * NB * qc + NT;   // prow * NB
     const int t = m < n ? m : n;
     const bool staged = m <= prow;
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pe = (t - p0 < NB ? t : p0 + NB);   // panel columns [p0, pe)
         // panel view: column k, row r -> Pb[r + (k - p0) * ldp]
-        double* Pb;
+        real* Pb;
         int64_t ldp;
         if (staged) {
             ldp = m - p0;
@@ -345,22 +364,23 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
             Pb = A + (int64_t)p0 * lda;
         }
         for (int k = p0; k < pe; k++) {
-            double* col = Pb + (int64_t)(k - p0) * ldp;
-            const double tk = cta_house(col, 1, k, m, red);
+            real* col = Pb + (int64_t)(k - p0) * ldp;
+            const double tkd = cta_house(col, 1, k, m, red);
+            const real tk = (real)tkd;
             if (threadIdx.x == 0) tau[k] = tk;
             const int ncol = pe - k - 1;
-            if (ncol > 0 && tk != 0.0) {
+            if (ncol > 0 && tkd != 0.0) {
                 // partial dots: NB column slots x (NT / NB) row groups
                 const int js = threadIdx.x % NB, g = threadIdx.x / NB;
-                double part = 0.0;
+                real part = 0;
                 if (js < ncol) {
-                    const double* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
+                    const real* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
                     for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
                 }
                 P[threadIdx.x] = part;
                 __syncthreads();
                 if (threadIdx.x < ncol) {
-                    double s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
+                    real s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
                     for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
                     Wk[threadIdx.x] = tk * s;
                 }
@@ -368,7 +388,7 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
                 const int rows = m - k;
                 for (int o = threadIdx.x; o < rows * ncol; o += NT) {
                     const int rr = o % rows, jj = o / rows, r = k + rr;
-                    const double v = rr == 0 ? 1.0 : col[r];
+                    const real v = rr == 0 ? (real)1 : col[r];
                     Pb[r + (int64_t)(k + 1 + jj - p0) * ldp] -= Wk[jj] * v;
                 }
             }
@@ -381,11 +401,11 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
             }
         }
         // T block of the panel (reflectors = panel rows p0.. of the panel view)
-        const double* Vp = Pb + p0;
+        const real* Vp = Pb + p0;
         cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G);
         // trailing update of the columns right of the panel
         if (pe < n) {
-            Mat B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};
+            Mat<real> B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};
             cta_apply_q_chunked(Vp, ldp, m - p0, pe - p0, T + p0 + (int64_t)p0 * ldt, ldt, false, B, n - pe, qc,
                                 true, W);
         }
@@ -398,23 +418,24 @@ static __device__ void cta_qr(double* A, int64_t lda, int m, int n, double* tau,
 // [b NB, b NB + bs), columns [0, bs) (ld n), upper triangular, zeros below.
 // One thread per column of a block (back substitution).  Sets *singular on a
 // zero diagonal entry (and writes zeros for it).
-static __device__ void cta_tri_inv_blocks(const double* R, int64_t ldr, int n, double* Dinv, int* singular) {
+template <class real>
+static __device__ void cta_tri_inv_blocks(const real* R, int64_t ldr, int n, real* Dinv, int* singular) {
     const int nbk = (n + NB - 1) / NB;
     for (int o = threadIdx.x; o < nbk * NB; o += NT) {
         const int b = o / NB, j = o % NB, b0 = b * NB;
         const int bs = n - b0 < NB ? n - b0 : NB;
         if (j >= bs) continue;
-        double* dj = Dinv + b0 + (int64_t)j * n;
-        for (int i = bs - 1; i > j; i--) dj[i] = 0.0;
+        real* dj = Dinv + b0 + (int64_t)j * n;
+        for (int i = bs - 1; i > j; i--) dj[i] = 0;
         for (int i = j; i >= 0; i--) {
             double s = i == j ? 1.0 : 0.0;
-            for (int u = i + 1; u <= j; u++) s -= R[(b0 + i) + (int64_t)(b0 + u) * ldr] * dj[u];
-            const double d = R[(b0 + i) + (int64_t)(b0 + i) * ldr];
+            for (int u = i + 1; u <= j; u++) s -= (double)R[(b0 + i) + (int64_t)(b0 + u) * ldr] * (double)dj[u];
+            const double d = (double)R[(b0 + i) + (int64_t)(b0 + i) * ldr];
             if (d == 0.0) {
                 if (singular) *singular = 1;
-                dj[i] = 0.0;
+                dj[i] = 0;
             } else {
-                dj[i] = s / d;
+                dj[i] = (real)(s / d);
             }
         }
     }
@@ -425,30 +446,31 @@ static __device__ void cta_tri_inv_blocks(const double* R, int64_t ldr, int n, d
 // inverted diagonal blocks Dinv (ld nj).  Per block of NB columns (left to
 // right): the update by the solved columns runs one thread per entry, then
 // the block is multiplied by Dinv_b one thread per row.
-static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int nj, const double* R, int64_t ldr,
-                                            const double* Dinv) {
+template <class real>
+static __device__ void cta_trsm_right_upper(real* B, int64_t ldb, int mi, int nj, const real* R, int64_t ldr,
+                                            const real* Dinv) {
     for (int b0 = 0; b0 < nj; b0 += NB) {
         const int bs = nj - b0 < NB ? nj - b0 : NB;
         if (b0 > 0) {
             for (int o = threadIdx.x; o < mi * bs; o += NT) {
                 const int r = o % mi, j = o / mi;
-                const double* rc = R + (int64_t)(b0 + j) * ldr;
-                double s = B[r + (int64_t)(b0 + j) * ldb];
+                const real* rc = R + (int64_t)(b0 + j) * ldr;
+                real s = B[r + (int64_t)(b0 + j) * ldb];
                 for (int u = 0; u < b0; u++) s -= B[r + (int64_t)u * ldb] * rc[u];
                 B[r + (int64_t)(b0 + j) * ldb] = s;
             }
             __syncthreads();
         }
-        const double* D = Dinv + b0;
+        const real* D = Dinv + b0;
         for (int r = threadIdx.x; r < mi; r += NT) {
-            double* br = B + r + (int64_t)b0 * ldb;
-            double t[NB];
+            real* br = B + r + (int64_t)b0 * ldb;
+            real t[NB];
 #pragma unroll
-            for (int j = 0; j < NB; j++) t[j] = j < bs ? br[(int64_t)j * ldb] : 0.0;
+            for (int j = 0; j < NB; j++) t[j] = j < bs ? br[(int64_t)j * ldb] : (real)0;
 #pragma unroll
             for (int j = NB - 1; j >= 0; j--) {
                 if (j < bs) {
-                    double x = 0.0;
+                    real x = 0;
 #pragma unroll
                     for (int l = 0; l <= j; l++) x += t[l] * D[l + (int64_t)j * nj];
                     br[(int64_t)j * ldb] = x;
@@ -463,15 +485,16 @@ static __device__ void cta_trsm_right_upper(double* B, int64_t ldb, int mi, int 
 // blocks Dinv (ld n).  Block back substitution: per block (bottom up)
 // x_b = Dinv_b y_b, then the rows above are updated.  tmp: NB * q doubles of
 // shared memory.
-static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, const double* Dinv, Mat X, int q,
-                                      double* tmp) {
+template <class real>
+static __device__ void cta_trsv_upper(const real* R, int64_t ldr, int n, const real* Dinv, Mat<real> X, int q,
+                                      real* tmp) {
     const int nbk = (n + NB - 1) / NB;
     for (int b = nbk - 1; b >= 0; b--) {
         const int b0 = b * NB;
         const int bs = n - b0 < NB ? n - b0 : NB;
         for (int o = threadIdx.x; o < bs * q; o += NT) {
             const int i = o % bs, c = o / bs;
-            double s = 0.0;
+            real s = 0;
             for (int u = i; u < bs; u++) s += Dinv[(b0 + i) + (int64_t)u * n] * X.at(b0 + u, c);
             tmp[o] = s;
         }
@@ -480,7 +503,7 @@ static __device__ void cta_trsv_upper(const double* R, int64_t ldr, int n, const
         __syncthreads();
         for (int o = threadIdx.x; o < b0 * q; o += NT) {
             const int r = o % b0, c = o / b0;
-            double s = 0.0;
+            real s = 0;
             for (int u = 0; u < bs; u++) s += R[r + (int64_t)(b0 + u) * ldr] * X.at(b0 + u, c);
             X.at(r, c) -= s;
         }

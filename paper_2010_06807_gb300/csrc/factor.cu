@@ -59,37 +59,39 @@ __global__ void k_colscale(int64_t n, const int64_t* __restrict__ csc_ptr,
     d[j] = 1.0 / sqrt(s);
 }
 
-// Level-1 arena <- A D scattered into column panels.
+// Level-1 arena <- A D scattered into column panels (rounded to the storage type).
+template <class real>
 __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int32_t* __restrict__ colind,
-                         const double* __restrict__ val, const double* __restrict__ d,
-                         double* __restrict__ arena) {
+                         const double* __restrict__ val, const double* __restrict__ d, real* __restrict__ arena) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
-    arena[off[e]] = val[e] * d[colind[e]];
+    arena[off[e]] = (real)(val[e] * d[colind[e]]);
 }
 
 constexpr int QC = 32;       // column chunk of the blocked updates
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 
-__global__ void __launch_bounds__(NT) k_qr(const QRTask* __restrict__ tasks, int prow) {
+template <class real>
+__global__ void __launch_bounds__(NT) k_qr(const QRTask<real>* __restrict__ tasks, int prow) {
     extern __shared__ double sm[];
-    const QRTask t = tasks[blockIdx.x];
+    const QRTask<real> t = tasks[blockIdx.x];
     const int tt = t.m < t.n ? t.m : t.n;
     cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, prow, sm);
     if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
 // smem layout: rmap (rmap_doubles doubles) then the work area of the apply
-// (staged: staged_smem_doubles(m, q); otherwise 2 * NB * q + NT).
-__global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask* __restrict__ tasks,
-                                                    const ApplyFront* __restrict__ fronts,
+// (staged: staged_smem_elems(m, q); otherwise 2 * NB * q + NT elements).
+template <class real>
+__global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask<real>* __restrict__ tasks,
+                                                    const ApplyFront<real>* __restrict__ fronts,
                                                     const Seg* __restrict__ segs, int rmap_doubles, int staged) {
     extern __shared__ double sm[];
     int* rmap = reinterpret_cast<int*>(sm);
-    double* W = sm + rmap_doubles;
-    const ApplyTask t = tasks[blockIdx.x];
+    real* W = reinterpret_cast<real*>(sm + rmap_doubles);
+    const ApplyTask<real> t = tasks[blockIdx.x];
     for (int f = 0; f < t.nfr; f++) {
-        const ApplyFront F = fronts[t.fr_begin + f];
+        const ApplyFront<real> F = fronts[t.fr_begin + f];
         int pos = 0;
         for (int s = 0; s < F.nseg; s++) {
             const Seg g = segs[F.seg_begin + s];
@@ -97,37 +99,43 @@ __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask* __restrict_
             pos += g.len;
         }
         __syncthreads();
-        const Mat B{t.B, 1, t.ldb, rmap};
+        const Mat<real> B{t.B, 1, t.ldb, rmap};
         if (staged) cta_apply_q_staged(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
         else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
     }
 }
 
-__global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask* __restrict__ tasks, int* singular) {
+template <class real>
+__global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask<real>* __restrict__ tasks) {
     extern __shared__ double sm[];
-    const ScaleTask t = tasks[blockIdx.x];
-    cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, Mat{t.A, 1, t.lda, nullptr}, t.nj, QC, true, sm);
+    real* W = reinterpret_cast<real*>(sm);
+    const ScaleTask<real> t = tasks[blockIdx.x];
+    cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, Mat<real>{t.A, 1, t.lda, nullptr}, t.nj, QC, true,
+                        W);
     cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, t.Dj);
-    (void)singular;
 }
 
 // Truncated CPQR of M_p (stored row-major) with column norms recomputed from
 // scratch at every step (fused into the reflector update, one thread per
 // column), pivot = largest norm, ties to the lowest column index; stops at the
-// first |R_kk| < eps |R_11|.
-__global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
-                                             const GatherSeg* __restrict__ gsegs, double eps) {
+// first |R_kk| < eps |R_11|.  The rank decision is taken in FP64: in the FP64
+// form |R_kk| is the pivot's recomputed norm; in the mixed form the norms that
+// choose the pivot are FP32 and |R_kk| is recomputed in FP64 from the pivot
+// column.
+template <class real>
+__global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ tasks,
+                                             const GatherSeg<real>* __restrict__ gsegs, double eps) {
     extern __shared__ double sm[];
     double* red = sm;                                            // NWARP
     long long* redv = reinterpret_cast<long long*>(sm + NWARP);  // NWARP
     int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
-    double* G = sm + 3 * NWARP;                                  // NB * NB
-    double* vs = G + NB * NB;                                    // n_p
-    const CPQRTask t = tasks[blockIdx.x];
+    real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
+    real* vs = G + NB * NB;                                      // n_p
+    const CPQRTask<real> t = tasks[blockIdx.x];
     const int m = t.np, c = t.ncols;
-    double* M = t.M;  // M(r, j) = M[r * c + j]
+    real* M = t.M;  // M(r, j) = M[r * c + j]
     for (int s = 0; s < t.nseg; s++) {
-        const GatherSeg g = gsegs[t.seg_begin + s];
+        const GatherSeg<real> g = gsegs[t.seg_begin + s];
         const int64_t tot = (int64_t)g.rows * g.cols;
         if (g.transpose) {
             // M(r, col_off + cc) = src[cc + r * ld], r < n_p (= cols), cc < rows
@@ -144,9 +152,9 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
     }
     __syncthreads();
     for (int j = threadIdx.x; j < c; j += NT) {
-        double s = 0.0;
+        real s = 0;
         for (int r = 0; r < m; r++) {
-            const double x = M[(int64_t)r * c + j];
+            const real x = M[(int64_t)r * c + j];
             s += x * x;
         }
         t.norms[j] = s;
@@ -159,13 +167,22 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
         double bv = -1.0;
         int bi = 0x7fffffff;
         for (int j = k + threadIdx.x; j < c; j += NT) {
-            const double v = t.norms[j];
+            const double v = (double)t.norms[j];
             if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
         }
         if (bv < 0.0) bv = 0.0;
         double gv;
         int gi;
         block_argmax(bv, bi, redv, redi, gv, gi);
+        if constexpr (sizeof(real) != 8) {
+            // |R_kk| in FP64 from the pivot column (rows k..m-1)
+            double part = 0.0;
+            for (int r = k + threadIdx.x; r < m; r += NT) {
+                const double x = (double)M[(int64_t)r * c + gi];
+                part += x * x;
+            }
+            gv = block_sum(part, red);
+        }
         const double pn = sqrt(gv);
         if (threadIdx.x == 0) t.rdiag[k] = pn;
         if (k == 0) R11 = pn;
@@ -173,8 +190,8 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
         if (pn < eps * R11) break;
         if (gi != k) {
             for (int r = threadIdx.x; r < m; r += NT) {
-                double* row = M + (int64_t)r * c;
-                const double x = row[k];
+                real* row = M + (int64_t)r * c;
+                const real x = row[k];
                 row[k] = row[gi];
                 row[gi] = x;
             }
@@ -182,18 +199,19 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
             if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
         }
         __syncthreads();
-        const double tk = cta_house(M + k, c, k, m, red);
+        const double tkd = cta_house(M + k, c, k, m, red);
+        const real tk = (real)tkd;
         if (threadIdx.x == 0) t.tau[k] = tk;
         for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
         __syncthreads();
         for (int j = k + 1 + threadIdx.x; j < c; j += NT) {
-            double d = M[(int64_t)k * c + j];
+            real d = M[(int64_t)k * c + j];
             for (int r = k + 1; r < m; r++) d += vs[r] * M[(int64_t)r * c + j];
-            const double f = tk * d;
+            const real f = tk * d;
             M[(int64_t)k * c + j] -= f;
-            double nrm = 0.0;
+            real nrm = 0;
             for (int r = k + 1; r < m; r++) {
-                const double x = M[(int64_t)r * c + j] - f * vs[r];
+                const real x = M[(int64_t)r * c + j] - f * vs[r];
                 M[(int64_t)r * c + j] = x;
                 nrm += x * x;
             }
@@ -205,7 +223,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
     // explicit reflectors V (n_p x rank, column-major), unit diagonal, zeros above
     for (int64_t o = threadIdx.x; o < (int64_t)m * rank; o += NT) {
         const int r = (int)(o % m), i = (int)(o / m);
-        t.V[r + (int64_t)i * m] = r < i ? 0.0 : (r == i ? 1.0 : M[(int64_t)r * c + i]);
+        t.V[r + (int64_t)i * m] = r < i ? (real)0 : (r == i ? (real)1 : M[(int64_t)r * c + i]);
     }
     if (threadIdx.x == 0) *t.rank = rank;
     __syncthreads();
@@ -214,9 +232,11 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask* __restrict__ tasks,
 
 // Coarse block [Q_i^T A Q_j](0:r_i, 0:r_j) into the merged block of the next
 // level; identity for diagonal blocks; plain copy when not sparsified.
-__global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask* __restrict__ tasks) {
+template <class real>
+__global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __restrict__ tasks) {
     extern __shared__ double sm[];
-    const SparsifyTask t = tasks[blockIdx.x];
+    real* W = reinterpret_cast<real*>(sm);
+    const SparsifyTask<real> t = tasks[blockIdx.x];
     if (t.mode == 2) {
         const int64_t tot = (int64_t)t.mi * t.nj;
         for (int64_t o = threadIdx.x; o < tot; o += NT) {
@@ -226,20 +246,20 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask* __restrict_
         return;
     }
     if (t.mode == 1) {
-        for (int i = threadIdx.x; i < t.ri; i += NT) t.D[i + (int64_t)i * t.ldd] = 1.0;
+        for (int i = threadIdx.x; i < t.ri; i += NT) t.D[i + (int64_t)i * t.ldd] = (real)1;
         return;
     }
     const int mi = t.mi, nj = t.nj;
-    double* X = t.scratch;  // mi x nj, ld mi
+    real* X = t.scratch;  // mi x nj, ld mi
     for (int64_t o = threadIdx.x; o < (int64_t)mi * nj; o += NT) {
         const int r = (int)(o % mi), c = (int)(o / mi);
         X[o] = t.A[r + (int64_t)c * t.lda];
     }
     __syncthreads();
     // X <- Q_i^T X
-    cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true, Mat{X, 1, mi, nullptr}, nj, QC, true, sm);
+    cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true, Mat<real>{X, 1, mi, nullptr}, nj, QC, true, W);
     // X <- X Q_j, i.e. X^T <- Q_j^T X^T with X^T(r, c) = X[c + r * mi]
-    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat{X, mi, 1, nullptr}, mi, QC, true, sm);
+    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat<real>{X, mi, 1, nullptr}, mi, QC, true, W);
     for (int64_t o = threadIdx.x; o < (int64_t)t.ri * t.rj; o += NT) {
         const int p = (int)(o % t.ri), q = (int)(o / t.ri);
         t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * mi];
@@ -325,10 +345,9 @@ void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& 
 const int kSmemMax = 200 * 1024;
 const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
-bool g_attr_set = false;
-
 }  // namespace
 
+template <class real>
 int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spaqr_factor_s* F) {
     Ctx C;
     C.F = F;
@@ -340,14 +359,18 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->L = L;
     F->skip = opt->skip;
     F->eps = opt->eps;
-    if (!g_attr_set) {
-        C.cuda(cudaFuncSetAttribute(k_front_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-        C.cuda(cudaFuncSetAttribute(k_scale_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-        C.cuda(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-        C.cuda(cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+    F->precision = sizeof(real) == 8 ? SPAQR_FP64 : SPAQR_FP32;
+    F->esz = (int)sizeof(real);
+    static bool attr_set = false;
+    if (!attr_set) {
+        C.cuda(cudaFuncSetAttribute(k_front_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_scale_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_qr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_cpqr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         if (C.rc != SPAQR_OK) return C.rc;
-        g_attr_set = true;
+        attr_set = true;
     }
+    const size_t esz = sizeof(real);
     // phase timers: (start, end, phase) event triples
     struct Timer { cudaEvent_t a, b; int ph; };
     std::vector<Timer> timers;
@@ -395,19 +418,19 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     LevelLayout lay;
     layout_of(o.steps[0], sz, lay);
     if (lay.total != o.arena1_size) { set_error("arena layout mismatch"); return SPAQR_ERR_INVALID_ARG; }
-    double* arena = C.alloc<double>(lay.total, true);
+    real* arena = C.alloc<real>(lay.total, true);
     if (C.rc) return C.rc;
-    C.cuda(cudaMemsetAsync(arena, 0, sizeof(double) * lay.total, st));
+    C.cuda(cudaMemsetAsync(arena, 0, sizeof(real) * lay.total, st));
     SPAQR_LAUNCH(KK_GATHER, 1.0 * nnz, 36.0 * nnz, st,
-                 k_gather<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, d_goff, dcol, dval, F->d_scale, arena));
+                 k_gather<real><<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, d_goff, dcol, dval, F->d_scale, arena));
     C.launched();
     tstop(3);
 
     // solve-plan host arrays
-    std::vector<SolveFront> sfronts;
+    std::vector<SolveFront<real>> sfronts;
     std::vector<Seg> ssegs;
-    std::vector<SolveRsj> srsj;
-    std::vector<SolveSS> sss;
+    std::vector<SolveRsj<real>> srsj;
+    std::vector<SolveSS<real>> sss;
     F->lv.assign(L, SolveLevelHost());
     int64_t ws = 0;
     double flops = 0.0, sflops = 0.0;
@@ -426,15 +449,15 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
 
         // ---------------- (i) factor the fronts ----------------
         double fl_qr = 0, by_qr = 0, fl_ap = 0, by_ap = 0;
-        std::vector<QRTask> qr;
-        std::vector<double*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr),
+        std::vector<QRTask<real>> qr;
+        std::vector<real*> ftau(sp.fronts.size(), nullptr), fT(sp.fronts.size(), nullptr),
             fD(sp.fronts.size(), nullptr);
         int64_t aux = 0;
         for (size_t f = 0; f < sp.fronts.size(); f++) {
             const int s = sp.fronts[f];
             aux += sz[s] + sz[s] * sz[s] + sz[s] * NB;
         }
-        double* faux = C.alloc<double>(aux, true);
+        real* faux = C.alloc<real>(aux, true);
         if (C.rc) return C.rc;
         int tmax = 1;
         {
@@ -448,7 +471,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 fD[f] = faux + a;
                 a += sz[s] * NB;
                 if (sz[s] == 0) continue;
-                qr.push_back(QRTask{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f], fD[f],
+                qr.push_back(QRTask<real>{arena + lay.poff[s], lay.H[s], (int)lay.H[s], (int)sz[s], ftau[f], fT[f], fD[f],
                                     d_flags + 2});
                 tmax = std::max<int>(tmax, (int)sz[s]);
                 const double fq = 2.0 * lay.H[s] * sz[s] * sz[s] - 2.0 / 3.0 * sz[s] * sz[s] * sz[s];
@@ -464,8 +487,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (sz[sp.fronts[f]] == 0) continue;
             for (size_t t = 1; t < sp.C[f].size(); t++) fronts_of[sp.C[f][t]].push_back((int)f);
         }
-        std::vector<ApplyTask> at;
-        std::vector<ApplyFront> af;
+        std::vector<ApplyTask<real>> at;
+        std::vector<ApplyFront<real>> af;
         std::vector<Seg> asg;
         size_t smem_apply = 0;
         // column chunk of a task: QAPPLY, halved while the staged work area of
@@ -483,7 +506,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 for (int j = 0; j < ncl; j++)
                     if (used[j]) cols += sz[j];
             }
-            while (qapply > 8 && ((mm + 1) / 2 + 1 + staged_smem_doubles(mm, qapply)) * 8 > kSmemMax) qapply /= 2;
+            while (qapply > 8 && ((mm + 1) / 2 + 1) * 8 + staged_smem_elems(mm, qapply) * (int64_t)esz > kSmemMax)
+                qapply /= 2;
             while (qapply > 4 && cols / qapply < 2 * 152) qapply /= 2;
         }
         for (int j = 0; j < ncl; j++) {
@@ -492,7 +516,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             int nmax = 1, mmax = 1;
             for (int f : fronts_of[j]) {
                 const int s = sp.fronts[f];
-                ApplyFront A1;
+                ApplyFront<real> A1;
                 A1.V = arena + lay.poff[s];
                 A1.T = fT[f];
                 A1.ldv = lay.H[s];
@@ -515,7 +539,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             const int q = qapply;
             for (int64_t c0 = 0; c0 < sz[j]; c0 += q) {
-                ApplyTask T1;
+                ApplyTask<real> T1;
                 T1.B = arena + lay.poff[j] + c0 * lay.H[j];
                 T1.ldb = lay.H[j];
                 T1.q = (int)std::min<int64_t>(q, sz[j] - c0);
@@ -530,35 +554,35 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         int rmap_d = 0, staged = 0;
         {
             int maxm = 1;
-            for (const ApplyTask& T1 : at) maxm = std::max(maxm, T1.m_max);
+            for (const ApplyTask<real>& T1 : at) maxm = std::max(maxm, T1.m_max);
             rmap_d = (maxm + 1) / 2 + 1;
-            const int64_t need = rmap_d + staged_smem_doubles(maxm, qapply);
-            if (need * 8 <= kSmemMax) {
+            const int64_t need = rmap_d * 8 + staged_smem_elems(maxm, qapply) * (int64_t)esz;
+            if (need <= kSmemMax) {
                 staged = 1;
-                smem_apply = (size_t)need * 8;
+                smem_apply = (size_t)need;
             } else {
-                smem_apply = (size_t)(rmap_d + 2 * NB * qapply + NT) * 8;
+                smem_apply = (size_t)rmap_d * 8 + (size_t)(2 * NB * qapply + NT) * esz;
             }
         }
         if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
         tstart();
         if (!qr.empty()) {
-            QRTask* d = C.upload(qr, false);
+            QRTask<real>* d = C.upload(qr, false);
             if (C.rc) return C.rc;
             int prow = 0;
-            for (const QRTask& q1 : qr) prow = std::max(prow, q1.m);
-            if (qr_smem_doubles(QC, prow) * 8 > kPanelSmem) prow = 0;
+            for (const QRTask<real>& q1 : qr) prow = std::max(prow, q1.m);
+            if (qr_smem_bytes((int)esz, QC, prow) > kPanelSmem) prow = 0;
             SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st,
-                         k_qr<<<(unsigned)qr.size(), NT, (size_t)qr_smem_doubles(QC, prow) * 8, st>>>(d, prow));
+                         k_qr<real><<<(unsigned)qr.size(), NT, (size_t)qr_smem_bytes((int)esz, QC, prow), st>>>(d, prow));
             C.launched();
         }
         if (!at.empty()) {
-            ApplyTask* d1 = C.upload(at, false);
-            ApplyFront* d2 = C.upload(af, false);
+            ApplyTask<real>* d1 = C.upload(at, false);
+            ApplyFront<real>* d2 = C.upload(af, false);
             Seg* d3 = C.upload(asg, false);
             if (C.rc) return C.rc;
             SPAQR_LAUNCH(KK_FRONT_APPLY, fl_ap, by_ap, st,
-                         k_front_apply<<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, rmap_d, staged));
+                         k_front_apply<real><<<(unsigned)at.size(), NT, smem_apply, st>>>(d1, d2, d3, rmap_d, staged));
             C.launched();
         }
         tstop(0);
@@ -581,7 +605,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
                 const int s = sp.fronts[f];
                 if (sz[s] == 0) continue;
-                SolveFront sf;
+                SolveFront<real> sf;
                 sf.V = arena + lay.poff[s];
                 sf.T = fT[f];
                 sf.Dinv = fD[f];
@@ -597,7 +621,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     const int j = sp.C[f][t];
                     if (sz[j] == 0) continue;
                     const int e = sp.find(s, j);
-                    srsj.push_back(SolveRsj{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
+                    srsj.push_back(SolveRsj<real>{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
                     sflops += 2.0 * sz[s] * sz[j];
                     sbytes += 8 * sz[s] * sz[j];
                 }
@@ -629,20 +653,20 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (!sp.is_front[i]) rest.push_back(i);
         const bool sparsify = (k + 1 > opt->skip) && !rest.empty();
         std::vector<int64_t> newsz(ncl, 0);
-        std::vector<double*> uT(ncl, nullptr), uD(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
+        std::vector<real*> uT(ncl, nullptr), uD(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
         std::vector<int> kmax(ncl, 0);
         if (sparsify) {
             // scaling QR of every diagonal block
             int64_t ua = 0;
             for (int p : rest) ua += sz[p] + sz[p] * sz[p] + sz[p] * NB;
-            double* uaux = C.alloc<double>(ua, true);
+            real* uaux = C.alloc<real>(ua, true);
             if (C.rc) return C.rc;
-            std::vector<QRTask> sq;
+            std::vector<QRTask<real>> sq;
             double fl_sq = 0, by_sq = 0, fl_sc = 0, by_sc = 0;
             int tm = 1;
             int64_t a = 0;
             for (int p : rest) {
-                double* tau = uaux + a;
+                real* tau = uaux + a;
                 a += sz[p];
                 uT[p] = uaux + a;
                 a += sz[p] * sz[p];
@@ -651,14 +675,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 if (sz[p] == 0) continue;
                 const int e = sp.find(p, p);
                 if (e < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
-                sq.push_back(QRTask{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p], uD[p], d_flags + 1});
+                sq.push_back(QRTask<real>{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p], uD[p], d_flags + 1});
                 tm = std::max<int>(tm, (int)sz[p]);
                 flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
                 fl_sq += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
                 by_sq += 24.0 * sz[p] * sz[p];
             }
             // scaling of the off-diagonal blocks
-            std::vector<ScaleTask> sc;
+            std::vector<ScaleTask<real>> sc;
             size_t smem_sc = 16;
             for (int j : rest) {
                 if (sz[j] == 0) continue;
@@ -667,7 +691,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     const int i = sp.rowidx[e];
                     if (i == j || sp.is_front[i] || sz[i] == 0) continue;
                     const int ei = sp.find(i, i);
-                    ScaleTask t;
+                    ScaleTask<real> t;
                     t.A = blk(e, j);
                     t.lda = lay.H[j];
                     t.mi = (int)sz[i];
@@ -679,7 +703,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     t.ldrj = lay.H[j];
                     t.Dj = uD[j];
                     t.q = QC;
-                    smem_sc = (size_t)(2 * NB * QC + NT) * 8;
+                    smem_sc = (size_t)(2 * NB * QC + NT) * esz;
                     sc.push_back(t);
                     const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
                     flops += fs;
@@ -689,20 +713,21 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             tstart();
             if (!sq.empty()) {
-                QRTask* d = C.upload(sq, false);
+                QRTask<real>* d = C.upload(sq, false);
                 if (C.rc) return C.rc;
                 int prow = 0;
-                for (const QRTask& q1 : sq) prow = std::max(prow, q1.m);
-                if (qr_smem_doubles(QC, prow) * 8 > kPanelSmem) prow = 0;
+                for (const QRTask<real>& q1 : sq) prow = std::max(prow, q1.m);
+                if (qr_smem_bytes((int)esz, QC, prow) > kPanelSmem) prow = 0;
                 SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st,
-                             k_qr<<<(unsigned)sq.size(), NT, (size_t)qr_smem_doubles(QC, prow) * 8, st>>>(d, prow));
+                             k_qr<real><<<(unsigned)sq.size(), NT, (size_t)qr_smem_bytes((int)esz, QC, prow), st>>>(d,
+                                                                                                                 prow));
                 C.launched();
             }
             if (!sc.empty()) {
-                ScaleTask* d = C.upload(sc, false);
+                ScaleTask<real>* d = C.upload(sc, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
-                             k_scale_apply<<<(unsigned)sc.size(), NT, smem_sc, st>>>(d, d_flags + 1));
+                             k_scale_apply<real><<<(unsigned)sc.size(), NT, smem_sc, st>>>(d));
                 C.launched();
             }
             tstop(1);
@@ -711,8 +736,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             std::vector<std::vector<std::pair<int, int>>> rowlist(ncl);   // row i -> (col j, entry)
             for (int j = 0; j < ncl; j++)
                 for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) rowlist[sp.rowidx[e]].push_back({j, e});
-            std::vector<CPQRTask> cp;
-            std::vector<GatherSeg> gs;
+            std::vector<CPQRTask<real>> cp;
+            std::vector<GatherSeg<real>> gs;
             std::vector<int> cp_of(ncl, -1);
             int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0;
             std::vector<int> ncols(ncl, 0);
@@ -735,10 +760,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 ttot += (int64_t)kmax[p] * kmax[p] + kmax[p];
                 rtot += kmax[p] + 1;
             }
-            double* Mbuf = C.alloc<double>(mtot, false);
-            double* Nbuf = C.alloc<double>(ntot, false);
-            double* Vbuf = C.alloc<double>(vtot, true);
-            double* Tbuf = C.alloc<double>(ttot, true);
+            real* Mbuf = C.alloc<real>(mtot, false);
+            real* Nbuf = C.alloc<real>(ntot, false);
+            real* Vbuf = C.alloc<real>(vtot, true);
+            real* Tbuf = C.alloc<real>(ttot, true);
             double* Rdg = C.alloc<double>(rtot, false);
             int* Rk = C.alloc<int>(ncl, false);
             if (C.rc) return C.rc;
@@ -749,7 +774,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             std::vector<int64_t> rdg_off(ncl, 0);
             for (int p : rest) {
                 if (sz[p] == 0) continue;
-                CPQRTask t;
+                CPQRTask<real> t;
                 t.M = Mbuf + mo;
                 t.norms = Nbuf + no;
                 t.np = (int)sz[p];
@@ -759,13 +784,13 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 for (int e = sp.colptr[p]; e < sp.colptr[p + 1]; e++) {
                     const int i = sp.rowidx[e];
                     if (i == p || sp.is_front[i] || sz[i] == 0) continue;
-                    gs.push_back(GatherSeg{blk(e, p), lay.H[p], (int)sz[i], (int)sz[p], 1, co});
+                    gs.push_back(GatherSeg<real>{blk(e, p), lay.H[p], (int)sz[i], (int)sz[p], 1, co});
                     co += (int)sz[i];
                 }
                 for (auto& je : rowlist[p]) {
                     const int j = je.first;
                     if (j == p || sp.is_front[j] || sz[j] == 0) continue;
-                    gs.push_back(GatherSeg{blk(je.second, j), lay.H[j], (int)sz[p], (int)sz[j], 0, co});
+                    gs.push_back(GatherSeg<real>{blk(je.second, j), lay.H[j], (int)sz[p], (int)sz[j], 0, co});
                     co += (int)sz[j];
                 }
                 t.nseg = (int)gs.size() - t.seg_begin;
@@ -789,11 +814,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 cp.push_back(t);
             }
             if (!cp.empty()) {
-                CPQRTask* d1 = C.upload(cp, false);
-                GatherSeg* d2 = C.upload(gs, false);
+                CPQRTask<real>* d1 = C.upload(cp, false);
+                GatherSeg<real>* d2 = C.upload(gs, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
-                             k_cpqr<<<(unsigned)cp.size(), NT, (size_t)(3 * NWARP + NB * NB + npmax) * 8, st>>>(d1, d2, opt->eps));
+                             k_cpqr<real><<<(unsigned)cp.size(), NT, (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz,
+                                            st>>>(d1, d2, opt->eps));
                 C.launched();
             }
             // ranks back to the host (the only device->host sync of a level)
@@ -834,11 +860,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             LevelLayout nl;
             layout_of(sn, nsz, nl);
-            double* narena = C.alloc<double>(nl.total, true);
+            real* narena = C.alloc<real>(nl.total, true);
             if (C.rc) return C.rc;
             tstart();
-            C.cuda(cudaMemsetAsync(narena, 0, sizeof(double) * nl.total, st));
-            std::vector<SparsifyTask> sk;
+            C.cuda(cudaMemsetAsync(narena, 0, sizeof(real) * nl.total, st));
+            std::vector<SparsifyTask<real>> sk;
             int64_t scr = 0;
             double fl_sp = 0, by_sp = 0;
             for (int j : rest) {
@@ -848,7 +874,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     const int I = sp.parent[i], J = sp.parent[j];
                     const int e2 = sn.find(I, J);
                     if (e2 < 0) { set_error("merged block missing"); return SPAQR_ERR_INVALID_ARG; }
-                    SparsifyTask t;
+                    SparsifyTask<real> t;
                     std::memset(&t, 0, sizeof(t));
                     t.A = blk(e, j);
                     t.lda = lay.H[j];
@@ -874,7 +900,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         t.Tj = qT[j];
                         t.rj = (int)newsz[j];
                         t.ldtj = kmax[j];
-                        t.scratch = (double*)(intptr_t)scr;  // offset, fixed below
+                        t.scratch = (real*)(intptr_t)scr;  // offset, fixed below
                         scr += (int64_t)t.mi * t.nj;
                         const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.rj * t.nj * t.mi;
                         flops += fp;
@@ -885,21 +911,21 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
             }
             if (!sk.empty()) {
-                double* sbuf = C.alloc<double>(scr, false);
+                real* sbuf = C.alloc<real>(scr, false);
                 if (C.rc) return C.rc;
-                for (SparsifyTask& t : sk)
+                for (SparsifyTask<real>& t : sk)
                     if (t.mode == 0) t.scratch = sbuf + (int64_t)(intptr_t)t.scratch;
-                SparsifyTask* d = C.upload(sk, false);
+                SparsifyTask<real>* d = C.upload(sk, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_SPARSIFY, fl_sp, by_sp, st,
-                             k_sparsify<<<(unsigned)sk.size(), NT, (size_t)(2 * NB * QC + NT) * 8, st>>>(d));
+                             k_sparsify<real><<<(unsigned)sk.size(), NT, (size_t)(2 * NB * QC + NT) * esz, st>>>(d));
                 C.launched();
             }
             tstop(3);
             // solve record of the surviving clusters
             LV.ss_begin = (int)sss.size();
             for (int p : rest) {
-                SolveSS s;
+                SolveSS<real> s;
                 std::memset(&s, 0, sizeof(s));
                 s.off = lay.voff[p];
                 s.noff = nl.voff[sp.parent[p]] + coff[p];
@@ -966,6 +992,9 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     return SPAQR_OK;
 }
 
+template int run_factor<double>(const Ordering&, const spaqr_csr*, const spaqr_opts*, spaqr_factor_s*);
+template int run_factor<float>(const Ordering&, const spaqr_csr*, const spaqr_opts*, spaqr_factor_s*);
+
 }  // namespace spaqr
 
 // ---------------------------------------------------------------------------
@@ -988,7 +1017,10 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
         return SPAQR_ERR_INVALID_ARG;
     }
     if (opts->scaling != 1) { set_error("only the scaled variant is built (scaling = 1)"); return SPAQR_ERR_UNSUPPORTED; }
-    if (opts->precision != SPAQR_FP64) { set_error("only FP64 factorisation is built"); return SPAQR_ERR_UNSUPPORTED; }
+    if (opts->precision != SPAQR_FP64 && opts->precision != SPAQR_FP32) {
+        set_error("precision must be SPAQR_FP64 or SPAQR_FP32");
+        return SPAQR_ERR_UNSUPPORTED;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -1000,7 +1032,8 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
     cudaGetDevice(&F->device);
     int rc;
     try {
-        rc = run_factor(ord->o, A, opts, F);
+        rc = opts->precision == SPAQR_FP32 ? run_factor<float>(ord->o, A, opts, F)
+                                           : run_factor<double>(ord->o, A, opts, F);
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
         rc = SPAQR_ERR_OOM;

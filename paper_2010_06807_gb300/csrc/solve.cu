@@ -33,21 +33,25 @@
 
 namespace spaqr {
 
+// Level-1 vector <- permuted right-hand sides (rounded to the factor's type).
+template <class real>
 __global__ void k_perm_in(int64_t n, int nrhs, const int64_t* __restrict__ perm, const double* __restrict__ B,
-                          int64_t ldb, double* __restrict__ Y, int64_t ldy) {
+                          int64_t ldb, real* __restrict__ Y, int64_t ldy) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t g = perm[i];
-    for (int c = 0; c < nrhs; c++) Y[i + c * ldy] = B[g + c * ldb];
+    for (int c = 0; c < nrhs; c++) Y[i + c * ldy] = (real)B[g + c * ldb];
 }
 
+// X <- D (permuted back) level-1 vector, in FP64.
+template <class real>
 __global__ void k_perm_out(int64_t n, int nrhs, const int64_t* __restrict__ perm, const double* __restrict__ d,
-                           const double* __restrict__ Y, int64_t ldy, double* __restrict__ X, int64_t ldx) {
+                           const real* __restrict__ Y, int64_t ldy, double* __restrict__ X, int64_t ldx) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t g = perm[i];
     const double s = d[g];
-    for (int c = 0; c < nrhs; c++) X[g + c * ldx] = s * Y[i + c * ldy];
+    for (int c = 0; c < nrhs; c++) X[g + c * ldx] = s * (double)Y[i + c * ldy];
 }
 
 // The right-hand sides of a launch are split into blockIdx.y chunks of qs
@@ -58,15 +62,16 @@ __device__ __forceinline__ bool rhs_chunk(int nrhs, int qs, int& c0, int& qn) {
     return qn > 0;
 }
 
-__global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
-                                                   double* Y, int64_t ldy, int nrhs, int qs, int rmap_doubles,
-                                                   int staged) {
+template <class real>
+__global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront<real>* __restrict__ fr,
+                                                   const Seg* __restrict__ segs, real* Y, int64_t ldy, int nrhs,
+                                                   int qs, int rmap_doubles, int staged) {
     extern __shared__ double sm[];
     int* rmap = reinterpret_cast<int*>(sm);
-    double* W = sm + rmap_doubles;
+    real* W = reinterpret_cast<real*>(sm + rmap_doubles);
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
-    const SolveFront F = fr[blockIdx.x];
+    const SolveFront<real> F = fr[blockIdx.x];
     int pos = 0;
     for (int s = 0; s < F.nseg; s++) {
         const Seg g = segs[F.seg_begin + s];
@@ -74,19 +79,21 @@ __global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront* __restrict_
         pos += g.len;
     }
     __syncthreads();
-    const Mat B{Y + (int64_t)c0 * ldy, 1, ldy, rmap};
+    const Mat<real> B{Y + (int64_t)c0 * ldy, 1, ldy, rmap};
     if (staged) cta_apply_q_staged(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, qn, true, W);
     else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, qn, true, W);
 }
 
-__global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy, double* Yn,
+template <class real>
+__global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS<real>* __restrict__ ss, real* Y, int64_t ldy, real* Yn,
                                                 int64_t ldyn, int nrhs, int qs, int staged) {
-    extern __shared__ double sm[];
+    extern __shared__ double smd[];
+    real* sm = reinterpret_cast<real*>(smd);
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
-    const SolveSS S = ss[blockIdx.x];
-    double* y = Y + S.off + (int64_t)c0 * ldy;
-    const Mat B{y, 1, ldy, nullptr};
+    const SolveSS<real> S = ss[blockIdx.x];
+    real* y = Y + S.off + (int64_t)c0 * ldy;
+    const Mat<real> B{y, 1, ldy, nullptr};
     if (S.UV) {
         if (staged) cta_apply_q_staged(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
         else cta_apply_q(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
@@ -101,20 +108,22 @@ __global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS* __restrict__ ss, 
     }
 }
 
-__global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, double* Y, int64_t ldy,
-                                                const double* Yn, int64_t ldyn, int nrhs, int qs, int staged,
+template <class real>
+__global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS<real>* __restrict__ ss, real* Y, int64_t ldy,
+                                                const real* Yn, int64_t ldyn, int nrhs, int qs, int staged,
                                                 int* singular) {
-    extern __shared__ double sm[];
+    extern __shared__ double smd[];
+    real* sm = reinterpret_cast<real*>(smd);
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
-    const SolveSS S = ss[blockIdx.x];
-    double* y = Y + S.off + (int64_t)c0 * ldy;
+    const SolveSS<real> S = ss[blockIdx.x];
+    real* y = Y + S.off + (int64_t)c0 * ldy;
     for (int64_t o = threadIdx.x; o < (int64_t)S.r * qn; o += NT) {
         const int r = (int)(o % S.r), c = (int)(o / S.r);
         y[r + c * ldy] = Yn[S.noff + r + (c0 + c) * ldyn];
     }
     __syncthreads();
-    const Mat B{y, 1, ldy, nullptr};
+    const Mat<real> B{y, 1, ldy, nullptr};
     if (S.QV && S.r > 0) {
         if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
         else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
@@ -123,17 +132,18 @@ __global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS* __restrict__ ss, 
     (void)singular;
 }
 
-__global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict__ fr, const Seg* __restrict__ segs,
-                                                   const SolveRsj* __restrict__ rsj, double* Y, int64_t ldy,
-                                                   int nrhs, int qs, int* singular) {
-    __shared__ double P[NT];
-    __shared__ double tmp[NB * 16];
+template <class real>
+__global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront<real>* __restrict__ fr,
+                                                   const Seg* __restrict__ segs, const SolveRsj<real>* __restrict__ rsj,
+                                                   real* Y, int64_t ldy, int nrhs, int qs, int* singular) {
+    __shared__ real P[NT];
+    __shared__ real tmp[NB * 16];
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
-    const SolveFront F = fr[blockIdx.x];
+    const SolveFront<real> F = fr[blockIdx.x];
     const Seg s0 = segs[F.seg_begin];  // the front's own rows
-    double* Yc = Y + (int64_t)c0 * ldy;
-    double* xs = Yc + s0.off;
+    real* Yc = Y + (int64_t)c0 * ldy;
+    real* xs = Yc + s0.off;
     const int n = F.n;
     // rhs = z_s - sum_j R_sj x_j; every output sum is split over G thread groups,
     // group g taking the blocks b = g, g + G, ...
@@ -143,13 +153,13 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict_
     for (int o0 = 0; o0 < nout; o0 += NT / G) {
         const int tt = threadIdx.x;
         const int o = o0 + tt % (NT / G), gg = tt / (NT / G);
-        double acc = 0.0;
+        real acc = 0;
         if (o < nout) {
             const int r = o % n, c = o / n;
             for (int b = gg; b < F.nrsj; b += G) {
-                const SolveRsj R = rsj[F.rsj_begin + b];
-                const double* xj = Yc + R.xoff + (int64_t)c * ldy;
-                const double* row = R.R + r;
+                const SolveRsj<real> R = rsj[F.rsj_begin + b];
+                const real* xj = Yc + R.xoff + (int64_t)c * ldy;
+                const real* row = R.R + r;
                 for (int u = 0; u < R.nj; u++) acc += row[(int64_t)u * R.ldr] * xj[u];
             }
         }
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict_
             __syncthreads();
             if (tt < NT / G && o0 + tt < nout) {
                 const int oo = o0 + tt;
-                double s = 0.0;
+                real s = 0;
                 for (int k = 0; k < G; k++) s += P[tt + k * (NT / G)];
                 xs[(oo % n) + (int64_t)(oo / n) * ldy] -= s;
             }
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront* __restrict_
         }
     }
     __syncthreads();
-    cta_trsv_upper(F.V, F.ldv, n, F.Dinv, Mat{xs, 1, ldy, nullptr}, qn, tmp);
+    cta_trsv_upper(F.V, F.ldv, n, F.Dinv, Mat<real>{xs, 1, ldy, nullptr}, qn, tmp);
     (void)singular;
 }
 
@@ -341,7 +351,6 @@ __global__ void k_scale_cols(int64_t n, int nrhs, double* __restrict__ U, const 
 namespace {
 
 const int kSmemMax = 200 * 1024;
-bool g_solve_attr = false;
 
 struct SCtx {
     cudaStream_t st;
@@ -386,12 +395,14 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+template <class real>
 void set_solve_attrs() {
-    if (g_solve_attr) return;
-    cudaFuncSetAttribute(k_sfront_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    cudaFuncSetAttribute(k_sss_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    cudaFuncSetAttribute(k_sss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    g_solve_attr = true;
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_sfront_fwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    cudaFuncSetAttribute(k_sss_fwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    cudaFuncSetAttribute(k_sss_bwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    done = true;
 }
 
 }  // namespace
@@ -407,20 +418,23 @@ static int rhs_split(int blocks, int nrhs) {
     return split;
 }
 
-static int64_t smem_limit_doubles() { return kSmemMax / 8; }
-
-int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
-                 cudaStream_t st, double* ws, int* singular) {
-    set_solve_attrs();
+template <class real>
+int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                   cudaStream_t st, real* ws, int* singular) {
+    set_solve_attrs<real>();
+    const int64_t esz = (int64_t)sizeof(real);
+    const SolveFront<real>* dfr = static_cast<const SolveFront<real>*>(F->d_fronts);
+    const SolveSS<real>* dss = static_cast<const SolveSS<real>*>(F->d_ss);
+    const SolveRsj<real>* drsj = static_cast<const SolveRsj<real>*>(F->d_rsj);
     const int64_t n = F->n;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    double* Y0 = ws + F->lv[0].ws_off * nrhs;
+    real* Y0 = ws + F->lv[0].ws_off * nrhs;
     SPAQR_LAUNCH(KK_SOLVE_PERM, 0.0, 8.0 * n + 16.0 * n * nrhs, st,
-                 k_perm_in<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows));
+                 k_perm_in<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows));
     const int L = F->L;
     for (int k = 0; k < L; k++) {
         const SolveLevelHost& LV = F->lv[k];
-        double* Y = ws + LV.ws_off * nrhs;
+        real* Y = ws + LV.ws_off * nrhs;
         const int64_t ldy = LV.rows;
         if (LV.nfront > 0) {
             const int rmap_d = (LV.max_front_m + 1) / 2 + 1;
@@ -429,12 +443,12 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
                 if (b <= a) continue;
                 const int split = rhs_split(b - a, nrhs);
                 const int qs = (nrhs + split - 1) / split;
-                const int staged = rmap_d + staged_smem_doubles(LV.max_front_m, qs) <= smem_limit_doubles();
-                const size_t smem = (size_t)(rmap_d + (staged ? staged_smem_doubles(LV.max_front_m, qs)
-                                                               : 2 * NB * qs + NT)) * 8;
+                const int staged = rmap_d * 8 + staged_smem_elems(LV.max_front_m, qs) * esz <= kSmemMax;
+                const size_t smem = (size_t)rmap_d * 8 +
+                                    (size_t)(staged ? staged_smem_elems(LV.max_front_m, qs) : 2 * NB * qs + NT) * esz;
                 SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs,
                              st,
-                             k_sfront_fwd<<<dim3(b - a, split), NT, smem, st>>>(F->d_fronts + LV.front_begin + a,
+                             k_sfront_fwd<real><<<dim3(b - a, split), NT, smem, st>>>(dfr + LV.front_begin + a,
                                                                                 F->d_segs, Y, ldy, nrhs, qs, rmap_d,
                                                                                 staged));
             }
@@ -443,26 +457,26 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
             const SolveLevelHost& LN = F->lv[k + 1];
             const int split = rhs_split(LV.nss, nrhs);
             const int qs = (nrhs + split - 1) / split;
-            const int staged = staged_smem_doubles(LV.max_ss_n, qs) <= smem_limit_doubles();
-            const size_t smem = (size_t)(staged ? staged_smem_doubles(LV.max_ss_n, qs) : 2 * NB * qs + NT) * 8;
+            const int staged = staged_smem_elems(LV.max_ss_n, qs) * esz <= kSmemMax;
+            const size_t smem = (size_t)(staged ? staged_smem_elems(LV.max_ss_n, qs) : 2 * NB * qs + NT) * esz;
             SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed * split + LV.ssf_vec * nrhs, st,
-                         k_sss_fwd<<<dim3(LV.nss, split), NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy,
+                         k_sss_fwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(dss + LV.ss_begin, Y, ldy,
                                                                           ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
                                                                           staged));
         }
     }
     for (int k = L - 1; k >= 0; k--) {
         const SolveLevelHost& LV = F->lv[k];
-        double* Y = ws + LV.ws_off * nrhs;
+        real* Y = ws + LV.ws_off * nrhs;
         const int64_t ldy = LV.rows;
         if (LV.nss > 0) {
             const SolveLevelHost& LN = F->lv[k + 1];
             const int split = rhs_split(LV.nss, nrhs);
             const int qs = (nrhs + split - 1) / split;
-            const int staged = staged_smem_doubles(LV.max_ss_n, qs) <= smem_limit_doubles();
-            const size_t smem = (size_t)(staged ? staged_smem_doubles(LV.max_ss_n, qs) : 2 * NB * qs + NT) * 8;
+            const int staged = staged_smem_elems(LV.max_ss_n, qs) * esz <= kSmemMax;
+            const size_t smem = (size_t)(staged ? staged_smem_elems(LV.max_ss_n, qs) : 2 * NB * qs + NT) * esz;
             SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed * split + LV.ssb_vec * nrhs, st,
-                         k_sss_bwd<<<dim3(LV.nss, split), NT, smem, st>>>(F->d_ss + LV.ss_begin, Y, ldy,
+                         k_sss_bwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(dss + LV.ss_begin, Y, ldy,
                                                                           ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
                                                                           staged, singular));
         }
@@ -470,13 +484,23 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
             const int split = rhs_split(LV.nfront, nrhs);
             const int qs = (nrhs + split - 1) / split;
             SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed * split + LV.fb_vec * nrhs, st,
-                         k_sfront_bwd<<<dim3(LV.nfront, split), NT, 0, st>>>(F->d_fronts + LV.front_begin, F->d_segs,
-                                                                             F->d_rsj, Y, ldy, nrhs, qs, singular));
+                         k_sfront_bwd<real><<<dim3(LV.nfront, split), NT, 0, st>>>(dfr + LV.front_begin, F->d_segs,
+                                                                                   drsj, Y, ldy, nrhs, qs, singular));
         }
     }
     SPAQR_LAUNCH(KK_SOLVE_PERM, 1.0 * n * nrhs, 16.0 * n + 16.0 * n * nrhs, st,
-                 k_perm_out<<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
+                 k_perm_out<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
     return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
+}
+
+// X = M^{-1} B with B, X device pointers (FP64, n x nrhs, leading dims) in the
+// factor's precision; `ws` holds ws_rows * nrhs elements of that type.
+// Stream-ordered, no synchronisation.
+int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                 cudaStream_t st, void* ws, int* singular) {
+    if (F->precision == SPAQR_FP32)
+        return apply_device_t<float>(F, nrhs, B, ldb, X, ldx, st, static_cast<float*>(ws), singular);
+    return apply_device_t<double>(F, nrhs, B, ldb, X, ldx, st, static_cast<double*>(ws), singular);
 }
 
 }  // namespace spaqr
@@ -517,7 +541,7 @@ extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, i
         dX = t;
         lb = lx = n;
     }
-    double* ws = C.alloc<double>(F->ws_rows * nrhs);
+    double* ws = C.alloc<double>((F->ws_rows * nrhs * F->esz + 7) / 8);
     int* flag = C.alloc<int>(1);
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), C.st));
@@ -584,7 +608,7 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     double* X0 = C.alloc<double>(n * nrhs);
     double* Wv = C.alloc<double>(n * nrhs);
     double* Zv = C.alloc<double>(n * nrhs);
-    double* ws = C.alloc<double>(F->ws_rows * nrhs);
+    double* ws = C.alloc<double>((F->ws_rows * nrhs * F->esz + 7) / 8);
     double* H = C.alloc<double>(hstride * nrhs);
     double* h1 = C.alloc<double>((int64_t)ldh * nrhs);
     double* h2 = C.alloc<double>((int64_t)ldh * nrhs);
@@ -602,6 +626,7 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     if (C.rc) return C.rc;
     int cap = std::min(maxit, 48) + 1;
     double* Vb = C.alloc<double>((int64_t)cap * n * nrhs);
+    double* Zb = C.alloc<double>((int64_t)cap * n * nrhs);   // Z_j = M^{-1} V_j (flexible GMRES)
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
     C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nrhs, st));
@@ -648,17 +673,22 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         if (j + 1 >= cap) {
             const int ncap = std::min(maxit, 2 * cap) + 1;
             double* nv = C.alloc<double>((int64_t)ncap * n * nrhs);
+            double* nz = C.alloc<double>((int64_t)ncap * n * nrhs);
             if (C.rc) break;
             C.cuda(cudaMemcpyAsync(nv, Vb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            C.cuda(cudaMemcpyAsync(nz, Zb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
             C.release(Vb);
+            C.release(Zb);
             Vb = nv;
+            Zb = nz;
             cap = ncap;
         }
         double* Vj = Vb + (int64_t)j * n * nrhs;
-        // z = M^{-1} v_j ; w = A z
-        int rc = apply_device(F, nrhs, Vj, n, Zv, n, st, ws, flag);
+        double* Zj = Zb + (int64_t)j * n * nrhs;
+        // z_j = M^{-1} v_j (kept: flexible GMRES) ; w = A z_j
+        int rc = apply_device(F, nrhs, Vj, n, Zj, n, st, ws, flag);
         if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
-        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st, k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zv, n, Wv, n));
+        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st, k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zj, n, Wv, n));
         // classical Gram-Schmidt, twice
         SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * ((j + 1) + 1) * nrhs, st, k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h1, ldh));
         SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 3) * nrhs, st, k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h1, ldh, Wv, active));
@@ -683,13 +713,11 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
             if (hest[c] <= tol || hnv[c] == 0.0 || j == maxit - 1) { hwant[c] = 1; anyw = true; }
         }
         if (!anyw) continue;
-        // candidate x = x0 + M^{-1} (V y) for the wanted columns; keep it if the
+        // candidate x = x0 + Z y for the wanted columns; keep it if the
         // recomputed residual meets tol
         C.cuda(cudaMemcpyAsync(want, hwant.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
         SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * (j + 1) * (j + 1) * nrhs, 8.0 * (j + 1) * (j + 1) * nrhs, st, k_hsolve<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, g, ldh, ycoef, want));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 2) * nrhs, st, k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, ycoef, ldh, Wv));
-        rc = apply_device(F, nrhs, Wv, n, Zv, n, st, ws, flag);
-        if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 2) * nrhs, st, k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Zb, j + 1, ycoef, ldh, Zv));
         // trial X into Wv: Wv = X0 + Zv (all columns), residual into Zv
         SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 24.0 * n * nrhs, st, k_accept<<<nbl, 256, 0, st>>>(n, nrhs, X0, n, Zv, Wv, n, want));
         SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv));
@@ -765,10 +793,10 @@ extern "C" int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const doub
         set_error("aliased B and X need the same leading dimension");
         return SPAQR_ERR_INVALID_ARG;
     }
-    if (F->ws_rows * (int64_t)nrhs > (int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) {
-        set_error("spaqr_solve_noalloc: needs " + std::to_string(F->ws_rows * (int64_t)nrhs) +
-                  " scratch doubles, the fixed array holds " + std::to_string((int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) +
-                  "; use fewer right-hand sides per call");
+    const int64_t need = (F->ws_rows * (int64_t)nrhs * F->esz + 7) / 8;
+    if (need > (int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) {
+        set_error("spaqr_solve_noalloc: needs " + std::to_string(need) + " scratch doubles, the fixed array holds " +
+                  std::to_string((int64_t)SPAQR_NOALLOC_SCRATCH_DOUBLES) + "; use fewer right-hand sides per call");
         return SPAQR_ERR_INVALID_ARG;
     }
     if (!is_device_ptr(B) || !is_device_ptr(X)) {

@@ -13,13 +13,14 @@ namespace spaqr {
 
 // Householder QR of an m x n block in place (front of a separator, Section
 // 2.4, or diagonal block of an interface, Section 2.5).
+template <class real>
 struct QRTask {
-    double* A;
+    real* A;
     int64_t lda;
     int m, n;
-    double* tau;   // min(m, n)
-    double* T;     // t x t block-diagonal T, ld = t
-    double* Dinv;  // inverted diagonal blocks of R (t x NB, ld t), or null
+    real* tau;   // min(m, n)
+    real* T;     // t x t block-diagonal T, ld = t
+    real* Dinv;  // inverted diagonal blocks of R (t x NB, ld t), or null
     int* singular; // set on a zero diagonal of R
 };
 
@@ -32,17 +33,19 @@ struct Seg {
 
 // One front applied to one column panel (Section 2.4: H_s^T on the columns
 // C(s) restricted to the rows R(s)).
+template <class real>
 struct ApplyFront {
-    const double* V;   // front panel (reflectors below the diagonal)
-    const double* T;
+    const real* V;   // front panel (reflectors below the diagonal)
+    const real* T;
     int64_t ldv;
     int m, n;          // front rows, reflectors
     int seg_begin, nseg;
 };
 
 // A chunk of columns of panel j, with the fronts to apply in order.
+template <class real>
 struct ApplyTask {
-    double* B;         // first column of the chunk
+    real* B;         // first column of the chunk
     int64_t ldb;
     int q;             // chunk width
     int fr_begin, nfr;
@@ -50,22 +53,24 @@ struct ApplyTask {
 };
 
 // Block (i, j) <- U_i^T A_ij R_j^{-1} (Section 2.5).
+template <class real>
 struct ScaleTask {
-    double* A;
+    real* A;
     int64_t lda;
     int mi, nj;
-    const double* Vi;   // diagonal block i after its QR (reflectors below the diagonal)
+    const real* Vi;   // diagonal block i after its QR (reflectors below the diagonal)
     int64_t ldvi;
-    const double* Ti;   // n_i x n_i, ld n_i
-    const double* Rj;   // diagonal block j (R on and above the diagonal)
+    const real* Ti;   // n_i x n_i, ld n_i
+    const real* Rj;   // diagonal block j (R on and above the diagonal)
     int64_t ldrj;
-    const double* Dj;   // inverted diagonal NB blocks of R_j (n_j x NB, ld n_j)
+    const real* Dj;   // inverted diagonal NB blocks of R_j (n_j x NB, ld n_j)
     int q;              // column chunk for the U^T product
 };
 
 // Column segment of M_p = [A_{k p}^T ... | A_{p j} ...] (Section 2.5).
+template <class real>
 struct GatherSeg {
-    const double* src;
+    const real* src;
     int64_t ld;
     int rows, cols;     // of the source block
     int transpose;      // 1: src is A_{k p} (n_k x n_p) and enters as its transpose
@@ -73,15 +78,16 @@ struct GatherSeg {
 };
 
 // Truncated column-pivoted QR of M_p (rank rule of Section 4).
+template <class real>
 struct CPQRTask {
-    double* M;          // scratch n_p x ncols, ld n_p
-    double* norms;      // scratch ncols
+    real* M;          // scratch n_p x ncols, ld n_p
+    real* norms;      // scratch ncols
     int np, ncols;
     int seg_begin, nseg;
-    double* V;          // out: n_p x kmax explicit reflectors, ld n_p
-    double* tau;        // out: kmax
-    double* T;          // out: r x r compact-WY, ld kmax
-    double* rdiag;      // out: pivot norms, kmax + 1 entries
+    real* V;          // out: n_p x kmax explicit reflectors, ld n_p
+    real* tau;        // out: kmax
+    real* T;          // out: r x r compact-WY, ld kmax
+    double* rdiag;    // out: pivot norms (FP64), kmax + 1 entries
     int* rank;          // out
     int kmax;           // min(n_p, ncols)
 };
@@ -89,19 +95,20 @@ struct CPQRTask {
 // New block (r_i x r_j) = [Q_i^T A_ij Q_j] (coarse rows/cols, Sections 2.5),
 // written at its place in the merged block of the next level (Section 2.6);
 // or a plain copy when the level is not sparsified.
+template <class real>
 struct SparsifyTask {
-    const double* A;
+    const real* A;
     int64_t lda;
     int mi, nj;
-    const double* Vi;   // n_i x r_i explicit, ld n_i
-    const double* Ti;   // ld kmax_i
+    const real* Vi;   // n_i x r_i explicit, ld n_i
+    const real* Ti;   // ld kmax_i
     int ri, ldti;
-    const double* Vj;
-    const double* Tj;
+    const real* Vj;
+    const real* Tj;
     int rj, ldtj;
-    double* D;
+    real* D;
     int64_t ldd;
-    double* scratch;    // 2 * r_i * n_j + 2 * r_i * r_j doubles
+    real* scratch;    // 2 * r_i * n_j + 2 * r_i * r_j doubles
     int mode;           // 0 sparsify, 1 identity r_i, 2 copy
 };
 
@@ -109,18 +116,20 @@ struct SparsifyTask {
 // solve descriptors
 // ---------------------------------------------------------------------------
 
+template <class real>
 struct SolveFront {
-    const double* V;   // front panel: reflectors below the diagonal, R_ss on top
-    const double* T;
-    const double* Dinv;  // inverted diagonal blocks of R_ss (n x NB, ld n)
+    const real* V;   // front panel: reflectors below the diagonal, R_ss on top
+    const real* T;
+    const real* Dinv;  // inverted diagonal blocks of R_ss (n x NB, ld n)
     int64_t ldv;
     int m, n;
     int seg_begin, nseg;   // rows R(s) in the level vector (first segment = s)
     int rsj_begin, nrsj;
 };
 
+template <class real>
 struct SolveRsj {
-    const double* R;   // n_s x n_j block of row s in column j
+    const real* R;   // n_s x n_j block of row s in column j
     int64_t ldr;
     int nj;
     int pad;
@@ -129,16 +138,17 @@ struct SolveRsj {
 
 // Scaling + sparsification (or plain carry-over) of one cluster that survives
 // a level.
+template <class real>
 struct SolveSS {
     int64_t off;       // rows in this level's vector
     int64_t noff;      // rows of its coarse part in the next level's vector
     int np, r;
-    const double* UV;  // diagonal block after the scaling QR (null: not scaled)
+    const real* UV;  // diagonal block after the scaling QR (null: not scaled)
     int64_t lduv;
-    const double* UT;  // n_p x n_p
-    const double* UD;  // inverted diagonal blocks of R_pp (n_p x NB, ld n_p)
-    const double* QV;  // n_p x r explicit
-    const double* QT;  // ld kmax
+    const real* UT;  // n_p x n_p
+    const real* UD;  // inverted diagonal blocks of R_pp (n_p x NB, ld n_p)
+    const real* QV;  // n_p x r explicit
+    const real* QT;  // ld kmax
     int ldqt;
     int pad;
 };
@@ -171,14 +181,16 @@ struct spaqr_factor_s {
     double eps = 0.0;
     std::vector<void*> allocs;     // device allocations owned by the factor
     int64_t bytes = 0;
-    double* d_scale = nullptr;     // column scaling D (n)
+    int precision = SPAQR_FP64;    // storage/arithmetic of the factor and its application
+    int esz = 8;                   // bytes per element of that type
+    double* d_scale = nullptr;     // column scaling D (n), FP64
     int64_t* d_perm = nullptr;     // new -> old
-    // solve plan
+    // solve plan (device arrays of SolveFront<real>, SolveRsj<real>, SolveSS<real>)
     std::vector<SolveLevelHost> lv;
-    spaqr::SolveFront* d_fronts = nullptr;
+    void* d_fronts = nullptr;
     spaqr::Seg* d_segs = nullptr;
-    spaqr::SolveRsj* d_rsj = nullptr;
-    spaqr::SolveSS* d_ss = nullptr;
+    void* d_rsj = nullptr;
+    void* d_ss = nullptr;
     int64_t ws_rows = 0;           // total rows of all level vectors
     // diagnostics
     std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
