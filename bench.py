@@ -196,6 +196,37 @@ def reference_arm(a):
     return 0
 
 
+def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, warmup):
+    """Time `steps` factor + GMRES steps of one form (after `warmup` untimed ones)
+    with CUDA events on `st`, L2 flushed between steps."""
+    rp, ci, va = A
+    fac, gm, tot, iters = [], [], [], []
+    X = None
+    with torch.cuda.stream(st):
+        for i in range(warmup + steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            em = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            F = sq.spaqr_factor(ordl, rp, ci, va, eps=eps, precision=precision, stream=st)
+            em.record(st)
+            Xd.zero_()
+            X, it, rr = sq.spaqr_gmres(F, rp, ci, va, Bd, X=Xd, tol=TOL, maxit=MAXIT, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            if i >= warmup:
+                fac.append(e0.elapsed_time(em))
+                gm.append(em.elapsed_time(e1))
+                tot.append(e0.elapsed_time(e1))
+                iters.append(int(it.max()))
+            del F
+    nrhs = Bd.shape[1]
+    return {"solves_per_s": nrhs * len(tot) / (sum(tot) / 1e3), "factor_ms_p50": _pct(fac, 50),
+            "gmres_ms_p50": _pct(gm, 50), "step_ms_p50": _pct(tot, 50), "gmres_iters_max": max(iters),
+            "relres_max": float(rr.max())}, X.clone()
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -351,6 +382,27 @@ def ours(a):
         "roofline": roof,
         "clocks": clk,
     }
+    # ---- mixed-precision form on the same workload: FP32 factor + FP64 GMRES ----
+    Xref = Xd.detach().cpu().numpy().copy()
+    mixed, X32 = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp32", 3, 1)
+    X32 = X32.cpu().numpy()
+    mixed["final_error_vs_fp64"] = float(np.max(np.linalg.norm(X32 - Xref, axis=0) / np.linalg.norm(Xref, axis=0)))
+    mixed["note"] = "same workload; FP32 factor and application, FP64 flexible GMRES to 1e-12"
+    line["mixed_fp32"] = mixed
+    # ---- 3D 32^3 workload (a ~ U[0.1,10], v = 20 (1,1,1), eps 1e-2, 16 RHS): FP64 vs FP32 factor ----
+    p3 = config_problem("3d_uniform_a", n=32)
+    b3 = rhs(p3, NRHS)
+    A3 = (torch.from_numpy(p3.rowptr).to(dev), torch.from_numpy(p3.colind).to(dev),
+          torch.from_numpy(p3.val).to(dev))
+    B3 = torch.from_numpy(np.ascontiguousarray(b3.T)).to(dev).T
+    X3 = torch.zeros(NRHS, p3.n, dtype=torch.float64, device=dev).T
+    o3 = sq.spaqr_order(p3.rowptr, p3.colind, p3.dims)
+    c64, x64 = _timed_form(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, "fp64", 2, 1)
+    c32, x32 = _timed_form(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, "fp32", 2, 1)
+    x64 = x64.cpu().numpy()
+    c32["final_error_vs_fp64"] = float(np.max(np.linalg.norm(x32.cpu().numpy() - x64, axis=0) /
+                                              np.linalg.norm(x64, axis=0)))
+    line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
     if not a.no_cpu_baseline:
         try:
             r = run_oracle(1)

@@ -17,6 +17,7 @@
 // column j stacked, rows ascending), column-major.  The arena of a level is
 // kept: it holds the front reflectors, R_ss, the R_sj rows and the scaled
 // diagonal blocks the solve needs.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,6 +70,8 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
 }
 
 constexpr int QC = 32;       // column chunk of the blocked updates
+constexpr int CPQR_CS = 8;   // CTAs per cluster of the large-interface CPQR
+constexpr int64_t kBigCPQR = 1 << 17;   // n_p x ncols from which an interface uses a cluster
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 
 template <class real>
@@ -230,6 +233,148 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
     cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G);
 }
 
+// Cluster form of k_cpqr for large interfaces: the CS CTAs of a thread-block
+// cluster share one M_p.  CTA q owns the columns [q cw, (q+1) cw); each step
+// combines the CTAs' pivot candidates through distributed shared memory, the
+// owner of column k swaps, forms the reflector and publishes it through
+// global memory, and every CTA reflects its own columns.  Per column the
+// arithmetic is that of k_cpqr, so ranks and reflectors are identical.
+template <class real, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+    k_cpqr_cluster(const CPQRTask<real>* __restrict__ tasks, const GatherSeg<real>* __restrict__ gsegs, double eps) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    double* red = sm;                                            // NWARP
+    long long* redv = reinterpret_cast<long long*>(sm + NWARP);  // NWARP
+    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
+    real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
+    real* vs = G + NB * NB;                                      // n_p
+    __shared__ double slot_v, slot_n;
+    __shared__ int slot_i;
+    const int q = (int)cl.block_rank();
+    const CPQRTask<real> t = tasks[blockIdx.x / CS];
+    const int m = t.np, c = t.ncols;
+    const int cw = (c + CS - 1) / CS;
+    const int j0 = q * cw, j1 = min(c, j0 + cw);
+    real* M = t.M;  // M(r, j) = M[r * c + j]
+    // gather, elements split over the cluster's CTAs
+    const int gt = q * NT + threadIdx.x, gstride = CS * NT;
+    for (int s = 0; s < t.nseg; s++) {
+        const GatherSeg<real> g = gsegs[t.seg_begin + s];
+        const int64_t tot = (int64_t)g.rows * g.cols;
+        if (g.transpose) {
+            for (int64_t o = gt; o < tot; o += gstride) {
+                const int cc = (int)(o % g.rows), r = (int)(o / g.rows);
+                M[(int64_t)r * c + g.col_off + cc] = g.src[cc + (int64_t)r * g.ld];
+            }
+        } else {
+            for (int64_t o = gt; o < tot; o += gstride) {
+                const int r = (int)(o % g.rows), cc = (int)(o / g.rows);
+                M[(int64_t)r * c + g.col_off + cc] = g.src[r + (int64_t)cc * g.ld];
+            }
+        }
+    }
+    cl.sync();
+    for (int j = j0 + threadIdx.x; j < j1; j += NT) {
+        real s = 0;
+        for (int r = 0; r < m; r++) {
+            const real x = M[(int64_t)r * c + j];
+            s += x * x;
+        }
+        t.norms[j] = s;
+    }
+    __syncthreads();
+    const int tmax = m < c ? m : c;
+    int rank = 0;
+    double R11 = 0.0;
+    for (int k = 0; k < tmax; k++) {
+        // pivot candidate of this CTA, then of the cluster
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int j = max(k, j0) + threadIdx.x; j < j1; j += NT) {
+            const double v = (double)t.norms[j];
+            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+        }
+        double lv;
+        int li;
+        block_argmax(bv, bi, redv, redi, lv, li);
+        // FP64 |R_kk|^2 of this CTA's candidate, published with it (computed
+        // before any CTA may swap columns)
+        double ln2 = lv;
+        if constexpr (sizeof(real) != 8) {
+            double part = 0.0;
+            if (li < c)
+                for (int r = k + threadIdx.x; r < m; r += NT) {
+                    const double x = (double)M[(int64_t)r * c + li];
+                    part += x * x;
+                }
+            ln2 = block_sum(part, red);
+        }
+        if (threadIdx.x == 0) { slot_v = lv; slot_i = li; slot_n = ln2; }
+        cl.sync();
+        double gv = -1.0, gn = 0.0;
+        int gi = 0x7fffffff;
+        for (int r = 0; r < CS; r++) {
+            const double v = *cl.map_shared_rank(&slot_v, r);
+            const int i = *cl.map_shared_rank(&slot_i, r);
+            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = *cl.map_shared_rank(&slot_n, r); }
+        }
+        if (gn < 0.0) gn = 0.0;
+        const double pn = sqrt(gn);
+        if (q == 0 && threadIdx.x == 0) t.rdiag[k] = pn;
+        if (k == 0) R11 = pn;
+        const bool stop = (R11 == 0.0) || (pn < eps * R11);
+        const int owner = k / cw;
+        if (!stop && q == owner && gi != k) {
+            for (int r = threadIdx.x; r < m; r += NT) {
+                real* row = M + (int64_t)r * c;
+                const real x = row[k];
+                row[k] = row[gi];
+                row[gi] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
+        }
+        // every CTA has read the slots and sees the swap before they change
+        cl.sync();
+        if (stop) break;
+        if (q == owner) {
+            const double tkd = cta_house(M + k, c, k, m, red);
+            if (threadIdx.x == 0) t.tau[k] = (real)tkd;
+        }
+        cl.sync();
+        const real tk = t.tau[k];
+        for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
+        __syncthreads();
+        for (int j = max(k + 1, j0) + threadIdx.x; j < j1; j += NT) {
+            real d = M[(int64_t)k * c + j];
+            for (int r = k + 1; r < m; r++) d += vs[r] * M[(int64_t)r * c + j];
+            const real f = tk * d;
+            M[(int64_t)k * c + j] -= f;
+            real nrm = 0;
+            for (int r = k + 1; r < m; r++) {
+                const real x = M[(int64_t)r * c + j] - f * vs[r];
+                M[(int64_t)r * c + j] = x;
+                nrm += x * x;
+            }
+            t.norms[j] = nrm;
+        }
+        __syncthreads();
+        rank = k + 1;
+    }
+    // explicit reflectors V (n_p x rank), split over the cluster
+    for (int64_t o = gt; o < (int64_t)m * rank; o += gstride) {
+        const int r = (int)(o % m), i = (int)(o / m);
+        t.V[r + (int64_t)i * m] = r < i ? (real)0 : (r == i ? (real)1 : M[(int64_t)r * c + i]);
+    }
+    cl.sync();
+    if (q == 0) {
+        if (threadIdx.x == 0) *t.rank = rank;
+        cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G);
+    }
+}
+
 // Coarse block [Q_i^T A Q_j](0:r_i, 0:r_j) into the merged block of the next
 // level; identity for diagonal blocks; plain copy when not sparsified.
 template <class real>
@@ -367,6 +512,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         C.cuda(cudaFuncSetAttribute(k_scale_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_qr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_cpqr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, CPQR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kSmemMax));
         if (C.rc != SPAQR_OK) return C.rc;
         attr_set = true;
     }
@@ -736,7 +883,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             std::vector<std::vector<std::pair<int, int>>> rowlist(ncl);   // row i -> (col j, entry)
             for (int j = 0; j < ncl; j++)
                 for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) rowlist[sp.rowidx[e]].push_back({j, e});
-            std::vector<CPQRTask<real>> cp;
+            std::vector<CPQRTask<real>> cp, cpb;
             std::vector<GatherSeg<real>> gs;
             std::vector<int> cp_of(ncl, -1);
             int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0;
@@ -811,15 +958,29 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 kmx = std::max(kmx, kmax[p]);
                 npmax = std::max(npmax, (int)sz[p]);
                 cp_of[p] = (int)cp.size();
-                cp.push_back(t);
+                // large interfaces go to the cluster kernel (CPQR_CS CTAs each)
+                if ((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= CPQR_CS * 64) cpb.push_back(t);
+                else cp.push_back(t);
+            }
+            const size_t smem_cp = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz;
+            GatherSeg<real>* dgs = nullptr;
+            if (!cp.empty() || !cpb.empty()) {
+                dgs = C.upload(gs, false);
+                if (C.rc) return C.rc;
+            }
+            if (!cpb.empty()) {
+                CPQRTask<real>* d1 = C.upload(cpb, false);
+                if (C.rc) return C.rc;
+                SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
+                             k_cpqr_cluster<real, CPQR_CS><<<(unsigned)(cpb.size() * CPQR_CS), NT, smem_cp, st>>>(
+                                 d1, dgs, opt->eps));
+                C.launched();
             }
             if (!cp.empty()) {
                 CPQRTask<real>* d1 = C.upload(cp, false);
-                GatherSeg<real>* d2 = C.upload(gs, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
-                             k_cpqr<real><<<(unsigned)cp.size(), NT, (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz,
-                                            st>>>(d1, d2, opt->eps));
+                             k_cpqr<real><<<(unsigned)cp.size(), NT, smem_cp, st>>>(d1, dgs, opt->eps));
                 C.launched();
             }
             // ranks back to the host (the only device->host sync of a level)

@@ -64,6 +64,8 @@ CASES = [
     ("3d_uniform_a", 10, 0, 0.0, 0),
     ("2d_uniform_a", 5, 4, 1e-1, 0),
     ("2d_uniform_a", 4, 0, 1e-2, 2),
+    ("3d_uniform_a", 16, 0, 1e-2, 2),    # large interfaces: cluster CPQR
+    ("2d_lognormal", 128, 0, 1e-4, 2),
 ]
 
 
