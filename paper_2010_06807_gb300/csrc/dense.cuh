@@ -330,6 +330,74 @@ __host__ __device__ constexpr int64_t qr_smem_bytes(int esz, int qc, int prow = 
     return 8 * NWARP + (int64_t)esz * (NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB);
 }
 
+// Factor the panel columns [p0, pe) of A (rows p0..m-1) in place, column by
+// column, and form its T block (T + p0 + p0 ldt).  With staged (m <= prow) the
+// panel is worked on in shared memory Ps and written back at the end.  Returns
+// the panel view (reflectors) for the trailing update: Vp with leading
+// dimension *ldv (shared memory when staged, otherwise A itself).
+template <class real>
+static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, int pe, real* tau, real* T, int ldt,
+                                           bool staged, double* red, real* P, real* Wk, real* G, real* Ps,
+                                           int64_t* ldv) {
+    // panel view: column k, row r -> Pb[r + (k - p0) * ldp]
+    real* Pb;
+    int64_t ldp;
+    if (staged) {
+        ldp = m - p0;
+        Pb = Ps - p0;
+        for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
+            const int rr = o % (m - p0), j = o / (m - p0);
+            Ps[rr + (int64_t)j * ldp] = A[(p0 + rr) + (int64_t)(p0 + j) * lda];
+        }
+        __syncthreads();
+    } else {
+        ldp = lda;
+        Pb = A + (int64_t)p0 * lda;
+    }
+    for (int k = p0; k < pe; k++) {
+        real* col = Pb + (int64_t)(k - p0) * ldp;
+        const double tkd = cta_house(col, 1, k, m, red);
+        const real tk = (real)tkd;
+        if (threadIdx.x == 0) tau[k] = tk;
+        const int ncol = pe - k - 1;
+        if (ncol > 0 && tkd != 0.0) {
+            // partial dots: NB column slots x (NT / NB) row groups
+            const int js = threadIdx.x % NB, g = threadIdx.x / NB;
+            real part = 0;
+            if (js < ncol) {
+                const real* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
+                for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
+            }
+            P[threadIdx.x] = part;
+            __syncthreads();
+            if (threadIdx.x < ncol) {
+                real s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
+                for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
+                Wk[threadIdx.x] = tk * s;
+            }
+            __syncthreads();
+            const int rows = m - k;
+            for (int o = threadIdx.x; o < rows * ncol; o += NT) {
+                const int rr = o % rows, jj = o / rows, r = k + rr;
+                const real v = rr == 0 ? (real)1 : col[r];
+                Pb[r + (int64_t)(k + 1 + jj - p0) * ldp] -= Wk[jj] * v;
+            }
+        }
+        __syncthreads();
+    }
+    if (staged) {
+        for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
+            const int rr = o % (m - p0), j = o / (m - p0);
+            A[(p0 + rr) + (int64_t)(p0 + j) * lda] = Ps[rr + (int64_t)j * ldp];
+        }
+    }
+    // T block of the panel (reflectors = panel rows p0.. of the panel view)
+    const real* Vp = Pb + p0;
+    cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G);
+    *ldv = ldp;
+    return Vp;
+}
+
 // In-place blocked Householder QR of A (m x n, lda).  tau gets min(m, n)
 // entries and T the diagonal NB blocks (ldt).  A panel of NB columns is
 // factored column by column (in shared memory when m <= prow), then applied
@@ -348,61 +416,8 @@ static __device__ void cta_qr(real* A, int64_t lda, int m, int n, real* tau, rea
     const bool staged = m <= prow;
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pe = (t - p0 < NB ? t : p0 + NB);   // panel columns [p0, pe)
-        // panel view: column k, row r -> Pb[r + (k - p0) * ldp]
-        real* Pb;
         int64_t ldp;
-        if (staged) {
-            ldp = m - p0;
-            Pb = Ps - p0;
-            for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
-                const int rr = o % (m - p0), j = o / (m - p0);
-                Ps[rr + (int64_t)j * ldp] = A[(p0 + rr) + (int64_t)(p0 + j) * lda];
-            }
-            __syncthreads();
-        } else {
-            ldp = lda;
-            Pb = A + (int64_t)p0 * lda;
-        }
-        for (int k = p0; k < pe; k++) {
-            real* col = Pb + (int64_t)(k - p0) * ldp;
-            const double tkd = cta_house(col, 1, k, m, red);
-            const real tk = (real)tkd;
-            if (threadIdx.x == 0) tau[k] = tk;
-            const int ncol = pe - k - 1;
-            if (ncol > 0 && tkd != 0.0) {
-                // partial dots: NB column slots x (NT / NB) row groups
-                const int js = threadIdx.x % NB, g = threadIdx.x / NB;
-                real part = 0;
-                if (js < ncol) {
-                    const real* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
-                    for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
-                }
-                P[threadIdx.x] = part;
-                __syncthreads();
-                if (threadIdx.x < ncol) {
-                    real s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
-                    for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
-                    Wk[threadIdx.x] = tk * s;
-                }
-                __syncthreads();
-                const int rows = m - k;
-                for (int o = threadIdx.x; o < rows * ncol; o += NT) {
-                    const int rr = o % rows, jj = o / rows, r = k + rr;
-                    const real v = rr == 0 ? (real)1 : col[r];
-                    Pb[r + (int64_t)(k + 1 + jj - p0) * ldp] -= Wk[jj] * v;
-                }
-            }
-            __syncthreads();
-        }
-        if (staged) {
-            for (int o = threadIdx.x; o < (m - p0) * (pe - p0); o += NT) {
-                const int rr = o % (m - p0), j = o / (m - p0);
-                A[(p0 + rr) + (int64_t)(p0 + j) * lda] = Ps[rr + (int64_t)j * ldp];
-            }
-        }
-        // T block of the panel (reflectors = panel rows p0.. of the panel view)
-        const real* Vp = Pb + p0;
-        cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G);
+        const real* Vp = cta_qr_panel(A, lda, m, p0, pe, tau, T, ldt, staged, red, P, Wk, G, Ps, &ldp);
         // trailing update of the columns right of the panel
         if (pe < n) {
             Mat<real> B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};

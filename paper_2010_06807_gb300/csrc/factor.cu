@@ -72,6 +72,8 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
 constexpr int QC = 32;       // column chunk of the blocked updates
 constexpr int CPQR_CS = 8;   // CTAs per cluster of the large-interface CPQR
 constexpr int64_t kBigCPQR = 1 << 17;   // n_p x ncols from which an interface uses a cluster
+constexpr int QR_CS = 8;     // CTAs per cluster of the large-front QR
+constexpr int64_t kBigQR = 1 << 16;     // m x n from which a front uses a cluster
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 
 template <class real>
@@ -81,6 +83,46 @@ __global__ void __launch_bounds__(NT) k_qr(const QRTask<real>* __restrict__ task
     const int tt = t.m < t.n ? t.m : t.n;
     cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, prow, sm);
     if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
+}
+
+// Cluster form of k_qr for large fronts: CTA 0 of the cluster factors each
+// panel of NB columns; after a cluster barrier the CS CTAs apply the panel to
+// their slices of the trailing columns (reflectors read from global memory).
+template <class real, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+    k_qr_cluster(const QRTask<real>* __restrict__ tasks, int prow) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    double* red = sm;
+    real* P = reinterpret_cast<real*>(red + NWARP);
+    real* Wk = P + NT;
+    real* G = Wk + NB;
+    real* W = G + NB * NB;
+    real* Ps = W + 2 * NB * QC + NT;
+    const int q = (int)cl.block_rank();
+    const QRTask<real> t = tasks[blockIdx.x / CS];
+    const int m = t.m, n = t.n, tt = m < n ? m : n;
+    const bool staged = m <= prow;
+    for (int p0 = 0; p0 < tt; p0 += NB) {
+        const int pe = (tt - p0 < NB ? tt : p0 + NB);
+        if (q == 0) {
+            int64_t ldp;
+            cta_qr_panel(t.A, t.lda, m, p0, pe, t.tau, t.T, tt, staged, red, P, Wk, G, Ps, &ldp);
+        }
+        cl.sync();
+        if (pe < n) {
+            const int w = (n - pe + CS - 1) / CS;
+            const int c0 = pe + q * w, c1 = min(n, c0 + w);
+            if (c1 > c0) {
+                Mat<real> B{t.A + p0 + (int64_t)c0 * t.lda, 1, t.lda, nullptr};
+                cta_apply_q_chunked(t.A + p0 + (int64_t)p0 * t.lda, t.lda, m - p0, pe - p0,
+                                    t.T + p0 + (int64_t)p0 * tt, tt, false, B, c1 - c0, QC, true, W);
+            }
+        }
+        cl.sync();
+    }
+    if (q == 0 && t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
 // smem layout: rmap (rmap_doubles doubles) then the work area of the apply
@@ -492,6 +534,45 @@ const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
 }  // namespace
 
+// Launch the QR tasks: small ones on one CTA each (k_qr), large ones on a
+// cluster of QR_CS CTAs (k_qr_cluster).
+template <class real>
+void launch_qr(Ctx& C, const std::vector<QRTask<real>>& all, size_t esz, int kind, double fl, double by) {
+    std::vector<QRTask<real>> small, big;
+    int pr_s = 0, pr_b = 0;
+    for (const QRTask<real>& q1 : all) {
+        const int tt = q1.m < q1.n ? q1.m : q1.n;
+        if ((int64_t)q1.m * q1.n >= kBigQR && tt >= 4 * NB) {
+            big.push_back(q1);
+            pr_b = std::max(pr_b, q1.m);
+        } else {
+            small.push_back(q1);
+            pr_s = std::max(pr_s, q1.m);
+        }
+    }
+    if (qr_smem_bytes((int)esz, QC, pr_s) > kPanelSmem) pr_s = 0;
+    if (qr_smem_bytes((int)esz, QC, pr_b) > kPanelSmem) pr_b = 0;
+    cudaStream_t st = C.st;
+    if (!big.empty()) {
+        QRTask<real>* d = C.upload(big, false);
+        if (C.rc) return;
+        SPAQR_LAUNCH(kind, fl, by, st,
+                     k_qr_cluster<real, QR_CS><<<(unsigned)(big.size() * QR_CS), NT,
+                                                 (size_t)qr_smem_bytes((int)esz, QC, pr_b), st>>>(d, pr_b));
+        C.launched();
+        fl = 0.0;
+        by = 0.0;
+    }
+    if (!small.empty()) {
+        QRTask<real>* d = C.upload(small, false);
+        if (C.rc) return;
+        SPAQR_LAUNCH(kind, fl, by, st,
+                     k_qr<real><<<(unsigned)small.size(), NT, (size_t)qr_smem_bytes((int)esz, QC, pr_s), st>>>(d,
+                                                                                                            pr_s));
+        C.launched();
+    }
+}
+
 template <class real>
 int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spaqr_factor_s* F) {
     Ctx C;
@@ -511,6 +592,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         C.cuda(cudaFuncSetAttribute(k_front_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_scale_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_qr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_qr_cluster<real, QR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_cpqr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, CPQR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kSmemMax));
@@ -714,13 +796,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
         tstart();
         if (!qr.empty()) {
-            QRTask<real>* d = C.upload(qr, false);
+            launch_qr<real>(C, qr, esz, KK_FRONT_QR, fl_qr, by_qr);
             if (C.rc) return C.rc;
-            int prow = 0;
-            for (const QRTask<real>& q1 : qr) prow = std::max(prow, q1.m);
-            if (qr_smem_bytes((int)esz, QC, prow) > kPanelSmem) prow = 0;
-            SPAQR_LAUNCH(KK_FRONT_QR, fl_qr, by_qr, st,
-                         k_qr<real><<<(unsigned)qr.size(), NT, (size_t)qr_smem_bytes((int)esz, QC, prow), st>>>(d, prow));
             C.launched();
         }
         if (!at.empty()) {
@@ -860,14 +937,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             tstart();
             if (!sq.empty()) {
-                QRTask<real>* d = C.upload(sq, false);
+                launch_qr<real>(C, sq, esz, KK_SCALE_QR, fl_sq, by_sq);
                 if (C.rc) return C.rc;
-                int prow = 0;
-                for (const QRTask<real>& q1 : sq) prow = std::max(prow, q1.m);
-                if (qr_smem_bytes((int)esz, QC, prow) > kPanelSmem) prow = 0;
-                SPAQR_LAUNCH(KK_SCALE_QR, fl_sq, by_sq, st,
-                             k_qr<real><<<(unsigned)sq.size(), NT, (size_t)qr_smem_bytes((int)esz, QC, prow), st>>>(d,
-                                                                                                                 prow));
                 C.launched();
             }
             if (!sc.empty()) {
