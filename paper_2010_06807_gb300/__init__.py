@@ -283,11 +283,15 @@ class Factor:
         self._h = ctypes.c_void_p(handle)
         self.n = n
 
-    def __del__(self):
+    def close(self):
+        """Free the factor's device memory now (waits for the device)."""
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib is not None:
             _lib.spaqr_factor_destroy(h)
-            self._h = None
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 SPAQR_FP64 = 0
