@@ -36,6 +36,23 @@ constexpr int NT = 256;          // threads per CTA of every kernel
 constexpr int NWARP = NT / 32;
 constexpr int NB = 16;           // reflectors per panel
 
+// Asynchronous element copies global -> shared (cp.async, 4 or 8 bytes):
+// a thread issues many without waiting, so a staged block has all its loads
+// in flight at once.  cp_async_wait<N> waits until at most N of this thread's
+// committed groups are pending; a __syncthreads must follow before other
+// threads read the data.
+template <class real>
+__device__ __forceinline__ void cp_async_elem(real* dst, const real* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(real) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

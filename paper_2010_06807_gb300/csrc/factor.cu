@@ -660,6 +660,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     std::vector<Seg> ssegs;
     std::vector<SolveRsj<real>> srsj;
     std::vector<SolveSS<real>> sss;
+    std::vector<RsjTile> tiles;
+    std::vector<SolveRsj<real>> pieces;
+    std::vector<WideFront> wfr;
+    int64_t zp_max = 0;
     F->lv.assign(L, SolveLevelHost());
     int64_t ws = 0;
     double flops = 0.0, sflops = 0.0;
@@ -869,6 +873,60 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
             LV.nfront = (int)sfronts.size() - LV.front_begin;
+        }
+        // wide solve forms where a colour (forward) or the level (backward)
+        // has too few fronts to fill the GPU with one CTA per front
+        LV.ff_wide.assign(LV.colour_ptr.size() - 1, 0);
+        LV.ff_maxm.assign(LV.colour_ptr.size() - 1, 0);
+        for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
+            const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
+            int mm = 0;
+            for (int f = a; f < b; f++) mm = std::max(mm, sfronts[LV.front_begin + f].m);
+            LV.ff_maxm[c] = mm;
+            LV.ff_wide[c] = (b > a && b - a <= kWideFronts && mm >= kWideMinM) ? 1 : 0;
+        }
+        LV.bwd_wide = LV.nfront > 0 && LV.nfront <= kWideFronts && LV.max_front_n >= kWideMinN;
+        if (LV.bwd_wide) {
+            LV.tile_begin = (int)tiles.size();
+            LV.wf_begin = (int)wfr.size();
+            int64_t zrows = 0;
+            for (int f = LV.front_begin; f < LV.front_begin + LV.nfront; f++) {
+                const SolveFront<real>& sf = sfronts[f];
+                // pieces of R_sj columns filling chunks of kTileK columns
+                std::vector<std::pair<int, int>> chunks;
+                int cw = 0, cb = (int)pieces.size(), cn = 0;
+                for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) {
+                    const SolveRsj<real> R = srsj[b];
+                    for (int u0 = 0; u0 < R.nj;) {
+                        const int w = std::min(R.nj - u0, kTileK - cw);
+                        pieces.push_back(SolveRsj<real>{R.R + (int64_t)u0 * R.ldr, R.ldr, w, 0, R.xoff + u0});
+                        cn++;
+                        cw += w;
+                        u0 += w;
+                        if (cw == kTileK) {
+                            chunks.push_back({cb, cn});
+                            cb = (int)pieces.size();
+                            cn = 0;
+                            cw = 0;
+                        }
+                    }
+                }
+                if (cn > 0) chunks.push_back({cb, cn});
+                const int nkc = (int)chunks.size();
+                for (int kc = 0; kc < nkc; kc++)
+                    for (int r0 = 0; r0 < sf.n; r0 += kTileRows)
+                        tiles.push_back(RsjTile{f, r0, std::min(kTileRows, sf.n - r0), chunks[kc].first,
+                                                chunks[kc].second, kc, zrows});
+                wfr.push_back(WideFront{f, nkc, zrows});
+                zrows += (int64_t)nkc * sf.n;
+                double snj = 0;
+                for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) snj += srsj[b].nj;
+                LV.rt_flops += 2.0 * sf.n * snj;
+                LV.rt_fixed += 8.0 * sf.n * snj;
+                LV.rt_vec += 8.0 * snj * ((sf.n + kTileRows - 1) / kTileRows) + 8.0 * nkc * sf.n;
+            }
+            LV.ntile = (int)tiles.size() - LV.tile_begin;
+            zp_max = std::max(zp_max, zrows);
         }
 
         // ---------------- (ii)/(iii) scale and sparsify ----------------
@@ -1202,6 +1260,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->d_segs = C.upload(ssegs, true);
     F->d_rsj = C.upload(srsj, true);
     F->d_ss = C.upload(sss, true);
+    F->d_tiles = C.upload(tiles, true);
+    F->d_pieces = C.upload(pieces, true);
+    F->d_wfronts = C.upload(wfr, true);
+    F->zp_off = ws;
+    F->zp_rows = zp_max;
+    ws += zp_max;
     F->ws_rows = ws;
     F->flops = flops;
     F->solve_flops = sflops;

@@ -11,6 +11,7 @@
 //            then x_s <- R_ss^{-1} (z_s - sum_j R_sj x_j) for every front.
 // Each level has its own vector (rows = sizes of its clusters), all in one
 // workspace, column-major with one column per right-hand side.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dense.cuh"
@@ -180,6 +182,339 @@ __global__ void __launch_bounds__(NT) k_sfront_bwd(const SolveFront<real>* __res
     __syncthreads();
     cta_trsv_upper(F.V, F.ldv, n, F.Dinv, Mat<real>{xs, 1, ldy, nullptr}, qn, tmp);
     (void)singular;
+}
+
+// ---------------------------------------------------------------------------
+// Wide forms for colours / levels with few fronts: a thread-block cluster of
+// CS CTAs shares one front (and one chunk of right-hand sides), every CTA
+// owning a slab of the front's rows (a multiple of NB rows).
+// ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int wide_slab_rows(int m, int cs) {
+    const int slab = (m + cs - 1) / cs;
+    return (slab + NB - 1) / NB * NB;
+}
+
+template <class real>
+__device__ __forceinline__ real warp_sum_r(real v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Shared memory (bytes) of k_sfront_fwd_wide for slabs of `slab` rows.
+__host__ __forceinline__ size_t fwd_wide_smem(int slab, int qs, int esz) {
+    const int64_t ld = slab | 1;
+    return (size_t)((slab + 1) / 2) * 8 + (size_t)(4 * NB * qs + 2 * NB * NB + 2 * ld * NB + ld * qs) * esz;
+}
+
+// Shared memory (bytes) of k_sfront_bwd_wide.
+__host__ __forceinline__ size_t bwd_wide_smem(int slab, int qs, int esz) {
+    const int64_t ld = slab | 1;
+    return (size_t)(3 * NB * qs + 2 * NB * NB + 2 * ld * NB + ld * qs) * esz;
+}
+
+// y_R(s) <- Q_s^T y_R(s) (the forward front step) with the front's rows split
+// over the cluster.  Per panel of NB reflectors every CTA forms the partial
+// products V_b^T y over its rows, the cluster adds them in rank order through
+// distributed shared memory (double-buffered, one barrier per panel), and
+// every CTA applies y <- y - V_b (T_b^T W) to its own rows.  The panel's V
+// rows and T block are staged with cp.async one panel ahead.
+template <class real, int CS, int Q>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+    k_sfront_fwd_wide(const SolveFront<real>* __restrict__ fr, const Seg* __restrict__ segs, real* Y, int64_t ldy,
+                      int nrhs, int qs, int slab_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    const int ld = slab_cap | 1;
+    int* rmap = reinterpret_cast<int*>(sm);
+    real* part = reinterpret_cast<real*>(sm + (slab_cap + 1) / 2);
+    real* W1 = part + 2 * NB * qs;
+    real* W2 = W1 + NB * qs;
+    real* Ts = W2 + NB * qs;            // 2 x NB x NB
+    real* Vs = Ts + 2 * NB * NB;        // 2 x ld x NB
+    real* Bs = Vs + 2 * (int64_t)ld * NB;
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;   // uniform over the cluster (same blockIdx.y)
+    const int rank = (int)cl.block_rank();
+    const SolveFront<real> F = fr[blockIdx.x / CS];
+    const int slab = wide_slab_rows(F.m, CS);
+    const int lo = min(F.m, rank * slab), hi = min(F.m, lo + slab);
+    const int rows = hi - lo;
+    int pos = 0;
+    for (int s = 0; s < F.nseg; s++) {
+        const Seg g = segs[F.seg_begin + s];
+        const int a = max(pos, lo), b = min(pos + g.len, hi);
+        for (int r = a + threadIdx.x; r < b; r += NT) rmap[r - lo] = (int)(g.off + (r - pos));
+        pos += g.len;
+    }
+    __syncthreads();
+    real* Yc = Y + (int64_t)c0 * ldy;
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        cp_async_elem(Bs + r + (int64_t)c * ld, Yc + rmap[r] + (int64_t)c * ldy);
+    }
+    const int nbk = (F.n + NB - 1) / NB;
+    // stage panel b: V rows r >= max(lo, p0) (unit diagonal, zeros above) and T_b
+    auto stage = [&](int b) {
+        const int p0 = b * NB, pb = min(NB, F.n - p0);
+        real* vs = Vs + (int64_t)(b & 1) * ld * NB;
+        real* ts = Ts + (b & 1) * NB * NB;
+        const int r0 = max(lo, p0), nr = hi - r0;
+        for (int o = threadIdx.x; o < nr * pb; o += NT) {
+            const int rr = o % nr, i = o / nr;
+            const int r = r0 + rr, col = p0 + i;
+            real* d = vs + (r - lo) + (int64_t)i * ld;
+            if (r > col) cp_async_elem(d, F.V + r + (int64_t)col * F.ldv);
+            else *d = r == col ? (real)1 : (real)0;
+        }
+        for (int o = threadIdx.x; o < pb * pb; o += NT)
+            cp_async_elem(ts + o, F.T + (p0 + o % pb) + (int64_t)(p0 + o / pb) * F.n);
+    };
+    stage(0);
+    cp_async_commit();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int b = 0; b < nbk; b++) {
+        const int p0 = b * NB;
+        const int pb = min(NB, F.n - p0);
+        if (b + 1 < nbk) stage(b + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const real* vs = Vs + (int64_t)(b & 1) * ld * NB;
+        real* myp = part + (b & 1) * NB * qs;
+        const int r0 = max(lo, p0);
+        // partial W(i, c) over own rows
+        for (int i = warp; i < pb; i += NWARP) {
+            real acc[Q];
+#pragma unroll
+            for (int c = 0; c < Q; c++) acc[c] = 0;
+            for (int r = max(r0, p0 + i) + lane; r < hi; r += 32) {
+                const real vr = vs[(r - lo) + i * ld];
+                const real* br = Bs + (r - lo);
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) acc[c] += vr * br[c * ld];
+            }
+#pragma unroll
+            for (int c = 0; c < Q; c++) {
+                if (c < qn) {
+                    const real t = warp_sum_r(acc[c]);
+                    if (lane == 0) myp[i + c * pb] = t;
+                }
+            }
+        }
+        cl.sync();
+        for (int o = threadIdx.x; o < pb * qn; o += NT) {
+            real t = 0;
+            for (int k = 0; k < CS; k++) t += cl.map_shared_rank(myp, k)[o];
+            W1[o] = t;
+        }
+        __syncthreads();
+        cta_tblock_mul(Ts + (b & 1) * NB * NB, pb, 0, pb, qn, true, W1, W2);
+        for (int r = r0 + (int)threadIdx.x; r < hi; r += NT) {
+            real acc[Q];
+#pragma unroll
+            for (int c = 0; c < Q; c++) acc[c] = 0;
+            const real* vr = vs + (r - lo);
+            for (int i = 0; i < pb; i++) {
+                const real v = vr[i * ld];
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) acc[c] += v * W2[i + c * pb];
+            }
+            real* br = Bs + (r - lo);
+#pragma unroll
+            for (int c = 0; c < Q; c++)
+                if (c < qn) br[c * ld] -= acc[c];
+        }
+        __syncthreads();
+    }
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        Yc[rmap[r] + (int64_t)c * ldy] = Bs[r + c * ld];
+    }
+    cl.sync();   // no CTA leaves while another may still read its partials
+}
+
+// Partial products R_sj x_j of the backward front step: one CTA per tile
+// (front, kTileRows rows, one K chunk of at most kTileK columns) and chunk of
+// right-hand sides; four thread groups split the chunk's columns and are
+// added in group order.  Each thread keeps eight loads of R in flight.
+// Partials go to Zp rows zoff + kc * n_s + r.
+template <class real, int Q>
+__global__ void __launch_bounds__(NT) k_rsj_tiles(const RsjTile* __restrict__ tiles,
+                                                  const SolveRsj<real>* __restrict__ pieces,
+                                                  const SolveFront<real>* __restrict__ fr, const real* __restrict__ Y,
+                                                  int64_t ldy, real* __restrict__ Zp, int64_t ldz, int nrhs, int qs) {
+    __shared__ real xs[kTileK * kTileQ];
+    constexpr int G = NT / kTileRows;
+    constexpr int U = 8;
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
+    const RsjTile t = tiles[blockIdx.x];
+    const int n = fr[t.front].n;
+    int koff = 0;
+    for (int p = 0; p < t.npiece; p++) {
+        const SolveRsj<real> P = pieces[t.piece_begin + p];
+        for (int o = threadIdx.x; o < P.nj * qn; o += NT) {
+            const int u = o % P.nj, c = o / P.nj;
+            cp_async_elem(xs + koff + u + c * kTileK, Y + P.xoff + u + (int64_t)(c0 + c) * ldy);
+        }
+        koff += P.nj;
+    }
+    cp_async_commit();
+    const int r = threadIdx.x % kTileRows, g = threadIdx.x / kTileRows;
+    real acc[Q];
+#pragma unroll
+    for (int c = 0; c < Q; c++) acc[c] = 0;
+    cp_async_wait<0>();
+    __syncthreads();
+    if (r < t.nrows) {
+        koff = 0;
+        for (int p = 0; p < t.npiece; p++) {
+            const SolveRsj<real> P = pieces[t.piece_begin + p];
+            const real* Rr = P.R + (t.row0 + r);
+            int u = g;
+            for (; u + (U - 1) * G < P.nj; u += U * G) {
+                real v[U];
+#pragma unroll
+                for (int k = 0; k < U; k++) v[k] = Rr[(int64_t)(u + k * G) * P.ldr];
+#pragma unroll
+                for (int k = 0; k < U; k++) {
+                    const real* xu = xs + koff + u + k * G;
+#pragma unroll
+                    for (int c = 0; c < Q; c++)
+                        if (c < qn) acc[c] += v[k] * xu[c * kTileK];
+                }
+            }
+            for (; u < P.nj; u += G) {
+                const real v = Rr[(int64_t)u * P.ldr];
+                const real* xu = xs + koff + u;
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) acc[c] += v * xu[c * kTileK];
+            }
+            koff += P.nj;
+        }
+    }
+    __syncthreads();
+    real* red = xs;   // (c * G + g) * kTileRows + r
+#pragma unroll
+    for (int c = 0; c < Q; c++)
+        if (c < qn) red[(c * G + g) * kTileRows + r] = acc[c];
+    __syncthreads();
+    for (int o = threadIdx.x; o < t.nrows * qn; o += NT) {
+        const int rr = o % t.nrows, c = o / t.nrows;
+        real s = 0;
+#pragma unroll
+        for (int k = 0; k < G; k++) s += red[(c * G + k) * kTileRows + rr];
+        Zp[t.zoff + (int64_t)t.kc * n + t.row0 + rr + (int64_t)(c0 + c) * ldz] = s;
+    }
+}
+
+// x_s <- R_ss^{-1} (y_s - sum of the R_sj partials) with the rows of x_s split
+// over the cluster.  Block back substitution from the bottom: the CTA owning
+// block b forms x_b = Dinv_b z_b and publishes it in distributed shared memory
+// (double-buffered, one barrier per block); every CTA with rows above b then
+// updates them with R(rows, b) x_b.  R(rows, b) and Dinv_b are staged with
+// cp.async one block ahead.
+template <class real, int CS, int Q>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+    k_sfront_bwd_wide(const WideFront* __restrict__ wf, const SolveFront<real>* __restrict__ fr,
+                      const Seg* __restrict__ segs, real* Y, int64_t ldy, const real* __restrict__ Zp, int64_t ldz,
+                      int nrhs, int qs, int slab_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double smb[];
+    const int ld = slab_cap | 1;
+    real* xb = reinterpret_cast<real*>(smb);   // 2 x NB x qs (read by the cluster)
+    real* xl = xb + 2 * NB * qs;
+    real* Ds = xl + NB * qs;                    // 2 x NB x NB
+    real* Rs = Ds + 2 * NB * NB;                // 2 x ld x NB
+    real* Zs = Rs + 2 * (int64_t)ld * NB;
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;   // uniform over the cluster
+    const int rank = (int)cl.block_rank();
+    const WideFront W = wf[blockIdx.x / CS];
+    const SolveFront<real> F = fr[W.front];
+    const int n = F.n;
+    const int slab = wide_slab_rows(n, CS);
+    const int lo = min(n, rank * slab), hi = min(n, lo + slab);
+    const int rows = hi - lo;
+    real* xs = Y + segs[F.seg_begin].off + (int64_t)c0 * ldy;
+    const int nbk = (n + NB - 1) / NB;
+    auto stage = [&](int b) {
+        const int b0 = b * NB, bs = min(NB, n - b0);
+        real* rs = Rs + (int64_t)(b & 1) * ld * NB;
+        const int nr = min(hi, b0) - lo;
+        for (int o = threadIdx.x; o < nr * bs; o += NT) {
+            const int rr = o % nr, u = o / nr;
+            cp_async_elem(rs + rr + (int64_t)u * ld, F.V + (lo + rr) + (int64_t)(b0 + u) * F.ldv);
+        }
+        if (b0 >= lo && b0 < hi) {
+            real* ds = Ds + (b & 1) * NB * NB;
+            for (int o = threadIdx.x; o < bs * bs; o += NT)
+                cp_async_elem(ds + o, F.Dinv + (b0 + o % bs) + (int64_t)(o / bs) * n);
+        }
+    };
+    stage(nbk - 1);
+    cp_async_commit();
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        const real* zp = Zp + W.zoff + lo + r + (int64_t)(c0 + c) * ldz;
+        real t = 0;
+        for (int kc = 0; kc < W.nkc; kc++) t += zp[(int64_t)kc * n];
+        Zs[r + c * ld] = xs[lo + r + (int64_t)c * ldy] - t;
+    }
+    for (int b = nbk - 1; b >= 0; b--) {
+        const int b0 = b * NB, bs = min(NB, n - b0);
+        if (b > 0) stage(b - 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        real* buf = xb + (b & 1) * NB * qs;
+        if (b0 >= lo && b0 < hi) {
+            const real* ds = Ds + (b & 1) * NB * NB;
+            for (int o = threadIdx.x; o < bs * qn; o += NT) {
+                const int i = o % bs, c = o / bs;
+                real t = 0;
+                for (int u = i; u < bs; u++) t += ds[i + u * bs] * Zs[(b0 - lo + u) + c * ld];
+                buf[i + c * bs] = t;
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < bs * qn; o += NT) Zs[(b0 - lo + o % bs) + (o / bs) * ld] = buf[o];
+        }
+        cl.sync();
+        if (lo < b0) {
+            const real* ob = cl.map_shared_rank(buf, b0 / slab);
+            for (int o = threadIdx.x; o < bs * qn; o += NT) xl[o] = ob[o];
+            __syncthreads();
+            const real* rs = Rs + (int64_t)(b & 1) * ld * NB;
+            const int top = min(hi, b0);
+            for (int r = lo + (int)threadIdx.x; r < top; r += NT) {
+                real acc[Q];
+#pragma unroll
+                for (int c = 0; c < Q; c++) acc[c] = 0;
+                for (int u = 0; u < bs; u++) {
+                    const real v = rs[(r - lo) + u * ld];
+#pragma unroll
+                    for (int c = 0; c < Q; c++)
+                        if (c < qn) acc[c] += v * xl[u + c * bs];
+                }
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) Zs[(r - lo) + c * ld] -= acc[c];
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        xs[lo + r + (int64_t)c * ldy] = Zs[r + c * ld];
+    }
+    cl.sync();   // no CTA leaves while another may still read its x_b
 }
 
 // ---------------------------------------------------------------------------
@@ -395,14 +730,32 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Calls f(std::integral_constant<int, Q>) with Q the smallest of 1, 2, 4, 8,
+// 16 that is >= q: the wide kernels unroll their column loops to Q.
+template <class Fn>
+static void with_q(int q, Fn f) {
+    if (q <= 1) f(std::integral_constant<int, 1>());
+    else if (q <= 2) f(std::integral_constant<int, 2>());
+    else if (q <= 4) f(std::integral_constant<int, 4>());
+    else if (q <= 8) f(std::integral_constant<int, 8>());
+    else f(std::integral_constant<int, 16>());
+}
+
 template <class real>
 void set_solve_attrs() {
-    static bool done = false;
-    if (done) return;
+    static std::once_flag once;
+    std::call_once(once, [] {
     cudaFuncSetAttribute(k_sfront_fwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
     cudaFuncSetAttribute(k_sss_fwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
     cudaFuncSetAttribute(k_sss_bwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    done = true;
+    for (int q : {1, 2, 4, 8, 16})
+        with_q(q, [](auto QC) {
+            cudaFuncSetAttribute(k_sfront_fwd_wide<real, kWideCS, QC.value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+            cudaFuncSetAttribute(k_sfront_bwd_wide<real, kWideCS, QC.value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+        });
+    });
 }
 
 }  // namespace
@@ -416,6 +769,24 @@ static int rhs_split(int blocks, int nrhs) {
     split = std::max(1, std::min(split, nrhs));
     split = std::max(split, (nrhs + 15) / 16);   // at most 16 columns per CTA
     return split;
+}
+
+constexpr int kNumSM = 152;
+
+
+// Right-hand-side chunks of a wide launch over `units` clusters: about two
+// CTAs per SM, at most kTileQ columns per chunk, and the chunk's shared
+// memory (smem(q) bytes) within the limit.  False if one column does not fit.
+template <class Smem>
+static bool wide_split(int units, int nrhs, Smem smem, int& qs, int& split) {
+    int qmax = kTileQ;
+    while (qmax > 0 && smem(qmax) > (size_t)kSmemMax) qmax--;
+    if (qmax == 0) return false;
+    split = std::max((nrhs + qmax - 1) / qmax,
+                     std::min(nrhs, (2 * kNumSM + units * kWideCS - 1) / (units * kWideCS)));
+    qs = (nrhs + split - 1) / split;
+    split = (nrhs + qs - 1) / qs;
+    return true;
 }
 
 template <class real>
@@ -441,6 +812,20 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
             for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
                 const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
                 if (b <= a) continue;
+                if (LV.ff_wide[c]) {
+                    const int slab = wide_slab_rows(LV.ff_maxm[c], kWideCS);
+                    int qs, split;
+                    if (wide_split(b - a, nrhs, [&](int q) { return fwd_wide_smem(slab, q, (int)esz); }, qs, split)) {
+                        SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs,
+                                     LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
+                                     with_q(qs, [&](auto QC) {
+                                         k_sfront_fwd_wide<real, kWideCS, QC.value>
+                                             <<<dim3((b - a) * kWideCS, split), NT, fwd_wide_smem(slab, qs, (int)esz),
+                                                st>>>(dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
+                                     }));
+                        continue;
+                    }
+                }
                 const int split = rhs_split(b - a, nrhs);
                 const int qs = (nrhs + split - 1) / split;
                 const int staged = rmap_d * 8 + staged_smem_elems(LV.max_front_m, qs) * esz <= kSmemMax;
@@ -479,6 +864,36 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
                          k_sss_bwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(dss + LV.ss_begin, Y, ldy,
                                                                           ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
                                                                           staged, singular));
+        }
+        if (LV.nfront > 0 && LV.bwd_wide) {
+            const int slab = wide_slab_rows(LV.max_front_n, kWideCS);
+            int qs, split;
+            if (wide_split(LV.nfront, nrhs, [&](int q) { return bwd_wide_smem(slab, q, (int)esz); }, qs, split)) {
+                real* Zp = ws + F->zp_off * nrhs;
+                const int64_t ldz = F->zp_rows;
+                if (LV.ntile > 0) {
+                    int tsplit = std::max((nrhs + kTileQ - 1) / kTileQ,
+                                          std::min(nrhs, (2 * kNumSM + LV.ntile - 1) / LV.ntile));
+                    const int tq = (nrhs + tsplit - 1) / tsplit;
+                    tsplit = (nrhs + tq - 1) / tq;
+                    SPAQR_LAUNCH(KK_SOLVE_RSJ, LV.rt_flops * nrhs, LV.rt_fixed * tsplit + LV.rt_vec * nrhs, st,
+                                 with_q(tq, [&](auto QC) {
+                                     k_rsj_tiles<real, QC.value><<<dim3(LV.ntile, tsplit), NT, 0, st>>>(
+                                         static_cast<const RsjTile*>(F->d_tiles) + LV.tile_begin,
+                                         static_cast<const SolveRsj<real>*>(F->d_pieces), dfr, Y, ldy, Zp, ldz, nrhs,
+                                         tq);
+                                 }));
+                }
+                SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, (LV.fb_flops - LV.rt_flops) * nrhs,
+                             (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st,
+                             with_q(qs, [&](auto QC) {
+                                 k_sfront_bwd_wide<real, kWideCS, QC.value>
+                                     <<<dim3(LV.nfront * kWideCS, split), NT, bwd_wide_smem(slab, qs, (int)esz), st>>>(
+                                         static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, dfr, F->d_segs, Y,
+                                         ldy, Zp, ldz, nrhs, qs, slab);
+                             }));
+                continue;
+            }
         }
         if (LV.nfront > 0) {
             const int split = rhs_split(LV.nfront, nrhs);

@@ -136,6 +136,34 @@ struct SolveRsj {
     int64_t xoff;      // rows of j in the level vector
 };
 
+// Launch shapes of the wide solve forms.
+constexpr int kWideCS = 8;        // CTAs per thread-block cluster
+constexpr int kWideFronts = 64;   // a colour / level with at most this many fronts runs wide
+constexpr int kWideMinM = 128;    // ... if its largest front has at least this many rows (forward)
+constexpr int kWideMinN = 32;     // ... or columns (backward)
+constexpr int kTileRows = 64;     // rows of an R_sj tile
+constexpr int kTileK = 256;       // columns of an R_sj tile chunk
+constexpr int kTileQ = 16;        // right-hand sides per R_sj tile
+
+// Wide form of the backward front step, for levels with few fronts: the
+// products R_sj x_j run as tiles over (front, row block, K chunk) and write
+// partial sums, which the cluster back substitution adds in chunk order.
+// A piece is a column range of one R_sj block (a SolveRsj with R and xoff
+// advanced to the range).
+struct RsjTile {
+    int front;          // index into the device SolveFront array
+    int row0, nrows;    // rows of R_s* (within the front's n_s)
+    int piece_begin, npiece;
+    int kc;             // chunk index within the front
+    int64_t zoff;       // the front's partials: rows zoff + kc * n_s + r
+};
+
+struct WideFront {
+    int front;          // index into the device SolveFront array
+    int nkc;            // K chunks (0: no R_sj blocks)
+    int64_t zoff;
+};
+
 // Scaling + sparsification (or plain carry-over) of one cluster that survives
 // a level.
 template <class real>
@@ -172,6 +200,13 @@ struct SolveLevelHost {
     double ssf_flops = 0, ssf_fixed = 0, ssf_vec = 0; // forward scale/sparsify
     double ssb_flops = 0, ssb_fixed = 0, ssb_vec = 0; // backward scale/sparsify
     double fb_flops = 0, fb_fixed = 0, fb_vec = 0;    // backward fronts
+    // wide forms (few fronts): forward colours flagged in ff_wide run one
+    // thread-block cluster per front; a wide backward level runs the R_sj
+    // tiles, then one cluster per front.
+    std::vector<int> ff_wide, ff_maxm;
+    bool bwd_wide = false;
+    int tile_begin = 0, ntile = 0, wf_begin = 0;
+    double rt_flops = 0, rt_fixed = 0, rt_vec = 0;     // R_sj tiles
 };
 
 struct spaqr_factor_s {
@@ -191,7 +226,11 @@ struct spaqr_factor_s {
     spaqr::Seg* d_segs = nullptr;
     void* d_rsj = nullptr;
     void* d_ss = nullptr;
-    int64_t ws_rows = 0;           // total rows of all level vectors
+    int64_t ws_rows = 0;           // total rows of all level vectors + the R_sj partials
+    int64_t zp_off = 0, zp_rows = 0;   // R_sj partial sums of a wide level (rows per RHS)
+    void* d_tiles = nullptr;       // RsjTile[]
+    void* d_pieces = nullptr;      // SolveRsj<real>[] of the tiles
+    void* d_wfronts = nullptr;     // WideFront[]
     // diagnostics
     std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
     std::vector<std::vector<std::pair<double, double>>> margins;
