@@ -202,39 +202,202 @@ __device__ __forceinline__ real warp_sum_r(real v) {
     return v;
 }
 
-// Shared memory (bytes) of k_sfront_fwd_wide for slabs of `slab` rows.
-__host__ __forceinline__ size_t fwd_wide_smem(int slab, int qs, int esz) {
+// Shared memory (bytes) of every wide kernel for slabs of `slab` rows:
+// [row map | P NT | part 2 NB qs | W1 NB qs | W2 NB qs | Ts 2 NB^2 | Vs 2 ld NB | Bs ld qs]
+__host__ __forceinline__ size_t wide_smem(int slab, int qs, int esz) {
     const int64_t ld = slab | 1;
-    return (size_t)((slab + 1) / 2) * 8 + (size_t)(4 * NB * qs + 2 * NB * NB + 2 * ld * NB + ld * qs) * esz;
+    return (size_t)((slab + 1) / 2) * 8 + (size_t)(NT + 4 * NB * qs + 2 * NB * NB + 2 * ld * NB + ld * qs) * esz;
 }
 
-// Shared memory (bytes) of k_sfront_bwd_wide.
-__host__ __forceinline__ size_t bwd_wide_smem(int slab, int qs, int esz) {
-    const int64_t ld = slab | 1;
-    return (size_t)(3 * NB * qs + 2 * NB * NB + 2 * ld * NB + ld * qs) * esz;
+// Work areas of a wide kernel.  part (and, in the back substitution, the
+// solved block) is read by the other CTAs of the cluster; it is indexed by
+// the parity of a phase counter that runs over all cluster barriers of the
+// kernel, so that a buffer is rewritten only two barriers after it was read.
+template <class real>
+struct WideSmem {
+    int* rmap;
+    real *P, *part, *W1, *W2, *Ts, *Vs, *Bs;
+    int ld;
+};
+
+template <class real>
+__device__ __forceinline__ WideSmem<real> wide_smem_layout(double* sm, int slab_cap, int qs) {
+    WideSmem<real> w;
+    w.ld = slab_cap | 1;
+    w.rmap = reinterpret_cast<int*>(sm);
+    w.P = reinterpret_cast<real*>(sm + (slab_cap + 1) / 2);
+    w.part = w.P + NT;
+    w.W1 = w.part + 2 * NB * qs;
+    w.W2 = w.W1 + NB * qs;
+    w.Ts = w.W2 + NB * qs;
+    w.Vs = w.Ts + 2 * NB * NB;
+    w.Bs = w.Vs + 2 * (int64_t)w.ld * NB;
+    return w;
 }
 
-// y_R(s) <- Q_s^T y_R(s) (the forward front step) with the front's rows split
-// over the cluster.  Per panel of NB reflectors every CTA forms the partial
-// products V_b^T y over its rows, the cluster adds them in rank order through
-// distributed shared memory (double-buffered, one barrier per panel), and
-// every CTA applies y <- y - V_b (T_b^T W) to its own rows.  The panel's V
-// rows and T block are staged with cp.async one panel ahead.
+// B <- Q^T B (trans) or Q B for the t reflectors in V (rows 0..m-1, ld ldv;
+// unit diagonal implied unless explicit_v) and the diagonal NB x NB blocks of
+// T (ld ldt), with B's rows split over the cluster: this CTA holds rows
+// [lo, hi) in w.Bs.  Per panel the partial products V_b^T B over every CTA's
+// rows are added in rank order through distributed shared memory, then every
+// CTA updates its rows.  V rows and T block of the next panel are staged by
+// cp.async while the current one is applied.
 template <class real, int CS, int Q>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+__device__ void cl_apply_q(cooperative_groups::cluster_group& cl, const WideSmem<real>& w, int lo, int hi,
+                           const real* V, int64_t ldv, int t, const real* T, int ldt, bool explicit_v, bool trans,
+                           int qn, int qs, int& ph) {
+    const int ld = w.ld;
+    const int nbk = (t + NB - 1) / NB;
+    auto stage = [&](int k) {
+        const int b = trans ? k : nbk - 1 - k;
+        const int p0 = b * NB, pb = min(NB, t - p0);
+        real* vs = w.Vs + (int64_t)(k & 1) * ld * NB;
+        real* ts = w.Ts + (k & 1) * NB * NB;
+        const int r0 = max(lo, p0), nr = hi - r0;
+        for (int o = threadIdx.x; o < nr * pb; o += NT) {
+            const int rr = o % nr, i = o / nr;
+            const int r = r0 + rr, col = p0 + i;
+            real* d = vs + (r - lo) + (int64_t)i * ld;
+            if (r > col || (r == col && explicit_v)) cp_async_elem(d, V + r + (int64_t)col * ldv);
+            else *d = r == col ? (real)1 : (real)0;
+        }
+        for (int o = threadIdx.x; o < pb * pb; o += NT)
+            cp_async_elem(ts + o, T + (p0 + o % pb) + (int64_t)(p0 + o / pb) * ldt);
+    };
+    stage(0);
+    cp_async_commit();
+    for (int k = 0; k < nbk; k++, ph++) {
+        const int b = trans ? k : nbk - 1 - k;
+        const int p0 = b * NB, pb = min(NB, t - p0);
+        if (k + 1 < nbk) stage(k + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const real* vs = w.Vs + (int64_t)(k & 1) * ld * NB;
+        real* myp = w.part + (ph & 1) * NB * qs;
+        const int r0 = max(lo, p0);
+        // partial W(i, c) over own rows, split into row groups added in order
+        cta_small_gemv(pb, qn, myp, w.P, [&](int i, int c, int g, int G) {
+            const real* vi = vs + i * ld - lo;
+            const real* bc = w.Bs + c * ld - lo;
+            real v = 0;
+            for (int r = max(r0, p0 + i) + g; r < hi; r += G) v += vi[r] * bc[r];
+            return v;
+        });
+        cl.sync();
+        for (int o = threadIdx.x; o < pb * qn; o += NT) {
+            real v = 0;
+            for (int q = 0; q < CS; q++) v += cl.map_shared_rank(myp, q)[o];
+            w.W1[o] = v;
+        }
+        __syncthreads();
+        cta_tblock_mul(w.Ts + (k & 1) * NB * NB, pb, 0, pb, qn, trans, w.W1, w.W2);
+        for (int r = r0 + (int)threadIdx.x; r < hi; r += NT) {
+            real acc[Q];
+#pragma unroll
+            for (int c = 0; c < Q; c++) acc[c] = 0;
+            const real* vr = vs + (r - lo);
+            for (int i = 0; i < pb; i++) {
+                const real v = vr[i * ld];
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) acc[c] += v * w.W2[i + c * pb];
+            }
+            real* br = w.Bs + (r - lo);
+#pragma unroll
+            for (int c = 0; c < Q; c++)
+                if (c < qn) br[c * ld] -= acc[c];
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+// X <- R^{-1} X for R upper n x n (ld ldr) with inverted diagonal blocks Dinv
+// (n x NB, ld n), with X's rows split over the cluster in slabs of `slab`
+// rows (this CTA: [lo, hi) in w.Bs).  Block back substitution from the
+// bottom: the CTA owning block b forms x_b = Dinv_b x_b and publishes it in
+// distributed shared memory (one barrier per block); every CTA with rows
+// above b updates them with R(rows, b) x_b.  R(rows, b) and Dinv_b are staged
+// by cp.async one block ahead.
+template <class real, int CS, int Q>
+__device__ void cl_trsv_upper(cooperative_groups::cluster_group& cl, const WideSmem<real>& w, int lo, int hi,
+                              int slab, const real* R, int64_t ldr, int n, const real* Dinv, int qn, int qs,
+                              int& ph) {
+    const int ld = w.ld;
+    real* xl = w.W1;
+    const int nbk = (n + NB - 1) / NB;
+    auto stage = [&](int b, int k) {
+        const int b0 = b * NB, bs = min(NB, n - b0);
+        real* rs = w.Vs + (int64_t)(k & 1) * ld * NB;
+        const int nr = min(hi, b0) - lo;
+        for (int o = threadIdx.x; o < nr * bs; o += NT) {
+            const int rr = o % nr, u = o / nr;
+            cp_async_elem(rs + rr + (int64_t)u * ld, R + (lo + rr) + (int64_t)(b0 + u) * ldr);
+        }
+        if (b0 >= lo && b0 < hi) {
+            real* ds = w.Ts + (k & 1) * NB * NB;
+            for (int o = threadIdx.x; o < bs * bs; o += NT)
+                cp_async_elem(ds + o, Dinv + (b0 + o % bs) + (int64_t)(o / bs) * n);
+        }
+    };
+    stage(nbk - 1, 0);
+    cp_async_commit();
+    for (int k = 0; k < nbk; k++, ph++) {
+        const int b = nbk - 1 - k;
+        const int b0 = b * NB, bs = min(NB, n - b0);
+        if (b > 0) stage(b - 1, k + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        real* buf = w.part + (ph & 1) * NB * qs;
+        if (b0 >= lo && b0 < hi) {
+            const real* ds = w.Ts + (k & 1) * NB * NB;
+            for (int o = threadIdx.x; o < bs * qn; o += NT) {
+                const int i = o % bs, c = o / bs;
+                real v = 0;
+                for (int u = i; u < bs; u++) v += ds[i + u * bs] * w.Bs[(b0 - lo + u) + c * ld];
+                buf[i + c * bs] = v;
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < bs * qn; o += NT) w.Bs[(b0 - lo + o % bs) + (o / bs) * ld] = buf[o];
+        }
+        cl.sync();
+        if (lo < b0) {
+            const real* ob = cl.map_shared_rank(buf, b0 / slab);
+            for (int o = threadIdx.x; o < bs * qn; o += NT) xl[o] = ob[o];
+            __syncthreads();
+            const real* rs = w.Vs + (int64_t)(k & 1) * ld * NB;
+            const int top = min(hi, b0);
+            for (int r = lo + (int)threadIdx.x; r < top; r += NT) {
+                real acc[Q];
+#pragma unroll
+                for (int c = 0; c < Q; c++) acc[c] = 0;
+                for (int u = 0; u < bs; u++) {
+                    const real v = rs[(r - lo) + u * ld];
+#pragma unroll
+                    for (int c = 0; c < Q; c++)
+                        if (c < qn) acc[c] += v * xl[u + c * bs];
+                }
+#pragma unroll
+                for (int c = 0; c < Q; c++)
+                    if (c < qn) w.Bs[(r - lo) + c * ld] -= acc[c];
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+// y_R(s) <- Q_s^T y_R(s) (the forward front step), one cluster per front.
+template <class real, int CS, int Q>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
     k_sfront_fwd_wide(const SolveFront<real>* __restrict__ fr, const Seg* __restrict__ segs, real* Y, int64_t ldy,
                       int nrhs, int qs, int slab_cap) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double sm[];
-    const int ld = slab_cap | 1;
-    int* rmap = reinterpret_cast<int*>(sm);
-    real* part = reinterpret_cast<real*>(sm + (slab_cap + 1) / 2);
-    real* W1 = part + 2 * NB * qs;
-    real* W2 = W1 + NB * qs;
-    real* Ts = W2 + NB * qs;            // 2 x NB x NB
-    real* Vs = Ts + 2 * NB * NB;        // 2 x ld x NB
-    real* Bs = Vs + 2 * (int64_t)ld * NB;
+    const WideSmem<real> w = wide_smem_layout<real>(sm, slab_cap, qs);
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;   // uniform over the cluster (same blockIdx.y)
     const int rank = (int)cl.block_rank();
@@ -246,96 +409,23 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     for (int s = 0; s < F.nseg; s++) {
         const Seg g = segs[F.seg_begin + s];
         const int a = max(pos, lo), b = min(pos + g.len, hi);
-        for (int r = a + threadIdx.x; r < b; r += NT) rmap[r - lo] = (int)(g.off + (r - pos));
+        for (int r = a + threadIdx.x; r < b; r += NT) w.rmap[r - lo] = (int)(g.off + (r - pos));
         pos += g.len;
     }
     __syncthreads();
     real* Yc = Y + (int64_t)c0 * ldy;
     for (int o = threadIdx.x; o < rows * qn; o += NT) {
         const int r = o % rows, c = o / rows;
-        cp_async_elem(Bs + r + (int64_t)c * ld, Yc + rmap[r] + (int64_t)c * ldy);
+        cp_async_elem(w.Bs + r + (int64_t)c * w.ld, Yc + w.rmap[r] + (int64_t)c * ldy);
     }
-    const int nbk = (F.n + NB - 1) / NB;
-    // stage panel b: V rows r >= max(lo, p0) (unit diagonal, zeros above) and T_b
-    auto stage = [&](int b) {
-        const int p0 = b * NB, pb = min(NB, F.n - p0);
-        real* vs = Vs + (int64_t)(b & 1) * ld * NB;
-        real* ts = Ts + (b & 1) * NB * NB;
-        const int r0 = max(lo, p0), nr = hi - r0;
-        for (int o = threadIdx.x; o < nr * pb; o += NT) {
-            const int rr = o % nr, i = o / nr;
-            const int r = r0 + rr, col = p0 + i;
-            real* d = vs + (r - lo) + (int64_t)i * ld;
-            if (r > col) cp_async_elem(d, F.V + r + (int64_t)col * F.ldv);
-            else *d = r == col ? (real)1 : (real)0;
-        }
-        for (int o = threadIdx.x; o < pb * pb; o += NT)
-            cp_async_elem(ts + o, F.T + (p0 + o % pb) + (int64_t)(p0 + o / pb) * F.n);
-    };
-    stage(0);
     cp_async_commit();
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int b = 0; b < nbk; b++) {
-        const int p0 = b * NB;
-        const int pb = min(NB, F.n - p0);
-        if (b + 1 < nbk) stage(b + 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const real* vs = Vs + (int64_t)(b & 1) * ld * NB;
-        real* myp = part + (b & 1) * NB * qs;
-        const int r0 = max(lo, p0);
-        // partial W(i, c) over own rows
-        for (int i = warp; i < pb; i += NWARP) {
-            real acc[Q];
-#pragma unroll
-            for (int c = 0; c < Q; c++) acc[c] = 0;
-            for (int r = max(r0, p0 + i) + lane; r < hi; r += 32) {
-                const real vr = vs[(r - lo) + i * ld];
-                const real* br = Bs + (r - lo);
-#pragma unroll
-                for (int c = 0; c < Q; c++)
-                    if (c < qn) acc[c] += vr * br[c * ld];
-            }
-#pragma unroll
-            for (int c = 0; c < Q; c++) {
-                if (c < qn) {
-                    const real t = warp_sum_r(acc[c]);
-                    if (lane == 0) myp[i + c * pb] = t;
-                }
-            }
-        }
-        cl.sync();
-        for (int o = threadIdx.x; o < pb * qn; o += NT) {
-            real t = 0;
-            for (int k = 0; k < CS; k++) t += cl.map_shared_rank(myp, k)[o];
-            W1[o] = t;
-        }
-        __syncthreads();
-        cta_tblock_mul(Ts + (b & 1) * NB * NB, pb, 0, pb, qn, true, W1, W2);
-        for (int r = r0 + (int)threadIdx.x; r < hi; r += NT) {
-            real acc[Q];
-#pragma unroll
-            for (int c = 0; c < Q; c++) acc[c] = 0;
-            const real* vr = vs + (r - lo);
-            for (int i = 0; i < pb; i++) {
-                const real v = vr[i * ld];
-#pragma unroll
-                for (int c = 0; c < Q; c++)
-                    if (c < qn) acc[c] += v * W2[i + c * pb];
-            }
-            real* br = Bs + (r - lo);
-#pragma unroll
-            for (int c = 0; c < Q; c++)
-                if (c < qn) br[c * ld] -= acc[c];
-        }
-        __syncthreads();
-    }
+    int ph = 0;
+    cl_apply_q<real, CS, Q>(cl, w, lo, hi, F.V, F.ldv, F.n, F.T, F.n, false, true, qn, qs, ph);
     for (int o = threadIdx.x; o < rows * qn; o += NT) {
         const int r = o % rows, c = o / rows;
-        Yc[rmap[r] + (int64_t)c * ldy] = Bs[r + c * ld];
+        Yc[w.rmap[r] + (int64_t)c * ldy] = w.Bs[r + c * w.ld];
     }
-    cl.sync();   // no CTA leaves while another may still read its partials
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // Partial products R_sj x_j of the backward front step: one CTA per tile
@@ -414,26 +504,16 @@ __global__ void __launch_bounds__(NT) k_rsj_tiles(const RsjTile* __restrict__ ti
     }
 }
 
-// x_s <- R_ss^{-1} (y_s - sum of the R_sj partials) with the rows of x_s split
-// over the cluster.  Block back substitution from the bottom: the CTA owning
-// block b forms x_b = Dinv_b z_b and publishes it in distributed shared memory
-// (double-buffered, one barrier per block); every CTA with rows above b then
-// updates them with R(rows, b) x_b.  R(rows, b) and Dinv_b are staged with
-// cp.async one block ahead.
+// x_s <- R_ss^{-1} (y_s - sum of the R_sj partials), one cluster per front.
 template <class real, int CS, int Q>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
     k_sfront_bwd_wide(const WideFront* __restrict__ wf, const SolveFront<real>* __restrict__ fr,
                       const Seg* __restrict__ segs, real* Y, int64_t ldy, const real* __restrict__ Zp, int64_t ldz,
                       int nrhs, int qs, int slab_cap) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ double smb[];
-    const int ld = slab_cap | 1;
-    real* xb = reinterpret_cast<real*>(smb);   // 2 x NB x qs (read by the cluster)
-    real* xl = xb + 2 * NB * qs;
-    real* Ds = xl + NB * qs;                    // 2 x NB x NB
-    real* Rs = Ds + 2 * NB * NB;                // 2 x ld x NB
-    real* Zs = Rs + 2 * (int64_t)ld * NB;
+    extern __shared__ double sm[];
+    const WideSmem<real> w = wide_smem_layout<real>(sm, slab_cap, qs);
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;   // uniform over the cluster
     const int rank = (int)cl.block_rank();
@@ -444,77 +524,99 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     const int lo = min(n, rank * slab), hi = min(n, lo + slab);
     const int rows = hi - lo;
     real* xs = Y + segs[F.seg_begin].off + (int64_t)c0 * ldy;
-    const int nbk = (n + NB - 1) / NB;
-    auto stage = [&](int b) {
-        const int b0 = b * NB, bs = min(NB, n - b0);
-        real* rs = Rs + (int64_t)(b & 1) * ld * NB;
-        const int nr = min(hi, b0) - lo;
-        for (int o = threadIdx.x; o < nr * bs; o += NT) {
-            const int rr = o % nr, u = o / nr;
-            cp_async_elem(rs + rr + (int64_t)u * ld, F.V + (lo + rr) + (int64_t)(b0 + u) * F.ldv);
-        }
-        if (b0 >= lo && b0 < hi) {
-            real* ds = Ds + (b & 1) * NB * NB;
-            for (int o = threadIdx.x; o < bs * bs; o += NT)
-                cp_async_elem(ds + o, F.Dinv + (b0 + o % bs) + (int64_t)(o / bs) * n);
-        }
-    };
-    stage(nbk - 1);
-    cp_async_commit();
     for (int o = threadIdx.x; o < rows * qn; o += NT) {
         const int r = o % rows, c = o / rows;
         const real* zp = Zp + W.zoff + lo + r + (int64_t)(c0 + c) * ldz;
         real t = 0;
         for (int kc = 0; kc < W.nkc; kc++) t += zp[(int64_t)kc * n];
-        Zs[r + c * ld] = xs[lo + r + (int64_t)c * ldy] - t;
+        w.Bs[r + c * w.ld] = xs[lo + r + (int64_t)c * ldy] - t;
     }
-    for (int b = nbk - 1; b >= 0; b--) {
-        const int b0 = b * NB, bs = min(NB, n - b0);
-        if (b > 0) stage(b - 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        real* buf = xb + (b & 1) * NB * qs;
-        if (b0 >= lo && b0 < hi) {
-            const real* ds = Ds + (b & 1) * NB * NB;
-            for (int o = threadIdx.x; o < bs * qn; o += NT) {
-                const int i = o % bs, c = o / bs;
-                real t = 0;
-                for (int u = i; u < bs; u++) t += ds[i + u * bs] * Zs[(b0 - lo + u) + c * ld];
-                buf[i + c * bs] = t;
-            }
-            __syncthreads();
-            for (int o = threadIdx.x; o < bs * qn; o += NT) Zs[(b0 - lo + o % bs) + (o / bs) * ld] = buf[o];
-        }
-        cl.sync();
-        if (lo < b0) {
-            const real* ob = cl.map_shared_rank(buf, b0 / slab);
-            for (int o = threadIdx.x; o < bs * qn; o += NT) xl[o] = ob[o];
-            __syncthreads();
-            const real* rs = Rs + (int64_t)(b & 1) * ld * NB;
-            const int top = min(hi, b0);
-            for (int r = lo + (int)threadIdx.x; r < top; r += NT) {
-                real acc[Q];
-#pragma unroll
-                for (int c = 0; c < Q; c++) acc[c] = 0;
-                for (int u = 0; u < bs; u++) {
-                    const real v = rs[(r - lo) + u * ld];
-#pragma unroll
-                    for (int c = 0; c < Q; c++)
-                        if (c < qn) acc[c] += v * xl[u + c * bs];
-                }
-#pragma unroll
-                for (int c = 0; c < Q; c++)
-                    if (c < qn) Zs[(r - lo) + c * ld] -= acc[c];
-            }
-        }
-        __syncthreads();
-    }
+    int ph = 0;
+    cl_trsv_upper<real, CS, Q>(cl, w, lo, hi, slab, F.V, F.ldv, n, F.Dinv, qn, qs, ph);
     for (int o = threadIdx.x; o < rows * qn; o += NT) {
         const int r = o % rows, c = o / rows;
-        xs[lo + r + (int64_t)c * ldy] = Zs[r + c * ld];
+        xs[lo + r + (int64_t)c * ldy] = w.Bs[r + c * w.ld];
     }
-    cl.sync();   // no CTA leaves while another may still read its x_b
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// Forward scale + sparsify of one surviving cluster p, one cluster of CTAs
+// per interface: y_p <- Q_p^T U_p^T y_p, then the coarse part moves to the
+// next level's vector.
+template <class real, int CS, int Q>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
+    k_sss_fwd_wide(const SolveSS<real>* __restrict__ ss, real* Y, int64_t ldy, real* Yn, int64_t ldyn, int nrhs,
+                   int qs, int slab_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    const WideSmem<real> w = wide_smem_layout<real>(sm, slab_cap, qs);
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
+    const int rank = (int)cl.block_rank();
+    const SolveSS<real> S = ss[blockIdx.x / CS];
+    const int m = S.np;
+    const int slab = wide_slab_rows(m, CS);
+    const int lo = min(m, rank * slab), hi = min(m, lo + slab);
+    const int rows = hi - lo;
+    real* y = Y + S.off + (int64_t)c0 * ldy;
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        cp_async_elem(w.Bs + r + (int64_t)c * w.ld, y + lo + r + (int64_t)c * ldy);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    int ph = 0;
+    if (S.UV) cl_apply_q<real, CS, Q>(cl, w, lo, hi, S.UV, S.lduv, m, S.UT, m, false, true, qn, qs, ph);
+    if (S.QV && S.r > 0)
+        cl_apply_q<real, CS, Q>(cl, w, lo, hi, S.QV, m, S.r, S.QT, S.ldqt, true, true, qn, qs, ph);
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        const real v = w.Bs[r + c * w.ld];
+        y[lo + r + (int64_t)c * ldy] = v;
+        if (lo + r < S.r) Yn[S.noff + lo + r + (int64_t)(c0 + c) * ldyn] = v;
+    }
+    cl.sync();
+}
+
+// Backward scale + sparsify of one surviving cluster p: the coarse part comes
+// back from the next level's vector, y_p <- Q_p y_p, then y_p <- R_pp^{-1} y_p.
+template <class real, int CS, int Q>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
+    k_sss_bwd_wide(const SolveSS<real>* __restrict__ ss, real* Y, int64_t ldy, const real* Yn, int64_t ldyn,
+                   int nrhs, int qs, int slab_cap) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    const WideSmem<real> w = wide_smem_layout<real>(sm, slab_cap, qs);
+    int c0, qn;
+    if (!rhs_chunk(nrhs, qs, c0, qn)) return;
+    const int rank = (int)cl.block_rank();
+    const SolveSS<real> S = ss[blockIdx.x / CS];
+    const int m = S.np;
+    const int slab = wide_slab_rows(m, CS);
+    const int lo = min(m, rank * slab), hi = min(m, lo + slab);
+    const int rows = hi - lo;
+    real* y = Y + S.off + (int64_t)c0 * ldy;
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        const real* src = lo + r < S.r ? Yn + S.noff + lo + r + (int64_t)(c0 + c) * ldyn
+                                       : y + lo + r + (int64_t)c * ldy;
+        cp_async_elem(w.Bs + r + (int64_t)c * w.ld, src);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    int ph = 0;
+    if (S.QV && S.r > 0)
+        cl_apply_q<real, CS, Q>(cl, w, lo, hi, S.QV, m, S.r, S.QT, S.ldqt, true, false, qn, qs, ph);
+    if (S.UV) cl_trsv_upper<real, CS, Q>(cl, w, lo, hi, slab, S.UV, S.lduv, m, S.UD, qn, qs, ph);
+    for (int o = threadIdx.x; o < rows * qn; o += NT) {
+        const int r = o % rows, c = o / rows;
+        y[lo + r + (int64_t)c * ldy] = w.Bs[r + c * w.ld];
+    }
+    cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -754,6 +856,10 @@ void set_solve_attrs() {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
             cudaFuncSetAttribute(k_sfront_bwd_wide<real, kWideCS, QC.value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+            cudaFuncSetAttribute(k_sss_fwd_wide<real, kWideCS, QC.value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+            cudaFuncSetAttribute(k_sss_bwd_wide<real, kWideCS, QC.value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
         });
     });
 }
@@ -773,6 +879,10 @@ static int rhs_split(int blocks, int nrhs) {
 
 constexpr int kNumSM = 152;
 
+
+// CTAs of the one-CTA-per-unit form of a launch; the wide (cluster) forms
+// are used where this leaves SMs idle.
+static int narrow_ctas(int units, int nrhs) { return units * rhs_split(units, nrhs); }
 
 // Right-hand-side chunks of a wide launch over `units` clusters: about two
 // CTAs per SM, at most kTileQ columns per chunk, and the chunk's shared
@@ -812,15 +922,15 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
             for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
                 const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
                 if (b <= a) continue;
-                if (LV.ff_wide[c]) {
+                if (LV.ff_wide[c] && narrow_ctas(b - a, nrhs) < kNumSM) {
                     const int slab = wide_slab_rows(LV.ff_maxm[c], kWideCS);
                     int qs, split;
-                    if (wide_split(b - a, nrhs, [&](int q) { return fwd_wide_smem(slab, q, (int)esz); }, qs, split)) {
+                    if (wide_split(b - a, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
                         SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs,
                                      LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
                                      with_q(qs, [&](auto QC) {
                                          k_sfront_fwd_wide<real, kWideCS, QC.value>
-                                             <<<dim3((b - a) * kWideCS, split), NT, fwd_wide_smem(slab, qs, (int)esz),
+                                             <<<dim3((b - a) * kWideCS, split), NT, wide_smem(slab, qs, (int)esz),
                                                 st>>>(dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
                                      }));
                         continue;
@@ -836,6 +946,20 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
                              k_sfront_fwd<real><<<dim3(b - a, split), NT, smem, st>>>(dfr + LV.front_begin + a,
                                                                                 F->d_segs, Y, ldy, nrhs, qs, rmap_d,
                                                                                 staged));
+            }
+        }
+        if (LV.nss > 0 && LV.max_ss_n >= kWideMinN && narrow_ctas(LV.nss, nrhs) < kNumSM) {
+            const SolveLevelHost& LN = F->lv[k + 1];
+            const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
+            int qs, split;
+            if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+                SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed * split + LV.ssf_vec * nrhs, st,
+                             with_q(qs, [&](auto QC) {
+                                 k_sss_fwd_wide<real, kWideCS, QC.value>
+                                     <<<dim3(LV.nss * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                         dss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, qs, slab);
+                             }));
+                continue;
             }
         }
         if (LV.nss > 0) {
@@ -854,7 +978,22 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
         const SolveLevelHost& LV = F->lv[k];
         real* Y = ws + LV.ws_off * nrhs;
         const int64_t ldy = LV.rows;
-        if (LV.nss > 0) {
+        bool ss_done = false;
+        if (LV.nss > 0 && LV.max_ss_n >= kWideMinN && narrow_ctas(LV.nss, nrhs) < kNumSM) {
+            const SolveLevelHost& LN = F->lv[k + 1];
+            const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
+            int qs, split;
+            if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+                SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed * split + LV.ssb_vec * nrhs, st,
+                             with_q(qs, [&](auto QC) {
+                                 k_sss_bwd_wide<real, kWideCS, QC.value>
+                                     <<<dim3(LV.nss * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                         dss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, qs, slab);
+                             }));
+                ss_done = true;
+            }
+        }
+        if (LV.nss > 0 && !ss_done) {
             const SolveLevelHost& LN = F->lv[k + 1];
             const int split = rhs_split(LV.nss, nrhs);
             const int qs = (nrhs + split - 1) / split;
@@ -868,7 +1007,7 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
         if (LV.nfront > 0 && LV.bwd_wide) {
             const int slab = wide_slab_rows(LV.max_front_n, kWideCS);
             int qs, split;
-            if (wide_split(LV.nfront, nrhs, [&](int q) { return bwd_wide_smem(slab, q, (int)esz); }, qs, split)) {
+            if (wide_split(LV.nfront, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
                 real* Zp = ws + F->zp_off * nrhs;
                 const int64_t ldz = F->zp_rows;
                 if (LV.ntile > 0) {
@@ -888,7 +1027,7 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
                              (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st,
                              with_q(qs, [&](auto QC) {
                                  k_sfront_bwd_wide<real, kWideCS, QC.value>
-                                     <<<dim3(LV.nfront * kWideCS, split), NT, bwd_wide_smem(slab, qs, (int)esz), st>>>(
+                                     <<<dim3(LV.nfront * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
                                          static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, dfr, F->d_segs, Y,
                                          ldy, Zp, ldz, nrhs, qs, slab);
                              }));
