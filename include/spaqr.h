@@ -140,6 +140,20 @@ const char* spaqr_last_error(void);
  * (spaqr_ordering_destroy). */
 int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out);
 
+/* Ordering of a batch of independent matrices A[0..count-1] on grids
+ * g[0..count-1], treated as the block-diagonal matrix diag(A_0, ..., A_{c-1})
+ * (rows and columns of A_i at base_i = n_0 + ... + n_{i-1}).  Every matrix
+ * gets the nested dissection spaqr_order gives it with nlevels = 0, and the
+ * trees are aligned at their leaves: level k of the batch (from the leaves)
+ * holds level k of every matrix with more than k levels, so a factorisation
+ * with this ordering (spaqr_factor on the block-diagonal CSR) runs each
+ * level's fronts of all matrices in the same launches, with one host
+ * synchronisation per level for the whole batch.  The batch's level count is
+ * the largest one.  Errors as spaqr_order; *out is owned by the caller.
+ * (Batching independent systems is not in the paper; each matrix's
+ * factorisation is the one Algorithm 2 gives it alone.) */
+int spaqr_order_batch(int count, const spaqr_csr* A, const spaqr_grid* g, spaqr_ordering** out);
+
 /* Sizes of the ordering's arrays. */
 int spaqr_ordering_info(const spaqr_ordering* ord, spaqr_ordering_info_t* info);
 
@@ -212,6 +226,22 @@ int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const double* B, int6
 int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B,
                 int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
                 double* relres, void* stream);
+
+/* GMRES for a batch factorised with a spaqr_order_batch ordering: A is the
+ * block-diagonal CSR diag(A_0, ..., A_{count-1}) (n = part_ptr[count]), and
+ * part_ptr[0..count] (host, int64) are the row offsets of the matrices
+ * (part_ptr[0] = 0, strictly increasing).  Every (matrix i, column c) pair is
+ * its own Krylov process, exactly as spaqr_gmres runs it on A_i alone up to
+ * rounding: its residual ||b_i - A_i x_i|| / ||b_i|| is what tol bounds, and it
+ * stops on its own.  The SpMV and the factor application of an iteration are
+ * one pass over the whole batch (every level's fronts of all matrices in the
+ * same launches).  iters and relres hold count * nrhs entries, entry
+ * c * count + i for matrix i and column c (may be NULL).  B, X as spaqr_gmres.
+ * Errors as spaqr_gmres, plus INVALID_ARG for a bad part_ptr.  (The paper
+ * solves one system at a time; batching is an addition.) */
+int spaqr_gmres_batch(const spaqr_factor_t* F, const spaqr_csr* A, int count, const int64_t* part_ptr,
+                      int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int maxit,
+                      int* iters, double* relres, void* stream);
 
 /* Summary and timings of a factor. */
 int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out);

@@ -15,8 +15,9 @@ import os
 import numpy as np
 
 __all__ = [
-    "SpaqrError", "load_library", "spaqr_order", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
-    "spaqr_gmres",
+    "SpaqrError", "load_library", "spaqr_order", "spaqr_order_batch", "blockdiag_csr",
+    "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
+    "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats",
 ]
@@ -76,9 +77,9 @@ _lib = None
 
 # every symbol include/spaqr.h declares
 EXPORTS = [
-    "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_ordering_info",
+    "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_batch", "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
-    "spaqr_gmres",
+    "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats",
 ]
@@ -98,6 +99,7 @@ def load_library(path=None):
     lib.spaqr_opts_default.argtypes = [ctypes.POINTER(_Opts)]
     lib.spaqr_opts_default.restype = None
     lib.spaqr_order.argtypes = [ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), i32, ctypes.POINTER(vp)]
+    lib.spaqr_order_batch.argtypes = [i32, ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), ctypes.POINTER(vp)]
     lib.spaqr_ordering_info.argtypes = [vp, ctypes.POINTER(_OrdInfo)]
     lib.spaqr_ordering_get.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.spaqr_ordering_destroy.argtypes = [vp]
@@ -108,6 +110,8 @@ def load_library(path=None):
         if hasattr(lib, "spaqr_solve_noalloc"):
             lib.spaqr_solve_noalloc.argtypes = [vp, i32, vp, i64, vp, i64, vp]
         lib.spaqr_gmres.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
+        lib.spaqr_gmres_batch.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i32, vp, i64, vp, i64, dbl, i32,
+                                          vp, vp, vp]
         lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
         lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_factor_destroy.argtypes = [vp]
@@ -272,6 +276,52 @@ def spaqr_order(rowptr, colind, dims, nlevels=0):
     return Ordering(h.value)
 
 
+def spaqr_order_batch(patterns, dims_list):
+    """Ordering of the block-diagonal batch diag(A_0, ..., A_{k-1})
+    (spaqr_order_batch).  patterns: [(rowptr, colind)] (all host or all
+    device); dims_list: the grid sides of every matrix.  The returned
+    Ordering has .part_ptr, the row offsets of the matrices."""
+    load_library()
+    k = len(patterns)
+    if k < 1 or len(dims_list) != k:
+        raise ValueError("one grid per matrix, at least one matrix")
+    csrs = (_CSR * k)()
+    grids = (_Grid * k)()
+    keep = []
+    part = [0]
+    for i, ((rp, ci), dims) in enumerate(zip(patterns, dims_list)):
+        c, kk = _make_csr(rp, ci)
+        keep.append(kk)
+        csrs[i] = c
+        dims = tuple(int(d) for d in dims)
+        grids[i] = _Grid(len(dims), dims[0], dims[1], dims[2] if len(dims) > 2 else 1)
+        part.append(part[-1] + c.n)
+    h = ctypes.c_void_p()
+    _check(_lib.spaqr_order_batch(k, csrs, grids, ctypes.byref(h)))
+    o = Ordering(h.value)
+    o.part_ptr = np.asarray(part, dtype=np.int64)
+    return o
+
+
+def blockdiag_csr(mats):
+    """Host CSR (rowptr int64, colind int32, val float64) of the block-diagonal
+    matrix diag(A_0, ..., A_{k-1}) from [(rowptr, colind, val)] host arrays:
+    the layout spaqr_order_batch orders."""
+    rps, cis, vals = [], [], []
+    e0 = 0
+    base = 0
+    for rp, ci, v in mats:
+        rp = np.asarray(rp, dtype=np.int64)
+        rps.append(rp[1:] + e0 if rps else rp + e0)
+        cis.append(np.asarray(ci, dtype=np.int64) + base)
+        vals.append(np.asarray(v, dtype=np.float64))
+        e0 += int(rp[-1])
+        base += rp.shape[0] - 1
+    if base > np.iinfo(np.int32).max:
+        raise ValueError("batch too large for int32 column indices")
+    return (np.concatenate(rps), np.concatenate(cis).astype(np.int32), np.concatenate(vals))
+
+
 # ---------------------------------------------------------------------------
 # factor / solve / gmres
 # ---------------------------------------------------------------------------
@@ -378,6 +428,34 @@ def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=
     _check(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
                             iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)))
     return X, iters, relres
+
+
+def spaqr_gmres_batch(F, rowptr, colind, val, part_ptr, B, X=None, tol=1e-12, maxit=300, stream=None):
+    """GMRES on a block-diagonal batch (spaqr_gmres_batch): every matrix and
+    column is its own Krylov process.  Returns (X, iters, relres) with iters /
+    relres of shape (nrhs, count)."""
+    load_library()
+    csr, keep = _make_csr(rowptr, colind, val)
+    part = np.ascontiguousarray(part_ptr, dtype=np.int64)
+    count = part.shape[0] - 1
+    bp, ldb, nrhs, kb, bdev = _dense_colmajor(B, F.n, "B")
+    if X is None:
+        if bdev:
+            import torch
+            X = torch.zeros(nrhs, F.n, dtype=torch.float64, device=B.device).T
+            if B.dim() == 1:
+                X = X[:, 0]
+        else:
+            X = np.zeros((F.n, nrhs), order="F")
+            if np.asarray(B).ndim == 1:
+                X = X[:, 0]
+    xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
+    iters = np.zeros(nrhs * count, dtype=np.int32)
+    relres = np.zeros(nrhs * count, dtype=np.float64)
+    _check(_lib.spaqr_gmres_batch(F._h, ctypes.byref(csr), count, part.ctypes.data, nrhs, bp, ldb, xp, ldx,
+                                  float(tol), int(maxit), iters.ctypes.data, relres.ctypes.data,
+                                  _stream_ptr(stream)))
+    return X, iters.reshape(nrhs, count), relres.reshape(nrhs, count)
 
 
 def spaqr_factor_info(F):

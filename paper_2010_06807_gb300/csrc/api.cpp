@@ -73,6 +73,61 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
     return SPAQR_OK;
 }
 
+extern "C" int spaqr_order_batch(int count, const spaqr_csr* A, const spaqr_grid* g, spaqr_ordering** out) {
+    if (!out) { spaqr::set_error("out is NULL"); return SPAQR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (count < 1 || !A || !g) { spaqr::set_error("count < 1 or NULL arrays"); return SPAQR_ERR_INVALID_ARG; }
+    std::vector<std::vector<int64_t>> rps(count);
+    std::vector<std::vector<int32_t>> cis(count);
+    std::vector<const int64_t*> rowptrs(count);
+    std::vector<const int32_t*> colinds(count);
+    std::vector<int64_t> ns(count), nnzs(count);
+    std::vector<int> dims(4 * (size_t)count);
+    for (int i = 0; i < count; i++) {
+        const spaqr_csr& Ai = A[i];
+        if (Ai.n <= 0 || Ai.nnz < Ai.n || !Ai.rowptr || !Ai.colind) {
+            spaqr::set_error("bad CSR sizes or pointers of matrix " + std::to_string(i));
+            return SPAQR_ERR_INVALID_ARG;
+        }
+        rowptrs[i] = Ai.rowptr;
+        colinds[i] = Ai.colind;
+        if (Ai.on_device) {
+            rps[i].resize(Ai.n + 1);
+            cis[i].resize(Ai.nnz);
+            if (cudaMemcpy(rps[i].data(), Ai.rowptr, sizeof(int64_t) * (Ai.n + 1), cudaMemcpyDeviceToHost) !=
+                    cudaSuccess ||
+                cudaMemcpy(cis[i].data(), Ai.colind, sizeof(int32_t) * Ai.nnz, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                spaqr::set_error("copying the device pattern failed");
+                return SPAQR_ERR_CUDA;
+            }
+            rowptrs[i] = rps[i].data();
+            colinds[i] = cis[i].data();
+        }
+        ns[i] = Ai.n;
+        nnzs[i] = Ai.nnz;
+        dims[4 * i] = g[i].dim;
+        dims[4 * i + 1] = g[i].nx;
+        dims[4 * i + 2] = g[i].ny;
+        dims[4 * i + 3] = g[i].dim == 3 ? g[i].nz : 1;
+    }
+    spaqr_ordering* ord = new (std::nothrow) spaqr_ordering();
+    if (!ord) { spaqr::set_error("host allocation failed"); return SPAQR_ERR_OOM; }
+    int rc;
+    try {
+        rc = spaqr::build_ordering_batch(count, rowptrs.data(), colinds.data(), ns.data(), nnzs.data(), dims.data(),
+                                         ord->o);
+    } catch (const std::bad_alloc&) {
+        spaqr::set_error("host allocation failed");
+        rc = SPAQR_ERR_OOM;
+    } catch (const std::exception& e) {
+        spaqr::set_error(std::string("ordering failed: ") + e.what());
+        rc = SPAQR_ERR_INVALID_ARG;
+    }
+    if (rc != SPAQR_OK) { delete ord; return rc; }
+    *out = ord;
+    return SPAQR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // launch accounting
 // ---------------------------------------------------------------------------

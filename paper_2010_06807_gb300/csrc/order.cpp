@@ -114,37 +114,28 @@ bool prefix_equal(const std::vector<Key>& a, const std::vector<Key>& b, int stag
 
 }  // namespace
 
-int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz, int dim,
-                   const int* dims, int nlevels, Ordering& o) {
-    if (dim != 2 && dim != 3) { set_error("grid dim must be 2 or 3"); return SPAQR_ERR_INVALID_ARG; }
-    int64_t N = 1;
-    for (int k = 0; k < dim; k++) {
-        if (dims[k] < 1) { set_error("grid sides must be >= 1"); return SPAQR_ERR_INVALID_ARG; }
-        N *= dims[k];
-    }
-    if (N != n) { set_error("grid size does not match matrix size"); return SPAQR_ERR_INVALID_ARG; }
-    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
-    o.dim = dim;
-    for (int k = 0; k < 3; k++) o.dims[k] = k < dim ? dims[k] : 1;
-    o.n = n;
-    o.nnz = nnz;
-    o.L = nlevels > 0 ? nlevels : num_levels(n);
-    const int L = o.L;
+namespace {
 
+struct Atom {
+    std::vector<int64_t> pts;
+    std::vector<Key> key;
+};
+
+// Geometric nested dissection of one grid with L levels: the tree (depth 0 =
+// root) and the atoms of every node, their points as grid indices.
+int nd_grid(int dim, const int* dims3, int L, std::vector<NDNode>& nodes_out,
+            std::vector<std::vector<Atom>>& node_atoms) {
     Builder b;
     b.dim = dim;
-    for (int k = 0; k < 3; k++) b.dims[k] = o.dims[k];
+    for (int k = 0; k < 3; k++) b.dims[k] = dims3[k];
     b.L = L;
-    int lo0[3] = {0, 0, 0}, hi0[3] = {o.dims[0], o.dims[1], o.dims[2]};
+    int lo0[3] = {0, 0, 0}, hi0[3] = {dims3[0], dims3[1], dims3[2]};
     b.build(lo0, hi0, 0, -1);
-    o.nodes = b.nodes;
-    const std::vector<NDNode>& nodes = o.nodes;
+    nodes_out = b.nodes;
+    const std::vector<NDNode>& nodes = nodes_out;
     const int nn = (int)nodes.size();
-    const int64_t stride[3] = {1, o.dims[0], (int64_t)o.dims[0] * o.dims[1]};
-
-    // ---- atoms of every node -------------------------------------------
-    struct Atom { std::vector<int64_t> pts; std::vector<Key> key; };
-    std::vector<std::vector<Atom>> node_atoms(nn);
+    const int64_t stride[3] = {1, dims3[0], (int64_t)dims3[0] * dims3[1]};
+    node_atoms.assign(nn, {});
     for (int id = 0; id < nn; id++) {
         const NDNode& nd = nodes[id];
         int lo[3], hi[3];
@@ -240,6 +231,18 @@ int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int6
         }
     }
 
+    return SPAQR_OK;
+}
+
+// Order, pattern, symbolic plan and gather map of a forest of nested-dissection
+// trees (o.nodes in preorder, every tree's leaves at depth o.L - 1) with the
+// atoms of every node and the CSR pattern of the whole matrix.
+int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
+                std::vector<std::vector<Atom>>& node_atoms) {
+    const std::vector<NDNode>& nodes = o.nodes;
+    const int nn = (int)nodes.size();
+    const int64_t n = o.n, nnz = o.nnz;
+    const int L = o.L;
     // ---- global order ----------------------------------------------------
     std::vector<int> norder(nn);
     for (int i = 0; i < nn; i++) norder[i] = i;
@@ -479,6 +482,107 @@ int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int6
         }
     }
     return SPAQR_OK;
+}
+
+int check_grid(int dim, const int* dims, int64_t n, const int64_t* rowptr, int64_t nnz, int* dims3) {
+    if (dim != 2 && dim != 3) { set_error("grid dim must be 2 or 3"); return SPAQR_ERR_INVALID_ARG; }
+    int64_t N = 1;
+    for (int k = 0; k < dim; k++) {
+        if (dims[k] < 1) { set_error("grid sides must be >= 1"); return SPAQR_ERR_INVALID_ARG; }
+        N *= dims[k];
+    }
+    if (N != n) { set_error("grid size does not match matrix size"); return SPAQR_ERR_INVALID_ARG; }
+    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+    for (int k = 0; k < 3; k++) dims3[k] = k < dim ? dims[k] : 1;
+    return SPAQR_OK;
+}
+
+}  // namespace
+
+int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz, int dim,
+                   const int* dims, int nlevels, Ordering& o) {
+    int rc = check_grid(dim, dims, n, rowptr, nnz, o.dims);
+    if (rc != SPAQR_OK) return rc;
+    o.dim = dim;
+    o.n = n;
+    o.nnz = nnz;
+    o.L = nlevels > 0 ? nlevels : num_levels(n);
+    std::vector<std::vector<Atom>> node_atoms;
+    rc = nd_grid(dim, o.dims, o.L, o.nodes, node_atoms);
+    if (rc != SPAQR_OK) return rc;
+    return plan_forest(o, rowptr, colind, node_atoms);
+}
+
+// Ordering of the block-diagonal matrix diag(A_0, ..., A_{count-1}): every
+// grid gets its own tree with its own level count; the trees' depths are
+// shifted so that all leaves sit at depth L - 1 (L = the largest count), so
+// level k of the forest holds level k (from the leaves) of every matrix that
+// has one.  Unknowns of matrix i keep their block: rows/columns base_i + r.
+int build_ordering_batch(int count, const int64_t* const* rowptrs, const int32_t* const* colinds,
+                         const int64_t* ns, const int64_t* nnzs, const int* dims_list, Ordering& o) {
+    if (count < 1) { set_error("count must be >= 1"); return SPAQR_ERR_INVALID_ARG; }
+    std::vector<std::vector<NDNode>> tnodes(count);
+    std::vector<std::vector<std::vector<Atom>>> tatoms(count);
+    std::vector<int> tl(count);
+    int L = 1;
+    int64_t n = 0, nnz = 0;
+    for (int i = 0; i < count; i++) {
+        const int* g = dims_list + 4 * i;   // dim, nx, ny, nz
+        int dims3[3];
+        int rc = check_grid(g[0], g + 1, ns[i], rowptrs[i], nnzs[i], dims3);
+        if (rc != SPAQR_OK) return rc;
+        tl[i] = num_levels(ns[i]);
+        L = std::max(L, tl[i]);
+        rc = nd_grid(g[0], dims3, tl[i], tnodes[i], tatoms[i]);
+        if (rc != SPAQR_OK) return rc;
+        n += ns[i];
+        nnz += nnzs[i];
+    }
+    o.dim = 0;   // a forest of grids
+    o.dims[0] = o.dims[1] = o.dims[2] = 1;
+    o.n = n;
+    o.nnz = nnz;
+    o.L = L;
+    o.nodes.clear();
+    std::vector<std::vector<Atom>> node_atoms;
+    std::vector<int64_t> rowptr(1, 0);
+    std::vector<int32_t> colind;
+    rowptr.reserve(n + 1);
+    colind.reserve(nnz);
+    int64_t base = 0;
+    for (int i = 0; i < count; i++) {
+        const int noff = (int)o.nodes.size();
+        const int shift = L - tl[i];
+        for (NDNode nd : tnodes[i]) {
+            nd.id += noff;
+            nd.depth += shift;
+            if (nd.parent >= 0) nd.parent += noff;
+            if (nd.left >= 0) nd.left += noff;
+            if (nd.right >= 0) nd.right += noff;
+            o.nodes.push_back(nd);
+        }
+        for (std::vector<Atom>& atoms : tatoms[i]) {
+            for (Atom& a : atoms) {
+                for (int64_t& p : a.pts) p += base;
+                for (Key& kk : a.key) {
+                    kk.depth += shift;
+                    kk.node += noff;
+                }
+            }
+            node_atoms.push_back(std::move(atoms));
+        }
+        const int64_t* rp = rowptrs[i];
+        const int32_t* ci = colinds[i];
+        const int64_t eb = (int64_t)colind.size();
+        for (int64_t r = 0; r < ns[i]; r++) rowptr.push_back(eb + rp[r + 1]);
+        for (int64_t e = 0; e < nnzs[i]; e++) {
+            if (ci[e] < 0 || ci[e] >= ns[i]) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
+            colind.push_back((int32_t)(ci[e] + base));
+        }
+        base += ns[i];
+    }
+    if (n > INT32_MAX) { set_error("batch too large for int32 column indices"); return SPAQR_ERR_INVALID_ARG; }
+    return plan_forest(o, rowptr.data(), colind.data(), node_atoms);
 }
 
 }  // namespace spaqr

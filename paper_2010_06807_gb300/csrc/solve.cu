@@ -621,7 +621,26 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
 
 // ---------------------------------------------------------------------------
 // GMRES kernels (FP64)
+//
+// The operator (SpMV, factor application) acts on whole columns of length n;
+// the Krylov processes are "virtual columns": with nseg segments (the
+// matrices of a block-diagonal batch, rows [seg_ptr[s], seg_ptr[s+1])),
+// virtual column v = c * nseg + s is segment s of right-hand-side column c.
+// nseg = 1 is the plain multi-RHS case.
 // ---------------------------------------------------------------------------
+
+struct VCols {
+    int nseg;                  // segments per column
+    const int* seg_of;         // row -> segment (nseg > 1)
+    const int64_t* seg_ptr;    // nseg + 1 row offsets (device)
+    __device__ __forceinline__ int of(int64_t r, int c) const { return nseg == 1 ? c : c * nseg + seg_of[r]; }
+    __device__ __forceinline__ void range(int v, int64_t n, int64_t& base, int64_t& len) const {
+        if (nseg == 1) { base = (int64_t)v * n; len = n; return; }
+        const int c = v / nseg, s = v % nseg;
+        base = (int64_t)c * n + seg_ptr[s];
+        len = seg_ptr[s + 1] - seg_ptr[s];
+    }
+};
 
 // Y = A X (CSR, nrhs columns)
 __global__ void k_spmv(int64_t n, int nrhs, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
@@ -649,58 +668,60 @@ __global__ void k_residual(int64_t n, int nrhs, const int64_t* __restrict__ rowp
     R[r + c * n] = B[r + c * ldb] - s;
 }
 
-// out[i + c * nout] = dot(U_i[:, c], W[:, c]) for i < nvec; U_i = U + i * n * nrhs.
-// One CTA per (i, c); fixed reduction order.
-__global__ void __launch_bounds__(NT) k_dots(int64_t n, int nrhs, const double* __restrict__ U, int nvec,
+// out[i + v * nout] = dot(U_i[v], W[v]) for i < nvec and every virtual column
+// v; U_i = U + i * n * nrhs.  One CTA per (i, v); fixed reduction order.
+__global__ void __launch_bounds__(NT) k_dots(int64_t n, int nrhs, VCols vc, const double* __restrict__ U, int nvec,
                                              const double* __restrict__ W, double* __restrict__ out, int nout) {
     __shared__ double red[NWARP];
-    const int i = blockIdx.x % nvec, c = blockIdx.x / nvec;
-    const double* u = U + ((int64_t)i * nrhs + c) * n;
-    const double* w = W + (int64_t)c * n;
+    const int i = blockIdx.x % nvec, v = blockIdx.x / nvec;
+    int64_t base, len;
+    vc.range(v, n, base, len);
+    const double* u = U + (int64_t)i * n * nrhs + base;
+    const double* w = W + base;
     double s = 0.0;
-    for (int64_t r = threadIdx.x; r < n; r += NT) s += u[r] * w[r];
+    for (int64_t r = threadIdx.x; r < len; r += NT) s += u[r] * w[r];
     s = block_sum(s, red);
-    if (threadIdx.x == 0) out[i + c * nout] = s;
+    if (threadIdx.x == 0) out[i + (int64_t)v * nout] = s;
 }
 
-// W[:, c] -= sum_i U_i[:, c] h[i, c] ; H[:, j] += h  (only active columns)
-__global__ void k_orth_update(int64_t n, int nrhs, const double* __restrict__ U, int nvec,
+// W[:, v] -= sum_i U_i[:, v] h[i, v]  (active virtual columns only)
+__global__ void k_orth_update(int64_t n, int nrhs, VCols vc, const double* __restrict__ U, int nvec,
                               const double* __restrict__ h, int nh, double* __restrict__ W,
                               const int* __restrict__ active) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n * nrhs) return;
     const int64_t r = o % n;
-    const int c = (int)(o / n);
-    if (!active[c]) return;
+    const int v = vc.of(r, (int)(o / n));
+    if (!active[v]) return;
     double s = 0.0;
-    for (int i = 0; i < nvec; i++) s += U[((int64_t)i * nrhs + c) * n + r] * h[i + c * nh];
-    W[r + c * n] -= s;
+    for (int i = 0; i < nvec; i++) s += U[(int64_t)i * n * nrhs + o] * h[i + (int64_t)v * nh];
+    W[o] -= s;
 }
 
-// U_{j+1}[:, c] = W[:, c] / hn[c] (zero for inactive columns or hn = 0)
-__global__ void k_normalize(int64_t n, int nrhs, const double* __restrict__ W, const double* __restrict__ hn,
-                            double* __restrict__ Unext, const int* __restrict__ active) {
+// U_{j+1} = W / hn[v] (zero for inactive virtual columns or hn = 0)
+__global__ void k_normalize(int64_t n, int nrhs, VCols vc, const double* __restrict__ W,
+                            const double* __restrict__ hn, double* __restrict__ Unext, const int* __restrict__ active) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n * nrhs) return;
-    const int c = (int)(o / n);
-    const double h = hn[c];
-    Unext[o] = (active[c] && h != 0.0) ? W[o] / h : 0.0;
+    const int v = vc.of(o % n, (int)(o / n));
+    const double h = hn[v];
+    Unext[o] = (active[v] && h != 0.0) ? W[o] / h : 0.0;
 }
 
 // Givens update of column j of every active Hessenberg matrix (one thread per
-// RHS).  H_c is (ldh x maxit) column-major; cs/sn/g per column.
-__global__ void k_givens(int nrhs, int j, double* H, int ldh, int64_t hstride, const double* h1,
+// virtual column).  H_v is (ldh x maxit) column-major; cs/sn/g per column.
+__global__ void k_givens(int nv, int j, double* H, int ldh, int64_t hstride, const double* h1,
                          const double* h2, const double* hn, double* cs, double* sn, double* g, int ldg,
                          const double* bnorm, double* est, const int* active) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nrhs) return;
+    if (c >= nv) return;
     double* Hc = H + c * hstride;
     double* col = Hc + (int64_t)j * ldh;
     double* csc = cs + (int64_t)c * ldg;
     double* snc = sn + (int64_t)c * ldg;
     double* gc = g + (int64_t)c * ldg;
     if (!active[c]) { est[c] = 0.0; return; }
-    for (int i = 0; i <= j; i++) col[i] = h1[i + c * ldh] + h2[i + c * ldh];
+    for (int i = 0; i <= j; i++) col[i] = h1[i + (int64_t)c * ldh] + h2[i + (int64_t)c * ldh];
     col[j + 1] = hn[c];
     for (int i = 0; i < j; i++) {
         const double t = csc[i] * col[i] + snc[i] * col[i + 1];
@@ -719,11 +740,11 @@ __global__ void k_givens(int nrhs, int j, double* H, int ldh, int64_t hstride, c
     est[c] = fabs(gc[j + 1]) / bnorm[c];
 }
 
-// y_c = H_c(0:j+1, 0:j+1)^{-1} g_c(0:j+1) for columns with want[c]; U = sum_i V_i y_i.
-__global__ void k_hsolve(int nrhs, int j, const double* H, int ldh, int64_t hstride, const double* g, int ldg,
+// y_v = H_v(0:j+1, 0:j+1)^{-1} g_v(0:j+1) for virtual columns with want[v].
+__global__ void k_hsolve(int nv, int j, const double* H, int ldh, int64_t hstride, const double* g, int ldg,
                          double* y, const int* want) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nrhs) return;
+    if (c >= nv) return;
     double* yc = y + (int64_t)c * ldg;
     if (!want[c]) {
         for (int i = 0; i <= j; i++) yc[i] = 0.0;
@@ -738,25 +759,26 @@ __global__ void k_hsolve(int nrhs, int j, const double* H, int ldh, int64_t hstr
     }
 }
 
-__global__ void k_combine(int64_t n, int nrhs, const double* __restrict__ U, int nvec, const double* __restrict__ y,
-                          int ldy, double* __restrict__ out) {
+// out = sum_i U_i y_i (per virtual column)
+__global__ void k_combine(int64_t n, int nrhs, VCols vc, const double* __restrict__ U, int nvec,
+                          const double* __restrict__ y, int ldy, double* __restrict__ out) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n * nrhs) return;
-    const int64_t r = o % n;
-    const int c = (int)(o / n);
+    const int v = vc.of(o % n, (int)(o / n));
     double s = 0.0;
-    for (int i = 0; i < nvec; i++) s += U[((int64_t)i * nrhs + c) * n + r] * y[i + (int64_t)c * ldy];
-    out[r + c * n] = s;
+    for (int i = 0; i < nvec; i++) s += U[(int64_t)i * n * nrhs + o] * y[i + (int64_t)v * ldy];
+    out[o] = s;
 }
 
-// X[:, c] = X0[:, c] + Z[:, c] for accepted columns
-__global__ void k_accept(int64_t n, int nrhs, const double* __restrict__ X0, int64_t ldx0, const double* __restrict__ Z,
-                         double* __restrict__ X, int64_t ldx, const int* __restrict__ take) {
+// X = X0 + Z where take[v] (the other entries keep X)
+__global__ void k_accept(int64_t n, int nrhs, VCols vc, const double* __restrict__ X0, int64_t ldx0,
+                         const double* __restrict__ Z, double* __restrict__ X, int64_t ldx,
+                         const int* __restrict__ take) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n * nrhs) return;
     const int64_t r = o % n;
     const int c = (int)(o / n);
-    if (!take[c]) return;
+    if (!take[vc.of(r, c)]) return;
     X[r + c * ldx] = X0[r + c * ldx0] + Z[r + c * n];
 }
 
@@ -769,15 +791,24 @@ __global__ void k_copy_cols(int64_t n, int nrhs, const double* __restrict__ S, i
     D[r + c * ldd] = S[r + c * lds];
 }
 
-__global__ void k_sqrtv(int nrhs, double* v) {
-    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) v[c] = sqrt(v[c]);
-}
-
-__global__ void k_scale_cols(int64_t n, int nrhs, double* __restrict__ U, const double* __restrict__ s) {
+// D[:, c] = S[:, c] for rows of accepted virtual columns (take[v])
+__global__ void k_copy_taken(int64_t n, int nrhs, VCols vc, const double* __restrict__ S, int64_t lds,
+                             double* __restrict__ D, int64_t ldd, const int* __restrict__ take) {
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n * nrhs) return;
+    const int64_t r = o % n;
     const int c = (int)(o / n);
-    const double v = s[c];
+    if (take[vc.of(r, c)]) D[r + c * ldd] = S[r + c * lds];
+}
+
+__global__ void k_sqrtv(int nv, double* v) {
+    for (int c = threadIdx.x; c < nv; c += blockDim.x) v[c] = sqrt(v[c]);
+}
+
+__global__ void k_scale_cols(int64_t n, int nrhs, VCols vc, double* __restrict__ U, const double* __restrict__ s) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n * nrhs) return;
+    const double v = s[vc.of(o % n, (int)(o / n))];
     U[o] = v != 0.0 ? U[o] / v : 0.0;
 }
 
@@ -1112,8 +1143,15 @@ extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, i
     return SPAQR_OK;
 }
 
-extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B, int64_t ldb,
-                           double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres, void* stream) {
+namespace {
+
+// Right-preconditioned flexible GMRES over virtual columns (see VCols):
+// nseg = 1 for one matrix, nseg = count for a block-diagonal batch with
+// segment row offsets seg_ptr (host).  iters / relres per virtual column
+// v = c * nseg + s.
+int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, const int64_t* seg_ptr,
+               const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
+               double* relres, void* stream) {
     if (!F || !A || !B || !X) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
     if (A->n != F->n || nrhs < 0 || ldb < F->n || ldx < F->n || maxit < 1 || !(tol >= 0.0)) {
         set_error("bad size, leading dimension, tol or maxit");
@@ -1124,8 +1162,25 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     C.st = (cudaStream_t)stream;
     cudaStream_t st = C.st;
     const int64_t n = F->n, nnz = A->nnz;
+    const int nv = nrhs * nseg;
     const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
     if (bdev != xdev) { set_error("B and X must both be host or both be device memory"); return SPAQR_ERR_INVALID_ARG; }
+    // virtual columns
+    VCols vc{nseg, nullptr, nullptr};
+    if (nseg > 1) {
+        std::vector<int> so(n);
+        for (int sg = 0; sg < nseg; sg++)
+            for (int64_t r = seg_ptr[sg]; r < seg_ptr[sg + 1]; r++) so[r] = sg;
+        int* d_so = C.alloc<int>(n);
+        int64_t* d_sp = C.alloc<int64_t>(nseg + 1);
+        if (C.rc) return C.rc;
+        C.cuda(cudaMemcpyAsync(d_so, so.data(), 4 * n, cudaMemcpyHostToDevice, st));
+        C.cuda(cudaMemcpyAsync(d_sp, seg_ptr, 8 * (nseg + 1), cudaMemcpyHostToDevice, st));
+        vc.seg_of = d_so;
+        vc.seg_ptr = d_sp;
+    }
+    auto seg_base = [&](int v) { return nseg == 1 ? (int64_t)0 : seg_ptr[v % nseg]; };
+    auto seg_len = [&](int v) { return nseg == 1 ? n : seg_ptr[v % nseg + 1] - seg_ptr[v % nseg]; };
     // matrix on the device
     const int64_t* rp = A->rowptr;
     const int32_t* ci = A->colind;
@@ -1157,25 +1212,27 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         lb = lx = n;
     }
     const unsigned nbl = (unsigned)((n * nrhs + 255) / 256);
+    const unsigned nbv = (unsigned)((nv + 31) / 32);
     const int ldh = maxit + 1;
     const int64_t hstride = (int64_t)ldh * maxit;
     double* X0 = C.alloc<double>(n * nrhs);
     double* Wv = C.alloc<double>(n * nrhs);
     double* Zv = C.alloc<double>(n * nrhs);
     double* ws = C.alloc<double>((F->ws_rows * nrhs * F->esz + 7) / 8);
-    double* H = C.alloc<double>(hstride * nrhs);
-    double* h1 = C.alloc<double>((int64_t)ldh * nrhs);
-    double* h2 = C.alloc<double>((int64_t)ldh * nrhs);
-    double* hn = C.alloc<double>(nrhs);
-    double* cs = C.alloc<double>((int64_t)ldh * nrhs);
-    double* sn = C.alloc<double>((int64_t)ldh * nrhs);
-    double* g = C.alloc<double>((int64_t)ldh * nrhs);
-    double* ycoef = C.alloc<double>((int64_t)ldh * nrhs);
-    double* bn = C.alloc<double>(nrhs);
-    double* est = C.alloc<double>(nrhs);
-    double* rn = C.alloc<double>(nrhs);
-    int* active = C.alloc<int>(nrhs);
-    int* want = C.alloc<int>(nrhs);
+    double* H = C.alloc<double>(hstride * nv);
+    double* h1 = C.alloc<double>((int64_t)ldh * nv);
+    double* h2 = C.alloc<double>((int64_t)ldh * nv);
+    double* hn = C.alloc<double>(nv);
+    double* cs = C.alloc<double>((int64_t)ldh * nv);
+    double* sn = C.alloc<double>((int64_t)ldh * nv);
+    double* g = C.alloc<double>((int64_t)ldh * nv);
+    double* ycoef = C.alloc<double>((int64_t)ldh * nv);
+    double* bn = C.alloc<double>(nv);
+    double* est = C.alloc<double>(nv);
+    double* rn = C.alloc<double>(nv);
+    int* active = C.alloc<int>(nv);
+    int* want = C.alloc<int>(nv);
+    int* taken = C.alloc<int>(nv);
     int* flag = C.alloc<int>(1);
     if (C.rc) return C.rc;
     int cap = std::min(maxit, 48) + 1;
@@ -1183,58 +1240,63 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     double* Zb = C.alloc<double>((int64_t)cap * n * nrhs);   // Z_j = M^{-1} V_j (flexible GMRES)
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nrhs, st));
-    C.cuda(cudaMemsetAsync(g, 0, sizeof(double) * ldh * nrhs, st));
+    C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nv, st));
+    C.cuda(cudaMemsetAsync(g, 0, sizeof(double) * ldh * nv, st));
     // X0 = X; r0 = B - A X0 (into V_0); beta = ||r0||; ||b||
     SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dX, lx, X0, n));
-    SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb));
+    SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st,
+                 k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb));
     SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n));
-    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, bn, 1));  // ||b||^2
     SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
-                 k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Vb, 1, Vb, hn, 1));  // ||r0||^2
+                 k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Wv, 1, Wv, bn, 1));  // ||b||^2
+    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
+                 k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Vb, 1, Vb, hn, 1));  // ||r0||^2
     C.launched();
-    std::vector<double> hb(nrhs), hr(nrhs), hest(nrhs), hres(nrhs, 1.0);
-    std::vector<int> hact(nrhs, 1), hit(nrhs, 0), hwant(nrhs, 0);
-    C.cuda(cudaMemcpyAsync(hb.data(), bn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
-    C.cuda(cudaMemcpyAsync(hr.data(), hn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+    std::vector<double> hb(nv), hr(nv), hest(nv), hres(nv, 1.0);
+    std::vector<int> hact(nv, 1), hit(nv, 0), hwant(nv, 0);
+    C.cuda(cudaMemcpyAsync(hb.data(), bn, 8 * nv, cudaMemcpyDeviceToHost, st));
+    C.cuda(cudaMemcpyAsync(hr.data(), hn, 8 * nv, cudaMemcpyDeviceToHost, st));
     C.cuda(cudaStreamSynchronize(st));
     if (C.rc) return C.rc;
-    std::vector<double> hg(ldh * nrhs, 0.0);
-    for (int c = 0; c < nrhs; c++) {
-        hb[c] = std::sqrt(hb[c]);
-        hr[c] = std::sqrt(hr[c]);
-        if (hb[c] == 0.0) {
+    std::vector<double> hg((size_t)ldh * nv, 0.0);
+    for (int v = 0; v < nv; v++) {
+        hb[v] = std::sqrt(hb[v]);
+        hr[v] = std::sqrt(hr[v]);
+        if (hb[v] == 0.0) {
             // b = 0: x = 0
-            hact[c] = 0;
-            hres[c] = 0.0;
-            C.cuda(cudaMemsetAsync(dX + c * lx, 0, 8 * n, st));
-        } else if (hr[c] / hb[c] <= tol) {
-            hact[c] = 0;  // the initial guess already satisfies tol
-            hres[c] = hr[c] / hb[c];
+            hact[v] = 0;
+            hres[v] = 0.0;
+            C.cuda(cudaMemsetAsync(dX + (int64_t)(v / nseg) * lx + seg_base(v), 0, 8 * seg_len(v), st));
+        } else if (hr[v] / hb[v] <= tol) {
+            hact[v] = 0;  // the initial guess already satisfies tol
+            hres[v] = hr[v] / hb[v];
         }
-        hg[(int64_t)c * ldh] = hr[c];
+        hg[(int64_t)v * ldh] = hr[v];
     }
-    C.cuda(cudaMemcpyAsync(bn, hb.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
-    C.cuda(cudaMemcpyAsync(g, hg.data(), 8 * ldh * nrhs, cudaMemcpyHostToDevice, st));
-    C.cuda(cudaMemcpyAsync(hn, hr.data(), 8 * nrhs, cudaMemcpyHostToDevice, st));
-    C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
-    SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, Vb, hn));  // V_0 = r0 / beta
+    C.cuda(cudaMemcpyAsync(bn, hb.data(), 8 * nv, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(g, hg.data(), 8 * ldh * nv, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(hn, hr.data(), 8 * nv, cudaMemcpyHostToDevice, st));
+    C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nv, cudaMemcpyHostToDevice, st));
+    SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st,
+                 k_scale_cols<<<nbl, 256, 0, st>>>(n, nrhs, vc, Vb, hn));  // V_0 = r0 / beta
     C.launched();
     int nact = 0;
-    for (int c = 0; c < nrhs; c++) nact += hact[c];
+    for (int v = 0; v < nv; v++) nact += hact[v];
+    std::vector<double> hnv(nv), hrn(nv);
+    std::vector<int> take(nv, 0);
     int j = 0;
     for (; j < maxit && nact > 0 && C.rc == SPAQR_OK; j++) {
         if (j + 1 >= cap) {
             const int ncap = std::min(maxit, 2 * cap) + 1;
-            double* nv = C.alloc<double>((int64_t)ncap * n * nrhs);
-            double* nz = C.alloc<double>((int64_t)ncap * n * nrhs);
+            double* nvb = C.alloc<double>((int64_t)ncap * n * nrhs);
+            double* nzb = C.alloc<double>((int64_t)ncap * n * nrhs);
             if (C.rc) break;
-            C.cuda(cudaMemcpyAsync(nv, Vb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
-            C.cuda(cudaMemcpyAsync(nz, Zb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            C.cuda(cudaMemcpyAsync(nvb, Vb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            C.cuda(cudaMemcpyAsync(nzb, Zb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
             C.release(Vb);
             C.release(Zb);
-            Vb = nv;
-            Zb = nz;
+            Vb = nvb;
+            Zb = nzb;
             cap = ncap;
         }
         double* Vj = Vb + (int64_t)j * n * nrhs;
@@ -1242,63 +1304,77 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
         // z_j = M^{-1} v_j (kept: flexible GMRES) ; w = A z_j
         int rc = apply_device(F, nrhs, Vj, n, Zj, n, st, ws, flag);
         if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
-        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st, k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zj, n, Wv, n));
+        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st,
+                     k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zj, n, Wv, n));
         // classical Gram-Schmidt, twice
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * ((j + 1) + 1) * nrhs, st, k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h1, ldh));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 3) * nrhs, st, k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h1, ldh, Wv, active));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * ((j + 1) + 1) * nrhs, st, k_dots<<<(j + 1) * nrhs, NT, 0, st>>>(n, nrhs, Vb, j + 1, Wv, h2, ldh));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 3) * nrhs, st, k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, Vb, j + 1, h2, ldh, Wv, active));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Wv, 1, Wv, hn, 1));
-        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * nrhs, 16.0 * nrhs, st, k_sqrtv<<<1, 32, 0, st>>>(nrhs, hn));
+        const double fo = 2.0 * n * (j + 1) * nrhs;
+        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 2) * nrhs, st,
+                     k_dots<<<(j + 1) * nv, NT, 0, st>>>(n, nrhs, vc, Vb, j + 1, Wv, h1, ldh));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 3) * nrhs, st,
+                     k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, vc, Vb, j + 1, h1, ldh, Wv, active));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 2) * nrhs, st,
+                     k_dots<<<(j + 1) * nv, NT, 0, st>>>(n, nrhs, vc, Vb, j + 1, Wv, h2, ldh));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 3) * nrhs, st,
+                     k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, vc, Vb, j + 1, h2, ldh, Wv, active));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
+                     k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Wv, 1, Wv, hn, 1));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * nv, 16.0 * nv, st, k_sqrtv<<<1, 32, 0, st>>>(nv, hn));
         C.launched();
-        std::vector<double> hnv(nrhs);
-        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st, k_normalize<<<nbl, 256, 0, st>>>(n, nrhs, Wv, hn, Vb + (int64_t)(j + 1) * n * nrhs, active));
-        SPAQR_LAUNCH(KK_GMRES_SMALL, 6.0 * (j + 1) * nrhs, 16.0 * (j + 2) * nrhs, st, k_givens<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, h1, h2, hn, cs, sn, g, ldh, bn, est, active));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st,
+                     k_normalize<<<nbl, 256, 0, st>>>(n, nrhs, vc, Wv, hn, Vb + (int64_t)(j + 1) * n * nrhs, active));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 6.0 * (j + 1) * nv, 16.0 * (j + 2) * nv, st,
+                     k_givens<<<nbv, 32, 0, st>>>(nv, j, H, ldh, hstride, h1, h2, hn, cs, sn, g, ldh, bn, est,
+                                                  active));
         C.launched();
-        C.cuda(cudaMemcpyAsync(hest.data(), est, 8 * nrhs, cudaMemcpyDeviceToHost, st));
-        C.cuda(cudaMemcpyAsync(hnv.data(), hn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaMemcpyAsync(hest.data(), est, 8 * nv, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaMemcpyAsync(hnv.data(), hn, 8 * nv, cudaMemcpyDeviceToHost, st));
         C.cuda(cudaStreamSynchronize(st));
         if (C.rc) break;
         bool anyw = false;
-        for (int c = 0; c < nrhs; c++) {
-            hwant[c] = 0;
-            if (!hact[c]) continue;
-            hit[c] = j + 1;
-            if (hest[c] <= tol || hnv[c] == 0.0 || j == maxit - 1) { hwant[c] = 1; anyw = true; }
+        for (int v = 0; v < nv; v++) {
+            hwant[v] = 0;
+            if (!hact[v]) continue;
+            hit[v] = j + 1;
+            if (hest[v] <= tol || hnv[v] == 0.0 || j == maxit - 1) { hwant[v] = 1; anyw = true; }
         }
         if (!anyw) continue;
         // candidate x = x0 + Z y for the wanted columns; keep it if the
         // recomputed residual meets tol
-        C.cuda(cudaMemcpyAsync(want, hwant.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
-        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * (j + 1) * (j + 1) * nrhs, 8.0 * (j + 1) * (j + 1) * nrhs, st, k_hsolve<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, H, ldh, hstride, g, ldh, ycoef, want));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 2) * nrhs, st, k_combine<<<nbl, 256, 0, st>>>(n, nrhs, Zb, j + 1, ycoef, ldh, Zv));
-        // trial X into Wv: Wv = X0 + Zv (all columns), residual into Zv
-        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 24.0 * n * nrhs, st, k_accept<<<nbl, 256, 0, st>>>(n, nrhs, X0, n, Zv, Wv, n, want));
-        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st, k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (1) * nrhs, 8.0 * n * ((1) + 1) * nrhs, st, k_dots<<<nrhs, NT, 0, st>>>(n, nrhs, Zv, 1, Zv, rn, 1));
+        C.cuda(cudaMemcpyAsync(want, hwant.data(), 4 * nv, cudaMemcpyHostToDevice, st));
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * (j + 1) * (j + 1) * nv, 8.0 * (j + 1) * (j + 1) * nv, st,
+                     k_hsolve<<<nbv, 32, 0, st>>>(nv, j, H, ldh, hstride, g, ldh, ycoef, want));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * (j + 1) * nrhs, 8.0 * n * (j + 2) * nrhs, st,
+                     k_combine<<<nbl, 256, 0, st>>>(n, nrhs, vc, Zb, j + 1, ycoef, ldh, Zv));
+        // trial X into Wv: Wv = X0 + Zv (wanted columns), residual into Zv
+        SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 24.0 * n * nrhs, st,
+                     k_accept<<<nbl, 256, 0, st>>>(n, nrhs, vc, X0, n, Zv, Wv, n, want));
+        SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st,
+                     k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
+                     k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Zv, 1, Zv, rn, 1));
         C.launched();
-        std::vector<double> hrn(nrhs);
-        C.cuda(cudaMemcpyAsync(hrn.data(), rn, 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        C.cuda(cudaMemcpyAsync(hrn.data(), rn, 8 * nv, cudaMemcpyDeviceToHost, st));
         C.cuda(cudaStreamSynchronize(st));
         if (C.rc) break;
-        std::vector<int> take(nrhs, 0);
         bool anyt = false;
-        for (int c = 0; c < nrhs; c++) {
-            if (!hwant[c]) continue;
-            const double rr = std::sqrt(hrn[c]) / hb[c];
-            hres[c] = rr;
-            if (rr <= tol || hnv[c] == 0.0 || j == maxit - 1) {
-                take[c] = 1;
+        for (int v = 0; v < nv; v++) {
+            take[v] = 0;
+            if (!hwant[v]) continue;
+            const double rr = std::sqrt(hrn[v]) / hb[v];
+            hres[v] = rr;
+            if (rr <= tol || hnv[v] == 0.0 || j == maxit - 1) {
+                take[v] = 1;
                 anyt = true;
-                hact[c] = 0;
+                hact[v] = 0;
                 nact--;
             }
         }
         if (anyt) {
-            // dX[:, c] = Wv[:, c] for accepted columns
-            for (int c = 0; c < nrhs; c++)
-                if (take[c]) C.cuda(cudaMemcpyAsync(dX + c * lx, Wv + c * n, 8 * n, cudaMemcpyDeviceToDevice, st));
-            C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nrhs, cudaMemcpyHostToDevice, st));
+            // X[:, v] = Wv[:, v] for accepted virtual columns
+            C.cuda(cudaMemcpyAsync(taken, take.data(), 4 * nv, cudaMemcpyHostToDevice, st));
+            SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st,
+                         k_copy_taken<<<nbl, 256, 0, st>>>(n, nrhs, vc, Wv, n, dX, lx, taken));
+            C.cuda(cudaMemcpyAsync(active, hact.data(), 4 * nv, cudaMemcpyHostToDevice, st));
         }
     }
     if (!bdev) C.cuda(cudaMemcpy2DAsync(X, ldx * 8, dX, n * 8, n * 8, nrhs, cudaMemcpyDeviceToHost, st));
@@ -1308,13 +1384,33 @@ extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs
     if (C.rc) return C.rc;
     if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
     bool ok = true;
-    for (int c = 0; c < nrhs; c++) {
-        if (iters) iters[c] = hit[c];
-        if (relres) relres[c] = hres[c];
-        if (!(hres[c] <= tol)) ok = false;
+    for (int v = 0; v < nv; v++) {
+        if (iters) iters[v] = hit[v];
+        if (relres) relres[v] = hres[v];
+        if (!(hres[v] <= tol)) ok = false;
     }
     if (!ok) { set_error("GMRES did not reach tol within maxit"); return SPAQR_ERR_NOT_CONVERGED; }
     return SPAQR_OK;
+}
+
+}  // namespace
+
+extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B, int64_t ldb,
+                           double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres, void* stream) {
+    return gmres_impl(F, A, nrhs, 1, nullptr, B, ldb, X, ldx, tol, maxit, iters, relres, stream);
+}
+
+extern "C" int spaqr_gmres_batch(const spaqr_factor_t* F, const spaqr_csr* A, int count, const int64_t* part_ptr,
+                                 int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                                 int maxit, int* iters, double* relres, void* stream) {
+    if (!F || !part_ptr || count < 1) { set_error("null argument or count < 1"); return SPAQR_ERR_INVALID_ARG; }
+    if (part_ptr[0] != 0 || part_ptr[count] != F->n) {
+        set_error("part_ptr must run from 0 to the batch's n");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < count; s++)
+        if (part_ptr[s + 1] <= part_ptr[s]) { set_error("empty or decreasing part"); return SPAQR_ERR_INVALID_ARG; }
+    return gmres_impl(F, A, nrhs, count, part_ptr, B, ldb, X, ldx, tol, maxit, iters, relres, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -71,6 +71,8 @@ struct Ordering {
     }
 };
 
+int build_ordering_batch(int count, const int64_t* const* rowptrs, const int32_t* const* colinds,
+                         const int64_t* ns, const int64_t* nnzs, const int* dims_list, Ordering& o);
 int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
                    int dim, const int* dims, int nlevels, Ordering& out);
 

@@ -25,7 +25,7 @@ coefficient field a, then the velocity angle field, then right-hand sides.
 """
 import numpy as np
 
-__all__ = ["Problem", "convdiff", "config_problem", "rhs"]
+__all__ = ["Problem", "convdiff", "config_problem", "batch_problems", "rhs"]
 
 
 class Problem:
@@ -170,6 +170,26 @@ def config_problem(kind, n=None, seed=None):
     p = Problem(dims, rowptr, colind, val, seed=seed, name=f"{kind}_{n}")
     p.rng = rng
     return p
+
+
+def batch_problems(count=64, seed=4000, sides=tuple(range(32, 129, 16))):
+    """The batched workload: `count` independent 2D problems, matrix i seeded
+    with seed + i: side drawn uniformly from `sides`, a ~ U[0.1,10] per cell,
+    Pe ~ U[1,100] and v = Pe (1, 1).  Draw order per matrix: side, Pe, a."""
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.PCG64(seed + i))
+        n = int(sides[int(rng.integers(0, len(sides)))])
+        pe = float(rng.uniform(1.0, 100.0))
+        N = n * n
+        a = _uniform_a(rng, N)
+        v = np.tile([pe, pe], (N, 1))
+        rowptr, colind, val = convdiff((n, n), a, v)
+        p = Problem((n, n), rowptr, colind, val, seed=seed + i, name=f"batch{i}_{n}_pe{pe:.1f}")
+        p.rng = rng
+        p.pe = pe
+        out.append(p)
+    return out
 
 
 def rhs(problem, nrhs=1, seed=None):

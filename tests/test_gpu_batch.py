@@ -1,0 +1,109 @@
+"""Batched factorisation and GMRES on the GPU against the one-matrix path.
+
+A batch ordering + spaqr_factor on the block-diagonal CSR runs every level's
+fronts of all matrices in the same launches; each matrix's factorisation must
+be the one it gets alone: the same ranks at every level (bit for bit), the
+same preconditioner application (to rounding) and, through
+spaqr_gmres_batch, the same solutions (1e-10 relative) with every matrix's own
+residual at 1e-12.
+"""
+import numpy as np
+import pytest
+
+import paper_2010_06807_gb300 as sq
+from synth.convdiff import batch_problems, config_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(probs, precision="fp64", eps=1e-2):
+    import torch
+    dev = torch.device("cuda:0")
+    ob = sq.spaqr_order_batch([(p.rowptr, p.colind) for p in probs], [p.dims for p in probs])
+    rp, ci, v = sq.blockdiag_csr([(p.rowptr, p.colind, p.val) for p in probs])
+    csr = [torch.from_numpy(x).to(dev) for x in (rp, ci, v)]
+    F = sq.spaqr_factor(ob, *csr, eps=eps, precision=precision)
+    return ob, F, csr
+
+
+def _single(p, precision="fp64", eps=1e-2):
+    import torch
+    dev = torch.device("cuda:0")
+    o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+    csr = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+    return o, sq.spaqr_factor(o, *csr, eps=eps, precision=precision), csr
+
+
+def _probs():
+    ps = batch_problems(6, seed=4000, sides=(32, 48, 64))
+    ps.append(config_problem("2d_uniform_a", n=16, seed=5))
+    return ps
+
+
+def test_batch_ranks_equal_single(spaqr_lib):
+    probs = _probs()
+    ob, F, _ = _batch(probs)
+    singles = [_single(p)[1] for p in probs]
+    for k in range(ob.L):
+        pairs_b, _ = sq.spaqr_factor_ranks(F, k)
+        ref = []
+        for p, Fs in zip(probs, singles):
+            if k < sq.num_levels(p.n):
+                ref += [tuple(x) for x in sq.spaqr_factor_ranks(Fs, k)[0]]
+        assert sorted(tuple(x) for x in pairs_b) == sorted(ref), k
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_batch_apply_equals_single(spaqr_lib, nrhs):
+    import torch
+    probs = _probs()
+    ob, F, _ = _batch(probs)
+    rng = np.random.default_rng(11)
+    Bh = np.asfortranarray(rng.standard_normal((ob.n, nrhs)))
+    B = torch.from_numpy(np.ascontiguousarray(Bh.T)).cuda().T
+    X = sq.spaqr_solve(F, B).T.cpu().numpy().T
+    for i, p in enumerate(probs):
+        a, b = ob.part_ptr[i], ob.part_ptr[i + 1]
+        _, Fs, _ = _single(p)
+        Bs = torch.from_numpy(np.ascontiguousarray(Bh[a:b].T)).cuda().T
+        Xs = sq.spaqr_solve(Fs, Bs).T.cpu().numpy().T
+        np.testing.assert_allclose(X[a:b], Xs, rtol=0, atol=1e-12 * np.abs(Xs).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_gmres_equals_single(spaqr_lib, precision):
+    import torch
+    probs = _probs()
+    ob, F, csr = _batch(probs, precision)
+    nrhs = 2
+    rng = np.random.default_rng(12)
+    Bh = np.asfortranarray(rng.standard_normal((ob.n, nrhs)))
+    B = torch.from_numpy(np.ascontiguousarray(Bh.T)).cuda().T
+    X, it, rr = sq.spaqr_gmres_batch(F, *csr, ob.part_ptr, B, tol=1e-12)
+    assert it.shape == (nrhs, len(probs)) and (rr <= 1e-12).all()
+    X = X.T.cpu().numpy().T
+    for i, p in enumerate(probs):
+        a, b = ob.part_ptr[i], ob.part_ptr[i + 1]
+        # the matrix's own residual
+        for c in range(nrhs):
+            res = np.linalg.norm(Bh[a:b, c] - p.matvec(X[a:b, c])) / np.linalg.norm(Bh[a:b, c])
+            assert res <= 2e-12, (i, c, res)
+        _, Fs, cs = _single(p, "fp64")
+        Bs = torch.from_numpy(np.ascontiguousarray(Bh[a:b].T)).cuda().T
+        Xs, its, rrs = sq.spaqr_gmres(Fs, *cs, Bs, tol=1e-12)
+        Xs = Xs.T.cpu().numpy().T
+        d = np.linalg.norm(X[a:b] - Xs) / np.linalg.norm(Xs)
+        assert d <= 1e-10, (i, d)
+        if precision == "fp64":
+            assert (np.abs(it[:, i] - its) <= 1).all()
+
+
+def test_batch_gmres_bad_parts(spaqr_lib):
+    import torch
+    probs = _probs()[:2]
+    ob, F, csr = _batch(probs)
+    B = torch.ones(ob.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(sq.SpaqrError):
+        sq.spaqr_gmres_batch(F, *csr, np.array([0, 5, 5, ob.n]), B)
+    with pytest.raises(sq.SpaqrError):
+        sq.spaqr_gmres_batch(F, *csr, np.array([0, ob.n - 1]), B)
