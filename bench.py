@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-s", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -227,6 +229,97 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
             "relres_max": float(rr.max())}, X.clone()
 
 
+def _batched(sq, torch, np, dev, st, flush, count=64, steps=3, warmup=1):
+    """Batched workload: `count` independent 2D problems (sides from
+    {32,48,...,128}, a ~ U[0.1,10], v = Pe (1,1), Pe ~ U[1,100]), one RHS per
+    matrix.  A step factors every matrix and solves every system to 1e-12.
+    Forms: the plain FP64 path matrix by matrix; the batch in FP64 and with the
+    FP32 factor (every level's fronts of all matrices in the same launches,
+    GMRES per matrix with the application replayed as a CUDA graph).  Also
+    GMRES alone on the resident FP32 batch factor with the rule launch forms
+    and after spaqr_autotune."""
+    from synth.convdiff import batch_problems, rhs
+    probs = batch_problems(count)
+    bs = [rhs(p, 1, seed=4000 + 10 ** 6 + i)[:, 0] for i, p in enumerate(probs)]
+    out = {"count": count, "n_total": int(sum(p.n for p in probs)),
+           "sides": sorted({p.dims[0] for p in probs})}
+    # plain FP64, one matrix at a time
+    per = []
+    for p, b in zip(probs, bs):
+        A = tuple(torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val))
+        o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+        per.append((o, A, torch.from_numpy(b).to(dev)))
+
+    def plain_step():
+        for o, A, b in per:
+            F = sq.spaqr_factor(o, *A, eps=EPS, stream=st)
+            sq.spaqr_gmres(F, *A, b, tol=TOL, maxit=MAXIT, stream=st)
+            del F
+
+    t0 = time.perf_counter()
+    ob = sq.spaqr_order_batch([(p.rowptr, p.colind) for p in probs], [p.dims for p in probs])
+    out["order_ms"] = (time.perf_counter() - t0) * 1e3
+    rp, ci, va = sq.blockdiag_csr([(p.rowptr, p.colind, p.val) for p in probs])
+    Ab = tuple(torch.from_numpy(x).to(dev) for x in (rp, ci, va))
+    Bb = torch.from_numpy(np.concatenate(bs)).to(dev)
+    res = {}
+
+    def batch_step(prec, ev_mid):
+        F = sq.spaqr_factor(ob, *Ab, eps=EPS, precision=prec, stream=st)
+        ev_mid.record(st)
+        X, it, rr = sq.spaqr_gmres_batch(F, *Ab, ob.part_ptr, Bb, tol=TOL, maxit=MAXIT, stream=st)
+        res[prec] = (float(rr.max()), int(it.max()), X)
+        return F
+
+    def timed(fn):
+        """fn(ev_mid) runs one step (recording ev_mid after the factor, if
+        any); returns step and factor times over `steps` after `warmup`."""
+        tot, fac = [], []
+        for i in range(warmup + steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            em = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            F = fn(em)
+            e1.record(st)
+            e1.synchronize()
+            if i >= warmup:
+                tot.append(e0.elapsed_time(e1))
+                if F is not None:
+                    fac.append(e0.elapsed_time(em))
+            del F
+        return tot, fac
+
+    with torch.cuda.stream(st):
+        t_plain, _ = timed(lambda em: plain_step())
+        out["plain_fp64_per_matrix"] = {"solves_per_s": count * len(t_plain) / (sum(t_plain) / 1e3),
+                                        "step_ms_p50": _pct(t_plain, 50)}
+        for prec in ("fp64", "fp32"):
+            t, fac = timed(lambda em: batch_step(prec, em))
+            out[f"batched_{prec}"] = {"solves_per_s": count * len(t) / (sum(t) / 1e3), "step_ms_p50": _pct(t, 50),
+                                      "factor_ms_p50": _pct(fac, 50), "relres_max": res[prec][0],
+                                      "gmres_iters_max": res[prec][1]}
+        x64 = res["fp64"][2].cpu().numpy()
+        x32 = res["fp32"][2].cpu().numpy()
+        out["batched_fp32"]["final_error_vs_fp64"] = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))
+        # resident FP32 batch factor: GMRES alone, rule launch forms vs autotuned
+        F = sq.spaqr_factor(ob, *Ab, eps=EPS, precision="fp32", stream=st)
+        st.synchronize()
+
+        def solve_only():
+            sq.spaqr_gmres_batch(F, *Ab, ob.part_ptr, Bb, tol=TOL, maxit=MAXIT, stream=st)
+
+        t_rule, _ = timed(lambda em: solve_only())
+        ms_rule, ms_tuned = sq.spaqr_autotune(F, 1, stream=st)
+        t_tuned, _ = timed(lambda em: solve_only())
+        out["resident_fp32_gmres"] = {"rule_solves_per_s": count * len(t_rule) / (sum(t_rule) / 1e3),
+                                      "tuned_solves_per_s": count * len(t_tuned) / (sum(t_tuned) / 1e3),
+                                      "apply_ms_rule": ms_rule, "apply_ms_tuned": ms_tuned}
+        del F
+    return out
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -282,7 +375,6 @@ def ours(a):
         clocks.start()
         time.sleep(0.3)
         sq.spaqr_stats_reset()
-        sq.spaqr_profile(True)
         fac_ms, gm_ms, step_ms, iters, relres = [], [], [], [], []
         for _ in range(a.steps):
             flush.zero_()                                   # evict L2 between steps
@@ -301,9 +393,21 @@ def ours(a):
             info = sq.spaqr_factor_info(F)
             del F
         torch.cuda.synchronize(dev)
-        sq.spaqr_profile(False)
-        launches, kstats = sq.spaqr_stats()
+        launches, _ = sq.spaqr_stats()
         clk = clocks.stop()
+        # per-kernel CUDA-event times from a separate profiled pass (profiling
+        # brackets every launch with events and turns graph replay off, so the
+        # timed steps above run without it)
+        sq.spaqr_stats_reset()
+        sq.spaqr_profile(True)
+        for _ in range(3):
+            flush.zero_()
+            ev_mid = torch.cuda.Event(enable_timing=True)
+            F, _, _ = step()
+            del F
+        torch.cuda.synchronize(dev)
+        sq.spaqr_profile(False)
+        _, kstats = sq.spaqr_stats()
     total_s = sum(step_ms) / 1e3
     if world > 1:
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
@@ -377,6 +481,7 @@ def ours(a):
         "e2e": {"value": NRHS * a.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "gpu_launches_note": "kernels of ours launched in the timed steps, graph replays counted per kernel",
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kstats.items()
                     if v["launches"]},
         "roofline": roof,
@@ -403,6 +508,13 @@ def ours(a):
     c32["final_error_vs_fp64"] = float(np.max(np.linalg.norm(x32.cpu().numpy() - x64, axis=0) /
                                               np.linalg.norm(x64, axis=0)))
     line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
+    line["batched_64x2d"] = _batched(sq, torch, np, dev, st, flush)
+    if not a.no_serve:
+        from paper_2010_06807_gb300.serve import run_workload
+        srv = {}
+        for prec in ("fp32", "fp64"):
+            srv[prec] = run_workload(duration=a.serve_s, precision=prec, device=dev)
+        line["serving_8x3d_poisson2000"] = srv
     if not a.no_cpu_baseline:
         try:
             r = run_oracle(1)

@@ -256,6 +256,31 @@ int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, doubl
 
 void spaqr_factor_destroy(spaqr_factor_t* F);
 
+/* Autotuner of the factor application for nrhs right-hand sides.  Every
+ * unit of the application (the fronts of one colour of a level forward, the
+ * scale-sparsify step of a level forward and backward, the fronts of a level
+ * backward) has two launch forms: one CTA per front / interface, or one
+ * thread-block cluster per front / interface (with the R_sj products as
+ * separate tiles).  The tuner times both forms of every unit on this factor
+ * (CUDA events, best of three runs from the same workspace snapshot, on
+ * stream), keeps the faster, and times whole applications with the untuned
+ * rules and with the table (*ms_rule, *ms_tuned; may be NULL).  The table is
+ * stored in F and used by later spaqr_solve / spaqr_gmres calls with the
+ * same nrhs if it is faster than the rules; the results do not depend on the
+ * forms chosen beyond rounding.  Must not run concurrently with another call
+ * on F.  Synchronises the stream.  Errors: INVALID_ARG (profiling on, bad
+ * arguments), OOM, CUDA.  (Launch-form tuning is ours; the paper has no
+ * counterpart.) */
+int spaqr_autotune(spaqr_factor_t* F, int nrhs, void* stream, double* ms_rule, double* ms_tuned);
+
+/* Process-wide switch (default on): spaqr_gmres / spaqr_gmres_batch run on a
+ * private non-blocking stream ordered after the caller's stream, and capture
+ * the factor application of an iteration once per call as a CUDA graph that
+ * every iteration replays (the same kernels with the same arguments, so the
+ * results are identical).  Off, or while profiling is on, every iteration
+ * launches the kernels directly on the caller's stream. */
+void spaqr_use_graphs(int on);
+
 /* Kernel launch statistics (process wide).  The paper reports the runtime of
  * every level split into factorize / scale / sparsify / merge (Section 4,
  * "runtime per level" figure); these counters refine that split per kernel.

@@ -19,7 +19,7 @@ __all__ = [
     "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
-    "spaqr_stats_reset", "spaqr_profile", "spaqr_stats",
+    "spaqr_stats_reset", "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -81,7 +81,7 @@ EXPORTS = [
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
-    "spaqr_profile", "spaqr_stats",
+    "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
 ]
 
 
@@ -121,6 +121,9 @@ def load_library(path=None):
         lib.spaqr_stats_reset.restype = None
         lib.spaqr_profile.argtypes = [i32]
         lib.spaqr_profile.restype = None
+        lib.spaqr_use_graphs.argtypes = [i32]
+        lib.spaqr_use_graphs.restype = None
+        lib.spaqr_autotune.argtypes = [vp, i32, vp, vp, vp]
         lib.spaqr_stats.argtypes = [ctypes.POINTER(_KStat), i32, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64)]
     if path is None:
@@ -488,6 +491,22 @@ def spaqr_profile(on=True):
     """Bracket every library launch with CUDA events (for per-kernel timing)."""
     load_library()
     _lib.spaqr_profile(1 if on else 0)
+
+
+def spaqr_autotune(F, nrhs, stream=None):
+    """Time the launch forms of every unit of the application for nrhs
+    columns and keep the fastest (spaqr_autotune).  Returns (ms_rule, ms_tuned)."""
+    load_library()
+    a = ctypes.c_double(0.0)
+    b = ctypes.c_double(0.0)
+    _check(_lib.spaqr_autotune(F._h, int(nrhs), _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def spaqr_use_graphs(on=True):
+    """Replay the factor application inside GMRES as a CUDA graph (default on)."""
+    load_library()
+    _lib.spaqr_use_graphs(1 if on else 0)
 
 
 def spaqr_stats():

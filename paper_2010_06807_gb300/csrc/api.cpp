@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -158,7 +159,22 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 
+thread_local LaunchTally* tl_capture = nullptr;
+
+void prof_capture_begin(LaunchTally* t) {
+    std::memset(t, 0, sizeof(*t));
+    tl_capture = t;
+}
+
+void prof_capture_end() { tl_capture = nullptr; }
+
 int prof_begin(void* stream, int kind, double flops, double bytes) {
+    if (tl_capture) {   // recorded into a graph: counted when it is replayed
+        tl_capture->count[kind]++;
+        tl_capture->flops[kind] += flops;
+        tl_capture->bytes[kind] += bytes;
+        return -1;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     g_launches++;
     g_count[kind]++;
@@ -181,6 +197,25 @@ void prof_end(void* stream, int rec) {
     if (rec < (int)g_recs.size()) cudaEventRecord(g_recs[rec].b, (cudaStream_t)stream);
 }
 
+
+void prof_add_tally(const LaunchTally& t, int sign) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < KK_COUNT; k++) {
+        g_count[k] += sign * t.count[k];
+        g_launches += sign * t.count[k];
+        g_flops[k] += sign * t.flops[k];
+        g_bytes[k] += sign * t.bytes[k];
+    }
+}
+
+bool prof_on() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_prof;
+}
+
+std::atomic<bool> g_graphs{true};
+bool graphs_on() { return g_graphs.load(); }
+
 void prof_add(int rec, int kind, double flops, double bytes) {
     (void)rec;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -201,6 +236,8 @@ extern "C" void spaqr_stats_reset(void) {
     g_launches = 0;
     for (int k = 0; k < KK_COUNT; k++) { g_count[k] = 0; g_ms[k] = g_flops[k] = g_bytes[k] = 0.0; }
 }
+
+extern "C" void spaqr_use_graphs(int on) { spaqr::g_graphs.store(on != 0); }
 
 extern "C" void spaqr_profile(int on) {
     std::lock_guard<std::mutex> lk(spaqr::g_mu);

@@ -885,8 +885,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             LV.ff_maxm[c] = mm;
             LV.ff_wide[c] = (b > a && b - a <= kWideFronts && mm >= kWideMinM) ? 1 : 0;
         }
+        // R_sj tiles are planned for every level (the autotuner may pick the
+        // wide backward form anywhere); bwd_wide is the untuned rule
         LV.bwd_wide = LV.nfront > 0 && LV.nfront <= kWideFronts && LV.max_front_n >= kWideMinN;
-        if (LV.bwd_wide) {
+        LV.bwd_tiles = LV.nfront > 0;
+        if (LV.bwd_tiles) {
             LV.tile_begin = (int)tiles.size();
             LV.wf_begin = (int)wfr.size();
             int64_t zrows = 0;

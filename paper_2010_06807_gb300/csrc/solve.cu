@@ -930,162 +930,270 @@ static bool wide_split(int units, int nrhs, Smem smem, int& qs, int& split) {
     return true;
 }
 
+enum { kChoiceRule = 0, kChoiceNarrow = 1, kChoiceWide = 2 };
+
+// One application in flight: the factor, right-hand-side count, stream and
+// workspace.
+template <class real>
+struct ApplyCtx {
+    const spaqr_factor_s* F;
+    int nrhs;
+    cudaStream_t st;
+    real* ws;
+    int* singular;
+    int64_t esz;
+    const SolveFront<real>* dfr;
+    const SolveSS<real>* dss;
+    const SolveRsj<real>* drsj;
+    ApplyCtx(const spaqr_factor_s* F_, int nrhs_, cudaStream_t st_, real* ws_, int* sg)
+        : F(F_), nrhs(nrhs_), st(st_), ws(ws_), singular(sg), esz((int64_t)sizeof(real)),
+          dfr(static_cast<const SolveFront<real>*>(F_->d_fronts)), dss(static_cast<const SolveSS<real>*>(F_->d_ss)),
+          drsj(static_cast<const SolveRsj<real>*>(F_->d_rsj)) {}
+    real* level(int k) const { return ws + F->lv[k].ws_off * nrhs; }
+};
+
+// Forward fronts of colour c at level k.
+template <class real>
+void launch_ff(const ApplyCtx<real>& A, int k, int c, int choice) {
+    const spaqr_factor_s* F = A.F;
+    const SolveLevelHost& LV = F->lv[k];
+    const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
+    if (b <= a) return;
+    const int nrhs = A.nrhs;
+    const int64_t esz = A.esz;
+    cudaStream_t st = A.st;
+    real* Y = A.level(k);
+    const int64_t ldy = LV.rows;
+    const bool wide = choice == kChoiceWide ||
+                      (choice == kChoiceRule && LV.ff_wide[c] && narrow_ctas(b - a, nrhs) < kNumSM);
+    if (wide) {
+        const int slab = wide_slab_rows(LV.ff_maxm[c], kWideCS);
+        int qs, split;
+        if (wide_split(b - a, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+            SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
+                         with_q(qs, [&](auto QC) {
+                             k_sfront_fwd_wide<real, kWideCS, QC.value>
+                                 <<<dim3((b - a) * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                     A.dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
+                         }));
+            return;
+        }
+    }
+    const int rmap_d = (LV.max_front_m + 1) / 2 + 1;
+    const int split = rhs_split(b - a, nrhs);
+    const int qs = (nrhs + split - 1) / split;
+    const int staged = rmap_d * 8 + staged_smem_elems(LV.max_front_m, qs) * esz <= kSmemMax;
+    const size_t smem =
+        (size_t)rmap_d * 8 + (size_t)(staged ? staged_smem_elems(LV.max_front_m, qs) : 2 * NB * qs + NT) * esz;
+    SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
+                 k_sfront_fwd<real><<<dim3(b - a, split), NT, smem, st>>>(A.dfr + LV.front_begin + a, F->d_segs, Y,
+                                                                          ldy, nrhs, qs, rmap_d, staged));
+}
+
+// Scale + sparsify of level k's surviving clusters, forward (fwd) or backward.
+template <class real>
+void launch_ss(const ApplyCtx<real>& A, int k, bool fwd, int choice) {
+    const spaqr_factor_s* F = A.F;
+    const SolveLevelHost& LV = F->lv[k];
+    if (LV.nss <= 0) return;
+    const SolveLevelHost& LN = F->lv[k + 1];
+    const int nrhs = A.nrhs;
+    const int64_t esz = A.esz;
+    cudaStream_t st = A.st;
+    real* Y = A.level(k);
+    real* Yn = A.level(k + 1);
+    const int64_t ldy = LV.rows;
+    const double fl = fwd ? LV.ssf_flops : LV.ssb_flops, fx = fwd ? LV.ssf_fixed : LV.ssb_fixed,
+                 fv = fwd ? LV.ssf_vec : LV.ssb_vec;
+    const int kind = fwd ? KK_SOLVE_SS_FWD : KK_SOLVE_SS_BWD;
+    const bool wide = LV.max_ss_n >= kWideMinN &&
+                      (choice == kChoiceWide || (choice == kChoiceRule && narrow_ctas(LV.nss, nrhs) < kNumSM));
+    if (wide) {
+        const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
+        int qs, split;
+        if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+            const size_t smem = wide_smem(slab, qs, (int)esz);
+            SPAQR_LAUNCH(kind, fl * nrhs, fx * split + fv * nrhs, st, with_q(qs, [&](auto QC) {
+                             if (fwd)
+                                 k_sss_fwd_wide<real, kWideCS, QC.value><<<dim3(LV.nss * kWideCS, split), NT, smem,
+                                                                           st>>>(A.dss + LV.ss_begin, Y, ldy, Yn,
+                                                                                 LN.rows, nrhs, qs, slab);
+                             else
+                                 k_sss_bwd_wide<real, kWideCS, QC.value><<<dim3(LV.nss * kWideCS, split), NT, smem,
+                                                                           st>>>(A.dss + LV.ss_begin, Y, ldy, Yn,
+                                                                                 LN.rows, nrhs, qs, slab);
+                         }));
+            return;
+        }
+    }
+    const int split = rhs_split(LV.nss, nrhs);
+    const int qs = (nrhs + split - 1) / split;
+    const int staged = staged_smem_elems(LV.max_ss_n, qs) * esz <= kSmemMax;
+    const size_t smem = (size_t)(staged ? staged_smem_elems(LV.max_ss_n, qs) : 2 * NB * qs + NT) * esz;
+    if (fwd)
+        SPAQR_LAUNCH(kind, fl * nrhs, fx * split + fv * nrhs, st,
+                     k_sss_fwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(A.dss + LV.ss_begin, Y, ldy, Yn, LN.rows,
+                                                                            nrhs, qs, staged));
+    else
+        SPAQR_LAUNCH(kind, fl * nrhs, fx * split + fv * nrhs, st,
+                     k_sss_bwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(A.dss + LV.ss_begin, Y, ldy, Yn, LN.rows,
+                                                                            nrhs, qs, staged, A.singular));
+}
+
+// Backward fronts of level k.
+template <class real>
+void launch_fb(const ApplyCtx<real>& A, int k, int choice) {
+    const spaqr_factor_s* F = A.F;
+    const SolveLevelHost& LV = F->lv[k];
+    if (LV.nfront <= 0) return;
+    const int nrhs = A.nrhs;
+    const int64_t esz = A.esz;
+    cudaStream_t st = A.st;
+    real* Y = A.level(k);
+    const int64_t ldy = LV.rows;
+    const bool wide = LV.bwd_tiles && (choice == kChoiceWide || (choice == kChoiceRule && LV.bwd_wide));
+    if (wide) {
+        const int slab = wide_slab_rows(LV.max_front_n, kWideCS);
+        int qs, split;
+        if (wide_split(LV.nfront, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+            real* Zp = A.ws + F->zp_off * nrhs;
+            const int64_t ldz = F->zp_rows;
+            if (LV.ntile > 0) {
+                int tsplit = std::max((nrhs + kTileQ - 1) / kTileQ,
+                                      std::min(nrhs, (2 * kNumSM + LV.ntile - 1) / LV.ntile));
+                const int tq = (nrhs + tsplit - 1) / tsplit;
+                tsplit = (nrhs + tq - 1) / tq;
+                SPAQR_LAUNCH(KK_SOLVE_RSJ, LV.rt_flops * nrhs, LV.rt_fixed * tsplit + LV.rt_vec * nrhs, st,
+                             with_q(tq, [&](auto QC) {
+                                 k_rsj_tiles<real, QC.value><<<dim3(LV.ntile, tsplit), NT, 0, st>>>(
+                                     static_cast<const RsjTile*>(F->d_tiles) + LV.tile_begin,
+                                     static_cast<const SolveRsj<real>*>(F->d_pieces), A.dfr, Y, ldy, Zp, ldz, nrhs,
+                                     tq);
+                             }));
+            }
+            SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, (LV.fb_flops - LV.rt_flops) * nrhs,
+                         (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st, with_q(qs, [&](auto QC) {
+                             k_sfront_bwd_wide<real, kWideCS, QC.value>
+                                 <<<dim3(LV.nfront * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                     static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, A.dfr, F->d_segs, Y,
+                                     ldy, Zp, ldz, nrhs, qs, slab);
+                         }));
+            return;
+        }
+    }
+    const int split = rhs_split(LV.nfront, nrhs);
+    const int qs = (nrhs + split - 1) / split;
+    SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed * split + LV.fb_vec * nrhs, st,
+                 k_sfront_bwd<real><<<dim3(LV.nfront, split), NT, 0, st>>>(A.dfr + LV.front_begin, F->d_segs, A.drsj,
+                                                                           Y, ldy, nrhs, qs, A.singular));
+}
+
+// X = M^{-1} B: forward over the levels, then backward, with the launch
+// forms of `tt` (null: the rules).
 template <class real>
 int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
-                   cudaStream_t st, real* ws, int* singular) {
+                   cudaStream_t st, real* ws, int* singular, const TuneTable* tt) {
     set_solve_attrs<real>();
-    const int64_t esz = (int64_t)sizeof(real);
-    const SolveFront<real>* dfr = static_cast<const SolveFront<real>*>(F->d_fronts);
-    const SolveSS<real>* dss = static_cast<const SolveSS<real>*>(F->d_ss);
-    const SolveRsj<real>* drsj = static_cast<const SolveRsj<real>*>(F->d_rsj);
+    const ApplyCtx<real> A(F, nrhs, st, ws, singular);
     const int64_t n = F->n;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    real* Y0 = ws + F->lv[0].ws_off * nrhs;
+    real* Y0 = A.level(0);
     SPAQR_LAUNCH(KK_SOLVE_PERM, 0.0, 8.0 * n + 16.0 * n * nrhs, st,
                  k_perm_in<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows));
     const int L = F->L;
     for (int k = 0; k < L; k++) {
         const SolveLevelHost& LV = F->lv[k];
-        real* Y = ws + LV.ws_off * nrhs;
-        const int64_t ldy = LV.rows;
-        if (LV.nfront > 0) {
-            const int rmap_d = (LV.max_front_m + 1) / 2 + 1;
-            for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
-                const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
-                if (b <= a) continue;
-                if (LV.ff_wide[c] && narrow_ctas(b - a, nrhs) < kNumSM) {
-                    const int slab = wide_slab_rows(LV.ff_maxm[c], kWideCS);
-                    int qs, split;
-                    if (wide_split(b - a, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
-                        SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs,
-                                     LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
-                                     with_q(qs, [&](auto QC) {
-                                         k_sfront_fwd_wide<real, kWideCS, QC.value>
-                                             <<<dim3((b - a) * kWideCS, split), NT, wide_smem(slab, qs, (int)esz),
-                                                st>>>(dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
-                                     }));
-                        continue;
-                    }
-                }
-                const int split = rhs_split(b - a, nrhs);
-                const int qs = (nrhs + split - 1) / split;
-                const int staged = rmap_d * 8 + staged_smem_elems(LV.max_front_m, qs) * esz <= kSmemMax;
-                const size_t smem = (size_t)rmap_d * 8 +
-                                    (size_t)(staged ? staged_smem_elems(LV.max_front_m, qs) : 2 * NB * qs + NT) * esz;
-                SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs,
-                             st,
-                             k_sfront_fwd<real><<<dim3(b - a, split), NT, smem, st>>>(dfr + LV.front_begin + a,
-                                                                                F->d_segs, Y, ldy, nrhs, qs, rmap_d,
-                                                                                staged));
-            }
-        }
-        if (LV.nss > 0 && LV.max_ss_n >= kWideMinN && narrow_ctas(LV.nss, nrhs) < kNumSM) {
-            const SolveLevelHost& LN = F->lv[k + 1];
-            const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
-            int qs, split;
-            if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
-                SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed * split + LV.ssf_vec * nrhs, st,
-                             with_q(qs, [&](auto QC) {
-                                 k_sss_fwd_wide<real, kWideCS, QC.value>
-                                     <<<dim3(LV.nss * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
-                                         dss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, qs, slab);
-                             }));
-                continue;
-            }
-        }
-        if (LV.nss > 0) {
-            const SolveLevelHost& LN = F->lv[k + 1];
-            const int split = rhs_split(LV.nss, nrhs);
-            const int qs = (nrhs + split - 1) / split;
-            const int staged = staged_smem_elems(LV.max_ss_n, qs) * esz <= kSmemMax;
-            const size_t smem = (size_t)(staged ? staged_smem_elems(LV.max_ss_n, qs) : 2 * NB * qs + NT) * esz;
-            SPAQR_LAUNCH(KK_SOLVE_SS_FWD, LV.ssf_flops * nrhs, LV.ssf_fixed * split + LV.ssf_vec * nrhs, st,
-                         k_sss_fwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(dss + LV.ss_begin, Y, ldy,
-                                                                          ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
-                                                                          staged));
-        }
+        for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) launch_ff(A, k, (int)c, tt ? tt->ff[k][c] : 0);
+        launch_ss(A, k, true, tt ? tt->ssf[k] : 0);
     }
     for (int k = L - 1; k >= 0; k--) {
-        const SolveLevelHost& LV = F->lv[k];
-        real* Y = ws + LV.ws_off * nrhs;
-        const int64_t ldy = LV.rows;
-        bool ss_done = false;
-        if (LV.nss > 0 && LV.max_ss_n >= kWideMinN && narrow_ctas(LV.nss, nrhs) < kNumSM) {
-            const SolveLevelHost& LN = F->lv[k + 1];
-            const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
-            int qs, split;
-            if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
-                SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed * split + LV.ssb_vec * nrhs, st,
-                             with_q(qs, [&](auto QC) {
-                                 k_sss_bwd_wide<real, kWideCS, QC.value>
-                                     <<<dim3(LV.nss * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
-                                         dss + LV.ss_begin, Y, ldy, ws + LN.ws_off * nrhs, LN.rows, nrhs, qs, slab);
-                             }));
-                ss_done = true;
-            }
-        }
-        if (LV.nss > 0 && !ss_done) {
-            const SolveLevelHost& LN = F->lv[k + 1];
-            const int split = rhs_split(LV.nss, nrhs);
-            const int qs = (nrhs + split - 1) / split;
-            const int staged = staged_smem_elems(LV.max_ss_n, qs) * esz <= kSmemMax;
-            const size_t smem = (size_t)(staged ? staged_smem_elems(LV.max_ss_n, qs) : 2 * NB * qs + NT) * esz;
-            SPAQR_LAUNCH(KK_SOLVE_SS_BWD, LV.ssb_flops * nrhs, LV.ssb_fixed * split + LV.ssb_vec * nrhs, st,
-                         k_sss_bwd<real><<<dim3(LV.nss, split), NT, smem, st>>>(dss + LV.ss_begin, Y, ldy,
-                                                                          ws + LN.ws_off * nrhs, LN.rows, nrhs, qs,
-                                                                          staged, singular));
-        }
-        if (LV.nfront > 0 && LV.bwd_wide) {
-            const int slab = wide_slab_rows(LV.max_front_n, kWideCS);
-            int qs, split;
-            if (wide_split(LV.nfront, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
-                real* Zp = ws + F->zp_off * nrhs;
-                const int64_t ldz = F->zp_rows;
-                if (LV.ntile > 0) {
-                    int tsplit = std::max((nrhs + kTileQ - 1) / kTileQ,
-                                          std::min(nrhs, (2 * kNumSM + LV.ntile - 1) / LV.ntile));
-                    const int tq = (nrhs + tsplit - 1) / tsplit;
-                    tsplit = (nrhs + tq - 1) / tq;
-                    SPAQR_LAUNCH(KK_SOLVE_RSJ, LV.rt_flops * nrhs, LV.rt_fixed * tsplit + LV.rt_vec * nrhs, st,
-                                 with_q(tq, [&](auto QC) {
-                                     k_rsj_tiles<real, QC.value><<<dim3(LV.ntile, tsplit), NT, 0, st>>>(
-                                         static_cast<const RsjTile*>(F->d_tiles) + LV.tile_begin,
-                                         static_cast<const SolveRsj<real>*>(F->d_pieces), dfr, Y, ldy, Zp, ldz, nrhs,
-                                         tq);
-                                 }));
-                }
-                SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, (LV.fb_flops - LV.rt_flops) * nrhs,
-                             (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st,
-                             with_q(qs, [&](auto QC) {
-                                 k_sfront_bwd_wide<real, kWideCS, QC.value>
-                                     <<<dim3(LV.nfront * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
-                                         static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, dfr, F->d_segs, Y,
-                                         ldy, Zp, ldz, nrhs, qs, slab);
-                             }));
-                continue;
-            }
-        }
-        if (LV.nfront > 0) {
-            const int split = rhs_split(LV.nfront, nrhs);
-            const int qs = (nrhs + split - 1) / split;
-            SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, LV.fb_flops * nrhs, LV.fb_fixed * split + LV.fb_vec * nrhs, st,
-                         k_sfront_bwd<real><<<dim3(LV.nfront, split), NT, 0, st>>>(dfr + LV.front_begin, F->d_segs,
-                                                                                   drsj, Y, ldy, nrhs, qs, singular));
-        }
+        launch_ss(A, k, false, tt ? tt->ssb[k] : 0);
+        launch_fb(A, k, tt ? tt->fb[k] : 0);
     }
     SPAQR_LAUNCH(KK_SOLVE_PERM, 1.0 * n * nrhs, 16.0 * n + 16.0 * n * nrhs, st,
                  k_perm_out<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
     return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
 }
 
+// Times the application's units one at a time on this factor (each form of a
+// unit three times from the same workspace snapshot, the fastest kept) and
+// returns the table of the fastest forms.  The workspace must hold the level
+// vectors of a completed application.
+template <class real>
+int autotune_t(const spaqr_factor_s* F, int nrhs, cudaStream_t st, real* ws, real* snap, int* singular,
+               TuneTable& tt) {
+    set_solve_attrs<real>();
+    const ApplyCtx<real> A(F, nrhs, st, ws, singular);
+    const size_t wbytes = (size_t)F->ws_rows * nrhs * sizeof(real);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SPAQR_ERR_CUDA;
+    auto time_unit = [&](auto&& launch) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaMemcpyAsync(ws, snap, wbytes, cudaMemcpyDeviceToDevice, st);
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            if (cudaGetLastError() != cudaSuccess) return 1e30f;   // form not launchable here
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    auto pick = [&](auto&& launch_with) {
+        const float tn = time_unit([&] { launch_with(kChoiceNarrow); });
+        const float tw = time_unit([&] { launch_with(kChoiceWide); });
+        return (uint8_t)(tw < tn ? kChoiceWide : kChoiceNarrow);
+    };
+    const int L = F->L;
+    tt.nrhs = nrhs;
+    tt.ff.assign(L, {});
+    tt.ssf.assign(L, 0);
+    tt.ssb.assign(L, 0);
+    tt.fb.assign(L, 0);
+    for (int k = 0; k < L; k++) {
+        const SolveLevelHost& LV = F->lv[k];
+        tt.ff[k].assign(LV.colour_ptr.size() > 0 ? LV.colour_ptr.size() - 1 : 0, 0);
+        for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++)
+            tt.ff[k][c] = pick([&](int ch) { launch_ff(A, k, (int)c, ch); });
+        if (LV.nss > 0) {
+            tt.ssf[k] = pick([&](int ch) { launch_ss(A, k, true, ch); });
+            tt.ssb[k] = pick([&](int ch) { launch_ss(A, k, false, ch); });
+        }
+        if (LV.nfront > 0) tt.fb[k] = pick([&](int ch) { launch_fb(A, k, ch); });
+    }
+    cudaMemcpyAsync(ws, snap, wbytes, cudaMemcpyDeviceToDevice, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
+}
+
 // X = M^{-1} B with B, X device pointers (FP64, n x nrhs, leading dims) in the
 // factor's precision; `ws` holds ws_rows * nrhs elements of that type.
 // Stream-ordered, no synchronisation.
+int apply_with(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+               cudaStream_t st, void* ws, int* singular, const TuneTable* tt) {
+    if (F->precision == SPAQR_FP32)
+        return apply_device_t<float>(F, nrhs, B, ldb, X, ldx, st, static_cast<float*>(ws), singular, tt);
+    return apply_device_t<double>(F, nrhs, B, ldb, X, ldx, st, static_cast<double*>(ws), singular, tt);
+}
+
+__global__ void k_fill_pattern(int64_t m, double* B) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 29;
+    B[i] = (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;   // in [-1, 1)
+}
+
 int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
                  cudaStream_t st, void* ws, int* singular) {
+    const std::shared_ptr<const TuneTable> tt = F->tune_for(nrhs);
     if (F->precision == SPAQR_FP32)
-        return apply_device_t<float>(F, nrhs, B, ldb, X, ldx, st, static_cast<float*>(ws), singular);
-    return apply_device_t<double>(F, nrhs, B, ldb, X, ldx, st, static_cast<double*>(ws), singular);
+        return apply_device_t<float>(F, nrhs, B, ldb, X, ldx, st, static_cast<float*>(ws), singular, tt.get());
+    return apply_device_t<double>(F, nrhs, B, ldb, X, ldx, st, static_cast<double*>(ws), singular, tt.get());
 }
 
 }  // namespace spaqr
@@ -1145,6 +1253,65 @@ extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, i
 
 namespace {
 
+// The factor application of one GMRES iteration as a CUDA graph: captured
+// once per GMRES call with fixed input / output buffers, replayed every
+// iteration (the launches it holds are counted at every replay).
+struct ApplyGraph {
+    cudaGraphExec_t exec = nullptr;
+    LaunchTally tally;
+    ~ApplyGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+bool capture_apply(const spaqr_factor_s* F, int nrhs, const double* Vin, double* Zout, cudaStream_t st, void* ws,
+                   int* flag, ApplyGraph& g) {
+    if (F->precision == SPAQR_FP32) set_solve_attrs<float>();
+    else set_solve_attrs<double>();
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    prof_capture_begin(&g.tally);
+    const int rc = apply_device(F, nrhs, Vin, F->n, Zout, F->n, st, ws, flag);
+    prof_capture_end();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    bool ok = rc == SPAQR_OK && e == cudaSuccess && graph != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        g.exec = nullptr;
+    }
+    return ok;
+}
+
+// A private non-blocking stream for one call, ordered after the caller's
+// stream: graphs cannot be captured on the legacy default stream.
+struct PrivateStream {
+    cudaStream_t s = nullptr;
+    bool init(cudaStream_t user) {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s = nullptr;
+            return false;
+        }
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); return false; }
+        cudaEventRecord(ev, user);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        return true;
+    }
+    ~PrivateStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+
 // Right-preconditioned flexible GMRES over virtual columns (see VCols):
 // nseg = 1 for one matrix, nseg = count for a block-diagonal batch with
 // segment row offsets seg_ptr (host).  iters / relres per virtual column
@@ -1158,8 +1325,11 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         return SPAQR_ERR_INVALID_ARG;
     }
     if (nrhs == 0) return SPAQR_OK;
+    const bool graphs = graphs_on() && !prof_on();
+    PrivateStream ps;   // destroyed after C, whose frees are ordered on it
+    if (graphs && !ps.init((cudaStream_t)stream)) { set_error("stream creation failed"); return SPAQR_ERR_CUDA; }
     SCtx C;
-    C.st = (cudaStream_t)stream;
+    C.st = graphs ? ps.s : (cudaStream_t)stream;
     cudaStream_t st = C.st;
     const int64_t n = F->n, nnz = A->nnz;
     const int nv = nrhs * nseg;
@@ -1240,6 +1410,16 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
     double* Zb = C.alloc<double>((int64_t)cap * n * nrhs);   // Z_j = M^{-1} V_j (flexible GMRES)
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    ApplyGraph ag;
+    double* Vin = nullptr;
+    double* Zout = nullptr;
+    bool use_graph = false;
+    if (graphs) {
+        Vin = C.alloc<double>(n * nrhs);
+        Zout = C.alloc<double>(n * nrhs);
+        if (C.rc) return C.rc;
+        use_graph = capture_apply(F, nrhs, Vin, Zout, st, ws, flag, ag);
+    }
     C.cuda(cudaMemsetAsync(H, 0, sizeof(double) * hstride * nv, st));
     C.cuda(cudaMemsetAsync(g, 0, sizeof(double) * ldh * nv, st));
     // X0 = X; r0 = B - A X0 (into V_0); beta = ||r0||; ||b||
@@ -1302,8 +1482,15 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         double* Vj = Vb + (int64_t)j * n * nrhs;
         double* Zj = Zb + (int64_t)j * n * nrhs;
         // z_j = M^{-1} v_j (kept: flexible GMRES) ; w = A z_j
-        int rc = apply_device(F, nrhs, Vj, n, Zj, n, st, ws, flag);
-        if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
+        if (use_graph) {
+            C.cuda(cudaMemcpyAsync(Vin, Vj, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            C.cuda(cudaGraphLaunch(ag.exec, st));
+            C.cuda(cudaMemcpyAsync(Zj, Zout, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            prof_add_tally(ag.tally, 1);
+        } else {
+            int rc = apply_device(F, nrhs, Vj, n, Zj, n, st, ws, flag);
+            if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); break; }
+        }
         SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 8.0 * n) * nrhs, st,
                      k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zj, n, Wv, n));
         // classical Gram-Schmidt, twice
@@ -1411,6 +1598,74 @@ extern "C" int spaqr_gmres_batch(const spaqr_factor_t* F, const spaqr_csr* A, in
     for (int s = 0; s < count; s++)
         if (part_ptr[s + 1] <= part_ptr[s]) { set_error("empty or decreasing part"); return SPAQR_ERR_INVALID_ARG; }
     return gmres_impl(F, A, nrhs, count, part_ptr, B, ldb, X, ldx, tol, maxit, iters, relres, stream);
+}
+
+extern "C" int spaqr_autotune(spaqr_factor_t* F, int nrhs, void* stream, double* ms_rule, double* ms_tuned) {
+    if (!F || nrhs < 1) { set_error("null factor or nrhs < 1"); return SPAQR_ERR_INVALID_ARG; }
+    if (prof_on()) { set_error("autotuning needs profiling off"); return SPAQR_ERR_INVALID_ARG; }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != F->device) cudaSetDevice(F->device);
+    SCtx C;
+    C.st = (cudaStream_t)stream;
+    cudaStream_t st = C.st;
+    const int64_t n = F->n;
+    const int64_t wdbl = (F->ws_rows * nrhs * F->esz + 7) / 8;
+    double* ws = C.alloc<double>(wdbl);
+    double* snap = C.alloc<double>(wdbl);
+    double* B = C.alloc<double>(n * nrhs);
+    double* X = C.alloc<double>(n * nrhs);
+    int* flag = C.alloc<int>(1);
+    if (C.rc) return C.rc;
+    C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_fill_pattern<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, st>>>(n * nrhs, B);
+    C.launched();
+    // one application by the rules fills the level vectors
+    int rc = apply_with(F, nrhs, B, n, X, n, st, ws, flag, nullptr);
+    if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); return C.rc ? C.rc : rc; }
+    C.cuda(cudaMemcpyAsync(snap, ws, sizeof(double) * wdbl, cudaMemcpyDeviceToDevice, st));
+    auto tt = std::make_shared<TuneTable>();
+    rc = F->precision == SPAQR_FP32
+             ? autotune_t<float>(F, nrhs, st, (float*)ws, (float*)snap, flag, *tt)
+             : autotune_t<double>(F, nrhs, st, ws, snap, flag, *tt);
+    if (rc != SPAQR_OK) { set_error("autotuning launch failed"); return rc; }
+    // whole applications, rules vs table (best of three)
+    cudaEvent_t e0, e1;
+    C.cuda(cudaEventCreate(&e0));
+    C.cuda(cudaEventCreate(&e1));
+    if (C.rc) return C.rc;
+    auto time_apply = [&](const TuneTable* t) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, st);
+            apply_with(F, nrhs, B, n, X, n, st, ws, flag, t);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return (double)best;
+    };
+    tt->ms_rule = time_apply(nullptr);
+    tt->ms_tuned = time_apply(tt.get());
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    C.cuda(cudaStreamSynchronize(st));
+    if (cur != F->device) cudaSetDevice(cur);
+    if (C.rc) return C.rc;
+    if (ms_rule) *ms_rule = tt->ms_rule;
+    if (ms_tuned) *ms_tuned = tt->ms_tuned;
+    {
+        std::lock_guard<std::mutex> lk(F->tune_mu);
+        auto& v = F->tunes;
+        v.erase(std::remove_if(v.begin(), v.end(), [&](const std::shared_ptr<const TuneTable>& t) {
+                    return t->nrhs == nrhs;
+                }),
+                v.end());
+        if (tt->ms_tuned < tt->ms_rule) v.push_back(tt);   // keep the rules where tuning does not pay
+    }
+    return SPAQR_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -92,6 +92,17 @@ int prof_begin(void* stream, int kind, double flops, double bytes);
 void prof_end(void* stream, int rec);
 // Add algorithmic flops to a record known only later (e.g. after ranks).
 void prof_add(int rec, int kind, double flops, double bytes);
+// Launch tallies: a CUDA-graph capture takes back the launches it recorded
+// (nothing ran) and every replay adds them again.
+struct LaunchTally {
+    int64_t count[KK_COUNT];
+    double flops[KK_COUNT], bytes[KK_COUNT];
+};
+void prof_capture_begin(LaunchTally* t);   // this thread's launches go to *t only
+void prof_capture_end();
+void prof_add_tally(const LaunchTally& t, int sign);
+bool prof_on();
+bool graphs_on();
 
 }  // namespace spaqr
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "spaqr_internal.h"
@@ -204,9 +206,20 @@ struct SolveLevelHost {
     // thread-block cluster per front; a wide backward level runs the R_sj
     // tiles, then one cluster per front.
     std::vector<int> ff_wide, ff_maxm;
-    bool bwd_wide = false;
+    bool bwd_wide = false, bwd_tiles = false;
     int tile_begin = 0, ntile = 0, wf_begin = 0;
     double rt_flops = 0, rt_fixed = 0, rt_vec = 0;     // R_sj tiles
+};
+
+// Launch forms chosen by spaqr_autotune for one right-hand-side count:
+// per unit of the application (forward colour, forward / backward
+// scale-sparsify, backward fronts of a level) 0 = rule, 1 = one CTA per
+// front / interface, 2 = thread-block cluster per front / interface.
+struct TuneTable {
+    int nrhs = 0;
+    std::vector<std::vector<uint8_t>> ff;
+    std::vector<uint8_t> ssf, ssb, fb;
+    double ms_rule = 0.0, ms_tuned = 0.0;
 };
 
 struct spaqr_factor_s {
@@ -231,6 +244,15 @@ struct spaqr_factor_s {
     void* d_tiles = nullptr;       // RsjTile[]
     void* d_pieces = nullptr;      // SolveRsj<real>[] of the tiles
     void* d_wfronts = nullptr;     // WideFront[]
+    // autotuned launch forms, one table per right-hand-side count
+    mutable std::mutex tune_mu;
+    std::vector<std::shared_ptr<const TuneTable>> tunes;
+    std::shared_ptr<const TuneTable> tune_for(int nrhs) const {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        for (const auto& t : tunes)
+            if (t->nrhs == nrhs) return t;
+        return nullptr;
+    }
     // diagnostics
     std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
     std::vector<std::vector<std::pair<double, double>>> margins;
