@@ -39,10 +39,12 @@ WORKLOAD = "convdiff2d_256x256_lognormal_a_pe50_randangle_fp64_eps1e-2_16rhs"
 # FP64 peak on GB300: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2070 MHz (nominal
 # 1.25 TFLOP/s); a DFMA microbenchmark measured 1.19 TFLOP/s at ~1990 MHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the current kernels on this workload (profiles/); None when
-# the kernel changed since the capture.
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# averaged over the kind's launches (one-CTA and cluster forms), from the ncu
+# launch list of the current kernels on this workload
+# (profiles/launches_convdiff2d_256x256_fp64_16rhs.md); a kind whose kernels
+# changed since that capture has no entry.
+TRAFFIC = {"solve_front_fwd": 4.0e6}
 
 
 def _args():
@@ -53,6 +55,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline workload (no mixed / 3D / batched / serving lines)")
     ap.add_argument("--serve-s", type=float, default=1.0)
     return ap.parse_args()
 
@@ -487,6 +491,12 @@ def ours(a):
         "roofline": roof,
         "clocks": clk,
     }
+    if a.no_extras:
+        print(json.dumps(line))
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
     # ---- mixed-precision form on the same workload: FP32 factor + FP64 GMRES ----
     Xref = Xd.detach().cpu().numpy().copy()
     mixed, X32 = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp32", 3, 1)
