@@ -266,12 +266,21 @@ void spaqr_factor_destroy(spaqr_factor_t* F);
  * stream), keeps the faster, and times whole applications with the untuned
  * rules and with the table (*ms_rule, *ms_tuned; may be NULL).  The table is
  * stored in F and used by later spaqr_solve / spaqr_gmres calls with the
- * same nrhs if it is faster than the rules; the results do not depend on the
+ * same nrhs (or, without a table for their nrhs, the nearest tuned count) if
+ * it is faster than the rules; the results do not depend on the
  * forms chosen beyond rounding.  Must not run concurrently with another call
  * on F.  Synchronises the stream.  Errors: INVALID_ARG (profiling on, bad
  * arguments), OOM, CUDA.  (Launch-form tuning is ours; the paper has no
  * counterpart.) */
 int spaqr_autotune(spaqr_factor_t* F, int nrhs, void* stream, double* ms_rule, double* ms_tuned);
+
+/* The launch forms spaqr_autotune kept for nrhs, level by level (0 = leaves):
+ * one entry per forward colour of the level, then the level's forward
+ * scale-sparsify, backward scale-sparsify and backward fronts; 1 = one CTA
+ * per front / interface, 2 = a cluster of 8 CTAs per front / interface,
+ * 3 = the staged cluster kernels with one CTA.  Writes up to cap entries and
+ * the total in *count (0: no table for nrhs, the rules apply). */
+int spaqr_factor_tuning(const spaqr_factor_t* F, int nrhs, int32_t* forms, int cap, int* count);
 
 /* Process-wide switch (default on): spaqr_gmres / spaqr_gmres_batch run on a
  * private non-blocking stream ordered after the caller's stream, and capture

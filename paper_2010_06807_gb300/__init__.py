@@ -20,6 +20,7 @@ __all__ = [
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
+    "spaqr_factor_tuning",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -81,7 +82,7 @@ EXPORTS = [
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
-    "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
+    "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
 ]
 
 
@@ -124,6 +125,7 @@ def load_library(path=None):
         lib.spaqr_use_graphs.argtypes = [i32]
         lib.spaqr_use_graphs.restype = None
         lib.spaqr_autotune.argtypes = [vp, i32, vp, vp, vp]
+        lib.spaqr_factor_tuning.argtypes = [vp, i32, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_stats.argtypes = [ctypes.POINTER(_KStat), i32, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64)]
     if path is None:
@@ -501,6 +503,16 @@ def spaqr_autotune(F, nrhs, stream=None):
     b = ctypes.c_double(0.0)
     _check(_lib.spaqr_autotune(F._h, int(nrhs), _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def spaqr_factor_tuning(F, nrhs):
+    """The launch forms spaqr_autotune kept for nrhs (empty: rules apply)."""
+    load_library()
+    cnt = ctypes.c_int(0)
+    _check(_lib.spaqr_factor_tuning(F._h, int(nrhs), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    _check(_lib.spaqr_factor_tuning(F._h, int(nrhs), out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
 
 
 def spaqr_use_graphs(on=True):

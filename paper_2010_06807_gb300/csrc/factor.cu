@@ -874,20 +874,16 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
             LV.nfront = (int)sfronts.size() - LV.front_begin;
         }
-        // wide solve forms where a colour (forward) or the level (backward)
-        // has too few fronts to fill the GPU with one CTA per front
-        LV.ff_wide.assign(LV.colour_ptr.size() - 1, 0);
+        // tallest front of every colour (shared-memory size of the staged and
+        // cluster forms of the forward step)
         LV.ff_maxm.assign(LV.colour_ptr.size() - 1, 0);
         for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
             const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
             int mm = 0;
             for (int f = a; f < b; f++) mm = std::max(mm, sfronts[LV.front_begin + f].m);
             LV.ff_maxm[c] = mm;
-            LV.ff_wide[c] = (b > a && b - a <= kWideFronts && mm >= kWideMinM) ? 1 : 0;
         }
-        // R_sj tiles are planned for every level (the autotuner may pick the
-        // wide backward form anywhere); bwd_wide is the untuned rule
-        LV.bwd_wide = LV.nfront > 0 && LV.nfront <= kWideFronts && LV.max_front_n >= kWideMinN;
+        // R_sj tiles of the backward step, planned for every level
         LV.bwd_tiles = LV.nfront > 0;
         if (LV.bwd_tiles) {
             LV.tile_begin = (int)tiles.size();

@@ -883,6 +883,14 @@ void set_solve_attrs() {
     cudaFuncSetAttribute(k_sss_bwd<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
     for (int q : {1, 2, 4, 8, 16})
         with_q(q, [](auto QC) {
+            cudaFuncSetAttribute(k_sfront_fwd_wide<real, 1, QC.value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
+            cudaFuncSetAttribute(k_sfront_bwd_wide<real, 1, QC.value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
+            cudaFuncSetAttribute(k_sss_fwd_wide<real, 1, QC.value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
+            cudaFuncSetAttribute(k_sss_bwd_wide<real, 1, QC.value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
             cudaFuncSetAttribute(k_sfront_fwd_wide<real, kWideCS, QC.value>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
             cudaFuncSetAttribute(k_sfront_bwd_wide<real, kWideCS, QC.value>,
@@ -919,18 +927,29 @@ static int narrow_ctas(int units, int nrhs) { return units * rhs_split(units, nr
 // CTAs per SM, at most kTileQ columns per chunk, and the chunk's shared
 // memory (smem(q) bytes) within the limit.  False if one column does not fit.
 template <class Smem>
-static bool wide_split(int units, int nrhs, Smem smem, int& qs, int& split) {
+static bool wide_split(int units, int nrhs, Smem smem, int& qs, int& split, int cs = kWideCS) {
     int qmax = kTileQ;
     while (qmax > 0 && smem(qmax) > (size_t)kSmemMax) qmax--;
     if (qmax == 0) return false;
     split = std::max((nrhs + qmax - 1) / qmax,
-                     std::min(nrhs, (2 * kNumSM + units * kWideCS - 1) / (units * kWideCS)));
+                     std::min(nrhs, (2 * kNumSM + units * cs - 1) / (units * cs)));
     qs = (nrhs + split - 1) / split;
     split = (nrhs + qs - 1) / qs;
     return true;
 }
 
-enum { kChoiceRule = 0, kChoiceNarrow = 1, kChoiceWide = 2 };
+// Launch forms of a unit: the rule's choice, one CTA per front / interface
+// (the original kernels), a thread-block cluster of kWideCS CTAs per front /
+// interface, or the cluster kernels with one CTA (cp.async-staged panels,
+// column loops unrolled to the chunk width).
+enum { kChoiceRule = 0, kChoiceNarrow = 1, kChoiceWide = 2, kChoiceSingle = 3 };
+
+// Calls f(std::integral_constant<int, CS>) for CS = cs (1 or kWideCS).
+template <class Fn>
+static void with_cs(int cs, Fn f) {
+    if (cs == 1) f(std::integral_constant<int, 1>());
+    else f(std::integral_constant<int, kWideCS>());
+}
 
 // One application in flight: the factor, right-hand-side count, stream and
 // workspace.
@@ -964,17 +983,28 @@ void launch_ff(const ApplyCtx<real>& A, int k, int c, int choice) {
     cudaStream_t st = A.st;
     real* Y = A.level(k);
     const int64_t ldy = LV.rows;
-    const bool wide = choice == kChoiceWide ||
-                      (choice == kChoiceRule && LV.ff_wide[c] && narrow_ctas(b - a, nrhs) < kNumSM);
-    if (wide) {
-        const int slab = wide_slab_rows(LV.ff_maxm[c], kWideCS);
+    int form = choice;
+    if (form == kChoiceRule) {
+        // rule (from autotuned choices on 2D and 3D grids): a cluster per
+        // front where one CTA per front leaves SMs idle and the fronts are
+        // tall, the staged one-CTA form otherwise
+        const int units = b - a;
+        if (narrow_ctas(units, nrhs) < kNumSM && LV.ff_maxm[c] >= kWideMinM) form = kChoiceWide;
+        else if (units <= 64 && LV.ff_maxm[c] >= 4 * kWideMinM) form = kChoiceWide;
+        else form = kChoiceSingle;
+    }
+    if (form == kChoiceWide || form == kChoiceSingle) {
+        const int cs = form == kChoiceWide ? kWideCS : 1;
+        const int slab = wide_slab_rows(LV.ff_maxm[c], cs);
         int qs, split;
-        if (wide_split(b - a, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+        if (wide_split(b - a, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split, cs)) {
             SPAQR_LAUNCH(KK_SOLVE_FRONT_FWD, LV.ff_flops[c] * nrhs, LV.ff_fixed[c] * split + LV.ff_vec[c] * nrhs, st,
-                         with_q(qs, [&](auto QC) {
-                             k_sfront_fwd_wide<real, kWideCS, QC.value>
-                                 <<<dim3((b - a) * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
-                                     A.dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
+                         with_cs(cs, [&](auto CSC) {
+                             with_q(qs, [&](auto QC) {
+                                 k_sfront_fwd_wide<real, CSC.value, QC.value>
+                                     <<<dim3((b - a) * CSC.value, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                         A.dfr + LV.front_begin + a, F->d_segs, Y, ldy, nrhs, qs, slab);
+                             });
                          }));
             return;
         }
@@ -1006,22 +1036,31 @@ void launch_ss(const ApplyCtx<real>& A, int k, bool fwd, int choice) {
     const double fl = fwd ? LV.ssf_flops : LV.ssb_flops, fx = fwd ? LV.ssf_fixed : LV.ssb_fixed,
                  fv = fwd ? LV.ssf_vec : LV.ssb_vec;
     const int kind = fwd ? KK_SOLVE_SS_FWD : KK_SOLVE_SS_BWD;
-    const bool wide = LV.max_ss_n >= kWideMinN &&
-                      (choice == kChoiceWide || (choice == kChoiceRule && narrow_ctas(LV.nss, nrhs) < kNumSM));
-    if (wide) {
-        const int slab = wide_slab_rows(LV.max_ss_n, kWideCS);
+    int form = choice;
+    if (form == kChoiceRule) {
+        // many interfaces: one CTA each; a few hundred large ones: the staged
+        // one-CTA form; the last few: a cluster each
+        if (LV.nss <= 8 && LV.max_ss_n >= kWideMinN) form = kChoiceWide;
+        else if (LV.nss <= 40 || (LV.nss <= 400 && LV.max_ss_n >= 3 * kWideMinN)) form = kChoiceSingle;
+        else form = kChoiceNarrow;
+    }
+    if (form == kChoiceWide || form == kChoiceSingle) {
+        const int cs = form == kChoiceWide ? kWideCS : 1;
+        const int slab = wide_slab_rows(LV.max_ss_n, cs);
         int qs, split;
-        if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+        if (wide_split(LV.nss, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split, cs)) {
             const size_t smem = wide_smem(slab, qs, (int)esz);
-            SPAQR_LAUNCH(kind, fl * nrhs, fx * split + fv * nrhs, st, with_q(qs, [&](auto QC) {
-                             if (fwd)
-                                 k_sss_fwd_wide<real, kWideCS, QC.value><<<dim3(LV.nss * kWideCS, split), NT, smem,
-                                                                           st>>>(A.dss + LV.ss_begin, Y, ldy, Yn,
-                                                                                 LN.rows, nrhs, qs, slab);
-                             else
-                                 k_sss_bwd_wide<real, kWideCS, QC.value><<<dim3(LV.nss * kWideCS, split), NT, smem,
-                                                                           st>>>(A.dss + LV.ss_begin, Y, ldy, Yn,
-                                                                                 LN.rows, nrhs, qs, slab);
+            SPAQR_LAUNCH(kind, fl * nrhs, fx * split + fv * nrhs, st, with_cs(cs, [&](auto CSC) {
+                             with_q(qs, [&](auto QC) {
+                                 if (fwd)
+                                     k_sss_fwd_wide<real, CSC.value, QC.value>
+                                         <<<dim3(LV.nss * CSC.value, split), NT, smem, st>>>(
+                                             A.dss + LV.ss_begin, Y, ldy, Yn, LN.rows, nrhs, qs, slab);
+                                 else
+                                     k_sss_bwd_wide<real, CSC.value, QC.value>
+                                         <<<dim3(LV.nss * CSC.value, split), NT, smem, st>>>(
+                                             A.dss + LV.ss_begin, Y, ldy, Yn, LN.rows, nrhs, qs, slab);
+                             });
                          }));
             return;
         }
@@ -1051,11 +1090,14 @@ void launch_fb(const ApplyCtx<real>& A, int k, int choice) {
     cudaStream_t st = A.st;
     real* Y = A.level(k);
     const int64_t ldy = LV.rows;
-    const bool wide = LV.bwd_tiles && (choice == kChoiceWide || (choice == kChoiceRule && LV.bwd_wide));
-    if (wide) {
-        const int slab = wide_slab_rows(LV.max_front_n, kWideCS);
+    int form = choice;
+    if (form == kChoiceRule)
+        form = LV.nfront <= 8 || (LV.nfront <= 32 && nrhs <= 4) ? kChoiceWide : kChoiceSingle;
+    if (LV.bwd_tiles && (form == kChoiceWide || form == kChoiceSingle)) {
+        const int cs = form == kChoiceWide ? kWideCS : 1;
+        const int slab = wide_slab_rows(LV.max_front_n, cs);
         int qs, split;
-        if (wide_split(LV.nfront, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split)) {
+        if (wide_split(LV.nfront, nrhs, [&](int q) { return wide_smem(slab, q, (int)esz); }, qs, split, cs)) {
             real* Zp = A.ws + F->zp_off * nrhs;
             const int64_t ldz = F->zp_rows;
             if (LV.ntile > 0) {
@@ -1072,11 +1114,13 @@ void launch_fb(const ApplyCtx<real>& A, int k, int choice) {
                              }));
             }
             SPAQR_LAUNCH(KK_SOLVE_FRONT_BWD, (LV.fb_flops - LV.rt_flops) * nrhs,
-                         (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st, with_q(qs, [&](auto QC) {
-                             k_sfront_bwd_wide<real, kWideCS, QC.value>
-                                 <<<dim3(LV.nfront * kWideCS, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
-                                     static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, A.dfr, F->d_segs, Y,
-                                     ldy, Zp, ldz, nrhs, qs, slab);
+                         (LV.fb_fixed - LV.rt_fixed) * split + LV.fb_vec * nrhs, st, with_cs(cs, [&](auto CSC) {
+                             with_q(qs, [&](auto QC) {
+                                 k_sfront_bwd_wide<real, CSC.value, QC.value>
+                                     <<<dim3(LV.nfront * CSC.value, split), NT, wide_smem(slab, qs, (int)esz), st>>>(
+                                         static_cast<const WideFront*>(F->d_wfronts) + LV.wf_begin, A.dfr,
+                                         F->d_segs, Y, ldy, Zp, ldz, nrhs, qs, slab);
+                             });
                          }));
             return;
         }
@@ -1143,9 +1187,16 @@ int autotune_t(const spaqr_factor_s* F, int nrhs, cudaStream_t st, real* ws, rea
         return best;
     };
     auto pick = [&](auto&& launch_with) {
-        const float tn = time_unit([&] { launch_with(kChoiceNarrow); });
-        const float tw = time_unit([&] { launch_with(kChoiceWide); });
-        return (uint8_t)(tw < tn ? kChoiceWide : kChoiceNarrow);
+        uint8_t best = kChoiceNarrow;
+        float tb = time_unit([&] { launch_with(kChoiceNarrow); });
+        for (int form : {kChoiceWide, kChoiceSingle}) {
+            const float t = time_unit([&] { launch_with(form); });
+            if (t < tb) {
+                tb = t;
+                best = (uint8_t)form;
+            }
+        }
+        return best;
     };
     const int L = F->L;
     tt.nrhs = nrhs;
@@ -1665,6 +1716,23 @@ extern "C" int spaqr_autotune(spaqr_factor_t* F, int nrhs, void* stream, double*
                 v.end());
         if (tt->ms_tuned < tt->ms_rule) v.push_back(tt);   // keep the rules where tuning does not pay
     }
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_tuning(const spaqr_factor_t* F, int nrhs, int32_t* forms, int cap, int* count) {
+    if (!F || !count || (cap > 0 && !forms)) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    const std::shared_ptr<const TuneTable> tt = F->tune_exact(nrhs);
+    std::vector<int32_t> v;
+    if (tt) {
+        for (int k = 0; k < F->L; k++) {
+            for (uint8_t f : tt->ff[k]) v.push_back(f);
+            v.push_back(tt->ssf[k]);
+            v.push_back(tt->ssb[k]);
+            v.push_back(tt->fb[k]);
+        }
+    }
+    *count = (int)v.size();
+    for (int i = 0; i < (int)v.size() && i < cap; i++) forms[i] = v[i];
     return SPAQR_OK;
 }
 

@@ -140,9 +140,8 @@ struct SolveRsj {
 
 // Launch shapes of the wide solve forms.
 constexpr int kWideCS = 8;        // CTAs per thread-block cluster
-constexpr int kWideFronts = 64;   // a colour / level with at most this many fronts runs wide
-constexpr int kWideMinM = 128;    // ... if its largest front has at least this many rows (forward)
-constexpr int kWideMinN = 32;     // ... or columns (backward)
+constexpr int kWideMinM = 128;    // rows of a front from which a cluster per front can pay (forward)
+constexpr int kWideMinN = 32;     // size of an interface from which a cluster can pay
 constexpr int kTileRows = 64;     // rows of an R_sj tile
 constexpr int kTileK = 256;       // columns of an R_sj tile chunk
 constexpr int kTileQ = 16;        // right-hand sides per R_sj tile
@@ -202,11 +201,10 @@ struct SolveLevelHost {
     double ssf_flops = 0, ssf_fixed = 0, ssf_vec = 0; // forward scale/sparsify
     double ssb_flops = 0, ssb_fixed = 0, ssb_vec = 0; // backward scale/sparsify
     double fb_flops = 0, fb_fixed = 0, fb_vec = 0;    // backward fronts
-    // wide forms (few fronts): forward colours flagged in ff_wide run one
-    // thread-block cluster per front; a wide backward level runs the R_sj
-    // tiles, then one cluster per front.
-    std::vector<int> ff_wide, ff_maxm;
-    bool bwd_wide = false, bwd_tiles = false;
+    // staged / cluster forms: tallest front per forward colour; the R_sj
+    // tiles of the backward step (bwd_tiles: planned for this level)
+    std::vector<int> ff_maxm;
+    bool bwd_tiles = false;
     int tile_begin = 0, ntile = 0, wf_begin = 0;
     double rt_flops = 0, rt_fixed = 0, rt_vec = 0;     // R_sj tiles
 };
@@ -247,7 +245,18 @@ struct spaqr_factor_s {
     // autotuned launch forms, one table per right-hand-side count
     mutable std::mutex tune_mu;
     std::vector<std::shared_ptr<const TuneTable>> tunes;
+    // the table for nrhs, else the one tuned for the nearest count (by ratio)
     std::shared_ptr<const TuneTable> tune_for(int nrhs) const {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        std::shared_ptr<const TuneTable> best;
+        double bd = 1e30;
+        for (const auto& t : tunes) {
+            const double d = t->nrhs > nrhs ? (double)t->nrhs / nrhs : (double)nrhs / t->nrhs;
+            if (d < bd) { bd = d; best = t; }
+        }
+        return best;
+    }
+    std::shared_ptr<const TuneTable> tune_exact(int nrhs) const {
         std::lock_guard<std::mutex> lk(tune_mu);
         for (const auto& t : tunes)
             if (t->nrhs == nrhs) return t;
