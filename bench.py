@@ -520,10 +520,11 @@ def ours(a):
     line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
     line["batched_64x2d"] = _batched(sq, torch, np, dev, st, flush)
     if not a.no_serve:
-        from paper_2010_06807_gb300.serve import run_workload
+        from paper_2010_06807_gb300.serve import run_plain, run_workload
         srv = {}
         for prec in ("fp32", "fp64"):
             srv[prec] = run_workload(duration=a.serve_s, precision=prec, device=dev)
+        srv["plain_fp64_one_at_a_time"] = run_plain(requests=200, device=dev)
         line["serving_8x3d_poisson2000"] = srv
     if not a.no_cpu_baseline:
         try:

@@ -151,13 +151,20 @@ __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask<real>* __res
 }
 
 template <class real>
-__global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask<real>* __restrict__ tasks) {
+__global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask<real>* __restrict__ tasks,
+                                                    const ScalePiece* __restrict__ pieces, int right) {
     extern __shared__ double sm[];
     real* W = reinterpret_cast<real*>(sm);
-    const ScaleTask<real> t = tasks[blockIdx.x];
-    cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false, Mat<real>{t.A, 1, t.lda, nullptr}, t.nj, QC, true,
-                        W);
-    cta_trsm_right_upper(t.A, t.lda, t.mi, t.nj, t.Rj, t.ldrj, t.Dj);
+    const ScalePiece pc = pieces[blockIdx.x];
+    const ScaleTask<real> t = tasks[pc.task];
+    if (!right) {
+        // rows i <- U_i^T (rows i): columns [off, off + len) of the block
+        cta_apply_q_chunked(t.Vi, t.ldvi, t.mi, t.mi, t.Ti, t.mi, false,
+                            Mat<real>{t.A + (int64_t)pc.off * t.lda, 1, t.lda, nullptr}, pc.len, QC, true, W);
+    } else {
+        // columns j <- (columns j) R_j^{-1}: rows [off, off + len) of the block
+        cta_trsm_right_upper(t.A + pc.off, t.lda, pc.len, t.nj, t.Rj, t.ldrj, t.Dj);
+    }
 }
 
 // Truncated CPQR of M_p (stored row-major) with column norms recomputed from
@@ -420,10 +427,12 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
 // Coarse block [Q_i^T A Q_j](0:r_i, 0:r_j) into the merged block of the next
 // level; identity for diagonal blocks; plain copy when not sparsified.
 template <class real>
-__global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __restrict__ tasks) {
+__global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __restrict__ tasks,
+                                                 const ScalePiece* __restrict__ pieces, int right) {
     extern __shared__ double sm[];
     real* W = reinterpret_cast<real*>(sm);
-    const SparsifyTask<real> t = tasks[blockIdx.x];
+    const ScalePiece pc = pieces[blockIdx.x];
+    const SparsifyTask<real> t = tasks[pc.task];
     if (t.mode == 2) {
         const int64_t tot = (int64_t)t.mi * t.nj;
         for (int64_t o = threadIdx.x; o < tot; o += NT) {
@@ -438,17 +447,24 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __res
     }
     const int mi = t.mi, nj = t.nj;
     real* X = t.scratch;  // mi x nj, ld mi
-    for (int64_t o = threadIdx.x; o < (int64_t)mi * nj; o += NT) {
-        const int r = (int)(o % mi), c = (int)(o / mi);
-        X[o] = t.A[r + (int64_t)c * t.lda];
+    if (!right) {
+        // columns [off, off + len): X <- Q_i^T A
+        const int c0 = pc.off, qn = pc.len;
+        for (int64_t o = threadIdx.x; o < (int64_t)mi * qn; o += NT) {
+            const int r = (int)(o % mi), c = c0 + (int)(o / mi);
+            X[r + (int64_t)c * mi] = t.A[r + (int64_t)c * t.lda];
+        }
+        __syncthreads();
+        cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true,
+                            Mat<real>{X + (int64_t)c0 * mi, 1, mi, nullptr}, qn, QC, true, W);
+        return;
     }
-    __syncthreads();
-    // X <- Q_i^T X
-    cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true, Mat<real>{X, 1, mi, nullptr}, nj, QC, true, W);
-    // X <- X Q_j, i.e. X^T <- Q_j^T X^T with X^T(r, c) = X[c + r * mi]
-    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat<real>{X, mi, 1, nullptr}, mi, QC, true, W);
-    for (int64_t o = threadIdx.x; o < (int64_t)t.ri * t.rj; o += NT) {
-        const int p = (int)(o % t.ri), q = (int)(o / t.ri);
+    // coarse rows [off, off + len) (< r_i): X <- X Q_j, i.e. X^T <- Q_j^T X^T
+    // with X^T(r, c) = X[c + r * mi]; then the r_i x r_j coarse block
+    const int r0 = pc.off, rn = pc.len;
+    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat<real>{X + r0, mi, 1, nullptr}, rn, QC, true, W);
+    for (int64_t o = threadIdx.x; o < (int64_t)rn * t.rj; o += NT) {
+        const int p = r0 + (int)(o % rn), q = (int)(o / rn);
         t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * mi];
     }
 }
@@ -459,11 +475,39 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __res
 
 namespace {
 
+// Pinned host staging for the task arrays a factorisation uploads (copies
+// from pageable memory are synchronous staging copies).  One buffer per host
+// thread, reused by the thread's next factorisation, which starts after this
+// one has synchronised its stream; it grows between calls to the largest
+// total seen.
+struct PinnedStage {
+    char* p = nullptr;
+    size_t cap = 0, want = 0;
+    void grow() {
+        if (want <= cap) return;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t bytes = want + want / 4;
+        if (cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return;
+        }
+        cap = bytes;
+    }
+    ~PinnedStage() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local PinnedStage tl_stage;
+
 struct Ctx {
     spaqr_factor_s* F;
     cudaStream_t st;
     std::vector<void*> temps;
     int rc = SPAQR_OK;
+    size_t stage_off = 0, stage_total = 0;
 
     template <class T>
     T* alloc(int64_t count, bool keep) {
@@ -488,7 +532,17 @@ struct Ctx {
     template <class T>
     T* upload(const std::vector<T>& h, bool keep) {
         T* d = alloc<T>((int64_t)h.size(), keep);
-        if (d && !h.empty()) cuda(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+        if (!d || h.empty()) return d;
+        const size_t bytes = sizeof(T) * h.size(), rounded = (bytes + 255) & ~(size_t)255;
+        stage_total += rounded;
+        tl_stage.want = std::max(tl_stage.want, stage_total);
+        if (stage_off + rounded <= tl_stage.cap) {
+            std::memcpy(tl_stage.p + stage_off, h.data(), bytes);
+            cuda(cudaMemcpyAsync(d, tl_stage.p + stage_off, bytes, cudaMemcpyHostToDevice, st));
+            stage_off += rounded;
+        } else {
+            cuda(cudaMemcpyAsync(d, h.data(), bytes, cudaMemcpyHostToDevice, st));
+        }
         return d;
     }
     void cuda(cudaError_t e) {
@@ -587,8 +641,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->eps = opt->eps;
     F->precision = sizeof(real) == 8 ? SPAQR_FP64 : SPAQR_FP32;
     F->esz = (int)sizeof(real);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
         C.cuda(cudaFuncSetAttribute(k_front_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_scale_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_qr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
@@ -596,9 +650,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         C.cuda(cudaFuncSetAttribute(k_cpqr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, CPQR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kSmemMax));
-        if (C.rc != SPAQR_OK) return C.rc;
-        attr_set = true;
-    }
+    });
+    if (C.rc != SPAQR_OK) return C.rc;
     const size_t esz = sizeof(real);
     // phase timers: (start, end, phase) event triples
     struct Timer { cudaEvent_t a, b; int ph; };
@@ -999,10 +1052,23 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 C.launched();
             }
             if (!sc.empty()) {
+                // U^T over column chunks of every block, then R^{-1} over row
+                // chunks (the two products of a block are independent across
+                // columns and across rows respectively)
+                std::vector<ScalePiece> pl, pr;
+                for (int t = 0; t < (int)sc.size(); t++) {
+                    for (int c0 = 0; c0 < sc[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sc[t].nj - c0)});
+                    for (int r0 = 0; r0 < sc[t].mi; r0 += 64) pr.push_back({t, r0, std::min(64, sc[t].mi - r0)});
+                }
                 ScaleTask<real>* d = C.upload(sc, false);
+                ScalePiece* dl = C.upload(pl, false);
+                ScalePiece* dr = C.upload(pr, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
-                             k_scale_apply<real><<<(unsigned)sc.size(), NT, smem_sc, st>>>(d));
+                             k_scale_apply<real><<<(unsigned)pl.size(), NT, smem_sc, st>>>(d, dl, 0));
+                C.launched();
+                SPAQR_LAUNCH(KK_SCALE_APPLY, 0.0, 0.0, st,
+                             k_scale_apply<real><<<(unsigned)pr.size(), NT, smem_sc, st>>>(d, dr, 1));
                 C.launched();
             }
             tstop(1);
@@ -1191,7 +1257,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         t.ldtj = kmax[j];
                         t.scratch = (real*)(intptr_t)scr;  // offset, fixed below
                         scr += (int64_t)t.mi * t.nj;
-                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.rj * t.nj * t.mi;
+                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.rj * t.nj * t.ri;
                         flops += fp;
                         fl_sp += fp;
                     }
@@ -1204,11 +1270,31 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 if (C.rc) return C.rc;
                 for (SparsifyTask<real>& t : sk)
                     if (t.mode == 0) t.scratch = sbuf + (int64_t)(intptr_t)t.scratch;
+                // Q_i^T over column chunks (copies and identities: one piece
+                // each), then Q_j over chunks of the r_i coarse rows, the only
+                // rows of Q_i^T A_ij the coarse block keeps
+                std::vector<ScalePiece> pl, pr;
+                for (int t = 0; t < (int)sk.size(); t++) {
+                    if (sk[t].mode != 0) {
+                        pl.push_back({t, 0, 0});
+                        continue;
+                    }
+                    for (int c0 = 0; c0 < sk[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sk[t].nj - c0)});
+                    for (int r0 = 0; r0 < sk[t].ri; r0 += 32) pr.push_back({t, r0, std::min(32, sk[t].ri - r0)});
+                }
                 SparsifyTask<real>* d = C.upload(sk, false);
+                ScalePiece* dl = C.upload(pl, false);
+                ScalePiece* dr = C.upload(pr, false);
                 if (C.rc) return C.rc;
+                const size_t smem_sp = (size_t)(2 * NB * QC + NT) * esz;
                 SPAQR_LAUNCH(KK_SPARSIFY, fl_sp, by_sp, st,
-                             k_sparsify<real><<<(unsigned)sk.size(), NT, (size_t)(2 * NB * QC + NT) * esz, st>>>(d));
+                             k_sparsify<real><<<(unsigned)pl.size(), NT, smem_sp, st>>>(d, dl, 0));
                 C.launched();
+                if (!pr.empty()) {
+                    SPAQR_LAUNCH(KK_SPARSIFY, 0.0, 0.0, st,
+                                 k_sparsify<real><<<(unsigned)pr.size(), NT, smem_sp, st>>>(d, dr, 1));
+                    C.launched();
+                }
             }
             tstop(3);
             // solve record of the surviving clusters
@@ -1274,6 +1360,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     C.cuda(cudaStreamSynchronize(st));
     C.free_temps();
     C.cuda(cudaStreamSynchronize(st));
+    tl_stage.grow();   // every staged copy has completed
     if (C.rc) return C.rc;
     for (Timer& t : timers) {
         float ms = 0.0f;

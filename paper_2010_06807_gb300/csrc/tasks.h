@@ -69,6 +69,13 @@ struct ScaleTask {
     int q;              // column chunk for the U^T product
 };
 
+// A piece of a ScaleTask: columns [off, off + len) for the U^T product, or
+// rows [off, off + len) for the R^{-1} product.
+struct ScalePiece {
+    int task;
+    int off, len;
+};
+
 // Column segment of M_p = [A_{k p}^T ... | A_{p j} ...] (Section 2.5).
 template <class real>
 struct GatherSeg {

@@ -34,7 +34,7 @@ import time
 
 import numpy as np
 
-__all__ = ["SolveServer", "Request", "DeviceOps", "run_workload"]
+__all__ = ["SolveServer", "Request", "DeviceOps", "run_workload", "run_plain"]
 
 
 class Request:
@@ -411,6 +411,46 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q))
 
 
+def _arrivals(probs, rate, duration, seed):
+    """Poisson arrivals (time, matrix, N(0,1) right-hand side) over `duration`."""
+    rng = np.random.Generator(np.random.PCG64(seed + 10 ** 6))
+    out = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        mid = int(rng.integers(0, len(probs)))
+        out.append((t, mid, rng.standard_normal(probs[mid].n)))
+    return out
+
+
+def run_plain(sides=(16, 24, 32, 40, 48, 48, 32, 24), requests=200, eps=1e-2, precision="fp64", seed=5000,
+              device=None):
+    """The same request stream served the plain way: resident factors, but
+    every request solved alone (one-column GMRES), one after another on one
+    stream, no batching and no overlap.  Returns its throughput."""
+    import torch
+
+    from synth.convdiff import config_problem
+    ops = DeviceOps(device, eps=eps, precision=precision)
+    probs = [config_problem("3d_uniform_a", n=s, seed=seed + i) for i, s in enumerate(sides)]
+    st = ops.new_stream()
+    handles = [ops.load(p, st) for p in probs]
+    arr = _arrivals(probs, 2000.0, 1.0, seed)[:requests]
+    torch.cuda.synchronize(ops.device)
+    t0 = time.perf_counter()
+    worst = 0.0
+    for _, mid, b in arr:
+        _, _, rr = ops.solve(handles[mid], b[None, :], st)
+        worst = max(worst, float(rr[0]))
+    dt = time.perf_counter() - t0
+    for h in handles:
+        ops.release(h)
+    return {"precision": precision, "requests": len(arr), "solves_per_s": len(arr) / dt, "relres_max": worst,
+            "note": "same arrivals, each request alone and in arrival order"}
+
+
 def run_workload(sides=(16, 24, 32, 40, 48, 48, 32, 24), rate=2000.0, duration=2.0, factor_every=1.0,
                  factor_side=32, eps=1e-2, precision="fp64", seed=5000, max_slots=32, device=None):
     """The serving workload: resident factors of 3D 7-point convection-diffusion
@@ -428,15 +468,7 @@ def run_workload(sides=(16, 24, 32, 40, 48, 48, 32, 24), rate=2000.0, duration=2
     for i, p in enumerate(probs):
         srv.add_matrix(i, p)
     setup_s = time.perf_counter() - t0
-    rng = np.random.Generator(np.random.PCG64(seed + 10 ** 6))
-    arrivals = []
-    t = 0.0
-    while True:
-        t += rng.exponential(1.0 / rate)
-        if t >= duration:
-            break
-        mid = int(rng.integers(0, len(sides)))
-        arrivals.append((t, mid, rng.standard_normal(probs[mid].n)))
+    arrivals = _arrivals(probs, rate, duration, seed)
     fact_times = [factor_every * (j + 1) for j in range(int(duration / factor_every + 1e-9))]
     fact_probs = [config_problem("3d_uniform_a", n=factor_side, seed=seed + 100 + j) for j in range(len(fact_times))]
     reqs, freqs = [], []
