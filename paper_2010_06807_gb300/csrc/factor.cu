@@ -167,6 +167,47 @@ __global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask<real>* __res
     }
 }
 
+// One column of the CPQR trailing update: a_j <- (I - tau v v^T) a_j over
+// rows k.. (v_k = 1, v_r = vs[r] below), returning the new squared norm of
+// rows k+1.. (the next step's pivot norm).  Column entries are row-major
+// with stride ld.  Rows are loaded eight at a time before they are used, so
+// a thread keeps eight loads in flight; the additions keep the row order.
+template <class real>
+__device__ __forceinline__ real cpqr_reflect_column(real* a, int ld, int k, int m, const real* vs, real tk) {
+    constexpr int U = 8;
+    real d = a[(int64_t)k * ld];
+    int r = k + 1;
+    for (; r + U <= m; r += U) {
+        real x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) x[u] = a[(int64_t)(r + u) * ld];
+#pragma unroll
+        for (int u = 0; u < U; u++) d += vs[r + u] * x[u];
+    }
+    for (; r < m; r++) d += vs[r] * a[(int64_t)r * ld];
+    const real f = tk * d;
+    a[(int64_t)k * ld] -= f;
+    real nrm = 0;
+    r = k + 1;
+    for (; r + U <= m; r += U) {
+        real x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) x[u] = a[(int64_t)(r + u) * ld];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const real y = x[u] - f * vs[r + u];
+            a[(int64_t)(r + u) * ld] = y;
+            nrm += y * y;
+        }
+    }
+    for (; r < m; r++) {
+        const real y = a[(int64_t)r * ld] - f * vs[r];
+        a[(int64_t)r * ld] = y;
+        nrm += y * y;
+    }
+    return nrm;
+}
+
 // Truncated CPQR of M_p (stored row-major) with column norms recomputed from
 // scratch at every step (fused into the reflector update, one thread per
 // column), pivot = largest norm, ties to the lowest column index; stops at the
@@ -257,17 +298,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
         for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
         __syncthreads();
         for (int j = k + 1 + threadIdx.x; j < c; j += NT) {
-            real d = M[(int64_t)k * c + j];
-            for (int r = k + 1; r < m; r++) d += vs[r] * M[(int64_t)r * c + j];
-            const real f = tk * d;
-            M[(int64_t)k * c + j] -= f;
-            real nrm = 0;
-            for (int r = k + 1; r < m; r++) {
-                const real x = M[(int64_t)r * c + j] - f * vs[r];
-                M[(int64_t)r * c + j] = x;
-                nrm += x * x;
-            }
-            t.norms[j] = nrm;
+            t.norms[j] = cpqr_reflect_column(M + j, c, k, m, vs, tk);
         }
         __syncthreads();
         rank = k + 1;
@@ -397,17 +428,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
         for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
         __syncthreads();
         for (int j = max(k + 1, j0) + threadIdx.x; j < j1; j += NT) {
-            real d = M[(int64_t)k * c + j];
-            for (int r = k + 1; r < m; r++) d += vs[r] * M[(int64_t)r * c + j];
-            const real f = tk * d;
-            M[(int64_t)k * c + j] -= f;
-            real nrm = 0;
-            for (int r = k + 1; r < m; r++) {
-                const real x = M[(int64_t)r * c + j] - f * vs[r];
-                M[(int64_t)r * c + j] = x;
-                nrm += x * x;
-            }
-            t.norms[j] = nrm;
+            t.norms[j] = cpqr_reflect_column(M + j, c, k, m, vs, tk);
         }
         __syncthreads();
         rank = k + 1;
