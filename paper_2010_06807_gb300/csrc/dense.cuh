@@ -249,7 +249,21 @@ static __device__ void cta_apply_q(const real* V, int64_t ldv, int m, int t, con
             const real* v = V + (int64_t)col * ldv;
             real s = 0;
             if (g == 0) s = (explicit_v ? v[col] : (real)1) * B.at(col, c);
-            for (int r = col + 1 + (g == 0 ? G - 1 : g - 1); r < m; r += G) s += v[r] * B.at(r, c);
+            // rows col+1+.. with stride G, loaded four at a time before use
+            // (the additions keep the row order)
+            constexpr int U = 4;
+            int r = col + 1 + (g == 0 ? G - 1 : g - 1);
+            for (; r + (U - 1) * G < m; r += U * G) {
+                real a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    a[u] = v[r + u * G];
+                    b[u] = B.at(r + u * G, c);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) s += a[u] * b[u];
+            }
+            for (; r < m; r += G) s += v[r] * B.at(r, c);
             return s;
         });
         cta_tblock_mul(T, ldt, p0, pb, q, trans, W1, W2);
@@ -383,7 +397,19 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
             real part = 0;
             if (js < ncol) {
                 const real* cj = Pb + (int64_t)(k + 1 + js - p0) * ldp;
-                for (int r = k + 1 + g; r < m; r += NT / NB) part += col[r] * cj[r];
+                constexpr int S = NT / NB, U = 8;
+                int r = k + 1 + g;
+                for (; r + (U - 1) * S < m; r += U * S) {   // eight loads in flight, order kept
+                    real a[U], b[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        a[u] = col[r + u * S];
+                        b[u] = cj[r + u * S];
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) part += a[u] * b[u];
+                }
+                for (; r < m; r += S) part += col[r] * cj[r];
             }
             P[threadIdx.x] = part;
             __syncthreads();
@@ -488,7 +514,20 @@ static __device__ void cta_trsm_right_upper(real* B, int64_t ldb, int mi, int nj
                 const int r = o % mi, j = o / mi;
                 const real* rc = R + (int64_t)(b0 + j) * ldr;
                 real s = B[r + (int64_t)(b0 + j) * ldb];
-                for (int u = 0; u < b0; u++) s -= B[r + (int64_t)u * ldb] * rc[u];
+                // solved columns u < b0, loaded four at a time (order kept)
+                constexpr int U = 4;
+                int u = 0;
+                for (; u + U <= b0; u += U) {
+                    real x[U], y[U];
+#pragma unroll
+                    for (int w = 0; w < U; w++) {
+                        x[w] = B[r + (int64_t)(u + w) * ldb];
+                        y[w] = rc[u + w];
+                    }
+#pragma unroll
+                    for (int w = 0; w < U; w++) s -= x[w] * y[w];
+                }
+                for (; u < b0; u++) s -= B[r + (int64_t)u * ldb] * rc[u];
                 B[r + (int64_t)(b0 + j) * ldb] = s;
             }
             __syncthreads();
