@@ -175,6 +175,9 @@ void spaqr_ordering_destroy(spaqr_ordering* ord);
  * returns after the factor is complete.  The factor lives in device memory of
  * the current device and is immutable afterwards, so concurrent
  * spaqr_solve / spaqr_gmres calls on different streams may share it.
+ * Temporaries come from the device's default memory pool (cudaMallocAsync);
+ * the first call on a device raises that pool's release threshold so freed
+ * memory stays with the process for reuse.
  * Errors: INVALID_ARG, UNSUPPORTED (scaling = 0, unknown precision), OOM,
  * CUDA, NO_DEVICE. */
 int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts* opts,

@@ -159,6 +159,27 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 
+// The device's default memory pool (cudaMallocAsync) keeps freed memory for
+// reuse instead of returning it to the system at every synchronisation: a
+// factorisation allocates and frees tens of megabytes of temporaries per
+// level around a host synchronisation, and re-mapping them each time left the
+// GPU waiting on the host.  Done once per device.
+void keep_pool_memory(int device) {
+    static std::mutex mu;
+    static std::vector<char> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0) return;
+    if ((int)done.size() <= device) done.resize(device + 1, 0);
+    if (done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[device] = 1;
+}
+
 thread_local LaunchTally* tl_capture = nullptr;
 
 void prof_capture_begin(LaunchTally* t) {

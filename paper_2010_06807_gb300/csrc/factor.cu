@@ -1433,6 +1433,7 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
     spaqr_factor_s* F = new (std::nothrow) spaqr_factor_s();
     if (!F) { set_error("host allocation failed"); return SPAQR_ERR_OOM; }
     cudaGetDevice(&F->device);
+    keep_pool_memory(F->device);
     int rc;
     try {
         rc = opts->precision == SPAQR_FP32 ? run_factor<float>(ord->o, A, opts, F)

@@ -1376,6 +1376,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         return SPAQR_ERR_INVALID_ARG;
     }
     if (nrhs == 0) return SPAQR_OK;
+    keep_pool_memory(F->device);
     const bool graphs = graphs_on() && !prof_on();
     PrivateStream ps;   // destroyed after C, whose frees are ordered on it
     if (graphs && !ps.init((cudaStream_t)stream)) { set_error("stream creation failed"); return SPAQR_ERR_CUDA; }

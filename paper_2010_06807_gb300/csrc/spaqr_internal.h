@@ -102,6 +102,7 @@ void prof_capture_begin(LaunchTally* t);   // this thread's launches go to *t on
 void prof_capture_end();
 void prof_add_tally(const LaunchTally& t, int sign);
 bool prof_on();
+void keep_pool_memory(int device);
 bool graphs_on();
 
 }  // namespace spaqr
