@@ -170,7 +170,7 @@ class SolveServer:
     the device's free memory when the server starts, for DeviceOps).
     """
 
-    def __init__(self, ops, max_slots=32, hbm_budget=None):
+    def __init__(self, ops, max_slots=64, hbm_budget=None):
         self.ops = ops
         self.max_slots = int(max_slots)
         if hbm_budget is None:
@@ -452,7 +452,7 @@ def run_plain(sides=(16, 24, 32, 40, 48, 48, 32, 24), requests=200, eps=1e-2, pr
 
 
 def run_workload(sides=(16, 24, 32, 40, 48, 48, 32, 24), rate=2000.0, duration=2.0, factor_every=1.0,
-                 factor_side=32, eps=1e-2, precision="fp64", seed=5000, max_slots=32, device=None):
+                 factor_side=32, eps=1e-2, precision="fp64", seed=5000, max_slots=64, device=None):
     """The serving workload: resident factors of 3D 7-point convection-diffusion
     problems with the given sides (a ~ U[0.1,10], velocity 20(1,1,1)); an
     open-loop Poisson stream of single-RHS N(0,1) solve requests with mean
@@ -510,7 +510,7 @@ if __name__ == "__main__":
     ap.add_argument("--duration", type=float, default=2.0)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--precision", default="fp64")
-    ap.add_argument("--max-slots", type=int, default=32)
+    ap.add_argument("--max-slots", type=int, default=64)
     a = ap.parse_args()
     print(json.dumps(run_workload(rate=a.rate, duration=a.duration, precision=a.precision,
                                   max_slots=a.max_slots)))
