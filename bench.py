@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # launch list of the current kernels on this workload
 # (profiles/launches_convdiff2d_256x256_fp64_16rhs.md); a kind whose kernels
 # changed since that capture has no entry.
-TRAFFIC = {"solve_front_fwd": 4.0e6}
+TRAFFIC = {"solve_front_fwd": 4.1e6}
 
 
 def _args():
