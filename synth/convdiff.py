@@ -6,16 +6,16 @@ arithmetic and is shared, unchanged, by the CPU oracle, the tests and the
 benchmark.
 
 Problem (the paper's benchmark family, Section 4): -div(a grad u) + v . grad u = f
-on the unit square/cube with u = 0 on the boundary, n points per side,
-h = 1/(n+1), lexicographic numbering with x fastest.
+on the unit square/cube with u = 0 on the boundary, n_k points in direction
+k, h_k = 1/(n_k+1), lexicographic numbering with x fastest.
 
 Discretisation (ours; the paper's own generator is not available):
   * diffusion: 5-/7-point stencil; the coefficient of the face between two
     cells is the harmonic mean of the cells' a; a boundary face uses the
     cell's own a;
   * convection: first-order upwind in advective form, per cell:
-    v_d > 0 adds v_d/h to the diagonal and -v_d/h to the (c, c-e_d) entry,
-    v_d < 0 adds |v_d|/h to the diagonal and -|v_d|/h to the (c, c+e_d) entry;
+    v_d > 0 adds v_d/h_d to the diagonal and -v_d/h_d to the (c, c-e_d) entry,
+    v_d < 0 adds |v_d|/h_d to the diagonal and -|v_d|/h_d to the (c, c+e_d) entry;
     entries that would couple to a boundary node are dropped.
 The result is a non-singular M-matrix, weakly row diagonally dominant (strictly
 on rows next to the boundary).
@@ -77,9 +77,7 @@ def convdiff(dims, a, v):
     dims = tuple(int(d) for d in dims)
     d = len(dims)
     N = int(np.prod(dims))
-    n = dims[0]
-    assert all(s == n for s in dims), "cubic grids only"
-    h = 1.0 / (n + 1)
+    hs = [1.0 / (dims[k] + 1) for k in range(d)]   # the unit box, n_k points in direction k
     a = np.asarray(a, dtype=np.float64).reshape(N)
     v = np.asarray(v, dtype=np.float64).reshape(N, d)
     strides = [1]
@@ -98,10 +96,10 @@ def convdiff(dims, a, v):
             nb = np.where(inside, idx + sgn * strides[k], idx)
             an = a[nb]
             face = np.where(inside, 2.0 * a * an / (a + an), a)
-            diag += face / (h * h)
-            offd[(k, sgn)] -= np.where(inside, face / (h * h), 0.0)
+            diag += face / (hs[k] * hs[k])
+            offd[(k, sgn)] -= np.where(inside, face / (hs[k] * hs[k]), 0.0)
         vk = v[:, k]
-        up = np.abs(vk) / h
+        up = np.abs(vk) / hs[k]
         diag += up
         # v > 0: couple to c - e_k ; v < 0: couple to c + e_k
         has_m = (vk > 0) & (coords[k] - 1 >= 0)

@@ -107,3 +107,32 @@ def test_batch_gmres_bad_parts(spaqr_lib):
         sq.spaqr_gmres_batch(F, *csr, np.array([0, 5, 5, ob.n]), B)
     with pytest.raises(sq.SpaqrError):
         sq.spaqr_gmres_batch(F, *csr, np.array([0, ob.n - 1]), B)
+
+
+def test_batch_of_one_is_the_single_factor(spaqr_lib):
+    import torch
+    p = config_problem("2d_lognormal", n=48, seed=21)
+    ob, F, csr = _batch([p])
+    _, Fs, cs = _single(p)
+    B = torch.from_numpy(np.random.default_rng(3).standard_normal((2, p.n))).cuda().T
+    X = sq.spaqr_solve(F, B)
+    Xs = sq.spaqr_solve(Fs, B)
+    assert torch.equal(X, Xs)
+
+
+def test_batch_mixing_2d_and_3d(spaqr_lib):
+    import torch
+    probs = [config_problem("3d_uniform_a", n=10, seed=31), config_problem("2d_uniform_a", n=40, seed=32),
+             config_problem("3d_uniform_a", n=6, seed=33)]
+    ob, F, csr = _batch(probs)
+    B = torch.from_numpy(np.random.default_rng(4).standard_normal(ob.n)).cuda()
+    X, it, rr = sq.spaqr_gmres_batch(F, *csr, ob.part_ptr, B, tol=1e-12)
+    assert (rr <= 1e-12).all()
+    X = X.cpu().numpy()
+    Bh = B.cpu().numpy()
+    for i, p in enumerate(probs):
+        a, b = ob.part_ptr[i], ob.part_ptr[i + 1]
+        _, Fs, cs = _single(p)
+        Xs, _, _ = sq.spaqr_gmres(Fs, *cs, torch.from_numpy(Bh[a:b].copy()).cuda(), tol=1e-12)
+        d = np.linalg.norm(X[a:b] - Xs.cpu().numpy()) / np.linalg.norm(Xs.cpu().numpy())
+        assert d <= 1e-10, (i, d)

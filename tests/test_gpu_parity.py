@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2010_06807_gb300 as sq
 from oracle import spaqr as osq
-from synth.convdiff import config_problem, rhs
+from synth.convdiff import Problem, config_problem, convdiff, rhs
 
 pytestmark = pytest.mark.gpu
 
@@ -83,6 +83,26 @@ def test_solve_matches_oracle(dev, kind, n, L, eps, skip):
     if eps == 0.0:
         rel = np.linalg.norm(b - p.matvec(xg), axis=0) / np.linalg.norm(b, axis=0)
         assert rel.max() < 1e-12
+
+
+@pytest.mark.parametrize("dims,eps,skip", [((20, 36), 1e-2, 2), ((37, 12), 1e-3, 1), ((6, 8, 11), 1e-2, 2),
+                                            ((3, 70), 1e-2, 0)])
+def test_nonsquare_grids_match_oracle(dev, dims, eps, skip):
+    """Boxes whose cuts change dimension between levels, a mixed-sign
+    velocity, and a strip two cells short of a single cut."""
+    rng = np.random.Generator(np.random.PCG64(77 + len(dims)))
+    N = int(np.prod(dims))
+    a = rng.uniform(0.1, 10.0, N)
+    v = np.tile(rng.uniform(-20.0, 20.0, len(dims)), (N, 1))
+    p = Problem(dims, *convdiff(dims, a, v))
+    ordl, F, _ = _gpu_factor(p, dev, eps, 0, skip)
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, p.dims, eps, nlevels=ordl.L, skip=skip)
+    _check_ranks(F, Fo)
+    b = rhs(p, 2, seed=5)
+    xo = osq.solve(Fo, b)
+    xg = sq.spaqr_solve(F, _colmajor(b, dev)).cpu().numpy()
+    err = np.linalg.norm(xg - xo, axis=0) / np.linalg.norm(xo, axis=0)
+    assert err.max() <= TOL, err
 
 
 def test_host_buffers_match_device_buffers(dev):
