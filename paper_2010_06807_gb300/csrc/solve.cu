@@ -678,9 +678,18 @@ __global__ void __launch_bounds__(NT) k_dots(int64_t n, int nrhs, VCols vc, cons
     vc.range(v, n, base, len);
     const double* u = U + (int64_t)i * n * nrhs + base;
     const double* w = W + base;
-    double s = 0.0;
-    for (int64_t r = threadIdx.x; r < len; r += NT) s += u[r] * w[r];
-    s = block_sum(s, red);
+    // four independent partial sums per thread (loads in flight), added in a
+    // fixed order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t r = threadIdx.x;
+    for (; r + 3 * NT < len; r += 4 * NT) {
+        s0 += u[r] * w[r];
+        s1 += u[r + NT] * w[r + NT];
+        s2 += u[r + 2 * NT] * w[r + 2 * NT];
+        s3 += u[r + 3 * NT] * w[r + 3 * NT];
+    }
+    for (; r < len; r += NT) s0 += u[r] * w[r];
+    double s = block_sum((s0 + s1) + (s2 + s3), red);
     if (threadIdx.x == 0) out[i + (int64_t)v * nout] = s;
 }
 
@@ -1338,6 +1347,22 @@ bool capture_apply(const spaqr_factor_s* F, int nrhs, const double* Vin, double*
     return ok;
 }
 
+// Makes the factor's device current for the scope of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // A private non-blocking stream for one call, ordered after the caller's
 // stream: graphs cannot be captured on the legacy default stream.
 struct PrivateStream {
@@ -1376,6 +1401,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         return SPAQR_ERR_INVALID_ARG;
     }
     if (nrhs == 0) return SPAQR_OK;
+    DeviceGuard dg(F->device);   // outlives the stream and allocations below
     keep_pool_memory(F->device);
     const bool graphs = graphs_on() && !prof_on();
     PrivateStream ps;   // destroyed after C, whose frees are ordered on it
