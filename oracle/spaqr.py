@@ -11,6 +11,7 @@ Matrices", arXiv 2010.06807):
                                     stacked column block, fill among neighbours)
   block-diagonal scaling .......... Section 2.5 ("Scaling of Interfaces")
   sparsification (scaled form) .... Sections 2.2/2.5, rank rule of Section 4
+  sparsification (unscaled form) .. Sections 2.2/3.2 with sigma of Lemma 1
   merge ........................... Section 2.6
   factor application .............. Section 2.7 (Q^T A W^{-1} ~ I)
   GMRES to ||Ax-b||/||b|| <= 1e-12  Section 4
@@ -37,6 +38,18 @@ Readings where the paper is silent (also in the design notes):
   F6  Q_p keeps only the r reflectors of the truncated CPQR; the first r
       columns of Q_p are the coarse basis, and the fine space is its
       complement (the solve only depends on that subspace).
+  F7  Unscaled variant (scaling=False; Sections 2.2 and 3.2, Lemma 1): no
+      scaling step; every interface p of a sparsified level gets
+      sigma_p = 1 / sigma_min(A_p), A_p = [A_pp; A_np] stacked over all rows
+      of column p, and M_p = [A_{k1 p}^T ... | sigma_p A_pp^T A_{p j1} ...]
+      (row-neighbours first, then column-neighbours, ascending ids).  After the
+      CPQR, T_p = A_pp Q_p; the fine columns f = T_p[:, r:] get a Householder
+      QR H_p (R_ff), H_p^T is applied to the coarse columns (top |f| rows:
+      R_fc, bottom rows: the new coarse diagonal block) and to every block
+      A_pj (top |f| rows: R_fn, dropped).  A_np Q_pf and R_fn are dropped.
+      Two-phase like F4: every sigma_p, Q_p and H_p comes from the matrix at
+      the start of the step, then all blocks are transformed,
+      A_ij <- (H_i^T A_ij)[f_i:, :] Q_j[:, :r_j].
 """
 from collections import defaultdict
 
@@ -77,11 +90,13 @@ def _greedy_colours(fronts, rows_of):
 
 
 def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
-           col_normalize=True, record_blocks=False):
+           col_normalize=True, scaling=True):
     """Compute the spaQR factorisation (Algorithm 2) of the CSR matrix A.
 
-    Returns a Factor with the op sequence and diagnostics (ranks per level,
-    CPQR pivot norms, algorithmic flop counts).
+    scaling=False gives the unscaled variant of Sections 2.2 / 3.2 (reading
+    F7).  Returns a Factor with the op sequence and diagnostics (ranks per
+    level, CPQR pivot norms, algorithmic flop counts; for the unscaled
+    variant also sigma_p and the Lemma 1 quantities per interface).
     """
     rowptr = np.asarray(rowptr, dtype=np.int64)
     colind = np.asarray(colind, dtype=np.int64)
@@ -129,6 +144,8 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
     F.rdiag = []       # per level: {cluster: pivot norms}
     F.dropped = []     # per level: {cluster: (||dropped||_F, #cols of M_p, |R_11|)}
     F.steps = []       # per level: dict(fronts, colours, R, C)
+    F.scaling = bool(scaling)
+    F.lemma = []       # per level (unscaled): {cluster: dict(sigma, smin, Rff, Wfn2, Rfn)}
     flops = defaultdict(float)
 
     for k in range(1, L + 1):
@@ -183,8 +200,11 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
         F.ranks.append({})
         F.rdiag.append({})
         F.dropped.append({})
+        F.lemma.append({})
+        if k > skip and active and not scaling:
+            blocks = _sparsify_unscaled(F, k, eps, blocks, active, size, ops, flops)
         # (ii) block-diagonal scaling, (iii) sparsification
-        if k > skip and active:
+        if k > skip and active and scaling:
             act = sorted(active)
             U = {}
             for p in act:
@@ -284,6 +304,76 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
     return F
 
 
+def _sparsify_unscaled(F, k, eps, blocks, active, size, ops, flops):
+    """One sparsified level of the unscaled variant (reading F7).
+
+    Returns the new block dictionary (coarse blocks only) and updates size.
+    """
+    act = sorted(active)
+    col_rows = defaultdict(list)
+    row_cols = defaultdict(list)
+    for (i, j) in blocks:
+        col_rows[j].append(i)
+        row_cols[i].append(j)
+    info = {}
+    for p in act:
+        np_ = size[p]
+        if np_ == 0:
+            continue
+        rows = sorted(col_rows[p])
+        Ap = np.vstack([blocks[(i, p)] for i in rows])
+        smin = float(np.linalg.svd(Ap, compute_uv=False)[-1])
+        if smin == 0.0:
+            raise ZeroDivisionError("interface column block A_p is rank deficient")
+        sigma = 1.0 / smin
+        App = blocks[(p, p)]
+        rparts = [blocks[(i, p)].T for i in rows if i != p]
+        cparts = [sigma * (App.T @ blocks[(p, j)]) for j in sorted(row_cols[p]) if j != p]
+        nrow = sum(b.shape[1] for b in rparts)
+        Mp = np.hstack(rparts + cparts) if rparts or cparts else np.zeros((np_, 0))
+        Vq, tq, r, rd, _ = dense.cpqr_truncated(Mp, eps)
+        flops["sparsify"] += 4.0 * np_ * Mp.shape[1] * r
+        QtM = dense.apply_qt(Vq, tq, Mp) if r > 0 else Mp
+        # T_p = A_pp Q_p, Householder QR of its fine columns, H^T on the coarse ones
+        Tp = dense.apply_qt(Vq, tq, App.T).T if r > 0 else App.copy()
+        f = np_ - r
+        if f > 0:
+            Vh, th, Rff = dense.qr(Tp[:, r:])
+            if np.any(np.diag(Rff) == 0.0):
+                raise ZeroDivisionError("zero diagonal in R_ff")
+            Cc = dense.apply_qt(Vh, th, Tp[:, :r])
+        else:
+            Vh, th, Rff = np.zeros((np_, 0)), np.zeros(0), np.zeros((0, 0))
+            Cc = Tp[:, :r]
+        info[p] = dict(Vq=Vq, tq=tq, r=r, Vh=Vh, th=th, f=f, Acc=Cc[f:].copy())
+        F.ranks[-1][p] = (np_, r)
+        F.rdiag[-1][p] = rd
+        F.dropped[-1][p] = (float(np.linalg.norm(QtM[r:])), Mp.shape[1], float(rd[0]) if len(rd) else 0.0)
+        F.lemma[-1][p] = dict(sigma=sigma, smin=smin, Rff=Rff, Wfn2=QtM[r:, nrow:].copy(),
+                              Wfn1=QtM[r:, :nrow].copy(), Ap=Ap, App=App.copy(),
+                              Apn=np.hstack([blocks[(p, j)] for j in sorted(row_cols[p]) if j != p] or
+                                            [np.zeros((np_, 0))]), Rfn=[])
+        ops.append(("usparsify", k, p, Vq, tq, r, Vh, th, Rff, Cc[:f].copy(), np_))
+    newb = {}
+    for (i, j), B in blocks.items():
+        ri = info[i]["r"] if i in info else 0
+        rj = info[j]["r"] if j in info else 0
+        if i == j:
+            newb[(i, i)] = info[i]["Acc"] if i in info else np.zeros((0, 0))
+            continue
+        fi = info[i]["f"] if i in info else 0
+        if fi > 0 and size[j] > 0:
+            B = dense.apply_qt(info[i]["Vh"], info[i]["th"], B)
+            F.lemma[-1][i]["Rfn"].append((j, B[:fi].copy()))
+        B = B[fi:]
+        if rj > 0 and B.shape[0] > 0:
+            B = dense.apply_qt(info[j]["Vq"], info[j]["tq"], B.T).T
+        newb[(i, j)] = B[:, :rj].copy()
+    for p in act:
+        size[p] = info[p]["r"] if p in info else 0
+    return newb
+
+
 def _apply_inverse_permuted(F, y):
     """Apply C_1 ... C_K L_K ... L_1 to y (rows in the new ordering)."""
     o = F.ordering
@@ -313,6 +403,12 @@ def _apply_inverse_permuted(F, y):
                 cur[p] = dense.apply_qt(V, tau, cur[p])
             saved[("f", k, p)] = cur[p][r:].copy()
             cur[p] = cur[p][:r].copy()
+        elif kind == "usparsify":
+            _, k, p, Vq, tq, r, Vh, th, Rff, Rfc, nb = op
+            f = nb - r
+            yp = dense.apply_qt(Vh, th, cur[p]) if f > 0 else cur[p]
+            saved[("f", k, p)] = yp[:f].copy()
+            cur[p] = yp[f:].copy()
         elif kind == "merge":
             _, k, mapping = op
             new = {}
@@ -337,6 +433,15 @@ def _apply_inverse_permuted(F, y):
             xp = np.vstack([x[p], saved[("f", k, p)]])
             if r > 0:
                 xp = dense.apply_q(V, tau, xp)
+            x[p] = xp
+        elif kind == "usparsify":
+            _, k, p, Vq, tq, r, Vh, th, Rff, Rfc, nb = op
+            xc = x[p]
+            yf = saved[("f", k, p)]
+            xf = dense.solve_upper(Rff, yf - Rfc @ xc) if nb > r else yf
+            xp = np.vstack([xc, xf])
+            if r > 0:
+                xp = dense.apply_q(Vq, tq, xp)
             x[p] = xp
         elif kind == "scale":
             _, k, p, V, tau, R = op
