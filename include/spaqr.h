@@ -77,7 +77,11 @@ typedef struct {
  * (|R_ii| >= eps |R_11| is kept, Section 4), eps = 0 keeps everything.
  * nlevels: 0 chooses ceil(log2(N/64)) (Section 4).  skip: number of levels
  * (from the leaves) factored before scaling/sparsification starts.
- * scaling must be 1 (the unscaled variant is not built).  precision:
+ * scaling: 1 (default) scales every interface before sparsifying it
+ * (Section 2.5: A_pp -> I); 0 selects the unscaled variant of Sections
+ * 2.2 / 3.2: no scaling, M_p = [A_np^T | sigma_p A_pp^T A_pn] with
+ * sigma_p = 1 / sigma_min([A_pp; A_np]) (Lemma 1), then a Householder QR of
+ * the fine columns of A_pp Q_p whose R_fn part is dropped.  precision:
  * SPAQR_FP64 (plain form) or SPAQR_FP32 (mixed form: factor stored and
  * applied in FP32, CPQR pivots from FP32 norms but each |R_kk| recomputed in
  * FP64 for the rank decision; GMRES around it stays FP64).
@@ -178,8 +182,9 @@ void spaqr_ordering_destroy(spaqr_ordering* ord);
  * Temporaries come from the device's default memory pool (cudaMallocAsync);
  * the first call on a device raises that pool's release threshold so freed
  * memory stays with the process for reuse.
- * Errors: INVALID_ARG, UNSUPPORTED (scaling = 0, unknown precision), OOM,
- * CUDA, NO_DEVICE. */
+ * Errors: INVALID_ARG (scaling other than 0 / 1), UNSUPPORTED (unknown
+ * precision), SINGULAR (zero column, zero diagonal of R_ss / R_pp, a rank
+ * deficient A_p or R_ff of the unscaled variant), OOM, CUDA, NO_DEVICE. */
 int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const spaqr_opts* opts,
                  spaqr_factor_t** out);
 
@@ -256,6 +261,15 @@ int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out);
  * margins[2*i], margins[2*i+1] if margins != NULL. */
 int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, double* margins,
                        int cap, int* count);
+
+/* sigma_p = 1 / sigma_min(A_p) of the interfaces sparsified at level k by the
+ * unscaled variant (Lemma 1), in the order of spaqr_factor_ranks; 0 for the
+ * scaled variant.  Writes up to cap values into sigma (may be NULL) and the
+ * count into *count.  Computed on the device in FP64: Householder QR of A_p,
+ * then Lanczos with full reorthogonalisation on (R^T R)^{-1}, stopped when
+ * the largest Ritz value of four consecutive steps agrees to 1e-15 relative.
+ * Errors: INVALID_ARG (null F or count, level out of range). */
+int spaqr_factor_sigmas(const spaqr_factor_t* F, int level, double* sigma, int cap, int* count);
 
 void spaqr_factor_destroy(spaqr_factor_t* F);
 

@@ -15,8 +15,14 @@ __all__ = ["house", "qr", "apply_qt", "apply_q", "cpqr_truncated", "solve_upper"
            "solve_upper_right"]
 
 
-def house(col):
-    """Return (v, tau, beta) for the column vector col (length >= 1)."""
+def house(col, sign_tol=0.0):
+    """Return (v, tau, beta) for the column vector col (length >= 1).
+
+    sign_tol > 0: alpha counts as negative only below -sign_tol * |col|, so a
+    leading entry that is zero up to rounding always gives beta = -|col|
+    (both signs give a valid reflector; the tolerance keeps rounding from
+    choosing between them).
+    """
     alpha = float(col[0])
     x = col[1:]
     xnorm2 = float(np.dot(x, x)) if x.shape[0] else 0.0
@@ -25,18 +31,18 @@ def house(col):
     if xnorm2 == 0.0:
         return v, 0.0, alpha
     s = np.sqrt(alpha * alpha + xnorm2)
-    beta = -s if alpha >= 0.0 else s
+    beta = -s if alpha >= -sign_tol * s else s
     tau = (beta - alpha) / beta
     v[1:] = x / (alpha - beta)
     return v, tau, beta
 
 
-def qr(A):
+def qr(A, sign_tol=0.0):
     """Unblocked Householder QR of an m x n matrix (m >= n not required).
 
     Returns (V, tau, R): V is m x t unit lower trapezoidal, tau has t entries,
     R is t x n upper trapezoidal, t = min(m, n).  A = Q R with
-    Q = H_0 H_1 ... H_{t-1} (first t columns).
+    Q = H_0 H_1 ... H_{t-1} (first t columns).  sign_tol: see house().
     """
     A = np.array(A, dtype=np.float64, copy=True)
     m, n = A.shape
@@ -44,7 +50,7 @@ def qr(A):
     V = np.zeros((m, t))
     tau = np.zeros(t)
     for k in range(t):
-        v, tk, beta = house(A[k:, k])
+        v, tk, beta = house(A[k:, k], sign_tol)
         V[k:, k] = v
         tau[k] = tk
         A[k, k] = beta

@@ -50,6 +50,11 @@ Readings where the paper is silent (also in the design notes):
       Two-phase like F4: every sigma_p, Q_p and H_p comes from the matrix at
       the start of the step, then all blocks are transformed,
       A_ij <- (H_i^T A_ij)[f_i:, :] Q_j[:, :r_j].
+  F8  The fine columns A_pp Q_pf often have a leading entry that is zero in
+      exact arithmetic, and either reflector sign is valid there.  In the QR
+      of those columns a leading entry within 1e-12 |column| of zero takes
+      beta = -|column| (sign +1), so that rounding cannot choose the
+      reflection and with it the basis of the coarse rows.
 """
 from collections import defaultdict
 
@@ -338,7 +343,7 @@ def _sparsify_unscaled(F, k, eps, blocks, active, size, ops, flops):
         Tp = dense.apply_qt(Vq, tq, App.T).T if r > 0 else App.copy()
         f = np_ - r
         if f > 0:
-            Vh, th, Rff = dense.qr(Tp[:, r:])
+            Vh, th, Rff = dense.qr(Tp[:, r:], sign_tol=1e-12)
             if np.any(np.diag(Rff) == 0.0):
                 raise ZeroDivisionError("zero diagonal in R_ff")
             Cc = dense.apply_qt(Vh, th, Tp[:, :r])

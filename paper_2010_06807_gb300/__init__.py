@@ -18,7 +18,7 @@ __all__ = [
     "SpaqrError", "load_library", "spaqr_order", "spaqr_order_batch", "blockdiag_csr",
     "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
-    "spaqr_factor_info", "spaqr_factor_ranks", "Ordering", "Factor", "num_levels",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
     "spaqr_factor_tuning",
 ]
@@ -81,7 +81,7 @@ EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_batch", "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
-    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_destroy", "spaqr_stats_reset",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
 ]
 
@@ -115,6 +115,7 @@ def load_library(path=None):
                                           vp, vp, vp]
         lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
         lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
+        lib.spaqr_factor_sigmas.argtypes = [vp, i32, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_factor_destroy.argtypes = [vp]
         lib.spaqr_factor_destroy.restype = None
     if hasattr(lib, "spaqr_stats"):
@@ -481,6 +482,17 @@ def spaqr_factor_ranks(F, level):
     _check(_lib.spaqr_factor_ranks(F._h, int(level), pairs.ctypes.data, margins.ctypes.data, n,
                                    ctypes.byref(cnt)))
     return pairs[:2 * n].reshape(n, 2), margins[:2 * n].reshape(n, 2)
+
+
+def spaqr_factor_sigmas(F, level):
+    """sigma_p = 1 / sigma_min(A_p) per interface of a level (unscaled variant; 0 when scaled)."""
+    load_library()
+    cnt = ctypes.c_int(0)
+    _check(_lib.spaqr_factor_sigmas(F._h, int(level), None, 0, ctypes.byref(cnt)))
+    n = cnt.value
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    _check(_lib.spaqr_factor_sigmas(F._h, int(level), out.ctypes.data, n, ctypes.byref(cnt)))
+    return out[:n]
 
 
 def spaqr_stats_reset():

@@ -113,9 +113,12 @@ struct Mat {
 // Householder vector of column `col` (rows k..m-1, element stride `stride`)
 // in place: col[k] <- beta, col[k+1..] <- v.  Returns tau to every thread.
 // beta, tau and the scaling are computed in FP64 whatever the storage type;
-// the norm is accumulated in the storage type.
+// the norm is accumulated in the storage type.  sign_tol > 0: alpha counts as
+// negative only below -sign_tol sqrt(alpha^2 + x.x), so that a leading entry
+// that is zero up to rounding always gives beta = -norm.
 template <class real>
-__device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, int m, double* red) {
+__device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, int m, double* red,
+                                            double sign_tol = 0.0) {
     real part = 0;
     for (int r = k + 1 + threadIdx.x; r < m; r += NT) {
         const real x = col[(int64_t)r * stride];
@@ -126,7 +129,7 @@ __device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, in
     double tk = 0.0, beta = alpha, denom = 1.0;
     if (xn2 != 0.0) {
         const double s = sqrt(alpha * alpha + xn2);
-        beta = alpha >= 0.0 ? -s : s;
+        beta = alpha >= -sign_tol * s ? -s : s;
         tk = (beta - alpha) / beta;
         denom = alpha - beta;
     }
@@ -369,7 +372,7 @@ __host__ __device__ constexpr int64_t qr_smem_bytes(int esz, int qc, int prow = 
 template <class real>
 static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, int pe, real* tau, real* T, int ldt,
                                            bool staged, double* red, real* P, real* Wk, real* G, real* Ps,
-                                           int64_t* ldv) {
+                                           int64_t* ldv, double sign_tol = 0.0) {
     // panel view: column k, row r -> Pb[r + (k - p0) * ldp]
     real* Pb;
     int64_t ldp;
@@ -387,7 +390,7 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
     }
     for (int k = p0; k < pe; k++) {
         real* col = Pb + (int64_t)(k - p0) * ldp;
-        const double tkd = cta_house(col, 1, k, m, red);
+        const double tkd = cta_house(col, 1, k, m, red, sign_tol);
         const real tk = (real)tkd;
         if (threadIdx.x == 0) tau[k] = tk;
         const int ncol = pe - k - 1;
@@ -448,7 +451,7 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
 // smem: qr_smem_bytes(sizeof(real), qc, prow).
 template <class real>
 static __device__ void cta_qr(real* A, int64_t lda, int m, int n, real* tau, real* T, int ldt, int qc, int prow,
-                              double* smem) {
+                              double* smem, double sign_tol = 0.0) {
     double* red = smem;
     real* P = reinterpret_cast<real*>(red + NWARP);   // NT partial dots
     real* Wk = P + NT;         // NB
@@ -460,7 +463,7 @@ static __device__ void cta_qr(real* A, int64_t lda, int m, int n, real* tau, rea
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pe = (t - p0 < NB ? t : p0 + NB);   // panel columns [p0, pe)
         int64_t ldp;
-        const real* Vp = cta_qr_panel(A, lda, m, p0, pe, tau, T, ldt, staged, red, P, Wk, G, Ps, &ldp);
+        const real* Vp = cta_qr_panel(A, lda, m, p0, pe, tau, T, ldt, staged, red, P, Wk, G, Ps, &ldp, sign_tol);
         // trailing update of the columns right of the panel
         if (pe < n) {
             Mat<real> B{A + p0 + (int64_t)pe * lda, 1, lda, nullptr};

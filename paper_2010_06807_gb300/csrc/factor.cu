@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NT) k_qr(const QRTask<real>* __restrict__ task
     extern __shared__ double sm[];
     const QRTask<real> t = tasks[blockIdx.x];
     const int tt = t.m < t.n ? t.m : t.n;
-    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, prow, sm);
+    cta_qr(t.A, t.lda, t.m, t.n, t.tau, t.T, tt, QC, prow, sm, t.sign_tol);
     if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
@@ -108,7 +108,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
         const int pe = (tt - p0 < NB ? tt : p0 + NB);
         if (q == 0) {
             int64_t ldp;
-            cta_qr_panel(t.A, t.lda, m, p0, pe, t.tau, t.T, tt, staged, red, P, Wk, G, Ps, &ldp);
+            cta_qr_panel(t.A, t.lda, m, p0, pe, t.tau, t.T, tt, staged, red, P, Wk, G, Ps, &ldp, t.sign_tol);
         }
         cl.sync();
         if (pe < n) {
@@ -476,18 +476,263 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __res
             X[r + (int64_t)c * mi] = t.A[r + (int64_t)c * t.lda];
         }
         __syncthreads();
-        cta_apply_q_chunked(t.Vi, mi, mi, t.ri, t.Ti, t.ldti, true,
-                            Mat<real>{X + (int64_t)c0 * mi, 1, mi, nullptr}, qn, QC, true, W);
+        if (t.li > 0)
+            cta_apply_q_chunked(t.Vi, mi, mi, t.li, t.Ti, t.ldti, t.lexp != 0,
+                                Mat<real>{X + (int64_t)c0 * mi, 1, mi, nullptr}, qn, QC, true, W);
         return;
     }
-    // coarse rows [off, off + len) (< r_i): X <- X Q_j, i.e. X^T <- Q_j^T X^T
+    // kept rows lkeep + [off, off + len): X <- X Q_j, i.e. X^T <- Q_j^T X^T
     // with X^T(r, c) = X[c + r * mi]; then the r_i x r_j coarse block
     const int r0 = pc.off, rn = pc.len;
-    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat<real>{X + r0, mi, 1, nullptr}, rn, QC, true, W);
+    real* Xk = X + t.lkeep;
+    cta_apply_q_chunked(t.Vj, nj, nj, t.rj, t.Tj, t.ldtj, true, Mat<real>{Xk + r0, mi, 1, nullptr}, rn, QC, true, W);
     for (int64_t o = threadIdx.x; o < (int64_t)rn * t.rj; o += NT) {
         const int p = r0 + (int)(o % rn), q = (int)(o / rn);
-        t.D[p + (int64_t)q * t.ldd] = X[p + (int64_t)q * mi];
+        t.D[p + (int64_t)q * t.ldd] = Xk[p + (int64_t)q * mi];
     }
+}
+
+// B <- Q^T B over a column chunk, or B <- B Q over a row chunk (Q^T applied
+// to the transposed view).
+template <class real>
+__global__ void __launch_bounds__(NT) k_refl_apply(const ReflTask<real>* __restrict__ tasks,
+                                                   const ScalePiece* __restrict__ pieces) {
+    extern __shared__ double sm[];
+    real* W = reinterpret_cast<real*>(sm);
+    const ScalePiece pc = pieces[blockIdx.x];
+    const ReflTask<real> t = tasks[pc.task];
+    const Mat<real> B = t.right ? Mat<real>{t.B + pc.off, t.ldb, 1, nullptr}
+                                : Mat<real>{t.B + (int64_t)pc.off * t.ldb, 1, t.ldb, nullptr};
+    cta_apply_q_chunked(t.V, t.ldv, t.m, t.t, t.T, t.ldt, t.vexp != 0, B, pc.len, QC, true, W);
+}
+
+// C = sigma_p (A_pp^T A_pj) over a column chunk of A_pj (the second part of
+// the unscaled M_p, Section 3.2): one output per thread, its dot product one
+// sequential chain.
+template <class real>
+__global__ void __launch_bounds__(NT) k_atb_sigma(const AtbTask<real>* __restrict__ tasks,
+                                                  const ScalePiece* __restrict__ pieces) {
+    const ScalePiece pc = pieces[blockIdx.x];
+    const AtbTask<real> t = tasks[pc.task];
+    const double sg = *t.sigma;
+    const int n = t.n;
+    for (int o = threadIdx.x; o < n * pc.len; o += NT) {
+        const int r = o % n, c = pc.off + o / n;
+        const real* a = t.A + (int64_t)r * t.lda;
+        const real* b = t.B + (int64_t)c * t.ldb;
+        real acc = 0;
+        for (int u = 0; u < n; u++) acc += a[u] * b[u];
+        t.C[r + (int64_t)c * n] = (real)(sg * (double)acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sigma_p = 1 / sigma_min(A_p) (Lemma 1) from the triangular factor R of A_p:
+// sigma_p^2 is the largest eigenvalue of (R^T R)^{-1}.  Lanczos on that
+// operator (two triangular solves per step) with full reorthogonalisation
+// (classical Gram-Schmidt, two passes), from a fixed hashed start vector.
+// Every fourth step the largest eigenvalue of the Lanczos tridiagonal is
+// found by multisection (32 points per round on one warp, Sturm counts) to
+// the last bits, and the iteration stops once it grew by at most 1e-15
+// relative over those four steps, at an invariant subspace, or after kmax
+// steps.  All of it in FP64; one CTA per interface.
+// ---------------------------------------------------------------------------
+constexpr int kLanczosMax = 160;
+
+// Eigenvalues of the k x k symmetric tridiagonal (diagonal a, squared
+// off-diagonal b2) below x: negative pivots of the LDL^T of T - x I.
+__device__ __forceinline__ int sturm_below(const double* a, const double* b2, int k, double x) {
+    int c = 0;
+    double q = a[0] - x;
+    c += q < 0.0;
+    for (int i = 1; i < k; i++) {
+        const double qq = q != 0.0 ? q : 1e-300;
+        q = a[i] - x - b2[i - 1] / qq;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+__device__ __forceinline__ double warp_max_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Largest eigenvalue in [lo, hi] (lo below it, hi above it); warp 0 only.
+__device__ double warp_top_eig(const double* a, const double* b2, int k, double lo, double hi) {
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < 20 && hi - lo > 2.3e-16 * hi; it++) {
+        const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+        const unsigned m = __ballot_sync(0xffffffffu, sturm_below(a, b2, k, x) == k);
+        const double xf = __shfl_sync(0xffffffffu, x, m ? __ffs(m) - 1 : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, m ? (__ffs(m) > 1 ? __ffs(m) - 2 : 0) : 31);
+        if (!m) lo = xf;
+        else {
+            hi = xf;
+            if (__ffs(m) > 1) lo = xp;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// w <- R^{-T} w (R upper n x n, ld; idg = 1 / diag R), blocks of 32: warp 0
+// solves the diagonal block, every thread updates the rows below it.
+template <class real>
+__device__ void lanczos_solve_rt(const real* R, int64_t ld, int n, const double* idg, double* w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int bs = n - b0 < 32 ? n - b0 : 32;
+        if (warp == 0) {
+            double x = lane < bs ? w[b0 + lane] : 0.0;
+            for (int k = 0; k < bs; k++) {
+                const double xk = __shfl_sync(0xffffffffu, x, k) * idg[b0 + k];
+                if (lane == k) x = xk;
+                else if (lane > k && lane < bs) x -= (double)R[(b0 + k) + (int64_t)(b0 + lane) * ld] * xk;
+            }
+            if (lane < bs) w[b0 + lane] = x;
+        }
+        __syncthreads();
+        for (int i = b0 + bs + threadIdx.x; i < n; i += NT) {
+            const real* col = R + b0 + (int64_t)i * ld;
+            double s = 0.0;
+            for (int k = 0; k < bs; k++) s += (double)col[k] * w[b0 + k];
+            w[i] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// w <- R^{-1} w, same blocking from the bottom block up.
+template <class real>
+__device__ void lanczos_solve_r(const real* R, int64_t ld, int n, const double* idg, double* w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = ((n - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
+        const int bs = n - b0 < 32 ? n - b0 : 32;
+        if (warp == 0) {
+            double x = lane < bs ? w[b0 + lane] : 0.0;
+            for (int k = bs - 1; k >= 0; k--) {
+                const double xk = __shfl_sync(0xffffffffu, x, k) * idg[b0 + k];
+                if (lane == k) x = xk;
+                else if (lane < k) x -= (double)R[(b0 + lane) + (int64_t)(b0 + k) * ld] * xk;
+            }
+            if (lane < bs) w[b0 + lane] = x;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < b0; i += NT) {
+            double s = 0.0;
+            for (int k = 0; k < bs; k++) s += (double)R[i + (int64_t)(b0 + k) * ld] * w[b0 + k];
+            w[i] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+template <class real>
+__global__ void __launch_bounds__(NT) k_sigma_min(const SigmaTask<real>* __restrict__ tasks) {
+    __shared__ double alpha[kLanczosMax], beta2[kLanczosMax], hc[kLanczosMax];
+    __shared__ double red[NWARP];
+    __shared__ double theta_sh;
+    __shared__ int bad;
+    const SigmaTask<real> t = tasks[blockIdx.x];
+    const int n = t.n, kmax = t.kmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* Vl = t.work;                         // Lanczos vectors, vector j at Vl + j n
+    double* w = t.work + (int64_t)(kmax + 1) * n;
+    double* idg = w + n;
+    const real* R = t.R;
+    const int64_t ld = t.ldr;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const double d = (double)R[i + (int64_t)i * ld];
+        if (d == 0.0) bad = 1;
+        idg[i] = d != 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) {
+            *t.singular = 1;
+            *t.sigma = 0.0;
+        }
+        return;
+    }
+    // start vector: hashed entries in [0.5, 1.5), normalised
+    double part = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const unsigned h = (unsigned)(i + 1) * 2654435761u;
+        const double v = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+        Vl[i] = v;
+        part += v * v;
+    }
+    const double nrm = sqrt(block_sum(part, red));
+    for (int i = threadIdx.x; i < n; i += NT) Vl[i] /= nrm;
+    __syncthreads();
+    double theta = 0.0;
+    for (int j = 0; j < kmax; j++) {
+        const double* v = Vl + (int64_t)j * n;
+        for (int i = threadIdx.x; i < n; i += NT) w[i] = v[i];
+        __syncthreads();
+        lanczos_solve_rt(R, ld, n, idg, w);
+        lanczos_solve_r(R, ld, n, idg, w);
+        part = 0.0;
+        for (int i = threadIdx.x; i < n; i += NT) part += w[i] * v[i];
+        const double a = block_sum(part, red);
+        const double bp = j > 0 ? sqrt(beta2[j - 1]) : 0.0;
+        for (int i = threadIdx.x; i < n; i += NT) {
+            double x = w[i] - a * v[i];
+            if (j > 0) x -= bp * Vl[(int64_t)(j - 1) * n + i];
+            w[i] = x;
+        }
+        if (threadIdx.x == 0) alpha[j] = a;
+        __syncthreads();
+        for (int pass = 0; pass < 2; pass++) {
+            for (int q = warp; q <= j; q += NWARP) {
+                const double* vq = Vl + (int64_t)q * n;
+                double s = 0.0;
+                for (int i = lane; i < n; i += 32) s += vq[i] * w[i];
+                s = warp_sum(s);
+                if (lane == 0) hc[q] = s;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += NT) {
+                double x = w[i];
+                for (int q = 0; q <= j; q++) x -= hc[q] * Vl[(int64_t)q * n + i];
+                w[i] = x;
+            }
+            __syncthreads();
+        }
+        part = 0.0;
+        for (int i = threadIdx.x; i < n; i += NT) part += w[i] * w[i];
+        const double b2 = block_sum(part, red);
+        if (threadIdx.x == 0) beta2[j] = b2;
+        const int k = j + 1;
+        const bool last = k == kmax || !(sqrt(b2) > 1e-15 * fmax(fabs(a), theta));
+        if (last || (k & 3) == 0) {
+            __syncthreads();
+            if (warp == 0) {
+                double lo = theta, hi = 0.0;
+                for (int i = lane; i < k; i += 32) {
+                    const double bl = i > 0 ? sqrt(beta2[i - 1]) : 0.0, br = i + 1 < k ? sqrt(beta2[i]) : 0.0;
+                    lo = fmax(lo, alpha[i]);
+                    hi = fmax(hi, alpha[i] + bl + br);
+                }
+                lo = warp_max_d(lo);
+                hi = warp_max_d(hi) * (1.0 + 1e-13);
+                if (lo > hi) lo = hi;
+                const double th = warp_top_eig(alpha, beta2, k, lo, hi);
+                if (lane == 0) theta_sh = th;
+            }
+            __syncthreads();
+            const double th_old = theta;
+            theta = theta_sh;
+            if (last || (k >= 8 && theta - th_old <= 1e-15 * theta)) break;
+        }
+        const double b = sqrt(b2);
+        double* vn = Vl + (int64_t)(j + 1) * n;
+        for (int i = threadIdx.x; i < n; i += NT) vn[i] = w[i] / b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *t.sigma = sqrt(theta);
 }
 
 // ---------------------------------------------------------------------------
@@ -661,6 +906,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->skip = opt->skip;
     F->eps = opt->eps;
     F->precision = sizeof(real) == 8 ? SPAQR_FP64 : SPAQR_FP32;
+    F->unscaled = opt->scaling == 0;
     F->esz = (int)sizeof(real);
     static std::once_flag attr_once;
     std::call_once(attr_once, [&] {
@@ -744,6 +990,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     int64_t sbytes = 0;
     F->ranks.assign(L, {});
     F->margins.assign(L, {});
+    F->sigmas.assign(L, {});
 
     for (int k = 0; k < L; k++) {
         const StepPlan& sp = o.steps[k];
@@ -1009,90 +1256,167 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         const bool sparsify = (k + 1 > opt->skip) && !rest.empty();
         std::vector<int64_t> newsz(ncl, 0);
         std::vector<real*> uT(ncl, nullptr), uD(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
+        std::vector<real*> hR(ncl, nullptr), hT(ncl, nullptr), hD(ncl, nullptr);   // unscaled form
+        std::vector<int> hF(ncl, 0);
         std::vector<int> kmax(ncl, 0);
         if (sparsify) {
-            // scaling QR of every diagonal block
-            int64_t ua = 0;
-            for (int p : rest) ua += sz[p] + sz[p] * sz[p] + sz[p] * NB;
-            real* uaux = C.alloc<real>(ua, true);
-            if (C.rc) return C.rc;
-            std::vector<QRTask<real>> sq;
-            double fl_sq = 0, by_sq = 0, fl_sc = 0, by_sc = 0;
-            int tm = 1;
-            int64_t a = 0;
-            for (int p : rest) {
-                real* tau = uaux + a;
-                a += sz[p];
-                uT[p] = uaux + a;
-                a += sz[p] * sz[p];
-                uD[p] = uaux + a;
-                a += sz[p] * NB;
-                if (sz[p] == 0) continue;
-                const int e = sp.find(p, p);
-                if (e < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
-                sq.push_back(QRTask<real>{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p], uD[p], d_flags + 1});
-                tm = std::max<int>(tm, (int)sz[p]);
-                flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
-                fl_sq += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
-                by_sq += 24.0 * sz[p] * sz[p];
-            }
-            // scaling of the off-diagonal blocks
-            std::vector<ScaleTask<real>> sc;
-            size_t smem_sc = 16;
-            for (int j : rest) {
-                if (sz[j] == 0) continue;
-                const int ej = sp.find(j, j);
-                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
-                    const int i = sp.rowidx[e];
-                    if (i == j || sp.is_front[i] || sz[i] == 0) continue;
-                    const int ei = sp.find(i, i);
-                    ScaleTask<real> t;
-                    t.A = blk(e, j);
-                    t.lda = lay.H[j];
-                    t.mi = (int)sz[i];
-                    t.nj = (int)sz[j];
-                    t.Vi = blk(ei, i);
-                    t.ldvi = lay.H[i];
-                    t.Ti = uT[i];
-                    t.Rj = blk(ej, j);
-                    t.ldrj = lay.H[j];
-                    t.Dj = uD[j];
-                    t.q = QC;
-                    smem_sc = (size_t)(2 * NB * QC + NT) * esz;
-                    sc.push_back(t);
-                    const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
-                    flops += fs;
-                    fl_sc += fs;
-                    by_sc += 16.0 * sz[i] * sz[j] + 8.0 * sz[i] * sz[i] + 8.0 * sz[j] * sz[j];
-                }
-            }
-            tstart();
-            if (!sq.empty()) {
-                launch_qr<real>(C, sq, esz, KK_SCALE_QR, fl_sq, by_sq);
+            const bool unscaled = opt->scaling == 0;
+            double* sig = nullptr;
+            if (!unscaled) {
+                // scaling QR of every diagonal block
+                int64_t ua = 0;
+                for (int p : rest) ua += sz[p] + sz[p] * sz[p] + sz[p] * NB;
+                real* uaux = C.alloc<real>(ua, true);
                 if (C.rc) return C.rc;
-                C.launched();
-            }
-            if (!sc.empty()) {
-                // U^T over column chunks of every block, then R^{-1} over row
-                // chunks (the two products of a block are independent across
-                // columns and across rows respectively)
-                std::vector<ScalePiece> pl, pr;
-                for (int t = 0; t < (int)sc.size(); t++) {
-                    for (int c0 = 0; c0 < sc[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sc[t].nj - c0)});
-                    for (int r0 = 0; r0 < sc[t].mi; r0 += 64) pr.push_back({t, r0, std::min(64, sc[t].mi - r0)});
+                std::vector<QRTask<real>> sq;
+                double fl_sq = 0, by_sq = 0, fl_sc = 0, by_sc = 0;
+                int tm = 1;
+                int64_t a = 0;
+                for (int p : rest) {
+                    real* tau = uaux + a;
+                    a += sz[p];
+                    uT[p] = uaux + a;
+                    a += sz[p] * sz[p];
+                    uD[p] = uaux + a;
+                    a += sz[p] * NB;
+                    if (sz[p] == 0) continue;
+                    const int e = sp.find(p, p);
+                    if (e < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
+                    sq.push_back(QRTask<real>{blk(e, p), lay.H[p], (int)sz[p], (int)sz[p], tau, uT[p], uD[p], d_flags + 1});
+                    tm = std::max<int>(tm, (int)sz[p]);
+                    flops += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
+                    fl_sq += 4.0 / 3.0 * sz[p] * sz[p] * sz[p];
+                    by_sq += 24.0 * sz[p] * sz[p];
                 }
-                ScaleTask<real>* d = C.upload(sc, false);
-                ScalePiece* dl = C.upload(pl, false);
-                ScalePiece* dr = C.upload(pr, false);
+                // scaling of the off-diagonal blocks
+                std::vector<ScaleTask<real>> sc;
+                size_t smem_sc = 16;
+                for (int j : rest) {
+                    if (sz[j] == 0) continue;
+                    const int ej = sp.find(j, j);
+                    for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                        const int i = sp.rowidx[e];
+                        if (i == j || sp.is_front[i] || sz[i] == 0) continue;
+                        const int ei = sp.find(i, i);
+                        ScaleTask<real> t;
+                        t.A = blk(e, j);
+                        t.lda = lay.H[j];
+                        t.mi = (int)sz[i];
+                        t.nj = (int)sz[j];
+                        t.Vi = blk(ei, i);
+                        t.ldvi = lay.H[i];
+                        t.Ti = uT[i];
+                        t.Rj = blk(ej, j);
+                        t.ldrj = lay.H[j];
+                        t.Dj = uD[j];
+                        t.q = QC;
+                        smem_sc = (size_t)(2 * NB * QC + NT) * esz;
+                        sc.push_back(t);
+                        const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
+                        flops += fs;
+                        fl_sc += fs;
+                        by_sc += 16.0 * sz[i] * sz[j] + 8.0 * sz[i] * sz[i] + 8.0 * sz[j] * sz[j];
+                    }
+                }
+                tstart();
+                if (!sq.empty()) {
+                    launch_qr<real>(C, sq, esz, KK_SCALE_QR, fl_sq, by_sq);
+                    if (C.rc) return C.rc;
+                    C.launched();
+                }
+                if (!sc.empty()) {
+                    // U^T over column chunks of every block, then R^{-1} over row
+                    // chunks (the two products of a block are independent across
+                    // columns and across rows respectively)
+                    std::vector<ScalePiece> pl, pr;
+                    for (int t = 0; t < (int)sc.size(); t++) {
+                        for (int c0 = 0; c0 < sc[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sc[t].nj - c0)});
+                        for (int r0 = 0; r0 < sc[t].mi; r0 += 64) pr.push_back({t, r0, std::min(64, sc[t].mi - r0)});
+                    }
+                    ScaleTask<real>* d = C.upload(sc, false);
+                    ScalePiece* dl = C.upload(pl, false);
+                    ScalePiece* dr = C.upload(pr, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
+                                 k_scale_apply<real><<<(unsigned)pl.size(), NT, smem_sc, st>>>(d, dl, 0));
+                    C.launched();
+                    SPAQR_LAUNCH(KK_SCALE_APPLY, 0.0, 0.0, st,
+                                 k_scale_apply<real><<<(unsigned)pr.size(), NT, smem_sc, st>>>(d, dr, 1));
+                    C.launched();
+                }
+                tstop(1);
+            } else {
+                // sigma_p = 1 / sigma_min(A_p), A_p = column p over all its
+                // rows (Lemma 1): copy, Householder QR, Lanczos on (R^T R)^{-1}
+                tstart();
+                sig = C.alloc<double>(ncl, false);
+                std::vector<int64_t> mp(ncl, 0), apo(ncl, 0);
+                int64_t atot = 0, wtot = 0, qtot = 0;
+                for (int p : rest) {
+                    if (sz[p] == 0) continue;
+                    if (sp.find(p, p) < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
+                    for (int e = sp.colptr[p]; e < sp.colptr[p + 1]; e++)
+                        if (!sp.is_front[sp.rowidx[e]]) mp[p] += sz[sp.rowidx[e]];
+                    apo[p] = atot;
+                    atot += mp[p] * sz[p];
+                    wtot += (std::min<int64_t>(sz[p], kLanczosMax) + 3) * sz[p];
+                    qtot += sz[p] + sz[p] * sz[p];
+                }
+                real* Ap = C.alloc<real>(atot, false);
+                real* Aq = C.alloc<real>(qtot, false);
+                double* lw = C.alloc<double>(wtot, false);
                 if (C.rc) return C.rc;
-                SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
-                             k_scale_apply<real><<<(unsigned)pl.size(), NT, smem_sc, st>>>(d, dl, 0));
-                C.launched();
-                SPAQR_LAUNCH(KK_SCALE_APPLY, 0.0, 0.0, st,
-                             k_scale_apply<real><<<(unsigned)pr.size(), NT, smem_sc, st>>>(d, dr, 1));
-                C.launched();
+                std::vector<SparsifyTask<real>> cpy;
+                std::vector<QRTask<real>> aq;
+                std::vector<SigmaTask<real>> sgt;
+                double fl_a = 0, by_a = 0;
+                int64_t qo = 0, wo = 0;
+                for (int p : rest) {
+                    if (sz[p] == 0) continue;
+                    int64_t ro = 0;
+                    for (int e = sp.colptr[p]; e < sp.colptr[p + 1]; e++) {
+                        const int i = sp.rowidx[e];
+                        if (sp.is_front[i] || sz[i] == 0) continue;
+                        SparsifyTask<real> t;
+                        std::memset(&t, 0, sizeof(t));
+                        t.A = blk(e, p);
+                        t.lda = lay.H[p];
+                        t.mi = (int)sz[i];
+                        t.nj = (int)sz[p];
+                        t.D = Ap + apo[p] + ro;
+                        t.ldd = mp[p];
+                        t.mode = 2;
+                        cpy.push_back(t);
+                        ro += sz[i];
+                    }
+                    aq.push_back(QRTask<real>{Ap + apo[p], mp[p], (int)mp[p], (int)sz[p], Aq + qo,
+                                              Aq + qo + sz[p], nullptr, d_flags + 1});
+                    qo += sz[p] + sz[p] * sz[p];
+                    const int km = (int)std::min<int64_t>(sz[p], kLanczosMax);
+                    sgt.push_back(SigmaTask<real>{Ap + apo[p], mp[p], lw + wo, sig + p, d_flags + 1, (int)sz[p], km});
+                    wo += (int64_t)(km + 3) * sz[p];
+                    const double m_ = (double)mp[p], n_ = (double)sz[p];
+                    flops += 2.0 * m_ * n_ * n_ - 2.0 / 3.0 * n_ * n_ * n_;
+                    fl_a += 2.0 * m_ * n_ * n_ - 2.0 / 3.0 * n_ * n_ * n_;
+                    by_a += 16.0 * m_ * n_;
+                }
+                if (!cpy.empty()) {
+                    std::vector<ScalePiece> pc;
+                    for (int t = 0; t < (int)cpy.size(); t++) pc.push_back({t, 0, 0});
+                    SparsifyTask<real>* d = C.upload(cpy, false);
+                    ScalePiece* dp = C.upload(pc, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_SIGMA, 0.0, by_a, st, k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
+                    C.launched();
+                    launch_qr<real>(C, aq, esz, KK_SIGMA, fl_a, 0.0);
+                    if (C.rc) return C.rc;
+                    SigmaTask<real>* ds = C.upload(sgt, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_SIGMA, 0.0, 0.0, st, k_sigma_min<real><<<(unsigned)sgt.size(), NT, 0, st>>>(ds));
+                    C.launched();
+                }
+                tstop(2);
             }
-            tstop(1);
             tstart();
             // CPQR of M_p
             std::vector<std::vector<std::pair<int, int>>> rowlist(ncl);   // row i -> (col j, entry)
@@ -1101,7 +1425,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             std::vector<CPQRTask<real>> cp, cpb;
             std::vector<GatherSeg<real>> gs;
             std::vector<int> cp_of(ncl, -1);
-            int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0;
+            int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0, ptot = 0;
             std::vector<int> ncols(ncl, 0);
             for (int p : rest) {
                 if (sz[p] == 0) continue;
@@ -1112,7 +1436,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
                 for (auto& je : rowlist[p]) {
                     const int j = je.first;
-                    if (j != p && !sp.is_front[j]) nc += (int)sz[j];
+                    if (j != p && !sp.is_front[j]) {
+                        nc += (int)sz[j];
+                        ptot += sz[p] * sz[j];
+                    }
                 }
                 ncols[p] = nc;
                 kmax[p] = (int)std::min<int64_t>(sz[p], nc);
@@ -1124,6 +1451,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             real* Mbuf = C.alloc<real>(mtot, false);
             real* Nbuf = C.alloc<real>(ntot, false);
+            // unscaled form: the column-neighbour part of M_p is sigma_p A_pp^T A_pj
+            real* Pbuf = unscaled ? C.alloc<real>(ptot, false) : nullptr;
+            std::vector<AtbTask<real>> atb;
+            int64_t po = 0;
+            double fl_atb = 0, by_atb = 0;
             real* Vbuf = C.alloc<real>(vtot, true);
             real* Tbuf = C.alloc<real>(ttot, true);
             double* Rdg = C.alloc<double>(rtot, false);
@@ -1149,10 +1481,23 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     gs.push_back(GatherSeg<real>{blk(e, p), lay.H[p], (int)sz[i], (int)sz[p], 1, co});
                     co += (int)sz[i];
                 }
+                const int epp = unscaled ? sp.find(p, p) : 0;
+                if (epp < 0) { set_error("interface without diagonal block"); return SPAQR_ERR_SINGULAR; }
                 for (auto& je : rowlist[p]) {
                     const int j = je.first;
                     if (j == p || sp.is_front[j] || sz[j] == 0) continue;
-                    gs.push_back(GatherSeg<real>{blk(je.second, j), lay.H[j], (int)sz[p], (int)sz[j], 0, co});
+                    if (unscaled) {
+                        atb.push_back(AtbTask<real>{blk(epp, p), blk(je.second, j), Pbuf + po, sig + p, lay.H[p],
+                                                    lay.H[j], (int)sz[p], (int)sz[j]});
+                        gs.push_back(GatherSeg<real>{Pbuf + po, sz[p], (int)sz[p], (int)sz[j], 0, co});
+                        po += sz[p] * sz[j];
+                        const double fa = 2.0 * sz[p] * sz[p] * sz[j];
+                        flops += fa;
+                        fl_atb += fa;
+                        by_atb += 8.0 * (sz[p] * sz[p] + 2.0 * sz[p] * sz[j]);
+                    } else {
+                        gs.push_back(GatherSeg<real>{blk(je.second, j), lay.H[j], (int)sz[p], (int)sz[j], 0, co});
+                    }
                     co += (int)sz[j];
                 }
                 t.nseg = (int)gs.size() - t.seg_begin;
@@ -1176,6 +1521,16 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 // large interfaces go to the cluster kernel (CPQR_CS CTAs each)
                 if ((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= CPQR_CS * 64) cpb.push_back(t);
                 else cp.push_back(t);
+            }
+            if (!atb.empty()) {
+                std::vector<ScalePiece> pc;
+                for (int t = 0; t < (int)atb.size(); t++)
+                    for (int c0 = 0; c0 < atb[t].nc; c0 += QC) pc.push_back({t, c0, std::min(QC, atb[t].nc - c0)});
+                AtbTask<real>* d = C.upload(atb, false);
+                ScalePiece* dp = C.upload(pc, false);
+                if (C.rc) return C.rc;
+                SPAQR_LAUNCH(KK_UNSCALED, fl_atb, by_atb, st, k_atb_sigma<real><<<(unsigned)pc.size(), NT, 0, st>>>(d, dp));
+                C.launched();
             }
             const size_t smem_cp = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz;
             GatherSeg<real>* dgs = nullptr;
@@ -1203,6 +1558,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             std::vector<double> rdg(std::max<int64_t>(rtot, 1), 0.0);
             C.cuda(cudaMemcpyAsync(rk.data(), Rk, sizeof(int) * ncl, cudaMemcpyDeviceToHost, st));
             if (rtot > 0) C.cuda(cudaMemcpyAsync(rdg.data(), Rdg, sizeof(double) * rtot, cudaMemcpyDeviceToHost, st));
+            std::vector<double> sgh(ncl, 0.0);
+            if (unscaled) C.cuda(cudaMemcpyAsync(sgh.data(), sig, sizeof(double) * ncl, cudaMemcpyDeviceToHost, st));
             tstop(2);
             C.cuda(cudaStreamSynchronize(st));
             if (C.rc) return C.rc;
@@ -1210,6 +1567,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 newsz[p] = sz[p] == 0 ? 0 : rk[p];
                 if (sz[p] == 0) continue;
                 F->ranks[k].push_back({(int)sz[p], rk[p]});
+                F->sigmas[k].push_back(sgh[p]);
                 const double* rd = rdg.data() + rdg_off[p];
                 const int r = rk[p];
                 const double rr = r < kmax[p] ? rd[r] : (r > 0 ? rd[r - 1] : 0.0);
@@ -1219,6 +1577,101 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 for (int kk = 0; kk < r; kk++) fc += 6.0 * (double)(sz[p] - kk) * (double)(ncols[p] - kk);
                 flops += fc;
                 prof_add(-1, KK_CPQR, fc, 0.0);
+            }
+            if (unscaled) {
+                // T_p = A_pp Q_p; Householder QR of its fine columns
+                // T_p[:, r:] (H_p, R_ff); H_p^T on its coarse columns, whose top
+                // f rows are R_fc and bottom r rows the new diagonal block
+                // (Section 3.2).  T_p stays with the factor for the solve.
+                tstart();
+                int64_t tt = 0;
+                for (int p : rest) {
+                    if (sz[p] == 0) continue;
+                    const int64_t f = sz[p] - newsz[p];
+                    tt += sz[p] * sz[p] + f + f * f + f * NB;
+                }
+                real* tb = C.alloc<real>(tt, true);
+                if (C.rc) return C.rc;
+                std::vector<SparsifyTask<real>> cpy;
+                std::vector<ReflTask<real>> rq, lh;
+                std::vector<QRTask<real>> hq;
+                std::vector<ScalePiece> prq, plh;
+                double fl_t = 0, by_t = 0, fl_h = 0, by_h = 0;
+                int64_t o2 = 0;
+                for (int p : rest) {
+                    if (sz[p] == 0) continue;
+                    const int np_ = (int)sz[p], r = (int)newsz[p], f = np_ - r;
+                    real* Tp = tb + o2;
+                    o2 += (int64_t)np_ * np_;
+                    hR[p] = Tp;
+                    hT[p] = tb + o2 + f;
+                    hD[p] = tb + o2 + f + (int64_t)f * f;
+                    SparsifyTask<real> c;
+                    std::memset(&c, 0, sizeof(c));
+                    c.A = blk(sp.find(p, p), p);
+                    c.lda = lay.H[p];
+                    c.mi = np_;
+                    c.nj = np_;
+                    c.D = Tp;
+                    c.ldd = np_;
+                    c.mode = 2;
+                    cpy.push_back(c);
+                    if (r > 0) {
+                        for (int r0 = 0; r0 < np_; r0 += QC) prq.push_back({(int)rq.size(), r0, std::min(QC, np_ - r0)});
+                        rq.push_back(ReflTask<real>{qV[p], qT[p], Tp, np_, np_, np_, r, kmax[p], 1, 1, 0});
+                        fl_t += 4.0 * np_ * np_ * r;
+                        by_t += 16.0 * np_ * np_ + 8.0 * np_ * r;
+                    }
+                    if (f > 0) {
+                        // the fine columns are often orthogonal to the first row of
+                        // A_pp: a leading entry that is zero up to rounding takes
+                        // beta = -norm, so that rounding does not pick the reflection
+                        hq.push_back(QRTask<real>{Tp + (int64_t)r * np_, np_, np_, f, tb + o2, hT[p], hD[p], d_flags + 1,
+                                                  sizeof(real) == 8 ? 1e-12 : 1e-5});
+                        fl_h += 2.0 * np_ * f * f - 2.0 / 3.0 * f * f * f;
+                        by_h += 16.0 * np_ * f;
+                        if (r > 0) {
+                            for (int c0 = 0; c0 < r; c0 += QC) plh.push_back({(int)lh.size(), c0, std::min(QC, r - c0)});
+                            lh.push_back(ReflTask<real>{Tp + (int64_t)r * np_, hT[p], Tp, np_, np_, np_, f, f, 0, 0, 0});
+                            fl_h += 4.0 * np_ * f * r;
+                            by_h += 16.0 * np_ * r + 8.0 * np_ * f;
+                        }
+                    }
+                    o2 += f + (int64_t)f * f + (int64_t)f * NB;
+                    hF[p] = f;
+                }
+                flops += fl_t + fl_h;
+                const size_t smem_rf = (size_t)(2 * NB * QC + NT) * esz;
+                if (!cpy.empty()) {
+                    std::vector<ScalePiece> pc;
+                    for (int t = 0; t < (int)cpy.size(); t++) pc.push_back({t, 0, 0});
+                    SparsifyTask<real>* d = C.upload(cpy, false);
+                    ScalePiece* dp = C.upload(pc, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_UNSCALED, 0.0, 0.0, st, k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
+                    C.launched();
+                }
+                if (!rq.empty()) {
+                    ReflTask<real>* d = C.upload(rq, false);
+                    ScalePiece* dp = C.upload(prq, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_UNSCALED, fl_t, by_t, st,
+                                 k_refl_apply<real><<<(unsigned)prq.size(), NT, smem_rf, st>>>(d, dp));
+                    C.launched();
+                }
+                if (!hq.empty()) {
+                    launch_qr<real>(C, hq, esz, KK_UNSCALED, fl_h, by_h);
+                    if (C.rc) return C.rc;
+                }
+                if (!lh.empty()) {
+                    ReflTask<real>* d = C.upload(lh, false);
+                    ScalePiece* dp = C.upload(plh, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_UNSCALED, 0.0, 0.0, st,
+                                 k_refl_apply<real><<<(unsigned)plh.size(), NT, smem_rf, st>>>(d, dp));
+                    C.launched();
+                }
+                tstop(2);
             }
         } else {
             for (int p : rest) newsz[p] = sz[p];
@@ -1261,6 +1714,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     if (!sparsify) {
                         if (sz[i] == 0 || sz[j] == 0) continue;
                         t.mode = 2;
+                    } else if (i == j && opt->scaling == 0) {
+                        // unscaled form: the coarse rows of H_p^T A_pp Q_p[:, 0:r]
+                        if (newsz[i] == 0) continue;
+                        t.mode = 2;
+                        t.A = hR[i] + hF[i];
+                        t.lda = sz[i];
+                        t.mi = (int)newsz[i];
+                        t.nj = (int)newsz[i];
                     } else if (i == j) {
                         if (newsz[i] == 0) continue;
                         t.mode = 1;
@@ -1268,17 +1729,31 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     } else {
                         if (newsz[i] == 0 || newsz[j] == 0) continue;
                         t.mode = 0;
-                        t.Vi = qV[i];
-                        t.Ti = qT[i];
+                        if (opt->scaling == 0) {
+                            // left: H_i^T (f_i reflectors), keep rows f_i..n_i
+                            t.Vi = hR[i] + newsz[i] * sz[i];
+                            t.Ti = hT[i];
+                            t.ldti = std::max(hF[i], 1);
+                            t.li = hF[i];
+                            t.lkeep = hF[i];
+                            t.lexp = 0;
+                        } else {
+                            // left: Q_i^T (r_i reflectors), keep rows 0..r_i
+                            t.Vi = qV[i];
+                            t.Ti = qT[i];
+                            t.ldti = kmax[i];
+                            t.li = (int)newsz[i];
+                            t.lkeep = 0;
+                            t.lexp = 1;
+                        }
                         t.ri = (int)newsz[i];
-                        t.ldti = kmax[i];
                         t.Vj = qV[j];
                         t.Tj = qT[j];
                         t.rj = (int)newsz[j];
                         t.ldtj = kmax[j];
                         t.scratch = (real*)(intptr_t)scr;  // offset, fixed below
                         scr += (int64_t)t.mi * t.nj;
-                        const double fp = 4.0 * t.ri * t.mi * t.nj + 4.0 * t.rj * t.nj * t.ri;
+                        const double fp = 4.0 * t.li * t.mi * t.nj + 4.0 * t.rj * t.nj * t.ri;
                         flops += fp;
                         fl_sp += fp;
                     }
@@ -1327,7 +1802,24 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 s.noff = nl.voff[sp.parent[p]] + coff[p];
                 s.np = (int)sz[p];
                 s.r = (int)newsz[p];
-                if (sparsify && sz[p] > 0) {
+                if (sparsify && sz[p] > 0 && opt->scaling == 0) {
+                    // unscaled form: forward H_p^T; backward R_ff^{-1} (y_f - R_fc x_c), then Q_p
+                    const int f = hF[p];
+                    s.QV = qV[p];
+                    s.QT = qT[p];
+                    s.ldqt = std::max(kmax[p], 1);
+                    s.f = f;
+                    s.HR = hR[p];
+                    s.HT = hT[p];
+                    s.HD = hD[p];
+                    const double n_ = (double)sz[p], r_ = (double)newsz[p], f_ = (double)f;
+                    sflops += 4.0 * n_ * f_ + 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_;
+                    sbytes += 8 * (int64_t)(n_ * f_ + f_ * r_ + f_ * f_ + n_ * r_);
+                    LV.ssf_flops += 4.0 * n_ * f_;
+                    LV.ssf_fixed += 8.0 * (n_ * f_ + f_ * f_);
+                    LV.ssb_flops += 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_;
+                    LV.ssb_fixed += 8.0 * (f_ * r_ + f_ * f_ + n_ * r_ + r_ * r_);
+                } else if (sparsify && sz[p] > 0) {
                     const int e = sp.find(p, p);
                     s.UV = blk(e, p);
                     s.lduv = lay.H[p];
@@ -1390,7 +1882,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         cudaEventDestroy(t.b);
     }
     if (flags[0]) { set_error("matrix has a zero column"); return SPAQR_ERR_SINGULAR; }
-    if (flags[1]) { set_error("zero diagonal in a scaling factor R_pp"); return SPAQR_ERR_SINGULAR; }
+    if (flags[1]) {
+        set_error(opt->scaling ? "zero diagonal in a scaling factor R_pp"
+                               : "zero diagonal in R of A_p or in R_ff (unscaled sparsification)");
+        return SPAQR_ERR_SINGULAR;
+    }
     if (flags[2]) { set_error("zero diagonal in a separator factor R_ss"); return SPAQR_ERR_SINGULAR; }
     return SPAQR_OK;
 }
@@ -1419,7 +1915,7 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
         set_error("opts.nlevels differs from the ordering's level count");
         return SPAQR_ERR_INVALID_ARG;
     }
-    if (opts->scaling != 1) { set_error("only the scaled variant is built (scaling = 1)"); return SPAQR_ERR_UNSUPPORTED; }
+    if (opts->scaling != 0 && opts->scaling != 1) { set_error("scaling must be 0 or 1"); return SPAQR_ERR_INVALID_ARG; }
     if (opts->precision != SPAQR_FP64 && opts->precision != SPAQR_FP32) {
         set_error("precision must be SPAQR_FP64 or SPAQR_FP32");
         return SPAQR_ERR_UNSUPPORTED;
@@ -1481,6 +1977,16 @@ extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
         }
     for (int i = 0; i < 4; i++) out->phase_ms[i] = F->phase_ms[i];
     out->top_size = F->top_size;
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_sigmas(const spaqr_factor_t* F, int level, double* sigma, int cap, int* count) {
+    if (!F || !count) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (level < 0 || level >= (int)F->sigmas.size()) { spaqr::set_error("level out of range"); return SPAQR_ERR_INVALID_ARG; }
+    const auto& S = F->sigmas[level];
+    *count = (int)S.size();
+    if (sigma)
+        for (int i = 0; i < std::min<int>(cap, (int)S.size()); i++) sigma[i] = S[i];
     return SPAQR_OK;
 }
 

@@ -86,6 +86,20 @@ __global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront<real>* __res
     else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, qn, true, W);
 }
 
+// Reverse rows [a, b) of every one of the q columns of y in place.
+template <class real>
+__device__ void cta_reverse_rows(real* y, int64_t ldy, int a, int b, int q) {
+    const int h = (b - a) / 2;
+    for (int o = threadIdx.x; o < h * q; o += NT) {
+        const int i = o % h, c = o / h;
+        real* col = y + (int64_t)c * ldy;
+        const real x = col[a + i];
+        col[a + i] = col[b - 1 - i];
+        col[b - 1 - i] = x;
+    }
+    __syncthreads();
+}
+
 template <class real>
 __global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS<real>* __restrict__ ss, real* Y, int64_t ldy, real* Yn,
                                                 int64_t ldyn, int nrhs, int qs, int staged) {
@@ -96,11 +110,24 @@ __global__ void __launch_bounds__(NT) k_sss_fwd(const SolveSS<real>* __restrict_
     const SolveSS<real> S = ss[blockIdx.x];
     real* y = Y + S.off + (int64_t)c0 * ldy;
     const Mat<real> B{y, 1, ldy, nullptr};
-    if (S.UV) {
+    if (S.HR) {
+        // unscaled form (Section 3.2): y_p <- H_p^T y_p, whose first f rows are
+        // the fine entries; rotate every column so that the r coarse entries
+        // come first (three reversals) and the fine ones wait at rows r..n_p
+        if (S.f > 0) {
+            const real* HV = S.HR + (int64_t)S.r * S.np;
+            if (staged) cta_apply_q_staged(HV, S.np, S.np, S.f, S.HT, S.f, false, B, qn, true, sm);
+            else cta_apply_q(HV, S.np, S.np, S.f, S.HT, S.f, false, B, qn, true, sm);
+            __syncthreads();
+            cta_reverse_rows(y, ldy, 0, S.f, qn);
+            cta_reverse_rows(y, ldy, S.f, S.np, qn);
+            cta_reverse_rows(y, ldy, 0, S.np, qn);
+        }
+    } else if (S.UV) {
         if (staged) cta_apply_q_staged(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
         else cta_apply_q(S.UV, S.lduv, S.np, S.np, S.UT, S.np, false, B, qn, true, sm);
     }
-    if (S.QV && S.r > 0) {
+    if (!S.HR && S.QV && S.r > 0) {
         if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, true, sm);
         else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, true, sm);
     }
@@ -126,6 +153,19 @@ __global__ void __launch_bounds__(NT) k_sss_bwd(const SolveSS<real>* __restrict_
     }
     __syncthreads();
     const Mat<real> B{y, 1, ldy, nullptr};
+    if (S.HR && S.f > 0) {
+        // unscaled form: x_f = R_ff^{-1} (y_f - R_fc x_c), fine rows at r..n_p
+        const int f = S.f, r = S.r, np_ = S.np;
+        for (int o = threadIdx.x; o < f * qn; o += NT) {
+            const int i = o % f, c = o / f;
+            const real* yc = y + (int64_t)c * ldy;
+            real acc = 0;
+            for (int u = 0; u < r; u++) acc += S.HR[i + (int64_t)u * np_] * yc[u];
+            y[r + i + (int64_t)c * ldy] -= acc;
+        }
+        __syncthreads();
+        cta_trsv_upper(S.HR + (int64_t)r * np_, np_, f, S.HD, Mat<real>{y + r, 1, ldy, nullptr}, qn, sm);
+    }
     if (S.QV && S.r > 0) {
         if (staged) cta_apply_q_staged(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
         else cta_apply_q(S.QV, S.np, S.np, S.r, S.QT, S.ldqt, true, B, qn, false, sm);
@@ -1046,6 +1086,7 @@ void launch_ss(const ApplyCtx<real>& A, int k, bool fwd, int choice) {
                  fv = fwd ? LV.ssf_vec : LV.ssb_vec;
     const int kind = fwd ? KK_SOLVE_SS_FWD : KK_SOLVE_SS_BWD;
     int form = choice;
+    if (F->unscaled) form = kChoiceNarrow;   // the cluster forms carry the scaled steps only
     if (form == kChoiceRule) {
         // many interfaces: one CTA each; a few hundred large ones: the staged
         // one-CTA form; the last few: a cluster each

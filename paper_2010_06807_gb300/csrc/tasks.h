@@ -24,6 +24,7 @@ struct QRTask {
     real* T;     // t x t block-diagonal T, ld = t
     real* Dinv;  // inverted diagonal blocks of R (t x NB, ld t), or null
     int* singular; // set on a zero diagonal of R
+    double sign_tol;  // reflector sign: alpha < -sign_tol |column| counts as negative (0: alpha < 0)
 };
 
 // Rows of a front inside another column panel (or inside a solve vector).
@@ -101,24 +102,65 @@ struct CPQRTask {
     int kmax;           // min(n_p, ncols)
 };
 
-// New block (r_i x r_j) = [Q_i^T A_ij Q_j] (coarse rows/cols, Sections 2.5),
-// written at its place in the merged block of the next level (Section 2.6);
-// or a plain copy when the level is not sparsified.
+// New block (r_i x r_j) = [L_i^T A_ij Q_j](keep rows, 0:r_j) (coarse rows and
+// columns), written at its place in the merged block of the next level
+// (Section 2.6); or a plain copy when the level is not sparsified.  The left
+// reflectors L_i are Q_i (scaled form, Section 2.5: keep rows 0..r_i) or the
+// Householder H_i of the fine columns (unscaled form, Section 3.2: keep rows
+// f_i..n_i).
 template <class real>
 struct SparsifyTask {
     const real* A;
     int64_t lda;
     int mi, nj;
-    const real* Vi;   // n_i x r_i explicit, ld n_i
-    const real* Ti;   // ld kmax_i
-    int ri, ldti;
+    const real* Vi;   // left reflectors, n_i rows, ld n_i
+    const real* Ti;   // ld ldti
+    int ri, ldti;     // kept rows, T leading dimension
+    int li, lkeep;    // left reflectors, first kept row
+    int lexp, pad;    // Vi holds its unit diagonal explicitly
     const real* Vj;
     const real* Tj;
     int rj, ldtj;
     real* D;
     int64_t ldd;
-    real* scratch;    // 2 * r_i * n_j + 2 * r_i * r_j doubles
+    real* scratch;    // n_i x n_j
     int mode;           // 0 sparsify, 1 identity r_i, 2 copy
+};
+
+// Reflectors applied to a block: B <- Q^T B over a chunk of columns (left) or
+// B <- B Q over a chunk of rows (right); pieces are ScalePiece ranges.
+template <class real>
+struct ReflTask {
+    const real* V;    // m rows, ld ldv
+    const real* T;    // ld ldt
+    real* B;
+    int64_t ldv, ldb;
+    int m, t, ldt;
+    int vexp;           // V holds its unit diagonal explicitly
+    int right;
+    int pad;
+};
+
+// sigma_p = 1 / sigma_min(A_p) from R of A_p = Q R (Lemma 1).
+template <class real>
+struct SigmaTask {
+    const real* R;    // n x n upper triangular, ld ldr
+    int64_t ldr;
+    double* work;     // (kmax + 3) * n doubles
+    double* sigma;    // out
+    int* singular;      // set on a zero diagonal of R
+    int n, kmax;
+};
+
+// C = sigma A^T B for the unscaled M_p (n x n A_pp, n x nc A_pj; C ld n).
+template <class real>
+struct AtbTask {
+    const real* A;
+    const real* B;
+    real* C;
+    const double* sigma;
+    int64_t lda, ldb;
+    int n, nc;
 };
 
 // ---------------------------------------------------------------------------
@@ -186,7 +228,13 @@ struct SolveSS {
     const real* QV;  // n_p x r explicit
     const real* QT;  // ld kmax
     int ldqt;
-    int pad;
+    int f;             // unscaled form: fine unknowns (0: scaled form)
+    // unscaled form (Section 3.2): H_p of the fine columns (reflectors below
+    // the diagonal of HR[:, r:], T blocks HT ld f) with R_ff on top of them,
+    // R_fc = HR[0:f, 0:r], inverted diagonal blocks of R_ff in HD (f x NB)
+    const real* HR;
+    const real* HT;
+    const real* HD;
 };
 
 }  // namespace spaqr
@@ -272,9 +320,11 @@ struct spaqr_factor_s {
     // diagnostics
     std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
     std::vector<std::vector<std::pair<double, double>>> margins;
+    std::vector<std::vector<double>> sigmas;               // per level: sigma_p (unscaled form), else 0
     double phase_ms[4] = {0, 0, 0, 0};
     double flops = 0.0;
     double solve_flops = 0.0;
     int64_t solve_bytes = 0;
     int top_size = 0;
+    bool unscaled = false;         // unscaled variant (Section 3.2): narrow solve forms only
 };

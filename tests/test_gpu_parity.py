@@ -167,8 +167,8 @@ def test_errors(dev):
     rp, ci, va = _to_dev(p, dev)
     ordl = sq.spaqr_order(rp, ci, p.dims)
     with pytest.raises(sq.SpaqrError) as e:
-        sq.spaqr_factor(ordl, rp, ci, va, eps=1e-2, scaling=0)
-    assert e.value.name == "UNSUPPORTED"
+        sq.spaqr_factor(ordl, rp, ci, va, eps=1e-2, scaling=2)
+    assert e.value.name == "INVALID_ARG"
     with pytest.raises(sq.SpaqrError) as e:
         sq.spaqr_factor(ordl, rp, ci, va, eps=-1.0)
     assert e.value.name == "INVALID_ARG"

@@ -50,6 +50,22 @@ def test_house_sign_convention():
     assert beta == -2.0  # sign(0) = +1
 
 
+def test_house_sign_tolerance():
+    """A leading entry within sign_tol |col| of zero takes beta = -|col| on
+    either side of zero; both reflections map col to beta e_1 exactly."""
+    for alpha in (-1e-18, 1e-18, -3e-13):
+        col = np.array([alpha, 3.0, 4.0])
+        v, tau, beta = dense.house(col, sign_tol=1e-12)
+        assert beta == -np.sqrt(alpha * alpha + 25.0)
+        h = col - tau * v * (v @ col)
+        assert abs(h[0] - beta) <= 1e-15 * 5 and np.abs(h[1:]).max() <= 1e-15 * 5
+    # outside the tolerance the LAPACK sign stands
+    v, tau, beta = dense.house(np.array([-1e-11, 3.0, 4.0]), sign_tol=1e-12)
+    assert beta > 0
+    v, tau, beta = dense.house(np.array([-1e-18, 3.0, 4.0]))
+    assert beta > 0
+
+
 def test_apply_qt_and_q_are_inverse():
     A = _rng(3).standard_normal((20, 8))
     V, tau, R = dense.qr(A)
