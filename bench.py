@@ -202,12 +202,13 @@ def reference_arm(a):
     return 0
 
 
-def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, warmup):
+def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, warmup, scaling=1):
     """Time `steps` factor + GMRES steps of one form (after `warmup` untimed ones)
     with CUDA events on `st`, L2 flushed between steps."""
     rp, ci, va = A
     fac, gm, tot, iters = [], [], [], []
     X = None
+    info = None
     with torch.cuda.stream(st):
         for i in range(warmup + steps):
             flush.zero_()
@@ -215,7 +216,7 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
             em = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            F = sq.spaqr_factor(ordl, rp, ci, va, eps=eps, precision=precision, stream=st)
+            F = sq.spaqr_factor(ordl, rp, ci, va, eps=eps, precision=precision, scaling=scaling, stream=st)
             em.record(st)
             Xd.zero_()
             X, it, rr = sq.spaqr_gmres(F, rp, ci, va, Bd, X=Xd, tol=TOL, maxit=MAXIT, stream=st)
@@ -226,11 +227,13 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
                 gm.append(em.elapsed_time(e1))
                 tot.append(e0.elapsed_time(e1))
                 iters.append(int(it.max()))
+                info = sq.spaqr_factor_info(F)
             del F
     nrhs = Bd.shape[1]
     return {"solves_per_s": nrhs * len(tot) / (sum(tot) / 1e3), "factor_ms_p50": _pct(fac, 50),
             "gmres_ms_p50": _pct(gm, 50), "step_ms_p50": _pct(tot, 50), "gmres_iters_max": max(iters),
-            "relres_max": float(rr.max())}, X.clone()
+            "relres_max": float(rr.max()), "rank_sum": info["rank_sum"], "size_sum": info["size_sum"],
+            "factor_mbytes": info["factor_bytes"] / 2 ** 20}, X.clone()
 
 
 def _batched(sq, torch, np, dev, st, flush, count=64, steps=3, warmup=1):
@@ -504,6 +507,22 @@ def ours(a):
     mixed["final_error_vs_fp64"] = float(np.max(np.linalg.norm(X32 - Xref, axis=0) / np.linalg.norm(Xref, axis=0)))
     mixed["note"] = "same workload; FP32 factor and application, FP64 flexible GMRES to 1e-12"
     line["mixed_fp32"] = mixed
+    # ---- unscaled variant (Sections 2.2 / 3.2) on the same workload: the scaling ablation ----
+    un, Xun = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp64", 3, 1, scaling=0)
+    un["final_error_vs_scaled"] = float(np.max(np.linalg.norm(Xun.cpu().numpy() - Xref, axis=0) /
+                                               np.linalg.norm(Xref, axis=0)))
+    sq.spaqr_stats_reset()
+    sq.spaqr_profile(True)
+    with torch.cuda.stream(st):
+        F = sq.spaqr_factor(ordl, rp, ci, va, eps=EPS, scaling=0, stream=st)
+        torch.cuda.synchronize(dev)
+        del F
+    sq.spaqr_profile(False)
+    _, ks = sq.spaqr_stats()
+    un["factor_kernels_ms"] = {k: round(v["total_ms"], 3) for k, v in ks.items() if v["launches"]}
+    un["note"] = ("same workload and eps, scaling = 0: sigma_p = 1/sigma_min(A_p), M_p = [A_np^T | "
+                  "sigma_p A_pp^T A_pn], Householder on the fine columns; headline keys are the scaled form")
+    line["unscaled_fp64"] = un
     # ---- 3D 32^3 workload (a ~ U[0.1,10], v = 20 (1,1,1), eps 1e-2, 16 RHS): FP64 vs FP32 factor ----
     p3 = config_problem("3d_uniform_a", n=32)
     b3 = rhs(p3, NRHS)

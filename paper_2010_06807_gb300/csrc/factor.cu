@@ -1406,9 +1406,9 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     SparsifyTask<real>* d = C.upload(cpy, false);
                     ScalePiece* dp = C.upload(pc, false);
                     if (C.rc) return C.rc;
-                    SPAQR_LAUNCH(KK_SIGMA, 0.0, by_a, st, k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
+                    SPAQR_LAUNCH(KK_SIGMA_QR, 0.0, by_a, st, k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
                     C.launched();
-                    launch_qr<real>(C, aq, esz, KK_SIGMA, fl_a, 0.0);
+                    launch_qr<real>(C, aq, esz, KK_SIGMA_QR, fl_a, 0.0);
                     if (C.rc) return C.rc;
                     SigmaTask<real>* ds = C.upload(sgt, false);
                     if (C.rc) return C.rc;
