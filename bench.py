@@ -236,6 +236,49 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
             "factor_mbytes": info["factor_bytes"] / 2 ** 20}, X.clone()
 
 
+def _high_contrast(sq, torch, np, dev, st, flush):
+    """Scaling ablation on the high-contrast 2D workload (the paper's Section 4
+    experiment, our own synthetic field and discretisation): GMRES iterations
+    and times, one RHS, eps 1e-3, for the scaled FP64 factor, the unscaled FP64
+    factor and the scaled FP32 factor.  rho = 100 uses tol 1e-10: there
+    1e-12 lies under the FP64 floor u |A| |x| / |b| (~3e-12 at n = 127) of the
+    recomputed residual itself."""
+    from synth.convdiff import config_problem, rhs
+    out = {}
+    for rho, tol in ((1.0, 1e-12), (10.0, 1e-12), (100.0, 1e-10)):
+        for n in (127, 255, 511):
+            p = config_problem("2d_high_contrast", n=n, rho=rho)
+            b = rhs(p, 1)
+            A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+            Bd = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
+            o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+            row = {}
+            for name, scal, prec in (("scaled_fp64", 1, "fp64"), ("unscaled_fp64", 0, "fp64"),
+                                     ("scaled_fp32", 1, "fp32")):
+                with torch.cuda.stream(st):
+                    flush.zero_()
+                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                    e0.record(st)
+                    F = sq.spaqr_factor(o, *A, eps=1e-3, scaling=scal, precision=prec, stream=st)
+                    e1.record(st)
+                    try:
+                        _, it, rr = sq.spaqr_gmres(F, *A, Bd, tol=tol, maxit=MAXIT, stream=st)
+                        conv = True
+                    except sq.SpaqrError as e:
+                        if e.name != "NOT_CONVERGED":
+                            raise
+                        it, rr, conv = e.iters, e.relres, False
+                    e2.record(st)
+                    e2.synchronize()
+                    row[name] = {"iters": int(it[0]), "relres": float(rr[0]), "converged": conv,
+                                 "factor_ms": e0.elapsed_time(e1), "gmres_ms": e1.elapsed_time(e2)}
+                    del F
+            out[f"rho{rho:g}_n{n}"] = row
+    out["note"] = ("eps 1e-3, 1 RHS, tol 1e-12 (rho 1, 10) / 1e-10 (rho 100), maxit 300; iterations of "
+                   "scaled vs unscaled FP64 and scaled FP32 factors")
+    return out
+
+
 def _batched(sq, torch, np, dev, st, flush, count=64, steps=3, warmup=1):
     """Batched workload: `count` independent 2D problems (sides from
     {32,48,...,128}, a ~ U[0.1,10], v = Pe (1,1), Pe ~ U[1,100]), one RHS per
@@ -538,6 +581,7 @@ def ours(a):
                                               np.linalg.norm(x64, axis=0)))
     line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
     line["batched_64x2d"] = _batched(sq, torch, np, dev, st, flush)
+    line["high_contrast_2d_ablation"] = _high_contrast(sq, torch, np, dev, st, flush)
     if not a.no_serve:
         from paper_2010_06807_gb300.serve import run_plain, run_workload
         srv = {}

@@ -139,6 +139,15 @@ def _check(rc):
         raise SpaqrError(rc, _lib.spaqr_last_error().decode(errors="replace"))
 
 
+def _check_gmres(rc, X, iters, relres):
+    """As _check; a NOT_CONVERGED error carries the best iterate and the
+    per-column counts (e.X, e.iters, e.relres)."""
+    if rc != SPAQR_OK:
+        e = SpaqrError(rc, _lib.spaqr_last_error().decode(errors="replace"))
+        e.X, e.iters, e.relres = X, iters, relres
+        raise e
+
+
 def num_levels(n):
     """ceil(log2(N/64)), at least 1 (Section 4)."""
     import math
@@ -413,7 +422,8 @@ def spaqr_solve_noalloc(F, B, X, stream=None):
 def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=None):
     """Right-preconditioned GMRES; returns (X, iters[nrhs], relres[nrhs]).
 
-    Raises SpaqrError(NOT_CONVERGED) if a column misses tol.
+    Raises SpaqrError(NOT_CONVERGED) if a column misses tol; the error carries
+    X, iters and relres.
     """
     load_library()
     csr, keep = _make_csr(rowptr, colind, val)
@@ -431,8 +441,8 @@ def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=
     xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
     iters = np.zeros(nrhs, dtype=np.int32)
     relres = np.zeros(nrhs, dtype=np.float64)
-    _check(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
-                            iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)))
+    _check_gmres(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
+                                  iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)), X, iters, relres)
     return X, iters, relres
 
 
@@ -458,9 +468,10 @@ def spaqr_gmres_batch(F, rowptr, colind, val, part_ptr, B, X=None, tol=1e-12, ma
     xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
     iters = np.zeros(nrhs * count, dtype=np.int32)
     relres = np.zeros(nrhs * count, dtype=np.float64)
-    _check(_lib.spaqr_gmres_batch(F._h, ctypes.byref(csr), count, part.ctypes.data, nrhs, bp, ldb, xp, ldx,
-                                  float(tol), int(maxit), iters.ctypes.data, relres.ctypes.data,
-                                  _stream_ptr(stream)))
+    _check_gmres(_lib.spaqr_gmres_batch(F._h, ctypes.byref(csr), count, part.ctypes.data, nrhs, bp, ldb, xp, ldx,
+                                        float(tol), int(maxit), iters.ctypes.data, relres.ctypes.data,
+                                        _stream_ptr(stream)),
+                 X, iters.reshape(nrhs, count), relres.reshape(nrhs, count))
     return X, iters.reshape(nrhs, count), relres.reshape(nrhs, count)
 
 

@@ -128,7 +128,38 @@ def _uniform_a(rng, N):
     return rng.uniform(0.1, 10.0, size=N)
 
 
-def config_problem(kind, n=None, seed=None):
+def gaussian_smooth(f, sigma=1.0, truncate=4.0):
+    """Separable Gaussian convolution of a 2D array (standard deviation
+    `sigma` grid cells, kernel cut at `truncate` sigma and normalised to sum
+    1), mirrored at the edges (edge sample repeated)."""
+    r = int(truncate * sigma + 0.5)
+    k = np.exp(-0.5 * (np.arange(-r, r + 1) / sigma) ** 2)
+    k /= k.sum()
+    out = np.asarray(f, dtype=np.float64)
+    for ax in range(out.ndim):
+        pad = [(0, 0)] * out.ndim
+        pad[ax] = (r, r)
+        g = np.pad(out, pad, mode="symmetric")
+        acc = np.zeros_like(out)
+        for i, w in enumerate(k):
+            sl = [slice(None)] * out.ndim
+            sl[ax] = slice(i, i + out.shape[ax])
+            acc += w * g[tuple(sl)]
+        out = acc
+    return out
+
+
+def high_contrast_field(rng, n, rho):
+    """High-contrast coefficient of the paper's 2D experiments (Section 4):
+    U[0,1] per grid point, smoothed with a unit-width Gaussian, then rho where
+    the smoothed value is >= 0.5 and 1/rho elsewhere.  Returned in
+    lexicographic order (x fastest)."""
+    ahat = rng.uniform(0.0, 1.0, size=(n, n))          # [y, x]
+    sm = gaussian_smooth(ahat, 1.0)
+    return np.where(sm >= 0.5, float(rho), 1.0 / float(rho)).ravel()
+
+
+def config_problem(kind, n=None, seed=None, rho=100.0):
     """Build one of the named synthetic workloads.
 
     kind:
@@ -136,6 +167,9 @@ def config_problem(kind, n=None, seed=None):
       "2d_lognormal"  : a = exp(g), g ~ N(0,1); v = 50 (cos t, sin t),
                         t ~ U[0, 2 pi) per cell                 (256x256 default)
       "3d_uniform_a"  : a ~ U[0.1,10], v = 20 (1, 1, 1)         (32^3 default)
+      "2d_high_contrast": a = rho / 1/rho from a thresholded smoothed
+                        U[0,1] field (high_contrast_field), v = (1, 1)
+                        (255x255 default; the draws do not depend on rho)
     """
     if kind == "2d_uniform_a":
         n = 64 if n is None else n
@@ -162,6 +196,14 @@ def config_problem(kind, n=None, seed=None):
         a = _uniform_a(rng, N)
         v = np.tile([20.0, 20.0, 20.0], (N, 1))
         dims = (n, n, n)
+    elif kind == "2d_high_contrast":
+        n = 255 if n is None else n
+        seed = 6000 if seed is None else seed
+        rng = np.random.Generator(np.random.PCG64(seed))
+        N = n * n
+        a = high_contrast_field(rng, n, rho)
+        v = np.tile([1.0, 1.0], (N, 1))
+        dims = (n, n)
     else:
         raise ValueError(kind)
     rowptr, colind, val = convdiff(dims, a, v)

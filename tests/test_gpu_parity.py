@@ -179,3 +179,5 @@ def test_errors(dev):
     with pytest.raises(sq.SpaqrError) as e:
         sq.spaqr_gmres(F, p.rowptr, p.colind, p.val, np.asfortranarray(b), tol=1e-15, maxit=1)
     assert e.value.name == "NOT_CONVERGED"
+    # the error carries the best iterate and the per-column counts
+    assert e.value.iters.tolist() == [1] and e.value.relres[0] > 1e-15 and e.value.X.shape == (p.n, 1)
