@@ -129,6 +129,25 @@ typedef struct {
     int32_t top_size;          /* size of the root separator when it was factored */
 } spaqr_info;
 
+/* Per-level diagnostics (spaqr_factor_level), level index k = 0 at the
+ * leaves: the quantities the paper's profiling figures plot per level
+ * (Section 4: sizes, ranks, time per phase). */
+typedef struct {
+    int32_t n_fronts;          /* separators factored at this level */
+    int32_t max_front_rows;    /* tallest front (rows of R(s), Section 2.4) */
+    int32_t max_front_cols;    /* widest front (|s|) */
+    int32_t n_interfaces;      /* interfaces sparsified at this level (0 below skip) */
+    int64_t front_rows;        /* sum of the front heights */
+    int64_t front_cols;        /* sum of |s| */
+    int32_t n_remaining;       /* clusters left after the fronts (interfaces) */
+    int32_t max_interface;     /* largest of them before sparsification */
+    int64_t remaining_size;    /* sum of their sizes before sparsification */
+    int64_t interface_after;   /* sum after sparsification (= before when not sparsified) */
+    int64_t block_entries;     /* dense entries of the level's block arena */
+    int64_t factor_bytes;      /* device bytes held by the factor after this level */
+    double  phase_ms[4];       /* factorize / scale / sparsify / merge of this level, CUDA events */
+} spaqr_level_info;
+
 /* Last error message of the calling thread (never NULL). */
 const char* spaqr_last_error(void);
 
@@ -261,6 +280,19 @@ int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out);
  * margins[2*i], margins[2*i+1] if margins != NULL. */
 int spaqr_factor_ranks(const spaqr_factor_t* F, int level, int32_t* pairs, double* margins,
                        int cap, int* count);
+
+/* Diagnostics of level k (0 = leaves) into *out.
+ * Errors: INVALID_ARG (null argument, level out of range). */
+int spaqr_factor_level(const spaqr_factor_t* F, int level, spaqr_level_info* out);
+
+/* CPQR pivot norms |R_kk| (Section 4's rank rule) of every interface
+ * sparsified at level k, in the order of spaqr_factor_ranks: the kept steps
+ * and the first rejected one.  Interface i owns norms[offsets[i] ..
+ * offsets[i+1]).  Writes up to cap norms and cap_offsets offsets (either
+ * array may be NULL) and the totals into *n_norms and *n_interfaces.
+ * Errors: INVALID_ARG (null counts, level out of range). */
+int spaqr_factor_pivots(const spaqr_factor_t* F, int level, double* norms, int64_t cap, int32_t* offsets,
+                        int cap_offsets, int64_t* n_norms, int* n_interfaces);
 
 /* sigma_p = 1 / sigma_min(A_p) of the interfaces sparsified at level k by the
  * unscaled variant (Lemma 1), in the order of spaqr_factor_ranks; 0 for the

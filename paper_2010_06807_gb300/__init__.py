@@ -18,7 +18,8 @@ __all__ = [
     "SpaqrError", "load_library", "spaqr_order", "spaqr_order_batch", "blockdiag_csr",
     "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
-    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "Ordering", "Factor", "num_levels",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level",
+    "spaqr_factor_pivots", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
     "spaqr_factor_tuning",
 ]
@@ -69,6 +70,16 @@ class _Info(ctypes.Structure):
                 ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32)]
 
 
+class _LevelInfo(ctypes.Structure):
+    _fields_ = [("n_fronts", ctypes.c_int32), ("max_front_rows", ctypes.c_int32),
+                ("max_front_cols", ctypes.c_int32), ("n_interfaces", ctypes.c_int32),
+                ("front_rows", ctypes.c_int64), ("front_cols", ctypes.c_int64),
+                ("n_remaining", ctypes.c_int32), ("max_interface", ctypes.c_int32),
+                ("remaining_size", ctypes.c_int64), ("interface_after", ctypes.c_int64),
+                ("block_entries", ctypes.c_int64), ("factor_bytes", ctypes.c_int64),
+                ("phase_ms", ctypes.c_double * 4)]
+
+
 class _KStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -81,7 +92,8 @@ EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_batch", "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
-    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_destroy", "spaqr_stats_reset",
+    "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
+    "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
 ]
 
@@ -116,6 +128,9 @@ def load_library(path=None):
         lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
         lib.spaqr_factor_ranks.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_factor_sigmas.argtypes = [vp, i32, vp, i32, ctypes.POINTER(ctypes.c_int)]
+        lib.spaqr_factor_level.argtypes = [vp, i32, ctypes.POINTER(_LevelInfo)]
+        lib.spaqr_factor_pivots.argtypes = [vp, i32, vp, i64, vp, i32, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_factor_destroy.argtypes = [vp]
         lib.spaqr_factor_destroy.restype = None
     if hasattr(lib, "spaqr_stats"):
@@ -493,6 +508,27 @@ def spaqr_factor_ranks(F, level):
     _check(_lib.spaqr_factor_ranks(F._h, int(level), pairs.ctypes.data, margins.ctypes.data, n,
                                    ctypes.byref(cnt)))
     return pairs[:2 * n].reshape(n, 2), margins[:2 * n].reshape(n, 2)
+
+
+def spaqr_factor_level(F, level):
+    """Per-level diagnostics (spaqr_level_info) of level k (0 = leaves) as a dict."""
+    load_library()
+    info = _LevelInfo()
+    _check(_lib.spaqr_factor_level(F._h, int(level), ctypes.byref(info)))
+    return {f: (list(getattr(info, f)) if f == "phase_ms" else getattr(info, f)) for f, _ in _LevelInfo._fields_}
+
+
+def spaqr_factor_pivots(F, level):
+    """CPQR pivot norms |R_kk| per interface sparsified at a level: a list of
+    arrays (kept steps and the first rejected one), in spaqr_factor_ranks order."""
+    load_library()
+    nn, ni = ctypes.c_int64(0), ctypes.c_int(0)
+    _check(_lib.spaqr_factor_pivots(F._h, int(level), None, 0, None, 0, ctypes.byref(nn), ctypes.byref(ni)))
+    norms = np.zeros(max(nn.value, 1), dtype=np.float64)
+    offs = np.zeros(ni.value + 1, dtype=np.int32)
+    _check(_lib.spaqr_factor_pivots(F._h, int(level), norms.ctypes.data, nn.value, offs.ctypes.data, ni.value + 1,
+                                    ctypes.byref(nn), ctypes.byref(ni)))
+    return [norms[offs[i]:offs[i + 1]].copy() for i in range(ni.value)]
 
 
 def spaqr_factor_sigmas(F, level):

@@ -772,6 +772,7 @@ struct Ctx {
     spaqr_factor_s* F;
     cudaStream_t st;
     std::vector<void*> temps;
+    std::vector<std::pair<void*, size_t>> kept_bytes;
     int rc = SPAQR_OK;
     size_t stage_off = 0, stage_total = 0;
 
@@ -790,6 +791,7 @@ struct Ctx {
         if (keep) {
             F->allocs.push_back(p);
             F->bytes += (int64_t)bytes;
+            kept_bytes.push_back({p, bytes});
         } else {
             temps.push_back(p);
         }
@@ -818,6 +820,22 @@ struct Ctx {
         }
     }
     void launched() { cuda(cudaGetLastError()); }
+    // Give back a kept allocation before the factor is complete (stream
+    // ordered: work already queued on st still sees it).
+    void release(void* p) {
+        for (size_t i = 0; i < kept_bytes.size(); i++)
+            if (kept_bytes[i].first == p) {
+                F->bytes -= (int64_t)kept_bytes[i].second;
+                kept_bytes.erase(kept_bytes.begin() + (int64_t)i);
+                break;
+            }
+        for (size_t i = 0; i < F->allocs.size(); i++)
+            if (F->allocs[i] == p) {
+                F->allocs.erase(F->allocs.begin() + (int64_t)i);
+                break;
+            }
+        cuda(cudaFreeAsync(p, st));
+    }
     void free_temps() {
         for (void* p : temps) cudaFreeAsync(p, st);
         temps.clear();
@@ -921,11 +939,13 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     if (C.rc != SPAQR_OK) return C.rc;
     const size_t esz = sizeof(real);
     // phase timers: (start, end, phase) event triples
-    struct Timer { cudaEvent_t a, b; int ph; };
+    struct Timer { cudaEvent_t a, b; int ph, lev; };
     std::vector<Timer> timers;
+    int cur_level = -1;
     auto tstart = [&]() {
         Timer t;
         t.ph = -1;
+        t.lev = cur_level;
         C.cuda(cudaEventCreate(&t.a));
         C.cuda(cudaEventCreate(&t.b));
         C.cuda(cudaEventRecord(t.a, st));
@@ -982,6 +1002,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     std::vector<SolveSS<real>> sss;
     std::vector<RsjTile> tiles;
     std::vector<SolveRsj<real>> pieces;
+    std::vector<std::pair<int, int>> piece_src;   // (R_sj record, first column) of every piece
     std::vector<WideFront> wfr;
     int64_t zp_max = 0;
     F->lv.assign(L, SolveLevelHost());
@@ -991,11 +1012,89 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->ranks.assign(L, {});
     F->margins.assign(L, {});
     F->sigmas.assign(L, {});
+    F->pivots.assign(L, {});
+    F->pivot_off.assign(L, std::vector<int32_t>(1, 0));
+    F->ldiag.assign(L, LevelDiag());
+
+    // Keep only what the solve reads of a finished level -- front panels
+    // (reflectors and R_ss), the R_sj rows and the scaled diagonal blocks --
+    // packed in one allocation, and give the level's block arena back: the
+    // blocks between interfaces have been carried into the next level's arena
+    // by the merge, and nothing else reads them.
+    auto compact_level = [&](int k, real* old_arena, int piece_begin) {
+        SolveLevelHost& LVk = F->lv[k];
+        int64_t tot = 0;
+        for (int f = LVk.front_begin; f < LVk.front_begin + LVk.nfront; f++) {
+            const SolveFront<real>& sf = sfronts[f];
+            tot += (int64_t)sf.m * sf.n;
+            for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) tot += (int64_t)sf.n * srsj[b].nj;
+        }
+        for (int q = LVk.ss_begin; q < LVk.ss_begin + LVk.nss; q++)
+            if (sss[q].UV) tot += (int64_t)sss[q].np * sss[q].np;
+        if (tot > 0) {
+            real* cb = C.alloc<real>(tot, true);
+            if (C.rc) return;
+            std::vector<SparsifyTask<real>> cp;
+            int64_t o = 0;
+            auto add = [&](const real* A, int64_t lda, int m, int n) {
+                SparsifyTask<real> t;
+                std::memset(&t, 0, sizeof(t));
+                t.A = A;
+                t.lda = lda;
+                t.mi = m;
+                t.nj = n;
+                t.D = cb + o;
+                t.ldd = m;
+                t.mode = 2;
+                cp.push_back(t);
+                o += (int64_t)m * n;
+                return t.D;
+            };
+            for (int f = LVk.front_begin; f < LVk.front_begin + LVk.nfront; f++) {
+                SolveFront<real>& sf = sfronts[f];
+                sf.V = add(sf.V, sf.ldv, sf.m, sf.n);
+                sf.ldv = sf.m;
+                for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) {
+                    srsj[b].R = add(srsj[b].R, srsj[b].ldr, sf.n, srsj[b].nj);
+                    srsj[b].ldr = sf.n;
+                }
+            }
+            for (int q = LVk.ss_begin; q < LVk.ss_begin + LVk.nss; q++)
+                if (sss[q].UV) {
+                    sss[q].UV = add(sss[q].UV, sss[q].lduv, sss[q].np, sss[q].np);
+                    sss[q].lduv = sss[q].np;
+                }
+            for (int pc = piece_begin; pc < (int)pieces.size(); pc++) {
+                const SolveRsj<real>& R = srsj[piece_src[pc].first];
+                pieces[pc].R = R.R + (int64_t)piece_src[pc].second * R.ldr;
+                pieces[pc].ldr = R.ldr;
+            }
+            std::vector<ScalePiece> pc;
+            for (int t = 0; t < (int)cp.size(); t++) pc.push_back({t, 0, 0});
+            SparsifyTask<real>* d = C.upload(cp, false);
+            ScalePiece* dp = C.upload(pc, false);
+            if (C.rc) return;
+            SPAQR_LAUNCH(KK_SPARSIFY, 0.0, 16.0 * tot, st, k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
+            C.launched();
+        }
+        C.release(old_arena);
+    };
 
     for (int k = 0; k < L; k++) {
         const StepPlan& sp = o.steps[k];
         const int ncl = (int)sp.cl.size();
         SolveLevelHost& LV = F->lv[k];
+        cur_level = k;
+        const int piece_begin = (int)pieces.size();
+        LevelDiag& DG = F->ldiag[k];
+        DG.block_entries = lay.total;
+        for (int s : sp.fronts) {
+            DG.n_fronts++;
+            DG.front_rows += lay.H[s];
+            DG.front_cols += sz[s];
+            DG.max_front_rows = std::max<int>(DG.max_front_rows, (int)lay.H[s]);
+            DG.max_front_cols = std::max<int>(DG.max_front_cols, (int)sz[s]);
+        }
         LV.rows = lay.rows;
         LV.ws_off = ws;
         ws += lay.rows;
@@ -1220,6 +1319,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     for (int u0 = 0; u0 < R.nj;) {
                         const int w = std::min(R.nj - u0, kTileK - cw);
                         pieces.push_back(SolveRsj<real>{R.R + (int64_t)u0 * R.ldr, R.ldr, w, 0, R.xoff + u0});
+                        piece_src.push_back({b, u0});
                         cn++;
                         cw += w;
                         u0 += w;
@@ -1570,6 +1670,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 F->sigmas[k].push_back(sgh[p]);
                 const double* rd = rdg.data() + rdg_off[p];
                 const int r = rk[p];
+                // pivot norms written by the CPQR: the r kept steps and the first rejected one
+                const int npiv = kmax[p] == 0 ? 0 : (rd[0] == 0.0 ? 1 : std::min(r + 1, kmax[p]));
+                F->pivots[k].insert(F->pivots[k].end(), rd, rd + npiv);
+                F->pivot_off[k].push_back((int32_t)F->pivots[k].size());
+                DG.n_interfaces++;
                 const double rr = r < kmax[p] ? rd[r] : (r > 0 ? rd[r - 1] : 0.0);
                 F->margins[k].push_back({rr, rd[0]});
                 // r steps of reflection (4 (m-k)(c-k)) and norm recomputation (2 (m-k)(c-k))
@@ -1675,6 +1780,13 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
         } else {
             for (int p : rest) newsz[p] = sz[p];
+        }
+
+        for (int p : rest) {
+            DG.n_remaining++;
+            DG.remaining_size += sz[p];
+            DG.interface_after += newsz[p];
+            DG.max_interface = std::max<int>(DG.max_interface, (int)sz[p]);
         }
 
         // ---------------- (iv) merge into the next level ----------------
@@ -1843,6 +1955,9 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 LV.max_ss_r = std::max(LV.max_ss_r, s.r);
             }
             LV.nss = (int)sss.size() - LV.ss_begin;
+            compact_level(k, arena, piece_begin);
+            if (C.rc) return C.rc;
+            DG.factor_bytes = F->bytes;
             C.free_temps();
             sz = nsz;
             lay = nl;
@@ -1850,6 +1965,9 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         } else {
             LV.ss_begin = (int)sss.size();
             LV.nss = 0;
+            compact_level(k, arena, piece_begin);
+            if (C.rc) return C.rc;
+            DG.factor_bytes = F->bytes;
             C.free_temps();
         }
     }
@@ -1877,7 +1995,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     if (C.rc) return C.rc;
     for (Timer& t : timers) {
         float ms = 0.0f;
-        if (t.ph >= 0 && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) F->phase_ms[t.ph] += ms;
+        if (t.ph >= 0 && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            F->phase_ms[t.ph] += ms;
+            if (t.lev >= 0) F->ldiag[t.lev].phase_ms[t.ph] += ms;
+        }
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
@@ -1977,6 +2098,41 @@ extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
         }
     for (int i = 0; i < 4; i++) out->phase_ms[i] = F->phase_ms[i];
     out->top_size = F->top_size;
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_level(const spaqr_factor_t* F, int level, spaqr_level_info* out) {
+    if (!F || !out) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (level < 0 || level >= (int)F->ldiag.size()) { spaqr::set_error("level out of range"); return SPAQR_ERR_INVALID_ARG; }
+    const LevelDiag& d = F->ldiag[level];
+    out->n_fronts = d.n_fronts;
+    out->max_front_rows = d.max_front_rows;
+    out->max_front_cols = d.max_front_cols;
+    out->n_interfaces = d.n_interfaces;
+    out->front_rows = d.front_rows;
+    out->front_cols = d.front_cols;
+    out->n_remaining = d.n_remaining;
+    out->max_interface = d.max_interface;
+    out->remaining_size = d.remaining_size;
+    out->interface_after = d.interface_after;
+    out->block_entries = d.block_entries;
+    out->factor_bytes = d.factor_bytes;
+    for (int i = 0; i < 4; i++) out->phase_ms[i] = d.phase_ms[i];
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_pivots(const spaqr_factor_t* F, int level, double* norms, int64_t cap,
+                                   int32_t* offsets, int cap_offsets, int64_t* n_norms, int* n_interfaces) {
+    if (!F || !n_norms || !n_interfaces) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (level < 0 || level >= (int)F->pivots.size()) { spaqr::set_error("level out of range"); return SPAQR_ERR_INVALID_ARG; }
+    const auto& P = F->pivots[level];
+    const auto& O = F->pivot_off[level];
+    *n_norms = (int64_t)P.size();
+    *n_interfaces = (int)O.size() - 1;
+    if (norms)
+        for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)P.size()); i++) norms[i] = P[i];
+    if (offsets)
+        for (int i = 0; i < std::min<int>(cap_offsets, (int)O.size()); i++) offsets[i] = O[i];
     return SPAQR_OK;
 }
 

@@ -275,6 +275,16 @@ struct TuneTable {
     double ms_rule = 0.0, ms_tuned = 0.0;
 };
 
+// Per-level diagnostics of a factorisation (spaqr_factor_level).
+struct LevelDiag {
+    int n_fronts = 0, max_front_rows = 0, max_front_cols = 0, n_interfaces = 0;
+    int64_t front_rows = 0, front_cols = 0;
+    int n_remaining = 0, max_interface = 0;
+    int64_t remaining_size = 0, interface_after = 0;
+    int64_t block_entries = 0, factor_bytes = 0;
+    double phase_ms[4] = {0, 0, 0, 0};
+};
+
 struct spaqr_factor_s {
     int device = 0;
     int64_t n = 0;
@@ -321,6 +331,9 @@ struct spaqr_factor_s {
     std::vector<std::vector<std::pair<int, int>>> ranks;   // per level: (size, rank)
     std::vector<std::vector<std::pair<double, double>>> margins;
     std::vector<std::vector<double>> sigmas;               // per level: sigma_p (unscaled form), else 0
+    std::vector<std::vector<double>> pivots;               // per level: CPQR pivot norms |R_kk|, interfaces concatenated
+    std::vector<std::vector<int32_t>> pivot_off;           // per level: offsets of each interface's norms (n + 1)
+    std::vector<LevelDiag> ldiag;
     double phase_ms[4] = {0, 0, 0, 0};
     double flops = 0.0;
     double solve_flops = 0.0;

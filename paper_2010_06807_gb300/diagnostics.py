@@ -1,0 +1,140 @@
+"""Profiling diagnostics of a spaQR factorisation, after the paper's
+profiling figures (Section 4): per level the fronts and interfaces, their
+sizes before and after sparsification, the decay of the CPQR pivots
+|R_kk| / |R_11| that sets the ranks, and the time of each phase; across grid
+sizes the factorisation time, the factor's device memory and the size of the
+top separator against N.
+
+Everything comes from the factor through the C ABI (spaqr_factor_level,
+spaqr_factor_pivots, spaqr_factor_ranks, spaqr_factor_info); the inputs are the
+seeded synthetic matrices of synth.convdiff.
+
+    python -m paper_2010_06807_gb300.diagnostics --kind 3d_uniform_a \\
+        --sizes 16 32 48 64 --eps 1e-2 [--scaling 0] [--json out.json]
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+import paper_2010_06807_gb300 as sq
+
+PHASES = ("factorize", "scale", "sparsify", "merge")
+DECAY_AT = (1, 2, 4, 8, 16, 32, 64)
+
+
+def pivot_decay(norms_list, at=DECAY_AT):
+    """Median over interfaces of |R_kk| / |R_11| at step k (1-based) for
+    the k in `at` that at least one interface reached; None where none did."""
+    out = {}
+    for k in at:
+        vals = [nm[k - 1] / nm[0] for nm in norms_list if len(nm) >= k and nm[0] > 0]
+        out[k] = float(np.median(vals)) if vals else None
+    return out
+
+
+def level_report(F):
+    """One dict per level (0 = leaves)."""
+    info = sq.spaqr_factor_info(F)
+    rows = []
+    for k in range(info["nlevels"]):
+        d = sq.spaqr_factor_level(F, k)
+        pairs, _ = sq.spaqr_factor_ranks(F, k)
+        piv = sq.spaqr_factor_pivots(F, k)
+        d["level"] = k
+        d["rank_fraction"] = (float(pairs[:, 1].sum()) / float(pairs[:, 0].sum())) if len(pairs) else None
+        d["pivot_decay"] = pivot_decay(piv) if piv else {}
+        rows.append(d)
+    return rows
+
+
+def factor_problem(p, eps, scaling=1, precision="fp64", skip=2, device=None):
+    """Order and factor one synthetic problem on the device; returns
+    (ordering, factor, csr tensors, factor wall ms by CUDA events)."""
+    import torch
+    dev = device or torch.device("cuda:0")
+    A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+    o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    F = sq.spaqr_factor(o, *A, eps=eps, skip=skip, scaling=scaling, precision=precision)
+    e1.record(st)
+    e1.synchronize()
+    return o, F, A, e0.elapsed_time(e1)
+
+
+def scaling_study(kind, sizes, eps, scaling=1, precision="fp64", gmres=True, device=None):
+    """Factor time, device memory, ranks and GMRES iterations per grid side."""
+    import torch
+    from synth.convdiff import config_problem, rhs
+    dev = device or torch.device("cuda:0")
+    out = []
+    for n in sizes:
+        p = config_problem(kind, n=n)
+        # warm-up factorisation (first-call attribute setup, memory pool growth)
+        _, F, _, _ = factor_problem(p, eps, scaling, precision, device=dev)
+        del F
+        o, F, A, ms = factor_problem(p, eps, scaling, precision, device=dev)
+        info = sq.spaqr_factor_info(F)
+        row = {"n_side": n, "N": p.n, "nnz": p.nnz, "levels": info["nlevels"], "factor_ms": ms,
+               "factor_bytes": info["factor_bytes"], "bytes_per_unknown": info["factor_bytes"] / p.n,
+               "top_separator": info["top_size"], "rank_sum": info["rank_sum"], "size_sum": info["size_sum"],
+               "phase_ms": dict(zip(PHASES, info["phase_ms"])), "levels_detail": level_report(F)}
+        if gmres:
+            b = torch.from_numpy(np.ascontiguousarray(rhs(p, 1).T)).to(dev).T
+            t0 = time.perf_counter()
+            _, it, rr = sq.spaqr_gmres(F, *A, b, tol=1e-12)
+            torch.cuda.synchronize(dev)
+            row.update(gmres_iters=int(it[0]), gmres_relres=float(rr[0]),
+                       gmres_ms=(time.perf_counter() - t0) * 1e3)
+        del F
+        out.append(row)
+    return out
+
+
+def markdown(study, title):
+    """Tables of a scaling_study result."""
+    lines = [f"### {title}", "",
+             "| side | N | levels | factor ms | MB | B/unknown | top sep. | ranks / sizes | GMRES it |",
+             "|---|---|---|---|---|---|---|---|---|"]
+    for r in study:
+        lines.append(f"| {r['n_side']} | {r['N']} | {r['levels']} | {r['factor_ms']:.1f} | "
+                     f"{r['factor_bytes'] / 2 ** 20:.0f} | {r['bytes_per_unknown']:.0f} | {r['top_separator']} | "
+                     f"{r['rank_sum']} / {r['size_sum']} | {r.get('gmres_iters', '')} |")
+    for r in study:
+        lines += ["", f"Per level, side {r['n_side']} (level 0 = leaves):", "",
+                  "| level | fronts | max front (rows x cols) | interfaces | max interface | size before -> after |"
+                  " median \\|R_kk\\|/\\|R_11\\| at k = 1,2,4,8,16,32,64 | ms factorize / scale / sparsify / merge |",
+                  "|---|---|---|---|---|---|---|---|"]
+        for d in r["levels_detail"]:
+            dec = " ".join("-" if d["pivot_decay"].get(k) is None else f"{d['pivot_decay'][k]:.1e}"
+                           for k in DECAY_AT) if d["pivot_decay"] else ""
+            ph = " / ".join(f"{x:.1f}" for x in d["phase_ms"])
+            lines.append(f"| {d['level']} | {d['n_fronts']} | {d['max_front_rows']} x {d['max_front_cols']} | "
+                         f"{d['n_interfaces']} | {d['max_interface']} | {d['remaining_size']} -> "
+                         f"{d['interface_after']} | {dec} | {ph} |")
+    return "\n".join(lines)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--kind", default="3d_uniform_a")
+    ap.add_argument("--sizes", type=int, nargs="+", default=[16, 32, 48, 64])
+    ap.add_argument("--eps", type=float, default=1e-2)
+    ap.add_argument("--scaling", type=int, default=1)
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--json")
+    a = ap.parse_args(argv)
+    study = scaling_study(a.kind, a.sizes, a.eps, a.scaling, a.precision, gmres=not a.no_gmres)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(study, f, indent=1)
+    print(markdown(study, f"{a.kind}, eps {a.eps:g}, scaling {a.scaling}, {a.precision}"))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
