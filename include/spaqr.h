@@ -127,6 +127,7 @@ typedef struct {
     int64_t size_sum;          /* sum of interface sizes before sparsification */
     double  phase_ms[4];       /* factorize / scale / sparsify / merge, CUDA events */
     int32_t top_size;          /* size of the root separator when it was factored */
+    int64_t peak_bytes;        /* most device bytes the factorisation held at once (factor + temporaries) */
 } spaqr_info;
 
 /* Per-level diagnostics (spaqr_factor_level), level index k = 0 at the

@@ -67,7 +67,8 @@ class _Info(ctypes.Structure):
                 ("solve_bytes", ctypes.c_int64), ("factor_flops", ctypes.c_double),
                 ("solve_flops", ctypes.c_double), ("n_interfaces_sparsified", ctypes.c_int32),
                 ("rank_sum", ctypes.c_int64), ("size_sum", ctypes.c_int64),
-                ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32)]
+                ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32),
+                ("peak_bytes", ctypes.c_int64)]
 
 
 class _LevelInfo(ctypes.Structure):

@@ -771,8 +771,9 @@ thread_local PinnedStage tl_stage;
 struct Ctx {
     spaqr_factor_s* F;
     cudaStream_t st;
-    std::vector<void*> temps;
+    std::vector<std::pair<void*, size_t>> temps;
     std::vector<std::pair<void*, size_t>> kept_bytes;
+    int64_t live = 0;   // bytes allocated by this factorisation and not yet given back
     int rc = SPAQR_OK;
     size_t stage_off = 0, stage_total = 0;
 
@@ -793,8 +794,10 @@ struct Ctx {
             F->bytes += (int64_t)bytes;
             kept_bytes.push_back({p, bytes});
         } else {
-            temps.push_back(p);
+            temps.push_back({p, bytes});
         }
+        live += (int64_t)bytes;
+        F->peak_bytes = std::max(F->peak_bytes, live);
         return (T*)p;
     }
     template <class T>
@@ -826,6 +829,7 @@ struct Ctx {
         for (size_t i = 0; i < kept_bytes.size(); i++)
             if (kept_bytes[i].first == p) {
                 F->bytes -= (int64_t)kept_bytes[i].second;
+                live -= (int64_t)kept_bytes[i].second;
                 kept_bytes.erase(kept_bytes.begin() + (int64_t)i);
                 break;
             }
@@ -836,8 +840,12 @@ struct Ctx {
             }
         cuda(cudaFreeAsync(p, st));
     }
+    ~Ctx() { free_temps(); }   // temporaries of a factorisation that stopped on an error
     void free_temps() {
-        for (void* p : temps) cudaFreeAsync(p, st);
+        for (auto& t : temps) {
+            cudaFreeAsync(t.first, st);
+            live -= (int64_t)t.second;
+        }
         temps.clear();
     }
 };
@@ -2098,6 +2106,7 @@ extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
         }
     for (int i = 0; i < 4; i++) out->phase_ms[i] = F->phase_ms[i];
     out->top_size = F->top_size;
+    out->peak_bytes = F->peak_bytes;
     return SPAQR_OK;
 }
 

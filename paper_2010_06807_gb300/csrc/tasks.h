@@ -340,4 +340,5 @@ struct spaqr_factor_s {
     int64_t solve_bytes = 0;
     int top_size = 0;
     bool unscaled = false;         // unscaled variant (Section 3.2): narrow solve forms only
+    int64_t peak_bytes = 0;        // most device bytes the factorisation held at once
 };

@@ -108,9 +108,10 @@ class DeviceOps:
 
     def factor_bytes(self, h):
         from . import spaqr_factor_info
-        nbytes = int(spaqr_factor_info(h["F"])["factor_bytes"])
+        info = spaqr_factor_info(h["F"])
+        nbytes = int(info["factor_bytes"])
         per = self._per_unknown.get(h["dim"], 0.0)
-        self._per_unknown[h["dim"]] = max(per, nbytes / h["n"])
+        self._per_unknown[h["dim"]] = max(per, int(info["peak_bytes"]) / h["n"])
         return nbytes
 
     def batch_bytes(self, n, k):
@@ -120,11 +121,12 @@ class DeviceOps:
         return 8 * n * k * (2 * cap + 8)
 
     def estimate_factor_bytes(self, problem):
-        # the largest bytes per unknown seen for factors of the same grid
-        # dimension, with half again for the factorisation's transient work
-        # arena; 16 KB per unknown before any factor of that dimension exists
+        # the largest peak bytes per unknown (factor plus the factorisation's
+        # temporaries) seen for factors of the same grid dimension, with a
+        # quarter again for larger grids; 16 KB per unknown before any factor
+        # of that dimension exists
         per = self._per_unknown.get(len(problem.dims))
-        return int(1.5 * per * problem.n) if per else 16384 * problem.n
+        return int(1.25 * per * problem.n) if per else 16384 * problem.n
 
     def solve(self, h, Bh, stream):
         """Bh: k x n host array (row i = right-hand side i).

@@ -122,8 +122,10 @@ def test_admission_evicts_on_device(spaqr_lib):
     srv = SolveServer(ops, max_slots=4, hbm_budget=1 << 40)
     b0 = srv.add_matrix(0, p0, pinned=False)
     srv.close()
-    # budget: one such factor plus its transient estimate, not two
-    srv = SolveServer(ops, max_slots=4, hbm_budget=int(2.2 * b0))
+    est = ops.estimate_factor_bytes(p1)       # from p0's peak bytes per unknown
+    assert est >= b0
+    # budget: room for the factorisation of p1 alone, not next to p0
+    srv = SolveServer(ops, max_slots=4, hbm_budget=int(est + 0.5 * b0))
     try:
         srv.add_matrix(0, p0, pinned=False)
         x0 = srv.submit_solve(0, np.ones(p0.n)).wait(600)
