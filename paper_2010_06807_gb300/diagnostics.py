@@ -109,8 +109,8 @@ def markdown(study, title):
                   " median \\|R_kk\\|/\\|R_11\\| at k = 1,2,4,8,16,32,64 | ms factorize / scale / sparsify / merge |",
                   "|---|---|---|---|---|---|---|---|"]
         for d in r["levels_detail"]:
-            dec = " ".join("-" if d["pivot_decay"].get(k) is None else f"{d['pivot_decay'][k]:.1e}"
-                           for k in DECAY_AT) if d["pivot_decay"] else ""
+            pd = {int(k): v for k, v in d["pivot_decay"].items()}   # int keys, also after a JSON round trip
+            dec = " ".join("-" if pd.get(k) is None else f"{pd[k]:.1e}" for k in DECAY_AT) if pd else ""
             ph = " / ".join(f"{x:.1f}" for x in d["phase_ms"])
             lines.append(f"| {d['level']} | {d['n_fronts']} | {d['max_front_rows']} x {d['max_front_cols']} | "
                          f"{d['n_interfaces']} | {d['max_interface']} | {d['remaining_size']} -> "
