@@ -1,0 +1,268 @@
+"""Oracle: modified nested dissection of a general sparse square matrix on
+G(A^T A), and the row assignment by a bipartite matching.
+
+TEST INFRASTRUCTURE ONLY (see package docstring).
+
+The paper (Section 2.3) orders general matrices with a hypergraph partitioner
+(PaToH, HUND) and assigns rows with MC64; neither is available here.  This is
+our own restatement of the same steps, in the paper's terms:
+  * nested dissection on the graph of A^T A gives the column partition
+    (Section 2.1: a vertex separator of G(A^T A) leaves no fill between the
+    two sides);
+  * modified nested dissection splits every separator into interfaces by the
+    descendant subdomains its columns connect to, and the cluster hierarchy
+    says which interfaces merge after each level (Sections 2.3, 2.6);
+  * rows are assigned through a matching that puts large entries on the
+    diagonal (Section 2.3, second heuristic), row i then sitting with its
+    matched column.
+
+Readings (also in the design notes):
+  G1  G(A^T A): columns i != j are adjacent when a row holds nonzeros in
+      both.  It is walked through A's rows and columns, never formed.
+  G2  Separator of a vertex set V (the columns of a node): a level set of a
+      breadth-first search.  Components of G restricted to V are taken in
+      the order of their smallest column; in each, the search starts from a
+      pseudo-peripheral column (start at the component's smallest column;
+      repeat: search, take the column of the last level with the fewest
+      neighbours in V, ties to the smallest index, and move there while the
+      number of levels grows).  The levels of all components are
+      concatenated; the separator is the first level l whose cumulative size
+      reaches half of |V|; the left child gets the levels before l, the right
+      child those after it.  Nodes at depth L-1 are leaves; empty sets still
+      get their subtree (no columns).
+  G3  Interfaces: a column x of the separator of node B gets, for every
+      non-leaf strict descendant D of B, a key (depth D, D, k) when x is
+      adjacent in G(A^T A) to some column of D's subtree: k = 1 if x touches
+      D's own separator or both of D's child subtrees, 0 if only the left
+      one, 2 if only the right one.  Keys are sorted by (depth, id); classes
+      of equal keys restricted to depths <= s are the interfaces at stage s
+      (as reading R5 of the grid ordering), atoms are the finest classes.
+  G4  Column order as reading R6 of the grid ordering, with the column index
+      in place of the grid index.
+  G5  Row matching: entries by decreasing |a_ij| (ties: row, then column)
+      are matched greedily; every row left unmatched (ascending) is then
+      matched by an augmenting path (columns of a row tried in ascending
+      order, depth first).  A structurally singular pattern is rejected.
+"""
+import sys
+
+import numpy as np
+
+from .ordering import NDOrdering, num_levels
+
+__all__ = ["nd_general", "row_matching", "column_graph"]
+
+
+class _GNode:
+    __slots__ = ("id", "depth", "parent", "left", "right", "size", "pts")
+
+    def __init__(self, nid, depth, parent):
+        self.id = nid
+        self.depth = depth
+        self.parent = parent
+        self.left = None
+        self.right = None
+        self.size = 1
+        self.pts = []
+
+
+def column_graph(n, rowptr, colind):
+    """Adjacency of G(A^T A) (reading G1): sorted neighbour lists, no self."""
+    rows = [set(int(c) for c in colind[rowptr[r]:rowptr[r + 1]]) for r in range(n)]
+    adj = [set() for _ in range(n)]
+    for cols in rows:
+        for c in cols:
+            adj[c] |= cols
+    return [sorted(a - {j}) for j, a in enumerate(adj)]
+
+
+def _bfs_levels(root, inV, adj):
+    levels = [[root]]
+    seen = {root}
+    while True:
+        nxt = sorted({y for x in levels[-1] for y in adj[x] if inV[y] and y not in seen})
+        if not nxt:
+            return levels
+        seen.update(nxt)
+        levels.append(nxt)
+
+
+def _pseudo_peripheral(start, inV, adj):
+    root = start
+    lv = _bfs_levels(root, inV, adj)
+    while True:
+        cand = min(lv[-1], key=lambda v: (sum(1 for y in adj[v] if inV[y]), v))
+        lv2 = _bfs_levels(cand, inV, adj)
+        if len(lv2) <= len(lv):
+            return root, lv
+        root, lv = cand, lv2
+
+
+def level_structure(V, adj, n):
+    """Breadth-first levels of G restricted to V, component by component (G2)."""
+    inV = np.zeros(n, dtype=bool)
+    inV[list(V)] = True
+    done = set()
+    levels = []
+    for s in sorted(V):
+        if s in done:
+            continue
+        _, lv = _pseudo_peripheral(s, inV, adj)
+        for level in lv:
+            done.update(level)
+        levels += lv
+    return levels
+
+
+def row_matching(n, rowptr, colind, val=None):
+    """rowcol[r] = the column row r is matched to (reading G5)."""
+    rowptr = np.asarray(rowptr)
+    colind = np.asarray(colind)
+    mag = np.ones(colind.shape[0]) if val is None else np.abs(np.asarray(val, dtype=np.float64))
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    order = np.lexsort((colind, rows, -mag))
+    rowcol = -np.ones(n, dtype=np.int64)
+    colrow = -np.ones(n, dtype=np.int64)
+    for e in order:
+        r, c = int(rows[e]), int(colind[e])
+        if rowcol[r] < 0 and colrow[c] < 0:
+            rowcol[r] = c
+            colrow[c] = r
+    sys.setrecursionlimit(max(10000, 4 * n))
+
+    def augment(r, seen):
+        for c in sorted(set(int(x) for x in colind[rowptr[r]:rowptr[r + 1]])):
+            if c in seen:
+                continue
+            seen.add(c)
+            if colrow[c] < 0 or augment(int(colrow[c]), seen):
+                rowcol[r] = c
+                colrow[c] = r
+                return True
+        return False
+
+    for r in range(n):
+        if rowcol[r] < 0 and not augment(r, set()):
+            raise ValueError("structurally singular matrix: no perfect matching")
+    return rowcol
+
+
+def _atoms(gidx, keys):
+    """Hierarchical atom order of one separator (reading G4 / R6)."""
+    gidx = np.asarray(gidx, dtype=np.int64)
+    depths = sorted(set(k[0] for kk in keys for k in kk))
+    sort_cols = []
+    for s in depths:
+        cls = [tuple(k for k in kk if k[0] <= s) for kk in keys]
+        minidx = {}
+        for i, cl in enumerate(cls):
+            if cl not in minidx or gidx[i] < minidx[cl]:
+                minidx[cl] = gidx[i]
+        sort_cols.append(np.array([minidx[cl] for cl in cls], dtype=np.int64))
+    order = np.lexsort(tuple([gidx] + sort_cols[::-1]))
+    atoms = []
+    cur = None
+    for i in order:
+        kk = tuple(keys[i])
+        if cur is None or kk != cur[1]:
+            cur = ([], kk)
+            atoms.append(cur)
+        cur[0].append(int(gidx[i]))
+    return [(np.array(a, dtype=np.int64), list(k)) for a, k in atoms]
+
+
+def nd_general(n, rowptr, colind, val=None, L=None):
+    """Modified nested dissection of a general matrix (readings G1-G5).
+
+    Returns an NDOrdering (as the grid ordering) with two more fields:
+    rowcol[r] (the column row r is matched to) and rperm[new] (old row of the
+    new position: the row matched to column perm[new]).
+    """
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    colind = np.asarray(colind, dtype=np.int64)
+    if L is None or L <= 0:
+        L = num_levels(n)
+    adj = column_graph(n, rowptr, colind)
+    nodes = []
+
+    def build(V, depth, parent):
+        nd = _GNode(len(nodes), depth, parent)
+        nodes.append(nd)
+        if depth == L - 1:
+            nd.pts = list(V)
+            return nd
+        if V:
+            levels = level_structure(V, adj, n)
+            cum = 0
+            for l, level in enumerate(levels):
+                cum += len(level)
+                if 2 * cum >= len(V):
+                    break
+            left = sorted(x for lv in levels[:l] for x in lv)
+            right = sorted(x for lv in levels[l + 1:] for x in lv)
+            nd.pts = sorted(levels[l])
+        else:
+            left, right = [], []
+        nd.left = build(left, depth + 1, nd)
+        nd.right = build(right, depth + 1, nd)
+        nd.size = 1 + nd.left.size + nd.right.size
+        return nd
+
+    build(list(range(n)), 0, None)
+    owner = np.zeros(n, dtype=np.int64)
+    for nd in nodes:
+        owner[nd.pts] = nd.id
+
+    node_atoms = {}
+    for nd in nodes:
+        if not nd.pts:
+            node_atoms[nd.id] = []
+            continue
+        if nd.depth == L - 1:
+            node_atoms[nd.id] = [(np.array(nd.pts, dtype=np.int64), [])]
+            continue
+        keys = []
+        for x in nd.pts:
+            marks = {}
+            for y in adj[x]:
+                o = int(owner[y])
+                if not (nd.id < o < nd.id + nd.size):
+                    continue
+                # every non-leaf node D on the path from owner(y) up to (not incl.) nd
+                child = None
+                D = nodes[o]
+                while D is not nd:
+                    if D.depth < L - 1:
+                        m = marks.setdefault(D.id, [False, False, False])
+                        if child is None:
+                            m[1] = True
+                        elif child is D.left:
+                            m[0] = True
+                        else:
+                            m[2] = True
+                    child = D
+                    D = D.parent
+            kk = []
+            for did in sorted(marks, key=lambda i: (nodes[i].depth, i)):
+                a, b, c = marks[did]
+                kk.append((nodes[did].depth, did, 1 if (b or (a and c)) else (0 if a else 2)))
+            keys.append(kk)
+        node_atoms[nd.id] = _atoms(nd.pts, keys)
+
+    order_nodes = sorted(nodes, key=lambda nd: (-nd.depth, nd.id))
+    perm, atom_ptr, atom_node, atom_keys = [], [0], [], []
+    for nd in order_nodes:
+        for gi, kk in node_atoms[nd.id]:
+            perm.append(gi)
+            atom_ptr.append(atom_ptr[-1] + gi.shape[0])
+            atom_node.append(nd.id)
+            atom_keys.append(kk)
+    perm = np.concatenate(perm) if perm else np.zeros(0, dtype=np.int64)
+    assert perm.shape[0] == n
+    o = NDOrdering((n,), L, nodes, perm.astype(np.int64), np.array(atom_ptr, dtype=np.int64),
+                   np.array(atom_node, dtype=np.int32), atom_keys)
+    o.rowcol = row_matching(n, rowptr, colind, val)
+    colrow = np.empty(n, dtype=np.int64)
+    colrow[o.rowcol] = np.arange(n)
+    o.rperm = colrow[o.perm]
+    return o

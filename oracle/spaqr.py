@@ -124,6 +124,9 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
     F.d = d
     iperm = np.empty(n, dtype=np.int64)
     iperm[o.perm] = np.arange(n)
+    # a row sits with its matched column (general orderings); else rows = columns
+    rowcol = getattr(o, "rowcol", None)
+    rowpos = iperm[rowcol] if rowcol is not None else iperm
     atom_of = np.searchsorted(o.atom_ptr, np.arange(n), side="right") - 1
     natom = o.n_atoms
     size = {a: o.atom_size(a) for a in range(natom)}
@@ -131,7 +134,7 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
     span = {a: (a, a + 1) for a in range(natom)}  # atom range of a cluster
     blocks = {}
     for r in range(n):
-        nr = iperm[r]
+        nr = rowpos[r]
         ar = atom_of[nr]
         for e in range(rowptr[r], rowptr[r + 1]):
             c = colind[e]
@@ -468,7 +471,8 @@ def solve(F, b):
     b = np.asarray(b, dtype=np.float64)
     vec = b.ndim == 1
     B = b.reshape(F.n, -1)
-    yp = _apply_inverse_permuted(F, B[F.ordering.perm])
+    rperm = getattr(F.ordering, "rperm", None)
+    yp = _apply_inverse_permuted(F, B[rperm if rperm is not None else F.ordering.perm])
     y = np.empty_like(yp)
     y[F.ordering.perm] = yp
     x = F.d[:, None] * y

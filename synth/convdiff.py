@@ -25,7 +25,8 @@ coefficient field a, then the velocity angle field, then right-hand sides.
 """
 import numpy as np
 
-__all__ = ["Problem", "convdiff", "config_problem", "batch_problems", "rhs"]
+__all__ = ["Problem", "convdiff", "config_problem", "batch_problems", "rhs", "permuted", "random_local",
+           "csr_from_coo"]
 
 
 class Problem:
@@ -36,7 +37,8 @@ class Problem:
     """
 
     def __init__(self, dims, rowptr, colind, val, seed=None, name=""):
-        self.dims = tuple(int(d) for d in dims)
+        # dims None: a general sparse matrix (no grid)
+        self.dims = None if dims is None else tuple(int(d) for d in dims)
         self.rowptr = rowptr
         self.colind = colind
         self.val = val
@@ -240,3 +242,78 @@ def rhs(problem, nrhs=1, seed=None):
         rng = np.random.Generator(np.random.PCG64(seed))
     b = rng.standard_normal((nrhs, problem.n))
     return np.asfortranarray(b.T)
+
+
+def csr_from_coo(n, rows, cols, vals):
+    """CSR (rowptr int64, colind int32 sorted in a row, val) of summed COO entries."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    key = rows * n + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    v = np.zeros(uk.shape[0])
+    np.add.at(v, inv, vals)
+    r, c = uk // n, uk % n
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    return np.cumsum(rowptr).astype(np.int64), c.astype(np.int32), v
+
+
+def permuted(problem, seed, rows=True, cols=True):
+    """P_r A P_c^T of a problem under random row / column permutations (a
+    general sparse matrix: no grid).  Draws the row permutation, then the
+    column one.  Row r of the result is row prow[r] of A; its entries move to
+    the columns pinv_c[old column]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = problem.n
+    prow = rng.permutation(n) if rows else np.arange(n)
+    pcol = rng.permutation(n) if cols else np.arange(n)
+    inv_c = np.empty(n, dtype=np.int64)
+    inv_c[pcol] = np.arange(n)
+    r_old = np.repeat(np.arange(n), np.diff(problem.rowptr))
+    inv_r = np.empty(n, dtype=np.int64)
+    inv_r[prow] = np.arange(n)
+    rowptr, colind, val = csr_from_coo(n, inv_r[r_old], inv_c[problem.colind], problem.val)
+    p = Problem(None, rowptr, colind, val, seed=seed, name=problem.name + "_perm")
+    p.rng = rng
+    p.prow, p.pcol = prow, pcol
+    return p
+
+
+def random_local(nside, k=4, radius=2.5, seed=7000):
+    """A general unsymmetric sparse matrix: nside^2 points scattered in the
+    unit square (one per grid cell, jittered); row i couples to k of the
+    points within `radius` cell widths, chosen at random, with N(0,1)
+    values; the diagonal is the row's absolute sum plus 1 (row diagonally
+    dominant).  Unknowns are numbered in a random order.  Draws: jitter,
+    numbering, then per row its neighbours and values."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = nside * nside
+    base = np.stack(np.meshgrid(np.arange(nside), np.arange(nside), indexing="xy"), -1).reshape(-1, 2)
+    pts = base + rng.uniform(-0.3, 0.3, size=(N, 2))
+    label = rng.permutation(N)
+    rows, cols, vals = [], [], []
+    cell = {tuple(b): i for i, b in enumerate(base.tolist())}
+    rr = int(np.ceil(radius))
+    for i in range(N):
+        bx, by = base[i]
+        cand = []
+        for dx in range(-rr, rr + 1):
+            for dy in range(-rr, rr + 1):
+                j = cell.get((bx + dx, by + dy))
+                if j is not None and j != i and np.hypot(*(pts[j] - pts[i])) <= radius:
+                    cand.append(j)
+        cand = sorted(cand)
+        pick = rng.choice(len(cand), size=min(k, len(cand)), replace=False) if cand else []
+        off = rng.standard_normal(len(pick))
+        for j, v in zip(pick, off):
+            rows.append(label[i])
+            cols.append(label[cand[j]])
+            vals.append(v)
+        rows.append(label[i])
+        cols.append(label[i])
+        vals.append(np.abs(off).sum() + 1.0)
+    rowptr, colind, val = csr_from_coo(N, rows, cols, vals)
+    p = Problem(None, rowptr, colind, val, seed=seed, name=f"random_local_{nside}")
+    p.rng = rng
+    return p
