@@ -157,8 +157,14 @@ const char* spaqr_last_error(void);
  * G(A^T A) for 5/7-point stencils), interfaces from the cuts of descendant
  * subdomains, cluster hierarchy, row order = column order.  Host-only integer
  * work (a device pattern is copied to the host).  nlevels = 0 picks
- * ceil(log2(N/64)).  g == NULL returns SPAQR_ERR_UNSUPPORTED (hypergraph
- * ordering for general matrices is not built).  Also builds the symbolic plan:
+ * ceil(log2(N/64)).  g == NULL orders a general sparse matrix instead
+ * (Section 2.3 uses a hypergraph partitioner and MC64 there; this is our
+ * restatement): nested dissection on G(A^T A) with breadth-first level sets
+ * as separators (pseudo-peripheral start), interfaces from the descendant
+ * subdomains each separator column is adjacent to, and rows assigned by a
+ * matching that puts large |a_ij| on the diagonal (greedy, then augmenting
+ * paths; A->val may be NULL for a pattern-only matching).  SINGULAR if the
+ * pattern has no perfect row matching.  Also builds the symbolic plan:
  * per level the active clusters, the block pattern with fill, the fronts and
  * their processing order.  *out is owned by the caller
  * (spaqr_ordering_destroy). */
@@ -191,6 +197,12 @@ int spaqr_ordering_info(const spaqr_ordering* ord, spaqr_ordering_info_t* info);
  *     front id, colour, |R|, R ids..., |C|, C ids... */
 int spaqr_ordering_get(const spaqr_ordering* ord, int64_t* perm, int64_t* atom_ptr,
                        int32_t* atom_node, int32_t* node_level, int32_t* plan);
+
+/* Row order of the ordering: rperm[new] = old row (n entries).  Equals perm
+ * for grid orderings (rows ordered as columns); for a general matrix, row
+ * rperm[k] is the row matched to column perm[k].
+ * Errors: INVALID_ARG (null argument). */
+int spaqr_ordering_rows(const spaqr_ordering* ord, int64_t* rperm);
 
 void spaqr_ordering_destroy(spaqr_ordering* ord);
 

@@ -91,7 +91,7 @@ _lib = None
 # every symbol include/spaqr.h declares
 EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_batch", "spaqr_ordering_info",
-    "spaqr_ordering_get", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
+    "spaqr_ordering_get", "spaqr_ordering_rows", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
     "spaqr_factor_destroy", "spaqr_stats_reset",
@@ -116,6 +116,7 @@ def load_library(path=None):
     lib.spaqr_order_batch.argtypes = [i32, ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), ctypes.POINTER(vp)]
     lib.spaqr_ordering_info.argtypes = [vp, ctypes.POINTER(_OrdInfo)]
     lib.spaqr_ordering_get.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.spaqr_ordering_rows.argtypes = [vp, vp]
     lib.spaqr_ordering_destroy.argtypes = [vp]
     lib.spaqr_ordering_destroy.restype = None
     if hasattr(lib, "spaqr_factor"):
@@ -268,7 +269,10 @@ class Ordering:
         plan = np.zeros(self.plan_len, dtype=np.int32)
         _check(_lib.spaqr_ordering_get(self._h, perm.ctypes.data, atom_ptr.ctypes.data,
                                        atom_node.ctypes.data, node_level.ctypes.data, plan.ctypes.data))
-        return dict(perm=perm, atom_ptr=atom_ptr, atom_node=atom_node, node_level=node_level, plan=plan)
+        rperm = np.zeros(self.n, dtype=np.int64)
+        _check(_lib.spaqr_ordering_rows(self._h, rperm.ctypes.data))
+        return dict(perm=perm, atom_ptr=atom_ptr, atom_node=atom_node, node_level=node_level, plan=plan,
+                    rperm=rperm)
 
     def plan(self):
         """Decode the symbolic plan: list of per-level dicts."""
@@ -296,14 +300,19 @@ class Ordering:
             self._h = None
 
 
-def spaqr_order(rowptr, colind, dims, nlevels=0):
-    """Geometric modified nested dissection + symbolic plan (spaqr_order)."""
+def spaqr_order(rowptr, colind, dims, nlevels=0, val=None):
+    """Modified nested dissection + symbolic plan (spaqr_order): geometric on
+    the grid `dims`, or, with dims None, the general-matrix ordering on
+    G(A^T A) with rows matched to columns (by |val| when given)."""
     load_library()
-    csr, keep = _make_csr(rowptr, colind)
-    dims = tuple(int(d) for d in dims)
-    g = _Grid(len(dims), dims[0], dims[1], dims[2] if len(dims) > 2 else 1)
+    csr, keep = _make_csr(rowptr, colind, val if dims is None else None)
     h = ctypes.c_void_p()
-    _check(_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), int(nlevels), ctypes.byref(h)))
+    if dims is None:
+        _check(_lib.spaqr_order(ctypes.byref(csr), None, int(nlevels), ctypes.byref(h)))
+    else:
+        dims = tuple(int(d) for d in dims)
+        g = _Grid(len(dims), dims[0], dims[1], dims[2] if len(dims) > 2 else 1)
+        _check(_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), int(nlevels), ctypes.byref(h)))
     return Ordering(h.value)
 
 

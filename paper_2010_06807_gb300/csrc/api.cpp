@@ -32,10 +32,6 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
     if (!out) { spaqr::set_error("out is NULL"); return SPAQR_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!A) { spaqr::set_error("A is NULL"); return SPAQR_ERR_INVALID_ARG; }
-    if (!g) {
-        spaqr::set_error("no grid given: hypergraph ordering of general matrices is not built");
-        return SPAQR_ERR_UNSUPPORTED;
-    }
     if (A->n <= 0 || A->nnz < A->n || !A->rowptr || !A->colind) {
         spaqr::set_error("bad CSR sizes or pointers");
         return SPAQR_ERR_INVALID_ARG;
@@ -56,12 +52,27 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
         rowptr = rp.data();
         colind = ci.data();
     }
-    int dims[3] = {g->nx, g->ny, g->dim == 3 ? g->nz : 1};
+    // general matrices (no grid): the row matching uses |a_ij| when values are given
+    std::vector<double> vh;
+    const double* val = A->val;
+    if (!g && val && A->on_device) {
+        vh.resize(A->nnz);
+        if (cudaMemcpy(vh.data(), A->val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            spaqr::set_error("copying the device values failed");
+            return SPAQR_ERR_CUDA;
+        }
+        val = vh.data();
+    }
     spaqr_ordering* ord = new (std::nothrow) spaqr_ordering();
     if (!ord) { spaqr::set_error("host allocation failed"); return SPAQR_ERR_OOM; }
     int rc;
     try {
-        rc = spaqr::build_ordering(rowptr, colind, A->n, A->nnz, g->dim, dims, nlevels, ord->o);
+        if (g) {
+            int dims[3] = {g->nx, g->ny, g->dim == 3 ? g->nz : 1};
+            rc = spaqr::build_ordering(rowptr, colind, A->n, A->nnz, g->dim, dims, nlevels, ord->o);
+        } else {
+            rc = spaqr::build_ordering_general(rowptr, colind, val, A->n, A->nnz, nlevels, ord->o);
+        }
     } catch (const std::bad_alloc&) {
         spaqr::set_error("host allocation failed");
         rc = SPAQR_ERR_OOM;

@@ -980,6 +980,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     int64_t* d_csce = C.upload(o.csc_entry, false);
     int64_t* d_goff = C.upload(o.gather_off, false);
     F->d_perm = C.upload(o.perm, true);
+    F->d_rperm = o.rperm.empty() ? F->d_perm : C.upload(o.rperm, true);
     F->d_scale = C.alloc<double>(n, true);
     int* d_flags = C.alloc<int>(4, true);
     if (C.rc) return C.rc;

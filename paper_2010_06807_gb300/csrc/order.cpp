@@ -298,9 +298,12 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
     }
 
     // ---- symbolic plan -------------------------------------------------
+    // a row sits at the position of its matched column (rows = columns when
+    // there is no matching)
+    auto rowpos = [&](int64_t r) { return o.rowcol.empty() ? o.iperm[r] : o.iperm[o.rowcol[r]]; };
     std::set<std::pair<int, int>> P;  // (row cluster, col cluster) by first atom
     for (int64_t r = 0; r < n; r++) {
-        int ar = o.atom_of[o.iperm[r]];
+        int ar = o.atom_of[rowpos(r)];
         for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
             int ac = o.atom_of[o.iperm[colind[e]]];
             if (!o.related(o.atom_node[ar], o.atom_node[ac])) {
@@ -470,7 +473,7 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         o.arena1_size = poff[ncl];
         o.gather_off.assign(nnz, 0);
         for (int64_t r = 0; r < n; r++) {
-            int64_t nr = o.iperm[r];
+            int64_t nr = rowpos(r);
             int ar = o.atom_of[nr];
             for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
                 int64_t nc = o.iperm[colind[e]];
@@ -480,6 +483,269 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
                                   (nc - o.atom_ptr[ac]) * H[ac];
             }
         }
+    }
+    return SPAQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// General sparse matrices: modified nested dissection on G(A^T A) and a row
+// matching (Section 2.3 orders such matrices with a hypergraph partitioner and
+// MC64; this is our restatement).  Readings:
+//  * G(A^T A): columns i != j adjacent when a row holds nonzeros in both;
+//  * separator of a node's column set V: a breadth-first level.  Components
+//    of G restricted to V are taken by their smallest column; each is
+//    searched from a pseudo-peripheral column (start at the smallest column;
+//    repeatedly search, take the last level's column with the fewest
+//    neighbours in V, ties to the smallest index, and move there while the
+//    number of levels grows); the levels of all components are concatenated
+//    and the separator is the first level whose cumulative size reaches half
+//    of |V|, the left child gets the levels before it, the right child those
+//    after it;
+//  * a separator column x gets, for every non-leaf strict descendant D of its
+//    node that x is adjacent to, the key (depth D, D, k): k = 1 when x touches
+//    D's separator or both of D's child subtrees, 0 when only the left one,
+//    2 when only the right one; atoms and their order as for grids, with the
+//    column index as the index;
+//  * rows: entries by decreasing |a_ij| (ties: row, column) matched greedily,
+//    then every unmatched row (ascending) by an augmenting path (columns of a
+//    row in ascending order, depth first); row r sits with its column.
+// ---------------------------------------------------------------------------
+struct GeneralND {
+    int64_t n = 0;
+    int L = 1;
+    std::vector<int64_t> ap, aj;         // G(A^T A), neighbours sorted
+    std::vector<int32_t> inset, seen, done;
+    int32_t setid = 0, seenid = 0, doneid = 0;
+    std::vector<NDNode> nodes;
+    std::vector<std::vector<int64_t>> pts;
+    using Levels = std::vector<std::vector<int64_t>>;
+
+    void graph(const int64_t* rp, const int32_t* ci) {
+        std::vector<int64_t> cp(n + 1, 0), ri(rp[n]);
+        for (int64_t e = 0; e < rp[n]; e++) cp[ci[e] + 1]++;
+        for (int64_t j = 0; j < n; j++) cp[j + 1] += cp[j];
+        {
+            std::vector<int64_t> f(cp.begin(), cp.end() - 1);
+            for (int64_t r = 0; r < n; r++)
+                for (int64_t e = rp[r]; e < rp[r + 1]; e++) ri[f[ci[e]]++] = r;
+        }
+        std::vector<int32_t> mark(n, -1);
+        ap.assign(n + 1, 0);
+        aj.clear();
+        std::vector<int64_t> tmp;
+        for (int64_t j = 0; j < n; j++) {
+            tmp.clear();
+            mark[j] = (int32_t)j;
+            for (int64_t e = cp[j]; e < cp[j + 1]; e++) {
+                const int64_t r = ri[e];
+                for (int64_t f = rp[r]; f < rp[r + 1]; f++) {
+                    const int64_t c = ci[f];
+                    if (mark[c] != (int32_t)j) {
+                        mark[c] = (int32_t)j;
+                        tmp.push_back(c);
+                    }
+                }
+            }
+            std::sort(tmp.begin(), tmp.end());
+            aj.insert(aj.end(), tmp.begin(), tmp.end());
+            ap[j + 1] = (int64_t)aj.size();
+        }
+        inset.assign(n, 0);
+        seen.assign(n, 0);
+        done.assign(n, 0);
+    }
+    int degree_in(int64_t v) const {
+        int d = 0;
+        for (int64_t e = ap[v]; e < ap[v + 1]; e++) d += inset[aj[e]] == setid;
+        return d;
+    }
+    void bfs(int64_t root, Levels& lv) {
+        ++seenid;
+        lv.assign(1, std::vector<int64_t>(1, root));
+        seen[root] = seenid;
+        while (true) {
+            std::vector<int64_t> nxt;
+            for (int64_t x : lv.back())
+                for (int64_t e = ap[x]; e < ap[x + 1]; e++) {
+                    const int64_t y = aj[e];
+                    if (inset[y] == setid && seen[y] != seenid) {
+                        seen[y] = seenid;
+                        nxt.push_back(y);
+                    }
+                }
+            if (nxt.empty()) return;
+            std::sort(nxt.begin(), nxt.end());
+            lv.push_back(std::move(nxt));
+        }
+    }
+    void pseudo_peripheral(int64_t s, Levels& lv) {
+        bfs(s, lv);
+        while (true) {
+            int64_t cand = -1;
+            int bd = 0;
+            for (int64_t v : lv.back()) {
+                const int d = degree_in(v);
+                if (cand < 0 || d < bd || (d == bd && v < cand)) { bd = d; cand = v; }
+            }
+            Levels lv2;
+            bfs(cand, lv2);
+            if (lv2.size() <= lv.size()) return;
+            lv.swap(lv2);
+        }
+    }
+    Levels level_structure(const std::vector<int64_t>& V) {
+        ++setid;
+        for (int64_t v : V) inset[v] = setid;
+        ++doneid;
+        Levels all, lv;
+        for (int64_t s : V) {
+            if (done[s] == doneid) continue;
+            pseudo_peripheral(s, lv);
+            for (auto& level : lv) {
+                for (int64_t v : level) done[v] = doneid;
+                all.push_back(level);
+            }
+        }
+        return all;
+    }
+    int build(const std::vector<int64_t>& V, int depth, int parent) {
+        const int id = (int)nodes.size();
+        nodes.push_back(NDNode());
+        pts.emplace_back();
+        nodes[id].id = id;
+        nodes[id].depth = depth;
+        nodes[id].parent = parent;
+        if (depth == L - 1) {
+            pts[id] = V;
+            return id;
+        }
+        std::vector<int64_t> S, Lf, Rt;
+        if (!V.empty()) {
+            Levels lv = level_structure(V);
+            size_t l = 0;
+            int64_t cum = 0;
+            for (; l < lv.size(); l++) {
+                cum += (int64_t)lv[l].size();
+                if (2 * cum >= (int64_t)V.size()) break;
+            }
+            S = lv[l];
+            for (size_t i = 0; i < l; i++) Lf.insert(Lf.end(), lv[i].begin(), lv[i].end());
+            for (size_t i = l + 1; i < lv.size(); i++) Rt.insert(Rt.end(), lv[i].begin(), lv[i].end());
+            std::sort(S.begin(), S.end());
+            std::sort(Lf.begin(), Lf.end());
+            std::sort(Rt.begin(), Rt.end());
+        }
+        const int left = build(Lf, depth + 1, id);
+        const int right = build(Rt, depth + 1, id);
+        nodes[id].left = left;
+        nodes[id].right = right;
+        nodes[id].cut_dim = 0;
+        nodes[id].size = 1 + nodes[left].size + nodes[right].size;
+        pts[id] = std::move(S);
+        return id;
+    }
+};
+
+// Atoms of one separator in hierarchical order (coarser classes first, each
+// class by its smallest index), points by index.
+void order_atoms(const std::vector<int64_t>& gidx, const std::vector<std::vector<Key>>& keys,
+                 std::vector<Atom>& atoms) {
+    const size_t np = gidx.size();
+    std::vector<int> depths;
+    for (auto& kk : keys)
+        for (const Key& k : kk) depths.push_back(k.depth);
+    std::sort(depths.begin(), depths.end());
+    depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
+    std::vector<std::vector<int64_t>> scol(depths.size(), std::vector<int64_t>(np));
+    for (size_t si = 0; si < depths.size(); si++) {
+        const int s = depths[si];
+        std::map<std::vector<std::tuple<int, int, int>>, int64_t> minidx;
+        std::vector<std::vector<std::tuple<int, int, int>>> cls(np);
+        for (size_t i = 0; i < np; i++) {
+            for (const Key& kk : keys[i])
+                if (kk.depth <= s) cls[i].push_back(std::make_tuple(kk.depth, kk.node, kk.k));
+            auto it = minidx.find(cls[i]);
+            if (it == minidx.end() || gidx[i] < it->second) minidx[cls[i]] = gidx[i];
+        }
+        for (size_t i = 0; i < np; i++) scol[si][i] = minidx[cls[i]];
+    }
+    std::vector<size_t> ord(np);
+    for (size_t i = 0; i < np; i++) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+        for (size_t si = 0; si < depths.size(); si++)
+            if (scol[si][a] != scol[si][b]) return scol[si][a] < scol[si][b];
+        return gidx[a] < gidx[b];
+    });
+    for (size_t t = 0; t < np; t++) {
+        const size_t i = ord[t];
+        if (atoms.empty() || atoms.back().key != keys[i]) {
+            Atom a;
+            a.key = keys[i];
+            atoms.push_back(std::move(a));
+        }
+        atoms.back().pts.push_back(gidx[i]);
+    }
+}
+
+// rowcol[r] = the column row r is matched to; SINGULAR when no perfect
+// matching exists.
+int row_matching(const int64_t* rp, const int32_t* ci, const double* val, int64_t n, std::vector<int64_t>& rowcol) {
+    const int64_t nnz = rp[n];
+    std::vector<int64_t> rows(nnz), ord(nnz);
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++) rows[e] = r;
+    for (int64_t e = 0; e < nnz; e++) ord[e] = e;
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        const double ma = val ? std::fabs(val[a]) : 1.0, mb = val ? std::fabs(val[b]) : 1.0;
+        if (ma != mb) return ma > mb;
+        if (rows[a] != rows[b]) return rows[a] < rows[b];
+        return ci[a] < ci[b];
+    });
+    rowcol.assign(n, -1);
+    std::vector<int64_t> colrow(n, -1);
+    for (int64_t e : ord) {
+        const int64_t r = rows[e], c = ci[e];
+        if (rowcol[r] < 0 && colrow[c] < 0) {
+            rowcol[r] = c;
+            colrow[c] = r;
+        }
+    }
+    // sorted distinct columns of every row, for the augmenting paths
+    std::vector<int64_t> cp(n + 1, 0), cc;
+    for (int64_t r = 0; r < n; r++) {
+        std::vector<int64_t> t(ci + rp[r], ci + rp[r + 1]);
+        std::sort(t.begin(), t.end());
+        t.erase(std::unique(t.begin(), t.end()), t.end());
+        cc.insert(cc.end(), t.begin(), t.end());
+        cp[r + 1] = (int64_t)cc.size();
+    }
+    std::vector<int32_t> vis(n, 0);
+    int32_t visid = 0;
+    struct Frame { int64_t r, k, c; };
+    std::vector<Frame> st;
+    for (int64_t r0 = 0; r0 < n; r0++) {
+        if (rowcol[r0] >= 0) continue;
+        ++visid;
+        st.assign(1, Frame{r0, cp[r0], -1});
+        bool found = false;
+        while (!st.empty() && !found) {
+            const int64_t r = st.back().r;
+            if (st.back().k >= cp[r + 1]) { st.pop_back(); continue; }
+            const int64_t c = cc[st.back().k++];
+            if (vis[c] == visid) continue;
+            vis[c] = visid;
+            st.back().c = c;
+            if (colrow[c] < 0) {
+                for (const Frame& f : st) {
+                    rowcol[f.r] = f.c;
+                    colrow[f.c] = f.r;
+                }
+                found = true;
+            } else {
+                st.push_back(Frame{colrow[c], cp[colrow[c]], -1});
+            }
+        }
+        if (!found) { set_error("structurally singular matrix: no perfect row matching"); return SPAQR_ERR_SINGULAR; }
     }
     return SPAQR_OK;
 }
@@ -511,6 +777,85 @@ int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int6
     rc = nd_grid(dim, o.dims, o.L, o.nodes, node_atoms);
     if (rc != SPAQR_OK) return rc;
     return plan_forest(o, rowptr, colind, node_atoms);
+}
+
+int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const double* val, int64_t n,
+                           int64_t nnz, int nlevels, Ordering& o) {
+    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+    for (int64_t e = 0; e < nnz; e++)
+        if (colind[e] < 0 || colind[e] >= n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    o.dim = 0;
+    o.dims[0] = (int)std::min<int64_t>(n, 0x7fffffff);
+    o.dims[1] = o.dims[2] = 1;
+    o.n = n;
+    o.nnz = nnz;
+    o.L = nlevels > 0 ? nlevels : num_levels(n);
+    int rc = row_matching(rowptr, colind, val, n, o.rowcol);
+    if (rc != SPAQR_OK) return rc;
+    GeneralND g;
+    g.n = n;
+    g.L = o.L;
+    g.graph(rowptr, colind);
+    std::vector<int64_t> all(n);
+    for (int64_t i = 0; i < n; i++) all[i] = i;
+    g.build(all, 0, -1);
+    const int nn = (int)g.nodes.size();
+    std::vector<int> owner(n, -1);
+    for (int id = 0; id < nn; id++)
+        for (int64_t v : g.pts[id]) owner[v] = id;
+    std::vector<std::vector<Atom>> node_atoms(nn);
+    std::vector<std::array<char, 3>> mk(nn);
+    std::vector<int32_t> mstamp(nn, -1);
+    for (int id = 0; id < nn; id++) {
+        const std::vector<int64_t>& S = g.pts[id];
+        if (S.empty()) continue;
+        if (g.nodes[id].depth == o.L - 1) {
+            Atom a;
+            a.pts = S;
+            node_atoms[id].push_back(std::move(a));
+            continue;
+        }
+        const int lo = id, hi = id + g.nodes[id].size;
+        std::vector<std::vector<Key>> keys(S.size());
+        for (size_t xi = 0; xi < S.size(); xi++) {
+            const int64_t x = S[xi];
+            std::vector<int> touched;
+            for (int64_t e = g.ap[x]; e < g.ap[x + 1]; e++) {
+                const int ow = owner[g.aj[e]];
+                if (!(lo < ow && ow < hi)) continue;
+                int child = -1;
+                for (int D = ow; D != id; child = D, D = g.nodes[D].parent) {
+                    if (g.nodes[D].depth >= o.L - 1) continue;
+                    if (mstamp[D] != (int32_t)(xi + 1)) {
+                        mstamp[D] = (int32_t)(xi + 1);
+                        mk[D] = {0, 0, 0};
+                        touched.push_back(D);
+                    }
+                    if (child < 0) mk[D][1] = 1;
+                    else if (child == g.nodes[D].left) mk[D][0] = 1;
+                    else mk[D][2] = 1;
+                }
+            }
+            std::sort(touched.begin(), touched.end(), [&](int a, int b) {
+                if (g.nodes[a].depth != g.nodes[b].depth) return g.nodes[a].depth < g.nodes[b].depth;
+                return a < b;
+            });
+            for (int D : touched) {
+                const int k = (mk[D][1] || (mk[D][0] && mk[D][2])) ? 1 : (mk[D][0] ? 0 : 2);
+                keys[xi].push_back(Key{g.nodes[D].depth, D, k});
+            }
+            for (int D : touched) mstamp[D] = -1;
+        }
+        order_atoms(S, keys, node_atoms[id]);
+    }
+    o.nodes = std::move(g.nodes);
+    rc = plan_forest(o, rowptr, colind, node_atoms);
+    if (rc != SPAQR_OK) return rc;
+    std::vector<int64_t> colrow(n);
+    for (int64_t r = 0; r < n; r++) colrow[o.rowcol[r]] = r;
+    o.rperm.resize(n);
+    for (int64_t k = 0; k < n; k++) o.rperm[k] = colrow[o.perm[k]];
+    return SPAQR_OK;
 }
 
 // Ordering of the block-diagonal matrix diag(A_0, ..., A_{count-1}): every
@@ -599,6 +944,14 @@ extern "C" int spaqr_ordering_info(const spaqr_ordering* ord, spaqr_ordering_inf
     info->n_atoms = (int32_t)ord->o.atom_node.size();
     info->n_nodes = (int32_t)ord->o.nodes.size();
     info->plan_len = (int64_t)ord->o.plan_code.size();
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_ordering_rows(const spaqr_ordering* ord, int64_t* rperm) {
+    if (!ord || !rperm) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    const auto& o = ord->o;
+    const std::vector<int64_t>& src = o.rperm.empty() ? o.perm : o.rperm;
+    std::copy(src.begin(), src.end(), rperm);
     return SPAQR_OK;
 }
 

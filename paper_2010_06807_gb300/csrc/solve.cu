@@ -1193,7 +1193,7 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
     const unsigned nb = (unsigned)((n + 255) / 256);
     real* Y0 = A.level(0);
     SPAQR_LAUNCH(KK_SOLVE_PERM, 0.0, 8.0 * n + 16.0 * n * nrhs, st,
-                 k_perm_in<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, B, ldb, Y0, F->lv[0].rows));
+                 k_perm_in<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_rperm, B, ldb, Y0, F->lv[0].rows));
     const int L = F->L;
     for (int k = 0; k < L; k++) {
         const SolveLevelHost& LV = F->lv[k];

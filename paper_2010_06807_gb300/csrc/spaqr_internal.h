@@ -51,6 +51,10 @@ struct Ordering {
     std::vector<NDNode> nodes;
     std::vector<int64_t> perm;       // new -> old
     std::vector<int64_t> iperm;      // old -> new
+    // general matrices: row r sits with column rowcol[r] (a matching of rows
+    // to columns); rperm[new] = old row.  Both empty: rows ordered as columns.
+    std::vector<int64_t> rowcol;
+    std::vector<int64_t> rperm;
     std::vector<int64_t> atom_ptr;
     std::vector<int32_t> atom_node;
     std::vector<int32_t> atom_of;    // new index -> atom
@@ -75,6 +79,8 @@ int build_ordering_batch(int count, const int64_t* const* rowptrs, const int32_t
                          const int64_t* ns, const int64_t* nnzs, const int* dims_list, Ordering& o);
 int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
                    int dim, const int* dims, int nlevels, Ordering& out);
+int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const double* val, int64_t n,
+                           int64_t nnz, int nlevels, Ordering& out);
 
 int num_levels(int64_t n);
 

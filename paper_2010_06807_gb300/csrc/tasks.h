@@ -296,6 +296,7 @@ struct spaqr_factor_s {
     int esz = 8;                   // bytes per element of that type
     double* d_scale = nullptr;     // column scaling D (n), FP64
     int64_t* d_perm = nullptr;     // new -> old
+    int64_t* d_rperm = nullptr;    // new -> old row (= d_perm unless rows were matched)
     // solve plan (device arrays of SolveFront<real>, SolveRsj<real>, SolveSS<real>)
     std::vector<SolveLevelHost> lv;
     void* d_fronts = nullptr;

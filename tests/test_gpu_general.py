@@ -1,0 +1,80 @@
+"""General sparse matrices (no grid) on the GPU against the FP64 oracle:
+the ordering of G(A^T A) with matched rows (spaqr_order with grid NULL), then
+the same factorisation and solve kernels.  Bars as for grids: ranks
+bit-exact, one application to 1e-10, eps = 0 exact, GMRES to 1e-12 with the
+oracle's iteration count +-1; the FP32 factor and the unscaled variant also
+converge."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2010_06807_gb300 as sq
+from oracle import spaqr as osq
+from oracle.ordering_general import nd_general
+from synth.convdiff import config_problem, permuted, random_local
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev(spaqr_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _colmajor(b, dev):
+    return torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
+
+
+def _problems():
+    g = config_problem("2d_uniform_a", n=24)
+    return [("row_col_permuted_grid", permuted(g, 31), 4),
+            ("rows_permuted_3d", permuted(config_problem("3d_uniform_a", n=8), 32, cols=False), 3),
+            ("random_local", random_local(20, seed=7021), 4),
+            ("random_local_auto_L", random_local(40, seed=7022), 0)]
+
+
+def _gpu(p, dev, eps, L, skip, **kw):
+    A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+    o = sq.spaqr_order(*A[:2], None, L, val=A[2])
+    return o, sq.spaqr_factor(o, *A, eps=eps, skip=skip, **kw), A
+
+
+@pytest.mark.parametrize("eps,skip", [(0.0, 0), (1e-2, 1), (1e-3, 2)])
+@pytest.mark.parametrize("name,p,L", _problems())
+def test_general_matches_oracle(dev, name, p, L, eps, skip):
+    o, F, _ = _gpu(p, dev, eps, L, skip)
+    og = nd_general(p.n, p.rowptr, p.colind, p.val, o.L)
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, None, eps, nlevels=o.L, skip=skip, ordering=og)
+    for lev, R in enumerate(Fo.ranks):
+        exp = [tuple(v) for _, v in sorted(R.items()) if v[0] > 0]
+        assert [tuple(x) for x in sq.spaqr_factor_ranks(F, lev)[0].tolist()] == exp, lev
+    b = np.random.default_rng(3).standard_normal((p.n, 2))
+    xo = osq.solve(Fo, b)
+    xg = sq.spaqr_solve(F, _colmajor(b, dev)).cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL
+    if eps == 0.0:
+        res = np.linalg.norm(b - p.matvec(xg), axis=0) / np.linalg.norm(b, axis=0)
+        assert res.max() <= 1e-12
+
+
+@pytest.mark.parametrize("name,p,L", _problems())
+def test_general_gmres(dev, name, p, L):
+    o, F, A = _gpu(p, dev, 1e-2, L, 2)
+    b = np.random.default_rng(4).standard_normal(p.n)
+    x, it, rr = sq.spaqr_gmres(F, *A, torch.from_numpy(b).to(dev), tol=1e-12)
+    assert rr[0] <= 1e-12
+    assert np.linalg.norm(b - p.matvec(x.cpu().numpy())) / np.linalg.norm(b) <= 2e-12
+    og = nd_general(p.n, p.rowptr, p.colind, p.val, o.L)
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-2, nlevels=o.L, skip=2, ordering=og)
+    _, ito, _, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: osq.solve(Fo, v))
+    assert abs(int(it[0]) - ito) <= 1, (it, ito)
+    # FP32 factor and the unscaled variant on the same ordering
+    for kw in (dict(precision="fp32"), dict(scaling=0)):
+        F2 = sq.spaqr_factor(o, *A, eps=1e-2, skip=2, **kw)
+        _, it2, rr2 = sq.spaqr_gmres(F2, *A, torch.from_numpy(b).to(dev), tol=1e-12)
+        assert rr2[0] <= 1e-12, kw

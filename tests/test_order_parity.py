@@ -57,3 +57,40 @@ def test_order_rejects_bad_input(spaqr_lib):
     ci[1] = 63 if ci[1] != 0 else ci[1]
     with pytest.raises(sq.SpaqrError):
         sq.spaqr_order(rp, np.sort(ci.reshape(-1)), (8, 8), 3)
+
+
+def _general_cases():
+    from synth.convdiff import permuted, random_local
+    g = config_problem("2d_uniform_a", n=20)
+    return [("grid_no_dims", g, 4), ("row_col_permuted", permuted(g, 21), 4),
+            ("rows_permuted_3d", permuted(config_problem("3d_uniform_a", n=7), 22, cols=False), 3),
+            ("random_local", random_local(18, seed=7011), 4), ("random_local_auto_L", random_local(26, seed=7012), 0)]
+
+
+@pytest.mark.parametrize("name,p,L", _general_cases())
+def test_general_ordering_bit_exact(spaqr_lib, name, p, L):
+    """Ordering of a general matrix (no grid): nested dissection on
+    G(A^T A), interfaces, row matching and symbolic plan equal the oracle's."""
+    from oracle.ordering_general import nd_general
+    ordl = sq.spaqr_order(p.rowptr, p.colind, None, L, val=p.val)
+    arr = ordl.arrays()
+    o = nd_general(p.n, p.rowptr, p.colind, p.val, L if L > 0 else None)
+    assert ordl.L == o.L
+    for k in ("perm", "atom_ptr", "atom_node", "node_level", "rperm"):
+        np.testing.assert_array_equal(arr[k], getattr(o, k), err_msg=k)
+    F = osq.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-2, nlevels=o.L, skip=1, ordering=o)
+    plan = ordl.plan()
+    assert len(plan) == len(F.steps)
+    for st_l, st_o in zip(plan, F.steps):
+        assert st_l["clusters"] == sorted(st_o["sizes"].keys())
+        assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
+        for f in st_l["fronts"]:
+            assert f["R"] == list(st_o["R"][f["id"]]) and f["C"] == list(st_o["C"][f["id"]])
+
+
+def test_general_ordering_rejects_singular_pattern(spaqr_lib):
+    rp = np.array([0, 1, 2, 3], dtype=np.int64)
+    ci = np.array([0, 0, 2], dtype=np.int32)
+    with pytest.raises(sq.SpaqrError) as e:
+        sq.spaqr_order(rp, ci, None, 1)
+    assert e.value.name == "SINGULAR"
