@@ -279,6 +279,31 @@ def _high_contrast(sq, torch, np, dev, st, flush):
     return out
 
 
+def _general(sq, torch, np, dev, st, flush):
+    """General sparse matrices through the grid-free ordering (nested
+    dissection on G(A^T A), matched rows): the headline matrix with its rows
+    and columns randomly permuted (same system, ordering found without the
+    grid) and a random local unsymmetric matrix (192^2 scattered points, 4
+    random neighbours per row); 16 RHS, eps 1e-2, FP64, factor + GMRES to
+    1e-12 as the headline step."""
+    from synth.convdiff import config_problem, permuted, random_local, rhs
+    out = {}
+    for name, p in (("headline_matrix_permuted", permuted(config_problem(KIND, n=NSIDE), 8001)),
+                    ("random_local_192", random_local(192, seed=8002))):
+        t0 = time.perf_counter()
+        o = sq.spaqr_order(p.rowptr, p.colind, None, 0, val=p.val)
+        order_ms = (time.perf_counter() - t0) * 1e3
+        b = rhs(p, NRHS)
+        A = (torch.from_numpy(p.rowptr).to(dev), torch.from_numpy(p.colind).to(dev),
+             torch.from_numpy(p.val).to(dev))
+        Bd = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
+        Xd = torch.zeros(NRHS, p.n, dtype=torch.float64, device=dev).T
+        res, _ = _timed_form(sq, torch, o, A, Bd, Xd, st, flush, EPS, "fp64", 3, 1)
+        res.update(order_ms=order_ms, n=p.n, nnz=p.nnz, levels=o.L)
+        out[name] = res
+    return out
+
+
 def _batched(sq, torch, np, dev, st, flush, count=64, steps=3, warmup=1):
     """Batched workload: `count` independent 2D problems (sides from
     {32,48,...,128}, a ~ U[0.1,10], v = Pe (1,1), Pe ~ U[1,100]), one RHS per
@@ -582,6 +607,7 @@ def ours(a):
     line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
     line["batched_64x2d"] = _batched(sq, torch, np, dev, st, flush)
     line["high_contrast_2d_ablation"] = _high_contrast(sq, torch, np, dev, st, flush)
+    line["general_sparse"] = _general(sq, torch, np, dev, st, flush)
     if not a.no_serve:
         from paper_2010_06807_gb300.serve import run_plain, run_workload
         srv = {}
