@@ -28,8 +28,10 @@ Readings (also in the design notes):
       number of levels grows).  The levels of all components are
       concatenated; the separator is the first level l whose cumulative size
       reaches half of |V|; the left child gets the levels before l, the right
-      child those after it.  Nodes at depth L-1 are leaves; empty sets still
-      get their subtree (no columns).
+      child those after it.  The separator then keeps only its columns that
+      are adjacent to the right side; the others join the left side (they
+      touch no right column, so the sides stay uncoupled).  Nodes at depth L-1
+      are leaves; empty sets still get their subtree (no columns).
   G3  Interfaces: a column x of the separator of node B gets, for every
       non-leaf strict descendant D of B, a key (depth D, D, k) when x is
       adjacent in G(A^T A) to some column of D's subtree: k = 1 if x touches
@@ -198,9 +200,12 @@ def nd_general(n, rowptr, colind, val=None, L=None):
                 cum += len(level)
                 if 2 * cum >= len(V):
                     break
-            left = sorted(x for lv in levels[:l] for x in lv)
+            left = [x for lv in levels[:l] for x in lv]
             right = sorted(x for lv in levels[l + 1:] for x in lv)
-            nd.pts = sorted(levels[l])
+            rset = set(right)
+            sep = sorted(levels[l])
+            nd.pts = [x for x in sep if any(y in rset for y in adj[x])]
+            left = sorted(left + [x for x in sep if not any(y in rset for y in adj[x])])
         else:
             left, right = [], []
         nd.left = build(left, depth + 1, nd)

@@ -500,7 +500,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
 //    number of levels grows); the levels of all components are concatenated
 //    and the separator is the first level whose cumulative size reaches half
 //    of |V|, the left child gets the levels before it, the right child those
-//    after it;
+//    after it; the separator keeps only its columns adjacent to the right
+//    side, the others join the left side;
 //  * a separator column x gets, for every non-leaf strict descendant D of its
 //    node that x is adjacent to, the key (depth D, D, k): k = 1 when x touches
 //    D's separator or both of D's child subtrees, 0 when only the left one,
@@ -628,9 +629,16 @@ struct GeneralND {
                 cum += (int64_t)lv[l].size();
                 if (2 * cum >= (int64_t)V.size()) break;
             }
-            S = lv[l];
             for (size_t i = 0; i < l; i++) Lf.insert(Lf.end(), lv[i].begin(), lv[i].end());
             for (size_t i = l + 1; i < lv.size(); i++) Rt.insert(Rt.end(), lv[i].begin(), lv[i].end());
+            // thin the separator: a column with no right neighbour joins the left side
+            ++seenid;
+            for (int64_t y : Rt) seen[y] = seenid;
+            for (int64_t x : lv[l]) {
+                bool right = false;
+                for (int64_t e = ap[x]; e < ap[x + 1] && !right; e++) right = seen[aj[e]] == seenid;
+                (right ? S : Lf).push_back(x);
+            }
             std::sort(S.begin(), S.end());
             std::sort(Lf.begin(), Lf.end());
             std::sort(Rt.begin(), Rt.end());
