@@ -164,7 +164,9 @@ const char* spaqr_last_error(void);
  * subdomains each separator column is adjacent to, and rows assigned by a
  * matching that puts large |a_ij| on the diagonal (greedy, then augmenting
  * paths; A->val may be NULL for a pattern-only matching).  SINGULAR if the
- * pattern has no perfect row matching.  Also builds the symbolic plan:
+ * pattern has no perfect row matching; UNSUPPORTED if the squared row
+ * lengths sum above 2^31 (G(A^T A) too large to form).  Also builds the
+ * symbolic plan:
  * per level the active clusters, the block pattern with fill, the fronts and
  * their processing order.  *out is owned by the caller
  * (spaqr_ordering_destroy). */

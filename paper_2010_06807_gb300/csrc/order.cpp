@@ -798,6 +798,20 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
     o.n = n;
     o.nnz = nnz;
     o.L = nlevels > 0 ? nlevels : num_levels(n);
+    // G(A^T A) holds up to sum_r nnz(row r)^2 entries: refuse patterns whose
+    // dense rows would make it exceed 2^31 (a partitioner working on A's
+    // hypergraph, Section 2.3, avoids forming it; not built here)
+    {
+        double pairs = 0.0;
+        for (int64_t r = 0; r < n; r++) {
+            const double k = (double)(rowptr[r + 1] - rowptr[r]);
+            pairs += k * k;
+        }
+        if (pairs > 2147483648.0) {
+            set_error("rows too dense for the G(A^T A) ordering (sum of squared row lengths above 2^31)");
+            return SPAQR_ERR_UNSUPPORTED;
+        }
+    }
     int rc = row_matching(rowptr, colind, val, n, o.rowcol);
     if (rc != SPAQR_OK) return rc;
     GeneralND g;

@@ -94,3 +94,13 @@ def test_general_ordering_rejects_singular_pattern(spaqr_lib):
     with pytest.raises(sq.SpaqrError) as e:
         sq.spaqr_order(rp, ci, None, 1)
     assert e.value.name == "SINGULAR"
+
+
+def test_general_ordering_rejects_dense_rows(spaqr_lib):
+    """Squared row lengths above 2^31: G(A^T A) is not formed (UNSUPPORTED)."""
+    n = 47000
+    rp = np.concatenate([[0, n], n + np.arange(1, n)]).astype(np.int64)
+    ci = np.concatenate([np.arange(n), np.arange(1, n)]).astype(np.int32)
+    with pytest.raises(sq.SpaqrError) as e:
+        sq.spaqr_order(rp, ci, None, 2)
+    assert e.value.name == "UNSUPPORTED"
