@@ -39,7 +39,7 @@ Readings where the paper is silent (each also listed in the design notes):
 import math
 import numpy as np
 
-__all__ = ["NDOrdering", "nd_order", "num_levels"]
+__all__ = ["NDOrdering", "nd_order", "num_levels", "hierarchical_atoms"]
 
 
 def num_levels(N):
@@ -118,6 +118,33 @@ class NDOrdering:
             out.append((a, b))
             a = b
         return out
+
+
+def hierarchical_atoms(gidx, keys):
+    """Atoms of one separator (reading R6): the finest classes of equal keys,
+    ordered hierarchically (for each stage depth, coarser classes first, each
+    class by the smallest index in it), points by index.  Returns a list of
+    (index array, key list)."""
+    gidx = np.asarray(gidx, dtype=np.int64)
+    depths = sorted(set(k[0] for kk in keys for k in kk))
+    sort_cols = []
+    for s in depths:
+        cls = [tuple(k for k in kk if k[0] <= s) for kk in keys]
+        minidx = {}
+        for i, cl in enumerate(cls):
+            if cl not in minidx or gidx[i] < minidx[cl]:
+                minidx[cl] = gidx[i]
+        sort_cols.append(np.array([minidx[cl] for cl in cls], dtype=np.int64))
+    order = np.lexsort(tuple([gidx] + sort_cols[::-1]))
+    atoms = []
+    cur = None
+    for i in order:
+        kk = tuple(keys[i])
+        if cur is None or kk != cur[1]:
+            cur = ([], kk)
+            atoms.append(cur)
+        cur[0].append(int(gidx[i]))
+    return [(np.array(a, dtype=np.int64), list(k)) for a, k in atoms]
 
 
 def nd_order(dims, L=None):
@@ -215,26 +242,7 @@ def nd_order(dims, L=None):
             kv = np.where(pts[:, cd] < D.cut_m, 0, np.where(pts[:, cd] < D.cut_m + 2, 1, 2))
             for i in np.nonzero(ok)[0]:
                 keys[i].append((D.depth, D.id, int(kv[i])))
-        # hierarchical sort key: for each stage depth, the min grid index of the class
-        depths = sorted(set(k[0] for kk in keys for k in kk))
-        sort_cols = []
-        for s in depths:
-            cls = [tuple(k for k in kk if k[0] <= s) for kk in keys]
-            minidx = {}
-            for i, cl in enumerate(cls):
-                if cl not in minidx or gidx[i] < minidx[cl]:
-                    minidx[cl] = gidx[i]
-            sort_cols.append(np.array([minidx[cl] for cl in cls], dtype=np.int64))
-        order = np.lexsort(tuple([gidx] + sort_cols[::-1]))
-        atoms = []
-        cur = None
-        for i in order:
-            kk = tuple(keys[i])
-            if cur is None or kk != cur[1]:
-                cur = ([], kk)
-                atoms.append(cur)
-            cur[0].append(gidx[i])
-        node_atoms[nd.id] = [(np.array(a, dtype=np.int64), list(k)) for a, k in atoms]
+        node_atoms[nd.id] = hierarchical_atoms(gidx, keys)
 
     order_nodes = sorted(nodes, key=lambda nd: (-nd.depth, nd.id))
     perm = []

@@ -50,7 +50,7 @@ import sys
 
 import numpy as np
 
-from .ordering import NDOrdering, num_levels
+from .ordering import NDOrdering, hierarchical_atoms, num_levels
 
 __all__ = ["nd_general", "row_matching", "column_graph"]
 
@@ -149,30 +149,6 @@ def row_matching(n, rowptr, colind, val=None):
     return rowcol
 
 
-def _atoms(gidx, keys):
-    """Hierarchical atom order of one separator (reading G4 / R6)."""
-    gidx = np.asarray(gidx, dtype=np.int64)
-    depths = sorted(set(k[0] for kk in keys for k in kk))
-    sort_cols = []
-    for s in depths:
-        cls = [tuple(k for k in kk if k[0] <= s) for kk in keys]
-        minidx = {}
-        for i, cl in enumerate(cls):
-            if cl not in minidx or gidx[i] < minidx[cl]:
-                minidx[cl] = gidx[i]
-        sort_cols.append(np.array([minidx[cl] for cl in cls], dtype=np.int64))
-    order = np.lexsort(tuple([gidx] + sort_cols[::-1]))
-    atoms = []
-    cur = None
-    for i in order:
-        kk = tuple(keys[i])
-        if cur is None or kk != cur[1]:
-            cur = ([], kk)
-            atoms.append(cur)
-        cur[0].append(int(gidx[i]))
-    return [(np.array(a, dtype=np.int64), list(k)) for a, k in atoms]
-
-
 def nd_general(n, rowptr, colind, val=None, L=None):
     """Modified nested dissection of a general matrix (readings G1-G5).
 
@@ -252,7 +228,7 @@ def nd_general(n, rowptr, colind, val=None, L=None):
                 a, b, c = marks[did]
                 kk.append((nodes[did].depth, did, 1 if (b or (a and c)) else (0 if a else 2)))
             keys.append(kk)
-        node_atoms[nd.id] = _atoms(nd.pts, keys)
+        node_atoms[nd.id] = hierarchical_atoms(nd.pts, keys)
 
     order_nodes = sorted(nodes, key=lambda nd: (-nd.depth, nd.id))
     perm, atom_ptr, atom_node, atom_keys = [], [0], [], []

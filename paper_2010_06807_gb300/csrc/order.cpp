@@ -121,6 +121,47 @@ struct Atom {
     std::vector<Key> key;
 };
 
+// Atoms of one separator in hierarchical order (coarser classes first, each
+// class by its smallest index), points by index.
+void order_atoms(const std::vector<int64_t>& gidx, const std::vector<std::vector<Key>>& keys,
+                 std::vector<Atom>& atoms) {
+    const size_t np = gidx.size();
+    std::vector<int> depths;
+    for (auto& kk : keys)
+        for (const Key& k : kk) depths.push_back(k.depth);
+    std::sort(depths.begin(), depths.end());
+    depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
+    std::vector<std::vector<int64_t>> scol(depths.size(), std::vector<int64_t>(np));
+    for (size_t si = 0; si < depths.size(); si++) {
+        const int s = depths[si];
+        std::map<std::vector<std::tuple<int, int, int>>, int64_t> minidx;
+        std::vector<std::vector<std::tuple<int, int, int>>> cls(np);
+        for (size_t i = 0; i < np; i++) {
+            for (const Key& kk : keys[i])
+                if (kk.depth <= s) cls[i].push_back(std::make_tuple(kk.depth, kk.node, kk.k));
+            auto it = minidx.find(cls[i]);
+            if (it == minidx.end() || gidx[i] < it->second) minidx[cls[i]] = gidx[i];
+        }
+        for (size_t i = 0; i < np; i++) scol[si][i] = minidx[cls[i]];
+    }
+    std::vector<size_t> ord(np);
+    for (size_t i = 0; i < np; i++) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+        for (size_t si = 0; si < depths.size(); si++)
+            if (scol[si][a] != scol[si][b]) return scol[si][a] < scol[si][b];
+        return gidx[a] < gidx[b];
+    });
+    for (size_t t = 0; t < np; t++) {
+        const size_t i = ord[t];
+        if (atoms.empty() || atoms.back().key != keys[i]) {
+            Atom a;
+            a.key = keys[i];
+            atoms.push_back(std::move(a));
+        }
+        atoms.back().pts.push_back(gidx[i]);
+    }
+}
+
 // Geometric nested dissection of one grid with L levels: the tree (depth 0 =
 // root) and the atoms of every node, their points as grid indices.
 int nd_grid(int dim, const int* dims3, int L, std::vector<NDNode>& nodes_out,
@@ -195,40 +236,7 @@ int nd_grid(int dim, const int* dims3, int L, std::vector<NDNode>& nodes_out,
                 keys[i].push_back(Key{D.depth, d, kv});
             }
         }
-        // hierarchical order: per stage depth, the smallest grid index of the class
-        std::vector<int> depths;
-        for (int d : cuts) depths.push_back(nodes[d].depth);
-        std::sort(depths.begin(), depths.end());
-        depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
-        std::vector<std::vector<int64_t>> scol(depths.size(), std::vector<int64_t>(np));
-        for (size_t si = 0; si < depths.size(); si++) {
-            int s = depths[si];
-            std::map<std::vector<std::tuple<int, int, int>>, int64_t> minidx;
-            std::vector<std::vector<std::tuple<int, int, int>>> cls(np);
-            for (size_t i = 0; i < np; i++) {
-                for (const Key& kk : keys[i])
-                    if (kk.depth <= s) cls[i].push_back(std::make_tuple(kk.depth, kk.node, kk.k));
-                auto it = minidx.find(cls[i]);
-                if (it == minidx.end() || gidx[i] < it->second) minidx[cls[i]] = gidx[i];
-            }
-            for (size_t i = 0; i < np; i++) scol[si][i] = minidx[cls[i]];
-        }
-        std::vector<size_t> ord(np);
-        for (size_t i = 0; i < np; i++) ord[i] = i;
-        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t bb) {
-            for (size_t si = 0; si < depths.size(); si++)
-                if (scol[si][a] != scol[si][bb]) return scol[si][a] < scol[si][bb];
-            return gidx[a] < gidx[bb];
-        });
-        for (size_t t = 0; t < np; t++) {
-            size_t i = ord[t];
-            if (node_atoms[id].empty() || node_atoms[id].back().key != keys[i]) {
-                Atom a;
-                a.key = keys[i];
-                node_atoms[id].push_back(std::move(a));
-            }
-            node_atoms[id].back().pts.push_back(gidx[i]);
-        }
+        order_atoms(gidx, keys, node_atoms[id]);
     }
 
     return SPAQR_OK;
@@ -653,47 +661,6 @@ struct GeneralND {
         return id;
     }
 };
-
-// Atoms of one separator in hierarchical order (coarser classes first, each
-// class by its smallest index), points by index.
-void order_atoms(const std::vector<int64_t>& gidx, const std::vector<std::vector<Key>>& keys,
-                 std::vector<Atom>& atoms) {
-    const size_t np = gidx.size();
-    std::vector<int> depths;
-    for (auto& kk : keys)
-        for (const Key& k : kk) depths.push_back(k.depth);
-    std::sort(depths.begin(), depths.end());
-    depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
-    std::vector<std::vector<int64_t>> scol(depths.size(), std::vector<int64_t>(np));
-    for (size_t si = 0; si < depths.size(); si++) {
-        const int s = depths[si];
-        std::map<std::vector<std::tuple<int, int, int>>, int64_t> minidx;
-        std::vector<std::vector<std::tuple<int, int, int>>> cls(np);
-        for (size_t i = 0; i < np; i++) {
-            for (const Key& kk : keys[i])
-                if (kk.depth <= s) cls[i].push_back(std::make_tuple(kk.depth, kk.node, kk.k));
-            auto it = minidx.find(cls[i]);
-            if (it == minidx.end() || gidx[i] < it->second) minidx[cls[i]] = gidx[i];
-        }
-        for (size_t i = 0; i < np; i++) scol[si][i] = minidx[cls[i]];
-    }
-    std::vector<size_t> ord(np);
-    for (size_t i = 0; i < np; i++) ord[i] = i;
-    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
-        for (size_t si = 0; si < depths.size(); si++)
-            if (scol[si][a] != scol[si][b]) return scol[si][a] < scol[si][b];
-        return gidx[a] < gidx[b];
-    });
-    for (size_t t = 0; t < np; t++) {
-        const size_t i = ord[t];
-        if (atoms.empty() || atoms.back().key != keys[i]) {
-            Atom a;
-            a.key = keys[i];
-            atoms.push_back(std::move(a));
-        }
-        atoms.back().pts.push_back(gidx[i]);
-    }
-}
 
 // rowcol[r] = the column row r is matched to; SINGULAR when no perfect
 // matching exists.

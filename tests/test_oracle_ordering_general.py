@@ -141,3 +141,13 @@ def test_general_factor_exact_and_gmres(name, p, L):
     F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-2, ordering=o, skip=1)
     x, it, rr, _ = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b[:, 0], lambda v: spaqr.solve(F, v))
     assert rr <= 1e-12
+
+
+def test_permuted_generator_is_PAQ():
+    g = config_problem("2d_uniform_a", n=9)
+    q = permuted(g, 17)
+    A = g.to_dense()
+    B = q.to_dense()
+    # row r of B is row prow[r] of A; column c of B is column pcol[c] of A
+    np.testing.assert_array_equal(B, A[np.ix_(q.prow, q.pcol)])
+    assert q.dims is None
