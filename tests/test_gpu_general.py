@@ -78,3 +78,22 @@ def test_general_gmres(dev, name, p, L):
         F2 = sq.spaqr_factor(o, *A, eps=1e-2, skip=2, **kw)
         _, it2, rr2 = sq.spaqr_gmres(F2, *A, torch.from_numpy(b).to(dev), tol=1e-12)
         assert rr2[0] <= 1e-12, kw
+
+
+@pytest.mark.parametrize("name,p,L", _problems()[:3])
+def test_general_unscaled_matches_oracle(dev, name, p, L):
+    """The unscaled variant on a general matrix: ranks, sigma_p and one
+    application against the oracle."""
+    o, F, _ = _gpu(p, dev, 1e-3, L, 1, scaling=0)
+    og = nd_general(p.n, p.rowptr, p.colind, p.val, o.L)
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-3, nlevels=o.L, skip=1, ordering=og, scaling=False)
+    for lev, R in enumerate(Fo.ranks):
+        items = [(c, v) for c, v in sorted(R.items()) if v[0] > 0]
+        assert [tuple(x) for x in sq.spaqr_factor_ranks(F, lev)[0].tolist()] == [tuple(v) for _, v in items], lev
+        if items:
+            np.testing.assert_allclose(sq.spaqr_factor_sigmas(F, lev), [Fo.lemma[lev][c]["sigma"] for c, _ in items],
+                                       rtol=TOL, atol=0)
+    b = np.random.default_rng(6).standard_normal((p.n, 2))
+    xo = osq.solve(Fo, b)
+    xg = sq.spaqr_solve(F, _colmajor(b, dev)).cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL
