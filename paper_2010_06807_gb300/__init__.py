@@ -8,6 +8,19 @@ torch tensors (host or CUDA).  Dense right-hand sides are column-major
 
 The library is loaded on first use; if it is missing this raises, there is no
 fallback.
+
+Typical use::
+
+    o = spaqr_order(rowptr, colind, (nx, ny))         # grid: geometric ordering
+    o = spaqr_order(rowptr, colind, None, val=val)    # general matrix: G(A^T A) ordering, matched rows
+    F = spaqr_factor(o, rowptr, colind, val, eps=1e-2)          # scaled, FP64
+    F = spaqr_factor(o, rowptr, colind, val, eps=1e-2, scaling=0, precision="fp32")
+    X, iters, relres = spaqr_gmres(F, rowptr, colind, val, B, tol=1e-12)
+
+Diagnostics per level: spaqr_factor_level, spaqr_factor_pivots,
+spaqr_factor_ranks, spaqr_factor_sigmas (and the diagnostics module);
+batches of independent grids: spaqr_order_batch + blockdiag_csr +
+spaqr_gmres_batch; serving: the serve module.
 """
 import ctypes
 import os
