@@ -104,3 +104,37 @@ def test_general_ordering_rejects_dense_rows(spaqr_lib):
     with pytest.raises(sq.SpaqrError) as e:
         sq.spaqr_order(rp, ci, None, 2)
     assert e.value.name == "UNSUPPORTED"
+
+
+def _disconnected():
+    from synth.convdiff import permuted, random_local
+    a, b = permuted(config_problem("2d_uniform_a", n=7), 51), random_local(6, seed=7031)
+    rp, ci, v = sq.blockdiag_csr([(a.rowptr, a.colind, a.val), (b.rowptr, b.colind, b.val)])
+    from synth.convdiff import Problem
+    return Problem(None, rp, ci.astype(np.int32), v, name="disconnected")
+
+
+@pytest.mark.parametrize("case", ["disconnected", "many_levels", "tiny"])
+def test_general_ordering_edge_cases(spaqr_lib, case):
+    """Disconnected patterns (components in order of their smallest column),
+    more levels than the columns can fill (empty subtrees) and a 1 x 1 matrix:
+    the host ordering still equals the oracle's, and the oracle's factor with
+    eps = 0 solves exactly."""
+    from oracle.ordering_general import nd_general
+    from synth.convdiff import Problem, permuted
+    if case == "disconnected":
+        p, L = _disconnected(), 4
+    elif case == "many_levels":
+        p, L = permuted(config_problem("2d_uniform_a", n=5), 52), 6
+    else:
+        p, L = Problem(None, np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32),
+                       np.array([2.0])), 1
+    ordl = sq.spaqr_order(p.rowptr, p.colind, None, L, val=p.val)
+    arr = ordl.arrays()
+    o = nd_general(p.n, p.rowptr, p.colind, p.val, L)
+    for k in ("perm", "atom_ptr", "atom_node", "node_level", "rperm"):
+        np.testing.assert_array_equal(arr[k], getattr(o, k), err_msg=k)
+    F = osq.factor(p.n, p.rowptr, p.colind, p.val, None, 0.0, nlevels=o.L, skip=0, ordering=o)
+    b = np.random.default_rng(2).standard_normal(p.n)
+    x = osq.solve(F, b)
+    assert np.linalg.norm(b - p.matvec(x)) <= 1e-12 * np.linalg.norm(b)
