@@ -95,11 +95,14 @@ def _greedy_colours(fronts, rows_of):
 
 
 def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
-           col_normalize=True, scaling=True):
+           col_normalize=True, scaling=True, sequential=False):
     """Compute the spaQR factorisation (Algorithm 2) of the CSR matrix A.
 
     scaling=False gives the unscaled variant of Sections 2.2 / 3.2 (reading
-    F7).  Returns a Factor with the op sequence and diagnostics (ranks per
+    F7).  sequential=True (scaled variant) sparsifies the interfaces of a
+    level one after the other, as the loop of Algorithm 2 is written: each
+    CPQR sees the matrix already transformed by the interfaces before it
+    (ascending id), instead of the two-phase reading F4.  Returns a Factor with the op sequence and diagnostics (ranks per
     level, CPQR pivot norms, algorithmic flop counts; for the unscaled
     variant also sigma_p and the Lemma 1 quantities per interface).
     """
@@ -239,6 +242,9 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
                 col_rows[j].append(i)
                 row_cols[i].append(j)
             Qs = {}
+            if sequential:
+                blocks = _sparsify_sequential(F, k, eps, blocks, act, size, ops, flops)
+                act = []
             for p in act:
                 if size[p] == 0:
                     continue
@@ -255,8 +261,8 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
                 F.dropped[-1][p] = (float(np.linalg.norm(QtM[r:])), Mp.shape[1],
                                     float(rd[0]) if len(rd) else 0.0)
                 ops.append(("sparsify", k, p, Vq, tq, r, size[p]))
-            newb = {}
-            for (i, j), B in blocks.items():
+            newb = {} if not sequential else dict(blocks)
+            for (i, j), B in (blocks.items() if not sequential else []):
                 if i == j:
                     ri = Qs[i][2] if i in Qs else 0
                     newb[(i, j)] = np.eye(ri)
@@ -310,6 +316,38 @@ def factor(n, rowptr, colind, val, dims, eps, nlevels=0, skip=2, ordering=None,
     F.ops = ops
     F.flops = dict(flops)
     return F
+
+
+def _sparsify_sequential(F, k, eps, blocks, act, size, ops, flops):
+    """Scaled sparsification of one level, interface after interface in
+    ascending id (Algorithm 2's loop taken literally): M_p is built from the
+    current blocks, and Q_p is applied at once -- rows p <- Q_p^T, columns
+    p <- Q_p, fine rows / columns dropped, A_pp <- I_r."""
+    for p in act:
+        if size[p] == 0:
+            continue
+        rows_of_p = sorted(i for (i, j) in blocks if j == p and i != p)
+        cols_of_p = sorted(j for (i, j) in blocks if i == p and j != p)
+        parts = [blocks[(i, p)].T for i in rows_of_p] + [blocks[(p, j)] for j in cols_of_p]
+        Mp = np.hstack(parts) if parts else np.zeros((size[p], 0))
+        Vq, tq, r, rd, _ = dense.cpqr_truncated(Mp, eps)
+        flops["sparsify"] += 4.0 * size[p] * Mp.shape[1] * r
+        F.ranks[-1][p] = (size[p], r)
+        F.rdiag[-1][p] = rd
+        QtM = dense.apply_qt(Vq, tq, Mp) if r > 0 else Mp
+        F.dropped[-1][p] = (float(np.linalg.norm(QtM[r:])), Mp.shape[1], float(rd[0]) if len(rd) else 0.0)
+        ops.append(("sparsify", k, p, Vq, tq, r, size[p]))
+        for j in cols_of_p:
+            B = dense.apply_qt(Vq, tq, blocks[(p, j)]) if r > 0 and blocks[(p, j)].shape[1] > 0 else blocks[(p, j)]
+            blocks[(p, j)] = B[:r].copy()
+        for i in rows_of_p:
+            B = blocks[(i, p)]
+            if r > 0 and B.shape[0] > 0:
+                B = dense.apply_qt(Vq, tq, B.T).T
+            blocks[(i, p)] = B[:, :r].copy()
+        blocks[(p, p)] = np.eye(r)
+        size[p] = r
+    return blocks
 
 
 def _sparsify_unscaled(F, k, eps, blocks, active, size, ops, flops):

@@ -140,3 +140,23 @@ def test_singleton_and_tiny_grids():
     b = rhs(p, 2)
     x = spaqr.solve(F, b)
     assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) < 1e-12
+
+
+@pytest.mark.parametrize("kind,n,eps", [("2d_uniform_a", 32, 1e-2), ("2d_lognormal", 48, 1e-1), ("3d_uniform_a", 10, 1e-2)])
+def test_sequential_sparsification_close_to_two_phase(kind, n, eps):
+    """Algorithm 2's loop taken literally (each interface's CPQR sees the
+    earlier interfaces' transformations) against the two-phase reading F4:
+    eps = 0 stays exact, and the GMRES iterations and total ranks are close."""
+    p = _prob(kind, n)
+    b = rhs(p, 1)[:, 0]
+    F0 = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 0.0, skip=0, sequential=True)
+    x = spaqr.solve(F0, b)
+    assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) < 1e-12
+    out = []
+    for seq in (False, True):
+        F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, eps, skip=1, sequential=seq)
+        _, it, rr, _ = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: spaqr.solve(F, v))
+        assert rr <= 1e-12
+        out.append((it, sum(r for lev in F.ranks for (_, r) in lev.values())))
+    assert abs(out[0][0] - out[1][0]) <= 3
+    assert abs(out[0][1] - out[1][1]) <= 0.05 * out[0][1]
