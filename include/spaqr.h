@@ -354,6 +354,13 @@ int spaqr_factor_tuning(const spaqr_factor_t* F, int nrhs, int32_t* forms, int c
  * launches the kernels directly on the caller's stream. */
 void spaqr_use_graphs(int on);
 
+/* Testing aid (host-side fault injection; the paper has no counterpart):
+ * after `after` more successful device allocations of the library, the next
+ * one reports failure exactly as a failed cudaMallocAsync would, once; the
+ * call then returns SPAQR_ERR_OOM after releasing what it allocated.
+ * after < 0 switches the injection off.  Process wide. */
+void spaqr_test_fail_alloc(int64_t after);
+
 /* Kernel launch statistics (process wide).  The paper reports the runtime of
  * every level split into factorize / scale / sparsify / merge (Section 4,
  * "runtime per level" figure); these counters refine that split per kernel.

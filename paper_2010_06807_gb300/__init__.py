@@ -34,7 +34,7 @@ __all__ = [
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level",
     "spaqr_factor_pivots", "Ordering", "Factor", "num_levels",
     "spaqr_stats_reset", "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune",
-    "spaqr_factor_tuning",
+    "spaqr_factor_tuning", "spaqr_test_fail_alloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,6 +109,7 @@ EXPORTS = [
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
+    "spaqr_test_fail_alloc",
 ]
 
 
@@ -154,6 +155,8 @@ def load_library(path=None):
         lib.spaqr_profile.argtypes = [i32]
         lib.spaqr_profile.restype = None
         lib.spaqr_use_graphs.argtypes = [i32]
+        lib.spaqr_test_fail_alloc.argtypes = [i64]
+        lib.spaqr_test_fail_alloc.restype = None
         lib.spaqr_use_graphs.restype = None
         lib.spaqr_autotune.argtypes = [vp, i32, vp, vp, vp]
         lib.spaqr_factor_tuning.argtypes = [vp, i32, vp, i32, ctypes.POINTER(ctypes.c_int)]
@@ -563,6 +566,13 @@ def spaqr_factor_sigmas(F, level):
     out = np.zeros(max(n, 1), dtype=np.float64)
     _check(_lib.spaqr_factor_sigmas(F._h, int(level), out.ctypes.data, n, ctypes.byref(cnt)))
     return out[:n]
+
+
+def spaqr_test_fail_alloc(after):
+    """Fault injection: the device allocation after `after` more successful
+    ones fails (once); -1 switches it off."""
+    load_library()
+    _lib.spaqr_test_fail_alloc(int(after))
 
 
 def spaqr_stats_reset():

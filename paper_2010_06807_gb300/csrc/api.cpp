@@ -249,6 +249,16 @@ bool prof_on() {
 std::atomic<bool> g_graphs{true};
 bool graphs_on() { return g_graphs.load(); }
 
+// Host-side fault injection: the allocation that finds the countdown at 0
+// reports failure (as a failed cudaMallocAsync would), once; -1 = off.
+std::atomic<int64_t> g_fail_alloc{-1};
+bool fail_this_alloc() {
+    int64_t v = g_fail_alloc.load();
+    while (v >= 0)
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
 void prof_add(int rec, int kind, double flops, double bytes) {
     (void)rec;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -271,6 +281,8 @@ extern "C" void spaqr_stats_reset(void) {
 }
 
 extern "C" void spaqr_use_graphs(int on) { spaqr::g_graphs.store(on != 0); }
+
+extern "C" void spaqr_test_fail_alloc(int64_t after) { spaqr::g_fail_alloc.store(after < 0 ? -1 : after); }
 
 extern "C" void spaqr_profile(int on) {
     std::lock_guard<std::mutex> lk(spaqr::g_mu);

@@ -783,7 +783,7 @@ struct Ctx {
         void* p = nullptr;
         size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
         bytes = (bytes + 255) & ~(size_t)255;
-        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        if (fail_this_alloc() || cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
             rc = SPAQR_ERR_OOM;

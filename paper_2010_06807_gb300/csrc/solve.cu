@@ -878,7 +878,7 @@ struct SCtx {
         if (rc != SPAQR_OK) return nullptr;
         void* p = nullptr;
         size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        if (fail_this_alloc() || cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
             cudaGetLastError();
             set_error("device allocation failed");
             rc = SPAQR_ERR_OOM;

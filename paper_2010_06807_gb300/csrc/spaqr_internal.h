@@ -110,6 +110,7 @@ void prof_add_tally(const LaunchTally& t, int sign);
 bool prof_on();
 void keep_pool_memory(int device);
 bool graphs_on();
+bool fail_this_alloc();   // fault injection (spaqr_test_fail_alloc)
 
 }  // namespace spaqr
 
