@@ -135,3 +135,26 @@ def test_unscaled_gmres_converges_and_iterations_fall():
         assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) <= 1e-12
         its.append(it)
     assert its[1] < its[0]
+
+
+def test_fine_column_sign_rule_is_benign(monkeypatch):
+    """Reading F8 only fixes which of two valid reflectors the fine-column QR
+    takes when its leading entry is zero up to rounding.  With the plain
+    LAPACK sign instead the factor is another valid one: GMRES converges with
+    the same iteration count within one, and eps = 0 stays exact."""
+    from oracle import dense
+    p = config_problem("2d_uniform_a", n=16)
+    b = rhs(p, 1)[:, 0]
+    its = []
+    orig = dense.qr
+    for strict in (False, True):
+        if strict:
+            monkeypatch.setattr(dense, "qr", lambda A, sign_tol=0.0: orig(A, 0.0))
+        F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-3, nlevels=4, skip=0, scaling=False)
+        _, it, rr, _ = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: spaqr.solve(F, v))
+        assert rr <= 1e-12
+        its.append(it)
+        F0 = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 0.0, nlevels=4, skip=0, scaling=False)
+        x = spaqr.solve(F0, b)
+        assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) < 1e-12
+    assert abs(its[0] - its[1]) <= 1, its
