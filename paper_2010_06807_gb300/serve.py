@@ -75,6 +75,12 @@ class Request:
         return None if self.t_done is None else self.t_done - self.t_submit
 
 
+def _dim_key(problem):
+    """Memory estimates are kept per grid dimension; general matrices (no
+    grid) have their own key, 0."""
+    return len(problem.dims) if problem.dims is not None else 0
+
+
 class DeviceOps:
     """libspaqr + torch streams on one CUDA device: what the server runs."""
 
@@ -102,9 +108,12 @@ class DeviceOps:
             csr = (torch.from_numpy(problem.rowptr).to(self.device),
                    torch.from_numpy(problem.colind).to(self.device),
                    torch.from_numpy(problem.val).to(self.device))
-            ordering = spaqr_order(problem.rowptr, problem.colind, problem.dims)
+            # grids: geometric ordering; general matrices (dims None): the
+            # G(A^T A) ordering with rows matched by |a_ij|
+            ordering = spaqr_order(problem.rowptr, problem.colind, problem.dims,
+                                   val=problem.val if problem.dims is None else None)
             F = spaqr_factor(ordering, *csr, eps=self.eps, precision=self.precision, stream=stream)
-        return {"F": F, "csr": csr, "ordering": ordering, "n": problem.n, "dim": len(problem.dims)}
+        return {"F": F, "csr": csr, "ordering": ordering, "n": problem.n, "dim": _dim_key(problem)}
 
     def factor_bytes(self, h):
         from . import spaqr_factor_info
@@ -125,7 +134,7 @@ class DeviceOps:
         # temporaries) seen for factors of the same grid dimension, with a
         # quarter again for larger grids; 16 KB per unknown before any factor
         # of that dimension exists
-        per = self._per_unknown.get(len(problem.dims))
+        per = self._per_unknown.get(_dim_key(problem))
         return int(1.25 * per * problem.n) if per else 16384 * problem.n
 
     def solve(self, h, Bh, stream):

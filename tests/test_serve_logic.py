@@ -179,3 +179,23 @@ def test_bad_requests():
     srv.close()
     with pytest.raises(RuntimeError):
         srv.submit_factor(3, _prob(3, 10))
+
+
+def test_device_ops_memory_estimates(monkeypatch, spaqr_lib):
+    """DeviceOps keeps the largest peak bytes per unknown of each grid
+    dimension (general matrices under their own key) and estimates a new
+    factor from it; resident bytes are the factor's own."""
+    import paper_2010_06807_gb300 as sq
+    from paper_2010_06807_gb300.serve import DeviceOps
+    infos = iter([{"factor_bytes": 1000, "peak_bytes": 4000}, {"factor_bytes": 50, "peak_bytes": 90}])
+    monkeypatch.setattr(sq, "spaqr_factor_info", lambda F: next(infos))
+    ops = DeviceOps("cuda:0")
+    p3 = _P(100, dims=(5, 5, 4))
+    assert ops.estimate_factor_bytes(p3) == 16384 * 100       # nothing seen yet
+    assert ops.factor_bytes({"F": None, "n": 100, "dim": 3}) == 1000
+    assert ops.estimate_factor_bytes(_P(200, dims=(5, 5, 8))) == int(1.25 * 40 * 200)
+    g = _P(10, dims=None)
+    g.dims = None
+    assert ops.estimate_factor_bytes(g) == 16384 * 10          # general matrices: own key
+    assert ops.factor_bytes({"F": None, "n": 10, "dim": 0}) == 50
+    assert ops.estimate_factor_bytes(g) == int(1.25 * 9 * 10)
