@@ -309,7 +309,13 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
     // a row sits at the position of its matched column (rows = columns when
     // there is no matching)
     auto rowpos = [&](int64_t r) { return o.rowcol.empty() ? o.iperm[r] : o.iperm[o.rowcol[r]]; };
-    std::set<std::pair<int, int>> P;  // (row cluster, col cluster) by first atom
+    // block pattern: (row cluster, col cluster) by first atom, kept sorted and
+    // unique (row, then column)
+    std::vector<std::pair<int, int>> P;
+    auto normalise = [](std::vector<std::pair<int, int>>& v) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    };
     for (int64_t r = 0; r < n; r++) {
         int ar = o.atom_of[rowpos(r)];
         for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++) {
@@ -318,9 +324,10 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
                 set_error("matrix pattern couples separated subdomains (not a 5/7-point stencil on this grid?)");
                 return SPAQR_ERR_UNSUPPORTED;
             }
-            P.insert({ar, ac});
+            P.push_back({ar, ac});
         }
     }
+    normalise(P);
     std::vector<int> active(na);
     std::vector<int> cnode(na), cend(na);
     for (int a = 0; a < na; a++) { active[a] = a; cnode[a] = o.atom_node[a]; cend[a] = a + 1; }
@@ -370,19 +377,19 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             }
         }
         // greedy colouring in ascending id: conflict = a shared row cluster
+        // (the earlier fronts of every row cluster are listed as we go)
         std::vector<int> col(fr.size(), 0);
-        for (size_t t = 0; t < fr.size(); t++) {
-            std::set<int> used;
-            std::vector<char> mine(ncl, 0);
-            for (int i : Rf[t]) mine[i] = 1;
-            for (size_t u = 0; u < t; u++) {
-                bool share = false;
-                for (int i : Rf[u]) if (mine[i]) { share = true; break; }
-                if (share) used.insert(col[u]);
+        {
+            std::vector<std::vector<int>> fronts_of_row(ncl);
+            for (size_t t = 0; t < fr.size(); t++) {
+                std::set<int> used;
+                for (int i : Rf[t])
+                    for (int u : fronts_of_row[i]) used.insert(col[u]);
+                int c = 0;
+                while (used.count(c)) c++;
+                col[t] = c;
+                for (int i : Rf[t]) fronts_of_row[i].push_back((int)t);
             }
-            int c = 0;
-            while (used.count(c)) c++;
-            col[t] = c;
         }
         std::vector<size_t> seq(fr.size());
         for (size_t t = 0; t < fr.size(); t++) seq[t] = t;
@@ -399,7 +406,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         // fill of this level
         for (size_t t = 0; t < fr.size(); t++)
             for (int i : Rf[t])
-                for (int j : Cf[t]) P.insert({active[i], active[j]});
+                for (int j : Cf[t]) P.push_back({active[i], active[j]});
+        normalise(P);
         // CSC of the pattern with fill
         sp.colptr.assign(ncl + 1, 0);
         for (auto& pr : P) sp.colptr[idx.at(pr.second) + 1]++;
@@ -424,10 +432,11 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             for (int j : sp.C[t]) o.plan_code.push_back(active[j]);
         }
         // eliminate the fronts
-        for (auto it = P.begin(); it != P.end();) {
-            if (sp.is_front[idx.at(it->first)] || sp.is_front[idx.at(it->second)]) it = P.erase(it);
-            else ++it;
-        }
+        P.erase(std::remove_if(P.begin(), P.end(),
+                               [&](const std::pair<int, int>& pr) {
+                                   return sp.is_front[idx.at(pr.first)] || sp.is_front[idx.at(pr.second)];
+                               }),
+                P.end());
         std::vector<int> rest;
         for (int i = 0; i < ncl; i++) if (!sp.is_front[i]) rest.push_back(active[i]);
         sp.parent.assign(ncl, -1);
@@ -448,9 +457,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             for (int i = 0; i < ncl; i++)
                 if (!sp.is_front[i]) sp.parent[i] = nidx.at(f[active[i]]);
             sp.n_next = (int)nxt.size();
-            std::set<std::pair<int, int>> P2;
-            for (auto& pr : P) P2.insert({f[pr.first], f[pr.second]});
-            P.swap(P2);
+            for (auto& pr : P) pr = {f[pr.first], f[pr.second]};
+            normalise(P);
             for (int g : nxt) {
                 cnode[g] = o.atom_node[g];
                 cend[g] = newid[g];
@@ -519,15 +527,32 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
 //    then every unmatched row (ascending) by an augmenting path (columns of a
 //    row in ascending order, depth first); row r sits with its column.
 // ---------------------------------------------------------------------------
+// G(A^T A) restricted to a column set: local vertices in ascending global
+// order, each with its neighbours inside the set (ascending).  Because the
+// local order is the global one, searches and tie-breaks on a subgraph give
+// what they give on the whole graph restricted to the set, with the set's
+// own compact arrays in cache.
+struct SubGraph {
+    std::vector<int64_t> gid;   // global column of every local vertex
+    std::vector<int64_t> xp;    // local CSR
+    std::vector<int32_t> adj;
+    int64_t size() const { return (int64_t)gid.size(); }
+    int64_t degree(int64_t v) const { return xp[v + 1] - xp[v]; }
+};
+
 struct GeneralND {
     int64_t n = 0;
     int L = 1;
-    std::vector<int64_t> ap, aj;         // G(A^T A), neighbours sorted
-    std::vector<int32_t> inset, seen, done;
-    int32_t setid = 0, seenid = 0, doneid = 0;
+    SubGraph root;                      // the whole G(A^T A); kept for the interfaces
     std::vector<NDNode> nodes;
     std::vector<std::vector<int64_t>> pts;
-    using Levels = std::vector<std::vector<int64_t>>;
+    // breadth-first levels: vertices in visiting order, level l holding
+    // ord[lptr[l] .. lptr[l+1])
+    struct Levels {
+        std::vector<int32_t> ord;
+        std::vector<int64_t> lptr;
+        size_t count() const { return lptr.empty() ? 0 : lptr.size() - 1; }
+    };
 
     void graph(const int64_t* rp, const int32_t* ci) {
         std::vector<int64_t> cp(n + 1, 0), ri(rp[n]);
@@ -539,16 +564,18 @@ struct GeneralND {
                 for (int64_t e = rp[r]; e < rp[r + 1]; e++) ri[f[ci[e]]++] = r;
         }
         std::vector<int32_t> mark(n, -1);
-        ap.assign(n + 1, 0);
-        aj.clear();
-        std::vector<int64_t> tmp;
+        root.gid.resize(n);
+        root.xp.assign(n + 1, 0);
+        root.adj.clear();
+        std::vector<int32_t> tmp;
         for (int64_t j = 0; j < n; j++) {
+            root.gid[j] = j;
             tmp.clear();
             mark[j] = (int32_t)j;
             for (int64_t e = cp[j]; e < cp[j + 1]; e++) {
                 const int64_t r = ri[e];
                 for (int64_t f = rp[r]; f < rp[r + 1]; f++) {
-                    const int64_t c = ci[f];
+                    const int32_t c = ci[f];
                     if (mark[c] != (int32_t)j) {
                         mark[c] = (int32_t)j;
                         tmp.push_back(c);
@@ -556,68 +583,84 @@ struct GeneralND {
                 }
             }
             std::sort(tmp.begin(), tmp.end());
-            aj.insert(aj.end(), tmp.begin(), tmp.end());
-            ap[j + 1] = (int64_t)aj.size();
+            root.adj.insert(root.adj.end(), tmp.begin(), tmp.end());
+            root.xp[j + 1] = (int64_t)root.adj.size();
         }
-        inset.assign(n, 0);
-        seen.assign(n, 0);
-        done.assign(n, 0);
     }
-    int degree_in(int64_t v) const {
-        int d = 0;
-        for (int64_t e = ap[v]; e < ap[v + 1]; e++) d += inset[aj[e]] == setid;
-        return d;
-    }
-    void bfs(int64_t root, Levels& lv) {
-        ++seenid;
-        lv.assign(1, std::vector<int64_t>(1, root));
-        seen[root] = seenid;
-        while (true) {
-            std::vector<int64_t> nxt;
-            for (int64_t x : lv.back())
-                for (int64_t e = ap[x]; e < ap[x + 1]; e++) {
-                    const int64_t y = aj[e];
-                    if (inset[y] == setid && seen[y] != seenid) {
-                        seen[y] = seenid;
-                        nxt.push_back(y);
+    // levels of the component of `r` (stamp: seen[v] == id marks a visit)
+    static void bfs(const SubGraph& G, int32_t r, std::vector<int32_t>& seen, int32_t id, Levels& lv) {
+        lv.ord.assign(1, r);
+        lv.lptr.assign(1, 0);
+        seen[r] = id;
+        int64_t b = 0;
+        while (b < (int64_t)lv.ord.size()) {
+            const int64_t e0 = (int64_t)lv.ord.size();
+            lv.lptr.push_back(e0);
+            for (int64_t i = b; i < e0; i++) {
+                const int32_t x = lv.ord[i];
+                for (int64_t e = G.xp[x]; e < G.xp[x + 1]; e++) {
+                    const int32_t y = G.adj[e];
+                    if (seen[y] != id) {
+                        seen[y] = id;
+                        lv.ord.push_back(y);
                     }
                 }
-            if (nxt.empty()) return;
-            std::sort(nxt.begin(), nxt.end());
-            lv.push_back(std::move(nxt));
+            }
+            b = e0;
         }
     }
-    void pseudo_peripheral(int64_t s, Levels& lv) {
-        bfs(s, lv);
-        while (true) {
-            int64_t cand = -1;
-            int bd = 0;
-            for (int64_t v : lv.back()) {
-                const int d = degree_in(v);
-                if (cand < 0 || d < bd || (d == bd && v < cand)) { bd = d; cand = v; }
+    // all levels of G, component by component (smallest vertex first), each
+    // component searched from a pseudo-peripheral vertex
+    static Levels level_structure(const SubGraph& G) {
+        const int64_t m = G.size();
+        std::vector<int32_t> seen(m, 0);
+        std::vector<char> done(m, 0);
+        int32_t id = 0;
+        Levels all, lv, lv2;
+        all.lptr.assign(1, 0);
+        for (int64_t s = 0; s < m; s++) {
+            if (done[s]) continue;
+            bfs(G, (int32_t)s, seen, ++id, lv);
+            while (true) {
+                int32_t cand = -1;
+                int64_t bd = 0;
+                for (int64_t i = lv.lptr[lv.count() - 1]; i < lv.lptr[lv.count()]; i++) {
+                    const int32_t v = lv.ord[i];
+                    const int64_t d = G.degree(v);
+                    if (cand < 0 || d < bd || (d == bd && v < cand)) { bd = d; cand = v; }
+                }
+                bfs(G, cand, seen, ++id, lv2);
+                if (lv2.count() <= lv.count()) break;
+                std::swap(lv, lv2);
             }
-            Levels lv2;
-            bfs(cand, lv2);
-            if (lv2.size() <= lv.size()) return;
-            lv.swap(lv2);
-        }
-    }
-    Levels level_structure(const std::vector<int64_t>& V) {
-        ++setid;
-        for (int64_t v : V) inset[v] = setid;
-        ++doneid;
-        Levels all, lv;
-        for (int64_t s : V) {
-            if (done[s] == doneid) continue;
-            pseudo_peripheral(s, lv);
-            for (auto& level : lv) {
-                for (int64_t v : level) done[v] = doneid;
-                all.push_back(level);
-            }
+            const int64_t base = (int64_t)all.ord.size();
+            for (int32_t v : lv.ord) done[v] = 1;
+            all.ord.insert(all.ord.end(), lv.ord.begin(), lv.ord.end());
+            for (size_t l = 1; l <= lv.count(); l++) all.lptr.push_back(base + lv.lptr[l]);
         }
         return all;
     }
-    int build(const std::vector<int64_t>& V, int depth, int parent) {
+    // subgraph of G on the ascending local vertices `keep`
+    static SubGraph induce(const SubGraph& G, const std::vector<int32_t>& keep, std::vector<int32_t>& loc) {
+        SubGraph H;
+        const int64_t k = (int64_t)keep.size();
+        for (int64_t i = 0; i < k; i++) loc[keep[i]] = (int32_t)i;
+        H.gid.resize(k);
+        H.xp.assign(k + 1, 0);
+        for (int64_t i = 0; i < k; i++) {
+            const int32_t x = keep[i];
+            H.gid[i] = G.gid[x];
+            for (int64_t e = G.xp[x]; e < G.xp[x + 1]; e++) {
+                const int32_t y = loc[G.adj[e]];
+                if (y >= 0) H.adj.push_back(y);
+            }
+            H.xp[i + 1] = (int64_t)H.adj.size();
+        }
+        for (int32_t x : keep) loc[x] = -1;
+        return H;
+    }
+    // node of column set G (released on return unless it is the root)
+    int build(SubGraph& G, int depth, int parent) {
         const int id = (int)nodes.size();
         nodes.push_back(NDNode());
         pts.emplace_back();
@@ -625,39 +668,48 @@ struct GeneralND {
         nodes[id].depth = depth;
         nodes[id].parent = parent;
         if (depth == L - 1) {
-            pts[id] = V;
+            pts[id] = G.gid;
+            if (&G != &root) G = SubGraph();
             return id;
         }
-        std::vector<int64_t> S, Lf, Rt;
-        if (!V.empty()) {
-            Levels lv = level_structure(V);
+        const int64_t m = G.size();
+        std::vector<int32_t> S, Lf, Rt;
+        if (m > 0) {
+            Levels lv = level_structure(G);
             size_t l = 0;
             int64_t cum = 0;
-            for (; l < lv.size(); l++) {
-                cum += (int64_t)lv[l].size();
-                if (2 * cum >= (int64_t)V.size()) break;
+            for (; l < lv.count(); l++) {
+                cum += lv.lptr[l + 1] - lv.lptr[l];
+                if (2 * cum >= m) break;
             }
-            for (size_t i = 0; i < l; i++) Lf.insert(Lf.end(), lv[i].begin(), lv[i].end());
-            for (size_t i = l + 1; i < lv.size(); i++) Rt.insert(Rt.end(), lv[i].begin(), lv[i].end());
+            Lf.assign(lv.ord.begin(), lv.ord.begin() + lv.lptr[l]);
+            Rt.assign(lv.ord.begin() + lv.lptr[l + 1], lv.ord.end());
             // thin the separator: a column with no right neighbour joins the left side
-            ++seenid;
-            for (int64_t y : Rt) seen[y] = seenid;
-            for (int64_t x : lv[l]) {
-                bool right = false;
-                for (int64_t e = ap[x]; e < ap[x + 1] && !right; e++) right = seen[aj[e]] == seenid;
-                (right ? S : Lf).push_back(x);
+            std::vector<char> right(m, 0);
+            for (int32_t y : Rt) right[y] = 1;
+            for (int64_t i = lv.lptr[l]; i < lv.lptr[l + 1]; i++) {
+                const int32_t x = lv.ord[i];
+                bool r = false;
+                for (int64_t e = G.xp[x]; e < G.xp[x + 1] && !r; e++) r = right[G.adj[e]];
+                (r ? S : Lf).push_back(x);
             }
             std::sort(S.begin(), S.end());
             std::sort(Lf.begin(), Lf.end());
             std::sort(Rt.begin(), Rt.end());
         }
-        const int left = build(Lf, depth + 1, id);
-        const int right = build(Rt, depth + 1, id);
+        std::vector<int32_t> loc(m, -1);
+        SubGraph GL = induce(G, Lf, loc), GR = induce(G, Rt, loc);
+        std::vector<int64_t> sep(S.size());
+        for (size_t i = 0; i < S.size(); i++) sep[i] = G.gid[S[i]];
+        if (&G != &root) G = SubGraph();
+        { std::vector<int32_t>().swap(loc); std::vector<int32_t>().swap(Lf); std::vector<int32_t>().swap(Rt); }
+        const int left = build(GL, depth + 1, id);
+        const int right = build(GR, depth + 1, id);
         nodes[id].left = left;
         nodes[id].right = right;
         nodes[id].cut_dim = 0;
         nodes[id].size = 1 + nodes[left].size + nodes[right].size;
-        pts[id] = std::move(S);
+        pts[id] = std::move(sep);
         return id;
     }
 };
@@ -785,9 +837,7 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
     g.n = n;
     g.L = o.L;
     g.graph(rowptr, colind);
-    std::vector<int64_t> all(n);
-    for (int64_t i = 0; i < n; i++) all[i] = i;
-    g.build(all, 0, -1);
+    g.build(g.root, 0, -1);
     const int nn = (int)g.nodes.size();
     std::vector<int> owner(n, -1);
     for (int id = 0; id < nn; id++)
@@ -809,8 +859,8 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
         for (size_t xi = 0; xi < S.size(); xi++) {
             const int64_t x = S[xi];
             std::vector<int> touched;
-            for (int64_t e = g.ap[x]; e < g.ap[x + 1]; e++) {
-                const int ow = owner[g.aj[e]];
+            for (int64_t e = g.root.xp[x]; e < g.root.xp[x + 1]; e++) {
+                const int ow = owner[g.root.adj[e]];
                 if (!(lo < ow && ow < hi)) continue;
                 int child = -1;
                 for (int D = ow; D != id; child = D, D = g.nodes[D].parent) {
