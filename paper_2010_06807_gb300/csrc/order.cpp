@@ -309,11 +309,29 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
     // a row sits at the position of its matched column (rows = columns when
     // there is no matching)
     auto rowpos = [&](int64_t r) { return o.rowcol.empty() ? o.iperm[r] : o.iperm[o.rowcol[r]]; };
-    // block pattern: (row cluster, col cluster) by first atom, kept sorted and
-    // unique (row, then column)
-    std::vector<std::pair<int, int>> P;
-    auto normalise = [](std::vector<std::pair<int, int>>& v) {
-        std::sort(v.begin(), v.end());
+    // block pattern: (row cluster, col cluster) by first atom as the key
+    // row * na + col, kept sorted and unique (row, then column)
+    std::vector<uint64_t> P;
+    const uint64_t NA = (uint64_t)na;
+    auto key = [NA](int r, int c) { return (uint64_t)r * NA + (uint64_t)c; };
+    auto krow = [NA](uint64_t k) { return (int)(k / NA); };
+    auto kcol = [NA](uint64_t k) { return (int)(k % NA); };
+    int kbits = 1;
+    while (kbits < 64 && (NA * NA) >> kbits) kbits++;
+    std::vector<uint64_t> ktmp;
+    auto normalise = [&](std::vector<uint64_t>& v) {
+        if (v.size() < 4096) {
+            std::sort(v.begin(), v.end());
+        } else {  // least-significant-digit radix sort, 11-bit digits
+            ktmp.resize(v.size());
+            for (int sh = 0; sh < kbits; sh += 11) {
+                std::vector<size_t> cnt(2049, 0);
+                for (uint64_t k : v) cnt[((k >> sh) & 2047) + 1]++;
+                for (int d = 0; d < 2048; d++) cnt[d + 1] += cnt[d];
+                for (uint64_t k : v) ktmp[cnt[(k >> sh) & 2047]++] = k;
+                v.swap(ktmp);
+            }
+        }
         v.erase(std::unique(v.begin(), v.end()), v.end());
     };
     for (int64_t r = 0; r < n; r++) {
@@ -324,10 +342,11 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
                 set_error("matrix pattern couples separated subdomains (not a 5/7-point stencil on this grid?)");
                 return SPAQR_ERR_UNSUPPORTED;
             }
-            P.push_back({ar, ac});
+            P.push_back(key(ar, ac));
         }
     }
     normalise(P);
+    std::vector<int> idx(na, -1);   // local index of an active cluster
     std::vector<int> active(na);
     std::vector<int> cnode(na), cend(na);
     for (int a = 0; a < na; a++) { active[a] = a; cnode[a] = o.atom_node[a]; cend[a] = a + 1; }
@@ -339,7 +358,6 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         sp.level = lev;
         sp.cl = active;  // sorted
         const int ncl = (int)active.size();
-        std::unordered_map<int, int> idx;
         for (int i = 0; i < ncl; i++) idx[active[i]] = i;
         sp.cl_node.resize(ncl);
         sp.is_front.assign(ncl, 0);
@@ -348,8 +366,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             if (nodes[sp.cl_node[i]].depth + 1 == lev) sp.is_front[i] = 1;
         }
         std::vector<std::vector<int>> col_rows(ncl), row_cols(ncl);
-        for (auto& pr : P) {
-            int i = idx.at(pr.first), j = idx.at(pr.second);
+        for (uint64_t pk : P) {
+            int i = idx[krow(pk)], j = idx[kcol(pk)];
             col_rows[j].push_back(i);
             row_cols[i].push_back(j);
         }
@@ -406,17 +424,17 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         // fill of this level
         for (size_t t = 0; t < fr.size(); t++)
             for (int i : Rf[t])
-                for (int j : Cf[t]) P.push_back({active[i], active[j]});
+                for (int j : Cf[t]) P.push_back(key(active[i], active[j]));
         normalise(P);
         // CSC of the pattern with fill
         sp.colptr.assign(ncl + 1, 0);
-        for (auto& pr : P) sp.colptr[idx.at(pr.second) + 1]++;
+        for (uint64_t pk : P) sp.colptr[idx[kcol(pk)] + 1]++;
         for (int j = 0; j < ncl; j++) sp.colptr[j + 1] += sp.colptr[j];
         sp.rowidx.assign(sp.colptr[ncl], 0);
         {
             std::vector<int> fillp(sp.colptr.begin(), sp.colptr.end() - 1);
             // P iterates by row then column; rows ascending within each column
-            for (auto& pr : P) sp.rowidx[fillp[idx.at(pr.second)]++] = idx.at(pr.first);
+            for (uint64_t pk : P) sp.rowidx[fillp[idx[kcol(pk)]]++] = idx[krow(pk)];
         }
         // encode
         o.plan_code.push_back(lev);
@@ -433,8 +451,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         }
         // eliminate the fronts
         P.erase(std::remove_if(P.begin(), P.end(),
-                               [&](const std::pair<int, int>& pr) {
-                                   return sp.is_front[idx.at(pr.first)] || sp.is_front[idx.at(pr.second)];
+                               [&](uint64_t pk) {
+                                   return sp.is_front[idx[krow(pk)]] || sp.is_front[idx[kcol(pk)]];
                                }),
                 P.end());
         std::vector<int> rest;
@@ -457,7 +475,7 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             for (int i = 0; i < ncl; i++)
                 if (!sp.is_front[i]) sp.parent[i] = nidx.at(f[active[i]]);
             sp.n_next = (int)nxt.size();
-            for (auto& pr : P) pr = {f[pr.first], f[pr.second]};
+            for (uint64_t& pk : P) pk = key(f[krow(pk)], f[kcol(pk)]);
             normalise(P);
             for (int g : nxt) {
                 cnode[g] = o.atom_node[g];
