@@ -42,7 +42,7 @@ extern "C" {
 /* status codes */
 #define SPAQR_OK                 0
 #define SPAQR_ERR_INVALID_ARG   -1   /* bad pointer, size, stride or option */
-#define SPAQR_ERR_UNSUPPORTED   -2   /* e.g. no grid (hypergraph ordering is not built), scaling off */
+#define SPAQR_ERR_UNSUPPORTED   -2   /* e.g. unknown precision, rows too dense for the G(A^T A) ordering */
 #define SPAQR_ERR_OOM           -3   /* device allocation failed */
 #define SPAQR_ERR_SINGULAR      -4   /* zero diagonal in an R_ss or R_pp factor */
 #define SPAQR_ERR_NOT_CONVERGED -5   /* GMRES hit maxit; X holds the last iterate */
@@ -54,6 +54,10 @@ extern "C" {
  * scaling and the CPQR rank decisions are always FP64 */
 #define SPAQR_FP64 0
 #define SPAQR_FP32 1
+
+/* Row matchings of the ordering of a general matrix (spaqr_order_general). */
+#define SPAQR_MATCH_GREEDY      0   /* largest |a_ij| first, then augmenting paths */
+#define SPAQR_MATCH_MAX_PRODUCT 1   /* maximum product of the matched |a_ij| */
 
 /* Sparse matrix in CSR form, rows sorted, N x N.  rowptr has n+1 entries,
  * colind/val have nnz entries.  If on_device != 0 the three arrays are device
@@ -171,6 +175,22 @@ const char* spaqr_last_error(void);
  * their processing order.  *out is owned by the caller
  * (spaqr_ordering_destroy). */
 int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out);
+
+/* The ordering of a general sparse matrix (spaqr_order with g == NULL) with a
+ * choice of row matching (Section 2.3 assigns rows by a bipartite matching
+ * that puts large entries on the diagonal, MC64 in the paper):
+ *   SPAQR_MATCH_GREEDY: entries by decreasing |a_ij| (ties: row, column)
+ *     matched greedily, then every unmatched row by an augmenting path
+ *     (what spaqr_order uses);
+ *   SPAQR_MATCH_MAX_PRODUCT: the perfect matching maximising the product of
+ *     the matched |a_ij| (the product matching of MC64): minimum cost on
+ *     c_ij = log max_k |a_kj| - log |a_ij| over the nonzero values
+ *     (duplicates summed, explicit zeros dropped) by shortest augmenting
+ *     paths with dual potentials; A->val NULL makes every entry 1.
+ * Row r then sits with its matched column.  Errors as spaqr_order, plus
+ * INVALID_ARG for another `matching`, and SINGULAR when no perfect matching
+ * exists on the nonzero values (an empty column included). */
+int spaqr_order_general(const spaqr_csr* A, int nlevels, int matching, spaqr_ordering** out);
 
 /* Ordering of a batch of independent matrices A[0..count-1] on grids
  * g[0..count-1], treated as the block-diagonal matrix diag(A_0, ..., A_{c-1})

@@ -103,7 +103,8 @@ _lib = None
 
 # every symbol include/spaqr.h declares
 EXPORTS = [
-    "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_batch", "spaqr_ordering_info",
+    "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_general", "spaqr_order_batch",
+    "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_rows", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
     "spaqr_gmres", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
@@ -127,6 +128,7 @@ def load_library(path=None):
     lib.spaqr_opts_default.argtypes = [ctypes.POINTER(_Opts)]
     lib.spaqr_opts_default.restype = None
     lib.spaqr_order.argtypes = [ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), i32, ctypes.POINTER(vp)]
+    lib.spaqr_order_general.argtypes = [ctypes.POINTER(_CSR), i32, i32, ctypes.POINTER(vp)]
     lib.spaqr_order_batch.argtypes = [i32, ctypes.POINTER(_CSR), ctypes.POINTER(_Grid), ctypes.POINTER(vp)]
     lib.spaqr_ordering_info.argtypes = [vp, ctypes.POINTER(_OrdInfo)]
     lib.spaqr_ordering_get.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -316,15 +318,23 @@ class Ordering:
             self._h = None
 
 
-def spaqr_order(rowptr, colind, dims, nlevels=0, val=None):
+MATCHINGS = {"greedy": 0, "max_product": 1}
+
+
+def spaqr_order(rowptr, colind, dims, nlevels=0, val=None, matching="greedy"):
     """Modified nested dissection + symbolic plan (spaqr_order): geometric on
     the grid `dims`, or, with dims None, the general-matrix ordering on
-    G(A^T A) with rows matched to columns (by |val| when given)."""
+    G(A^T A) with rows matched to columns (by |val| when given;
+    spaqr_order_general): matching "greedy" (largest entries first, then
+    augmenting paths) or "max_product" (the perfect matching maximising the
+    product of the matched |a_ij|)."""
     load_library()
     csr, keep = _make_csr(rowptr, colind, val if dims is None else None)
     h = ctypes.c_void_p()
     if dims is None:
-        _check(_lib.spaqr_order(ctypes.byref(csr), None, int(nlevels), ctypes.byref(h)))
+        if matching not in MATCHINGS:
+            raise ValueError(f"matching must be one of {sorted(MATCHINGS)}")
+        _check(_lib.spaqr_order_general(ctypes.byref(csr), int(nlevels), MATCHINGS[matching], ctypes.byref(h)))
     else:
         dims = tuple(int(d) for d in dims)
         g = _Grid(len(dims), dims[0], dims[1], dims[2] if len(dims) > 2 else 1)

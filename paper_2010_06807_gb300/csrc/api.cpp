@@ -28,7 +28,8 @@ extern "C" void spaqr_opts_default(spaqr_opts* o) {
     o->stream = nullptr;
 }
 
-extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out) {
+namespace {
+int order_impl(const spaqr_csr* A, const spaqr_grid* g, int nlevels, int matching, spaqr_ordering** out) {
     if (!out) { spaqr::set_error("out is NULL"); return SPAQR_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!A) { spaqr::set_error("A is NULL"); return SPAQR_ERR_INVALID_ARG; }
@@ -71,7 +72,7 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
             int dims[3] = {g->nx, g->ny, g->dim == 3 ? g->nz : 1};
             rc = spaqr::build_ordering(rowptr, colind, A->n, A->nnz, g->dim, dims, nlevels, ord->o);
         } else {
-            rc = spaqr::build_ordering_general(rowptr, colind, val, A->n, A->nnz, nlevels, ord->o);
+            rc = spaqr::build_ordering_general(rowptr, colind, val, A->n, A->nnz, nlevels, matching, ord->o);
         }
     } catch (const std::bad_alloc&) {
         spaqr::set_error("host allocation failed");
@@ -83,6 +84,20 @@ extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels,
     if (rc != SPAQR_OK) { delete ord; return rc; }
     *out = ord;
     return SPAQR_OK;
+}
+}  // namespace
+
+extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out) {
+    return order_impl(A, g, nlevels, SPAQR_MATCH_GREEDY, out);
+}
+
+extern "C" int spaqr_order_general(const spaqr_csr* A, int nlevels, int matching, spaqr_ordering** out) {
+    if (matching != SPAQR_MATCH_GREEDY && matching != SPAQR_MATCH_MAX_PRODUCT) {
+        if (out) *out = nullptr;
+        spaqr::set_error("matching must be SPAQR_MATCH_GREEDY or SPAQR_MATCH_MAX_PRODUCT");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    return order_impl(A, nullptr, nlevels, matching, out);
 }
 
 extern "C" int spaqr_order_batch(int count, const spaqr_csr* A, const spaqr_grid* g, spaqr_ordering** out) {

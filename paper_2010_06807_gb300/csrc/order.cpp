@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <set>
 #include <tuple>
 #include <unordered_map>
@@ -795,6 +796,120 @@ int row_matching(const int64_t* rp, const int32_t* ci, const double* val, int64_
     return SPAQR_OK;
 }
 
+// rowcol[r] = the column row r is matched to, maximising the product of the
+// matched |a_ij| (the large-entries-on-the-diagonal matching Section 2.3 takes
+// from MC64): a minimum-cost perfect matching on
+// c_ij = log max_k |a_kj| - log |a_ij| over the nonzero entries (duplicates
+// summed in storage order, explicit zeros dropped), by shortest augmenting
+// paths with dual potentials u (rows) and v (columns):
+//  * v = 0, u_i = min_j c_ij; every row (ascending) takes its first free
+//    column (ascending) of zero reduced cost (c_ij - u_i) - v_j;
+//  * every row left free (ascending) starts a Dijkstra search over columns
+//    (ties to the smaller column) that crosses matched edges at no cost, up
+//    to the first free column, at distance D; every column k settled on the
+//    way gets v_k -= D - d_k and its matched row u += D - d_k, the start row
+//    u += D; the path is flipped.
+// SINGULAR when no perfect matching exists on the nonzero values.
+int row_matching_max_product(const int64_t* rp, const int32_t* ci, const double* val, int64_t n,
+                             std::vector<int64_t>& rowcol) {
+    std::vector<int64_t> xp(n + 1, 0), ord;
+    std::vector<int32_t> cc;
+    std::vector<double> cv;
+    for (int64_t r = 0; r < n; r++) {
+        ord.clear();
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++) ord.push_back(e);
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return ci[a] < ci[b]; });
+        size_t k = 0;
+        while (k < ord.size()) {
+            const int32_t c = ci[ord[k]];
+            double x = val ? val[ord[k]] : 1.0;
+            size_t m = k + 1;
+            for (; m < ord.size() && ci[ord[m]] == c; m++) x = x + (val ? val[ord[m]] : 1.0);
+            if (x != 0.0) {
+                cc.push_back(c);
+                cv.push_back(x);
+            }
+            k = m;
+        }
+        xp[r + 1] = (int64_t)cc.size();
+    }
+    std::vector<double> amax(n, 0.0);
+    for (size_t e = 0; e < cc.size(); e++) amax[cc[e]] = std::max(amax[cc[e]], std::fabs(cv[e]));
+    for (int64_t j = 0; j < n; j++)
+        if (amax[j] == 0.0) { set_error("structurally singular matrix: an empty column"); return SPAQR_ERR_SINGULAR; }
+    std::vector<double> w(cc.size());
+    for (size_t e = 0; e < cc.size(); e++) w[e] = std::log(amax[cc[e]]) - std::log(std::fabs(cv[e]));
+    std::vector<double> u(n, 0.0), v(n, 0.0);
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t e = xp[r]; e < xp[r + 1]; e++)
+            if (e == xp[r] || w[e] < u[r]) u[r] = w[e];
+    rowcol.assign(n, -1);
+    std::vector<int64_t> colrow(n, -1);
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t e = xp[r]; e < xp[r + 1]; e++) {
+            const int32_t c = cc[e];
+            if (colrow[c] < 0 && (w[e] - u[r]) - v[c] == 0.0) {
+                rowcol[r] = c;
+                colrow[c] = r;
+                break;
+            }
+        }
+    std::vector<double> d(n, 0.0);
+    std::vector<int64_t> pred(n, -1), touched, settled;
+    std::vector<char> reached(n, 0), done(n, 0);
+    using Entry = std::pair<double, int64_t>;   // (distance, column): ties to the smaller column
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> heap;
+    auto relax = [&](int64_t c, double nd, int64_t i) {
+        if (!reached[c] || nd < d[c]) {
+            if (!reached[c]) { reached[c] = 1; touched.push_back(c); }
+            d[c] = nd;
+            pred[c] = i;
+            heap.push(Entry(nd, c));
+        }
+    };
+    for (int64_t r = 0; r < n; r++) {
+        if (rowcol[r] >= 0) continue;
+        for (int64_t e = xp[r]; e < xp[r + 1]; e++) relax(cc[e], (w[e] - u[r]) - v[cc[e]], r);
+        int64_t end = -1;
+        while (!heap.empty()) {
+            const Entry top = heap.top();
+            heap.pop();
+            const double dj = top.first;
+            const int64_t j = top.second;
+            if (done[j]) continue;
+            done[j] = 1;
+            settled.push_back(j);
+            if (colrow[j] < 0) { end = j; break; }
+            const int64_t i = colrow[j];
+            for (int64_t e = xp[i]; e < xp[i + 1]; e++) {
+                const int32_t c = cc[e];
+                if (done[c]) continue;
+                relax(c, dj + ((w[e] - u[i]) - v[c]), i);
+            }
+        }
+        if (end < 0) { set_error("structurally singular matrix: no perfect row matching"); return SPAQR_ERR_SINGULAR; }
+        const double D = d[end];
+        u[r] = u[r] + D;
+        for (int64_t k : settled) {
+            const double delta = D - d[k];
+            v[k] = v[k] - delta;
+            if (k != end) u[colrow[k]] = u[colrow[k]] + delta;
+        }
+        for (int64_t j = end;;) {
+            const int64_t i = pred[j], prev = rowcol[i];
+            rowcol[i] = j;
+            colrow[j] = i;
+            if (i == r) break;
+            j = prev;
+        }
+        while (!heap.empty()) heap.pop();
+        for (int64_t c : touched) reached[c] = done[c] = 0;
+        touched.clear();
+        settled.clear();
+    }
+    return SPAQR_OK;
+}
+
 int check_grid(int dim, const int* dims, int64_t n, const int64_t* rowptr, int64_t nnz, int* dims3) {
     if (dim != 2 && dim != 3) { set_error("grid dim must be 2 or 3"); return SPAQR_ERR_INVALID_ARG; }
     int64_t N = 1;
@@ -825,7 +940,11 @@ int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int6
 }
 
 int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const double* val, int64_t n,
-                           int64_t nnz, int nlevels, Ordering& o) {
+                           int64_t nnz, int nlevels, int matching, Ordering& o) {
+    if (matching != SPAQR_MATCH_GREEDY && matching != SPAQR_MATCH_MAX_PRODUCT) {
+        set_error("unknown row matching");
+        return SPAQR_ERR_INVALID_ARG;
+    }
     if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
     for (int64_t e = 0; e < nnz; e++)
         if (colind[e] < 0 || colind[e] >= n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
@@ -849,7 +968,8 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
             return SPAQR_ERR_UNSUPPORTED;
         }
     }
-    int rc = row_matching(rowptr, colind, val, n, o.rowcol);
+    int rc = matching == SPAQR_MATCH_GREEDY ? row_matching(rowptr, colind, val, n, o.rowcol)
+                                            : row_matching_max_product(rowptr, colind, val, n, o.rowcol);
     if (rc != SPAQR_OK) return rc;
     GeneralND g;
     g.n = n;

@@ -80,7 +80,7 @@ int build_ordering_batch(int count, const int64_t* const* rowptrs, const int32_t
 int build_ordering(const int64_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
                    int dim, const int* dims, int nlevels, Ordering& out);
 int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const double* val, int64_t n,
-                           int64_t nnz, int nlevels, Ordering& out);
+                           int64_t nnz, int nlevels, int matching, Ordering& out);
 
 int num_levels(int64_t n);
 

@@ -280,13 +280,17 @@ def permuted(problem, seed, rows=True, cols=True):
     return p
 
 
-def random_local(nside, k=4, radius=2.5, seed=7000):
+def random_local(nside, k=4, radius=2.5, seed=7000, weak_diag=None):
     """A general unsymmetric sparse matrix: nside^2 points scattered in the
     unit square (one per grid cell, jittered); row i couples to k of the
     points within `radius` cell widths, chosen at random, with N(0,1)
     values; the diagonal is the row's absolute sum plus 1 (row diagonally
     dominant).  Unknowns are numbered in a random order.  Draws: jitter,
-    numbering, then per row its neighbours and values."""
+    numbering, then per row its neighbours and values.
+
+    weak_diag = w > 0 instead draws the diagonal as w * N(0,1) right after
+    the row's values (a matrix whose large entries are off the diagonal, so
+    that the row matching matters); the other draws are unchanged."""
     rng = np.random.Generator(np.random.PCG64(seed))
     N = nside * nside
     base = np.stack(np.meshgrid(np.arange(nside), np.arange(nside), indexing="xy"), -1).reshape(-1, 2)
@@ -312,8 +316,9 @@ def random_local(nside, k=4, radius=2.5, seed=7000):
             vals.append(v)
         rows.append(label[i])
         cols.append(label[i])
-        vals.append(np.abs(off).sum() + 1.0)
+        vals.append(np.abs(off).sum() + 1.0 if weak_diag is None else weak_diag * rng.standard_normal())
     rowptr, colind, val = csr_from_coo(N, rows, cols, vals)
-    p = Problem(None, rowptr, colind, val, seed=seed, name=f"random_local_{nside}")
+    name = f"random_local_{nside}" if weak_diag is None else f"random_local_weak_{nside}"
+    p = Problem(None, rowptr, colind, val, seed=seed, name=name)
     p.rng = rng
     return p

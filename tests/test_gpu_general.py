@@ -97,3 +97,34 @@ def test_general_unscaled_matches_oracle(dev, name, p, L):
     xo = osq.solve(Fo, b)
     xg = sq.spaqr_solve(F, _colmajor(b, dev)).cpu().numpy()
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL
+
+
+@pytest.mark.parametrize("eps,skip", [(0.0, 0), (1e-2, 1), (1e-3, 2)])
+@pytest.mark.parametrize("nside,L,seed", [(20, 4, 7025), (32, 0, 7026)])
+def test_max_product_matching_matches_oracle(dev, nside, L, seed, eps, skip):
+    """A matrix whose large entries are off the diagonal, ordered with the
+    maximum-product row matching (spaqr_order_general): ranks bit-exact,
+    one application to 1e-10, eps = 0 exact, and GMRES at eps = 1e-2 with
+    the oracle's iteration count +-1."""
+    p = random_local(nside, seed=seed, weak_diag=0.1)
+    A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+    o = sq.spaqr_order(*A[:2], None, L, val=A[2], matching="max_product")
+    F = sq.spaqr_factor(o, *A, eps=eps, skip=skip)
+    og = nd_general(p.n, p.rowptr, p.colind, p.val, o.L, matching="max_product")
+    np.testing.assert_array_equal(o.arrays()["rperm"], og.rperm)
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, None, eps, nlevels=o.L, skip=skip, ordering=og)
+    for lev, R in enumerate(Fo.ranks):
+        exp = [tuple(v) for _, v in sorted(R.items()) if v[0] > 0]
+        assert [tuple(x) for x in sq.spaqr_factor_ranks(F, lev)[0].tolist()] == exp, lev
+    b = np.random.default_rng(3).standard_normal((p.n, 2))
+    xo = osq.solve(Fo, b)
+    xg = sq.spaqr_solve(F, _colmajor(b, dev)).cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= TOL
+    if eps == 0.0:
+        res = np.linalg.norm(b - p.matvec(xg), axis=0) / np.linalg.norm(b, axis=0)
+        assert res.max() <= 1e-12
+    if eps == 1e-2:
+        x, it, rr = sq.spaqr_gmres(F, *A, torch.from_numpy(b[:, 0].copy()).to(dev), tol=1e-12)
+        assert rr[0] <= 1e-12
+        _, ito, _, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, 0], lambda v: osq.solve(Fo, v))
+        assert abs(int(it[0]) - ito) <= 1, (it, ito)

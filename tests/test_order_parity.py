@@ -138,3 +138,87 @@ def test_general_ordering_edge_cases(spaqr_lib, case):
     b = np.random.default_rng(2).standard_normal(p.n)
     x = osq.solve(F, b)
     assert np.linalg.norm(b - p.matvec(x)) <= 1e-12 * np.linalg.norm(b)
+
+
+def _with_duplicates_and_zeros(p, seed):
+    """p with some entries split into two stored parts (same sum up to one
+    rounding), explicit zeros at new positions of existing rows, and every
+    row's entries in a shuffled storage order."""
+    from synth.convdiff import Problem
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for r in range(p.n):
+        ent = [(int(c), float(x)) for c, x in zip(p.colind[p.rowptr[r]:p.rowptr[r + 1]],
+                                                  p.val[p.rowptr[r]:p.rowptr[r + 1]])]
+        out = []
+        for c, x in ent:
+            if rng.random() < 0.3:
+                t = rng.uniform(0.2, 0.8)
+                out += [(c, t * x), (c, x - t * x)]
+            else:
+                out.append((c, x))
+        if rng.random() < 0.3:
+            out.append((int(rng.integers(p.n)), 0.0))
+        rng.shuffle(out)
+        for c, x in out:
+            rows.append(r)
+            cols.append(c)
+            vals.append(x)
+    counts = np.bincount(np.asarray(rows), minlength=p.n)
+    rp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return Problem(None, rp, np.asarray(cols, dtype=np.int32), np.asarray(vals), name=p.name + "_dup")
+
+
+def _max_product_cases():
+    from synth.convdiff import permuted, random_local
+    g = config_problem("2d_uniform_a", n=20)
+    w = random_local(16, seed=7016, weak_diag=0.1)
+    return [("weak_18", random_local(18, seed=7013, weak_diag=0.1), 4, True),
+            ("weak_30_auto_L", random_local(30, seed=7014, weak_diag=0.05), 0, True),
+            ("row_col_permuted", permuted(g, 23), 4, True),
+            ("pattern_only", random_local(16, seed=7015, weak_diag=0.1), 4, False),
+            ("duplicates_zeros", _with_duplicates_and_zeros(w, 3), 4, True)]
+
+
+@pytest.mark.parametrize("name,p,L,values", _max_product_cases())
+def test_general_ordering_max_product_bit_exact(spaqr_lib, name, p, L, values):
+    """The maximum-product row matching (and the ordering and plan built on
+    it) equals the oracle's, ties included (pattern only: every cost is 0)."""
+    from oracle.ordering_general import nd_general
+    val = p.val if values else None
+    ordl = sq.spaqr_order(p.rowptr, p.colind, None, L, val=val, matching="max_product")
+    arr = ordl.arrays()
+    o = nd_general(p.n, p.rowptr, p.colind, val, L if L > 0 else None, matching="max_product")
+    assert ordl.L == o.L
+    for k in ("perm", "atom_ptr", "atom_node", "node_level", "rperm"):
+        np.testing.assert_array_equal(arr[k], getattr(o, k), err_msg=k)
+    F = osq.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-2, nlevels=o.L, skip=1, ordering=o)
+    plan = ordl.plan()
+    assert len(plan) == len(F.steps)
+    for st_l, st_o in zip(plan, F.steps):
+        assert st_l["clusters"] == sorted(st_o["sizes"].keys())
+        assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
+
+
+def test_general_ordering_matching_errors(spaqr_lib):
+    import ctypes
+    g = config_problem("2d_uniform_a", n=6)
+    with pytest.raises(ValueError):
+        sq.spaqr_order(g.rowptr, g.colind, None, 2, val=g.val, matching="mc64")
+    # an unknown matching code at the C ABI
+    csr, keep = sq._make_csr(g.rowptr, g.colind, g.val)
+    h = ctypes.c_void_p(1)
+    assert sq._lib.spaqr_order_general(ctypes.byref(csr), 2, 7, ctypes.byref(h)) == -1
+    assert not h.value
+    # column 0 holds only explicit zeros: a perfect matching on the pattern,
+    # none on the values
+    rp = np.array([0, 2, 4, 5], dtype=np.int64)
+    ci = np.array([0, 1, 0, 2, 1], dtype=np.int32)
+    v = np.array([0.0, 1.0, 0.0, 3.0, 2.0])
+    sq.spaqr_order(rp, ci, None, 1, val=v)   # greedy: uses the pattern
+    with pytest.raises(sq.SpaqrError) as e:
+        sq.spaqr_order(rp, ci, None, 1, val=v, matching="max_product")
+    assert e.value.name == "SINGULAR"
+    from oracle.ordering_general import row_matching_max_product
+    with pytest.raises(ValueError):
+        row_matching_max_product(3, rp, ci, v)
