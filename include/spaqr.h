@@ -160,7 +160,9 @@ const char* spaqr_last_error(void);
  * (Sections 2.1, 2.3): separators two grid planes thick (a vertex separator of
  * G(A^T A) for 5/7-point stencils), interfaces from the cuts of descendant
  * subdomains, cluster hierarchy, row order = column order.  Host-only integer
- * work (a device pattern is copied to the host).  nlevels = 0 picks
+ * work (a device pattern is copied to the host; INVALID_ARG unless rowptr
+ * runs from 0 to nnz without decreasing and every column index is in
+ * [0, n)).  nlevels = 0 picks
  * ceil(log2(N/64)).  g == NULL orders a general sparse matrix instead
  * (Section 2.3 uses a hypergraph partitioner and MC64 there; this is our
  * restatement): nested dissection on G(A^T A) with breadth-first level sets
@@ -284,7 +286,11 @@ int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const double* B, int6
  * iters[c] and relres[c] (host arrays of nrhs entries, may be NULL) receive
  * per-column iteration counts and final relative residuals.  maxit bounds the
  * Krylov dimension (no restart).  Returns NOT_CONVERGED if any column missed
- * tol (X holds the last iterate).  Synchronous on `stream`. */
+ * tol (X holds the last iterate).  Synchronous on `stream`.
+ * A must be the factored matrix: INVALID_ARG if A->nnz differs from the
+ * factored pattern's, and, for a host CSR, if its rowptr does not run from 0
+ * to nnz without decreasing or a column index is out of range (checked
+ * before any kernel); a device CSR is trusted (its SpMV reads it as given). */
 int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B,
                 int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
                 double* relres, void* stream);

@@ -928,6 +928,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     const int64_t n = o.n, nnz = o.nnz;
     const int L = o.L;
     F->n = n;
+    F->nnz = nnz;
     F->L = L;
     F->skip = opt->skip;
     F->eps = opt->eps;

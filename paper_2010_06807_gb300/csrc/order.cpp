@@ -32,6 +32,7 @@
 #include <map>
 #include <queue>
 #include <set>
+#include <string>
 #include <tuple>
 #include <unordered_map>
 
@@ -910,6 +911,15 @@ int row_matching_max_product(const int64_t* rp, const int32_t* ci, const double*
     return SPAQR_OK;
 }
 
+// rowptr starts at 0, never decreases and ends at nnz (every host loop over a
+// row's entries then stays inside colind)
+int check_rowptr(const int64_t* rowptr, int64_t n, int64_t nnz) {
+    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr (first entry not 0 or last not nnz)"); return SPAQR_ERR_INVALID_ARG; }
+    for (int64_t r = 0; r < n; r++)
+        if (rowptr[r + 1] < rowptr[r]) { set_error("bad CSR rowptr (decreasing at row " + std::to_string(r) + ")"); return SPAQR_ERR_INVALID_ARG; }
+    return SPAQR_OK;
+}
+
 int check_grid(int dim, const int* dims, int64_t n, const int64_t* rowptr, int64_t nnz, int* dims3) {
     if (dim != 2 && dim != 3) { set_error("grid dim must be 2 or 3"); return SPAQR_ERR_INVALID_ARG; }
     int64_t N = 1;
@@ -918,7 +928,7 @@ int check_grid(int dim, const int* dims, int64_t n, const int64_t* rowptr, int64
         N *= dims[k];
     }
     if (N != n) { set_error("grid size does not match matrix size"); return SPAQR_ERR_INVALID_ARG; }
-    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+    if (check_rowptr(rowptr, n, nnz) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     for (int k = 0; k < 3; k++) dims3[k] = k < dim ? dims[k] : 1;
     return SPAQR_OK;
 }
@@ -945,7 +955,7 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
         set_error("unknown row matching");
         return SPAQR_ERR_INVALID_ARG;
     }
-    if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+    if (check_rowptr(rowptr, n, nnz) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     for (int64_t e = 0; e < nnz; e++)
         if (colind[e] < 0 || colind[e] >= n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
     o.dim = 0;

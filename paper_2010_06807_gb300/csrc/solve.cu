@@ -1441,6 +1441,20 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         set_error("bad size, leading dimension, tol or maxit");
         return SPAQR_ERR_INVALID_ARG;
     }
+    // A must be the factored matrix: its pattern has as many entries, and a
+    // host CSR is checked in full before any kernel reads it (a device CSR
+    // is trusted: checking it would cost a pass and a synchronisation)
+    if (A->nnz != F->nnz || !A->rowptr || !A->colind || !A->val) {
+        set_error("A does not match the factored pattern (nnz) or has NULL arrays");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    if (!A->on_device) {
+        if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
+        for (int64_t r = 0; r < A->n; r++)
+            if (A->rowptr[r + 1] < A->rowptr[r]) { set_error("bad CSR rowptr (decreasing)"); return SPAQR_ERR_INVALID_ARG; }
+        for (int64_t e = 0; e < A->nnz; e++)
+            if (A->colind[e] < 0 || A->colind[e] >= A->n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    }
     if (nrhs == 0) return SPAQR_OK;
     DeviceGuard dg(F->device);   // outlives the stream and allocations below
     keep_pool_memory(F->device);

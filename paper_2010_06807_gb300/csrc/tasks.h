@@ -288,6 +288,7 @@ struct LevelDiag {
 struct spaqr_factor_s {
     int device = 0;
     int64_t n = 0;
+    int64_t nnz = 0;               // entries of the factored pattern
     int L = 0, skip = 0;
     double eps = 0.0;
     std::vector<void*> allocs;     // device allocations owned by the factor

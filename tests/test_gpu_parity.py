@@ -181,3 +181,26 @@ def test_errors(dev):
     assert e.value.name == "NOT_CONVERGED"
     # the error carries the best iterate and the per-column counts
     assert e.value.iters.tolist() == [1] and e.value.relres[0] > 1e-15 and e.value.X.shape == (p.n, 1)
+
+
+def test_gmres_rejects_mismatched_or_bad_host_csr(dev):
+    """GMRES reads A's CSR in its SpMV kernels: a host CSR with another entry
+    count than the factored pattern, a decreasing rowptr or a column index
+    out of range is refused on the host (INVALID_ARG) before any kernel."""
+    p = config_problem("2d_uniform_a", n=16)
+    rp, ci, va = _to_dev(p, dev)
+    F = sq.spaqr_factor(sq.spaqr_order(rp, ci, p.dims), rp, ci, va, eps=1e-2)
+    b = np.asfortranarray(rhs(p, 1))
+    short = p.rowptr.copy()
+    short[-1] -= 1
+    bad_rp = p.rowptr.copy()
+    bad_rp[3] = bad_rp[5] + 1
+    bad_ci = p.colind.copy()
+    bad_ci[5] = p.n
+    for A in ((short, p.colind[:-1], p.val[:-1]), (bad_rp, p.colind, p.val), (p.rowptr, bad_ci, p.val)):
+        with pytest.raises(sq.SpaqrError) as e:
+            sq.spaqr_gmres(F, *A, b, tol=1e-12)
+        assert e.value.name == "INVALID_ARG"
+    # the factor is untouched: the right matrix still converges
+    _, it, rr = sq.spaqr_gmres(F, p.rowptr, p.colind, p.val, b, tol=1e-12)
+    assert rr[0] <= 1e-12

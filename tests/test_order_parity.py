@@ -222,3 +222,20 @@ def test_general_ordering_matching_errors(spaqr_lib):
     from oracle.ordering_general import row_matching_max_product
     with pytest.raises(ValueError):
         row_matching_max_product(3, rp, ci, v)
+
+
+def test_orderings_reject_decreasing_rowptr(spaqr_lib):
+    """A rowptr that starts at 0 and ends at nnz but decreases in between
+    would send the host loops outside colind: all three ordering paths
+    refuse it (INVALID_ARG) before reading the rows."""
+    p = config_problem("2d_uniform_a", n=8)
+    rp = p.rowptr.copy()
+    rp[3] = rp[5] + 1          # rows 2 and 3 now run backwards
+    for call in (lambda: sq.spaqr_order(rp, p.colind, p.dims, 2),
+                 lambda: sq.spaqr_order(rp, p.colind, None, 2, val=p.val),
+                 lambda: sq.spaqr_order(rp, p.colind, None, 2, val=p.val, matching="max_product"),
+                 lambda: sq.spaqr_order_batch([(p.rowptr, p.colind), (rp, p.colind)], [p.dims, p.dims])):
+        with pytest.raises(sq.SpaqrError) as e:
+            call()
+        assert e.value.name == "INVALID_ARG"
+        assert "rowptr" in str(e.value)
