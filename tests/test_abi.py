@@ -35,3 +35,25 @@ def test_host_only_calls_without_gpu(spaqr_lib):
     sq.spaqr_stats_reset()
     tot, st = sq.spaqr_stats()
     assert tot == 0 and "cpqr" in st
+
+
+def test_plain_c_program(spaqr_lib, tmp_path):
+    """The header compiles as strict C99 (-pedantic -Werror) and a C program
+    linked against libspaqr.so orders a matrix through the ABI alone
+    (tests/c_abi_host.c: host-only calls)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(os.path.abspath(spaqr_lib._name))
+    exe = str(tmp_path / "c_abi_host")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c_abi_host.c"),
+                        "-L", libdir, "-lspaqr", "-Wl,-rpath," + libdir, "-o", exe],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok n=1600 ")
