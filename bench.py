@@ -101,17 +101,45 @@ for c in cols:
     out["gmres_s"].append(time.perf_counter() - t0)
     out["iters"].append(int(it))
     out["relres_max"] = max(out.get("relres_max", 0.0), float(rr))
+ncores = %(parallel)d
+if ncores > 1:
+    # the same oracle on several host cores: the right-hand sides are
+    # independent, so each forked worker brings whole columns to tol
+    import multiprocessing as mp
+
+    def _solve(c):
+        x, it, rr, _ = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, c], lambda v: osq.solve(F, v),
+                                 tol=%(tol)r, maxit=%(maxit)d)
+        return int(it), float(rr)
+
+    try:
+        t0 = time.perf_counter()
+        with mp.get_context("fork").Pool(ncores) as pool:
+            res = pool.map(_solve, range(b.shape[1]), chunksize=1)
+        out["parallel_s"] = time.perf_counter() - t0
+        out["parallel_cores"] = ncores
+        out["parallel_iters"] = [r[0] for r in res]
+        out["parallel_relres_max"] = max(r[1] for r in res)
+    except Exception as e:
+        out["parallel_error"] = repr(e)
 print(json.dumps(out))
 """
 
 
-def run_oracle(ncols, mode="baseline"):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_oracle(ncols, mode="baseline", parallel=1, nside=None):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = _ORACLE_SCRIPT % dict(root=ROOT, kind=KIND, n=NSIDE, nrhs=NRHS, mode=mode, eps=EPS, tol=TOL,
-                                 maxit=MAXIT, ncols=ncols)
+    code = _ORACLE_SCRIPT % dict(root=ROOT, kind=KIND, n=nside or NSIDE, nrhs=NRHS, mode=mode, eps=EPS, tol=TOL,
+                                 maxit=MAXIT, ncols=ncols, parallel=int(parallel))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -617,13 +645,24 @@ def ours(a):
         line["serving_8x3d_poisson2000"] = srv
     if not a.no_cpu_baseline:
         try:
-            r = run_oracle(1)
+            r = run_oracle(1, parallel=min(host_cores(), NRHS))
             cv = NRHS / (r["factor_s"] + NRHS * r["gmres_s"][0])
             line["cpu_baseline"] = {
                 "value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": (f"oracle factorisation of the full 256x256 matrix ({r['factor_s']:.1f} s) + oracle "
                            f"GMRES of 1 of the 16 RHS ({r['gmres_s'][0]:.1f} s, {r['iters'][0]} iters); "
                            "value = 16 / (factor + 16 x gmres)")}
+            if "parallel_s" in r:
+                line["cpu_baseline_parallel"] = {
+                    "value": NRHS / (r["factor_s"] + r["parallel_s"]), "unit": UNIT,
+                    "cores": r["parallel_cores"], "kind": "oracle",
+                    "sample": (f"the same factorisation on one core ({r['factor_s']:.1f} s), then all 16 RHS "
+                               f"brought to 1e-12 by the oracle GMRES in {r['parallel_cores']} forked processes "
+                               f"({r['parallel_s']:.1f} s wall, iters {sorted(set(r['parallel_iters']))}); "
+                               "value = 16 / (factor + wall)")}
+            elif "parallel_error" in r:
+                line["cpu_baseline_parallel"] = {"value": None, "unit": UNIT, "kind": "oracle",
+                                                 "sample": "failed: " + r["parallel_error"]}
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {e}"}
