@@ -13,6 +13,7 @@ Typical use::
 
     o = spaqr_order(rowptr, colind, (nx, ny))         # grid: geometric ordering
     o = spaqr_order(rowptr, colind, None, val=val)    # general matrix: G(A^T A) ordering, matched rows
+    o = spaqr_order(rowptr, colind, None, val=val, matching="max_product")
     F = spaqr_factor(o, rowptr, colind, val, eps=1e-2)          # scaled, FP64
     F = spaqr_factor(o, rowptr, colind, val, eps=1e-2, scaling=0, precision="fp32")
     X, iters, relres = spaqr_gmres(F, rowptr, colind, val, B, tol=1e-12)
