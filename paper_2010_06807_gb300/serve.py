@@ -84,7 +84,9 @@ def _dim_key(problem):
 class DeviceOps:
     """libspaqr + torch streams on one CUDA device: what the server runs."""
 
-    def __init__(self, device=None, eps=1e-2, precision="fp64", tol=1e-12, maxit=300):
+    def __init__(self, device=None, eps=1e-2, precision="fp64", tol=1e-12, maxit=300, matching="greedy"):
+        """matching: the row matching of general matrices (no grid), "greedy"
+        or "max_product" (see spaqr_order)."""
         import torch
 
         from . import load_library
@@ -95,6 +97,10 @@ class DeviceOps:
         self.precision = precision
         self.tol = tol
         self.maxit = maxit
+        from . import MATCHINGS
+        if matching not in MATCHINGS:
+            raise ValueError(f"matching must be one of {sorted(MATCHINGS)}")
+        self.matching = matching
         self._per_unknown = {}
 
     def new_stream(self):
@@ -110,8 +116,10 @@ class DeviceOps:
                    torch.from_numpy(problem.val).to(self.device))
             # grids: geometric ordering; general matrices (dims None): the
             # G(A^T A) ordering with rows matched by |a_ij|
+            general = problem.dims is None
             ordering = spaqr_order(problem.rowptr, problem.colind, problem.dims,
-                                   val=problem.val if problem.dims is None else None)
+                                   val=problem.val if general else None,
+                                   matching=self.matching if general else "greedy")
             F = spaqr_factor(ordering, *csr, eps=self.eps, precision=self.precision, stream=stream)
         return {"F": F, "csr": csr, "ordering": ordering, "n": problem.n, "dim": _dim_key(problem)}
 

@@ -199,3 +199,14 @@ def test_device_ops_memory_estimates(monkeypatch, spaqr_lib):
     assert ops.estimate_factor_bytes(g) == 16384 * 10          # general matrices: own key
     assert ops.factor_bytes({"F": None, "n": 10, "dim": 0}) == 50
     assert ops.estimate_factor_bytes(g) == int(1.25 * 9 * 10)
+
+
+def test_device_ops_matching_option():
+    """The served ordering of general matrices takes the row matching given
+    to DeviceOps; an unknown one is refused when the server is set up."""
+    import pytest as _pt
+    from paper_2010_06807_gb300.serve import DeviceOps
+    assert DeviceOps("cuda:0").matching == "greedy"
+    assert DeviceOps("cuda:0", matching="max_product").matching == "max_product"
+    with _pt.raises(ValueError):
+        DeviceOps("cuda:0", matching="mc64")
