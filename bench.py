@@ -71,6 +71,24 @@ def _peaks():
         return {}
 
 
+def max_over_ranks(x, world, dist=None, device=None):
+    """The largest x over all ranks (the slowest rank's time); x itself on
+    one rank.  device: where the reduced tensor lives (the rank's GPU under
+    NCCL, the CPU under gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, slowest_s):
+    """Units all ranks processed per second of the slowest rank (every rank
+    runs its own replica with the same work: weak scaling)."""
+    return units_per_rank * world / slowest_s
+
+
 def _pct(v, q):
     v = sorted(v)
     if not v:
@@ -549,12 +567,8 @@ def ours(a):
         torch.cuda.synchronize(dev)
         sq.spaqr_profile(False)
         _, kstats = sq.spaqr_stats()
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = NRHS * a.steps * world / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dist, dev)
+    value = whole_job_rate(NRHS * a.steps, world, total_s)
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     rph = torch.from_numpy(p.rowptr).pin_memory()
@@ -574,11 +588,7 @@ def ours(a):
         del F
         if i >= a.warmup:
             e2e_t.append(t1 - t0)
-    e2e_total = sum(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_t), world, dist, dev)
     nnz, n = p.nnz, p.n
     h2d = (8 * nnz + 4 * nnz) + (8 * (n + 1) + 4 * nnz + 8 * nnz) + 2 * 8 * n * NRHS
     d2h = 8 * n * NRHS
@@ -619,7 +629,7 @@ def ours(a):
         "factor_gflop": info["factor_flops"] / 1e9, "factor_mbytes": info["factor_bytes"] / 2 ** 20,
         "rank_sum": info["rank_sum"], "size_sum": info["size_sum"], "top_separator": info["top_size"],
         "phase_ms": dict(zip(["factorize", "scale", "sparsify", "merge"], info["phase_ms"])),
-        "e2e": {"value": NRHS * a.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(NRHS * a.steps, world, e2e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "gpu_launches_note": "kernels of ours launched in the timed steps, graph replays counted per kernel",
