@@ -57,3 +57,35 @@ def test_plain_c_program(spaqr_lib, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok n=1600 ")
+
+
+def test_host_only_error_paths(spaqr_lib):
+    """Bad arguments of the host-only calls come back as INVALID_ARG with a
+    message (no crash, no handle): NULL handles, nnz < n, nlevels out of
+    range, an empty batch; destroying NULL is a no-op."""
+    import ctypes
+
+    import numpy as np
+    from synth.convdiff import config_problem
+    INVALID = -1
+    info = sq._OrdInfo()
+    assert spaqr_lib.spaqr_ordering_info(None, ctypes.byref(info)) == INVALID
+    assert spaqr_lib.spaqr_ordering_rows(None, None) == INVALID
+    assert spaqr_lib.spaqr_ordering_get(None, None, None, None, None, None) == INVALID
+    assert spaqr_lib.spaqr_last_error()
+    spaqr_lib.spaqr_ordering_destroy(None)
+    p = config_problem("2d_uniform_a", n=6)
+    csr, keep = sq._make_csr(p.rowptr, p.colind, p.val)
+    g = sq._Grid(2, 6, 6, 1)
+    h = ctypes.c_void_p()
+    assert spaqr_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), 41, ctypes.byref(h)) == INVALID
+    assert spaqr_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), -1, ctypes.byref(h)) == INVALID
+    short = sq._CSR(csr.n, csr.n - 1, csr.rowptr, csr.colind, csr.val, 0)
+    assert spaqr_lib.spaqr_order(ctypes.byref(short), ctypes.byref(g), 0, ctypes.byref(h)) == INVALID
+    assert spaqr_lib.spaqr_order_batch(0, ctypes.byref(csr), ctypes.byref(g), ctypes.byref(h)) == INVALID
+    assert not h.value
+    # a grid whose size does not match n
+    g2 = sq._Grid(2, 6, 5, 1)
+    assert spaqr_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g2), 0, ctypes.byref(h)) == INVALID
+    assert b"grid" in spaqr_lib.spaqr_last_error()
+    del keep
