@@ -239,3 +239,49 @@ def test_orderings_reject_decreasing_rowptr(spaqr_lib):
             call()
         assert e.value.name == "INVALID_ARG"
         assert "rowptr" in str(e.value)
+
+
+@pytest.mark.parametrize("matching", ["greedy", "max_product"])
+def test_matchings_random_small_matrices(spaqr_lib, matching):
+    """Many small random patterns with heavy ties (values from a six-value
+    set, zeros included), duplicate entries, shuffled rows and pattern-only
+    runs: the host matching equals the oracle's, and both refuse the same
+    structurally singular cases."""
+    from oracle.ordering_general import row_matching, row_matching_max_product
+    ref_fn = row_matching if matching == "greedy" else row_matching_max_product
+    rng = np.random.default_rng(321 if matching == "greedy" else 123)
+    tested = 0
+    for t in range(150):
+        n = int(rng.integers(2, 40))
+        M = rng.random((n, n)) < rng.uniform(0.05, 0.4)
+        M[np.arange(n), rng.permutation(n)] = True
+        rows, cols, vals = [], [], []
+        for r in range(n):
+            cs = list(np.nonzero(M[r])[0])
+            rng.shuffle(cs)
+            for c in cs:
+                for _ in range(2 if rng.random() < 0.15 else 1):
+                    rows.append(r)
+                    cols.append(int(c))
+                    vals.append(float(rng.choice([1.0, -1.0, 2.0, 0.5, -3.0, 0.0])) if t % 2
+                                else float(rng.lognormal()))
+        rp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]).astype(np.int64)
+        ci = np.asarray(cols, dtype=np.int32)
+        va = None if t % 7 == 0 else np.asarray(vals)
+        try:
+            ref = ref_fn(n, rp, ci, va)
+        except ValueError:
+            ref = None
+        try:
+            arr = sq.spaqr_order(rp, ci, None, 2 if n > 8 else 1, val=va, matching=matching).arrays()
+        except sq.SpaqrError as e:
+            assert e.name == "SINGULAR", e
+            arr = None
+        assert (ref is None) == (arr is None), t
+        if ref is None:
+            continue
+        colrow = np.empty(n, dtype=np.int64)
+        colrow[ref] = np.arange(n)
+        np.testing.assert_array_equal(arr["rperm"], colrow[arr["perm"]], err_msg=str(t))
+        tested += 1
+    assert tested >= 100
