@@ -285,3 +285,39 @@ def test_matchings_random_small_matrices(spaqr_lib, matching):
         np.testing.assert_array_equal(arr["rperm"], colrow[arr["perm"]], err_msg=str(t))
         tested += 1
     assert tested >= 100
+
+
+def test_general_ordering_random_patterns(spaqr_lib):
+    """Random sparse patterns of 1-60 columns (some split into two
+    disconnected blocks, some with shuffled rows and columns) at 1-5 levels:
+    the host ordering equals the oracle's, and every fifth plan too."""
+    from oracle.ordering_general import nd_general
+    rng = np.random.default_rng(77)
+    for t in range(120):
+        n = int(rng.integers(1, 60))
+        M = rng.random((n, n)) < rng.uniform(0.02, 0.2)
+        M[np.arange(n), np.arange(n)] = True
+        if t % 3 == 0 and n > 4:
+            h = n // 2
+            M[:h, h:] = False
+            M[h:, :h] = False
+        if t % 2:
+            M = M[rng.permutation(n)][:, rng.permutation(n)]
+        rp = np.concatenate([[0], np.cumsum(M.sum(1))]).astype(np.int64)
+        ci = np.concatenate([np.nonzero(M[r])[0] for r in range(n)]).astype(np.int32)
+        va = rng.standard_normal(ci.shape[0])
+        L = int(rng.integers(1, 6))
+        o = nd_general(n, rp, ci, va, L)
+        ol = sq.spaqr_order(rp, ci, None, L, val=va)
+        arr = ol.arrays()
+        for k in ("perm", "atom_ptr", "atom_node", "node_level", "rperm"):
+            np.testing.assert_array_equal(arr[k], getattr(o, k), err_msg=f"{t} {k}")
+        if t % 5 == 0:
+            F = osq.factor(n, rp, ci, va, None, 1e-2, nlevels=L, skip=1, ordering=o)
+            plan = ol.plan()
+            assert len(plan) == len(F.steps)
+            for st_l, st_o in zip(plan, F.steps):
+                assert st_l["clusters"] == sorted(st_o["sizes"].keys())
+                assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
+                for f in st_l["fronts"]:
+                    assert f["R"] == list(st_o["R"][f["id"]]) and f["C"] == list(st_o["C"][f["id"]])
