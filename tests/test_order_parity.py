@@ -321,3 +321,30 @@ def test_general_ordering_random_patterns(spaqr_lib):
                 assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
                 for f in st_l["fronts"]:
                     assert f["R"] == list(st_o["R"][f["id"]]) and f["C"] == list(st_o["C"][f["id"]])
+
+
+def test_grid_ordering_random_shapes(spaqr_lib):
+    """Random 2D (1-23 per side) and 3D (1-8 per side) grids, degenerate
+    sides of 1 included, at 0 (automatic) to 5 levels: the geometric
+    ordering equals the oracle's, and every third plan too."""
+    rng = np.random.default_rng(5)
+    for t in range(100):
+        if t % 2:
+            dims = (int(rng.integers(1, 24)), int(rng.integers(1, 24)))
+        else:
+            dims = (int(rng.integers(1, 9)), int(rng.integers(1, 9)), int(rng.integers(1, 9)))
+        L = int(rng.integers(0, 6))
+        N = int(np.prod(dims))
+        rp, ci, va = convdiff(dims, np.ones(N), np.ones((N, len(dims))))[:3]
+        ol = sq.spaqr_order(rp, ci, dims, L)
+        arr = ol.arrays()
+        o = nd_order(dims, L if L > 0 else None)
+        for k in ("perm", "atom_ptr", "atom_node", "node_level"):
+            np.testing.assert_array_equal(arr[k], getattr(o, k), err_msg=f"{dims} L={L} {k}")
+        if t % 3 == 0:
+            F = osq.factor(N, rp, ci, va, dims, 1e-2, nlevels=o.L, skip=1, ordering=o)
+            plan = ol.plan()
+            assert len(plan) == len(F.steps)
+            for st_l, st_o in zip(plan, F.steps):
+                assert st_l["clusters"] == sorted(st_o["sizes"].keys())
+                assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
