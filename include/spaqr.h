@@ -190,8 +190,9 @@ int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_orde
  *     (duplicates summed, explicit zeros dropped) by shortest augmenting
  *     paths with dual potentials; A->val NULL makes every entry 1.
  * Row r then sits with its matched column.  Errors as spaqr_order, plus
- * INVALID_ARG for another `matching`, and SINGULAR when no perfect matching
- * exists on the nonzero values (an empty column included). */
+ * INVALID_ARG for another `matching` or a NaN / infinite value in A->val,
+ * and SINGULAR when no perfect matching exists on the nonzero values (an
+ * empty column included). */
 int spaqr_order_general(const spaqr_csr* A, int nlevels, int matching, spaqr_ordering** out);
 
 /* Ordering of a batch of independent matrices A[0..count-1] on grids

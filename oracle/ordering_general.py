@@ -58,6 +58,7 @@ Readings (also in the design notes):
       free column at distance D; every column k settled meanwhile gets
       v_k -= D - d_k, its matched row u += D - d_k, the start row u += D; the
       path is then flipped.  No path: structurally singular.
+  Both matchings order entries by |a_ij|: a NaN or infinite value is refused.
 """
 import heapq
 import math
@@ -263,6 +264,8 @@ def nd_general(n, rowptr, colind, val=None, L=None, matching="greedy"):
     """
     if matching not in ("greedy", "max_product"):
         raise ValueError("matching must be 'greedy' or 'max_product'")
+    if val is not None and not np.all(np.isfinite(np.asarray(val, dtype=np.float64))):
+        raise ValueError("non-finite matrix value: the matchings order entries by |a_ij|")
     rowptr = np.asarray(rowptr, dtype=np.int64)
     colind = np.asarray(colind, dtype=np.int64)
     if L is None or L <= 0:

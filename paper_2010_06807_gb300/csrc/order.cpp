@@ -738,25 +738,30 @@ struct GeneralND {
 // matching exists.
 int row_matching(const int64_t* rp, const int32_t* ci, const double* val, int64_t n, std::vector<int64_t>& rowcol) {
     const int64_t nnz = rp[n];
-    std::vector<int64_t> rows(nnz), ord(nnz);
+    // entries by decreasing |a_ij|, ties by row then column (entries equal in
+    // all three are one (row, column) pair: their order does not matter)
+    struct Entry {
+        double mag;
+        int64_t r;
+        int32_t c;
+    };
+    std::vector<Entry> ent(nnz);
     for (int64_t r = 0; r < n; r++)
-        for (int64_t e = rp[r]; e < rp[r + 1]; e++) rows[e] = r;
-    for (int64_t e = 0; e < nnz; e++) ord[e] = e;
-    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
-        const double ma = val ? std::fabs(val[a]) : 1.0, mb = val ? std::fabs(val[b]) : 1.0;
-        if (ma != mb) return ma > mb;
-        if (rows[a] != rows[b]) return rows[a] < rows[b];
-        return ci[a] < ci[b];
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++) ent[e] = Entry{val ? std::fabs(val[e]) : 1.0, r, ci[e]};
+    std::sort(ent.begin(), ent.end(), [](const Entry& a, const Entry& b) {
+        if (a.mag != b.mag) return a.mag > b.mag;
+        if (a.r != b.r) return a.r < b.r;
+        return a.c < b.c;
     });
     rowcol.assign(n, -1);
     std::vector<int64_t> colrow(n, -1);
-    for (int64_t e : ord) {
-        const int64_t r = rows[e], c = ci[e];
-        if (rowcol[r] < 0 && colrow[c] < 0) {
-            rowcol[r] = c;
-            colrow[c] = r;
+    for (const Entry& x : ent) {
+        if (rowcol[x.r] < 0 && colrow[x.c] < 0) {
+            rowcol[x.r] = x.c;
+            colrow[x.c] = x.r;
         }
     }
+    std::vector<Entry>().swap(ent);
     // sorted distinct columns of every row, for the augmenting paths
     std::vector<int64_t> cp(n + 1, 0), cc;
     for (int64_t r = 0; r < n; r++) {
@@ -958,6 +963,10 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
     if (check_rowptr(rowptr, n, nnz) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     for (int64_t e = 0; e < nnz; e++)
         if (colind[e] < 0 || colind[e] >= n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    // the matchings order entries by |a_ij|: a NaN has no place in that order
+    if (val)
+        for (int64_t e = 0; e < nnz; e++)
+            if (!std::isfinite(val[e])) { set_error("non-finite matrix value"); return SPAQR_ERR_INVALID_ARG; }
     o.dim = 0;
     o.dims[0] = (int)std::min<int64_t>(n, 0x7fffffff);
     o.dims[1] = o.dims[2] = 1;

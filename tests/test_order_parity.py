@@ -348,3 +348,20 @@ def test_grid_ordering_random_shapes(spaqr_lib):
             for st_l, st_o in zip(plan, F.steps):
                 assert st_l["clusters"] == sorted(st_o["sizes"].keys())
                 assert [f["id"] for f in st_l["fronts"]] == list(st_o["order"])
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_general_ordering_rejects_non_finite_values(spaqr_lib, bad):
+    """The matchings order entries by |a_ij|; a NaN or infinite value is
+    refused (INVALID_ARG) by the host and the oracle alike."""
+    from oracle.ordering_general import nd_general
+    g = config_problem("2d_uniform_a", n=6)
+    v = g.val.copy()
+    v[7] = bad
+    for m in ("greedy", "max_product"):
+        with pytest.raises(sq.SpaqrError) as e:
+            sq.spaqr_order(g.rowptr, g.colind, None, 2, val=v, matching=m)
+        assert e.value.name == "INVALID_ARG"
+        with pytest.raises(ValueError):
+            nd_general(g.n, g.rowptr, g.colind, v, 2, matching=m)
+    sq.spaqr_order(g.rowptr, g.colind, None, 2, val=None)   # pattern only: no values to check
