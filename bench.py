@@ -638,7 +638,9 @@ def ours(a):
         "roofline": roof,
         "clocks": clk,
     }
-    if a.no_extras:
+    # the other forms, the extra workloads and the CPU baselines run at N = 1
+    # only: under torchrun the other ranks would wait at the final barrier
+    if a.no_extras or world > 1:
         print(json.dumps(line))
         if world > 1:
             dist.barrier()
