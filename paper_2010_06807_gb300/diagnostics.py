@@ -6,11 +6,19 @@ sizes the factorisation time, the factor's device memory and the size of the
 top separator against N.
 
 Everything comes from the factor through the C ABI (spaqr_factor_level,
-spaqr_factor_pivots, spaqr_factor_ranks, spaqr_factor_info); the inputs are the
+spaqr_factor_pivots, spaqr_factor_ranks, spaqr_factor_info); the plan report
+comes from the ordering alone (spaqr_ordering_get).  The inputs are the
 seeded synthetic matrices of synth.convdiff.
 
     python -m paper_2010_06807_gb300.diagnostics --kind 3d_uniform_a \\
         --sizes 16 32 48 64 --eps 1e-2 [--scaling 0] [--json out.json]
+
+The symbolic plan alone (host only, no GPU): front and interface sizes per
+level before sparsification and the atom counts, for the geometric ordering
+or, with --permute SEED, the grid-free ordering of the permuted matrix:
+
+    python -m paper_2010_06807_gb300.diagnostics --plan-only --kind 2d_lognormal \\
+        --sizes 128 256 [--permute 11 [--matching max_product]]
 """
 import argparse
 import json
@@ -32,6 +40,66 @@ def pivot_decay(norms_list, at=DECAY_AT):
         vals = [nm[k - 1] / nm[0] for nm in norms_list if len(nm) >= k and nm[0] > 0]
         out[k] = float(np.median(vals)) if vals else None
     return out
+
+
+def plan_report(ordering):
+    """Host-only summary of an ordering's symbolic plan (no factorisation, no
+    GPU): per level (0 = leaves) the fronts (count, sizes |s|, heights = the
+    summed sizes of their row clusters) and the interfaces left after them
+    (count, sizes), all before sparsification; plus the atom counts.
+    Cluster sizes come from the atoms: an active cluster spans the atoms from
+    its first one up to the next active cluster of the same node (the
+    clusters of a node partition its atoms at every level)."""
+    arr = ordering.arrays()
+    atom_ptr, atom_node = arr["atom_ptr"], arr["atom_node"]
+    na = atom_node.shape[0]
+    node_end = {}
+    for a in range(na):
+        node_end[int(atom_node[a])] = a + 1
+    leaf_level = int(arr["node_level"].max()) if arr["node_level"].size else 1
+    sep_atoms = np.array([atom_ptr[a + 1] - atom_ptr[a] for a in range(na)
+                          if arr["node_level"][atom_node[a]] < leaf_level], dtype=np.int64)
+    rows = []
+    for k, st in enumerate(ordering.plan()):
+        cl = sorted(st["clusters"])
+        size = {}
+        for i, c in enumerate(cl):
+            nd = int(atom_node[c])
+            end = node_end[nd]
+            if i + 1 < len(cl) and int(atom_node[cl[i + 1]]) == nd:
+                end = cl[i + 1]
+            size[c] = int(atom_ptr[end] - atom_ptr[c])
+        fronts = [f["id"] for f in st["fronts"]]
+        fs = set(fronts)
+        s_sizes = [size[f] for f in fronts]
+        heights = [sum(size[r] for r in f["R"]) for f in st["fronts"]]
+        inter = [size[c] for c in cl if c not in fs]
+        rows.append({"level": k, "clusters": len(cl), "n_fronts": len(fronts),
+                     "front_cols": int(sum(s_sizes)), "max_front": max(s_sizes) if s_sizes else 0,
+                     "max_front_rows": max(heights) if heights else 0,
+                     "n_interfaces": len(inter), "interface_cols": int(sum(inter)),
+                     "max_interface": max(inter) if inter else 0,
+                     "median_interface": float(np.median(inter)) if inter else 0.0})
+    return {"n": int(ordering.n), "levels": ordering.L, "atoms": int(na),
+            "separator_atoms": int(sep_atoms.size),
+            "separator_atom_median": float(np.median(sep_atoms)) if sep_atoms.size else 0.0,
+            "separator_atoms_le2": int((sep_atoms <= 2).sum()), "per_level": rows}
+
+
+def plan_markdown(rep, title):
+    """Table of a plan_report result."""
+    lines = [f"### {title}", "",
+             f"N = {rep['n']}, {rep['levels']} levels, {rep['atoms']} atoms ({rep['separator_atoms']} in "
+             f"separators: median {rep['separator_atom_median']:g} columns, {rep['separator_atoms_le2']} of at "
+             "most 2)", "",
+             "| level | clusters | fronts | front columns | largest front (rows x cols) | interfaces after |"
+             " interface columns | largest / median interface |",
+             "|---|---|---|---|---|---|---|---|"]
+    for r in rep["per_level"]:
+        lines.append(f"| {r['level']} | {r['clusters']} | {r['n_fronts']} | {r['front_cols']} | "
+                     f"{r['max_front_rows']} x {r['max_front']} | {r['n_interfaces']} | {r['interface_cols']} | "
+                     f"{r['max_interface']} / {r['median_interface']:g} |")
+    return "\n".join(lines)
 
 
 def level_report(F):
@@ -127,7 +195,32 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--json")
+    ap.add_argument("--plan-only", action="store_true",
+                    help="host only: the symbolic plan of each size's ordering, no factorisation")
+    ap.add_argument("--permute", type=int, default=None, metavar="SEED",
+                    help="with --plan-only: permute rows and columns and use the grid-free ordering")
+    ap.add_argument("--matching", default="greedy", help="row matching of the grid-free ordering")
     a = ap.parse_args(argv)
+    if a.plan_only:
+        from synth.convdiff import config_problem, permuted
+        reps = []
+        for n in a.sizes:
+            p = config_problem(a.kind, n=n)
+            if a.permute is None:
+                o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+                how = "geometric ordering"
+            else:
+                p = permuted(p, a.permute)
+                o = sq.spaqr_order(p.rowptr, p.colind, None, val=p.val, matching=a.matching)
+                how = f"rows and columns permuted (seed {a.permute}), grid-free ordering, {a.matching} matching"
+            rep = plan_report(o)
+            reps.append(rep)
+            print(plan_markdown(rep, f"{a.kind}, side {n}: {how}"))
+            print()
+        if a.json:
+            with open(a.json, "w") as f:
+                json.dump(reps, f, indent=1)
+        return 0
     study = scaling_study(a.kind, a.sizes, a.eps, a.scaling, a.precision, gmres=not a.no_gmres)
     if a.json:
         with open(a.json, "w") as f:

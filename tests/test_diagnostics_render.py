@@ -32,3 +32,31 @@ def test_markdown_survives_json_round_trip():
     assert a == b
     assert "| 8 | 64 | 1 | 1.5 | 1 | 16384 | 5 | 18 / 30 | 4 |" in a
     assert "1.0e+00 3.8e-01 -" in a
+
+
+def test_plan_report_invariants():
+    """The host-only plan report (no GPU): without sparsification every
+    unknown is a front column exactly once, and each level's interfaces are
+    the next level's fronts and interfaces; level 0 holds every atom."""
+    import paper_2010_06807_gb300 as sq
+    from paper_2010_06807_gb300.diagnostics import plan_markdown, plan_report
+    from synth.convdiff import config_problem, permuted, random_local
+    g = config_problem("2d_lognormal", n=48)
+    q = permuted(g, 3)
+    r = random_local(20, seed=7050)
+    c = config_problem("3d_uniform_a", n=9)
+    cases = [sq.spaqr_order(g.rowptr, g.colind, g.dims),
+             sq.spaqr_order(q.rowptr, q.colind, None, val=q.val),
+             sq.spaqr_order(r.rowptr, r.colind, None, val=r.val, matching="max_product"),
+             sq.spaqr_order(c.rowptr, c.colind, c.dims)]
+    for o in cases:
+        rep = plan_report(o)
+        lv = rep["per_level"]
+        assert len(lv) == o.L and lv[0]["clusters"] == rep["atoms"]
+        assert sum(x["front_cols"] for x in lv) == o.n
+        assert lv[0]["front_cols"] + lv[0]["interface_cols"] == o.n
+        for a, b in zip(lv, lv[1:]):
+            assert a["interface_cols"] == b["front_cols"] + b["interface_cols"]
+            assert a["n_interfaces"] >= b["clusters"]          # interfaces only merge
+        assert lv[-1]["n_interfaces"] == 0 and lv[-1]["n_fronts"] == 1
+        assert plan_markdown(rep, "t").count("\n|") == o.L + 2   # header, rule, one row per level
