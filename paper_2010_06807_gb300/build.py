@@ -17,7 +17,8 @@ OUT = os.path.join(HERE, "libspaqr.so")
 BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-lineinfo", "-I", INCLUDE, "-I", CSRC]
+COMMON = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-lineinfo", "-I", INCLUDE,
+          "-I", CSRC]
 
 
 def _nvcc():
@@ -73,7 +74,7 @@ def build(force=False, verbose=False):
                 sys.stderr.write(r.stdout + r.stderr)
             objs.append(obj)
     tmp = OUT + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)

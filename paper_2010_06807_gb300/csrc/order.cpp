@@ -32,6 +32,8 @@
 #include <map>
 #include <queue>
 #include <set>
+#include <thread>
+#include <exception>
 #include <string>
 #include <tuple>
 #include <unordered_map>
@@ -679,18 +681,25 @@ struct GeneralND {
         for (int32_t x : keep) loc[x] = -1;
         return H;
     }
-    // node of column set G (released on return unless it is the root)
-    int build(SubGraph& G, int depth, int parent) {
-        const int id = (int)nodes.size();
-        nodes.push_back(NDNode());
-        pts.emplace_back();
-        nodes[id].id = id;
-        nodes[id].depth = depth;
-        nodes[id].parent = parent;
+    // The nested-dissection subtree of column set G, nodes in preorder with
+    // ids local to the subtree (its root is node 0, parent -1).  G is released
+    // once its children's subgraphs exist, unless it is the root graph.  With
+    // threads > 1 the two child subtrees are built concurrently: they share
+    // nothing, and splicing them under the parent in preorder gives the same
+    // tree whatever the timing.
+    struct Tree {
+        std::vector<NDNode> nodes;
+        std::vector<std::vector<int64_t>> pts;
+    };
+    Tree build(SubGraph& G, int depth, int threads) {
+        Tree T;
+        T.nodes.emplace_back();
+        T.pts.emplace_back();
+        T.nodes[0].depth = depth;
         if (depth == L - 1) {
-            pts[id] = G.gid;
+            T.pts[0] = G.gid;
             if (&G != &root) G = SubGraph();
-            return id;
+            return T;
         }
         const int64_t m = G.size();
         std::vector<int32_t> S, Lf, Rt;
@@ -723,14 +732,49 @@ struct GeneralND {
         for (size_t i = 0; i < S.size(); i++) sep[i] = G.gid[S[i]];
         if (&G != &root) G = SubGraph();
         { std::vector<int32_t>().swap(loc); std::vector<int32_t>().swap(Lf); std::vector<int32_t>().swap(Rt); }
-        const int left = build(GL, depth + 1, id);
-        const int right = build(GR, depth + 1, id);
-        nodes[id].left = left;
-        nodes[id].right = right;
-        nodes[id].cut_dim = 0;
-        nodes[id].size = 1 + nodes[left].size + nodes[right].size;
-        pts[id] = std::move(sep);
-        return id;
+        Tree A, B;
+        if (threads > 1) {
+            std::exception_ptr err;
+            std::thread th([&] {
+                try {
+                    A = build(GL, depth + 1, threads / 2);
+                } catch (...) {
+                    err = std::current_exception();
+                }
+            });
+            try {
+                B = build(GR, depth + 1, threads - threads / 2);
+            } catch (...) {
+                th.join();
+                throw;
+            }
+            th.join();
+            if (err) std::rethrow_exception(err);
+        } else {
+            A = build(GL, depth + 1, 1);
+            B = build(GR, depth + 1, 1);
+        }
+        const int na = (int)A.nodes.size(), nb = (int)B.nodes.size();
+        auto splice = [&](Tree& X, int off) {
+            for (NDNode nd : X.nodes) {
+                nd.id += off;
+                nd.parent = nd.parent < 0 ? 0 : nd.parent + off;
+                if (nd.left >= 0) nd.left += off;
+                if (nd.right >= 0) nd.right += off;
+                T.nodes.push_back(nd);
+            }
+            for (auto& p : X.pts) T.pts.push_back(std::move(p));
+        };
+        T.nodes.reserve(1 + na + nb);
+        T.pts.reserve(1 + na + nb);
+        splice(A, 1);
+        splice(B, 1 + na);
+        T.nodes[0].left = 1;
+        T.nodes[0].right = 1 + na;
+        T.nodes[0].cut_dim = 0;
+        T.nodes[0].size = 1 + na + nb;
+        T.pts[0] = std::move(sep);
+        return T;
     }
 };
 
@@ -994,7 +1038,12 @@ int build_ordering_general(const int64_t* rowptr, const int32_t* colind, const d
     g.n = n;
     g.L = o.L;
     g.graph(rowptr, colind);
-    g.build(g.root, 0, -1);
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        GeneralND::Tree T = g.build(g.root, 0, (int)std::max(1u, std::min(hw, 8u)));
+        g.nodes = std::move(T.nodes);
+        g.pts = std::move(T.pts);
+    }
     const int nn = (int)g.nodes.size();
     std::vector<int> owner(n, -1);
     for (int id = 0; id < nn; id++)
