@@ -547,7 +547,8 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
 //    column index as the index;
 //  * rows: entries by decreasing |a_ij| (ties: row, column) matched greedily,
 //    then every unmatched row (ascending) by an augmenting path (columns of a
-//    row in ascending order, depth first); row r sits with its column.
+//    row in ascending order, depth first), or the maximum-product matching
+//    (row_matching_max_product); row r sits with its column.
 // ---------------------------------------------------------------------------
 // G(A^T A) restricted to a column set: local vertices in ascending global
 // order, each with its neighbours inside the set (ascending).  Because the
