@@ -385,14 +385,18 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
             }
         }
         std::vector<std::vector<int>> Rf(fr.size()), Cf(fr.size());
+        std::vector<int> seen_by(ncl, -1);   // front that last took column cluster j
         for (size_t t = 0; t < fr.size(); t++) {
             int s = fr[t];
-            Rf[t] = col_rows[s];  // ascending (set order)
-            std::set<int> cs;
+            Rf[t] = col_rows[s];  // ascending (pattern order)
+            std::vector<int>& cs = Cf[t];
             for (int i : Rf[t])
                 for (int j : row_cols[i])
-                    if (o.related(sp.cl_node[j], sp.cl_node[s])) cs.insert(j);
-            Cf[t].assign(cs.begin(), cs.end());
+                    if (seen_by[j] != (int)t && o.related(sp.cl_node[j], sp.cl_node[s])) {
+                        seen_by[j] = (int)t;
+                        cs.push_back(j);
+                    }
+            std::sort(cs.begin(), cs.end());
             if (Rf[t].empty() || Rf[t][0] != s || Cf[t][0] != s) {
                 set_error("front without its diagonal block");
                 return SPAQR_ERR_SINGULAR;
