@@ -330,6 +330,9 @@ def spaqr_order(rowptr, colind, dims, nlevels=0, val=None, matching="greedy"):
     augmenting paths) or "max_product" (the perfect matching maximising the
     product of the matched |a_ij|)."""
     load_library()
+    if dims is not None and matching != "greedy":
+        raise ValueError("a row matching applies to the grid-free ordering (dims None); "
+                         "grid orderings keep every row with its column")
     csr, keep = _make_csr(rowptr, colind, val if dims is None else None)
     h = ctypes.c_void_p()
     if dims is None:

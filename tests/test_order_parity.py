@@ -205,6 +205,8 @@ def test_general_ordering_matching_errors(spaqr_lib):
     g = config_problem("2d_uniform_a", n=6)
     with pytest.raises(ValueError):
         sq.spaqr_order(g.rowptr, g.colind, None, 2, val=g.val, matching="mc64")
+    with pytest.raises(ValueError):   # grids keep every row with its column
+        sq.spaqr_order(g.rowptr, g.colind, g.dims, 2, matching="max_product")
     # an unknown matching code at the C ABI
     csr, keep = sq._make_csr(g.rowptr, g.colind, g.val)
     h = ctypes.c_void_p(1)
