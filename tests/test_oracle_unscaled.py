@@ -158,3 +158,38 @@ def test_fine_column_sign_rule_is_benign(monkeypatch):
         x = spaqr.solve(F0, b)
         assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) < 1e-12
     assert abs(its[0] - its[1]) <= 1, its
+
+
+def _general_cases():
+    from oracle.ordering_general import nd_general
+    from synth.convdiff import permuted, random_local
+    q = permuted(config_problem("2d_uniform_a", n=24), 61)
+    r = random_local(20, seed=7060)
+    w = random_local(20, seed=7061, weak_diag=0.1)
+    return [("permuted_grid", q, nd_general(q.n, q.rowptr, q.colind, q.val, 4)),
+            ("random_local", r, nd_general(r.n, r.rowptr, r.colind, r.val, 4)),
+            ("weak_diag_max_product", w, nd_general(w.n, w.rowptr, w.colind, w.val, 4, matching="max_product"))]
+
+
+@pytest.mark.parametrize("name,p,o", _general_cases())
+def test_unscaled_on_grid_free_orderings(name, p, o):
+    """The unscaled variant on matrices without a grid (rows matched to
+    columns): eps = 0 solves exactly, and Lemma 1's identity
+    sigma R_ff^T R_fn = W_fn^(2) holds at eps = 1e-2 on every interface
+    that drops something."""
+    b = np.random.default_rng(9).standard_normal((p.n, 2))
+    F0 = spaqr.factor(p.n, p.rowptr, p.colind, p.val, None, 0.0, nlevels=o.L, skip=0, ordering=o, scaling=False)
+    x = spaqr.solve(F0, b)
+    assert np.max(np.linalg.norm(b - p.matvec(x), axis=0) / np.linalg.norm(b, axis=0)) < 1e-11
+    F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, None, 1e-2, nlevels=o.L, skip=0, ordering=o, scaling=False)
+    checked = 0
+    for c, d in _interfaces(F):
+        if d["Rff"].shape[0] == 0 or not d["Rfn"]:
+            continue
+        Rfn = np.hstack([B for _, B in sorted(d["Rfn"], key=lambda t: t[0])])
+        W2 = d["Wfn2"]
+        scale = d["sigma"] * np.linalg.norm(d["App"], 2) * np.linalg.norm(d["Apn"], 2)
+        lhs = d["sigma"] * d["Rff"].T @ Rfn
+        assert np.linalg.norm(lhs - W2) <= 1e-12 * scale * np.sqrt(W2.size) + 1e-12 * np.linalg.norm(W2)
+        checked += 1
+    assert checked >= 1
