@@ -234,3 +234,17 @@ def test_max_product_ordering_factor_and_gmres():
         _, its[m], rr, _ = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: spaqr.solve(F, v))
         assert rr <= 1e-12
     assert its["max_product"] < its["greedy"], its
+
+
+@pytest.mark.parametrize("matching", ["greedy", "max_product"])
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+def test_preconditioned_operator_O_eps_on_grid_free_orderings(matching, eps):
+    """Section 3.3 on grid-free orderings: the right-preconditioned operator
+    is I + O(eps), ||A M^{-1} - I||_2 < 20 eps as on grids (a permuted grid
+    matrix and a diagonally dominant random local one; something dropped)."""
+    for p in (permuted(config_problem("2d_uniform_a", n=24), 71), random_local(20, seed=7070)):
+        o = nd_general(p.n, p.rowptr, p.colind, p.val, 4, matching=matching)
+        F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, None, eps, nlevels=4, skip=0, ordering=o)
+        AM = p.to_dense() @ spaqr.solve(F, np.eye(p.n))
+        assert np.linalg.norm(AM - np.eye(p.n), 2) < 20 * eps
+        assert any(r < nb for R in F.ranks for (nb, r) in R.values())
