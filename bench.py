@@ -388,6 +388,31 @@ def _general(sq, torch, np, dev, st, flush):
     return out
 
 
+def _matchings(sq, torch, np, dev, st, flush):
+    """The two row matchings of the grid-free ordering on a matrix whose
+    large entries sit off the diagonal (random local, 64^2 points, diagonal
+    0.1 N(0,1)); 16 RHS, eps 1e-3, FP64, factor + GMRES to 1e-12.  A form
+    whose GMRES does not reach 1e-12 in the iteration limit is reported with
+    its residual (the oracle: greedy > 300 iterations, maximum product 34)."""
+    from synth.convdiff import random_local, rhs
+    p = random_local(64, seed=8003, weak_diag=0.1)
+    b = rhs(p, NRHS)
+    A = (torch.from_numpy(p.rowptr).to(dev), torch.from_numpy(p.colind).to(dev), torch.from_numpy(p.val).to(dev))
+    out = {"n": p.n, "nnz": p.nnz, "eps": 1e-3}
+    for m in ("greedy", "max_product"):
+        Bd = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
+        Xd = torch.zeros(NRHS, p.n, dtype=torch.float64, device=dev).T
+        try:
+            o = sq.spaqr_order(p.rowptr, p.colind, None, 0, val=p.val, matching=m)
+            res, _ = _timed_form(sq, torch, o, A, Bd, Xd, st, flush, 1e-3, "fp64", 2, 1)
+            out[m] = res
+        except sq.SpaqrError as e:
+            it, rr = getattr(e, "iters", None), getattr(e, "relres", None)
+            out[m] = {"error": e.name, "gmres_iters_max": None if it is None else int(np.max(it)),
+                      "relres_max": None if rr is None else float(np.max(rr))}
+    return out
+
+
 def _batched(sq, torch, np, dev, st, flush, count=64, steps=3, warmup=1):
     """Batched workload: `count` independent 2D problems (sides from
     {32,48,...,128}, a ~ U[0.1,10], v = Pe (1,1), Pe ~ U[1,100]), one RHS per
@@ -693,6 +718,10 @@ def ours(a):
             srv[prec] = run_workload(duration=a.serve_s, precision=prec, device=dev)
         srv["plain_fp64_one_at_a_time"] = run_plain(requests=200, device=dev)
         line["serving_8x3d_poisson2000"] = srv
+    try:
+        line["row_matchings_weak_diagonal"] = _matchings(sq, torch, np, dev, st, flush)
+    except Exception as e:  # report, do not hide
+        line["row_matchings_weak_diagonal"] = {"error": repr(e)}
     if not a.no_cpu_baseline:
         try:
             r = run_oracle(1, parallel=min(host_cores(), NRHS))
