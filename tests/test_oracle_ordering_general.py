@@ -248,3 +248,26 @@ def test_preconditioned_operator_O_eps_on_grid_free_orderings(matching, eps):
         AM = p.to_dense() @ spaqr.solve(F, np.eye(p.n))
         assert np.linalg.norm(AM - np.eye(p.n), 2) < 20 * eps
         assert any(r < nb for R in F.ranks for (nb, r) in R.values())
+
+
+def _golden_path(case):
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in case["rows"]])]).astype(np.int64)
+    ci = np.asarray([c for r in case["rows"] for c, _ in r], dtype=np.int32)
+    va = np.asarray([v for r in case["rows"] for _, v in r], dtype=np.float64)
+    return rp, ci, va
+
+
+def test_golden_hand_derived_paths():
+    """Hand-derived orderings (tests/golden/general_paths.json, derived from
+    the readings G1-G5 and R6, not by code): tridiagonal matrices and a case
+    where a separator column touches both child subtrees of a node but not
+    its separator; separators, atoms, their order and the matched rows."""
+    import json
+    import os
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "general_paths.json")))
+    for case in golden["cases"]:
+        rp, ci, va = _golden_path(case)
+        o = nd_general(case["n"], rp, ci, va, case["L"])
+        assert [list(nd.pts) for nd in o.nodes] == case["node_pts"], case["name"]
+        for k in ("perm", "atom_ptr", "atom_node", "rperm"):
+            assert getattr(o, k).tolist() == case[k], (case["name"], k)
