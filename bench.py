@@ -383,7 +383,7 @@ def _general(sq, torch, np, dev, st, flush):
         Bd = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
         Xd = torch.zeros(NRHS, p.n, dtype=torch.float64, device=dev).T
         res, _ = _timed_form(sq, torch, o, A, Bd, Xd, st, flush, EPS, "fp64", 3, 1)
-        res.update(order_ms=order_ms, n=p.n, nnz=p.nnz, levels=o.L)
+        res.update(order_ms=order_ms, n=p.n, nnz=p.nnz, levels=o.L, atoms=o.n_atoms)
         out[name] = res
     return out
 
@@ -405,6 +405,7 @@ def _matchings(sq, torch, np, dev, st, flush):
         try:
             o = sq.spaqr_order(p.rowptr, p.colind, None, 0, val=p.val, matching=m)
             res, _ = _timed_form(sq, torch, o, A, Bd, Xd, st, flush, 1e-3, "fp64", 2, 1)
+            res.update(atoms=o.n_atoms)
             out[m] = res
         except sq.SpaqrError as e:
             it, rr = getattr(e, "iters", None), getattr(e, "relres", None)
