@@ -32,6 +32,7 @@
 #include <map>
 #include <queue>
 #include <set>
+#include <system_error>
 #include <thread>
 #include <exception>
 #include <string>
@@ -738,15 +739,22 @@ struct GeneralND {
         if (&G != &root) G = SubGraph();
         { std::vector<int32_t>().swap(loc); std::vector<int32_t>().swap(Lf); std::vector<int32_t>().swap(Rt); }
         Tree A, B;
+        std::thread th;
+        std::exception_ptr err;
         if (threads > 1) {
-            std::exception_ptr err;
-            std::thread th([&] {
-                try {
-                    A = build(GL, depth + 1, threads / 2);
-                } catch (...) {
-                    err = std::current_exception();
-                }
-            });
+            try {
+                th = std::thread([&] {
+                    try {
+                        A = build(GL, depth + 1, threads / 2);
+                    } catch (...) {
+                        err = std::current_exception();
+                    }
+                });
+            } catch (const std::system_error&) {
+                threads = 1;   // no thread to be had: the same tree, serially
+            }
+        }
+        if (threads > 1) {
             try {
                 B = build(GR, depth + 1, threads - threads / 2);
             } catch (...) {
