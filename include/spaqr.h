@@ -61,7 +61,10 @@ extern "C" {
 
 /* Sparse matrix in CSR form, rows sorted, N x N.  rowptr has n+1 entries,
  * colind/val have nnz entries.  If on_device != 0 the three arrays are device
- * pointers, otherwise host pointers.  Borrowed for the duration of a call. */
+ * pointers, otherwise host pointers; every call that takes a spaqr_csr checks
+ * this against where the arrays are (INVALID_ARG for device memory flagged
+ * as host or plain host memory flagged as device; pinned and managed memory
+ * pass either way).  Borrowed for the duration of a call. */
 typedef struct {
     int64_t n, nnz;
     const int64_t* rowptr;

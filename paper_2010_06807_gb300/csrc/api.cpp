@@ -28,6 +28,30 @@ extern "C" void spaqr_opts_default(spaqr_opts* o) {
     o->stream = nullptr;
 }
 
+namespace spaqr {
+// A->on_device must say where the arrays are: device memory flagged as host
+// would be read by the host, plain host memory flagged as device by the
+// kernels.  Pinned and managed memory are readable from both sides.
+int check_csr_location(const spaqr_csr* A) {
+    const void* ps[3] = {A->rowptr, A->colind, A->val};
+    for (const void* p : ps) {
+        if (!p) continue;
+        cudaPointerAttributes a;
+        cudaMemoryType t = cudaMemoryTypeUnregistered;
+        if (cudaPointerGetAttributes(&a, p) == cudaSuccess)
+            t = a.type;
+        else
+            cudaGetLastError();
+        if (A->on_device ? t == cudaMemoryTypeUnregistered : t == cudaMemoryTypeDevice) {
+            set_error(A->on_device ? "A->on_device is set but an array is plain host memory"
+                                   : "A->on_device is 0 but an array is device memory");
+            return SPAQR_ERR_INVALID_ARG;
+        }
+    }
+    return SPAQR_OK;
+}
+}  // namespace spaqr
+
 namespace {
 int order_impl(const spaqr_csr* A, const spaqr_grid* g, int nlevels, int matching, spaqr_ordering** out) {
     if (!out) { spaqr::set_error("out is NULL"); return SPAQR_ERR_INVALID_ARG; }
@@ -38,6 +62,7 @@ int order_impl(const spaqr_csr* A, const spaqr_grid* g, int nlevels, int matchin
         return SPAQR_ERR_INVALID_ARG;
     }
     if (nlevels < 0 || nlevels > 40) { spaqr::set_error("nlevels out of range"); return SPAQR_ERR_INVALID_ARG; }
+    if (spaqr::check_csr_location(A) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     std::vector<int64_t> rp;
     std::vector<int32_t> ci;
     const int64_t* rowptr = A->rowptr;
@@ -116,6 +141,7 @@ extern "C" int spaqr_order_batch(int count, const spaqr_csr* A, const spaqr_grid
             spaqr::set_error("bad CSR sizes or pointers of matrix " + std::to_string(i));
             return SPAQR_ERR_INVALID_ARG;
         }
+        if (spaqr::check_csr_location(&Ai) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
         rowptrs[i] = Ai.rowptr;
         colinds[i] = Ai.colind;
         if (Ai.on_device) {

@@ -2041,6 +2041,7 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
         set_error("matrix does not match the ordering's pattern");
         return SPAQR_ERR_INVALID_ARG;
     }
+    if (check_csr_location(A) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     if (!(opts->eps >= 0.0) || opts->skip < 0) { set_error("eps must be >= 0 and skip >= 0"); return SPAQR_ERR_INVALID_ARG; }
     if (opts->nlevels != 0 && opts->nlevels != ord->o.L) {
         set_error("opts.nlevels differs from the ordering's level count");

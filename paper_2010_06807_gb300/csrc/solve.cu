@@ -1448,6 +1448,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         set_error("A does not match the factored pattern (nnz) or has NULL arrays");
         return SPAQR_ERR_INVALID_ARG;
     }
+    if (check_csr_location(A) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     if (!A->on_device) {
         if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
         for (int64_t r = 0; r < A->n; r++)

@@ -111,6 +111,7 @@ bool prof_on();
 void keep_pool_memory(int device);
 bool graphs_on();
 bool fail_this_alloc();   // fault injection (spaqr_test_fail_alloc)
+int check_csr_location(const spaqr_csr* A);   // A->on_device against where the arrays are
 
 }  // namespace spaqr
 

@@ -89,3 +89,21 @@ def test_host_only_error_paths(spaqr_lib):
     assert spaqr_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g2), 0, ctypes.byref(h)) == INVALID
     assert b"grid" in spaqr_lib.spaqr_last_error()
     del keep
+
+
+def test_csr_location_flag_checked(spaqr_lib):
+    """A->on_device must say where the arrays are: host arrays flagged as
+    device memory are refused (INVALID_ARG) before anything reads them."""
+    import ctypes
+
+    from synth.convdiff import config_problem
+    p = config_problem("2d_uniform_a", n=6)
+    csr, keep = sq._make_csr(p.rowptr, p.colind, p.val)
+    csr.on_device = 1
+    g = sq._Grid(2, 6, 6, 1)
+    h = ctypes.c_void_p()
+    assert spaqr_lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), 0, ctypes.byref(h)) == -1
+    assert b"host memory" in spaqr_lib.spaqr_last_error()
+    assert spaqr_lib.spaqr_order_general(ctypes.byref(csr), 0, 0, ctypes.byref(h)) == -1
+    assert not h.value
+    del keep

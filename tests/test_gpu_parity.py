@@ -204,3 +204,30 @@ def test_gmres_rejects_mismatched_or_bad_host_csr(dev):
     # the factor is untouched: the right matrix still converges
     _, it, rr = sq.spaqr_gmres(F, p.rowptr, p.colind, p.val, b, tol=1e-12)
     assert rr[0] <= 1e-12
+
+
+def test_csr_location_flag_checked_on_device(dev):
+    """Device arrays flagged as host memory are refused by the ordering, the
+    factorisation and GMRES before the host or a kernel reads them."""
+    import ctypes
+    p = config_problem("2d_uniform_a", n=16)
+    rp, ci, va = _to_dev(p, dev)
+    ordl = sq.spaqr_order(rp, ci, p.dims)
+    F = sq.spaqr_factor(ordl, rp, ci, va, eps=1e-2)
+    csr, keep = sq._make_csr(rp, ci, va)
+    assert csr.on_device == 1
+    csr.on_device = 0
+    h = ctypes.c_void_p()
+    g = sq._Grid(2, 16, 16, 1)
+    assert sq._lib.spaqr_order(ctypes.byref(csr), ctypes.byref(g), 0, ctypes.byref(h)) == -1
+    assert b"device memory" in sq._lib.spaqr_last_error()
+    o = sq._Opts()
+    sq._lib.spaqr_opts_default(ctypes.byref(o))
+    assert sq._lib.spaqr_factor(ordl._h, ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)) == -1
+    b = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    it = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1)
+    assert sq._lib.spaqr_gmres(F._h, ctypes.byref(csr), 1, b.data_ptr(), p.n, x.data_ptr(), p.n, 1e-12, 10,
+                               it.ctypes.data, rr.ctypes.data, None) == -1
+    del keep
