@@ -299,6 +299,17 @@ int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const dou
                 int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
                 double* relres, void* stream);
 
+/* spaqr_gmres with the residual history the paper's convergence figures plot
+ * (Section 4): `history` (host, nrhs * maxit doubles, not NULL) receives for
+ * column c at history[c * maxit + j] the Arnoldi estimate |g_{j+1}| / ||b_c||
+ * of the relative residual after iteration j + 1 (the quantity the stopping
+ * test reads), for j < iters[c]; the remaining entries are NaN.  The
+ * estimates are non-increasing.  Errors as spaqr_gmres, plus INVALID_ARG for
+ * a NULL history. */
+int spaqr_gmres_history(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B,
+                        int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
+                        double* relres, double* history, void* stream);
+
 /* GMRES for a batch factorised with a spaqr_order_batch ordering: A is the
  * block-diagonal CSR diag(A_0, ..., A_{count-1}) (n = part_ptr[count]), and
  * part_ptr[0..count] (host, int64) are the row offsets of the matrices

@@ -107,7 +107,7 @@ EXPORTS = [
     "spaqr_last_error", "spaqr_opts_default", "spaqr_order", "spaqr_order_general", "spaqr_order_batch",
     "spaqr_ordering_info",
     "spaqr_ordering_get", "spaqr_ordering_rows", "spaqr_ordering_destroy", "spaqr_factor", "spaqr_solve", "spaqr_solve_noalloc",
-    "spaqr_gmres", "spaqr_gmres_batch",
+    "spaqr_gmres", "spaqr_gmres_history", "spaqr_gmres_batch",
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
@@ -142,6 +142,8 @@ def load_library(path=None):
         if hasattr(lib, "spaqr_solve_noalloc"):
             lib.spaqr_solve_noalloc.argtypes = [vp, i32, vp, i64, vp, i64, vp]
         lib.spaqr_gmres.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp]
+        lib.spaqr_gmres_history.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp,
+                                            vp]
         lib.spaqr_gmres_batch.argtypes = [vp, ctypes.POINTER(_CSR), i32, vp, i32, vp, i64, vp, i64, dbl, i32,
                                           vp, vp, vp]
         lib.spaqr_factor_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -474,11 +476,13 @@ def spaqr_solve_noalloc(F, B, X, stream=None):
     return X
 
 
-def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=None):
-    """Right-preconditioned GMRES; returns (X, iters[nrhs], relres[nrhs]).
+def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=None, history=False):
+    """Right-preconditioned GMRES; returns (X, iters[nrhs], relres[nrhs]), and
+    with history=True also a list of per-column arrays: the Arnoldi estimate
+    of the relative residual after each iteration (spaqr_gmres_history).
 
     Raises SpaqrError(NOT_CONVERGED) if a column misses tol; the error carries
-    X, iters and relres.
+    X, iters and relres (and .history with history=True).
     """
     load_library()
     csr, keep = _make_csr(rowptr, colind, val)
@@ -496,9 +500,20 @@ def spaqr_gmres(F, rowptr, colind, val, B, X=None, tol=1e-12, maxit=300, stream=
     xp, ldx, nrx, kx, xdev = _dense_colmajor(X, F.n, "X")
     iters = np.zeros(nrhs, dtype=np.int32)
     relres = np.zeros(nrhs, dtype=np.float64)
-    _check_gmres(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
-                                  iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)), X, iters, relres)
-    return X, iters, relres
+    if not history:
+        _check_gmres(_lib.spaqr_gmres(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
+                                      iters.ctypes.data, relres.ctypes.data, _stream_ptr(stream)), X, iters, relres)
+        return X, iters, relres
+    hist = np.zeros((max(nrhs, 1), int(maxit)), dtype=np.float64)
+    rc = _lib.spaqr_gmres_history(F._h, ctypes.byref(csr), nrhs, bp, ldb, xp, ldx, float(tol), int(maxit),
+                                  iters.ctypes.data, relres.ctypes.data, hist.ctypes.data, _stream_ptr(stream))
+    per_col = [hist[c, :iters[c]].copy() for c in range(nrhs)]
+    try:
+        _check_gmres(rc, X, iters, relres)
+    except SpaqrError as e:
+        e.history = per_col
+        raise
+    return X, iters, relres, per_col
 
 
 def spaqr_gmres_batch(F, rowptr, colind, val, part_ptr, B, X=None, tol=1e-12, maxit=300, stream=None):

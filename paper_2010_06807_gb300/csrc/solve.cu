@@ -21,6 +21,7 @@
 #include <string>
 #include <type_traits>
 #include <vector>
+#include <limits>
 
 #include "dense.cuh"
 #include "spaqr_internal.h"
@@ -1433,9 +1434,12 @@ struct PrivateStream {
 // nseg = 1 for one matrix, nseg = count for a block-diagonal batch with
 // segment row offsets seg_ptr (host).  iters / relres per virtual column
 // v = c * nseg + s.
+// hist (host, may be null): nv x maxit, hist[v * maxit + j] = the Arnoldi
+// estimate of virtual column v's relative residual after iteration j + 1, NaN
+// once the column has stopped.
 int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, const int64_t* seg_ptr,
                const double* B, int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
-               double* relres, void* stream) {
+               double* relres, void* stream, double* hist = nullptr) {
     if (!F || !A || !B || !X) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
     if (A->n != F->n || nrhs < 0 || ldb < F->n || ldx < F->n || maxit < 1 || !(tol >= 0.0)) {
         set_error("bad size, leading dimension, tol or maxit");
@@ -1457,6 +1461,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
             if (A->colind[e] < 0 || A->colind[e] >= A->n) { set_error("column index out of range"); return SPAQR_ERR_INVALID_ARG; }
     }
     if (nrhs == 0) return SPAQR_OK;
+    if (hist) std::fill(hist, hist + (int64_t)nrhs * nseg * maxit, std::numeric_limits<double>::quiet_NaN());
     DeviceGuard dg(F->device);   // outlives the stream and allocations below
     keep_pool_memory(F->device);
     const bool graphs = graphs_on() && !prof_on();
@@ -1656,6 +1661,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
             hwant[v] = 0;
             if (!hact[v]) continue;
             hit[v] = j + 1;
+            if (hist) hist[(int64_t)v * maxit + j] = hest[v];
             if (hest[v] <= tol || hnv[v] == 0.0 || j == maxit - 1) { hwant[v] = 1; anyw = true; }
         }
         if (!anyw) continue;
@@ -1719,6 +1725,14 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
 extern "C" int spaqr_gmres(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B, int64_t ldb,
                            double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres, void* stream) {
     return gmres_impl(F, A, nrhs, 1, nullptr, B, ldb, X, ldx, tol, maxit, iters, relres, stream);
+}
+
+extern "C" int spaqr_gmres_history(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, const double* B,
+                                   int64_t ldb, double* X, int64_t ldx, double tol, int maxit, int* iters,
+                                   double* relres, double* history, void* stream) {
+    using namespace spaqr;
+    if (!history) { set_error("history is NULL (use spaqr_gmres)"); return SPAQR_ERR_INVALID_ARG; }
+    return gmres_impl(F, A, nrhs, 1, nullptr, B, ldb, X, ldx, tol, maxit, iters, relres, stream, history);
 }
 
 extern "C" int spaqr_gmres_batch(const spaqr_factor_t* F, const spaqr_csr* A, int count, const int64_t* part_ptr,

@@ -231,3 +231,40 @@ def test_csr_location_flag_checked_on_device(dev):
     assert sq._lib.spaqr_gmres(F._h, ctypes.byref(csr), 1, b.data_ptr(), p.n, x.data_ptr(), p.n, 1e-12, 10,
                                it.ctypes.data, rr.ctypes.data, None) == -1
     del keep
+
+
+def test_gmres_residual_history(dev):
+    """spaqr_gmres_history: per column the Arnoldi estimate of the relative
+    residual after every iteration -- non-increasing, at most tol when it
+    stopped the column -- equal to the oracle's estimates (MGS there, CGS2
+    here) over the first iterations; NaN after the column stopped."""
+    import ctypes
+    p = config_problem("2d_uniform_a", n=32)
+    rp, ci, va = _to_dev(p, dev)
+    F = sq.spaqr_factor(sq.spaqr_order(rp, ci, p.dims), rp, ci, va, eps=1e-2)
+    b = rhs(p, 2)
+    X, it, rr, hist = sq.spaqr_gmres(F, p.rowptr, p.colind, p.val, np.asfortranarray(b), tol=1e-12, history=True)
+    assert (rr <= 1e-12).all()
+    Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-2)
+    for c in range(2):
+        h = hist[c]
+        assert len(h) == it[c] and np.all(np.isfinite(h)) and h[-1] <= 1e-12
+        assert np.all(h[1:] <= h[:-1] * (1 + 1e-12))
+        _, ito, _, ho = osq.gmres(p.n, p.rowptr, p.colind, p.val, b[:, c], lambda v: osq.solve(Fo, v))
+        k = min(3, len(h), len(ho) - 1)
+        np.testing.assert_allclose(h[:k], np.asarray(ho[1:k + 1]), rtol=1e-6)
+    # the raw array: NaN after each column's last iteration
+    csr, keep = sq._make_csr(p.rowptr, p.colind, p.val)
+    maxit = 40
+    raw = np.zeros((2, maxit))
+    its = np.zeros(2, dtype=np.int32)
+    res = np.zeros(2)
+    Xh = np.zeros((p.n, 2), order="F")
+    bf = np.asfortranarray(b)
+    assert sq._lib.spaqr_gmres_history(F._h, ctypes.byref(csr), 2, bf.ctypes.data, p.n, Xh.ctypes.data, p.n,
+                                       1e-12, maxit, its.ctypes.data, res.ctypes.data, raw.ctypes.data, None) == 0
+    for c in range(2):
+        assert np.all(np.isfinite(raw[c, :its[c]])) and np.all(np.isnan(raw[c, its[c]:]))
+    assert sq._lib.spaqr_gmres_history(F._h, ctypes.byref(csr), 2, bf.ctypes.data, p.n, Xh.ctypes.data, p.n,
+                                       1e-12, maxit, its.ctypes.data, res.ctypes.data, None, None) == -1
+    del keep
