@@ -19,6 +19,9 @@
 // diagonal blocks the solve needs.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 
 #include <algorithm>
 #include <cmath>
@@ -951,7 +954,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     struct Timer { cudaEvent_t a, b; int ph, lev; };
     std::vector<Timer> timers;
     int cur_level = -1;
-    auto tstart = [&]() {
+    // every timed phase is also an NVTX range "L<level> <phase>" (level -1:
+    // the initial gather), so profilers can select a level's or a phase's
+    // kernels; without a profiler attached the ranges cost nothing
+    static const char* const kPhaseName[4] = {"factorize", "scale", "sparsify", "merge"};
+    auto tstart = [&](int ph) {
         Timer t;
         t.ph = -1;
         t.lev = cur_level;
@@ -959,10 +966,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         C.cuda(cudaEventCreate(&t.b));
         C.cuda(cudaEventRecord(t.a, st));
         timers.push_back(t);
+        char name[48];
+        std::snprintf(name, sizeof(name), "L%d %s", cur_level, kPhaseName[ph]);
+        nvtxRangePushA(name);
     };
     auto tstop = [&](int ph) {
         timers.back().ph = ph;
         C.cuda(cudaEventRecord(timers.back().b, st));
+        nvtxRangePop();
     };
 
     // ---- inputs on the device ----
@@ -986,7 +997,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     int* d_flags = C.alloc<int>(4, true);
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), st));
-    tstart();
+    tstart(3);
     SPAQR_LAUNCH(KK_COLSCALE, 2.0 * nnz, 24.0 * nnz + 16.0 * n, st,
                  k_colscale<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_cscp, d_csce, dval,
                                                                           opt->col_normalize, F->d_scale, d_flags));
@@ -1228,7 +1239,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
         }
         if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
-        tstart();
+        tstart(0);
         if (!qr.empty()) {
             launch_qr<real>(C, qr, esz, KK_FRONT_QR, fl_qr, by_qr);
             if (C.rc) return C.rc;
@@ -1428,7 +1439,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         by_sc += 16.0 * sz[i] * sz[j] + 8.0 * sz[i] * sz[i] + 8.0 * sz[j] * sz[j];
                     }
                 }
-                tstart();
+                tstart(1);
                 if (!sq.empty()) {
                     launch_qr<real>(C, sq, esz, KK_SCALE_QR, fl_sq, by_sq);
                     if (C.rc) return C.rc;
@@ -1458,7 +1469,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             } else {
                 // sigma_p = 1 / sigma_min(A_p), A_p = column p over all its
                 // rows (Lemma 1): copy, Householder QR, Lanczos on (R^T R)^{-1}
-                tstart();
+                tstart(2);
                 sig = C.alloc<double>(ncl, false);
                 std::vector<int64_t> mp(ncl, 0), apo(ncl, 0);
                 int64_t atot = 0, wtot = 0, qtot = 0;
@@ -1527,7 +1538,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
                 tstop(2);
             }
-            tstart();
+            tstart(2);
             // CPQR of M_p
             std::vector<std::vector<std::pair<int, int>>> rowlist(ncl);   // row i -> (col j, entry)
             for (int j = 0; j < ncl; j++)
@@ -1698,7 +1709,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 // T_p[:, r:] (H_p, R_ff); H_p^T on its coarse columns, whose top
                 // f rows are R_fc and bottom r rows the new diagonal block
                 // (Section 3.2).  T_p stays with the factor for the solve.
-                tstart();
+                tstart(2);
                 int64_t tt = 0;
                 for (int p : rest) {
                     if (sz[p] == 0) continue;
@@ -1813,7 +1824,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             layout_of(sn, nsz, nl);
             real* narena = C.alloc<real>(nl.total, true);
             if (C.rc) return C.rc;
-            tstart();
+            tstart(3);
             C.cuda(cudaMemsetAsync(narena, 0, sizeof(real) * nl.total, st));
             std::vector<SparsifyTask<real>> sk;
             int64_t scr = 0;
