@@ -153,10 +153,11 @@ def scaling_study(kind, sizes, eps, scaling=1, precision="fp64", gmres=True, dev
         if gmres:
             b = torch.from_numpy(np.ascontiguousarray(rhs(p, 1).T)).to(dev).T
             t0 = time.perf_counter()
-            _, it, rr = sq.spaqr_gmres(F, *A, b, tol=1e-12)
+            _, it, rr, hist = sq.spaqr_gmres(F, *A, b, tol=1e-12, history=True)
             torch.cuda.synchronize(dev)
             row.update(gmres_iters=int(it[0]), gmres_relres=float(rr[0]),
-                       gmres_ms=(time.perf_counter() - t0) * 1e3)
+                       gmres_ms=(time.perf_counter() - t0) * 1e3,
+                       gmres_history=[float(x) for x in hist[0]])
         del F
         out.append(row)
     return out
@@ -171,6 +172,11 @@ def markdown(study, title):
         lines.append(f"| {r['n_side']} | {r['N']} | {r['levels']} | {r['factor_ms']:.1f} | "
                      f"{r['factor_bytes'] / 2 ** 20:.0f} | {r['bytes_per_unknown']:.0f} | {r['top_separator']} | "
                      f"{r['rank_sum']} / {r['size_sum']} | {r.get('gmres_iters', '')} |")
+    hist = [r for r in study if r.get("gmres_history")]
+    if hist:
+        lines += ["", "GMRES residual estimates ||b - A x_j|| / ||b|| (iterations 1, 2, ...):", ""]
+        for r in hist:
+            lines.append(f"- side {r['n_side']}: " + " ".join(f"{x:.1e}" for x in r["gmres_history"]))
     for r in study:
         lines += ["", f"Per level, side {r['n_side']} (level 0 = leaves):", "",
                   "| level | fronts | max front (rows x cols) | interfaces | max interface | size before -> after |"

@@ -60,3 +60,13 @@ def test_plan_report_invariants():
             assert a["n_interfaces"] >= b["clusters"]          # interfaces only merge
         assert lv[-1]["n_interfaces"] == 0 and lv[-1]["n_fronts"] == 1
         assert plan_markdown(rep, "t").count("\n|") == o.L + 2   # header, rule, one row per level
+
+
+def test_markdown_residual_history():
+    """A study row with its GMRES residual estimates renders them in order,
+    also after a JSON round trip."""
+    st, _ = _study()
+    st[0]["gmres_history"] = [0.5, 2.5e-3, 7.0e-13]
+    a = diagnostics.markdown(st, "t")
+    assert "- side 8: 5.0e-01 2.5e-03 7.0e-13" in a
+    assert diagnostics.markdown(json.loads(json.dumps(st)), "t") == a

@@ -66,5 +66,6 @@ def test_scaling_study_runs(dev):
     st = diagnostics.scaling_study("3d_uniform_a", [8, 12], 1e-2, device=dev)
     assert [r["N"] for r in st] == [512, 1728]
     assert all(r["gmres_relres"] <= 1e-12 for r in st)
+    assert all(len(r["gmres_history"]) == r["gmres_iters"] and r["gmres_history"][-1] <= 1e-12 for r in st)
     md = diagnostics.markdown(st, "t")
-    assert "| 12 | 1728 |" in md
+    assert "| 12 | 1728 |" in md and "GMRES residual estimates" in md
