@@ -528,8 +528,11 @@ def gmres(n, rowptr, colind, val, b, precond, tol=1e-12, maxit=300):
     """Right-preconditioned GMRES (modified Gram-Schmidt Arnoldi, Givens).
 
     x0 = 0; no restart within maxit.  Convergence: the recomputed true
-    residual ||b - A x|| / ||b|| <= tol (Section 4).  Returns (x, iters, relres,
-    history of the Arnoldi residual estimates).
+    residual ||b - A x|| / ||b|| <= tol (Section 4).  x and the true residual
+    are formed only at an iteration whose Arnoldi residual estimate
+    |g_{j+1}| / ||b|| is <= tol, at a breakdown (zero subdiagonal entry before
+    its rotation: the Krylov space is invariant) and at maxit.  Returns (x,
+    iters, relres, history of the Arnoldi residual estimates).
     """
     rowptr = np.asarray(rowptr, dtype=np.int64)
     colind = np.asarray(colind, dtype=np.int64)
@@ -557,7 +560,11 @@ def gmres(n, rowptr, colind, val, b, precond, tol=1e-12, maxit=300):
             H[i, j] = Vb[i] @ w
             w = w - H[i, j] * Vb[i]
         H[j + 1, j] = float(np.linalg.norm(w))
-        if H[j + 1, j] != 0.0:
+        # breakdown: the Krylov space is invariant, and the Arnoldi step has
+        # no next basis vector (tested here, before the rotation below
+        # zeroes this entry)
+        breakdown = H[j + 1, j] == 0.0
+        if not breakdown:
             Vb[j + 1] = w / H[j + 1, j]
         for i in range(j):
             t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
@@ -572,13 +579,13 @@ def gmres(n, rowptr, colind, val, b, precond, tol=1e-12, maxit=300):
         g[j] = cs[j] * g[j]
         est = abs(g[j + 1]) / bnorm
         hist.append(est)
-        if est <= tol or H[j + 1, j] == 0.0 or j == maxit - 1:
+        if est <= tol or breakdown or j == maxit - 1:
             yk = dense.solve_upper(H[:j + 1, :j + 1], g[:j + 1])
             xt = np.zeros(n)
             for i in range(j + 1):
                 xt += yk[i] * Z[i]
             res = float(np.linalg.norm(b - _matvec(n, rowptr, colind, val, xt))) / bnorm
             x, relres = xt, res
-            if res <= tol:
+            if res <= tol or breakdown:
                 return x, j + 1, relres, hist
     return x, maxit, relres, hist

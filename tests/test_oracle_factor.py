@@ -160,3 +160,84 @@ def test_sequential_sparsification_close_to_two_phase(kind, n, eps):
         out.append((it, sum(r for lev in F.ranks for (_, r) in lev.values())))
     assert abs(out[0][0] - out[1][0]) <= 3
     assert abs(out[0][1] - out[1][1]) <= 0.05 * out[0][1]
+
+
+def _krylov_min_residuals(Aop, b, jmax):
+    """min over y in K_j(A, b) of ||b - A y|| / ||b||, j = 1..jmax, by brute
+    force: an orthonormal basis of the Krylov space from numpy's QR of
+    [b, Ab, ..., A^{j-1} b] (columns normalised first) and a least-squares
+    solve over it (the definition of the GMRES iterate, Section 4)."""
+    n = b.shape[0]
+    K = np.zeros((n, jmax))
+    v = b / np.linalg.norm(b)
+    for j in range(jmax):
+        K[:, j] = v
+        v = Aop(v)
+        v = v / np.linalg.norm(v)
+    out = []
+    for j in range(1, jmax + 1):
+        Qk, _ = np.linalg.qr(K[:, :j])
+        AQ = np.column_stack([Aop(Qk[:, i]) for i in range(j)])
+        y, *_ = np.linalg.lstsq(AQ, b, rcond=None)
+        out.append(np.linalg.norm(b - AQ @ y) / np.linalg.norm(b))
+    return np.array(out)
+
+
+def test_gmres_estimates_equal_krylov_minimum():
+    """The Arnoldi residual estimates are the minimum residuals over the
+    Krylov spaces of A M^{-1} (right preconditioning), computed here by
+    brute force; a dropped Givens rotation, a wrong sign in it or a
+    left-preconditioned residual fails this."""
+    p = _prob("2d_uniform_a", 12)
+    b = rhs(p, 1)[:, 0]
+    F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-1, nlevels=3, skip=0)
+    _, it, rr, hist = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: spaqr.solve(F, v))
+    jm = min(it, 6)
+    ref = _krylov_min_residuals(lambda v: p.matvec(spaqr.solve(F, v)), b, jm)
+    np.testing.assert_allclose(hist[1:jm + 1], ref, rtol=1e-6, atol=1e-14)
+
+
+def test_gmres_stops_at_first_estimate_below_tol():
+    """The true residual is recomputed only once the Arnoldi estimate passes
+    tol, so the iteration count is the first j with estimate <= tol (when the
+    recomputed residual passes there too), and a looser tol stops earlier."""
+    p = _prob("2d_uniform_a", 16)
+    b = rhs(p, 1)[:, 0]
+    F = spaqr.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-1, nlevels=3, skip=0)
+    for tol in (1e-6, 1e-12):
+        x, it, rr, hist = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, lambda v: spaqr.solve(F, v), tol=tol)
+        first = next(j for j in range(1, len(hist)) if hist[j] <= tol)
+        assert it == first and rr <= tol
+        assert np.linalg.norm(b - p.matvec(x)) / np.linalg.norm(b) == pytest.approx(rr, rel=1e-12)
+        assert all(h > tol for h in hist[1:it])
+
+
+def test_gmres_exact_breakdown():
+    """A M^{-1} = I (the exact inverse as preconditioner): the first Arnoldi
+    vector spans an invariant space, the next basis vector is exactly zero,
+    and GMRES stops after one iteration with the exact solution."""
+    p = _prob("2d_uniform_a", 6)
+    b = rhs(p, 1)[:, 0]
+    Ad = np.zeros((p.n, p.n))
+    for r in range(p.n):
+        for e in range(p.rowptr[r], p.rowptr[r + 1]):
+            Ad[r, p.colind[e]] += p.val[e]
+    Ainv = np.linalg.inv(Ad)
+
+    def exact(v):
+        return Ainv @ v
+
+    def ident_matvec_solver(v):
+        return v
+
+    # identity matrix and identity preconditioner: w = v_0 exactly
+    n = 8
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int64)
+    va = np.ones(n)
+    bb = np.linspace(1.0, 2.0, n)
+    x, it, rr, hist = spaqr.gmres(n, rp, ci, va, bb, ident_matvec_solver, tol=0.0, maxit=5)
+    assert it == 1 and rr == 0.0 and np.array_equal(x, bb)
+    # the exact inverse on a grid matrix: converged after one iteration
+    x, it, rr, _ = spaqr.gmres(p.n, p.rowptr, p.colind, p.val, b, exact)
+    assert it == 1 and rr <= 1e-13
