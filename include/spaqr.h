@@ -135,6 +135,9 @@ typedef struct {
     double  phase_ms[4];       /* factorize / scale / sparsify / merge, CUDA events */
     int32_t top_size;          /* size of the root separator when it was factored */
     int64_t peak_bytes;        /* most device bytes the factorisation held at once (factor + temporaries) */
+    int64_t workspace_rows;    /* scratch rows per right-hand side of one application (level vectors
+                                  and partial sums), in elements of the factor's precision */
+    int32_t precision;         /* SPAQR_FP64 or SPAQR_FP32: storage and arithmetic of the factor */
 } spaqr_info;
 
 /* Per-level diagnostics (spaqr_factor_level), level index k = 0 at the
@@ -171,8 +174,9 @@ const char* spaqr_last_error(void);
  * restatement): nested dissection on G(A^T A) with breadth-first level sets
  * as separators (pseudo-peripheral start), interfaces from the descendant
  * subdomains each separator column is adjacent to, and rows assigned by a
- * matching that puts large |a_ij| on the diagonal (greedy, then augmenting
- * paths; A->val may be NULL for a pattern-only matching).  SINGULAR if the
+ * matching that puts large |a_ij| on the diagonal (the maximum-product
+ * matching of spaqr_order_general; A->val may be NULL for a pattern-only
+ * matching).  SINGULAR if the
  * pattern has no perfect row matching; UNSUPPORTED if the squared row
  * lengths sum above 2^31 (G(A^T A) too large to form).  Also builds the
  * symbolic plan:
@@ -185,9 +189,9 @@ int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_orde
  * choice of row matching (Section 2.3 assigns rows by a bipartite matching
  * that puts large entries on the diagonal, MC64 in the paper):
  *   SPAQR_MATCH_GREEDY: entries by decreasing |a_ij| (ties: row, column)
- *     matched greedily, then every unmatched row by an augmenting path
- *     (what spaqr_order uses);
- *   SPAQR_MATCH_MAX_PRODUCT: the perfect matching maximising the product of
+ *     matched greedily, then every unmatched row by an augmenting path;
+ *   SPAQR_MATCH_MAX_PRODUCT (what spaqr_order uses): the perfect matching
+ *     maximising the product of
  *     the matched |a_ij| (the product matching of MC64): minimum cost on
  *     c_ij = log max_k |a_kj| - log |a_ij| over the nonzero values
  *     (duplicates summed, explicit zeros dropped) by shortest augmenting
@@ -264,13 +268,16 @@ int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, int64_t ldb,
  * allocator because cudaMalloc / cudaFree can synchronise the device and take
  * an unbounded time.  The paper has no counterpart; it is an interface
  * convenience.
- * The scratch space (one vector per level, F's total level rows x nrhs
- * doubles) lives in a fixed array of SPAQR_NOALLOC_SCRATCH_DOUBLES doubles
+ * The scratch space (one vector per level plus partial sums:
+ * spaqr_info.workspace_rows x nrhs elements of the factor's precision, i.e.
+ * ceil(workspace_rows x nrhs x element bytes / 8) doubles) lives in a fixed
+ * array of SPAQR_NOALLOC_SCRATCH_DOUBLES doubles
  * (16 MiB) inside the library, which every GPU that loads the library holds
  * until the process exits.  Calls needing more return SPAQR_ERR_INVALID_ARG
  * (use fewer right-hand sides per call).  B and X must be device pointers
  * (n x nrhs, leading dimensions ldb, ldx >= n; same aliasing rule as
- * spaqr_solve).  The first call on a device looks up the array's device
+ * spaqr_solve), device memory of the factor's GPU.  The first call on a
+ * device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array, so calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the

@@ -254,13 +254,13 @@ def row_matching_max_product(n, rowptr, colind, val=None):
     return np.array(rowcol, dtype=np.int64)
 
 
-def nd_general(n, rowptr, colind, val=None, L=None, matching="greedy"):
+def nd_general(n, rowptr, colind, val=None, L=None, matching="max_product"):
     """Modified nested dissection of a general matrix (readings G1-G5).
 
     Returns an NDOrdering (as the grid ordering) with two more fields:
     rowcol[r] (the column row r is matched to) and rperm[new] (old row of the
-    new position: the row matched to column perm[new]).  matching: "greedy"
-    (reading G5) or "max_product" (reading G6).
+    new position: the row matched to column perm[new]).  matching:
+    "max_product" (reading G6, the default) or "greedy" (reading G5).
     """
     if matching not in ("greedy", "max_product"):
         raise ValueError("matching must be 'greedy' or 'max_product'")

@@ -82,7 +82,8 @@ class _Info(ctypes.Structure):
                 ("solve_flops", ctypes.c_double), ("n_interfaces_sparsified", ctypes.c_int32),
                 ("rank_sum", ctypes.c_int64), ("size_sum", ctypes.c_int64),
                 ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32),
-                ("peak_bytes", ctypes.c_int64)]
+                ("peak_bytes", ctypes.c_int64), ("workspace_rows", ctypes.c_int64),
+                ("precision", ctypes.c_int32)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -324,20 +325,21 @@ class Ordering:
 MATCHINGS = {"greedy": 0, "max_product": 1}
 
 
-def spaqr_order(rowptr, colind, dims, nlevels=0, val=None, matching="greedy"):
+def spaqr_order(rowptr, colind, dims, nlevels=0, val=None, matching=None):
     """Modified nested dissection + symbolic plan (spaqr_order): geometric on
     the grid `dims`, or, with dims None, the general-matrix ordering on
     G(A^T A) with rows matched to columns (by |val| when given;
-    spaqr_order_general): matching "greedy" (largest entries first, then
-    augmenting paths) or "max_product" (the perfect matching maximising the
-    product of the matched |a_ij|)."""
+    spaqr_order_general): matching "max_product" (the default: the perfect
+    matching maximising the product of the matched |a_ij|) or "greedy"
+    (largest entries first, then augmenting paths)."""
     load_library()
-    if dims is not None and matching != "greedy":
+    if dims is not None and matching is not None:
         raise ValueError("a row matching applies to the grid-free ordering (dims None); "
                          "grid orderings keep every row with its column")
     csr, keep = _make_csr(rowptr, colind, val if dims is None else None)
     h = ctypes.c_void_p()
     if dims is None:
+        matching = "max_product" if matching is None else matching
         if matching not in MATCHINGS:
             raise ValueError(f"matching must be one of {sorted(MATCHINGS)}")
         _check(_lib.spaqr_order_general(ctypes.byref(csr), int(nlevels), MATCHINGS[matching], ctypes.byref(h)))
@@ -418,6 +420,8 @@ class Factor:
 
 SPAQR_FP64 = 0
 SPAQR_FP32 = 1
+# doubles of the fixed device scratch array of spaqr_solve_noalloc (include/spaqr.h)
+SPAQR_NOALLOC_SCRATCH_DOUBLES = 2 * 1024 * 1024
 
 
 def spaqr_factor(ordering, rowptr, colind, val, eps=1e-2, nlevels=0, skip=2, scaling=1,

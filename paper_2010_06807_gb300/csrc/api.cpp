@@ -50,6 +50,30 @@ int check_csr_location(const spaqr_csr* A) {
     }
     return SPAQR_OK;
 }
+
+int check_on_device(const void* p, int dev, const char* what) {
+    if (!p) return SPAQR_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return SPAQR_OK;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        set_error(std::string(what) + " is device memory of GPU " + std::to_string(a.device) +
+                  ", the call runs on GPU " + std::to_string(dev));
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    return SPAQR_OK;
+}
+
+int check_csr_device(const spaqr_csr* A, int dev) {
+    if (!A->on_device) return SPAQR_OK;
+    if (check_on_device(A->rowptr, dev, "A->rowptr") != SPAQR_OK ||
+        check_on_device(A->colind, dev, "A->colind") != SPAQR_OK ||
+        check_on_device(A->val, dev, "A->val") != SPAQR_OK)
+        return SPAQR_ERR_INVALID_ARG;
+    return SPAQR_OK;
+}
 }  // namespace spaqr
 
 namespace {
@@ -113,7 +137,7 @@ int order_impl(const spaqr_csr* A, const spaqr_grid* g, int nlevels, int matchin
 }  // namespace
 
 extern "C" int spaqr_order(const spaqr_csr* A, const spaqr_grid* g, int nlevels, spaqr_ordering** out) {
-    return order_impl(A, g, nlevels, SPAQR_MATCH_GREEDY, out);
+    return order_impl(A, g, nlevels, SPAQR_MATCH_MAX_PRODUCT, out);
 }
 
 extern "C" int spaqr_order_general(const spaqr_csr* A, int nlevels, int matching, spaqr_ordering** out) {

@@ -2069,9 +2069,16 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
         set_error("no CUDA device");
         return SPAQR_ERR_NO_DEVICE;
     }
+    int curdev = 0;
+    if (cudaGetDevice(&curdev) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGetDevice failed");
+        return SPAQR_ERR_CUDA;
+    }
+    if (check_csr_device(A, curdev) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
     spaqr_factor_s* F = new (std::nothrow) spaqr_factor_s();
     if (!F) { set_error("host allocation failed"); return SPAQR_ERR_OOM; }
-    cudaGetDevice(&F->device);
+    F->device = curdev;
     keep_pool_memory(F->device);
     int rc;
     try {
@@ -2121,6 +2128,8 @@ extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
     for (int i = 0; i < 4; i++) out->phase_ms[i] = F->phase_ms[i];
     out->top_size = F->top_size;
     out->peak_bytes = F->peak_bytes;
+    out->workspace_rows = F->ws_rows;
+    out->precision = F->precision;
     return SPAQR_OK;
 }
 

@@ -1207,7 +1207,12 @@ int apply_device_t(const spaqr_factor_s* F, int nrhs, const double* B, int64_t l
     }
     SPAQR_LAUNCH(KK_SOLVE_PERM, 1.0 * n * nrhs, 16.0 * n + 16.0 * n * nrhs, st,
                  k_perm_out<real><<<nb, 256, 0, st>>>(n, nrhs, F->d_perm, F->d_scale, Y0, F->lv[0].rows, X, ldx));
-    return cudaGetLastError() == cudaSuccess ? SPAQR_OK : SPAQR_ERR_CUDA;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+        return SPAQR_ERR_CUDA;
+    }
+    return SPAQR_OK;
 }
 
 // Times the application's units one at a time on this factor (each form of a
@@ -1298,6 +1303,22 @@ int apply_device(const spaqr_factor_s* F, int nrhs, const double* B, int64_t ldb
     return apply_device_t<double>(F, nrhs, B, ldb, X, ldx, st, static_cast<double*>(ws), singular, tt.get());
 }
 
+// Makes the factor's device current for the scope of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace spaqr
 
 using namespace spaqr;
@@ -1317,13 +1338,13 @@ extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, i
         set_error("aliased B and X need the same leading dimension");
         return SPAQR_ERR_INVALID_ARG;
     }
-    int cur = 0;
-    cudaGetDevice(&cur);
-    if (cur != F->device) cudaSetDevice(F->device);
-    SCtx C;
-    C.st = (cudaStream_t)stream;
+    if (check_on_device(B, F->device, "B") != SPAQR_OK || check_on_device(X, F->device, "X") != SPAQR_OK)
+        return SPAQR_ERR_INVALID_ARG;
     const bool bdev = is_device_ptr(B), xdev = is_device_ptr(X);
     if (bdev != xdev) { set_error("B and X must both be host or both be device memory"); return SPAQR_ERR_INVALID_ARG; }
+    DeviceGuard dg(F->device);   // outlives C, whose frees run on the factor's device
+    SCtx C;
+    C.st = (cudaStream_t)stream;
     const int64_t n = F->n;
     const double* dB = B;
     double* dX = X;
@@ -1341,13 +1362,12 @@ extern "C" int spaqr_solve(const spaqr_factor_t* F, int nrhs, const double* B, i
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), C.st));
     C.cuda((cudaError_t)0);
-    int rc = apply_device(F, nrhs, dB, lb, dX, lx, C.st, ws, flag);
-    if (rc != SPAQR_OK) { C.cuda(cudaGetLastError()); return C.rc ? C.rc : rc; }
+    const int rc = apply_device(F, nrhs, dB, lb, dX, lx, C.st, ws, flag);
+    if (rc != SPAQR_OK) return C.rc ? C.rc : rc;
     if (!bdev) C.cuda(cudaMemcpy2DAsync(X, ldx * 8, dX, n * 8, n * 8, nrhs, cudaMemcpyDeviceToHost, C.st));
     int hflag = 0;
     C.cuda(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, C.st));
     C.cuda(cudaStreamSynchronize(C.st));
-    if (cur != F->device) cudaSetDevice(cur);
     if (C.rc) return C.rc;
     if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
     return SPAQR_OK;
@@ -1388,22 +1408,6 @@ bool capture_apply(const spaqr_factor_s* F, int nrhs, const double* Vin, double*
     }
     return ok;
 }
-
-// Makes the factor's device current for the scope of a call.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            cudaGetLastError();
-            prev = -1;
-        }
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 // A private non-blocking stream for one call, ordered after the caller's
 // stream: graphs cannot be captured on the legacy default stream.
@@ -1452,7 +1456,9 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
         set_error("A does not match the factored pattern (nnz) or has NULL arrays");
         return SPAQR_ERR_INVALID_ARG;
     }
-    if (check_csr_location(A) != SPAQR_OK) return SPAQR_ERR_INVALID_ARG;
+    if (check_csr_location(A) != SPAQR_OK || check_csr_device(A, F->device) != SPAQR_OK ||
+        check_on_device(B, F->device, "B") != SPAQR_OK || check_on_device(X, F->device, "X") != SPAQR_OK)
+        return SPAQR_ERR_INVALID_ARG;
     if (!A->on_device) {
         if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) { set_error("bad CSR rowptr"); return SPAQR_ERR_INVALID_ARG; }
         for (int64_t r = 0; r < A->n; r++)
@@ -1873,24 +1879,19 @@ extern "C" int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const doub
         set_error("spaqr_solve_noalloc takes device pointers only");
         return SPAQR_ERR_INVALID_ARG;
     }
-    int cur = 0;
-    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); set_error("cudaGetDevice failed"); return SPAQR_ERR_CUDA; }
-    if (cur != F->device && cudaSetDevice(F->device) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("cudaSetDevice failed");
-        return SPAQR_ERR_CUDA;
-    }
     const int dev = F->device;
+    if (dev < 0 || dev >= 128) { set_error("device index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    if (check_on_device(B, dev, "B") != SPAQR_OK || check_on_device(X, dev, "X") != SPAQR_OK)
+        return SPAQR_ERR_INVALID_ARG;
+    DeviceGuard dg(dev);   // the caller's device is current again on every return
     double* ws = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (dev < 0 || dev >= 128) { set_error("device index out of range"); return SPAQR_ERR_INVALID_ARG; }
         if (!g_noalloc_ptr[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
                 cudaGetLastError();
-                if (cur != F->device) cudaSetDevice(cur);
                 set_error(std::string("cudaGetSymbolAddress of the solve scratch failed: ") + cudaGetErrorString(e));
                 return SPAQR_ERR_CUDA;
             }
@@ -1900,20 +1901,23 @@ extern "C" int spaqr_solve_noalloc(const spaqr_factor_t* F, int nrhs, const doub
     }
     cudaStream_t st = (cudaStream_t)stream;
     int* flag = reinterpret_cast<int*>(ws + SPAQR_NOALLOC_SCRATCH_DOUBLES);
-    int rc = SPAQR_OK;
     // the flag must start at zero; the level vectors are written before read
-    if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) rc = SPAQR_ERR_CUDA;
-    if (rc == SPAQR_OK) rc = apply_device(F, nrhs, B, ldb, X, ldx, st, ws, flag);
-    int hflag = 0;
-    if (rc == SPAQR_OK && cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rc = SPAQR_ERR_CUDA;
-    if (rc == SPAQR_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPAQR_ERR_CUDA;
-    if (rc != SPAQR_OK) {
-        const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+        return SPAQR_ERR_CUDA;
     }
-    if (cur != F->device) cudaSetDevice(cur);
+    const int rc = apply_device(F, nrhs, B, ldb, X, ldx, st, ws, flag);   // sets the message on failure
     if (rc != SPAQR_OK) return rc;
+    int hflag = 0;
+    e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+        return SPAQR_ERR_CUDA;
+    }
     if (hflag) { set_error("zero diagonal in an R factor"); return SPAQR_ERR_SINGULAR; }
     return SPAQR_OK;
 }

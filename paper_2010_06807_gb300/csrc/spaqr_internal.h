@@ -112,6 +112,11 @@ void keep_pool_memory(int device);
 bool graphs_on();
 bool fail_this_alloc();   // fault injection (spaqr_test_fail_alloc)
 int check_csr_location(const spaqr_csr* A);   // A->on_device against where the arrays are
+// INVALID_ARG (with the message) when p is device memory of a GPU other than
+// dev; host, pinned and managed memory pass.  Kernels on dev would otherwise
+// reach another GPU's memory through unified addressing.
+int check_on_device(const void* p, int dev, const char* what);
+int check_csr_device(const spaqr_csr* A, int dev);   // check_on_device on a device CSR's arrays
 
 }  // namespace spaqr
 

@@ -205,7 +205,7 @@ def main(argv=None):
                     help="host only: the symbolic plan of each size's ordering, no factorisation")
     ap.add_argument("--permute", type=int, default=None, metavar="SEED",
                     help="with --plan-only: permute rows and columns and use the grid-free ordering")
-    ap.add_argument("--matching", default="greedy", help="row matching of the grid-free ordering")
+    ap.add_argument("--matching", default="max_product", help="row matching of the grid-free ordering")
     a = ap.parse_args(argv)
     if a.plan_only:
         from synth.convdiff import config_problem, permuted

@@ -84,9 +84,9 @@ def _dim_key(problem):
 class DeviceOps:
     """libspaqr + torch streams on one CUDA device: what the server runs."""
 
-    def __init__(self, device=None, eps=1e-2, precision="fp64", tol=1e-12, maxit=300, matching="greedy"):
-        """matching: the row matching of general matrices (no grid), "greedy"
-        or "max_product" (see spaqr_order)."""
+    def __init__(self, device=None, eps=1e-2, precision="fp64", tol=1e-12, maxit=300, matching="max_product"):
+        """matching: the row matching of general matrices (no grid),
+        "max_product" (the default) or "greedy" (see spaqr_order)."""
         import torch
 
         from . import load_library
@@ -119,7 +119,7 @@ class DeviceOps:
             general = problem.dims is None
             ordering = spaqr_order(problem.rowptr, problem.colind, problem.dims,
                                    val=problem.val if general else None,
-                                   matching=self.matching if general else "greedy")
+                                   matching=self.matching if general else None)
             F = spaqr_factor(ordering, *csr, eps=self.eps, precision=self.precision, stream=stream)
         return {"F": F, "csr": csr, "ordering": ordering, "n": problem.n, "dim": _dim_key(problem)}
 

@@ -71,3 +71,24 @@ def test_gmres_allocation_failures(setup):
     assert failed >= 1
     X, it, rr = sq.spaqr_gmres(F, *A, b, tol=1e-12)
     assert torch.equal(X, g_ref)
+
+
+def test_buffers_of_another_gpu_are_refused(setup):
+    """B or X in device memory of a GPU other than the factor's is refused
+    on the host (INVALID_ARG) before any kernel is launched: kernels on the
+    factor's GPU would otherwise reach the other GPU's memory through
+    unified addressing.  Needs two visible GPUs."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU visible")
+    dev, o, A, b, x_ref, _ = setup
+    F = sq.spaqr_factor(o, *A, eps=1e-3, skip=1)
+    other = torch.device("cuda:1")
+    b1 = b.T.contiguous().to(other).T
+    sq.spaqr_stats_reset()
+    for fn in (lambda: sq.spaqr_solve(F, b1), lambda: sq.spaqr_solve_noalloc(F, b1, torch.zeros_like(b1.T).T),
+               lambda: sq.spaqr_gmres(F, *A, b1)):
+        with pytest.raises(sq.SpaqrError) as e:
+            fn()
+        assert e.value.name == "INVALID_ARG"
+    launches, _ = sq.spaqr_stats()
+    assert launches == 0

@@ -217,9 +217,9 @@ def test_general_ordering_matching_errors(spaqr_lib):
     rp = np.array([0, 2, 4, 5], dtype=np.int64)
     ci = np.array([0, 1, 0, 2, 1], dtype=np.int32)
     v = np.array([0.0, 1.0, 0.0, 3.0, 2.0])
-    sq.spaqr_order(rp, ci, None, 1, val=v)   # greedy: uses the pattern
+    sq.spaqr_order(rp, ci, None, 1, val=v, matching="greedy")   # greedy: uses the pattern
     with pytest.raises(sq.SpaqrError) as e:
-        sq.spaqr_order(rp, ci, None, 1, val=v, matching="max_product")
+        sq.spaqr_order(rp, ci, None, 1, val=v)   # the default, maximum product
     assert e.value.name == "SINGULAR"
     from oracle.ordering_general import row_matching_max_product
     with pytest.raises(ValueError):

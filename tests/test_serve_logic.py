@@ -206,7 +206,7 @@ def test_device_ops_matching_option():
     to DeviceOps; an unknown one is refused when the server is set up."""
     import pytest as _pt
     from paper_2010_06807_gb300.serve import DeviceOps
-    assert DeviceOps("cuda:0").matching == "greedy"
-    assert DeviceOps("cuda:0", matching="max_product").matching == "max_product"
+    assert DeviceOps("cuda:0").matching == "max_product"
+    assert DeviceOps("cuda:0", matching="greedy").matching == "greedy"
     with _pt.raises(ValueError):
         DeviceOps("cuda:0", matching="mc64")
