@@ -159,6 +159,42 @@ typedef struct {
     double  phase_ms[4];       /* factorize / scale / sparsify / merge of this level, CUDA events */
 } spaqr_level_info;
 
+/* Kinds of stored factor blocks (spaqr_factor_block).  Every block is a
+ * dense column-major matrix; clusters are named by their first atom (the
+ * finest cluster they contain), the same names at every level. */
+#define SPAQR_BLK_FRONT      0  /* separator s (Section 2.4): the front panel after
+                                   its Householder QR, rows R(s) stacked in
+                                   ascending cluster order (s first), |s|
+                                   columns: reflectors below the diagonal
+                                   (unit diagonal implied), R_ss on and above */
+#define SPAQR_BLK_FRONT_TAU  1  /* the |s| Householder scalars of that QR */
+#define SPAQR_BLK_RSJ        2  /* R_sj: row s of the triangular factor in column
+                                   cluster j (`other`), |s| x |j| */
+#define SPAQR_BLK_SCALE      3  /* interface p (Section 2.5): A_pp = U_pp R_pp after
+                                   its Householder QR, reflectors of U_pp below the
+                                   diagonal, R_pp on and above, |p| x |p| */
+#define SPAQR_BLK_SCALE_TAU  4  /* the |p| Householder scalars of U_pp */
+#define SPAQR_BLK_CPQR       5  /* Q_pp of the truncated CPQR of M_p (Sections 2.2,
+                                   2.5, 4): |p| x r reflectors, unit diagonal and
+                                   zeros above it stored explicitly */
+#define SPAQR_BLK_CPQR_TAU   6  /* the r Householder scalars of Q_pp */
+#define SPAQR_BLK_FINE       7  /* unscaled form (Section 3.2): |p| x |p|, columns
+                                   0..r-1 = H_p^T (A_pp Q_p)[:, :r] (R_fc on top,
+                                   the new coarse diagonal block below), columns
+                                   r.. = the QR of the fine columns A_pp Q_pf
+                                   (reflectors of H_p below the diagonal, R_ff on
+                                   and above) */
+#define SPAQR_BLK_FINE_TAU   8  /* the |p| - r Householder scalars of H_p */
+
+/* Description of one stored block (spaqr_factor_block). */
+typedef struct {
+    int32_t level;      /* 0 = the leaves */
+    int32_t kind;       /* SPAQR_BLK_* */
+    int32_t cluster;    /* s or p (first atom) */
+    int32_t other;      /* column cluster j of SPAQR_BLK_RSJ, else -1 */
+    int32_t rows, cols;
+} spaqr_block_info;
+
 /* Last error message of the calling thread (never NULL). */
 const char* spaqr_last_error(void);
 
@@ -336,6 +372,18 @@ int spaqr_gmres_batch(const spaqr_factor_t* F, const spaqr_csr* A, int count, co
 /* Summary and timings of a factor. */
 int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out);
 
+/* Number of stored blocks of F (every block the application reads, level by
+ * level: fronts, R_sj, scaling and sparsification factors).  For inspection
+ * and parity checks; not on the hot path. */
+int spaqr_factor_nblocks(const spaqr_factor_t* F, int64_t* count);
+
+/* Block `index` (0 <= index < spaqr_factor_nblocks) of F: its description in
+ * *info and, when out is not NULL, a copy of its rows x cols entries in out
+ * (host, column-major, leading dimension rows; FP32 factors are widened to
+ * double).  Synchronous device-to-host copy on the factor's GPU.
+ * Errors: INVALID_ARG (NULL F or info, index out of range), CUDA. */
+int spaqr_factor_block(const spaqr_factor_t* F, int64_t index, spaqr_block_info* info, double* out);
+
 /* Per-level interface ranks: for level index k (0 = leaves) writes up to cap
  * pairs (size before, kept rank) of the interfaces sparsified at that level,
  * in ascending cluster order, and the count in *count.  Also the CPQR pivot
@@ -433,6 +481,31 @@ void spaqr_profile(int on);
  * the number of kernel kinds and *total_launches to the launch count since the
  * last reset.  Waits for pending events.  Errors: INVALID_ARG, CUDA. */
 int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t* total_launches);
+
+/* ---- Measurement aids (the paper has no counterpart) ---- */
+
+/* Arithmetic peak microbenchmarks of the current GPU, the denominators of
+ * roofline fractions: which = SPAQR_PEAK_DFMA (FP64 fused multiply-add on
+ * the CUDA cores), SPAQR_PEAK_DMMA (FP64 mma.sync m8n8k4), SPAQR_PEAK_FFMA
+ * (FP32 fused multiply-add), SPAQR_PEAK_TF32 (tcgen05.mma kind::tf32,
+ * M = 128, N = 256, FP32 accumulation in tensor memory).  One warm-up launch,
+ * then `reps` timed launches on the legacy default stream with CUDA events;
+ * *flops = flops of one launch, *ms = mean milliseconds per launch.
+ * Errors: INVALID_ARG, OOM, TIMEOUT (a bounded tensor-core wait ran out),
+ * CUDA. */
+#define SPAQR_PEAK_DFMA 0
+#define SPAQR_PEAK_DMMA 1
+#define SPAQR_PEAK_FFMA 2
+#define SPAQR_PEAK_TF32 3
+int spaqr_peak(int which, int reps, double* flops, double* ms);
+
+/* Self-check of the tcgen05 TF32 tile the mixed-precision factorisation
+ * builds on: D (128 x N, row-major) = A (128 x K, row-major) B^T (B: N x K,
+ * row-major), inputs rounded to TF32, FP32 accumulation.  Device pointers;
+ * 16 <= N <= 256 with N % 16 == 0, 8 <= K <= 128 with K % 8 == 0, else
+ * INVALID_ARG.  Synchronous on `stream`.  Errors: INVALID_ARG, OOM,
+ * TIMEOUT, CUDA. */
+int spaqr_tc_tile_check(const float* A, const float* B, float* D, int N, int K, void* stream);
 
 #ifdef __cplusplus
 }

@@ -86,6 +86,16 @@ class _Info(ctypes.Structure):
                 ("precision", ctypes.c_int32)]
 
 
+class _BlockInfo(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("kind", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("other", ctypes.c_int32), ("rows", ctypes.c_int32), ("cols", ctypes.c_int32)]
+
+
+# kinds of stored factor blocks (spaqr_factor_block, include/spaqr.h)
+BLOCK_KINDS = {0: "front", 1: "front_tau", 2: "rsj", 3: "scale", 4: "scale_tau", 5: "cpqr", 6: "cpqr_tau",
+               7: "fine", 8: "fine_tau"}
+
+
 class _LevelInfo(ctypes.Structure):
     _fields_ = [("n_fronts", ctypes.c_int32), ("max_front_rows", ctypes.c_int32),
                 ("max_front_cols", ctypes.c_int32), ("n_interfaces", ctypes.c_int32),
@@ -112,7 +122,7 @@ EXPORTS = [
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
-    "spaqr_test_fail_alloc",
+    "spaqr_test_fail_alloc", "spaqr_factor_nblocks", "spaqr_factor_block", "spaqr_peak", "spaqr_tc_tile_check",
 ]
 
 
@@ -153,6 +163,8 @@ def load_library(path=None):
         lib.spaqr_factor_level.argtypes = [vp, i32, ctypes.POINTER(_LevelInfo)]
         lib.spaqr_factor_pivots.argtypes = [vp, i32, vp, i64, vp, i32, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int)]
+        lib.spaqr_factor_nblocks.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.spaqr_factor_block.argtypes = [vp, i64, ctypes.POINTER(_BlockInfo), vp]
         lib.spaqr_factor_destroy.argtypes = [vp]
         lib.spaqr_factor_destroy.restype = None
     if hasattr(lib, "spaqr_stats"):
@@ -168,6 +180,9 @@ def load_library(path=None):
         lib.spaqr_factor_tuning.argtypes = [vp, i32, vp, i32, ctypes.POINTER(ctypes.c_int)]
         lib.spaqr_stats.argtypes = [ctypes.POINTER(_KStat), i32, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64)]
+    if hasattr(lib, "spaqr_peak"):
+        lib.spaqr_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.spaqr_tc_tile_check.argtypes = [vp, vp, vp, i32, i32, vp]
     if path is None:
         _lib = lib
     return lib
@@ -590,6 +605,25 @@ def spaqr_factor_pivots(F, level):
     return [norms[offs[i]:offs[i + 1]].copy() for i in range(ni.value)]
 
 
+def spaqr_factor_blocks(F):
+    """Every stored block of the factor (spaqr_factor_nblocks /
+    spaqr_factor_block): a list of dicts with level, kind (a BLOCK_KINDS
+    name), cluster, other (the column cluster of an R_sj block, else -1) and
+    data (rows x cols float64 array, a copy)."""
+    load_library()
+    cnt = ctypes.c_int64(0)
+    _check(_lib.spaqr_factor_nblocks(F._h, ctypes.byref(cnt)))
+    out = []
+    info = _BlockInfo()
+    for i in range(cnt.value):
+        _check(_lib.spaqr_factor_block(F._h, i, ctypes.byref(info), None))
+        a = np.zeros((info.cols, info.rows), dtype=np.float64)   # column-major
+        _check(_lib.spaqr_factor_block(F._h, i, ctypes.byref(info), a.ctypes.data if a.size else None))
+        out.append({"level": info.level, "kind": BLOCK_KINDS[info.kind], "cluster": info.cluster,
+                    "other": info.other, "data": a.T})
+    return out
+
+
 def spaqr_factor_sigmas(F, level):
     """sigma_p = 1 / sigma_min(A_p) per interface of a level (unscaled variant; 0 when scaled)."""
     load_library()
@@ -659,3 +693,30 @@ def spaqr_stats():
         out[k.name.decode()] = dict(launches=int(k.launches), total_ms=float(k.total_ms),
                                     flops=float(k.flops), bytes=float(k.bytes))
     return int(tot.value), out
+
+
+PEAKS = {"dfma": 0, "dmma": 1, "ffma": 2, "tf32": 3}
+
+
+def spaqr_peak(which, reps=10):
+    """Arithmetic peak microbenchmark ("dfma", "dmma", "ffma" or "tf32"):
+    returns (flops per launch, mean ms per launch); TFLOP/s = flops / ms / 1e9."""
+    load_library()
+    f, m = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.spaqr_peak(PEAKS[which], int(reps), ctypes.byref(f), ctypes.byref(m)))
+    return f.value, m.value
+
+
+def spaqr_tc_tile_check(A, B, stream=None):
+    """D = A B^T (A 128 x K, B N x K, float32 CUDA tensors, row-major) through
+    one tcgen05 TF32 tile; returns D (128 x N, float32)."""
+    import torch
+    load_library()
+    if A.dim() != 2 or A.shape[0] != 128 or B.dim() != 2 or B.shape[1] != A.shape[1]:
+        raise ValueError("A must be 128 x K and B N x K")
+    A = A.contiguous()
+    B = B.contiguous()
+    D = torch.empty(A.shape[0], B.shape[0], dtype=torch.float32, device=A.device)
+    _check(_lib.spaqr_tc_tile_check(A.data_ptr(), B.data_ptr(), D.data_ptr(), B.shape[0], A.shape[1],
+                                    _stream_ptr(stream)))
+    return D

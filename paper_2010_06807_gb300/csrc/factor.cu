@@ -1025,6 +1025,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     std::vector<SolveRsj<real>> pieces;
     std::vector<std::pair<int, int>> piece_src;   // (R_sj record, first column) of every piece
     std::vector<WideFront> wfr;
+    std::vector<int> front_cl, rsj_cl, ss_cl;   // first atom of the cluster of every solve record
     int64_t zp_max = 0;
     F->lv.assign(L, SolveLevelHost());
     int64_t ws = 0;
@@ -1291,6 +1292,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     if (sz[j] == 0) continue;
                     const int e = sp.find(s, j);
                     srsj.push_back(SolveRsj<real>{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
+                    rsj_cl.push_back(sp.cl[j]);
                     sflops += 2.0 * sz[s] * sz[j];
                     sbytes += 8 * sz[s] * sz[j];
                 }
@@ -1307,6 +1309,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     LV.fb_vec += 16.0 * n_ + 8.0 * snj;
                 }
                 sfronts.push_back(sf);
+                front_cl.push_back(sp.cl[s]);
                 LV.max_front_m = std::max(LV.max_front_m, sf.m);
                 LV.max_front_n = std::max(LV.max_front_n, sf.n);
                 sflops += 4.0 * sf.m * sf.n - 2.0 * sf.n * sf.n + 1.0 * sf.n * sf.n;
@@ -1972,6 +1975,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 LV.ssf_vec += 16.0 * sz[p] + 8.0 * newsz[p];
                 LV.ssb_vec += 16.0 * sz[p] + 8.0 * newsz[p];
                 sss.push_back(s);
+                ss_cl.push_back(sp.cl[p]);
                 LV.max_ss_n = std::max(LV.max_ss_n, s.np);
                 LV.max_ss_r = std::max(LV.max_ss_r, s.r);
             }
@@ -1990,6 +1994,36 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (C.rc) return C.rc;
             DG.factor_bytes = F->bytes;
             C.free_temps();
+        }
+    }
+    // index of the stored blocks (final device locations, after the
+    // per-level compaction)
+    for (int k = 0; k < L; k++) {
+        const SolveLevelHost& LVk = F->lv[k];
+        for (int f = LVk.front_begin; f < LVk.front_begin + LVk.nfront; f++) {
+            const SolveFront<real>& sf = sfronts[f];
+            const int c = front_cl[f];
+            F->blocks.push_back({k, SPAQR_BLK_FRONT, c, -1, sf.m, sf.n, sf.V, sf.ldv, 1});
+            F->blocks.push_back({k, SPAQR_BLK_FRONT_TAU, c, -1, sf.n, 1, sf.T, sf.n, (int64_t)sf.n + 1});
+            for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++)
+                F->blocks.push_back({k, SPAQR_BLK_RSJ, c, rsj_cl[b], sf.n, srsj[b].nj, srsj[b].R, srsj[b].ldr, 1});
+        }
+        for (int q = LVk.ss_begin; q < LVk.ss_begin + LVk.nss; q++) {
+            const SolveSS<real>& s = sss[q];
+            const int c = ss_cl[q];
+            if (s.UV) {
+                F->blocks.push_back({k, SPAQR_BLK_SCALE, c, -1, s.np, s.np, s.UV, s.lduv, 1});
+                F->blocks.push_back({k, SPAQR_BLK_SCALE_TAU, c, -1, s.np, 1, s.UT, s.np, (int64_t)s.np + 1});
+            }
+            if (s.QV && s.r > 0) {
+                F->blocks.push_back({k, SPAQR_BLK_CPQR, c, -1, s.np, s.r, s.QV, s.np, 1});
+                F->blocks.push_back({k, SPAQR_BLK_CPQR_TAU, c, -1, s.r, 1, s.QT, s.ldqt, (int64_t)s.ldqt + 1});
+            }
+            if (s.HR) {
+                F->blocks.push_back({k, SPAQR_BLK_FINE, c, -1, s.np, s.np, s.HR, s.np, 1});
+                if (s.f > 0)
+                    F->blocks.push_back({k, SPAQR_BLK_FINE_TAU, c, -1, s.f, 1, s.HT, s.f, (int64_t)s.f + 1});
+            }
         }
     }
     // upload the solve plan
@@ -2106,6 +2140,51 @@ extern "C" void spaqr_factor_destroy(spaqr_factor_t* F) {
     for (void* p : F->allocs) cudaFree(p);
     cudaSetDevice(cur);
     delete F;
+}
+
+extern "C" int spaqr_factor_nblocks(const spaqr_factor_t* F, int64_t* count) {
+    if (!F || !count) { spaqr::set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    *count = (int64_t)F->blocks.size();
+    return SPAQR_OK;
+}
+
+extern "C" int spaqr_factor_block(const spaqr_factor_t* F, int64_t index, spaqr_block_info* info, double* out) {
+    using namespace spaqr;
+    if (!F || !info) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
+    if (index < 0 || index >= (int64_t)F->blocks.size()) { set_error("block index out of range"); return SPAQR_ERR_INVALID_ARG; }
+    const BlockRec& b = F->blocks[(size_t)index];
+    info->level = b.level;
+    info->kind = b.kind;
+    info->cluster = b.cluster;
+    info->other = b.other;
+    info->rows = b.rows;
+    info->cols = b.cols;
+    if (!out || b.rows == 0 || b.cols == 0) return SPAQR_OK;
+    const size_t esz = (size_t)F->esz;
+    std::vector<char> tmp((size_t)b.rows * b.cols * esz);
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); cur = -1; }
+    if (cur != F->device) cudaSetDevice(F->device);
+    cudaError_t e;
+    if (b.rstride == 1)
+        e = cudaMemcpy2D(tmp.data(), b.rows * esz, b.ptr, (size_t)b.ld * esz, b.rows * esz, (size_t)b.cols,
+                         cudaMemcpyDeviceToHost);
+    else
+        e = cudaMemcpy2D(tmp.data(), esz, b.ptr, (size_t)b.rstride * esz, esz, (size_t)b.rows, cudaMemcpyDeviceToHost);
+    if (cur >= 0 && cur != F->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+        return SPAQR_ERR_CUDA;
+    }
+    const size_t cnt = (size_t)b.rows * b.cols;
+    if (esz == 8) {
+        std::memcpy(out, tmp.data(), cnt * 8);
+    } else {
+        const float* f = reinterpret_cast<const float*>(tmp.data());
+        for (size_t i = 0; i < cnt; i++) out[i] = (double)f[i];
+    }
+    return SPAQR_OK;
 }
 
 extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {

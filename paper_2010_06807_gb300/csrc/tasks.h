@@ -285,6 +285,16 @@ struct LevelDiag {
     double phase_ms[4] = {0, 0, 0, 0};
 };
 
+// One stored block of the factor (spaqr_factor_block): device location and
+// the clusters (first atoms) it belongs to.  Rows are read with stride
+// `rstride` elements and columns with stride `ld` (a diagonal is read as a
+// column with rstride = ld + 1).
+struct BlockRec {
+    int level, kind, cluster, other, rows, cols;
+    const void* ptr;
+    int64_t ld, rstride;
+};
+
 struct spaqr_factor_s {
     int device = 0;
     int64_t n = 0;
@@ -343,4 +353,5 @@ struct spaqr_factor_s {
     int top_size = 0;
     bool unscaled = false;         // unscaled variant (Section 3.2): narrow solve forms only
     int64_t peak_bytes = 0;        // most device bytes the factorisation held at once
+    std::vector<BlockRec> blocks;  // every stored block, level by level (spaqr_factor_block)
 };

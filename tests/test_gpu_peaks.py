@@ -1,0 +1,61 @@
+"""The tcgen05 TF32 tile (the tensor-core building block of the
+mixed-precision factorisation) against a plain FP64 product of the same
+TF32-rounded inputs, and the arithmetic peak microbenchmarks (positive,
+plausible rates)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2010_06807_gb300 as sq
+
+pytestmark = pytest.mark.gpu
+
+
+def tf32_round(x):
+    """FP32 -> TF32 (10 explicit mantissa bits), round to nearest with ties
+    away from zero, as cvt.rna.tf32.f32 does for finite values."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x1000) & 0xFFFFE000) & 0xFFFFFFFF
+    return b.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def dev(spaqr_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("N,K", [(16, 8), (64, 32), (256, 128), (128, 24), (240, 72)])
+def test_tc_tile_matches_fp64_product(dev, N, K):
+    rng = np.random.default_rng(N * 1000 + K)
+    A = rng.standard_normal((128, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = sq.spaqr_tc_tile_check(torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)).cpu().numpy()
+    ref = tf32_round(A).astype(np.float64) @ tf32_round(B).astype(np.float64).T
+    # FP32 accumulation of K products of TF32 values
+    bound = 2 * K * np.finfo(np.float32).eps * (np.abs(tf32_round(A)).astype(np.float64) @
+                                                 np.abs(tf32_round(B)).astype(np.float64).T)
+    assert np.all(np.abs(D - ref) <= bound + 1e-30)
+    # and the rounding of the inputs matters: the FP64 product of the
+    # unrounded inputs differs by far more than that
+    raw = A.astype(np.float64) @ B.astype(np.float64).T
+    assert np.abs(raw - ref).max() > 10 * bound.max() / K
+
+
+def test_tc_tile_rejects_bad_shapes(dev):
+    A = torch.zeros(128, 12, device=dev)
+    with pytest.raises(sq.SpaqrError):
+        sq.spaqr_tc_tile_check(A, torch.zeros(16, 12, device=dev))
+
+
+def test_peaks_plausible(dev):
+    rates = {}
+    for w in ("dfma", "dmma", "ffma", "tf32"):
+        f, ms = sq.spaqr_peak(w, reps=3)
+        assert f > 0 and ms > 0
+        rates[w] = f / ms / 1e9
+    assert 0.2 < rates["dfma"] < 10 and 0.1 < rates["dmma"] < 10
+    assert 10 < rates["ffma"] < 200
+    assert rates["tf32"] > rates["ffma"]
