@@ -507,6 +507,22 @@ int spaqr_peak(int which, int reps, double* flops, double* ms);
  * TIMEOUT, CUDA. */
 int spaqr_tc_tile_check(const float* A, const float* B, float* D, int N, int K, void* stream);
 
+/* The tensor-core matrix product of the mixed-precision factorisation, for
+ * one product: C = alpha A B + beta C with M x K A, K x N B and M x N C in
+ * device memory, FP32, any element strides (A(i, k) = A[i a_rs + k a_cs],
+ * B(k, j) = B[k b_rs + j b_cs], C(i, j) = C[i c_rs + j c_cs]).  a_reflectors:
+ * A is a factored panel read as its unit lower trapezoidal reflector matrix
+ * (entries below the diagonal as stored, 1 on it, 0 above it), the V of
+ * Section 2.4's block Householder step.  The product runs on tcgen05.mma
+ * kind::tf32 with FP32 accumulation in tensor memory: one TF32 pass, or with
+ * split3 three (hi*hi + hi*lo + lo*hi of the TF32 split x = hi + lo, about
+ * FP32 accuracy).  beta = 0 does not read C.  Synchronous on `stream`.
+ * Errors: INVALID_ARG, OOM, TIMEOUT (a bounded tensor-core wait ran out),
+ * CUDA. */
+int spaqr_tc_gemm(int M, int N, int K, float alpha, const float* A, int64_t a_rs, int64_t a_cs,
+                  int a_reflectors, const float* B, int64_t b_rs, int64_t b_cs, float beta, float* C,
+                  int64_t c_rs, int64_t c_cs, int split3, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,11 @@ def solve_upper_right(B, R):
     return X
 
 
+# Leading entries within this fraction of the column norm count as zero in
+# the CPQR's reflectors (beta = -|column|).
+CPQR_SIGN_TOL = 1e-12
+
+
 def cpqr_truncated(M, eps):
     """Column-pivoted Householder QR of M (m x c), truncated at tolerance eps.
 
@@ -117,6 +122,11 @@ def cpqr_truncated(M, eps):
     (no downdating); the pivot is the largest, ties to the lowest column index.
     |R_kk| is taken as that recomputed pivot norm.  Stops at the first step that
     fails the rule.  If M has no rows/columns or R_11 = 0, the rank is 0.
+    The reflector of each step takes the sign tolerance CPQR_SIGN_TOL (see
+    house()): M_p is assembled from sparse blocks, so the pivot column's
+    leading entry is often zero in exact arithmetic, and only a tolerance
+    keeps rounding from choosing the reflection (and with it the coarse basis
+    vectors' signs and every later reflector).
 
     Returns (V, tau, r, rdiag, perm): V is m x r, tau r entries, rdiag the
     pivot norms |R_kk| of the r kept steps plus the first rejected one (if any),
@@ -145,7 +155,7 @@ def cpqr_truncated(M, eps):
         if j != k:
             M[:, [k, j]] = M[:, [j, k]]
             perm[[k, j]] = perm[[j, k]]
-        v, tk, beta = house(M[k:, k])
+        v, tk, beta = house(M[k:, k], CPQR_SIGN_TOL)
         V[k:, k] = v
         tau[k] = tk
         M[k, k] = beta

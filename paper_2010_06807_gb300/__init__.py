@@ -123,6 +123,7 @@ EXPORTS = [
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
     "spaqr_test_fail_alloc", "spaqr_factor_nblocks", "spaqr_factor_block", "spaqr_peak", "spaqr_tc_tile_check",
+    "spaqr_tc_gemm",
 ]
 
 
@@ -183,6 +184,8 @@ def load_library(path=None):
     if hasattr(lib, "spaqr_peak"):
         lib.spaqr_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.spaqr_tc_tile_check.argtypes = [vp, vp, vp, i32, i32, vp]
+        lib.spaqr_tc_gemm.argtypes = [i32, i32, i32, ctypes.c_float, vp, i64, i64, i32, vp, i64, i64,
+                                      ctypes.c_float, vp, i64, i64, i32, vp]
     if path is None:
         _lib = lib
     return lib
@@ -720,3 +723,18 @@ def spaqr_tc_tile_check(A, B, stream=None):
     _check(_lib.spaqr_tc_tile_check(A.data_ptr(), B.data_ptr(), D.data_ptr(), B.shape[0], A.shape[1],
                                     _stream_ptr(stream)))
     return D
+
+
+def spaqr_tc_gemm(A, B, C, alpha=1.0, beta=0.0, reflectors=False, split3=False, stream=None):
+    """C = alpha A B + beta C in place on the tensor cores (spaqr_tc_gemm):
+    A (M x K), B (K x N), C (M x N) float32 CUDA tensors with any strides;
+    reflectors: A read as its unit lower trapezoidal reflector matrix."""
+    load_library()
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K or tuple(C.shape) != (M, N):
+        raise ValueError("shapes do not match")
+    _check(_lib.spaqr_tc_gemm(M, N, K, float(alpha), A.data_ptr(), A.stride(0), A.stride(1), int(bool(reflectors)),
+                              B.data_ptr(), B.stride(0), B.stride(1), float(beta), C.data_ptr(), C.stride(0),
+                              C.stride(1), int(bool(split3)), _stream_ptr(stream)))
+    return C

@@ -78,6 +78,11 @@ constexpr int64_t kBigCPQR = 1 << 17;   // n_p x ncols from which an interface u
 constexpr int QR_CS = 8;     // CTAs per cluster of the large-front QR
 constexpr int64_t kBigQR = 1 << 16;     // m x n from which a front uses a cluster
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
+// CPQR reflectors: a pivot column's leading entry within this fraction of
+// the column's norm counts as zero (beta = -norm).  M_p is assembled from
+// sparse blocks, so that entry is often zero in exact arithmetic, and the
+// tolerance keeps rounding from choosing the reflection.
+constexpr double kCpqrSignTol = 1e-12;
 
 template <class real>
 __global__ void __launch_bounds__(NT) k_qr(const QRTask<real>* __restrict__ tasks, int prow) {
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
             if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
         }
         __syncthreads();
-        const double tkd = cta_house(M + k, c, k, m, red);
+        const double tkd = cta_house(M + k, c, k, m, red, kCpqrSignTol);
         const real tk = (real)tkd;
         if (threadIdx.x == 0) t.tau[k] = tk;
         for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
@@ -423,7 +428,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
         cl.sync();
         if (stop) break;
         if (q == owner) {
-            const double tkd = cta_house(M + k, c, k, m, red);
+            const double tkd = cta_house(M + k, c, k, m, red, kCpqrSignTol);
             if (threadIdx.x == 0) t.tau[k] = (real)tkd;
         }
         cl.sync();

@@ -59,3 +59,51 @@ def test_peaks_plausible(dev):
     assert 0.2 < rates["dfma"] < 10 and 0.1 < rates["dmma"] < 10
     assert 10 < rates["ffma"] < 200
     assert rates["tf32"] > rates["ffma"]
+
+
+def _refl(P):
+    """Unit lower trapezoidal reflector matrix of a stored panel."""
+    V = np.tril(P, -1)
+    k = min(P.shape)
+    V[np.arange(k), np.arange(k)] = 1.0
+    return V
+
+
+@pytest.mark.parametrize("M,N,K,layout,refl,alpha,beta", [
+    (200, 70, 45, "cc", False, 1.5, -0.5),
+    (128, 128, 32, "rr", False, 1.0, 0.0),
+    (1, 1, 1, "cc", False, 2.0, 1.0),
+    (300, 257, 129, "rc", True, -1.0, 1.0),
+    (1300, 600, 370, "cr", True, -1.0, 1.0),
+    (90, 33, 0, "cc", False, 1.0, 0.25),
+])
+@pytest.mark.parametrize("split3", [False, True])
+def test_tc_gemm_matches_fp64(dev, M, N, K, layout, refl, alpha, beta, split3):
+    """C = alpha A B + beta C on the tensor cores against an FP64 product:
+    ragged tiles on every edge, both memory orders of A and B, the reflector
+    view of A, K = 0.  One TF32 pass is within the FP32-accumulation bound of
+    the TF32-rounded operands; three passes within a few FP32 roundings of
+    the exact product."""
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((K, N)).astype(np.float32)
+    C0 = rng.standard_normal((M, N)).astype(np.float32)
+
+    def place(x, order):
+        t = torch.from_numpy(np.ascontiguousarray(x if order == "r" else x.T)).to(dev)
+        return t if order == "r" else t.T
+
+    Ad, Bd = place(A, layout[0]), place(B, layout[1])
+    Cd = place(C0, "c")
+    sq.spaqr_tc_gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, reflectors=refl, split3=split3)
+    got = Cd.cpu().numpy().astype(np.float64)
+    Ae = _refl(A) if refl else A
+    if split3:
+        ref = alpha * (Ae.astype(np.float64) @ B.astype(np.float64)) + beta * C0
+        mag = np.abs(alpha) * (np.abs(Ae) @ np.abs(B)) + np.abs(beta * C0)
+        assert np.all(np.abs(got - ref) <= (3 * K + 8) * np.finfo(np.float32).eps * mag + 1e-30)
+    else:
+        At, Bt = tf32_round(Ae), tf32_round(B)
+        ref = alpha * (At.astype(np.float64) @ Bt.astype(np.float64)) + beta * C0
+        mag = np.abs(alpha) * (np.abs(At).astype(np.float64) @ np.abs(Bt).astype(np.float64)) + np.abs(beta * C0)
+        assert np.all(np.abs(got - ref) <= (2 * K + 4) * np.finfo(np.float32).eps * mag + 1e-30)

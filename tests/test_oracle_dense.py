@@ -126,3 +126,30 @@ def test_cpqr_degenerate():
     M = np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 0.0]])
     V, tau, r, rd, perm = dense.cpqr_truncated(M, 0.0)
     assert perm[0] == 0
+
+
+def test_cpqr_zero_leading_entry_takes_negative_beta():
+    """A pivot column whose leading entry is zero in exact arithmetic: exact
+    zero and rounding residue of either sign give the same reflectors and
+    the same R (beta = -|column|), so rounding cannot choose the coarse
+    basis; a leading entry well outside the tolerance keeps LAPACK's sign."""
+    base = np.array([[0.0, 1.0, 0.5],
+                     [3.0, 0.2, 0.1],
+                     [4.0, 0.3, 0.7],
+                     [0.0, 0.4, 0.2]])
+    outs = []
+    for a in (0.0, 1e-17, -1e-17):
+        M = base.copy()
+        M[0, 0] = a
+        V, tau, r, rd, perm = dense.cpqr_truncated(M, 0.0)
+        assert perm[0] == 0 and r == 3
+        R = dense.apply_qt(V, tau, M[:, perm])
+        assert R[0, 0] < 0
+        outs.append((V, tau, R))
+    for V, tau, R in outs[1:]:
+        np.testing.assert_allclose(V, outs[0][0], atol=1e-15)
+        np.testing.assert_allclose(R, outs[0][2], atol=1e-14)
+    M = base.copy()
+    M[0, 0] = -1e-6
+    V, tau, r, rd, perm = dense.cpqr_truncated(M, 0.0)
+    assert dense.apply_qt(V, tau, M[:, perm])[0, 0] > 0
