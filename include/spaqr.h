@@ -51,9 +51,12 @@ extern "C" {
 #define SPAQR_ERR_NO_DEVICE     -8   /* no CUDA device is visible */
 
 /* precision of the factorisation and of its application; GMRES, the column
- * scaling and the CPQR rank decisions are always FP64 */
-#define SPAQR_FP64 0
-#define SPAQR_FP32 1
+ * scaling, the Householder scalars and the CPQR rank decisions are always
+ * FP64 */
+#define SPAQR_FP64 0   /* FP64 storage and arithmetic */
+#define SPAQR_FP32 1   /* FP32 storage; the contractions of large fronts on the tensor
+                          cores in three TF32 passes (about FP32 accuracy) */
+#define SPAQR_TF32 2   /* FP32 storage; those contractions in one TF32 pass */
 
 /* Row matchings of the ordering of a general matrix (spaqr_order_general). */
 #define SPAQR_MATCH_GREEDY      0   /* largest |a_ij| first, then augmenting paths */
@@ -137,7 +140,8 @@ typedef struct {
     int64_t peak_bytes;        /* most device bytes the factorisation held at once (factor + temporaries) */
     int64_t workspace_rows;    /* scratch rows per right-hand side of one application (level vectors
                                   and partial sums), in elements of the factor's precision */
-    int32_t precision;         /* SPAQR_FP64 or SPAQR_FP32: storage and arithmetic of the factor */
+    int32_t precision;         /* SPAQR_FP64 or SPAQR_FP32: storage of the factor */
+    int32_t tc_levels;         /* levels whose fronts were applied on the tensor cores */
 } spaqr_info;
 
 /* Per-level diagnostics (spaqr_factor_level), level index k = 0 at the
@@ -449,6 +453,13 @@ int spaqr_factor_tuning(const spaqr_factor_t* F, int nrhs, int32_t* forms, int c
  * results are identical).  Off, or while profiling is on, every iteration
  * launches the kernels directly on the caller's stream. */
 void spaqr_use_graphs(int on);
+
+/* Process-wide switch (default on): factorisations with FP32 storage
+ * (SPAQR_FP32, SPAQR_TF32) apply the reflectors of the levels whose fronts
+ * are large on the tensor cores (spaqr_tc_gemm's products: compact-WY form
+ * Q^T B = B - V T^T (V^T B), Section 2.4).  Off, every front is applied on the
+ * CUDA cores as in the FP64 form.  Read when a factorisation starts. */
+void spaqr_use_tensor_cores(int on);
 
 /* Testing aid (host-side fault injection; the paper has no counterpart):
  * after `after` more successful device allocations of the library, the next

@@ -83,7 +83,7 @@ class _Info(ctypes.Structure):
                 ("rank_sum", ctypes.c_int64), ("size_sum", ctypes.c_int64),
                 ("phase_ms", ctypes.c_double * 4), ("top_size", ctypes.c_int32),
                 ("peak_bytes", ctypes.c_int64), ("workspace_rows", ctypes.c_int64),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("tc_levels", ctypes.c_int32)]
 
 
 class _BlockInfo(ctypes.Structure):
@@ -123,7 +123,7 @@ EXPORTS = [
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
     "spaqr_test_fail_alloc", "spaqr_factor_nblocks", "spaqr_factor_block", "spaqr_peak", "spaqr_tc_tile_check",
-    "spaqr_tc_gemm",
+    "spaqr_tc_gemm", "spaqr_use_tensor_cores",
 ]
 
 
@@ -174,6 +174,8 @@ def load_library(path=None):
         lib.spaqr_profile.argtypes = [i32]
         lib.spaqr_profile.restype = None
         lib.spaqr_use_graphs.argtypes = [i32]
+        lib.spaqr_use_tensor_cores.argtypes = [i32]
+        lib.spaqr_use_tensor_cores.restype = None
         lib.spaqr_test_fail_alloc.argtypes = [i64]
         lib.spaqr_test_fail_alloc.restype = None
         lib.spaqr_use_graphs.restype = None
@@ -438,6 +440,7 @@ class Factor:
 
 SPAQR_FP64 = 0
 SPAQR_FP32 = 1
+SPAQR_TF32 = 2
 # doubles of the fixed device scratch array of spaqr_solve_noalloc (include/spaqr.h)
 SPAQR_NOALLOC_SCRATCH_DOUBLES = 2 * 1024 * 1024
 
@@ -446,14 +449,16 @@ def spaqr_factor(ordering, rowptr, colind, val, eps=1e-2, nlevels=0, skip=2, sca
                  col_normalize=1, precision="fp64", stream=None):
     """Numeric spaQR factorisation (Algorithm 2) on the current CUDA device.
 
-    precision: "fp64" (plain form) or "fp32" (mixed form: factor stored and
-    applied in FP32; rank decisions and GMRES stay FP64).
+    precision: "fp64" (plain form), "fp32" (mixed form: factor stored and
+    applied in FP32, the contractions of large fronts on the tensor cores in
+    three TF32 passes; rank decisions and GMRES stay FP64) or "tf32" (as
+    "fp32" with one TF32 pass).
     """
     load_library()
     csr, keep = _make_csr(rowptr, colind, val)
     o = _Opts()
     _lib.spaqr_opts_default(ctypes.byref(o))
-    o.precision = {"fp64": SPAQR_FP64, "fp32": SPAQR_FP32}[precision]
+    o.precision = {"fp64": SPAQR_FP64, "fp32": SPAQR_FP32, "tf32": SPAQR_TF32}[precision]
     o.eps = float(eps)
     o.nlevels = int(nlevels)
     o.skip = int(skip)
@@ -655,6 +660,12 @@ def spaqr_profile(on=True):
     """Bracket every library launch with CUDA events (for per-kernel timing)."""
     load_library()
     _lib.spaqr_profile(1 if on else 0)
+
+
+def spaqr_use_tensor_cores(on=True):
+    """Tensor-core application of large fronts in the FP32 / TF32 forms (default on)."""
+    load_library()
+    _lib.spaqr_use_tensor_cores(1 if on else 0)
 
 
 def spaqr_autotune(F, nrhs, stream=None):

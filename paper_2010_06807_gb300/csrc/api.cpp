@@ -314,6 +314,9 @@ bool prof_on() {
 std::atomic<bool> g_graphs{true};
 bool graphs_on() { return g_graphs.load(); }
 
+std::atomic<bool> g_tensor_cores{true};
+bool tensor_cores_on() { return g_tensor_cores.load(); }
+
 // Host-side fault injection: the allocation that finds the countdown at 0
 // reports failure (as a failed cudaMallocAsync would), once; -1 = off.
 std::atomic<int64_t> g_fail_alloc{-1};
@@ -346,6 +349,7 @@ extern "C" void spaqr_stats_reset(void) {
 }
 
 extern "C" void spaqr_use_graphs(int on) { spaqr::g_graphs.store(on != 0); }
+extern "C" void spaqr_use_tensor_cores(int on) { spaqr::g_tensor_cores.store(on != 0); }
 
 extern "C" void spaqr_test_fail_alloc(int64_t after) { spaqr::g_fail_alloc.store(after < 0 ? -1 : after); }
 

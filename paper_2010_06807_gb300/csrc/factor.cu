@@ -33,6 +33,7 @@
 #include "dense.cuh"
 #include "spaqr_internal.h"
 #include "tasks.h"
+#include "tcgemm.h"
 
 #define SPAQR_LAUNCH(kind, flops, bytes, stream, ...)                            \
     do {                                                                         \
@@ -155,6 +156,101 @@ __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask<real>* __res
         const Mat<real> B{t.B, 1, t.ldb, rmap};
         if (staged) cta_apply_q_staged(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
         else cta_apply_q(F.V, F.ldv, F.m, F.n, F.T, F.n, false, B, t.q, true, W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core application of a level's fronts (FP32 storage).  A front's
+// rows R(s) of its columns C(s) \ {s} are copied into one dense m x w matrix
+// B, and Q_s^T B = B - V T^T (V^T B) is formed by products on the tensor
+// cores (tcgemm.h) with the full n x n compact-WY factor T of the front's n
+// reflectors (Section 2.4's block Householder step); T comes from
+// G = V^T V and tau.  Fronts of one colour share no row cluster, so their
+// copies are disjoint; the colours run in order.
+// ---------------------------------------------------------------------------
+
+// One column panel j of a front: rows R(s) of the panel <-> the panel's
+// columns in the front's dense copy.
+struct FrontCopy {
+    float* panel;     // first column of panel j (column-major, ld)
+    int64_t ld;
+    float* dense;     // first of its columns in the dense copy (ld m)
+    int m, ncol;
+    int seg_begin, nseg;   // row segments R(s) in panel j, in front row order
+};
+
+// to_dense = 1: panel -> dense copy; 0: dense copy -> panel.  One CTA per
+// (front, panel); smem: the front's row map (m ints).
+__global__ void __launch_bounds__(NT) k_front_copy(const FrontCopy* __restrict__ tasks, const Seg* __restrict__ segs,
+                                                   int to_dense) {
+    extern __shared__ int rmap_sm[];
+    const FrontCopy c = tasks[blockIdx.x];
+    int pos = 0;
+    for (int s = 0; s < c.nseg; s++) {
+        const Seg g = segs[c.seg_begin + s];
+        for (int r = threadIdx.x; r < g.len; r += NT) rmap_sm[pos + r] = (int)(g.off + r);
+        pos += g.len;
+    }
+    __syncthreads();
+    const int64_t tot = (int64_t)c.m * c.ncol;
+    for (int64_t o = threadIdx.x; o < tot; o += NT) {
+        const int r = (int)(o % c.m), col = (int)(o / c.m);
+        float* p = c.panel + rmap_sm[r] + (int64_t)col * c.ld;
+        float* d = c.dense + r + (int64_t)col * c.m;
+        if (to_dense) *d = *p;
+        else *p = *d;
+    }
+}
+
+struct TfullTask {
+    const float* G;     // n x n, G = V^T V (ld n)
+    const float* tau;   // n
+    float* T;           // out: n x n upper triangular (ld n), zeros below
+    float* X;           // scratch n x 16
+    int n;
+};
+
+// Full compact-WY factor of a front's reflectors, Q = I - V T V^T, by blocks
+// of 16 columns: the diagonal block by the column recurrence
+// T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), the rows above it by
+// T_12 = -T_11 G_12 T_22 (the product of two block reflectors).  One CTA per
+// front, FP32.
+__global__ void __launch_bounds__(NT) k_tfull(const TfullTask* __restrict__ tasks) {
+    const TfullTask t = tasks[blockIdx.x];
+    const int n = t.n;
+    const float* G = t.G;
+    float* T = t.T;
+    for (int64_t o = threadIdx.x; o < (int64_t)n * n; o += NT) {
+        const int r = (int)(o % n), c = (int)(o / n);
+        if (r > c) T[o] = 0.0f;
+    }
+    for (int c0 = 0; c0 < n; c0 += NB) {
+        const int cb = n - c0 < NB ? n - c0 : NB;
+        for (int k = 0; k < cb; k++) {
+            const float tk = t.tau[c0 + k];
+            for (int i = threadIdx.x; i < k; i += NT) {
+                float s = 0.0f;
+                for (int u = i; u < k; u++) s += T[(c0 + i) + (int64_t)(c0 + u) * n] * G[(c0 + u) + (int64_t)(c0 + k) * n];
+                T[(c0 + i) + (int64_t)(c0 + k) * n] = -tk * s;
+            }
+            if (threadIdx.x == 0) T[(c0 + k) + (int64_t)(c0 + k) * n] = tk;
+            __syncthreads();
+        }
+        if (c0 == 0) continue;
+        for (int o = threadIdx.x; o < c0 * cb; o += NT) {
+            const int i = o % c0, j = o / c0;
+            float s = 0.0f;
+            for (int u = i; u < c0; u++) s += T[i + (int64_t)u * n] * G[u + (int64_t)(c0 + j) * n];
+            t.X[i + (int64_t)j * c0] = s;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < c0 * cb; o += NT) {
+            const int i = o % c0, j = o / c0;
+            float s = 0.0f;
+            for (int l = 0; l <= j; l++) s += t.X[i + (int64_t)l * c0] * T[(c0 + l) + (int64_t)(c0 + j) * n];
+            T[i + (int64_t)(c0 + j) * n] = -s;
+        }
+        __syncthreads();
     }
 }
 
@@ -884,6 +980,7 @@ void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& 
 }
 
 const int kSmemMax = 200 * 1024;
+const int kTcMinN = 48;   // reflectors of a front from which its application is a tensor-core product
 const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
 }  // namespace
@@ -927,6 +1024,186 @@ void launch_qr(Ctx& C, const std::vector<QRTask<real>>& all, size_t esz, int kin
     }
 }
 
+// Whether a level's fronts go to the tensor cores: the level's apply work is
+// dominated by fronts wide enough (n reflectors) to be dense contractions.
+bool tc_level(const StepPlan& sp, const LevelLayout& lay, const std::vector<int64_t>& sz) {
+    double big = 0.0, all = 0.0;
+    for (size_t f = 0; f < sp.fronts.size(); f++) {
+        const int s = sp.fronts[f];
+        double w = 0.0;
+        for (size_t t = 1; t < sp.C[f].size(); t++) w += (double)sz[sp.C[f][t]];
+        const double fl = (4.0 * lay.H[s] * sz[s] - 2.0 * sz[s] * sz[s]) * w;
+        all += fl;
+        if (sz[s] >= kTcMinN) big += fl;
+    }
+    return all > 0.0 && big >= 0.8 * all;
+}
+
+// Tensor-core application of the fronts of a level (FP32 storage; see
+// k_front_copy / k_tfull): per front, G = V^T V and T (once), then per
+// colour the dense copies B of the fronts' columns, W = V^T B, W <- T^T W,
+// B <- B - V W, and the copies written back.  split3: three TF32 passes for
+// the application products (G always takes three).
+int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std::vector<int64_t>& sz, float* arena,
+                   const std::vector<float*>& ftau, bool split3, int* d_err) {
+    cudaStream_t st = C.st;
+    struct FI {
+        int f, s, m, n, w;
+        int64_t oB, oG, oT, oW, oW2, oX;
+    };
+    std::vector<FI> fi;
+    int64_t tot = 0;
+    for (size_t f = 0; f < sp.fronts.size(); f++) {
+        const int s = sp.fronts[f];
+        if (sz[s] == 0) continue;
+        int64_t w = 0;
+        for (size_t t = 1; t < sp.C[f].size(); t++) w += sz[sp.C[f][t]];
+        if (w == 0) continue;
+        FI x;
+        x.f = (int)f;
+        x.s = s;
+        x.m = (int)lay.H[s];
+        x.n = (int)sz[s];
+        x.w = (int)w;
+        x.oB = tot;
+        tot += (int64_t)x.m * w;
+        x.oG = tot;
+        tot += (int64_t)x.n * x.n;
+        x.oT = tot;
+        tot += (int64_t)x.n * x.n;
+        x.oW = tot;
+        tot += (int64_t)x.n * w;
+        x.oW2 = tot;
+        tot += (int64_t)x.n * w;
+        x.oX = tot;
+        tot += (int64_t)x.n * NB;
+        tot = (tot + 31) & ~(int64_t)31;
+        fi.push_back(x);
+    }
+    if (fi.empty()) return SPAQR_OK;
+    float* S = C.alloc<float>(tot, false);
+    if (C.rc) return C.rc;
+    auto vt = [&](const FI& x) {   // V^T as a product operand: (i, k) = V(k, i)
+        return GemmOperand{arena + lay.poff[x.s], lay.H[x.s], 1, 1, 1};
+    };
+    {
+        std::vector<GemmTask> g;
+        std::vector<TfullTask> tf;
+        for (const FI& x : fi) {
+            GemmTask t{};
+            t.a = vt(x);
+            t.bt = vt(x);
+            t.c = S + x.oG;
+            t.c_rs = 1;
+            t.c_cs = x.n;
+            t.M = x.n;
+            t.N = x.n;
+            t.K = x.m;
+            t.alpha = 1.0f;
+            t.beta = 0.0f;
+            g.push_back(t);
+            tf.push_back(TfullTask{S + x.oG, ftau[x.f], S + x.oT, S + x.oX, x.n});
+        }
+        gemm_tiles(g);
+        GemmTask* dg = C.upload(g, false);
+        TfullTask* dtf = C.upload(tf, false);
+        if (C.rc) return C.rc;
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dg, g, true, d_err, st));
+        C.launched();
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, k_tfull<<<(unsigned)tf.size(), NT, 0, st>>>(dtf));
+        C.launched();
+    }
+    size_t a = 0;
+    while (a < fi.size()) {
+        const int colour = sp.colour[fi[a].f];
+        size_t b = a;
+        while (b < fi.size() && sp.colour[fi[b].f] == colour) b++;
+        std::vector<FrontCopy> cp;
+        std::vector<Seg> segs;
+        std::vector<GemmTask> gw, gw2, gu;
+        double fl = 0.0, by = 0.0;
+        int mmax = 1;
+        for (size_t q = a; q < b; q++) {
+            const FI& x = fi[q];
+            mmax = std::max(mmax, x.m);
+            int64_t coff = 0;
+            for (size_t t = 1; t < sp.C[x.f].size(); t++) {
+                const int j = sp.C[x.f][t];
+                if (sz[j] == 0) continue;
+                FrontCopy c;
+                c.panel = arena + lay.poff[j];
+                c.ld = lay.H[j];
+                c.dense = S + x.oB + coff * x.m;
+                c.m = x.m;
+                c.ncol = (int)sz[j];
+                c.seg_begin = (int)segs.size();
+                for (int i : sp.R[x.f]) {
+                    const int e = sp.find(i, j);
+                    if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
+                    if (sz[i] > 0) segs.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
+                }
+                c.nseg = (int)segs.size() - c.seg_begin;
+                cp.push_back(c);
+                coff += sz[j];
+                by += 16.0 * x.m * sz[j] + 8.0 * x.m * x.n;
+            }
+            fl += (4.0 * x.m * x.n - 2.0 * x.n * x.n) * x.w;
+            GemmTask t{};
+            t.a = vt(x);
+            t.bt = GemmOperand{S + x.oB, x.m, 1, 0, 0};
+            t.c = S + x.oW;
+            t.c_rs = 1;
+            t.c_cs = x.n;
+            t.M = x.n;
+            t.N = x.w;
+            t.K = x.m;
+            t.alpha = 1.0f;
+            t.beta = 0.0f;
+            gw.push_back(t);
+            t.a = GemmOperand{S + x.oT, x.n, 1, 0, 0};   // T^T: (i, k) = T(k, i)
+            t.bt = GemmOperand{S + x.oW, x.n, 1, 0, 0};
+            t.c = S + x.oW2;
+            t.K = x.n;
+            gw2.push_back(t);
+            t.a = GemmOperand{arena + lay.poff[x.s], 1, lay.H[x.s], 1, 0};   // V: (i, k) = V(i, k)
+            t.bt = GemmOperand{S + x.oW2, x.n, 1, 0, 0};
+            t.c = S + x.oB;
+            t.c_rs = 1;
+            t.c_cs = x.m;
+            t.M = x.m;
+            t.N = x.w;
+            t.K = x.n;
+            t.alpha = -1.0f;
+            t.beta = 1.0f;
+            gu.push_back(t);
+        }
+        gemm_tiles(gw);
+        gemm_tiles(gw2);
+        gemm_tiles(gu);
+        FrontCopy* dcp = C.upload(cp, false);
+        Seg* dsg = C.upload(segs, false);
+        GemmTask* dw = C.upload(gw, false);
+        GemmTask* dw2 = C.upload(gw2, false);
+        GemmTask* du = C.upload(gu, false);
+        if (C.rc) return C.rc;
+        const size_t smem = (size_t)mmax * sizeof(int);
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st,
+                     k_front_copy<<<(unsigned)cp.size(), NT, smem, st>>>(dcp, dsg, 1));
+        C.launched();
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dw, gw, split3, d_err, st));
+        C.launched();
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dw2, gw2, split3, d_err, st));
+        C.launched();
+        SPAQR_LAUNCH(KK_FRONT_APPLY, fl, by, st, launch_tc_gemm(du, gu, split3, d_err, st));
+        C.launched();
+        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st,
+                     k_front_copy<<<(unsigned)cp.size(), NT, smem, st>>>(dcp, dsg, 0));
+        C.launched();
+        a = b;
+    }
+    return SPAQR_OK;
+}
+
 template <class real>
 int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spaqr_factor_s* F) {
     Ctx C;
@@ -943,6 +1220,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
     F->precision = sizeof(real) == 8 ? SPAQR_FP64 : SPAQR_FP32;
     F->unscaled = opt->scaling == 0;
     F->esz = (int)sizeof(real);
+    // tensor-core products of the FP32 storage forms: 1 = three TF32 passes, 2 = one
+    const int tcmode = (sizeof(real) == 4 && tensor_cores_on()) ? (opt->precision == SPAQR_TF32 ? 2 : 1) : 0;
     static std::once_flag attr_once;
     std::call_once(attr_once, [&] {
         C.cuda(cudaFuncSetAttribute(k_front_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
@@ -1251,7 +1530,17 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             if (C.rc) return C.rc;
             C.launched();
         }
-        if (!at.empty()) {
+        bool tc_done = false;
+        if constexpr (sizeof(real) == 4) {
+            if (tcmode && !at.empty() && tc_level(sp, lay, sz)) {
+                const int rc = tc_front_apply(C, sp, lay, sz, arena, ftau, tcmode == 1, d_flags + 3);
+                if (rc != SPAQR_OK) return rc;
+                if (C.rc) return C.rc;
+                tc_done = true;
+                F->tc_levels++;
+            }
+        }
+        if (!at.empty() && !tc_done) {
             ApplyTask<real>* d1 = C.upload(at, false);
             ApplyFront<real>* d2 = C.upload(af, false);
             Seg* d3 = C.upload(asg, false);
@@ -2069,6 +2358,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         return SPAQR_ERR_SINGULAR;
     }
     if (flags[2]) { set_error("zero diagonal in a separator factor R_ss"); return SPAQR_ERR_SINGULAR; }
+    if (flags[3]) { set_error("a bounded tensor-core wait ran out"); return SPAQR_ERR_TIMEOUT; }
     return SPAQR_OK;
 }
 
@@ -2098,8 +2388,8 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
         return SPAQR_ERR_INVALID_ARG;
     }
     if (opts->scaling != 0 && opts->scaling != 1) { set_error("scaling must be 0 or 1"); return SPAQR_ERR_INVALID_ARG; }
-    if (opts->precision != SPAQR_FP64 && opts->precision != SPAQR_FP32) {
-        set_error("precision must be SPAQR_FP64 or SPAQR_FP32");
+    if (opts->precision != SPAQR_FP64 && opts->precision != SPAQR_FP32 && opts->precision != SPAQR_TF32) {
+        set_error("precision must be SPAQR_FP64, SPAQR_FP32 or SPAQR_TF32");
         return SPAQR_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -2121,7 +2411,7 @@ extern "C" int spaqr_factor(const spaqr_ordering* ord, const spaqr_csr* A, const
     keep_pool_memory(F->device);
     int rc;
     try {
-        rc = opts->precision == SPAQR_FP32 ? run_factor<float>(ord->o, A, opts, F)
+        rc = opts->precision != SPAQR_FP64 ? run_factor<float>(ord->o, A, opts, F)
                                            : run_factor<double>(ord->o, A, opts, F);
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
@@ -2214,6 +2504,7 @@ extern "C" int spaqr_factor_info(const spaqr_factor_t* F, spaqr_info* out) {
     out->peak_bytes = F->peak_bytes;
     out->workspace_rows = F->ws_rows;
     out->precision = F->precision;
+    out->tc_levels = F->tc_levels;
     return SPAQR_OK;
 }
 

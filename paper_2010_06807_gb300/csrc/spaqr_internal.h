@@ -110,6 +110,7 @@ void prof_add_tally(const LaunchTally& t, int sign);
 bool prof_on();
 void keep_pool_memory(int device);
 bool graphs_on();
+bool tensor_cores_on();   // spaqr_use_tensor_cores
 bool fail_this_alloc();   // fault injection (spaqr_test_fail_alloc)
 int check_csr_location(const spaqr_csr* A);   // A->on_device against where the arrays are
 // INVALID_ARG (with the message) when p is device memory of a GPU other than

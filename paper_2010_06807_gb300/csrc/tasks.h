@@ -354,4 +354,5 @@ struct spaqr_factor_s {
     bool unscaled = false;         // unscaled variant (Section 3.2): narrow solve forms only
     int64_t peak_bytes = 0;        // most device bytes the factorisation held at once
     std::vector<BlockRec> blocks;  // every stored block, level by level (spaqr_factor_block)
+    int tc_levels = 0;             // levels whose fronts were applied on the tensor cores
 };

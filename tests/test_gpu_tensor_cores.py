@@ -1,0 +1,65 @@
+"""The mixed-precision factorisation with its large fronts applied on the
+tensor cores (tcgen05, compact-WY form of Section 2.4's block Householder
+step) against the same factorisation with every front on the CUDA cores, and
+against the FP64 factor through GMRES: the application agrees with the
+CUDA-core FP32 form to FP32-level rounding (three TF32 passes) or TF32-level
+rounding (one pass), ranks agree within 1%, and FP64 GMRES still reaches
+1e-12 with at most one iteration more than the FP64 factor needs (three
+passes)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2010_06807_gb300 as sq
+from synth.convdiff import config_problem, rhs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev(spaqr_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _factor(o, A, eps, precision, tc):
+    sq.spaqr_use_tensor_cores(tc)
+    try:
+        return sq.spaqr_factor(o, *A, eps=eps, precision=precision)
+    finally:
+        sq.spaqr_use_tensor_cores(True)
+
+
+def _rank_sum(F):
+    return sq.spaqr_factor_info(F)["rank_sum"]
+
+
+@pytest.mark.parametrize("kind,n,eps", [("3d_uniform_a", 16, 1e-2), ("3d_uniform_a", 20, 1e-3),
+                                        ("2d_lognormal", 128, 1e-2)])
+def test_tensor_core_apply_matches_cuda_core_apply(dev, kind, n, eps):
+    p = config_problem(kind, n=n)
+    A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
+    o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
+    b = rhs(p, 4)
+    B = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T
+    F64 = sq.spaqr_factor(o, *A, eps=eps)
+    Fcc = _factor(o, A, eps, "fp32", False)
+    assert sq.spaqr_factor_info(Fcc)["tc_levels"] == 0
+    xcc = sq.spaqr_solve(Fcc, B).cpu().numpy()
+    _, it64, _ = sq.spaqr_gmres(F64, *A, B, tol=1e-12)
+    for prec, bar in (("fp32", 2e-4), ("tf32", 5e-2)):
+        F = _factor(o, A, eps, prec, True)
+        assert sq.spaqr_factor_info(F)["tc_levels"] > 0
+        # rank decisions are FP64 on FP32 data: rounding may move a pivot
+        # that sits at the threshold
+        assert abs(_rank_sum(F) - _rank_sum(Fcc)) <= 0.01 * _rank_sum(Fcc)
+        x = sq.spaqr_solve(F, B).cpu().numpy()
+        err = np.linalg.norm(x - xcc, axis=0) / np.linalg.norm(xcc, axis=0)
+        assert err.max() <= bar, (prec, err)
+        X, it, rr = sq.spaqr_gmres(F, *A, B, tol=1e-12)
+        res = np.linalg.norm(b - p.matvec(X.cpu().numpy()), axis=0) / np.linalg.norm(b, axis=0)
+        assert res.max() <= 1e-12 and rr.max() <= 1e-12
+        if prec == "fp32":
+            assert int(it.max()) <= int(it64.max()) + 1
