@@ -36,9 +36,17 @@ METRIC = "factor s + solves/s to rel.resid 1e-12 (mixed/batched vs plain FP64); 
 UNIT = "solves/s"
 KIND, NSIDE, NRHS, EPS, TOL, MAXIT = "2d_lognormal", 256, 16, 1e-2, 1e-12, 300
 WORKLOAD = "convdiff2d_256x256_lognormal_a_pe50_randangle_fp64_eps1e-2_16rhs"
-# FP64 peak on GB300: 152 SMs x 2 DFMA/clk/SM x 2 flops x 2070 MHz (nominal
-# 1.25 TFLOP/s); a DFMA microbenchmark measured 1.19 TFLOP/s at ~1990 MHz.
+# Peaks the rooflines are stated against (TFLOP/s):
+# - FP64 on the CUDA cores ("alu"): 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz,
+#   derived from the unit counts and the maximum clock (1.259; the nominal
+#   1.25 TFLOP/s of GB300's FP64); the DFMA microbenchmark is measured live
+#   beside it (spaqr_peak);
+# - FP32 on the CUDA cores ("alu"): 152 SMs x 128 FFMA/clk x 2 x 2070 MHz;
+# - TF32 on the tensor cores ("tensor"): the measured dense BF16 peak of
+#   MEASURED_PEAKS.json x the nominal TF32/BF16 ratio 1.1 / 2.25.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # averaged over the kind's launches (one-CTA and cluster forms), from the ncu
 # launch list of the current kernels on this workload
@@ -57,7 +65,8 @@ def _args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload (no mixed / 3D / batched / serving lines)")
-    ap.add_argument("--serve-s", type=float, default=1.0)
+    ap.add_argument("--serve-s", type=float, default=10.0,
+                    help="seconds of Poisson arrivals per steady-state serving run")
     a = ap.parse_args()
     if a.steps < 1 or a.warmup < 0 or a.gpus < 1:
         ap.error("need --steps >= 1, --warmup >= 0, --gpus >= 1")
@@ -95,6 +104,46 @@ def _pct(v, q):
         return None
     k = max(0, min(len(v) - 1, int(round(q / 100.0 * (len(v) - 1)))))
     return v[k]
+
+
+def measure_peaks(sq, reps=5):
+    """Arithmetic peak microbenchmarks of this GPU (spaqr_peak): TFLOP/s of
+    DFMA, DMMA, FFMA and tcgen05 TF32, measured now."""
+    out = {}
+    for w in ("dfma", "dmma", "ffma", "tf32"):
+        f, ms = sq.spaqr_peak(w, reps=reps)
+        out[w] = f / ms / 1e9
+    return out
+
+
+def kernel_rooflines(kstats, peaks, fp64, bf16_tflops):
+    """One roofline per kernel kind with algorithmic flops: achieved = the
+    kind's algorithmic flops (the per-unit counts of the launch accounting)
+    / its CUDA-event time over the profiled pass.  FP64 kinds against the
+    derived FP64 peak; FP32 kinds against the derived FFMA peak; the
+    tensor-core front application against the TF32 peak (measured BF16 x the
+    nominal TF32 / BF16 ratio).  The live microbenchmark of the same pipe is
+    given beside each."""
+    out = []
+    for name, d in sorted(kstats.items(), key=lambda kv: -kv[1]["total_ms"]):
+        if not d["launches"] or d["flops"] <= 0 or d["total_ms"] <= 0:
+            continue
+        if name == "front_apply_tc":
+            bound, peak, meas = "tensor", bf16_tflops * TF32_OVER_BF16, peaks.get("tf32")
+            note = "TF32 tensor cores: measured BF16 x 1.1/2.25 (of measured)"
+        elif fp64:
+            bound, peak, meas = "alu", FP64_PEAK_TFLOPS, peaks.get("dfma")
+            note = "FP64 CUDA cores: 152 SMs x 4 flop/clk x 2070 MHz (derived)"
+        else:
+            bound, peak, meas = "alu", FP32_PEAK_TFLOPS, peaks.get("ffma")
+            note = "FP32 CUDA cores: 152 SMs x 256 flop/clk x 2070 MHz (derived)"
+        ach = d["flops"] / (d["total_ms"] * 1e-3) / 1e12
+        out.append({"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_note": note, "peak_microbenchmark": meas,
+                    "launches": d["launches"], "total_ms": d["total_ms"],
+                    "algorithmic_gflop_per_launch": d["flops"] / d["launches"] / 1e9,
+                    "traffic": TRAFFIC.get(name) if fp64 else None})
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -286,6 +335,26 @@ def reference_arm(a):
     return 0
 
 
+def _profiled_kinds(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, passes=2, scaling=1):
+    """Per-kernel-kind CUDA-event times and algorithmic flops of `passes`
+    factor + GMRES steps of one form (profiling brackets every launch with
+    events and turns graph replay off, so it runs apart from timed steps)."""
+    rp, ci, va = A
+    sq.spaqr_stats_reset()
+    sq.spaqr_profile(True)
+    with torch.cuda.stream(st):
+        for _ in range(passes):
+            flush.zero_()
+            F = sq.spaqr_factor(ordl, rp, ci, va, eps=eps, precision=precision, scaling=scaling, stream=st)
+            Xd.zero_()
+            sq.spaqr_gmres(F, rp, ci, va, Bd, X=Xd, tol=TOL, maxit=MAXIT, stream=st)
+            del F
+    torch.cuda.synchronize()
+    sq.spaqr_profile(False)
+    _, ks = sq.spaqr_stats()
+    return ks
+
+
 def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, warmup, scaling=1):
     """Time `steps` factor + GMRES steps of one form (after `warmup` untimed ones)
     with CUDA events on `st`, L2 flushed between steps."""
@@ -317,7 +386,8 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
     return {"solves_per_s": nrhs * len(tot) / (sum(tot) / 1e3), "factor_ms_p50": _pct(fac, 50),
             "gmres_ms_p50": _pct(gm, 50), "step_ms_p50": _pct(tot, 50), "gmres_iters_max": max(iters),
             "relres_max": float(rr.max()), "rank_sum": info["rank_sum"], "size_sum": info["size_sum"],
-            "factor_mbytes": info["factor_bytes"] / 2 ** 20}, X.clone()
+            "factor_mbytes": info["factor_bytes"] / 2 ** 20, "factor_gflop": info["factor_flops"] / 1e9,
+            "tensor_core_levels": info["tc_levels"]}, X.clone()
 
 
 def _high_contrast(sq, torch, np, dev, st, flush):
@@ -525,6 +595,8 @@ def ours(a):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     sq.load_library()
+    peaks = measure_peaks(sq)
+    bf16 = float(_peaks().get("bf16_tflops", 1900.0))
 
     p = config_problem(KIND, n=NSIDE)
     b = rhs(p, NRHS)
@@ -635,7 +707,8 @@ def ours(a):
     ach = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(dname), "kernel": dname,
-            "peak_note": "FP64 DFMA: 152 SMs x 4 flop/clk x 2070 MHz (derived; DFMA microbenchmark 1.19-1.20)",
+            "peak_note": "FP64 CUDA cores: 152 SMs x 4 flop/clk x 2070 MHz (derived)",
+            "peak_microbenchmark": peaks["dfma"], "frac_of_microbenchmark": ach / peaks["dfma"],
             "launches": d["launches"], "avg_launch_ms": per_launch_ms,
             "algorithmic_gflop_per_launch": d["flops"] / d["launches"] / 1e9,
             "algorithmic_mb_per_launch": d["bytes"] / d["launches"] / 2 ** 20}
@@ -662,6 +735,8 @@ def ours(a):
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kstats.items()
                     if v["launches"]},
         "roofline": roof,
+        "rooflines": kernel_rooflines(kstats, peaks, True, bf16),
+        "peaks_measured_tflops": peaks,
         "clocks": clk,
     }
     # the other forms, the extra workloads and the CPU baselines run at N = 1
@@ -672,13 +747,33 @@ def ours(a):
             dist.barrier()
             dist.destroy_process_group()
         return 0
-    # ---- mixed-precision form on the same workload: FP32 factor + FP64 GMRES ----
+    # ---- mixed-precision forms on the same workload: FP32 factor + FP64 GMRES ----
     Xref = Xd.detach().cpu().numpy().copy()
+
+    def relerr(X):
+        X = X.cpu().numpy()
+        return float(np.max(np.linalg.norm(X - Xref, axis=0) / np.linalg.norm(Xref, axis=0)))
+
     mixed, X32 = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp32", 3, 1)
-    X32 = X32.cpu().numpy()
-    mixed["final_error_vs_fp64"] = float(np.max(np.linalg.norm(X32 - Xref, axis=0) / np.linalg.norm(Xref, axis=0)))
-    mixed["note"] = "same workload; FP32 factor and application, FP64 flexible GMRES to 1e-12"
+    mixed["final_error_vs_fp64"] = relerr(X32)
+    mixed["note"] = ("same workload; FP32 factor and application (large fronts on the tensor cores, three TF32 "
+                     "passes), FP64 flexible GMRES to 1e-12")
+    mixed["rooflines"] = kernel_rooflines(
+        _profiled_kinds(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp32"), peaks, False, bf16)
     line["mixed_fp32"] = mixed
+    m1, X1 = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "tf32", 3, 1)
+    m1["final_error_vs_fp64"] = relerr(X1)
+    line["mixed_tf32"] = m1
+    sq.spaqr_use_tensor_cores(False)
+    mc, Xc = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp32", 3, 1)
+    sq.spaqr_use_tensor_cores(True)
+    mc["final_error_vs_fp64"] = relerr(Xc)
+    line["mixed_fp32_cuda_cores"] = mc
+    # ---- the configuration's second tolerance: eps = 1e-4, FP64 ----
+    e4, _ = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, 1e-4, "fp64", 3, 1)
+    e4["rooflines"] = kernel_rooflines(
+        _profiled_kinds(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, 1e-4, "fp64", passes=1), peaks, True, bf16)
+    line["eps1e-4_fp64"] = e4
     # ---- unscaled variant (Sections 2.2 / 3.2) on the same workload: the scaling ablation ----
     un, Xun = _timed_form(sq, torch, ordl, (rp, ci, va), Bd, Xd, st, flush, EPS, "fp64", 3, 1, scaling=0)
     un["final_error_vs_scaled"] = float(np.max(np.linalg.norm(Xun.cpu().numpy() - Xref, axis=0) /
@@ -704,19 +799,39 @@ def ours(a):
     X3 = torch.zeros(NRHS, p3.n, dtype=torch.float64, device=dev).T
     o3 = sq.spaqr_order(p3.rowptr, p3.colind, p3.dims)
     c64, x64 = _timed_form(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, "fp64", 2, 1)
-    c32, x32 = _timed_form(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, "fp32", 2, 1)
+    c64["rooflines"] = kernel_rooflines(
+        _profiled_kinds(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, "fp64", passes=1), peaks, True, bf16)
     x64 = x64.cpu().numpy()
-    c32["final_error_vs_fp64"] = float(np.max(np.linalg.norm(x32.cpu().numpy() - x64, axis=0) /
-                                              np.linalg.norm(x64, axis=0)))
-    line["convdiff3d_32cube_eps1e-2_16rhs"] = {"fp64": c64, "fp32_factor_fp64_gmres": c32}
+    out3 = {"fp64": c64}
+    for name, prec, tc in (("fp32_factor_fp64_gmres", "fp32", True), ("tf32_factor_fp64_gmres", "tf32", True),
+                           ("fp32_cuda_cores_factor_fp64_gmres", "fp32", False)):
+        sq.spaqr_use_tensor_cores(tc)
+        c32, x32 = _timed_form(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, prec, 2, 1)
+        c32["final_error_vs_fp64"] = float(np.max(np.linalg.norm(x32.cpu().numpy() - x64, axis=0) /
+                                                  np.linalg.norm(x64, axis=0)))
+        if name == "fp32_factor_fp64_gmres":
+            c32["rooflines"] = kernel_rooflines(
+                _profiled_kinds(sq, torch, o3, A3, B3, X3, st, flush, 1e-2, prec, passes=1), peaks, False, bf16)
+        out3[name] = c32
+    sq.spaqr_use_tensor_cores(True)
+    line["convdiff3d_32cube_eps1e-2_16rhs"] = out3
     line["batched_64x2d"] = _batched(sq, torch, np, dev, st, flush)
     line["high_contrast_2d_ablation"] = _high_contrast(sq, torch, np, dev, st, flush)
     line["general_sparse"] = _general(sq, torch, np, dev, st, flush)
     if not a.no_serve:
         from paper_2010_06807_gb300.serve import run_plain, run_workload
         srv = {}
+        # the configured stream (2000/s): FP32 factors for serve_s seconds;
+        # FP64 factors for 2 s (far over capacity, its queue only grows)
+        srv["fp32"] = run_workload(duration=a.serve_s, precision="fp32", device=dev)
+        srv["fp64"] = run_workload(duration=2.0, precision="fp64", device=dev)
+        # steady state: 80% of the throughput each form reached over capacity,
+        # serve_s seconds (one factor request per second throughout)
         for prec in ("fp32", "fp64"):
-            srv[prec] = run_workload(duration=a.serve_s, precision=prec, device=dev)
+            rate = 0.8 * srv[prec]["solves_per_s"]
+            r = run_workload(duration=a.serve_s, rate=rate, precision=prec, device=dev)
+            r["sustained"] = r["wall_s"] <= a.serve_s + 2.0
+            srv[f"{prec}_steady"] = r
         srv["plain_fp64_one_at_a_time"] = run_plain(requests=200, device=dev)
         line["serving_8x3d_poisson2000"] = srv
     try:

@@ -179,12 +179,18 @@ struct FrontCopy {
     int seg_begin, nseg;   // row segments R(s) in panel j, in front row order
 };
 
-// to_dense = 1: panel -> dense copy; 0: dense copy -> panel.  One CTA per
-// (front, panel); smem: the front's row map (m ints).
+constexpr int kCopyCols = 8;   // columns of one k_front_copy CTA
+
+// to_dense = 1: panel -> dense copy; 0: dense copy -> panel.  CTA
+// (x, y) copies columns [8 y, 8 y + 8) of (front, panel) pair x; smem: the
+// front's row map (m ints).
 __global__ void __launch_bounds__(NT) k_front_copy(const FrontCopy* __restrict__ tasks, const Seg* __restrict__ segs,
                                                    int to_dense) {
     extern __shared__ int rmap_sm[];
     const FrontCopy c = tasks[blockIdx.x];
+    const int c0 = (int)blockIdx.y * kCopyCols;
+    if (c0 >= c.ncol) return;
+    const int c1 = min(c.ncol, c0 + kCopyCols);
     int pos = 0;
     for (int s = 0; s < c.nseg; s++) {
         const Seg g = segs[c.seg_begin + s];
@@ -192,13 +198,13 @@ __global__ void __launch_bounds__(NT) k_front_copy(const FrontCopy* __restrict__
         pos += g.len;
     }
     __syncthreads();
-    const int64_t tot = (int64_t)c.m * c.ncol;
-    for (int64_t o = threadIdx.x; o < tot; o += NT) {
-        const int r = (int)(o % c.m), col = (int)(o / c.m);
-        float* p = c.panel + rmap_sm[r] + (int64_t)col * c.ld;
-        float* d = c.dense + r + (int64_t)col * c.m;
-        if (to_dense) *d = *p;
-        else *p = *d;
+    for (int col = c0; col < c1; col++) {
+        float* p = c.panel + (int64_t)col * c.ld;
+        float* d = c.dense + (int64_t)col * c.m;
+        if (to_dense)
+            for (int r = threadIdx.x; r < c.m; r += NT) d[r] = p[rmap_sm[r]];
+        else
+            for (int r = threadIdx.x; r < c.m; r += NT) p[rmap_sm[r]] = d[r];
     }
 }
 
@@ -1108,9 +1114,9 @@ int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std
         GemmTask* dg = C.upload(g, false);
         TfullTask* dtf = C.upload(tf, false);
         if (C.rc) return C.rc;
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dg, g, true, d_err, st));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st, launch_tc_gemm(dg, g, true, d_err, st));
         C.launched();
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, k_tfull<<<(unsigned)tf.size(), NT, 0, st>>>(dtf));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st, k_tfull<<<(unsigned)tf.size(), NT, 0, st>>>(dtf));
         C.launched();
     }
     size_t a = 0;
@@ -1187,17 +1193,20 @@ int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std
         GemmTask* du = C.upload(gu, false);
         if (C.rc) return C.rc;
         const size_t smem = (size_t)mmax * sizeof(int);
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st,
-                     k_front_copy<<<(unsigned)cp.size(), NT, smem, st>>>(dcp, dsg, 1));
+        int ccmax = 1;
+        for (const FrontCopy& c : cp) ccmax = std::max(ccmax, (c.ncol + kCopyCols - 1) / kCopyCols);
+        const dim3 cgrid((unsigned)cp.size(), (unsigned)ccmax);
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st,
+                     k_front_copy<<<cgrid, NT, smem, st>>>(dcp, dsg, 1));
         C.launched();
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dw, gw, split3, d_err, st));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st, launch_tc_gemm(dw, gw, split3, d_err, st));
         C.launched();
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st, launch_tc_gemm(dw2, gw2, split3, d_err, st));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st, launch_tc_gemm(dw2, gw2, split3, d_err, st));
         C.launched();
-        SPAQR_LAUNCH(KK_FRONT_APPLY, fl, by, st, launch_tc_gemm(du, gu, split3, d_err, st));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, fl, by, st, launch_tc_gemm(du, gu, split3, d_err, st));
         C.launched();
-        SPAQR_LAUNCH(KK_FRONT_APPLY, 0.0, 0.0, st,
-                     k_front_copy<<<(unsigned)cp.size(), NT, smem, st>>>(dcp, dsg, 0));
+        SPAQR_LAUNCH(KK_FRONT_APPLY_TC, 0.0, 0.0, st,
+                     k_front_copy<<<cgrid, NT, smem, st>>>(dcp, dsg, 0));
         C.launched();
         a = b;
     }
@@ -1595,7 +1604,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     double snj = 0;
                     for (int b = sf.rsj_begin; b < (int)srsj.size(); b++) snj += srsj[b].nj;
                     const double m_ = sf.m, n_ = sf.n;
-                    LV.ff_flops.back() += 4.0 * m_ * n_ + n_ * n_;
+                    // applying n reflectors of m rows to one column: 4mn - 2n^2
+                    LV.ff_flops.back() += 4.0 * m_ * n_ - 2.0 * n_ * n_;
                     LV.ff_fixed.back() += 8.0 * (m_ * n_ + n_ * n_);
                     LV.ff_vec.back() += 16.0 * m_;
                     LV.fb_flops += 2.0 * n_ * snj + n_ * n_;
@@ -2243,11 +2253,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     s.HT = hT[p];
                     s.HD = hD[p];
                     const double n_ = (double)sz[p], r_ = (double)newsz[p], f_ = (double)f;
-                    sflops += 4.0 * n_ * f_ + 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_;
+                    sflops += 4.0 * n_ * f_ - 2.0 * f_ * f_ + 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_ - 2.0 * r_ * r_;
                     sbytes += 8 * (int64_t)(n_ * f_ + f_ * r_ + f_ * f_ + n_ * r_);
-                    LV.ssf_flops += 4.0 * n_ * f_;
+                    LV.ssf_flops += 4.0 * n_ * f_ - 2.0 * f_ * f_;
                     LV.ssf_fixed += 8.0 * (n_ * f_ + f_ * f_);
-                    LV.ssb_flops += 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_;
+                    LV.ssb_flops += 2.0 * f_ * r_ + f_ * f_ + 4.0 * n_ * r_ - 2.0 * r_ * r_;
                     LV.ssb_fixed += 8.0 * (f_ * r_ + f_ * f_ + n_ * r_ + r_ * r_);
                 } else if (sparsify && sz[p] > 0) {
                     const int e = sp.find(p, p);
@@ -2258,12 +2268,17 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     s.QV = qV[p];
                     s.QT = qT[p];
                     s.ldqt = std::max(kmax[p], 1);
-                    sflops += 2.0 * (4.0 * sz[p] * sz[p] + 4.0 * sz[p] * newsz[p]);
+                    {
+                        const double n_ = (double)sz[p], r_ = (double)newsz[p];
+                        sflops += 2.0 * n_ * n_ + 2.0 * (4.0 * n_ * r_ - 2.0 * r_ * r_) + n_ * n_;
+                    }
                     sbytes += 8 * (2 * sz[p] * sz[p] + sz[p] * newsz[p]);
                     const double n_ = (double)sz[p], r_ = (double)newsz[p];
-                    LV.ssf_flops += 5.0 * n_ * n_ + 4.0 * n_ * r_ + r_ * r_;
+                    // U_pp^T (n reflectors of n rows), then Q_pp^T (r reflectors)
+                    LV.ssf_flops += 2.0 * n_ * n_ + 4.0 * n_ * r_ - 2.0 * r_ * r_;
                     LV.ssf_fixed += 8.0 * (2.0 * n_ * n_ + n_ * r_ + r_ * r_);
-                    LV.ssb_flops += 4.0 * n_ * r_ + r_ * r_ + n_ * n_;
+                    // Q_pp, then R_pp^{-1}
+                    LV.ssb_flops += 4.0 * n_ * r_ - 2.0 * r_ * r_ + n_ * n_;
                     LV.ssb_fixed += 8.0 * (n_ * n_ + n_ * r_ + r_ * r_);
                 }
                 LV.ssf_vec += 16.0 * sz[p] + 8.0 * newsz[p];

@@ -25,39 +25,43 @@ namespace spaqr {
 
 namespace {
 
-// Element (i, k) of an operand view (0 past the edges).
-__device__ __forceinline__ float op_at(const GemmOperand& o, int rows, int K, int i, int k) {
-    if (i >= rows || k >= K) return 0.0f;
-    if (o.unit_lower) {
-        const int r = o.trans ? k : i, c = o.trans ? i : k;   // row / column of the stored panel
-        if (r < c) return 0.0f;
-        if (r == c) return 1.0f;
-    }
-    return o.p[(int64_t)i * o.rs + (int64_t)k * o.cs];
-}
-
 // Stage one BM x BK (or BN x BK) chunk of an operand at K offset k0 into
 // shared memory (TF32 hi, and lo for the three-pass form).
 template <int BK, bool SPLIT3>
 __device__ __forceinline__ void stage_operand(const GemmOperand& o, int rows, int K, int i0, int k0, float* hi,
                                               float* lo) {
-    constexpr int ELEMS = 128 * BK;
-    const bool kfast = o.cs == 1 || (o.rs != 1 && o.cs < o.rs);   // contiguous along K: a warp reads a row
-#pragma unroll 4
-    for (int o4 = threadIdx.x; o4 < ELEMS; o4 += 128) {
-        int i, k;
-        if (kfast) {
-            i = o4 / BK;
-            k = o4 % BK;
-        } else {
-            i = o4 % 128;
-            k = o4 / 128;
+    // thread t reads element (ib + di u, kb + dk u) at its u-th load: along K
+    // when the operand is contiguous along K (a warp reads a row), else along
+    // the rows (a warp reads a column)
+    const bool kfast = o.cs == 1 || (o.rs != 1 && o.cs < o.rs);
+    const int t = threadIdx.x;
+    const int ib = kfast ? t / BK : t, kb = kfast ? t % BK : 0;
+    const int di = kfast ? 128 / BK : 0, dk = kfast ? 0 : 1;
+    const int64_t step = (int64_t)di * o.rs + (int64_t)dk * o.cs;
+    const float* p0 = o.p + (int64_t)(i0 + ib) * o.rs + (int64_t)(k0 + kb) * o.cs;
+    // every load of the chunk is issued before the first is used (BK values
+    // per thread in flight), then converted and stored
+    float x[BK];
+#pragma unroll
+    for (int u = 0; u < BK; u++) {
+        const int i = i0 + ib + di * u, k = k0 + kb + dk * u;
+        float v = 0.0f;
+        if (i < rows && k < K) {
+            if (o.unit_lower) {
+                const int r = o.trans ? k : i, c = o.trans ? i : k;
+                v = r > c ? p0[step * u] : (r == c ? 1.0f : 0.0f);
+            } else {
+                v = p0[step * u];
+            }
         }
-        const float x = op_at(o, rows, K, i0 + i, k0 + k);
-        const float h = tc::to_tf32(x);
-        const uint32_t off = tc::kmajor_off(i, k, BK) >> 2;
+        x[u] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < BK; u++) {
+        const float h = tc::to_tf32(x[u]);
+        const uint32_t off = tc::kmajor_off(ib + di * u, kb + dk * u, BK) >> 2;
         hi[off] = h;
-        if constexpr (SPLIT3) lo[off] = tc::to_tf32(x - h);
+        if constexpr (SPLIT3) lo[off] = tc::to_tf32(x[u] - h);
     }
 }
 
