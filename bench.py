@@ -48,11 +48,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum),
-# averaged over the kind's launches (one-CTA and cluster forms), from the ncu
-# launch list of the current kernels on this workload
-# (profiles/launches_convdiff2d_256x256_fp64_16rhs.md); a kind whose kernels
-# changed since that capture has no entry.
-TRAFFIC = {"solve_front_fwd": 4.1e6}
+# averaged over the kind's launches (one-CTA and cluster forms), from ncu
+# launch lists of the current kernels on this workload (profiles/:
+# launches_convdiff2d_256x256_fp64_16rhs.md for the application,
+# factor_kernels_dram_convdiff2d_256x256_fp64.md for the factorisation); a
+# kind whose kernels changed since its capture, or whose kernel serves
+# several kinds (k_qr: front and scaling QR), has no entry.
+TRAFFIC = {"solve_front_fwd": 4.1e6, "front_apply": 40.81e6, "cpqr": 92.51e6, "scale_apply": 13.56e6,
+           "sparsify_merge": 18.80e6}
 
 
 def _args():
@@ -116,14 +119,15 @@ def measure_peaks(sq, reps=5):
     return out
 
 
-def kernel_rooflines(kstats, peaks, fp64, bf16_tflops):
+def kernel_rooflines(kstats, peaks, fp64, bf16_tflops, traffic_table=None):
     """One roofline per kernel kind with algorithmic flops: achieved = the
     kind's algorithmic flops (the per-unit counts of the launch accounting)
     / its CUDA-event time over the profiled pass.  FP64 kinds against the
     derived FP64 peak; FP32 kinds against the derived FFMA peak; the
     tensor-core front application against the TF32 peak (measured BF16 x the
     nominal TF32 / BF16 ratio).  The live microbenchmark of the same pipe is
-    given beside each."""
+    given beside each.  traffic_table: DRAM bytes per launch measured by ncu
+    on this same workload and form (kind -> bytes), else no traffic."""
     out = []
     for name, d in sorted(kstats.items(), key=lambda kv: -kv[1]["total_ms"]):
         if not d["launches"] or d["flops"] <= 0 or d["total_ms"] <= 0:
@@ -138,11 +142,14 @@ def kernel_rooflines(kstats, peaks, fp64, bf16_tflops):
             bound, peak, meas = "alu", FP32_PEAK_TFLOPS, peaks.get("ffma")
             note = "FP32 CUDA cores: 152 SMs x 256 flop/clk x 2070 MHz (derived)"
         ach = d["flops"] / (d["total_ms"] * 1e-3) / 1e12
+        alg_b = d["bytes"] / d["launches"]
+        traffic = (traffic_table or {}).get(name)
         out.append({"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "peak_note": note, "peak_microbenchmark": meas,
                     "launches": d["launches"], "total_ms": d["total_ms"],
                     "algorithmic_gflop_per_launch": d["flops"] / d["launches"] / 1e9,
-                    "traffic": TRAFFIC.get(name) if fp64 else None})
+                    "algorithmic_mb_per_launch": alg_b / 1e6, "traffic": traffic,
+                    "traffic_over_algorithmic": traffic / alg_b if traffic and alg_b > 0 else None})
     return out
 
 
@@ -735,7 +742,7 @@ def ours(a):
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kstats.items()
                     if v["launches"]},
         "roofline": roof,
-        "rooflines": kernel_rooflines(kstats, peaks, True, bf16),
+        "rooflines": kernel_rooflines(kstats, peaks, True, bf16, TRAFFIC),
         "peaks_measured_tflops": peaks,
         "clocks": clk,
     }

@@ -1973,6 +1973,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                              k_cpqr_cluster<real, CPQR_CS><<<(unsigned)(cpb.size() * CPQR_CS), NT, smem_cp, st>>>(
                                  d1, dgs, opt->eps));
                 C.launched();
+                by_cp = 0.0;   // M_p's bytes are counted once per level
             }
             if (!cp.empty()) {
                 CPQRTask<real>* d1 = C.upload(cp, false);

@@ -136,3 +136,39 @@ def test_batch_mixing_2d_and_3d(spaqr_lib):
         Xs, _, _ = sq.spaqr_gmres(Fs, *cs, torch.from_numpy(Bh[a:b].copy()).cuda(), tol=1e-12)
         d = np.linalg.norm(X[a:b] - Xs.cpu().numpy()) / np.linalg.norm(Xs.cpu().numpy())
         assert d <= 1e-10, (i, d)
+
+
+def test_batch_at_config_scale_against_oracle(spaqr_lib):
+    """The 64-matrix batch of the batched configuration (sides 32 to 128,
+    a ~ U[0.1, 10], Pe ~ U[1, 100]), factored together in FP64 at eps 1e-2:
+    three sampled matrices (the largest side, a middle one and the smallest)
+    against the oracle on that matrix alone.  Their ranks at every level are
+    among the batch's ranks of that level, and the batch factor applied to a
+    right-hand side that is nonzero on one matrix only equals the oracle's
+    application entry by entry to 1e-10 there and is exactly zero on every
+    other matrix."""
+    import torch
+    from oracle import spaqr as osq
+    probs = batch_problems(64)
+    ob, F, _ = _batch(probs)
+    sides = [p.dims[0] for p in probs]
+    order = np.argsort(sides, kind="stable")
+    picks = [int(order[-1]), int(order[len(order) // 2]), int(order[0])]
+    batch_ranks = [[tuple(x) for x in sq.spaqr_factor_ranks(F, k)[0]] for k in range(ob.L)]
+    for i in picks:
+        p = probs[i]
+        Fo = osq.factor(p.n, p.rowptr, p.colind, p.val, p.dims, 1e-2)
+        for k, R in enumerate(Fo.ranks):
+            pool = list(batch_ranks[k])
+            for e in (v for _, v in sorted(R.items()) if v[0] > 0):
+                assert e in pool, (i, k, e)
+                pool.remove(e)
+        a, b = int(ob.part_ptr[i]), int(ob.part_ptr[i + 1])
+        Bh = np.zeros((ob.n, 2))
+        Bh[a:b] = np.random.default_rng(100 + i).standard_normal((b - a, 2))
+        B = torch.from_numpy(np.ascontiguousarray(Bh.T)).cuda().T
+        X = sq.spaqr_solve(F, B).T.cpu().numpy().T
+        xo = osq.solve(Fo, Bh[a:b])
+        err = np.abs(X[a:b] - xo).max(axis=0) / np.abs(xo).max(axis=0)
+        assert err.max() <= 1e-10, (i, err)
+        assert np.all(X[:a] == 0.0) and np.all(X[b:] == 0.0)
