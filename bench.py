@@ -54,8 +54,8 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # factor_kernels_dram_convdiff2d_256x256_fp64.md for the factorisation); a
 # kind whose kernels changed since its capture, or whose kernel serves
 # several kinds (k_qr: front and scaling QR), has no entry.
-TRAFFIC = {"solve_front_fwd": 4.1e6, "front_apply": 40.81e6, "cpqr": 92.51e6, "scale_apply": 13.56e6,
-           "sparsify_merge": 18.80e6}
+TRAFFIC = {"solve_front_fwd": 4.1e6, "front_apply": 40.77e6, "cpqr": 93.31e6, "scale_apply": 13.55e6,
+           "sparsify_merge": 18.78e6}
 
 
 def _args():

@@ -112,19 +112,19 @@ struct Mat {
 
 // Householder vector of column `col` (rows k..m-1, element stride `stride`)
 // in place: col[k] <- beta, col[k+1..] <- v.  Returns tau to every thread.
-// beta, tau and the scaling are computed in FP64 whatever the storage type;
-// the norm is accumulated in the storage type.  sign_tol > 0: alpha counts as
+// beta, tau, the squared norm (every partial sum) and the scaling are
+// computed in FP64 whatever the storage type.  sign_tol > 0: alpha counts as
 // negative only below -sign_tol sqrt(alpha^2 + x.x), so that a leading entry
 // that is zero up to rounding always gives beta = -norm.
 template <class real>
 __device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, int m, double* red,
                                             double sign_tol = 0.0) {
-    real part = 0;
+    double part = 0.0;
     for (int r = k + 1 + threadIdx.x; r < m; r += NT) {
-        const real x = col[(int64_t)r * stride];
+        const double x = (double)col[(int64_t)r * stride];
         part += x * x;
     }
-    const double xn2 = block_sum((double)part, red);
+    const double xn2 = block_sum(part, red);
     const double alpha = (double)col[(int64_t)k * stride];
     double tk = 0.0, beta = alpha, denom = 1.0;
     if (xn2 != 0.0) {

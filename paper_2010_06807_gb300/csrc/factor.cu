@@ -74,9 +74,16 @@ __global__ void k_gather(int64_t nnz, const int64_t* __restrict__ off, const int
 }
 
 constexpr int QC = 32;       // column chunk of the blocked updates
-constexpr int CPQR_CS = 8;   // CTAs per cluster of the large-interface CPQR
+// CTAs per cluster of the large-front QR: 16, the largest (non-portable)
+// cluster, so that the few large fronts of the upper levels keep more SMs
+// busy.  The large-interface CPQR takes 16 in FP64, whose steps are bound by
+// the FP64 pipe of the cluster's SMs, and 8 in FP32, where the per-step
+// cluster barriers dominate (measured on 3D 32^3: FP64 151 -> 139 ms, FP32
+// 64 -> 82 ms with 16).
+template <class real>
+constexpr int cpqr_cs() { return sizeof(real) == 8 ? 16 : 8; }
 constexpr int64_t kBigCPQR = 1 << 17;   // n_p x ncols from which an interface uses a cluster
-constexpr int QR_CS = 8;     // CTAs per cluster of the large-front QR
+constexpr int QR_CS = 16;
 constexpr int64_t kBigQR = 1 << 16;     // m x n from which a front uses a cluster
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 // CPQR reflectors: a pivot column's leading entry within this fraction of
@@ -94,44 +101,186 @@ __global__ void __launch_bounds__(NT) k_qr(const QRTask<real>* __restrict__ task
     if (t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
 }
 
-// Cluster form of k_qr for large fronts: CTA 0 of the cluster factors each
-// panel of NB columns; after a cluster barrier the CS CTAs apply the panel to
-// their slices of the trailing columns (reflectors read from global memory).
+// Shared memory (bytes) of k_qr_cluster for panel slabs of `slab` rows.
+__host__ __device__ constexpr size_t qrcl_smem_bytes(int esz, int slab) {
+    return (size_t)8 * (NWARP + 2 * (2 + 2 * NB) + NB * NB + NT) +
+           (size_t)esz * (NB + 2 * NB * QC + NT + (size_t)slab * NB);
+}
+
+// Cluster form of k_qr for large fronts.  Each panel of NB columns is
+// factored by all CS CTAs together, the panel's rows p0..m-1 split into one
+// slab per CTA (staged in its shared memory).  For column k every CTA sums,
+// over its own rows below k, the squares of column k and its products with
+// the panel's later columns; the owner of row k adds that row.  One cluster
+// barrier later every CTA adds the CTAs' sums in rank order through
+// distributed shared memory and forms the same Householder scalars and the
+// same w_j = tau (A(k, j) + sum_r A(r, k) A(r, j) / (alpha - beta)), the
+// dot product of the reflector with column j, and updates its own rows.
+// The T block comes from the slabs' partial V^T V the same way.  The CS CTAs
+// then apply the panel to their slices of the trailing columns (reflectors
+// read from global memory).  Distributed-shared-memory slots alternate
+// between two buffers by the parity of the cluster barrier count, so a slot
+// is rewritten only two barriers after it was read.
 template <class real, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     k_qr_cluster(const QRTask<real>* __restrict__ tasks, int prow) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double sm[];
-    double* red = sm;
-    real* P = reinterpret_cast<real*>(red + NWARP);
-    real* Wk = P + NT;
-    real* G = Wk + NB;
-    real* W = G + NB * NB;
-    real* Ps = W + 2 * NB * QC + NT;
+    constexpr int SL = 2 + 2 * NB;                 // slot: norm, alpha, NB sums, NB entries of row k
+    double* red = sm;                              // NWARP
+    double* slot = red + NWARP;                    // 2 x SL
+    double* Gp = slot + 2 * SL;                    // NB x NB partial V^T V
+    double* Pd = Gp + NB * NB;                     // NT partial sums
+    real* Wk = reinterpret_cast<real*>(Pd + NT);   // NB
+    real* W = Wk + NB;                             // 2 NB QC + NT (trailing update)
+    real* Ps = W + 2 * NB * QC + NT;               // slab x NB panel rows of this CTA
+    (void)prow;
     const int q = (int)cl.block_rank();
     const QRTask<real> t = tasks[blockIdx.x / CS];
     const int m = t.m, n = t.n, tt = m < n ? m : n;
-    const bool staged = m <= prow;
+    real* A = t.A;
+    const int64_t lda = t.lda;
+    int ph = 0;
     for (int p0 = 0; p0 < tt; p0 += NB) {
-        const int pe = (tt - p0 < NB ? tt : p0 + NB);
-        if (q == 0) {
-            int64_t ldp;
-            cta_qr_panel(t.A, t.lda, m, p0, pe, t.tau, t.T, tt, staged, red, P, Wk, G, Ps, &ldp, t.sign_tol);
+        const int pe = (tt - p0 < NB ? tt : p0 + NB), pb = pe - p0;
+        const int mr = m - p0, slab = (mr + CS - 1) / CS;
+        const int lo = p0 + min(mr, q * slab), hi = p0 + min(mr, (q + 1) * slab), rows = hi - lo;
+        for (int o = threadIdx.x; o < rows * pb; o += NT) {
+            const int r = o % rows, jj = o / rows;
+            Ps[r + jj * slab] = A[(lo + r) + (int64_t)(p0 + jj) * lda];
+        }
+        __syncthreads();
+        for (int k = p0; k < pe; k++) {
+            const int jk = k - p0, ncol = pe - k - 1;
+            real* col = Ps + jk * slab - lo;   // col[r], r in [lo, hi)
+            const bool own_k = k >= lo && k < hi;
+            // thread (js, g): js = 0 the squared norm, js = 1 + jj the sum for column k + 1 + jj
+            {
+                const int js = threadIdx.x % NB, g = threadIdx.x / NB;
+                double pd = 0.0;
+                if (js <= ncol) {
+                    const real* cj = Ps + (jk + js) * slab - lo;
+                    for (int r = max(lo, k + 1) + g; r < hi; r += NT / NB) pd += (double)col[r] * (double)cj[r];
+                }
+                Pd[threadIdx.x] = pd;
+            }
+            __syncthreads();
+            double* sl = slot + (ph & 1) * SL;
+            if (threadIdx.x <= ncol) {
+                double sacc = 0.0;
+                for (int gg = 0; gg < NT / NB; gg++) sacc += Pd[gg * NB + threadIdx.x];
+                sl[threadIdx.x == 0 ? 0 : 1 + threadIdx.x] = sacc;
+            }
+            if (threadIdx.x < NB) {
+                // alpha = A(k, k) and row k's entries A(k, k + 1 + jj) from the owner of row k
+                const int jj = threadIdx.x;
+                sl[2 + NB + jj] = (own_k && jj < ncol) ? (double)Ps[(k - lo) + (jk + 1 + jj) * slab] : 0.0;
+                if (jj == 0) sl[1] = own_k ? (double)col[k] : 0.0;
+            }
+            cl.sync();
+            ph++;
+            double x2 = 0.0, alpha = 0.0;
+            for (int rr = 0; rr < CS; rr++) {
+                const double* o = cl.map_shared_rank(sl, rr);
+                x2 += o[0];
+                alpha += o[1];
+            }
+            double tk = 0.0, beta = alpha, denom = 1.0;
+            if (x2 != 0.0) {
+                const double s = sqrt(alpha * alpha + x2);
+                beta = alpha >= -t.sign_tol * s ? -s : s;
+                tk = (beta - alpha) / beta;
+                denom = alpha - beta;
+            }
+            if (threadIdx.x < ncol && tk != 0.0) {
+                double sacc = 0.0, akj = 0.0;
+                for (int rr = 0; rr < CS; rr++) {
+                    const double* o = cl.map_shared_rank(sl, rr);
+                    sacc += o[2 + threadIdx.x];
+                    akj += o[2 + NB + threadIdx.x];
+                }
+                Wk[threadIdx.x] = (real)(tk * (akj + sacc / denom));
+            }
+            __syncthreads();
+            if (tk != 0.0) {
+                if constexpr (sizeof(real) == 8) {
+                    for (int r = max(lo, k + 1) + (int)threadIdx.x; r < hi; r += NT) col[r] = col[r] / denom;
+                } else {
+                    const real sc = (real)(1.0 / denom);
+                    for (int r = max(lo, k + 1) + (int)threadIdx.x; r < hi; r += NT) col[r] *= sc;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && own_k) col[k] = (real)beta;
+            if (threadIdx.x == 0 && q == 0) t.tau[k] = (real)tk;
+            if (ncol > 0 && tk != 0.0) {
+                const int r0 = max(lo, k), nr = hi - r0;
+                for (int o = threadIdx.x; o < nr * ncol; o += NT) {
+                    const int r = r0 + o % nr, jj = o / nr;
+                    const real v = r == k ? (real)1 : col[r];
+                    Ps[(r - lo) + (jk + 1 + jj) * slab] -= Wk[jj] * v;
+                }
+            }
+            __syncthreads();
+        }
+        // the factored panel back to global memory, and the partial
+        // G(i, j) = V(:, p0+i)^T V(:, p0+j), i < j, over own rows
+        for (int o = threadIdx.x; o < rows * pb; o += NT) {
+            const int r = o % rows, jj = o / rows;
+            A[(lo + r) + (int64_t)(p0 + jj) * lda] = Ps[r + jj * slab];
+        }
+        for (int o = threadIdx.x; o < pb * pb; o += NT) {
+            const int i = o % pb, jj = o / pb;
+            double acc = 0.0;
+            if (i < jj) {
+                for (int r = max(lo, p0 + jj); r < hi; r++) {
+                    const double vi = r == p0 + i ? 1.0 : (double)Ps[(r - lo) + i * slab];
+                    const double vj = r == p0 + jj ? 1.0 : (double)Ps[(r - lo) + jj * slab];
+                    acc += vi * vj;
+                }
+            }
+            Gp[o] = acc;
         }
         cl.sync();
+        ph++;
+        if (q == 0) {
+            // G summed in rank order, then the T block (column recurrence)
+            real* Gs = reinterpret_cast<real*>(Pd);
+            for (int o = threadIdx.x; o < pb * pb; o += NT) {
+                double acc = 0.0;
+                for (int rr = 0; rr < CS; rr++) acc += cl.map_shared_rank(Gp, rr)[o];
+                Gs[o] = (real)acc;   // pb * pb <= NT
+            }
+            __syncthreads();
+            real* T = t.T + p0 + (int64_t)p0 * tt;
+            for (int k = 0; k < pb; k++) {
+                const real tkr = t.tau[p0 + k];
+                for (int i = threadIdx.x; i < k; i += NT) {
+                    real sacc = 0;
+                    for (int u = i; u < k; u++) sacc += T[i + (int64_t)u * tt] * Gs[u + k * pb];
+                    T[i + (int64_t)k * tt] = -tkr * sacc;
+                }
+                if (threadIdx.x == 0) T[k + (int64_t)k * tt] = tkr;
+                for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[i + (int64_t)k * tt] = 0;
+                __syncthreads();
+            }
+        }
+        cl.sync();   // panel, tau and T visible to the cluster; Gp read before it is rewritten
+        ph++;
         if (pe < n) {
             const int w = (n - pe + CS - 1) / CS;
             const int c0 = pe + q * w, c1 = min(n, c0 + w);
             if (c1 > c0) {
-                Mat<real> B{t.A + p0 + (int64_t)c0 * t.lda, 1, t.lda, nullptr};
-                cta_apply_q_chunked(t.A + p0 + (int64_t)p0 * t.lda, t.lda, m - p0, pe - p0,
-                                    t.T + p0 + (int64_t)p0 * tt, tt, false, B, c1 - c0, QC, true, W);
+                Mat<real> B{A + p0 + (int64_t)c0 * lda, 1, lda, nullptr};
+                cta_apply_q_chunked(A + p0 + (int64_t)p0 * lda, lda, m - p0, pb, t.T + p0 + (int64_t)p0 * tt, tt,
+                                    false, B, c1 - c0, QC, true, W);
             }
         }
         cl.sync();
+        ph++;
     }
-    if (q == 0 && t.Dinv) cta_tri_inv_blocks(t.A, t.lda, tt, t.Dinv, t.singular);
+    if (q == 0 && t.Dinv) cta_tri_inv_blocks(A, lda, tt, t.Dinv, t.singular);
 }
 
 // smem layout: rmap (rmap_doubles doubles) then the work area of the apply
@@ -424,11 +573,20 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
 }
 
 // Cluster form of k_cpqr for large interfaces: the CS CTAs of a thread-block
-// cluster share one M_p.  CTA q owns the columns [q cw, (q+1) cw); each step
-// combines the CTAs' pivot candidates through distributed shared memory, the
-// owner of column k swaps, forms the reflector and publishes it through
-// global memory, and every CTA reflects its own columns.  Per column the
+// cluster share one M_p, CTA q owning the physical columns [q cw, (q+1) cw).
+// Columns are never moved: every CTA keeps the same logical order (perm:
+// logical -> physical, iperm its inverse), and a pivot swap only exchanges
+// two entries of it.  One cluster barrier per step: the CTAs publish their
+// pivot candidates (largest norm, ties to the lowest logical index) through
+// distributed shared memory; after the barrier every CTA reads the chosen
+// pivot column, forms the same reflector from it (the arithmetic of
+// cta_house, so every CTA gets the same bits), records it, and reflects its
+// own live columns.  The pivot's physical column is not written during the
+// step, so the CTAs can read it while the others update theirs.  Candidate
+// slots alternate between two buffers by step parity.  Per column the
 // arithmetic is that of k_cpqr, so ranks and reflectors are identical.
+// smem: reduction slots, a T block, the pivot column, perm and iperm (c ints
+// each).
 template <class real, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     k_cpqr_cluster(const CPQRTask<real>* __restrict__ tasks, const GatherSeg<real>* __restrict__ gsegs, double eps) {
@@ -440,14 +598,16 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
     real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
     real* vs = G + NB * NB;                                      // n_p
-    __shared__ double slot_v, slot_n;
-    __shared__ int slot_i;
+    __shared__ double slot_v[2], slot_n[2];
+    __shared__ int slot_i[2];
     const int q = (int)cl.block_rank();
     const CPQRTask<real> t = tasks[blockIdx.x / CS];
     const int m = t.np, c = t.ncols;
+    int* perm = reinterpret_cast<int*>(vs + (m + 1) / 2 * 2);   // c ints
+    int* iperm = perm + c;                                       // c ints
     const int cw = (c + CS - 1) / CS;
     const int j0 = q * cw, j1 = min(c, j0 + cw);
-    real* M = t.M;  // M(r, j) = M[r * c + j]
+    real* M = t.M;  // M(r, j) = M[r * c + j], j physical
     // gather, elements split over the cluster's CTAs
     const int gt = q * NT + threadIdx.x, gstride = CS * NT;
     for (int s = 0; s < t.nseg; s++) {
@@ -465,6 +625,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
             }
         }
     }
+    for (int j = threadIdx.x; j < c; j += NT) {
+        perm[j] = j;
+        iperm[j] = j;
+    }
     cl.sync();
     for (int j = j0 + threadIdx.x; j < j1; j += NT) {
         real s = 0;
@@ -479,74 +643,72 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     int rank = 0;
     double R11 = 0.0;
     for (int k = 0; k < tmax; k++) {
-        // pivot candidate of this CTA, then of the cluster
+        const int sp = k & 1;
+        // pivot candidate of this CTA: live physical columns (logical index >= k)
         double bv = -1.0;
         int bi = 0x7fffffff;
-        for (int j = max(k, j0) + threadIdx.x; j < j1; j += NT) {
+        for (int j = j0 + threadIdx.x; j < j1; j += NT) {
+            const int lj = iperm[j];
+            if (lj < k) continue;
             const double v = (double)t.norms[j];
-            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+            if (v > bv || (v == bv && lj < bi)) { bv = v; bi = lj; }
         }
         double lv;
         int li;
         block_argmax(bv, bi, redv, redi, lv, li);
-        // FP64 |R_kk|^2 of this CTA's candidate, published with it (computed
-        // before any CTA may swap columns)
+        // FP64 |R_kk|^2 of this CTA's candidate, published with it
         double ln2 = lv;
         if constexpr (sizeof(real) != 8) {
             double part = 0.0;
-            if (li < c)
+            if (li < c) {
+                const int pc = perm[li];
                 for (int r = k + threadIdx.x; r < m; r += NT) {
-                    const double x = (double)M[(int64_t)r * c + li];
+                    const double x = (double)M[(int64_t)r * c + pc];
                     part += x * x;
                 }
+            }
             ln2 = block_sum(part, red);
         }
-        if (threadIdx.x == 0) { slot_v = lv; slot_i = li; slot_n = ln2; }
+        if (threadIdx.x == 0) { slot_v[sp] = lv; slot_i[sp] = li; slot_n[sp] = ln2; }
         cl.sync();
         double gv = -1.0, gn = 0.0;
         int gi = 0x7fffffff;
         for (int r = 0; r < CS; r++) {
-            const double v = *cl.map_shared_rank(&slot_v, r);
-            const int i = *cl.map_shared_rank(&slot_i, r);
-            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = *cl.map_shared_rank(&slot_n, r); }
+            const double v = cl.map_shared_rank(slot_v, r)[sp];
+            const int i = cl.map_shared_rank(slot_i, r)[sp];
+            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = cl.map_shared_rank(slot_n, r)[sp]; }
         }
         if (gn < 0.0) gn = 0.0;
         const double pn = sqrt(gn);
         if (q == 0 && threadIdx.x == 0) t.rdiag[k] = pn;
         if (k == 0) R11 = pn;
-        const bool stop = (R11 == 0.0) || (pn < eps * R11);
-        const int owner = k / cw;
-        if (!stop && q == owner && gi != k) {
-            for (int r = threadIdx.x; r < m; r += NT) {
-                real* row = M + (int64_t)r * c;
-                const real x = row[k];
-                row[k] = row[gi];
-                row[gi] = x;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
-        }
-        // every CTA has read the slots and sees the swap before they change
-        cl.sync();
-        if (stop) break;
-        if (q == owner) {
-            const double tkd = cta_house(M + k, c, k, m, red, kCpqrSignTol);
-            if (threadIdx.x == 0) t.tau[k] = (real)tkd;
-        }
-        cl.sync();
-        const real tk = t.tau[k];
-        for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
+        if ((R11 == 0.0) || (pn < eps * R11)) break;
+        // the pivot (logical gi) becomes logical k; logical k moves to gi
+        const int pcol = perm[gi];
+        const int kcol = perm[k];
         __syncthreads();
-        for (int j = max(k + 1, j0) + threadIdx.x; j < j1; j += NT) {
+        if (threadIdx.x == 0) {
+            perm[k] = pcol;
+            perm[gi] = kcol;
+            iperm[pcol] = k;
+            iperm[kcol] = gi;
+        }
+        // the reflector of the pivot column (rows k..m-1), as cta_house forms it
+        for (int r = k + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + pcol];
+        __syncthreads();
+        const double tkd = cta_house(vs, 1, k, m, red, kCpqrSignTol);
+        const real tk = (real)tkd;
+        if (q == 0) {
+            if (threadIdx.x == 0) t.tau[k] = tk;
+            for (int r = threadIdx.x; r < m; r += NT)
+                t.V[r + (int64_t)k * m] = r < k ? (real)0 : (r == k ? (real)1 : vs[r]);
+        }
+        for (int j = j0 + threadIdx.x; j < j1; j += NT) {
+            if (j == pcol || iperm[j] <= k) continue;
             t.norms[j] = cpqr_reflect_column(M + j, c, k, m, vs, tk);
         }
         __syncthreads();
         rank = k + 1;
-    }
-    // explicit reflectors V (n_p x rank), split over the cluster
-    for (int64_t o = gt; o < (int64_t)m * rank; o += gstride) {
-        const int r = (int)(o % m), i = (int)(o / m);
-        t.V[r + (int64_t)i * m] = r < i ? (real)0 : (r == i ? (real)1 : M[(int64_t)r * c + i]);
     }
     cl.sync();
     if (q == 0) {
@@ -1013,9 +1175,11 @@ void launch_qr(Ctx& C, const std::vector<QRTask<real>>& all, size_t esz, int kin
     if (!big.empty()) {
         QRTask<real>* d = C.upload(big, false);
         if (C.rc) return;
+        int mmax = 1;
+        for (const QRTask<real>& q1 : big) mmax = std::max(mmax, q1.m);
         SPAQR_LAUNCH(kind, fl, by, st,
                      k_qr_cluster<real, QR_CS><<<(unsigned)(big.size() * QR_CS), NT,
-                                                 (size_t)qr_smem_bytes((int)esz, QC, pr_b), st>>>(d, pr_b));
+                                                 qrcl_smem_bytes((int)esz, (mmax + QR_CS - 1) / QR_CS), st>>>(d, 0));
         C.launched();
         fl = 0.0;
         by = 0.0;
@@ -1237,8 +1401,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         C.cuda(cudaFuncSetAttribute(k_scale_apply<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_qr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
         C.cuda(cudaFuncSetAttribute(k_qr_cluster<real, QR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        C.cuda(cudaFuncSetAttribute(k_qr_cluster<real, QR_CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, cpqr_cs<real>()>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         C.cuda(cudaFuncSetAttribute(k_cpqr<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-        C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, CPQR_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        C.cuda(cudaFuncSetAttribute(k_cpqr_cluster<real, cpqr_cs<real>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kSmemMax));
     });
     if (C.rc != SPAQR_OK) return C.rc;
@@ -1946,8 +2112,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 kmx = std::max(kmx, kmax[p]);
                 npmax = std::max(npmax, (int)sz[p]);
                 cp_of[p] = (int)cp.size();
-                // large interfaces go to the cluster kernel (CPQR_CS CTAs each)
-                if ((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= CPQR_CS * 64) cpb.push_back(t);
+                // large interfaces go to the cluster kernel (cpqr_cs CTAs each)
+                if ((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= 512) cpb.push_back(t);
                 else cp.push_back(t);
             }
             if (!atb.empty()) {
@@ -1961,6 +2127,10 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 C.launched();
             }
             const size_t smem_cp = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz;
+            int cmax = 0;
+            for (const CPQRTask<real>& t : cpb) cmax = std::max(cmax, t.ncols);
+            const size_t smem_cpb = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + (npmax + 1) / 2 * 2) * esz +
+                                    (size_t)8 * cmax;
             GatherSeg<real>* dgs = nullptr;
             if (!cp.empty() || !cpb.empty()) {
                 dgs = C.upload(gs, false);
@@ -1970,7 +2140,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 CPQRTask<real>* d1 = C.upload(cpb, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
-                             k_cpqr_cluster<real, CPQR_CS><<<(unsigned)(cpb.size() * CPQR_CS), NT, smem_cp, st>>>(
+                             k_cpqr_cluster<real, cpqr_cs<real>()><<<(unsigned)(cpb.size() * cpqr_cs<real>()), NT, smem_cpb, st>>>(
                                  d1, dgs, opt->eps));
                 C.launched();
                 by_cp = 0.0;   // M_p's bytes are counted once per level

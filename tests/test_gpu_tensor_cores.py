@@ -44,8 +44,10 @@ def test_tensor_core_apply_matches_cuda_core_apply(dev, kind, n, eps):
     times FP32 rounding, so the bar is relative to the CUDA-core FP32 form's
     own distance from FP64.  Three TF32 passes represent each operand to
     2^-22 (x = hi + lo + O(2^-22 x)) against FP32's 2^-24, and the tensor
-    core's FP32 accumulation adds its own rounding: the bar is 30x the
-    CUDA-core form's distance plus 1e-5 (measured: 19x on 3D 20^3)."""
+    core's FP32 accumulation adds its own rounding: the bar is 50x the
+    CUDA-core form's distance plus 1e-5 (measured: 19x on 3D 20^3, 31x on
+    2D 128^2 once the CUDA-core form's Householder norms were accumulated in
+    FP64)."""
     p = config_problem(kind, n=n)
     A = [torch.from_numpy(x).to(dev) for x in (p.rowptr, p.colind, p.val)]
     o = sq.spaqr_order(p.rowptr, p.colind, p.dims)
@@ -67,7 +69,7 @@ def test_tensor_core_apply_matches_cuda_core_apply(dev, kind, n, eps):
         x = sq.spaqr_solve(F, B).cpu().numpy()
         e = (np.linalg.norm(x - x64, axis=0) / np.linalg.norm(x64, axis=0)).max()
         if prec == "fp32":
-            assert e <= 30 * e_cc + 1e-5, (e, e_cc)
+            assert e <= 50 * e_cc + 1e-5, (e, e_cc)
         X, it, rr = sq.spaqr_gmres(F, *A, B, tol=1e-12)
         res = np.linalg.norm(b - p.matvec(X.cpu().numpy()), axis=0) / np.linalg.norm(b, axis=0)
         assert res.max() <= 1e-12 and rr.max() <= 1e-12
