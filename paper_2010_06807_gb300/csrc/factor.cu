@@ -573,20 +573,11 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
 }
 
 // Cluster form of k_cpqr for large interfaces: the CS CTAs of a thread-block
-// cluster share one M_p, CTA q owning the physical columns [q cw, (q+1) cw).
-// Columns are never moved: every CTA keeps the same logical order (perm:
-// logical -> physical, iperm its inverse), and a pivot swap only exchanges
-// two entries of it.  One cluster barrier per step: the CTAs publish their
-// pivot candidates (largest norm, ties to the lowest logical index) through
-// distributed shared memory; after the barrier every CTA reads the chosen
-// pivot column, forms the same reflector from it (the arithmetic of
-// cta_house, so every CTA gets the same bits), records it, and reflects its
-// own live columns.  The pivot's physical column is not written during the
-// step, so the CTAs can read it while the others update theirs.  Candidate
-// slots alternate between two buffers by step parity.  Per column the
+// cluster share one M_p.  CTA q owns the columns [q cw, (q+1) cw); each step
+// combines the CTAs' pivot candidates through distributed shared memory, the
+// owner of column k swaps, forms the reflector and publishes it through
+// global memory, and every CTA reflects its own columns.  Per column the
 // arithmetic is that of k_cpqr, so ranks and reflectors are identical.
-// smem: reduction slots, a T block, the pivot column, perm and iperm (c ints
-// each).
 template <class real, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     k_cpqr_cluster(const CPQRTask<real>* __restrict__ tasks, const GatherSeg<real>* __restrict__ gsegs, double eps) {
@@ -598,16 +589,14 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
     real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
     real* vs = G + NB * NB;                                      // n_p
-    __shared__ double slot_v[2], slot_n[2];
-    __shared__ int slot_i[2];
+    __shared__ double slot_v, slot_n;
+    __shared__ int slot_i;
     const int q = (int)cl.block_rank();
     const CPQRTask<real> t = tasks[blockIdx.x / CS];
     const int m = t.np, c = t.ncols;
-    int* perm = reinterpret_cast<int*>(vs + (m + 1) / 2 * 2);   // c ints
-    int* iperm = perm + c;                                       // c ints
     const int cw = (c + CS - 1) / CS;
     const int j0 = q * cw, j1 = min(c, j0 + cw);
-    real* M = t.M;  // M(r, j) = M[r * c + j], j physical
+    real* M = t.M;  // M(r, j) = M[r * c + j]
     // gather, elements split over the cluster's CTAs
     const int gt = q * NT + threadIdx.x, gstride = CS * NT;
     for (int s = 0; s < t.nseg; s++) {
@@ -625,10 +614,6 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
             }
         }
     }
-    for (int j = threadIdx.x; j < c; j += NT) {
-        perm[j] = j;
-        iperm[j] = j;
-    }
     cl.sync();
     for (int j = j0 + threadIdx.x; j < j1; j += NT) {
         real s = 0;
@@ -643,72 +628,74 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     int rank = 0;
     double R11 = 0.0;
     for (int k = 0; k < tmax; k++) {
-        const int sp = k & 1;
-        // pivot candidate of this CTA: live physical columns (logical index >= k)
+        // pivot candidate of this CTA, then of the cluster
         double bv = -1.0;
         int bi = 0x7fffffff;
-        for (int j = j0 + threadIdx.x; j < j1; j += NT) {
-            const int lj = iperm[j];
-            if (lj < k) continue;
+        for (int j = max(k, j0) + threadIdx.x; j < j1; j += NT) {
             const double v = (double)t.norms[j];
-            if (v > bv || (v == bv && lj < bi)) { bv = v; bi = lj; }
+            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
         }
         double lv;
         int li;
         block_argmax(bv, bi, redv, redi, lv, li);
-        // FP64 |R_kk|^2 of this CTA's candidate, published with it
+        // FP64 |R_kk|^2 of this CTA's candidate, published with it (computed
+        // before any CTA may swap columns)
         double ln2 = lv;
         if constexpr (sizeof(real) != 8) {
             double part = 0.0;
-            if (li < c) {
-                const int pc = perm[li];
+            if (li < c)
                 for (int r = k + threadIdx.x; r < m; r += NT) {
-                    const double x = (double)M[(int64_t)r * c + pc];
+                    const double x = (double)M[(int64_t)r * c + li];
                     part += x * x;
                 }
-            }
             ln2 = block_sum(part, red);
         }
-        if (threadIdx.x == 0) { slot_v[sp] = lv; slot_i[sp] = li; slot_n[sp] = ln2; }
+        if (threadIdx.x == 0) { slot_v = lv; slot_i = li; slot_n = ln2; }
         cl.sync();
         double gv = -1.0, gn = 0.0;
         int gi = 0x7fffffff;
         for (int r = 0; r < CS; r++) {
-            const double v = cl.map_shared_rank(slot_v, r)[sp];
-            const int i = cl.map_shared_rank(slot_i, r)[sp];
-            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = cl.map_shared_rank(slot_n, r)[sp]; }
+            const double v = *cl.map_shared_rank(&slot_v, r);
+            const int i = *cl.map_shared_rank(&slot_i, r);
+            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = *cl.map_shared_rank(&slot_n, r); }
         }
         if (gn < 0.0) gn = 0.0;
         const double pn = sqrt(gn);
         if (q == 0 && threadIdx.x == 0) t.rdiag[k] = pn;
         if (k == 0) R11 = pn;
-        if ((R11 == 0.0) || (pn < eps * R11)) break;
-        // the pivot (logical gi) becomes logical k; logical k moves to gi
-        const int pcol = perm[gi];
-        const int kcol = perm[k];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            perm[k] = pcol;
-            perm[gi] = kcol;
-            iperm[pcol] = k;
-            iperm[kcol] = gi;
+        const bool stop = (R11 == 0.0) || (pn < eps * R11);
+        const int owner = k / cw;
+        if (!stop && q == owner && gi != k) {
+            for (int r = threadIdx.x; r < m; r += NT) {
+                real* row = M + (int64_t)r * c;
+                const real x = row[k];
+                row[k] = row[gi];
+                row[gi] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) t.norms[gi] = t.norms[k];
         }
-        // the reflector of the pivot column (rows k..m-1), as cta_house forms it
-        for (int r = k + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + pcol];
-        __syncthreads();
-        const double tkd = cta_house(vs, 1, k, m, red, kCpqrSignTol);
-        const real tk = (real)tkd;
-        if (q == 0) {
-            if (threadIdx.x == 0) t.tau[k] = tk;
-            for (int r = threadIdx.x; r < m; r += NT)
-                t.V[r + (int64_t)k * m] = r < k ? (real)0 : (r == k ? (real)1 : vs[r]);
+        // every CTA has read the slots and sees the swap before they change
+        cl.sync();
+        if (stop) break;
+        if (q == owner) {
+            const double tkd = cta_house(M + k, c, k, m, red, kCpqrSignTol);
+            if (threadIdx.x == 0) t.tau[k] = (real)tkd;
         }
-        for (int j = j0 + threadIdx.x; j < j1; j += NT) {
-            if (j == pcol || iperm[j] <= k) continue;
+        cl.sync();
+        const real tk = t.tau[k];
+        for (int r = k + 1 + threadIdx.x; r < m; r += NT) vs[r] = M[(int64_t)r * c + k];
+        __syncthreads();
+        for (int j = max(k + 1, j0) + threadIdx.x; j < j1; j += NT) {
             t.norms[j] = cpqr_reflect_column(M + j, c, k, m, vs, tk);
         }
         __syncthreads();
         rank = k + 1;
+    }
+    // explicit reflectors V (n_p x rank), split over the cluster
+    for (int64_t o = gt; o < (int64_t)m * rank; o += gstride) {
+        const int r = (int)(o % m), i = (int)(o / m);
+        t.V[r + (int64_t)i * m] = r < i ? (real)0 : (r == i ? (real)1 : M[(int64_t)r * c + i]);
     }
     cl.sync();
     if (q == 0) {
@@ -2127,10 +2114,6 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 C.launched();
             }
             const size_t smem_cp = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz;
-            int cmax = 0;
-            for (const CPQRTask<real>& t : cpb) cmax = std::max(cmax, t.ncols);
-            const size_t smem_cpb = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + (npmax + 1) / 2 * 2) * esz +
-                                    (size_t)8 * cmax;
             GatherSeg<real>* dgs = nullptr;
             if (!cp.empty() || !cpb.empty()) {
                 dgs = C.upload(gs, false);
@@ -2140,7 +2123,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 CPQRTask<real>* d1 = C.upload(cpb, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
-                             k_cpqr_cluster<real, cpqr_cs<real>()><<<(unsigned)(cpb.size() * cpqr_cs<real>()), NT, smem_cpb, st>>>(
+                             k_cpqr_cluster<real, cpqr_cs<real>()><<<(unsigned)(cpb.size() * cpqr_cs<real>()), NT, smem_cp, st>>>(
                                  d1, dgs, opt->eps));
                 C.launched();
                 by_cp = 0.0;   // M_p's bytes are counted once per level
