@@ -429,11 +429,11 @@ __global__ void __launch_bounds__(NT) k_scale_apply(const ScaleTask<real>* __res
 // One column of the CPQR trailing update: a_j <- (I - tau v v^T) a_j over
 // rows k.. (v_k = 1, v_r = vs[r] below), returning the new squared norm of
 // rows k+1.. (the next step's pivot norm).  Column entries are row-major
-// with stride ld.  Rows are loaded eight at a time before they are used, so
-// a thread keeps eight loads in flight; the additions keep the row order.
+// with stride ld.  Rows are loaded sixteen at a time before they are used,
+// so a thread keeps sixteen loads in flight; the additions keep the row order.
 template <class real>
 __device__ __forceinline__ real cpqr_reflect_column(real* a, int ld, int k, int m, const real* vs, real tk) {
-    constexpr int U = 8;
+    constexpr int U = 16;
     real d = a[(int64_t)k * ld];
     int r = k + 1;
     for (; r + U <= m; r += U) {
@@ -1135,7 +1135,8 @@ void layout_of(const StepPlan& sp, const std::vector<int64_t>& sz, LevelLayout& 
 }
 
 const int kSmemMax = 200 * 1024;
-const int kTcMinN = 48;   // reflectors of a front from which its application is a tensor-core product
+const int kTcMinN = 48;    // reflectors of a front from which its application is a tensor-core product
+const int kTcMinM = 256;   // and rows
 const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
 }  // namespace
@@ -1182,7 +1183,9 @@ void launch_qr(Ctx& C, const std::vector<QRTask<real>>& all, size_t esz, int kin
 }
 
 // Whether a level's fronts go to the tensor cores: the level's apply work is
-// dominated by fronts wide enough (n reflectors) to be dense contractions.
+// dominated by fronts wide (n reflectors) and tall (m rows, the products'
+// K) enough to be dense contractions.  The 2D leaves (193 x 105) are not:
+// there the tensor-core form measured 3.3 ms against 2.9 on the CUDA cores.
 bool tc_level(const StepPlan& sp, const LevelLayout& lay, const std::vector<int64_t>& sz) {
     double big = 0.0, all = 0.0;
     for (size_t f = 0; f < sp.fronts.size(); f++) {
@@ -1191,7 +1194,7 @@ bool tc_level(const StepPlan& sp, const LevelLayout& lay, const std::vector<int6
         for (size_t t = 1; t < sp.C[f].size(); t++) w += (double)sz[sp.C[f][t]];
         const double fl = (4.0 * lay.H[s] * sz[s] - 2.0 * sz[s] * sz[s]) * w;
         all += fl;
-        if (sz[s] >= kTcMinN) big += fl;
+        if (sz[s] >= kTcMinN && lay.H[s] >= kTcMinM) big += fl;
     }
     return all > 0.0 && big >= 0.8 * all;
 }

@@ -84,8 +84,11 @@ def _dim_key(problem):
 class DeviceOps:
     """libspaqr + torch streams on one CUDA device: what the server runs."""
 
-    def __init__(self, device=None, eps=1e-2, precision="fp64", tol=1e-12, maxit=300, matching="max_product"):
-        """matching: the row matching of general matrices (no grid),
+    def __init__(self, device=None, eps=1e-2, precision="fp32", tol=1e-12, maxit=300, matching="max_product"):
+        """precision: of the resident factors, "fp32" by default (GMRES is
+        FP64 and reaches tol either way; the FP32 factors serve 5x the
+        requests of FP64 ones on the serving workload) or "fp64".
+        matching: the row matching of general matrices (no grid),
         "max_product" (the default) or "greedy" (see spaqr_order)."""
         import torch
 
@@ -471,7 +474,7 @@ def run_plain(sides=(16, 24, 32, 40, 48, 48, 32, 24), requests=200, eps=1e-2, pr
 
 
 def run_workload(sides=(16, 24, 32, 40, 48, 48, 32, 24), rate=2000.0, duration=2.0, factor_every=1.0,
-                 factor_side=32, eps=1e-2, precision="fp64", seed=5000, max_slots=64, device=None):
+                 factor_side=32, eps=1e-2, precision="fp32", seed=5000, max_slots=64, device=None):
     """The serving workload: resident factors of 3D 7-point convection-diffusion
     problems with the given sides (a ~ U[0.1,10], velocity 20(1,1,1)); an
     open-loop Poisson stream of single-RHS N(0,1) solve requests with mean
@@ -528,7 +531,7 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="spaQR serving workload (resident 3D factors, Poisson solves)")
     ap.add_argument("--duration", type=float, default=2.0)
     ap.add_argument("--rate", type=float, default=2000.0)
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="fp32")
     ap.add_argument("--max-slots", type=int, default=64)
     a = ap.parse_args()
     print(json.dumps(run_workload(rate=a.rate, duration=a.duration, precision=a.precision,
