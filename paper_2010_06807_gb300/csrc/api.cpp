@@ -214,7 +214,7 @@ const char* kKindNames[KK_COUNT] = {
     "colscale", "gather", "front_qr", "front_apply", "scale_qr", "scale_apply", "cpqr",
     "sparsify_merge", "solve_perm", "solve_front_fwd", "solve_ss_fwd", "solve_ss_bwd",
     "solve_front_bwd", "spmv", "gmres_orth", "gmres_small", "solve_rsj", "sigma_min",
-    "unscaled_sparsify", "sigma_qr", "front_apply_tc"};
+    "unscaled_sparsify", "sigma_qr", "front_apply_tc", "interface_tc"};
 struct Rec { int kind; cudaEvent_t a, b; };
 std::mutex g_mu;
 bool g_prof = false;

@@ -1367,6 +1367,74 @@ int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std
     return SPAQR_OK;
 }
 
+// Full compact-WY factors T (Q = I - V T V^T) of a set of reflector blocks
+// on the tensor cores: G = V^T V (three TF32 passes), then k_tfull.  vt: V^T
+// as a product operand (r x n), tau: r scalars, T: r x r output, scratch:
+// r x r (G) + r x NB (k_tfull).
+struct WySpec {
+    GemmOperand vt;
+    int n, r;
+    const float* tau;
+    float* T;
+    float* scratch;
+};
+
+int tc_full_t(Ctx& C, const std::vector<WySpec>& ws, int kind, int* d_err) {
+    if (ws.empty()) return SPAQR_OK;
+    cudaStream_t st = C.st;
+    std::vector<GemmTask> g;
+    std::vector<TfullTask> tf;
+    for (const WySpec& w : ws) {
+        GemmTask t{};
+        t.a = w.vt;
+        t.bt = w.vt;
+        t.c = w.scratch;
+        t.c_rs = 1;
+        t.c_cs = w.r;
+        t.M = w.r;
+        t.N = w.r;
+        t.K = w.n;
+        t.alpha = 1.0f;
+        t.beta = 0.0f;
+        g.push_back(t);
+        tf.push_back(TfullTask{w.scratch, w.tau, w.T, w.scratch + (int64_t)w.r * w.r, w.r});
+    }
+    gemm_tiles(g);
+    GemmTask* dg = C.upload(g, false);
+    TfullTask* dtf = C.upload(tf, false);
+    if (C.rc) return C.rc;
+    SPAQR_LAUNCH(kind, 0.0, 0.0, st, launch_tc_gemm(dg, g, true, d_err, st));
+    C.launched();
+    SPAQR_LAUNCH(kind, 0.0, 0.0, st, k_tfull<<<(unsigned)tf.size(), NT, 0, st>>>(dtf));
+    C.launched();
+    return SPAQR_OK;
+}
+
+// One batch of products on the tensor cores (tiles filled in here).
+int tc_batch(Ctx& C, std::vector<GemmTask>& g, bool split3, int kind, double fl, double by, int* d_err) {
+    if (g.empty()) return SPAQR_OK;
+    gemm_tiles(g);
+    GemmTask* d = C.upload(g, false);
+    if (C.rc) return C.rc;
+    cudaStream_t st = C.st;
+    SPAQR_LAUNCH(kind, fl, by, st, launch_tc_gemm(d, g, split3, d_err, st));
+    C.launched();
+    return SPAQR_OK;
+}
+
+// Whether the interfaces of a level are large enough for their scaling and
+// sparsification products to go to the tensor cores: interfaces of at least
+// kTcMinN unknowns carry 80% of the level's n_p^3.
+bool tc_iface_level(const std::vector<int>& rest, const std::vector<int64_t>& sz) {
+    double big = 0.0, all = 0.0;
+    for (int p : rest) {
+        const double w = (double)sz[p] * sz[p] * sz[p];
+        all += w;
+        if (sz[p] >= kTcMinN) big += w;
+    }
+    return all > 0.0 && big >= 0.8 * all;
+}
+
 template <class real>
 int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spaqr_factor_s* F) {
     Ctx C;
@@ -1840,6 +1908,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         const bool sparsify = (k + 1 > opt->skip) && !rest.empty();
         std::vector<int64_t> newsz(ncl, 0);
         std::vector<real*> uT(ncl, nullptr), uD(ncl, nullptr), qV(ncl, nullptr), qT(ncl, nullptr);
+        std::vector<real*> uTau(ncl, nullptr), qTau(ncl, nullptr);   // scaling / CPQR Householder scalars
         std::vector<real*> hR(ncl, nullptr), hT(ncl, nullptr), hD(ncl, nullptr);   // unscaled form
         std::vector<int> hF(ncl, 0);
         std::vector<int> kmax(ncl, 0);
@@ -1858,6 +1927,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 int64_t a = 0;
                 for (int p : rest) {
                     real* tau = uaux + a;
+                    uTau[p] = tau;
                     a += sz[p];
                     uT[p] = uaux + a;
                     a += sz[p] * sz[p];
@@ -1874,6 +1944,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
                 // scaling of the off-diagonal blocks
                 std::vector<ScaleTask<real>> sc;
+                std::vector<int> sc_row;   // row interface of every task
                 size_t smem_sc = 16;
                 for (int j : rest) {
                     if (sz[j] == 0) continue;
@@ -1896,6 +1967,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         t.q = QC;
                         smem_sc = (size_t)(2 * NB * QC + NT) * esz;
                         sc.push_back(t);
+                        sc_row.push_back(i);
                         const double fs = 2.0 * sz[i] * sz[i] * sz[j] + 1.0 * sz[j] * sz[j] * sz[i];
                         flops += fs;
                         fl_sc += fs;
@@ -1921,10 +1993,95 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     ScalePiece* dl = C.upload(pl, false);
                     ScalePiece* dr = C.upload(pr, false);
                     if (C.rc) return C.rc;
+                    bool tc_left = false;
+                    if constexpr (sizeof(real) == 4) {
+                        if (tcmode && tc_iface_level(rest, sz)) {
+                            // rows i <- U_i^T (rows i) on the tensor cores:
+                            // W = V_i^T A_ij, W <- T_i^T W, A_ij <- A_ij - V_i W,
+                            // T_i the full compact-WY factor of U_i
+                            tc_left = true;
+                            std::vector<int64_t> toff(ncl, -1);
+                            int64_t tot = 0;
+                            std::vector<WySpec> ws;
+                            // every row interface once
+                            std::vector<char> seen(ncl, 0);
+                            std::vector<int> rows_i;
+                            for (int j : rest) {
+                                if (sz[j] == 0) continue;
+                                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                                    const int i = sp.rowidx[e];
+                                    if (i == j || sp.is_front[i] || sz[i] == 0 || seen[i]) continue;
+                                    seen[i] = 1;
+                                    rows_i.push_back(i);
+                                }
+                            }
+                            for (int i : rows_i) {
+                                toff[i] = tot;
+                                tot += sz[i] * sz[i] * 2 + sz[i] * NB;
+                            }
+                            int64_t wtot = 0;
+                            for (const ScaleTask<real>& t : sc) wtot += 2 * (int64_t)t.mi * t.nj;
+                            float* S = C.alloc<float>(tot + wtot, false);
+                            if (C.rc) return C.rc;
+                            for (int i : rows_i) {
+                                const int ei = sp.find(i, i);
+                                ws.push_back(WySpec{GemmOperand{blk(ei, i), lay.H[i], 1, 1, 1}, (int)sz[i], (int)sz[i],
+                                                    uTau[i], S + toff[i], S + toff[i] + sz[i] * sz[i]});
+                            }
+                            int rc = tc_full_t(C, ws, KK_IFACE_TC, d_flags + 3);
+                            if (rc != SPAQR_OK) return rc;
+                            std::vector<GemmTask> g1, g2, g3;
+                            int64_t wo = tot;
+                            double fl_l = 0.0, by_l = 0.0;
+                            for (size_t ti = 0; ti < sc.size(); ti++) {
+                                const ScaleTask<real>& t = sc[ti];
+                                const int i = sc_row[ti];
+                                float* W = S + wo;
+                                float* W2 = W + (int64_t)t.mi * t.nj;
+                                wo += 2 * (int64_t)t.mi * t.nj;
+                                GemmTask a{};
+                                a.a = GemmOperand{t.Vi, t.ldvi, 1, 1, 1};
+                                a.bt = GemmOperand{t.A, t.lda, 1, 0, 0};
+                                a.c = W;
+                                a.c_rs = 1;
+                                a.c_cs = t.mi;
+                                a.M = t.mi;
+                                a.N = t.nj;
+                                a.K = t.mi;
+                                a.alpha = 1.0f;
+                                a.beta = 0.0f;
+                                g1.push_back(a);
+                                a.a = GemmOperand{S + toff[i], t.mi, 1, 0, 0};
+                                a.bt = GemmOperand{W, t.mi, 1, 0, 0};
+                                a.c = W2;
+                                g2.push_back(a);
+                                a.a = GemmOperand{t.Vi, 1, t.ldvi, 1, 0};
+                                a.bt = GemmOperand{W2, t.mi, 1, 0, 0};
+                                a.c = t.A;
+                                a.c_rs = 1;
+                                a.c_cs = t.lda;
+                                a.alpha = -1.0f;
+                                a.beta = 1.0f;
+                                g3.push_back(a);
+                                fl_l += 2.0 * t.mi * t.mi * t.nj;
+                                by_l += 16.0 * t.mi * t.nj + 8.0 * t.mi * t.mi;
+                            }
+                            rc = tc_batch(C, g1, tcmode == 1, KK_IFACE_TC, 0.0, 0.0, d_flags + 3);
+                            if (rc == SPAQR_OK) rc = tc_batch(C, g2, tcmode == 1, KK_IFACE_TC, 0.0, 0.0, d_flags + 3);
+                            if (rc == SPAQR_OK) rc = tc_batch(C, g3, tcmode == 1, KK_IFACE_TC, fl_l, by_l, d_flags + 3);
+                            if (rc != SPAQR_OK) return rc;
+                            fl_sc -= fl_l;
+                            by_sc -= by_l;
+                        }
+                    }
+                    if (!tc_left) {
+                        SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
+                                     k_scale_apply<real><<<(unsigned)pl.size(), NT, smem_sc, st>>>(d, dl, 0));
+                        C.launched();
+                        fl_sc = 0.0;
+                        by_sc = 0.0;
+                    }
                     SPAQR_LAUNCH(KK_SCALE_APPLY, fl_sc, by_sc, st,
-                                 k_scale_apply<real><<<(unsigned)pl.size(), NT, smem_sc, st>>>(d, dl, 0));
-                    C.launched();
-                    SPAQR_LAUNCH(KK_SCALE_APPLY, 0.0, 0.0, st,
                                  k_scale_apply<real><<<(unsigned)pr.size(), NT, smem_sc, st>>>(d, dr, 1));
                     C.launched();
                 }
@@ -2093,6 +2250,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 t.rank = Rk + p;
                 qV[p] = t.V;
                 qT[p] = t.T;
+                qTau[p] = t.tau;
                 rdg_off[p] = ro;
                 mo += sz[p] * ncols[p];
                 no += ncols[p];
@@ -2358,7 +2516,107 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     sk.push_back(t);
                 }
             }
-            if (!sk.empty()) {
+            bool tc_sp = false;
+            if constexpr (sizeof(real) == 4) {
+                if (!sk.empty() && sparsify && tcmode && opt->scaling != 0 && tc_iface_level(rest, sz)) {
+                    // coarse blocks on the tensor cores: X = (Q_i^T A_ij)[0:r_i, :]
+                    // as A - V_i T_i^T (V_i^T A) on the kept rows (in place in the
+                    // level's arena), then X Q_j on the kept columns,
+                    // X - (X V_j) T_j V_j[0:r_j, :]^T, and a copy into the merged
+                    // block; T_i, T_j the full compact-WY factors of the CPQRs
+                    tc_sp = true;
+                    std::vector<int64_t> toff(ncl, -1);
+                    int64_t tot = 0;
+                    for (int q : rest)
+                        if (sz[q] > 0 && newsz[q] > 0) {
+                            toff[q] = tot;
+                            tot += newsz[q] * newsz[q] * 2 + newsz[q] * NB;
+                        }
+                    int64_t wtot = 0;
+                    for (const SparsifyTask<real>& t : sk)
+                        if (t.mode == 0) wtot += 2 * (int64_t)t.ri * t.nj + 2 * (int64_t)t.ri * t.rj;
+                    float* S = C.alloc<float>(tot + wtot, false);
+                    if (C.rc) return C.rc;
+                    std::vector<WySpec> ws;
+                    std::vector<const float*> tq(ncl, nullptr);
+                    for (int q : rest)
+                        if (toff[q] >= 0) {
+                            ws.push_back(WySpec{GemmOperand{qV[q], sz[q], 1, 0, 0}, (int)sz[q], (int)newsz[q], qTau[q],
+                                                S + toff[q], S + toff[q] + newsz[q] * newsz[q]});
+                            tq[q] = S + toff[q];
+                        }
+                    int rc = tc_full_t(C, ws, KK_IFACE_TC, d_flags + 3);
+                    if (rc != SPAQR_OK) return rc;
+                    std::vector<GemmTask> g[6];
+                    std::vector<SparsifyTask<real>> rest_tasks;
+                    int64_t wo = tot;
+                    double fl_t = 0.0;
+                    for (const SparsifyTask<real>& t : sk) {
+                        if (t.mode != 0) {
+                            rest_tasks.push_back(t);
+                            continue;
+                        }
+                        // the interfaces of this block: Q_i from t.Vi, Q_j from t.Vj
+                        int ii = -1, jj = -1;
+                        for (int q : rest) {
+                            if (qV[q] == t.Vi) ii = q;
+                            if (qV[q] == t.Vj) jj = q;
+                        }
+                        if (ii < 0 || jj < 0 || !tq[ii] || !tq[jj]) {
+                            set_error("sparsification task without its interfaces");
+                            return SPAQR_ERR_INVALID_ARG;
+                        }
+                        const int mi = t.mi, nj = t.nj, ri = t.ri, rj = t.rj;
+                        float* W = S + wo;
+                        float* W2 = W + (int64_t)ri * nj;
+                        float* W3 = W2 + (int64_t)ri * nj;
+                        float* W4 = W3 + (int64_t)ri * rj;
+                        wo += 2 * (int64_t)ri * nj + 2 * (int64_t)ri * rj;
+                        float* Ab = const_cast<float*>(t.A);
+                        auto task = [](GemmOperand a, GemmOperand bt, float* c, int64_t crs, int64_t ccs, int M, int N,
+                                       int K, float alpha, float beta) {
+                            GemmTask x{};
+                            x.a = a;
+                            x.bt = bt;
+                            x.c = c;
+                            x.c_rs = crs;
+                            x.c_cs = ccs;
+                            x.M = M;
+                            x.N = N;
+                            x.K = K;
+                            x.alpha = alpha;
+                            x.beta = beta;
+                            return x;
+                        };
+                        g[0].push_back(task({t.Vi, mi, 1, 0, 0}, {t.A, t.lda, 1, 0, 0}, W, 1, ri, ri, nj, mi, 1.f, 0.f));
+                        g[1].push_back(task({tq[ii], ri, 1, 0, 0}, {W, ri, 1, 0, 0}, W2, 1, ri, ri, nj, ri, 1.f, 0.f));
+                        g[2].push_back(task({t.Vi, 1, mi, 0, 0}, {W2, ri, 1, 0, 0}, Ab, 1, t.lda, ri, nj, ri, -1.f, 1.f));
+                        g[3].push_back(task({t.A, 1, t.lda, 0, 0}, {t.Vj, nj, 1, 0, 0}, W3, 1, ri, ri, rj, nj, 1.f, 0.f));
+                        g[4].push_back(task({W3, 1, ri, 0, 0}, {tq[jj], rj, 1, 0, 0}, W4, 1, ri, ri, rj, rj, 1.f, 0.f));
+                        g[5].push_back(task({W4, 1, ri, 0, 0}, {t.Vj, 1, nj, 0, 0}, Ab, 1, t.lda, ri, rj, rj, -1.f, 1.f));
+                        SparsifyTask<real> cp = t;
+                        cp.mode = 2;
+                        cp.mi = ri;
+                        cp.nj = rj;
+                        rest_tasks.push_back(cp);
+                        fl_t += 4.0 * t.li * mi * nj + 4.0 * rj * nj * ri;
+                    }
+                    for (int b = 0; b < 6 && rc == SPAQR_OK; b++)
+                        rc = tc_batch(C, g[b], tcmode == 1, KK_IFACE_TC, b == 5 ? fl_t : 0.0, 0.0, d_flags + 3);
+                    if (rc != SPAQR_OK) return rc;
+                    if (!rest_tasks.empty()) {
+                        std::vector<ScalePiece> pc;
+                        for (int t = 0; t < (int)rest_tasks.size(); t++) pc.push_back({t, 0, 0});
+                        SparsifyTask<real>* d = C.upload(rest_tasks, false);
+                        ScalePiece* dp = C.upload(pc, false);
+                        if (C.rc) return C.rc;
+                        SPAQR_LAUNCH(KK_SPARSIFY, fl_sp - fl_t, by_sp, st,
+                                     k_sparsify<real><<<(unsigned)pc.size(), NT, 16, st>>>(d, dp, 0));
+                        C.launched();
+                    }
+                }
+            }
+            if (!sk.empty() && !tc_sp) {
                 real* sbuf = C.alloc<real>(scr, false);
                 if (C.rc) return C.rc;
                 for (SparsifyTask<real>& t : sk)

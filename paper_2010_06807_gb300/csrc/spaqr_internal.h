@@ -91,7 +91,7 @@ enum KernelKind {
     KK_COLSCALE = 0, KK_GATHER, KK_FRONT_QR, KK_FRONT_APPLY, KK_SCALE_QR, KK_SCALE_APPLY, KK_CPQR,
     KK_SPARSIFY, KK_SOLVE_PERM, KK_SOLVE_FRONT_FWD, KK_SOLVE_SS_FWD, KK_SOLVE_SS_BWD, KK_SOLVE_FRONT_BWD,
     KK_SPMV, KK_GMRES_ORTH, KK_GMRES_SMALL, KK_SOLVE_RSJ, KK_SIGMA, KK_UNSCALED, KK_SIGMA_QR, KK_FRONT_APPLY_TC,
-    KK_COUNT
+    KK_IFACE_TC, KK_COUNT
 };
 // Call immediately before a launch; returns a record id (or -1).
 int prof_begin(void* stream, int kind, double flops, double bytes);

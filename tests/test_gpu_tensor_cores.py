@@ -60,8 +60,12 @@ def test_tensor_core_apply_matches_cuda_core_apply(dev, kind, n, eps):
     e_cc = (np.linalg.norm(xcc - x64, axis=0) / np.linalg.norm(x64, axis=0)).max()
     _, it64, _ = sq.spaqr_gmres(F64, *A, B, tol=1e-12)
     for prec in ("fp32", "tf32"):
+        sq.spaqr_stats_reset()
         F = _factor(o, A, eps, prec, True)
         assert sq.spaqr_factor_info(F)["tc_levels"] > 0
+        # the scaling and sparsification products of the large interfaces
+        # ran on the tensor cores too
+        assert sq.spaqr_stats()[1]["interface_tc"]["launches"] > 0
         # rank decisions are FP64 on FP32 data: rounding may move a pivot
         # that sits at the threshold
         assert abs(_rank_sum(F) - _rank_sum(Fcc)) <= 0.01 * _rank_sum(Fcc)
