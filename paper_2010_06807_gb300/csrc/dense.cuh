@@ -59,25 +59,37 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the CTA, result returned to every thread.  `red` holds NWARP
-// doubles of shared memory.  Fixed reduction order (deterministic).
+// Doubles of shared memory that block_sum and cta_house work in.
+constexpr int RED = NT + 8;
+
+// Sum over the CTA, result returned to every thread.  `red` holds RED doubles
+// of shared memory.  Fixed reduction order (deterministic): the NT partials go
+// to shared memory and warp 0 alone adds them (eight per lane, then across the
+// warp).  On GB300 an FP64 instruction occupies the SM's FP64 pipe for the
+// same time whatever its active lanes, so an FP64 reduction run by one warp
+// instead of all of them costs a fraction of the pipe time and less latency.
 __device__ __forceinline__ double block_sum(double v, double* red) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    red[threadIdx.x] = v;
     __syncthreads();
-    if (l == 0) red[w] = v;
+    if (threadIdx.x < 32) {
+        const double* p = red + threadIdx.x;
+        double s = ((p[0] + p[32]) + (p[64] + p[96])) + ((p[128] + p[160]) + (p[192] + p[224]));
+        s = warp_sum(s);
+        if (threadIdx.x == 0) red[NT] = s;
+    }
     __syncthreads();
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < NWARP; i++) s += red[i];
-    return s;
+    return red[NT];
 }
 
-// Largest value over the CTA, ties to the smallest index; every thread gets it.
-// Values are non-negative, so their IEEE bit patterns order like the values and
-// the comparison runs on the integer pipe.
-__device__ __forceinline__ void block_argmax(double v, int idx, long long* redv, int* redi, double& bv, int& bi) {
-    long long key = __double_as_longlong(v);
+// Order key of a non-negative value: its IEEE bit pattern, which orders like
+// the value, so that comparisons run on the integer pipe (an FP64 compare
+// occupies the slow FP64 pipe on GB300).
+__device__ __forceinline__ long long nonneg_key(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ long long nonneg_key(float v) { return (long long)__float_as_int(v); }
+
+// Largest key over the CTA, ties to the smallest index; every thread gets it.
+__device__ __forceinline__ void block_argmax_key(long long key, int idx, long long* redv, int* redi, long long& bk,
+                                                 int& bi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
@@ -88,12 +100,11 @@ __device__ __forceinline__ void block_argmax(double v, int idx, long long* redv,
     __syncthreads();
     if (l == 0) { redv[w] = key; redi[w] = idx; }
     __syncthreads();
-    long long bk = redv[0];
+    bk = redv[0];
     bi = redi[0];
     for (int i = 1; i < NWARP; i++) {
         if (redv[i] > bk || (redv[i] == bk && redi[i] < bi)) { bk = redv[i]; bi = redi[i]; }
     }
-    bv = __longlong_as_double(bk);
 }
 
 // Strided view of a matrix: element (r, c) is base[row(r) * rs + c * cs] with
@@ -112,47 +123,115 @@ struct Mat {
 
 // Householder vector of column `col` (rows k..m-1, element stride `stride`)
 // in place: col[k] <- beta, col[k+1..] <- v.  Returns tau to every thread.
-// beta, tau, the squared norm (every partial sum) and the scaling are
-// computed in FP64 whatever the storage type.  sign_tol > 0: alpha counts as
-// negative only below -sign_tol sqrt(alpha^2 + x.x), so that a leading entry
-// that is zero up to rounding always gives beta = -norm.
+// The squared norm (every partial sum), beta, tau and alpha - beta are FP64
+// whatever the storage type; v = x / (alpha - beta) is divided in FP64 in the
+// FP64 form and by alpha - beta rounded to FP32 in the FP32 form.
+// sign_tol > 0: alpha counts as negative only below
+// -sign_tol sqrt(alpha^2 + x.x), so that a leading entry that is zero up to
+// rounding always gives beta = -norm.  `red`: RED doubles of shared memory.
 template <class real>
 __device__ __forceinline__ double cta_house(real* col, int64_t stride, int k, int m, double* red,
                                             double sign_tol = 0.0) {
+    static_assert(NT == 256, "the reduction below adds eight partials per lane");
     double part = 0.0;
     for (int r = k + 1 + threadIdx.x; r < m; r += NT) {
         const double x = (double)col[(int64_t)r * stride];
         part += x * x;
     }
-    const double xn2 = block_sum(part, red);
-    const double alpha = (double)col[(int64_t)k * stride];
-    double tk = 0.0, beta = alpha, denom = 1.0;
-    if (xn2 != 0.0) {
-        const double s = sqrt(alpha * alpha + xn2);
-        beta = alpha >= -sign_tol * s ? -s : s;
-        tk = (beta - alpha) / beta;
-        denom = alpha - beta;
-    }
+    // squared norm by warp 0; the scalars by its lane 0 (FP64 work of one
+    // warp, not of every warp), shared through red[NT..]
+    red[threadIdx.x] = part;
     __syncthreads();
-    if (threadIdx.x == 0) col[(int64_t)k * stride] = (real)beta;
-    if (tk != 0.0) {
-        if constexpr (sizeof(real) == 8) {
-            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] = col[(int64_t)r * stride] / denom;
-        } else {
-            const real sc = (real)(1.0 / denom);
-            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] *= sc;
+    if (threadIdx.x < 32) {
+        const double* p = red + threadIdx.x;
+        double xn2 = ((p[0] + p[32]) + (p[64] + p[96])) + ((p[128] + p[160]) + (p[192] + p[224]));
+        xn2 = warp_sum(xn2);
+        if (threadIdx.x == 0) {
+            const double alpha = (double)col[(int64_t)k * stride];
+            double beta = alpha, denom = 1.0;
+            if (xn2 != 0.0) {
+                const double s = sqrt(alpha * alpha + xn2);
+                beta = alpha >= -sign_tol * s ? -s : s;
+                denom = alpha - beta;
+            }
+            red[NT] = denom;
+            red[NT + 1] = beta;
+            red[NT + 2] = alpha;
+            reinterpret_cast<float*>(red + NT + 3)[0] = (float)denom;
+            reinterpret_cast<int*>(red + NT + 4)[0] = xn2 != 0.0;
         }
     }
     __syncthreads();
-    return tk;
+    const bool reflect = reinterpret_cast<const int*>(red + NT + 4)[0] != 0;
+    if (reflect) {
+        if constexpr (sizeof(real) == 8) {
+            const double denom = red[NT];
+            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] = col[(int64_t)r * stride] / denom;
+        } else {
+            const float denom = reinterpret_cast<const float*>(red + NT + 3)[0];
+            for (int r = k + 1 + threadIdx.x; r < m; r += NT) col[(int64_t)r * stride] /= denom;
+        }
+    }
+    if (threadIdx.x == 0) {
+        // tau off the critical path: thread 0 forms it while the others divide
+        const double beta = red[NT + 1], alpha = red[NT + 2];
+        red[NT + 5] = reflect ? (beta - alpha) / beta : 0.0;
+        col[(int64_t)k * stride] = (real)beta;
+    }
+    __syncthreads();
+    return red[NT + 5];
 }
 
 // Diagonal T blocks of the t reflectors in V (m rows, column-major, ldv); the
 // diagonal/upper part of V is not read (unit diagonal implied).  `G` holds
-// NB * NB doubles of shared memory.
+// NB * NB and `X` NB * NB / 2 elements of shared memory.  cta_t_from_g forms
+// one block (pb <= NB reflectors) from G (strict upper part, ld ldg) and tau.
+//
+// A block's T is built by doubling (the compact-WY identity for a product of
+// two block reflectors): with T11, T22 the factors of reflectors [a, b) and
+// [b, c), the factor of [a, c) is [[T11, -T11 G12 T22], [0, T22]],
+// G12 = V(:, a:b)^T V(:, b:c).  Merging pairs of blocks of 1, 2, 4 and 8
+// reflectors gives the same T as the column recurrence
+// T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), in four steps instead of sixteen
+// sequential ones (every FP64 operation costs ~64 cycles of latency on GB300).
+template <class real>
+static __device__ void cta_t_from_g(const real* G, int ldg, const real* tau, real* Tb, int ldt, int pb, real* X) {
+    // the diagonal of T and zeros elsewhere
+    for (int o = threadIdx.x; o < pb * pb; o += NT) {
+        const int i = o % pb, k = o / pb;
+        Tb[i + (int64_t)k * ldt] = i == k ? tau[i] : (real)0;
+    }
+    __syncthreads();
+    for (int h = 1; h < pb; h *= 2) {
+        // merges of [b0, b0 + h) and [b0 + h, b0 + h + h2), b0 = 2 h g
+        const int nm = (pb + 2 * h - 1) / (2 * h);
+        // X_g = G12 T22 (h x h2; T22 upper triangular)
+        for (int o = threadIdx.x; o < nm * h * h; o += NT) {
+            const int g = o / (h * h), i = o % h, j = (o / h) % h;
+            const int b0 = 2 * h * g, h2 = min(h, pb - b0 - h);
+            if (j >= h2) continue;
+            real s = 0;
+            for (int u = 0; u <= j; u++)
+                s += G[(b0 + i) + (b0 + h + u) * ldg] * Tb[(b0 + h + u) + (int64_t)(b0 + h + j) * ldt];
+            X[g * h * h + i + j * h] = s;
+        }
+        __syncthreads();
+        // T12 = -T11 X_g (T11 upper triangular)
+        for (int o = threadIdx.x; o < nm * h * h; o += NT) {
+            const int g = o / (h * h), i = o % h, j = (o / h) % h;
+            const int b0 = 2 * h * g, h2 = min(h, pb - b0 - h);
+            if (j >= h2) continue;
+            real s = 0;
+            for (int u = i; u < h; u++) s += Tb[(b0 + i) + (int64_t)(b0 + u) * ldt] * X[g * h * h + u + j * h];
+            Tb[(b0 + i) + (int64_t)(b0 + h + j) * ldt] = -s;
+        }
+        __syncthreads();
+    }
+}
+
 template <class real>
 static __device__ void cta_form_tblocks(const real* V, int64_t ldv, int m, int t, const real* tau, real* T, int ldt,
-                                        real* G) {
+                                        real* G, real* X) {
     for (int p0 = 0; p0 < t; p0 += NB) {
         const int pb = t - p0 < NB ? t - p0 : NB;
         // G(i, k) = V(:, p0+i)^T V(:, p0+k), i < k
@@ -166,17 +245,7 @@ static __device__ void cta_form_tblocks(const real* V, int64_t ldv, int m, int t
             G[i + k * NB] = s;
         }
         __syncthreads();
-        for (int k = 0; k < pb; k++) {
-            const real tk = tau[p0 + k];
-            for (int i = threadIdx.x; i < k; i += NT) {
-                real s = 0;
-                for (int u = i; u < k; u++) s += T[(p0 + i) + (int64_t)(p0 + u) * ldt] * G[u + k * NB];
-                T[(p0 + i) + (int64_t)(p0 + k) * ldt] = -tk * s;
-            }
-            if (threadIdx.x == 0) T[(p0 + k) + (int64_t)(p0 + k) * ldt] = tk;
-            for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[(p0 + i) + (int64_t)(p0 + k) * ldt] = 0;
-            __syncthreads();
-        }
+        cta_t_from_g(G, NB, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, pb, X);
     }
 }
 
@@ -206,9 +275,16 @@ __device__ __forceinline__ void cta_small_gemv(int pb, int q, real* W1, real* P,
     }
     __syncthreads();
     for (int o = threadIdx.x; o < nout; o += NT) {
-        real s = P[o];
-        for (int g = 1; g < G; g++) s += P[o + g * nout];
-        W1[o] = s;
+        // the G row-group partials added as a tree (G a power of two <= 16)
+        real v[16];
+#pragma unroll
+        for (int g = 0; g < 16; g++) v[g] = g < G ? P[o + g * nout] : (real)0;
+#pragma unroll
+        for (int h = 8; h > 0; h >>= 1)
+            if (h < G)
+#pragma unroll
+                for (int g = 0; g < h; g++) v[g] += v[g + h];
+        W1[o] = v[0];
     }
     __syncthreads();
 }
@@ -361,7 +437,7 @@ static __device__ void cta_apply_q_chunked(const real* V, int64_t ldv, int m, in
 // Shared memory (bytes) needed by cta_qr with column chunk qc and a staged
 // panel of up to prow rows (prow = 0: panels stay in global memory).
 __host__ __device__ constexpr int64_t qr_smem_bytes(int esz, int qc, int prow = 0) {
-    return 8 * NWARP + (int64_t)esz * (NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB);
+    return 8 * RED + (int64_t)esz * (NT + NB + NB * NB + 2 * NB * qc + NT + (int64_t)prow * NB);
 }
 
 // Factor the panel columns [p0, pe) of A (rows p0..m-1) in place, column by
@@ -417,9 +493,14 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
             P[threadIdx.x] = part;
             __syncthreads();
             if (threadIdx.x < ncol) {
-                real s = Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp];
-                for (int gg = 0; gg < NT / NB; gg++) s += P[gg * NB + threadIdx.x];
-                Wk[threadIdx.x] = tk * s;
+                // row k's entry plus the 16 row-group partials (added as a tree)
+                static_assert(NT / NB == 16, "sixteen row groups");
+                const real* pp = P + threadIdx.x;
+                const real s = (((pp[0] + pp[NB]) + (pp[2 * NB] + pp[3 * NB])) +
+                                ((pp[4 * NB] + pp[5 * NB]) + (pp[6 * NB] + pp[7 * NB]))) +
+                               (((pp[8 * NB] + pp[9 * NB]) + (pp[10 * NB] + pp[11 * NB])) +
+                                ((pp[12 * NB] + pp[13 * NB]) + (pp[14 * NB] + pp[15 * NB])));
+                Wk[threadIdx.x] = tk * (Pb[k + (int64_t)(k + 1 + threadIdx.x - p0) * ldp] + s);
             }
             __syncthreads();
             const int rows = m - k;
@@ -439,7 +520,7 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
     }
     // T block of the panel (reflectors = panel rows p0.. of the panel view)
     const real* Vp = Pb + p0;
-    cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G);
+    cta_form_tblocks(Vp, ldp, m - p0, pe - p0, tau + p0, T + p0 + (int64_t)p0 * ldt, ldt, G, P);
     *ldv = ldp;
     return Vp;
 }
@@ -452,8 +533,8 @@ static __device__ const real* cta_qr_panel(real* A, int64_t lda, int m, int p0, 
 template <class real>
 static __device__ void cta_qr(real* A, int64_t lda, int m, int n, real* tau, real* T, int ldt, int qc, int prow,
                               double* smem, double sign_tol = 0.0) {
-    double* red = smem;
-    real* P = reinterpret_cast<real*>(red + NWARP);   // NT partial dots
+    double* red = smem;                               // RED
+    real* P = reinterpret_cast<real*>(red + RED);     // NT partial dots
     real* Wk = P + NT;         // NB
     real* G = Wk + NB;         // NB * NB
     real* W = G + NB * NB;     // 2 * NB * qc + NT

@@ -85,6 +85,7 @@ constexpr int cpqr_cs() { return sizeof(real) == 8 ? 16 : 8; }
 constexpr int64_t kBigCPQR = 1 << 17;   // n_p x ncols from which an interface uses a cluster
 constexpr int QR_CS = 16;
 constexpr int64_t kBigQR = 1 << 16;     // m x n from which a front uses a cluster
+constexpr int kNumSM = 152;             // SMs of a GB300
 constexpr int QAPPLY = 32;   // column chunk of one front-apply task
 // CPQR reflectors: a pivot column's leading entry within this fraction of
 // the column's norm counts as zero (beta = -norm).  M_p is assembled from
@@ -112,10 +113,11 @@ __host__ __device__ constexpr size_t qrcl_smem_bytes(int esz, int slab) {
 // slab per CTA (staged in its shared memory).  For column k every CTA sums,
 // over its own rows below k, the squares of column k and its products with
 // the panel's later columns; the owner of row k adds that row.  One cluster
-// barrier later every CTA adds the CTAs' sums in rank order through
-// distributed shared memory and forms the same Householder scalars and the
-// same w_j = tau (A(k, j) + sum_r A(r, k) A(r, j) / (alpha - beta)), the
-// dot product of the reflector with column j, and updates its own rows.
+// barrier later warp 0 of every CTA adds the CTAs' sums (a fixed tree over
+// the ranks, read through distributed shared memory) and forms the same
+// Householder scalars and the same
+// w_j = tau (A(k, j) + sum_r A(r, k) A(r, j) / (alpha - beta)), the dot
+// product of the reflector with column j; then every CTA updates its rows.
 // The T block comes from the slabs' partial V^T V the same way.  The CS CTAs
 // then apply the panel to their slices of the trailing columns (reflectors
 // read from global memory).  Distributed-shared-memory slots alternate
@@ -168,8 +170,12 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
             __syncthreads();
             double* sl = slot + (ph & 1) * SL;
             if (threadIdx.x <= ncol) {
-                double sacc = 0.0;
-                for (int gg = 0; gg < NT / NB; gg++) sacc += Pd[gg * NB + threadIdx.x];
+                // the NT / NB = 16 row-group partials of this column, added as a tree
+                const double* pp = Pd + threadIdx.x;
+                const double sacc = (((pp[0] + pp[NB]) + (pp[2 * NB] + pp[3 * NB])) +
+                                     ((pp[4 * NB] + pp[5 * NB]) + (pp[6 * NB] + pp[7 * NB]))) +
+                                    (((pp[8 * NB] + pp[9 * NB]) + (pp[10 * NB] + pp[11 * NB])) +
+                                     ((pp[12 * NB] + pp[13 * NB]) + (pp[14 * NB] + pp[15 * NB])));
                 sl[threadIdx.x == 0 ? 0 : 1 + threadIdx.x] = sacc;
             }
             if (threadIdx.x < NB) {
@@ -180,35 +186,64 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
             }
             cl.sync();
             ph++;
-            double x2 = 0.0, alpha = 0.0;
-            for (int rr = 0; rr < CS; rr++) {
-                const double* o = cl.map_shared_rank(sl, rr);
-                x2 += o[0];
-                alpha += o[1];
-            }
-            double tk = 0.0, beta = alpha, denom = 1.0;
-            if (x2 != 0.0) {
-                const double s = sqrt(alpha * alpha + x2);
-                beta = alpha >= -t.sign_tol * s ? -s : s;
-                tk = (beta - alpha) / beta;
-                denom = alpha - beta;
-            }
-            if (threadIdx.x < ncol && tk != 0.0) {
-                double sacc = 0.0, akj = 0.0;
-                for (int rr = 0; rr < CS; rr++) {
-                    const double* o = cl.map_shared_rank(sl, rr);
-                    sacc += o[2 + threadIdx.x];
-                    akj += o[2 + NB + threadIdx.x];
+            // the CTAs' sums added by warp 0 (a tree over the ranks, the same
+            // in every CTA), the scalars by its lane 0, the w_j by lane j: FP64
+            // work of one warp instead of every thread
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                double x2 = 0.0, alpha = 0.0;
+                if (lane < CS) {
+                    const double* o = cl.map_shared_rank(sl, lane);
+                    x2 = o[0];
+                    alpha = o[1];
                 }
-                Wk[threadIdx.x] = (real)(tk * (akj + sacc / denom));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+                    alpha += __shfl_xor_sync(0xffffffffu, alpha, off);
+                }
+                x2 = __shfl_sync(0xffffffffu, x2, 0);
+                alpha = __shfl_sync(0xffffffffu, alpha, 0);
+                double beta = alpha, denom = 1.0;
+                if (x2 != 0.0) {
+                    const double sq = sqrt(alpha * alpha + x2);
+                    beta = alpha >= -t.sign_tol * sq ? -sq : sq;
+                    denom = alpha - beta;
+                }
+                double u = 0.0;
+                if (lane < ncol && x2 != 0.0) {
+                    double sa[CS], ak[CS];
+#pragma unroll
+                    for (int rr = 0; rr < CS; rr++) {
+                        const double* o = cl.map_shared_rank(sl, rr);
+                        sa[rr] = o[2 + lane];
+                        ak[rr] = o[2 + NB + lane];
+                    }
+#pragma unroll
+                    for (int h = CS / 2; h > 0; h >>= 1)
+#pragma unroll
+                        for (int rr = 0; rr < h; rr++) {
+                            sa[rr] += sa[rr + h];
+                            ak[rr] += ak[rr + h];
+                        }
+                    u = ak[0] + sa[0] / denom;
+                }
+                const double tk = x2 != 0.0 ? (beta - alpha) / beta : 0.0;
+                if (lane < ncol && tk != 0.0) Wk[lane] = (real)(tk * u);
+                if (lane == 0) {
+                    Pd[0] = tk;
+                    Pd[1] = beta;
+                    Pd[2] = denom;
+                }
             }
             __syncthreads();
+            const double tk = Pd[0], beta = Pd[1], denom = Pd[2];
             if (tk != 0.0) {
                 if constexpr (sizeof(real) == 8) {
                     for (int r = max(lo, k + 1) + (int)threadIdx.x; r < hi; r += NT) col[r] = col[r] / denom;
                 } else {
-                    const real sc = (real)(1.0 / denom);
-                    for (int r = max(lo, k + 1) + (int)threadIdx.x; r < hi; r += NT) col[r] *= sc;
+                    const real dn = (real)denom;
+                    for (int r = max(lo, k + 1) + (int)threadIdx.x; r < hi; r += NT) col[r] /= dn;
                 }
             }
             __syncthreads();
@@ -245,26 +280,21 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
         cl.sync();
         ph++;
         if (q == 0) {
-            // G summed in rank order, then the T block (column recurrence)
+            // G summed over the ranks (a tree), then the T block
             real* Gs = reinterpret_cast<real*>(Pd);
             for (int o = threadIdx.x; o < pb * pb; o += NT) {
-                double acc = 0.0;
-                for (int rr = 0; rr < CS; rr++) acc += cl.map_shared_rank(Gp, rr)[o];
-                Gs[o] = (real)acc;   // pb * pb <= NT
+                if (o % pb >= o / pb) continue;   // strict upper part only
+                double a[CS];
+#pragma unroll
+                for (int rr = 0; rr < CS; rr++) a[rr] = cl.map_shared_rank(Gp, rr)[o];
+#pragma unroll
+                for (int h = CS / 2; h > 0; h >>= 1)
+#pragma unroll
+                    for (int rr = 0; rr < h; rr++) a[rr] += a[rr + h];
+                Gs[o] = (real)a[0];   // pb * pb <= NT
             }
             __syncthreads();
-            real* T = t.T + p0 + (int64_t)p0 * tt;
-            for (int k = 0; k < pb; k++) {
-                const real tkr = t.tau[p0 + k];
-                for (int i = threadIdx.x; i < k; i += NT) {
-                    real sacc = 0;
-                    for (int u = i; u < k; u++) sacc += T[i + (int64_t)u * tt] * Gs[u + k * pb];
-                    T[i + (int64_t)k * tt] = -tkr * sacc;
-                }
-                if (threadIdx.x == 0) T[k + (int64_t)k * tt] = tkr;
-                for (int i = k + 1 + threadIdx.x; i < pb; i += NT) T[i + (int64_t)k * tt] = 0;
-                __syncthreads();
-            }
+            cta_t_from_g(Gs, pb, t.tau + p0, t.T + p0 + (int64_t)p0 * tt, tt, pb, W);
         }
         cl.sync();   // panel, tau and T visible to the cluster; Gp read before it is rewritten
         ph++;
@@ -478,11 +508,12 @@ template <class real>
 __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ tasks,
                                              const GatherSeg<real>* __restrict__ gsegs, double eps) {
     extern __shared__ double sm[];
-    double* red = sm;                                            // NWARP
-    long long* redv = reinterpret_cast<long long*>(sm + NWARP);  // NWARP
-    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
-    real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
-    real* vs = G + NB * NB;                                      // n_p
+    double* red = sm;                                                // RED
+    long long* redv = reinterpret_cast<long long*>(sm + RED);        // NWARP
+    int* redi = reinterpret_cast<int*>(sm + RED + NWARP);            // NWARP ints
+    real* G = reinterpret_cast<real*>(sm + RED + 2 * NWARP);         // NB * NB
+    real* X = G + NB * NB;                                           // NB * NB / 2
+    real* vs = X + NB * NB / 2;                                      // n_p
     const CPQRTask<real> t = tasks[blockIdx.x];
     const int m = t.np, c = t.ncols;
     real* M = t.M;  // M(r, j) = M[r * c + j]
@@ -515,18 +546,22 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
     const int tmax = m < c ? m : c;
     int rank = 0;
     double R11 = 0.0;
+    __shared__ int s_stop;
     for (int k = 0; k < tmax; k++) {
-        double bv = -1.0;
+        // pivot: largest norm, ties to the lowest column (integer keys)
+        long long bk = -1;
         int bi = 0x7fffffff;
         for (int j = k + threadIdx.x; j < c; j += NT) {
-            const double v = (double)t.norms[j];
-            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+            const long long key = nonneg_key(t.norms[j]);
+            if (key > bk || (key == bk && j < bi)) { bk = key; bi = j; }
         }
-        if (bv < 0.0) bv = 0.0;
-        double gv;
+        long long gk;
         int gi;
-        block_argmax(bv, bi, redv, redi, gv, gi);
-        if constexpr (sizeof(real) != 8) {
+        block_argmax_key(bk, bi, redv, redi, gk, gi);
+        double gv = 0.0;
+        if constexpr (sizeof(real) == 8) {
+            gv = __longlong_as_double(gk);
+        } else {
             // |R_kk| in FP64 from the pivot column (rows k..m-1)
             double part = 0.0;
             for (int r = k + threadIdx.x; r < m; r += NT) {
@@ -535,11 +570,15 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
             }
             gv = block_sum(part, red);
         }
-        const double pn = sqrt(gv);
-        if (threadIdx.x == 0) t.rdiag[k] = pn;
-        if (k == 0) R11 = pn;
-        if (R11 == 0.0) break;
-        if (pn < eps * R11) break;
+        // the rank decision by one thread (FP64), shared with the CTA
+        if (threadIdx.x == 0) {
+            const double pn = sqrt(gv);
+            t.rdiag[k] = pn;
+            if (k == 0) R11 = pn;
+            s_stop = (R11 == 0.0) || (pn < eps * R11);
+        }
+        __syncthreads();
+        if (s_stop) break;
         if (gi != k) {
             for (int r = threadIdx.x; r < m; r += NT) {
                 real* row = M + (int64_t)r * c;
@@ -569,7 +608,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CPQRTask<real>* __restrict__ 
     }
     if (threadIdx.x == 0) *t.rank = rank;
     __syncthreads();
-    cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G);
+    cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G, X);
 }
 
 // Cluster form of k_cpqr for large interfaces: the CS CTAs of a thread-block
@@ -584,13 +623,15 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double sm[];
-    double* red = sm;                                            // NWARP
-    long long* redv = reinterpret_cast<long long*>(sm + NWARP);  // NWARP
-    int* redi = reinterpret_cast<int*>(sm + 2 * NWARP);          // NWARP ints
-    real* G = reinterpret_cast<real*>(sm + 3 * NWARP);           // NB * NB
-    real* vs = G + NB * NB;                                      // n_p
-    __shared__ double slot_v, slot_n;
-    __shared__ int slot_i;
+    double* red = sm;                                                // RED
+    long long* redv = reinterpret_cast<long long*>(sm + RED);        // NWARP
+    int* redi = reinterpret_cast<int*>(sm + RED + NWARP);            // NWARP ints
+    real* G = reinterpret_cast<real*>(sm + RED + 2 * NWARP);         // NB * NB
+    real* X = G + NB * NB;                                           // NB * NB / 2
+    real* vs = X + NB * NB / 2;                                      // n_p
+    __shared__ long long slot_k;
+    __shared__ double slot_n;
+    __shared__ int slot_i, s_gi, s_stop;
     const int q = (int)cl.block_rank();
     const CPQRTask<real> t = tasks[blockIdx.x / CS];
     const int m = t.np, c = t.ncols;
@@ -628,20 +669,22 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     int rank = 0;
     double R11 = 0.0;
     for (int k = 0; k < tmax; k++) {
-        // pivot candidate of this CTA, then of the cluster
-        double bv = -1.0;
+        // pivot candidate of this CTA, then of the cluster (integer keys)
+        long long bk = -1;
         int bi = 0x7fffffff;
         for (int j = max(k, j0) + threadIdx.x; j < j1; j += NT) {
-            const double v = (double)t.norms[j];
-            if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+            const long long key = nonneg_key(t.norms[j]);
+            if (key > bk || (key == bk && j < bi)) { bk = key; bi = j; }
         }
-        double lv;
+        long long lk;
         int li;
-        block_argmax(bv, bi, redv, redi, lv, li);
+        block_argmax_key(bk, bi, redv, redi, lk, li);
         // FP64 |R_kk|^2 of this CTA's candidate, published with it (computed
         // before any CTA may swap columns)
-        double ln2 = lv;
-        if constexpr (sizeof(real) != 8) {
+        double ln2 = 0.0;
+        if constexpr (sizeof(real) == 8) {
+            if (lk >= 0) ln2 = __longlong_as_double(lk);
+        } else {
             double part = 0.0;
             if (li < c)
                 for (int r = k + threadIdx.x; r < m; r += NT) {
@@ -650,20 +693,33 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
                 }
             ln2 = block_sum(part, red);
         }
-        if (threadIdx.x == 0) { slot_v = lv; slot_i = li; slot_n = ln2; }
+        if (threadIdx.x == 0) { slot_k = lk; slot_i = li; slot_n = ln2; }
         cl.sync();
-        double gv = -1.0, gn = 0.0;
-        int gi = 0x7fffffff;
-        for (int r = 0; r < CS; r++) {
-            const double v = *cl.map_shared_rank(&slot_v, r);
-            const int i = *cl.map_shared_rank(&slot_i, r);
-            if (v > gv || (v == gv && i < gi)) { gv = v; gi = i; gn = *cl.map_shared_rank(&slot_n, r); }
+        // the cluster's pivot and the rank decision by one thread per CTA
+        // (every CTA reaches the same result)
+        if (threadIdx.x == 0) {
+            long long ks[CS];
+            int is[CS];
+#pragma unroll
+            for (int r = 0; r < CS; r++) {   // all loads in flight, then the compares
+                ks[r] = *cl.map_shared_rank(&slot_k, r);
+                is[r] = *cl.map_shared_rank(&slot_i, r);
+            }
+            long long gk = -1;
+            int gi = 0x7fffffff, gr = 0;
+#pragma unroll
+            for (int r = 0; r < CS; r++)
+                if (ks[r] > gk || (ks[r] == gk && is[r] < gi)) { gk = ks[r]; gi = is[r]; gr = r; }
+            const double gn = *cl.map_shared_rank(&slot_n, gr);
+            const double pn = sqrt(gn);
+            if (q == 0) t.rdiag[k] = pn;
+            if (k == 0) R11 = pn;
+            s_gi = gi;
+            s_stop = (R11 == 0.0) || (pn < eps * R11);
         }
-        if (gn < 0.0) gn = 0.0;
-        const double pn = sqrt(gn);
-        if (q == 0 && threadIdx.x == 0) t.rdiag[k] = pn;
-        if (k == 0) R11 = pn;
-        const bool stop = (R11 == 0.0) || (pn < eps * R11);
+        __syncthreads();
+        const int gi = s_gi;
+        const bool stop = s_stop != 0;
         const int owner = k / cw;
         if (!stop && q == owner && gi != k) {
             for (int r = threadIdx.x; r < m; r += NT) {
@@ -700,7 +756,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT)
     cl.sync();
     if (q == 0) {
         if (threadIdx.x == 0) *t.rank = rank;
-        cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G);
+        cta_form_tblocks(t.V, m, m, rank, t.tau, t.T, t.kmax, G, X);
     }
 }
 
@@ -889,7 +945,7 @@ __device__ void lanczos_solve_r(const real* R, int64_t ld, int n, const double* 
 template <class real>
 __global__ void __launch_bounds__(NT) k_sigma_min(const SigmaTask<real>* __restrict__ tasks) {
     __shared__ double alpha[kLanczosMax], beta2[kLanczosMax], hc[kLanczosMax];
-    __shared__ double red[NWARP];
+    __shared__ double red[RED];
     __shared__ double theta_sh;
     __shared__ int bad;
     const SigmaTask<real> t = tasks[blockIdx.x];
@@ -1700,7 +1756,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
             while (qapply > 8 && ((mm + 1) / 2 + 1) * 8 + staged_smem_elems(mm, qapply) * (int64_t)esz > kSmemMax)
                 qapply /= 2;
-            while (qapply > 4 && cols / qapply < 2 * 152) qapply /= 2;
+            while (qapply > 4 && cols / qapply < 2 * kNumSM) qapply /= 2;
         }
         for (int j = 0; j < ncl; j++) {
             if (fronts_of[j].empty() || sz[j] == 0) continue;
@@ -2165,7 +2221,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) rowlist[sp.rowidx[e]].push_back({j, e});
             std::vector<CPQRTask<real>> cp, cpb;
             std::vector<GatherSeg<real>> gs;
-            std::vector<int> cp_of(ncl, -1);
+            int nif = 0;   // interfaces of the level (CPQR units)
+            for (int p : rest) nif += sz[p] > 0;
             int64_t mtot = 0, ntot = 0, vtot = 0, ttot = 0, rtot = 0, ptot = 0;
             std::vector<int> ncols(ncl, 0);
             for (int p : rest) {
@@ -2259,10 +2316,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 ro += kmax[p] + 1;
                 kmx = std::max(kmx, kmax[p]);
                 npmax = std::max(npmax, (int)sz[p]);
-                cp_of[p] = (int)cp.size();
-                // large interfaces go to the cluster kernel (cpqr_cs CTAs each)
-                if ((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= 512) cpb.push_back(t);
-                else cp.push_back(t);
+                // large interfaces go to the cluster kernel (cpqr_cs CTAs each),
+                // and at levels with fewer interfaces than SMs every interface
+                // with two or more columns per CTA of the cluster
+                if (((int64_t)t.np * t.ncols >= kBigCPQR && t.ncols >= 512) ||
+                    (nif <= kNumSM && t.ncols >= 2 * cpqr_cs<real>() && t.np >= 8))
+                    cpb.push_back(t);
+                else
+                    cp.push_back(t);
             }
             if (!atb.empty()) {
                 std::vector<ScalePiece> pc;
@@ -2274,7 +2335,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 SPAQR_LAUNCH(KK_UNSCALED, fl_atb, by_atb, st, k_atb_sigma<real><<<(unsigned)pc.size(), NT, 0, st>>>(d, dp));
                 C.launched();
             }
-            const size_t smem_cp = (size_t)(3 * NWARP) * 8 + (size_t)(NB * NB + npmax) * esz;
+            const size_t smem_cp = (size_t)(RED + 2 * NWARP) * 8 + (size_t)(NB * NB + NB * NB / 2 + npmax) * esz;
             GatherSeg<real>* dgs = nullptr;
             if (!cp.empty() || !cpb.empty()) {
                 dgs = C.upload(gs, false);

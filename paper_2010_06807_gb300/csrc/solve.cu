@@ -280,7 +280,8 @@ __device__ __forceinline__ WideSmem<real> wide_smem_layout(double* sm, int slab_
 // unit diagonal implied unless explicit_v) and the diagonal NB x NB blocks of
 // T (ld ldt), with B's rows split over the cluster: this CTA holds rows
 // [lo, hi) in w.Bs.  Per panel the partial products V_b^T B over every CTA's
-// rows are added in rank order through distributed shared memory, then every
+// rows are added (a fixed tree over the ranks) through distributed shared
+// memory, then every
 // CTA updates its rows.  V rows and T block of the next panel are staged by
 // cp.async while the current one is applied.
 template <class real, int CS, int Q>
@@ -327,9 +328,15 @@ __device__ void cl_apply_q(cooperative_groups::cluster_group& cl, const WideSmem
         });
         cl.sync();
         for (int o = threadIdx.x; o < pb * qn; o += NT) {
-            real v = 0;
-            for (int q = 0; q < CS; q++) v += cl.map_shared_rank(myp, q)[o];
-            w.W1[o] = v;
+            // the CTAs' partials added as a tree over the ranks
+            real v[CS];
+#pragma unroll
+            for (int q = 0; q < CS; q++) v[q] = cl.map_shared_rank(myp, q)[o];
+#pragma unroll
+            for (int h = CS / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int q = 0; q < h; q++) v[q] += v[q + h];
+            w.W1[o] = v[0];
         }
         __syncthreads();
         cta_tblock_mul(w.Ts + (k & 1) * NB * NB, pb, 0, pb, qn, trans, w.W1, w.W2);
@@ -709,30 +716,49 @@ __global__ void k_residual(int64_t n, int nrhs, const int64_t* __restrict__ rowp
     R[r + c * n] = B[r + c * ldb] - s;
 }
 
-// out[i + v * nout] = dot(U_i[v], W[v]) for i < nvec and every virtual column
-// v; U_i = U + i * n * nrhs.  One CTA per (i, v); fixed reduction order.
-__global__ void __launch_bounds__(NT) k_dots(int64_t n, int nrhs, VCols vc, const double* __restrict__ U, int nvec,
-                                             const double* __restrict__ W, double* __restrict__ out, int nout) {
-    __shared__ double red[NWARP];
-    const int i = blockIdx.x % nvec, v = blockIdx.x / nvec;
+// Partial dot products: part[(i + v * nvec) * S + s] = dot over chunk s of
+// the S row chunks of U_i[v] and W[v], for i < nvec and every virtual column
+// v; U_i = U + i * n * nrhs.  One CTA per (i, v, chunk), so that a few long
+// dot products still spread over every SM; fixed reduction order.
+__global__ void __launch_bounds__(NT) k_dots_part(int64_t n, int nrhs, VCols vc, const double* __restrict__ U,
+                                                  int nvec, const double* __restrict__ W, double* __restrict__ part,
+                                                  int S) {
+    __shared__ double red[RED];
+    const int i = blockIdx.x % nvec, v = blockIdx.x / nvec, sc = blockIdx.y;
     int64_t base, len;
     vc.range(v, n, base, len);
+    const int64_t a = len * sc / S, b = len * (sc + 1) / S;
     const double* u = U + (int64_t)i * n * nrhs + base;
     const double* w = W + base;
     // four independent partial sums per thread (loads in flight), added in a
     // fixed order
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int64_t r = threadIdx.x;
-    for (; r + 3 * NT < len; r += 4 * NT) {
+    int64_t r = a + threadIdx.x;
+    for (; r + 3 * NT < b; r += 4 * NT) {
         s0 += u[r] * w[r];
         s1 += u[r + NT] * w[r + NT];
         s2 += u[r + 2 * NT] * w[r + 2 * NT];
         s3 += u[r + 3 * NT] * w[r + 3 * NT];
     }
-    for (; r < len; r += NT) s0 += u[r] * w[r];
-    double s = block_sum((s0 + s1) + (s2 + s3), red);
-    if (threadIdx.x == 0) out[i + (int64_t)v * nout] = s;
+    for (; r < b; r += NT) s0 += u[r] * w[r];
+    const double s = block_sum((s0 + s1) + (s2 + s3), red);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * S + sc] = s;
 }
+
+// out[i + v * nout] = the S partials of (i, v) added in chunk order.
+__global__ void k_dots_sum(int nvec, int nv, const double* __restrict__ part, int S, double* __restrict__ out,
+                           int nout) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nvec * nv) return;
+    const int i = o % nvec, v = o / nvec;
+    const double* p = part + (int64_t)o * S;
+    double s = 0.0;
+    for (int c = 0; c < S; c++) s += p[c];
+    out[i + (int64_t)v * nout] = s;
+}
+
+// Row chunks of a dot product of len rows: about 4096 rows each, at most 32.
+static inline int dot_chunks(int64_t len) { return (int)std::max<int64_t>(1, std::min<int64_t>(32, len / 4096)); }
 
 // W[:, v] -= sum_i U_i[:, v] h[i, v]  (active virtual columns only)
 __global__ void k_orth_update(int64_t n, int nrhs, VCols vc, const double* __restrict__ U, int nvec,
@@ -1553,6 +1579,16 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
     int cap = std::min(maxit, 48) + 1;
     double* Vb = C.alloc<double>((int64_t)cap * n * nrhs);
     double* Zb = C.alloc<double>((int64_t)cap * n * nrhs);   // Z_j = M^{-1} V_j (flexible GMRES)
+    const int dS = dot_chunks(n / nseg);                       // row chunks of a dot product
+    double* dpart = C.alloc<double>((int64_t)cap * nv * dS);   // their partial sums
+    // out[i + v * nout] = dot(U_i[v], W[v]) for i < nvec, every virtual column v
+    auto dots = [&](const double* U, int nvec, const double* W, double* out, int nout, double fl, double by) {
+        SPAQR_LAUNCH(KK_GMRES_ORTH, fl, by, st,
+                     k_dots_part<<<dim3((unsigned)(nvec * nv), (unsigned)dS), NT, 0, st>>>(n, nrhs, vc, U, nvec, W,
+                                                                                        dpart, dS));
+        SPAQR_LAUNCH(KK_GMRES_ORTH, 0.0, 8.0 * nvec * nv * dS, st,
+                     k_dots_sum<<<(unsigned)((nvec * nv + 255) / 256), 256, 0, st>>>(nvec, nv, dpart, dS, out, nout));
+    };
     if (C.rc) return C.rc;
     C.cuda(cudaMemsetAsync(flag, 0, sizeof(int), st));
     ApplyGraph ag;
@@ -1572,10 +1608,8 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
     SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st,
                  k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, X0, n, dB, lb, Vb));
     SPAQR_LAUNCH(KK_GMRES_SMALL, 0.0, 16.0 * n * nrhs, st, k_copy_cols<<<nbl, 256, 0, st>>>(n, nrhs, dB, lb, Wv, n));
-    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
-                 k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Wv, 1, Wv, bn, 1));  // ||b||^2
-    SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
-                 k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Vb, 1, Vb, hn, 1));  // ||r0||^2
+    dots(Wv, 1, Wv, bn, 1, 2.0 * n * nrhs, 16.0 * n * nrhs);   // ||b||^2
+    dots(Vb, 1, Vb, hn, 1, 2.0 * n * nrhs, 16.0 * n * nrhs);   // ||r0||^2
     C.launched();
     std::vector<double> hb(nv), hr(nv), hest(nv), hres(nv, 1.0);
     std::vector<int> hact(nv, 1), hit(nv, 0), hwant(nv, 0);
@@ -1620,9 +1654,12 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
             C.cuda(cudaMemcpyAsync(nzb, Zb, sizeof(double) * cap * n * nrhs, cudaMemcpyDeviceToDevice, st));
             C.release(Vb);
             C.release(Zb);
+            C.release(dpart);
             Vb = nvb;
             Zb = nzb;
             cap = ncap;
+            dpart = C.alloc<double>((int64_t)cap * nv * dS);
+            if (C.rc) break;
         }
         double* Vj = Vb + (int64_t)j * n * nrhs;
         double* Zj = Zb + (int64_t)j * n * nrhs;
@@ -1640,16 +1677,13 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
                      k_spmv<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Zj, n, Wv, n));
         // classical Gram-Schmidt, twice
         const double fo = 2.0 * n * (j + 1) * nrhs;
-        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 2) * nrhs, st,
-                     k_dots<<<(j + 1) * nv, NT, 0, st>>>(n, nrhs, vc, Vb, j + 1, Wv, h1, ldh));
+        dots(Vb, j + 1, Wv, h1, ldh, fo, 8.0 * n * (j + 2) * nrhs);
         SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 3) * nrhs, st,
                      k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, vc, Vb, j + 1, h1, ldh, Wv, active));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 2) * nrhs, st,
-                     k_dots<<<(j + 1) * nv, NT, 0, st>>>(n, nrhs, vc, Vb, j + 1, Wv, h2, ldh));
+        dots(Vb, j + 1, Wv, h2, ldh, fo, 8.0 * n * (j + 2) * nrhs);
         SPAQR_LAUNCH(KK_GMRES_ORTH, fo, 8.0 * n * (j + 3) * nrhs, st,
                      k_orth_update<<<nbl, 256, 0, st>>>(n, nrhs, vc, Vb, j + 1, h2, ldh, Wv, active));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
-                     k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Wv, 1, Wv, hn, 1));
+        dots(Wv, 1, Wv, hn, 1, 2.0 * n * nrhs, 16.0 * n * nrhs);
         SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * nv, 16.0 * nv, st, k_sqrtv<<<1, 32, 0, st>>>(nv, hn));
         C.launched();
         SPAQR_LAUNCH(KK_GMRES_SMALL, 1.0 * n * nrhs, 16.0 * n * nrhs, st,
@@ -1683,8 +1717,7 @@ int gmres_impl(const spaqr_factor_t* F, const spaqr_csr* A, int nrhs, int nseg, 
                      k_accept<<<nbl, 256, 0, st>>>(n, nrhs, vc, X0, n, Zv, Wv, n, want));
         SPAQR_LAUNCH(KK_SPMV, 2.0 * nnz * nrhs, 12.0 * nnz + (8.0 * nnz + 16.0 * n) * nrhs, st,
                      k_residual<<<nbl, 256, 0, st>>>(n, nrhs, rp, ci, va, Wv, n, dB, lb, Zv));
-        SPAQR_LAUNCH(KK_GMRES_ORTH, 2.0 * n * nrhs, 16.0 * n * nrhs, st,
-                     k_dots<<<nv, NT, 0, st>>>(n, nrhs, vc, Zv, 1, Zv, rn, 1));
+        dots(Zv, 1, Zv, rn, 1, 2.0 * n * nrhs, 16.0 * n * nrhs);
         C.launched();
         C.cuda(cudaMemcpyAsync(hrn.data(), rn, 8 * nv, cudaMemcpyDeviceToHost, st));
         C.cuda(cudaStreamSynchronize(st));
