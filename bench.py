@@ -739,8 +739,10 @@ def ours(a):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "gpu_launches_note": "kernels of ours launched in the timed steps, graph replays counted per kernel",
-        "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)} for k, v in kstats.items()
-                    if v["launches"]},
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3), "idle_ms": round(v["idle_ms"], 3)}
+                    for k, v in kstats.items() if v["launches"]},
+        "kernels_note": "profiled pass of 3 steps: ms = CUDA-event time of the kind's launches, idle_ms = time "
+                        "the stream stood idle before them (waiting for the host; upper bound)",
         "roofline": roof,
         "rooflines": kernel_rooflines(kstats, peaks, True, bf16, TRAFFIC),
         "peaks_measured_tflops": peaks,

@@ -482,6 +482,10 @@ typedef struct {
     double total_ms;
     double flops;
     double bytes;
+    double idle_ms;     /* with spaqr_profile(1): time the stream stood idle between the
+                           previous profiled launch on it and each launch of this kind
+                           (the GPU waiting for the host); an upper bound, since the
+                           event records add host time of their own */
 } spaqr_kernel_stat;
 
 /* Zero all counters and drop pending event records. */

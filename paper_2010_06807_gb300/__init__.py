@@ -108,7 +108,7 @@ class _LevelInfo(ctypes.Structure):
 
 class _KStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("idle_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -695,7 +695,8 @@ def spaqr_use_graphs(on=True):
 
 
 def spaqr_stats():
-    """(total launches, {kernel: dict(launches, total_ms, flops, bytes)}) since the last reset."""
+    """(total launches, {kernel: dict(launches, total_ms, flops, bytes, idle_ms)}) since the last
+    reset; idle_ms: time the stream stood idle before the kind's launches (profiling on)."""
     load_library()
     cnt = ctypes.c_int(0)
     tot = ctypes.c_int64(0)
@@ -705,7 +706,7 @@ def spaqr_stats():
     out = {}
     for k in arr:
         out[k.name.decode()] = dict(launches=int(k.launches), total_ms=float(k.total_ms),
-                                    flops=float(k.flops), bytes=float(k.bytes))
+                                    flops=float(k.flops), bytes=float(k.bytes), idle_ms=float(k.idle_ms))
     return int(tot.value), out
 
 

@@ -215,12 +215,12 @@ const char* kKindNames[KK_COUNT] = {
     "sparsify_merge", "solve_perm", "solve_front_fwd", "solve_ss_fwd", "solve_ss_bwd",
     "solve_front_bwd", "spmv", "gmres_orth", "gmres_small", "solve_rsj", "sigma_min",
     "unscaled_sparsify", "sigma_qr", "front_apply_tc", "interface_tc"};
-struct Rec { int kind; cudaEvent_t a, b; };
+struct Rec { int kind; cudaEvent_t a, b; void* stream; };
 std::mutex g_mu;
 bool g_prof = false;
 int64_t g_launches = 0;
 int64_t g_count[KK_COUNT];
-double g_ms[KK_COUNT], g_flops[KK_COUNT], g_bytes[KK_COUNT];
+double g_ms[KK_COUNT], g_flops[KK_COUNT], g_bytes[KK_COUNT], g_idle[KK_COUNT];
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -281,6 +281,7 @@ int prof_begin(void* stream, int kind, double flops, double bytes) {
     if (!g_prof) return -1;
     Rec r;
     r.kind = kind;
+    r.stream = stream;
     r.a = get_event();
     r.b = get_event();
     if (!r.a || !r.b) return -1;
@@ -345,7 +346,7 @@ extern "C" void spaqr_stats_reset(void) {
     }
     g_recs.clear();
     g_launches = 0;
-    for (int k = 0; k < KK_COUNT; k++) { g_count[k] = 0; g_ms[k] = g_flops[k] = g_bytes[k] = 0.0; }
+    for (int k = 0; k < KK_COUNT; k++) { g_count[k] = 0; g_ms[k] = g_flops[k] = g_bytes[k] = g_idle[k] = 0.0; }
 }
 
 extern "C" void spaqr_use_graphs(int on) { spaqr::g_graphs.store(on != 0); }
@@ -362,6 +363,9 @@ extern "C" int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t*
     using namespace spaqr;
     if ((cap > 0 && !out) || !count) { set_error("null argument"); return SPAQR_ERR_INVALID_ARG; }
     std::lock_guard<std::mutex> lk(g_mu);
+    // idle gaps: from the end of the previous record on the same stream to
+    // the start of this one
+    std::vector<std::pair<void*, cudaEvent_t>> last;
     for (Rec& r : g_recs) {
         float ms = 0.0f;
         if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
@@ -370,6 +374,19 @@ extern "C" int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t*
             return SPAQR_ERR_CUDA;
         }
         g_ms[r.kind] += ms;
+        cudaEvent_t* prev = nullptr;
+        for (auto& l : last)
+            if (l.first == r.stream) prev = &l.second;
+        if (prev) {
+            float gap = 0.0f;
+            if (cudaEventElapsedTime(&gap, *prev, r.a) == cudaSuccess && gap > 0.0f) g_idle[r.kind] += gap;
+            cudaGetLastError();
+            *prev = r.b;
+        } else {
+            last.push_back({r.stream, r.b});
+        }
+    }
+    for (Rec& r : g_recs) {
         g_pool.push_back(r.a);
         g_pool.push_back(r.b);
     }
@@ -383,6 +400,7 @@ extern "C" int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t*
         out[k].total_ms = g_ms[k];
         out[k].flops = g_flops[k];
         out[k].bytes = g_bytes[k];
+        out[k].idle_ms = g_idle[k];
     }
     return SPAQR_OK;
 }
