@@ -807,6 +807,24 @@ __global__ void __launch_bounds__(NT) k_sparsify(const SparsifyTask<real>* __res
     }
 }
 
+// Merge of a level below the sparsified ones: one CTA per column chunk
+// copies its row segments into the merged panel (one task per chunk instead
+// of one per block keeps the host's planning of the many small blocks of the
+// lower levels short).
+template <class real>
+__global__ void __launch_bounds__(NT) k_merge_copy(const CopyCol<real>* __restrict__ cols,
+                                                   const RowSeg* __restrict__ segs) {
+    const CopyCol<real> t = cols[blockIdx.x];
+    for (int s = 0; s < t.nseg; s++) {
+        const RowSeg g = segs[t.seg_begin + s];
+        const int64_t tot = (int64_t)g.len * t.ncols;
+        for (int64_t o = threadIdx.x; o < tot; o += NT) {
+            const int r = (int)(o % g.len), c = (int)(o / g.len);
+            t.D[(g.dst + r) + (int64_t)c * t.ldd] = t.A[(g.src + r) + (int64_t)c * t.lda];
+        }
+    }
+}
+
 // B <- Q^T B over a column chunk, or B <- B Q over a row chunk (Q^T applied
 // to the transposed view).
 template <class real>
@@ -1353,8 +1371,9 @@ int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std
                 c.m = x.m;
                 c.ncol = (int)sz[j];
                 c.seg_begin = (int)segs.size();
-                for (int i : sp.R[x.f]) {
-                    const int e = sp.find(i, j);
+                const int* ep = sp.apply_e.data() + sp.fcol_ebase[sp.fcol_ptr[x.f] + t - 1];
+                for (size_t u = 0; u < sp.R[x.f].size(); u++) {
+                    const int i = sp.R[x.f][u], e = ep[u];
                     if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
                     if (sz[i] > 0) segs.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
                 }
@@ -1729,12 +1748,15 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 if (k == L - 1) F->top_size = (int)sz[s];
             }
         }
-        // apply: per column j, the fronts containing it (processing order)
-        std::vector<std::vector<int>> fronts_of(ncl);
-        for (size_t f = 0; f < sp.fronts.size(); f++) {
-            if (sz[sp.fronts[f]] == 0) continue;
-            for (size_t t = 1; t < sp.C[f].size(); t++) fronts_of[sp.C[f][t]].push_back((int)f);
+        tstart(0);
+        if (!qr.empty()) {
+            launch_qr<real>(C, qr, esz, KK_FRONT_QR, fl_qr, by_qr);
+            if (C.rc) return C.rc;
+            C.launched();
         }
+        // (the application's tasks are planned while the QR runs)
+        // apply: per column j, the fronts containing it (processing order,
+        // sp.colf_*, with the positions of their row blocks in column j)
         std::vector<ApplyTask<real>> at;
         std::vector<ApplyFront<real>> af;
         std::vector<Seg> asg;
@@ -1759,11 +1781,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             while (qapply > 4 && cols / qapply < 2 * kNumSM) qapply /= 2;
         }
         for (int j = 0; j < ncl; j++) {
-            if (fronts_of[j].empty() || sz[j] == 0) continue;
+            if (sz[j] == 0) continue;
             const int fb = (int)af.size();
             int nmax = 1, mmax = 1;
-            for (int f : fronts_of[j]) {
+            for (int q = sp.colf_ptr[j]; q < sp.colf_ptr[j + 1]; q++) {
+                const int f = sp.colf_front[q];
                 const int s = sp.fronts[f];
+                if (sz[s] == 0) continue;
+                const int* ep = sp.apply_e.data() + sp.colf_ebase[q];
                 ApplyFront<real> A1;
                 A1.V = arena + lay.poff[s];
                 A1.T = fT[f];
@@ -1771,8 +1796,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 A1.m = (int)lay.H[s];
                 A1.n = (int)sz[s];
                 A1.seg_begin = (int)asg.size();
-                for (int i : sp.R[f]) {
-                    const int e = sp.find(i, j);
+                for (size_t t = 0; t < sp.R[f].size(); t++) {
+                    const int i = sp.R[f][t], e = ep[t];
                     if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
                     if (sz[i] > 0) asg.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
                 }
@@ -1785,6 +1810,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 fl_ap += fa;
                 by_ap += 16.0 * A1.m * sz[j] + 8.0 * A1.m * A1.n;
             }
+            const int nfr = (int)af.size() - fb;
+            if (nfr == 0) continue;
             const int q = qapply;
             for (int64_t c0 = 0; c0 < sz[j]; c0 += q) {
                 ApplyTask<real> T1;
@@ -1792,7 +1819,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 T1.ldb = lay.H[j];
                 T1.q = (int)std::min<int64_t>(q, sz[j] - c0);
                 T1.fr_begin = fb;
-                T1.nfr = (int)fronts_of[j].size();
+                T1.nfr = nfr;
                 T1.m_max = mmax;
                 at.push_back(T1);
             }
@@ -1813,12 +1840,6 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
         }
         if (smem_apply > (size_t)kSmemMax) { set_error("front too tall for the apply kernel"); return SPAQR_ERR_UNSUPPORTED; }
-        tstart(0);
-        if (!qr.empty()) {
-            launch_qr<real>(C, qr, esz, KK_FRONT_QR, fl_qr, by_qr);
-            if (C.rc) return C.rc;
-            C.launched();
-        }
         bool tc_done = false;
         if constexpr (sizeof(real) == 4) {
             if (tcmode && !at.empty() && tc_level(sp, lay, sz)) {
@@ -1840,122 +1861,129 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
         }
         tstop(0);
 
-        // solve record of the fronts, grouped by colour
-        LV.front_begin = (int)sfronts.size();
-        LV.colour_ptr.assign(1, 0);
-        {
-            int cur = 0;
-            LV.ff_flops.assign(1, 0.0);
-            LV.ff_fixed.assign(1, 0.0);
-            LV.ff_vec.assign(1, 0.0);
-            for (size_t f = 0; f < sp.fronts.size(); f++) {
-                while (sp.colour[f] > cur) {
-                    LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
-                    LV.ff_flops.push_back(0.0);
-                    LV.ff_fixed.push_back(0.0);
-                    LV.ff_vec.push_back(0.0);
-                    cur++;
+        // solve record of the fronts and the R_sj tiles of the backward step:
+        // host planning that no launch of this level's factorisation needs, so
+        // it runs while the GPU works on the level (before the rank sync)
+        bool front_solve_planned = false;
+        auto plan_front_solve = [&]() {
+            front_solve_planned = true;
+            // solve record of the fronts, grouped by colour
+            LV.front_begin = (int)sfronts.size();
+            LV.colour_ptr.assign(1, 0);
+            {
+                int cur = 0;
+                LV.ff_flops.assign(1, 0.0);
+                LV.ff_fixed.assign(1, 0.0);
+                LV.ff_vec.assign(1, 0.0);
+                for (size_t f = 0; f < sp.fronts.size(); f++) {
+                    while (sp.colour[f] > cur) {
+                        LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
+                        LV.ff_flops.push_back(0.0);
+                        LV.ff_fixed.push_back(0.0);
+                        LV.ff_vec.push_back(0.0);
+                        cur++;
+                    }
+                    const int s = sp.fronts[f];
+                    if (sz[s] == 0) continue;
+                    SolveFront<real> sf;
+                    sf.V = arena + lay.poff[s];
+                    sf.T = fT[f];
+                    sf.Dinv = fD[f];
+                    sf.ldv = lay.H[s];
+                    sf.m = (int)lay.H[s];
+                    sf.n = (int)sz[s];
+                    sf.seg_begin = (int)ssegs.size();
+                    for (int i : sp.R[f])
+                        if (sz[i] > 0) ssegs.push_back(Seg{lay.voff[i], (int)sz[i], 0});
+                    sf.nseg = (int)ssegs.size() - sf.seg_begin;
+                    sf.rsj_begin = (int)srsj.size();
+                    for (size_t t = 1; t < sp.C[f].size(); t++) {
+                        const int j = sp.C[f][t];
+                        if (sz[j] == 0) continue;
+                        const int e = sp.find(s, j);
+                        srsj.push_back(SolveRsj<real>{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
+                        rsj_cl.push_back(sp.cl[j]);
+                        sflops += 2.0 * sz[s] * sz[j];
+                        sbytes += 8 * sz[s] * sz[j];
+                    }
+                    sf.nrsj = (int)srsj.size() - sf.rsj_begin;
+                    {
+                        double snj = 0;
+                        for (int b = sf.rsj_begin; b < (int)srsj.size(); b++) snj += srsj[b].nj;
+                        const double m_ = sf.m, n_ = sf.n;
+                        // applying n reflectors of m rows to one column: 4mn - 2n^2
+                        LV.ff_flops.back() += 4.0 * m_ * n_ - 2.0 * n_ * n_;
+                        LV.ff_fixed.back() += 8.0 * (m_ * n_ + n_ * n_);
+                        LV.ff_vec.back() += 16.0 * m_;
+                        LV.fb_flops += 2.0 * n_ * snj + n_ * n_;
+                        LV.fb_fixed += 8.0 * (n_ * n_ + n_ * snj);
+                        LV.fb_vec += 16.0 * n_ + 8.0 * snj;
+                    }
+                    sfronts.push_back(sf);
+                    front_cl.push_back(sp.cl[s]);
+                    LV.max_front_m = std::max(LV.max_front_m, sf.m);
+                    LV.max_front_n = std::max(LV.max_front_n, sf.n);
+                    sflops += 4.0 * sf.m * sf.n - 2.0 * sf.n * sf.n + 1.0 * sf.n * sf.n;
+                    sbytes += 8 * (int64_t)sf.m * sf.n + 8 * (int64_t)sf.n * sf.n;
                 }
-                const int s = sp.fronts[f];
-                if (sz[s] == 0) continue;
-                SolveFront<real> sf;
-                sf.V = arena + lay.poff[s];
-                sf.T = fT[f];
-                sf.Dinv = fD[f];
-                sf.ldv = lay.H[s];
-                sf.m = (int)lay.H[s];
-                sf.n = (int)sz[s];
-                sf.seg_begin = (int)ssegs.size();
-                for (int i : sp.R[f])
-                    if (sz[i] > 0) ssegs.push_back(Seg{lay.voff[i], (int)sz[i], 0});
-                sf.nseg = (int)ssegs.size() - sf.seg_begin;
-                sf.rsj_begin = (int)srsj.size();
-                for (size_t t = 1; t < sp.C[f].size(); t++) {
-                    const int j = sp.C[f][t];
-                    if (sz[j] == 0) continue;
-                    const int e = sp.find(s, j);
-                    srsj.push_back(SolveRsj<real>{blk(e, j), lay.H[j], (int)sz[j], 0, lay.voff[j]});
-                    rsj_cl.push_back(sp.cl[j]);
-                    sflops += 2.0 * sz[s] * sz[j];
-                    sbytes += 8 * sz[s] * sz[j];
-                }
-                sf.nrsj = (int)srsj.size() - sf.rsj_begin;
-                {
-                    double snj = 0;
-                    for (int b = sf.rsj_begin; b < (int)srsj.size(); b++) snj += srsj[b].nj;
-                    const double m_ = sf.m, n_ = sf.n;
-                    // applying n reflectors of m rows to one column: 4mn - 2n^2
-                    LV.ff_flops.back() += 4.0 * m_ * n_ - 2.0 * n_ * n_;
-                    LV.ff_fixed.back() += 8.0 * (m_ * n_ + n_ * n_);
-                    LV.ff_vec.back() += 16.0 * m_;
-                    LV.fb_flops += 2.0 * n_ * snj + n_ * n_;
-                    LV.fb_fixed += 8.0 * (n_ * n_ + n_ * snj);
-                    LV.fb_vec += 16.0 * n_ + 8.0 * snj;
-                }
-                sfronts.push_back(sf);
-                front_cl.push_back(sp.cl[s]);
-                LV.max_front_m = std::max(LV.max_front_m, sf.m);
-                LV.max_front_n = std::max(LV.max_front_n, sf.n);
-                sflops += 4.0 * sf.m * sf.n - 2.0 * sf.n * sf.n + 1.0 * sf.n * sf.n;
-                sbytes += 8 * (int64_t)sf.m * sf.n + 8 * (int64_t)sf.n * sf.n;
+                LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
+                LV.nfront = (int)sfronts.size() - LV.front_begin;
             }
-            LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
-            LV.nfront = (int)sfronts.size() - LV.front_begin;
-        }
-        // tallest front of every colour (shared-memory size of the staged and
-        // cluster forms of the forward step)
-        LV.ff_maxm.assign(LV.colour_ptr.size() - 1, 0);
-        for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
-            const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
-            int mm = 0;
-            for (int f = a; f < b; f++) mm = std::max(mm, sfronts[LV.front_begin + f].m);
-            LV.ff_maxm[c] = mm;
-        }
-        // R_sj tiles of the backward step, planned for every level
-        LV.bwd_tiles = LV.nfront > 0;
-        if (LV.bwd_tiles) {
-            LV.tile_begin = (int)tiles.size();
-            LV.wf_begin = (int)wfr.size();
-            int64_t zrows = 0;
-            for (int f = LV.front_begin; f < LV.front_begin + LV.nfront; f++) {
-                const SolveFront<real>& sf = sfronts[f];
-                // pieces of R_sj columns filling chunks of kTileK columns
-                std::vector<std::pair<int, int>> chunks;
-                int cw = 0, cb = (int)pieces.size(), cn = 0;
-                for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) {
-                    const SolveRsj<real> R = srsj[b];
-                    for (int u0 = 0; u0 < R.nj;) {
-                        const int w = std::min(R.nj - u0, kTileK - cw);
-                        pieces.push_back(SolveRsj<real>{R.R + (int64_t)u0 * R.ldr, R.ldr, w, 0, R.xoff + u0});
-                        piece_src.push_back({b, u0});
-                        cn++;
-                        cw += w;
-                        u0 += w;
-                        if (cw == kTileK) {
-                            chunks.push_back({cb, cn});
-                            cb = (int)pieces.size();
-                            cn = 0;
-                            cw = 0;
+            // tallest front of every colour (shared-memory size of the staged and
+            // cluster forms of the forward step)
+            LV.ff_maxm.assign(LV.colour_ptr.size() - 1, 0);
+            for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
+                const int a = LV.colour_ptr[c], b = LV.colour_ptr[c + 1];
+                int mm = 0;
+                for (int f = a; f < b; f++) mm = std::max(mm, sfronts[LV.front_begin + f].m);
+                LV.ff_maxm[c] = mm;
+            }
+            // R_sj tiles of the backward step, planned for every level
+            LV.bwd_tiles = LV.nfront > 0;
+            if (LV.bwd_tiles) {
+                LV.tile_begin = (int)tiles.size();
+                LV.wf_begin = (int)wfr.size();
+                int64_t zrows = 0;
+                for (int f = LV.front_begin; f < LV.front_begin + LV.nfront; f++) {
+                    const SolveFront<real>& sf = sfronts[f];
+                    // pieces of R_sj columns filling chunks of kTileK columns
+                    std::vector<std::pair<int, int>> chunks;
+                    int cw = 0, cb = (int)pieces.size(), cn = 0;
+                    for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) {
+                        const SolveRsj<real> R = srsj[b];
+                        for (int u0 = 0; u0 < R.nj;) {
+                            const int w = std::min(R.nj - u0, kTileK - cw);
+                            pieces.push_back(SolveRsj<real>{R.R + (int64_t)u0 * R.ldr, R.ldr, w, 0, R.xoff + u0});
+                            piece_src.push_back({b, u0});
+                            cn++;
+                            cw += w;
+                            u0 += w;
+                            if (cw == kTileK) {
+                                chunks.push_back({cb, cn});
+                                cb = (int)pieces.size();
+                                cn = 0;
+                                cw = 0;
+                            }
                         }
                     }
+                    if (cn > 0) chunks.push_back({cb, cn});
+                    const int nkc = (int)chunks.size();
+                    for (int kc = 0; kc < nkc; kc++)
+                        for (int r0 = 0; r0 < sf.n; r0 += kTileRows)
+                            tiles.push_back(RsjTile{f, r0, std::min(kTileRows, sf.n - r0), chunks[kc].first,
+                                                    chunks[kc].second, kc, zrows});
+                    wfr.push_back(WideFront{f, nkc, zrows});
+                    zrows += (int64_t)nkc * sf.n;
+                    double snj = 0;
+                    for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) snj += srsj[b].nj;
+                    LV.rt_flops += 2.0 * sf.n * snj;
+                    LV.rt_fixed += 8.0 * sf.n * snj;
+                    LV.rt_vec += 8.0 * snj * ((sf.n + kTileRows - 1) / kTileRows) + 8.0 * nkc * sf.n;
                 }
-                if (cn > 0) chunks.push_back({cb, cn});
-                const int nkc = (int)chunks.size();
-                for (int kc = 0; kc < nkc; kc++)
-                    for (int r0 = 0; r0 < sf.n; r0 += kTileRows)
-                        tiles.push_back(RsjTile{f, r0, std::min(kTileRows, sf.n - r0), chunks[kc].first,
-                                                chunks[kc].second, kc, zrows});
-                wfr.push_back(WideFront{f, nkc, zrows});
-                zrows += (int64_t)nkc * sf.n;
-                double snj = 0;
-                for (int b = sf.rsj_begin; b < sf.rsj_begin + sf.nrsj; b++) snj += srsj[b].nj;
-                LV.rt_flops += 2.0 * sf.n * snj;
-                LV.rt_fixed += 8.0 * sf.n * snj;
-                LV.rt_vec += 8.0 * snj * ((sf.n + kTileRows - 1) / kTileRows) + 8.0 * nkc * sf.n;
+                LV.ntile = (int)tiles.size() - LV.tile_begin;
+                zp_max = std::max(zp_max, zrows);
             }
-            LV.ntile = (int)tiles.size() - LV.tile_begin;
-            zp_max = std::max(zp_max, zrows);
-        }
+        };
 
         // ---------------- (ii)/(iii) scale and sparsify ----------------
         std::vector<int> rest;
@@ -2004,11 +2032,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 size_t smem_sc = 16;
                 for (int j : rest) {
                     if (sz[j] == 0) continue;
-                    const int ej = sp.find(j, j);
+                    const int ej = sp.diag[j];
                     for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
                         const int i = sp.rowidx[e];
                         if (i == j || sp.is_front[i] || sz[i] == 0) continue;
-                        const int ei = sp.find(i, i);
+                        const int ei = sp.diag[i];
                         ScaleTask<real> t;
                         t.A = blk(e, j);
                         t.lda = lay.H[j];
@@ -2357,6 +2385,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                              k_cpqr<real><<<(unsigned)cp.size(), NT, smem_cp, st>>>(d1, dgs, opt->eps));
                 C.launched();
             }
+            plan_front_solve();
             // ranks back to the host (the only device->host sync of a level)
             std::vector<int> rk(ncl, 0);
             std::vector<double> rdg(std::max<int64_t>(rtot, 1), 0.0);
@@ -2493,6 +2522,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             DG.max_interface = std::max<int>(DG.max_interface, (int)sz[p]);
         }
 
+        if (!front_solve_planned) plan_front_solve();
+
         // ---------------- (iv) merge into the next level ----------------
         if (k < L - 1) {
             const StepPlan& sn = o.steps[k + 1];
@@ -2510,14 +2541,57 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             tstart(3);
             C.cuda(cudaMemsetAsync(narena, 0, sizeof(real) * nl.total, st));
             std::vector<SparsifyTask<real>> sk;
+            std::vector<std::pair<int, int>> sk_ij;   // (i, j) of every task
+            if (sparsify) sk.reserve(sp.rowidx.size());
             int64_t scr = 0;
             double fl_sp = 0, by_sp = 0;
+            if (!sparsify) {
+                // copies only: per column chunk, its interface row segments
+                // (adjacent ones joined)
+                std::vector<CopyCol<real>> cc;
+                std::vector<RowSeg> cs;
+                constexpr int kCopyCols = 32;
+                for (int j : rest) {
+                    if (sz[j] == 0) continue;
+                    const int J = sp.parent[j];
+                    const int sb = (int)cs.size();
+                    for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                        const int i = sp.rowidx[e];
+                        if (sp.is_front[i] || sz[i] == 0) continue;
+                        const int e2 = sp.merge_e[e];
+                        if (e2 < 0) { set_error("merged block missing"); return SPAQR_ERR_INVALID_ARG; }
+                        const int64_t src = lay.rowoff[e], dst = nl.rowoff[e2] + coff[i];
+                        if ((int)cs.size() > sb && cs.back().src + cs.back().len == src &&
+                            cs.back().dst + cs.back().len == dst)
+                            cs.back().len += (int)sz[i];
+                        else
+                            cs.push_back(RowSeg{src, dst, (int)sz[i], 0});
+                        by_sp += 8.0 * sz[i] * sz[j] + 8.0;
+                    }
+                    const int ns = (int)cs.size() - sb;
+                    if (ns == 0) continue;
+                    const real* A0 = arena + lay.poff[j];
+                    real* D0 = narena + nl.poff[J] + coff[j] * nl.H[J];
+                    for (int64_t c0 = 0; c0 < sz[j]; c0 += kCopyCols)
+                        cc.push_back(CopyCol<real>{A0 + c0 * lay.H[j], lay.H[j], D0 + c0 * nl.H[J], nl.H[J],
+                                                   (int)std::min<int64_t>(kCopyCols, sz[j] - c0), sb, ns, 0});
+                }
+                if (!cc.empty()) {
+                    CopyCol<real>* d = C.upload(cc, false);
+                    RowSeg* dsg = C.upload(cs, false);
+                    if (C.rc) return C.rc;
+                    SPAQR_LAUNCH(KK_SPARSIFY, 0.0, by_sp, st,
+                                 k_merge_copy<real><<<(unsigned)cc.size(), NT, 0, st>>>(d, dsg));
+                    C.launched();
+                }
+            }
             for (int j : rest) {
+                if (!sparsify) break;   // copies above
                 for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
                     const int i = sp.rowidx[e];
                     if (sp.is_front[i]) continue;
                     const int I = sp.parent[i], J = sp.parent[j];
-                    const int e2 = sn.find(I, J);
+                    const int e2 = sp.merge_e[e];
                     if (e2 < 0) { set_error("merged block missing"); return SPAQR_ERR_INVALID_ARG; }
                     SparsifyTask<real> t;
                     std::memset(&t, 0, sizeof(t));
@@ -2527,10 +2601,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     t.nj = (int)sz[j];
                     t.D = narena + nl.poff[J] + nl.rowoff[e2] + coff[i] + coff[j] * nl.H[J];
                     t.ldd = nl.H[J];
-                    if (!sparsify) {
-                        if (sz[i] == 0 || sz[j] == 0) continue;
-                        t.mode = 2;
-                    } else if (i == j && opt->scaling == 0) {
+                    if (i == j && opt->scaling == 0) {
                         // unscaled form: the coarse rows of H_p^T A_pp Q_p[:, 0:r]
                         if (newsz[i] == 0) continue;
                         t.mode = 2;
@@ -2575,6 +2646,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     }
                     by_sp += 8.0 * t.mi * t.nj + 8.0 * std::max(t.ri, 1) * std::max(t.rj, 1);
                     sk.push_back(t);
+                    sk_ij.push_back({i, j});
                 }
             }
             bool tc_sp = false;
@@ -2612,18 +2684,15 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     std::vector<SparsifyTask<real>> rest_tasks;
                     int64_t wo = tot;
                     double fl_t = 0.0;
-                    for (const SparsifyTask<real>& t : sk) {
+                    for (size_t ti = 0; ti < sk.size(); ti++) {
+                        const SparsifyTask<real>& t = sk[ti];
                         if (t.mode != 0) {
                             rest_tasks.push_back(t);
                             continue;
                         }
-                        // the interfaces of this block: Q_i from t.Vi, Q_j from t.Vj
-                        int ii = -1, jj = -1;
-                        for (int q : rest) {
-                            if (qV[q] == t.Vi) ii = q;
-                            if (qV[q] == t.Vj) jj = q;
-                        }
-                        if (ii < 0 || jj < 0 || !tq[ii] || !tq[jj]) {
+                        // the interfaces of this block
+                        const int ii = sk_ij[ti].first, jj = sk_ij[ti].second;
+                        if (!tq[ii] || !tq[jj]) {
                             set_error("sparsification task without its interfaces");
                             return SPAQR_ERR_INVALID_ARG;
                         }

@@ -50,6 +50,53 @@ int num_levels(int64_t n) {
     return L < 1 ? 1 : L;
 }
 
+// The lookups of StepPlan that a factorisation needs, from the pattern.
+static void index_plan(Ordering& o) {
+    for (size_t k = 0; k < o.steps.size(); k++) {
+        StepPlan& sp = o.steps[k];
+        const int ncl = (int)sp.cl.size();
+        sp.diag.assign(ncl, -1);
+        for (int j = 0; j < ncl; j++) sp.diag[j] = sp.find(j, j);
+        sp.colf_ptr.assign(ncl + 1, 0);
+        for (size_t f = 0; f < sp.fronts.size(); f++)
+            for (size_t t = 1; t < sp.C[f].size(); t++) sp.colf_ptr[sp.C[f][t] + 1]++;
+        for (int j = 0; j < ncl; j++) sp.colf_ptr[j + 1] += sp.colf_ptr[j];
+        sp.colf_front.assign(sp.colf_ptr[ncl], 0);
+        sp.colf_ebase.assign(sp.colf_ptr[ncl], 0);
+        std::vector<int> fill(sp.colf_ptr.begin(), sp.colf_ptr.end() - 1);
+        std::vector<int> slot;   // (f, t) in front order -> position in colf
+        sp.fcol_ptr.assign(sp.fronts.size() + 1, 0);
+        for (size_t f = 0; f < sp.fronts.size(); f++) {
+            for (size_t t = 1; t < sp.C[f].size(); t++) {
+                const int q = fill[sp.C[f][t]]++;
+                sp.colf_front[q] = (int)f;
+                slot.push_back(q);
+            }
+            sp.fcol_ptr[f + 1] = (int)slot.size();
+        }
+        sp.apply_e.clear();
+        for (int j = 0; j < ncl; j++)
+            for (int q = sp.colf_ptr[j]; q < sp.colf_ptr[j + 1]; q++) {
+                sp.colf_ebase[q] = (int)sp.apply_e.size();
+                for (int i : sp.R[sp.colf_front[q]]) sp.apply_e.push_back(sp.find(i, j));
+            }
+        sp.fcol_ebase.assign(slot.size(), 0);
+        for (size_t u = 0; u < slot.size(); u++) sp.fcol_ebase[u] = sp.colf_ebase[slot[u]];
+        sp.merge_e.assign(sp.rowidx.size(), -1);
+        if (k + 1 < o.steps.size() && !sp.parent.empty()) {
+            const StepPlan& sn = o.steps[k + 1];
+            for (int j = 0; j < ncl; j++) {
+                if (sp.is_front[j] || sp.parent[j] < 0) continue;
+                for (int e = sp.colptr[j]; e < sp.colptr[j + 1]; e++) {
+                    const int i = sp.rowidx[e];
+                    if (sp.is_front[i] || sp.parent[i] < 0) continue;
+                    sp.merge_e[e] = sn.find(sp.parent[i], sp.parent[j]);
+                }
+            }
+        }
+    }
+}
+
 int StepPlan::find(int i, int j) const {
     auto b = rowidx.begin() + colptr[j], e = rowidx.begin() + colptr[j + 1];
     auto it = std::lower_bound(b, e, i);
@@ -497,6 +544,7 @@ int plan_forest(Ordering& o, const int64_t* rowptr, const int32_t* colind,
         o.steps.push_back(std::move(sp));
     }
     if (!active.empty() || !P.empty()) { set_error("plan left active clusters"); return SPAQR_ERR_INVALID_ARG; }
+    index_plan(o);
 
     // ---- gather map into the level-1 arena --------------------------------
     {

@@ -41,6 +41,20 @@ struct StepPlan {
     int n_next = 0;
     // position of block (i, j) within the CSC arrays: lookup helper
     int find(int i, int j) const;
+    // Lookups derived from the pattern once per ordering (index_plan), so
+    // that a factorisation does not search for blocks:
+    //  diag[j]: position of block (j, j) (-1 if absent);
+    //  per column j, the fronts applied to it in processing order
+    //  (colf_front[colf_ptr[j] ..]), each with apply_e[colf_ebase[..] + t] =
+    //  position of block (R(s)[t], j) (-1 if absent);
+    //  the same bases per front and column C(s)[t], t >= 1:
+    //  fcol_ebase[fcol_ptr[f] + t - 1];
+    //  merge_e[e]: for a block (i, j) of two non-front clusters, the position
+    //  of block (parent[i], parent[j]) in the next level (-1 otherwise).
+    std::vector<int> diag;
+    std::vector<int> colf_ptr, colf_front, colf_ebase, apply_e;
+    std::vector<int> fcol_ptr, fcol_ebase;
+    std::vector<int> merge_e;
 };
 
 struct Ordering {

@@ -77,6 +77,25 @@ struct ScalePiece {
     int off, len;
 };
 
+// Merge of a level that is not sparsified (Section 2.6): the interface rows
+// of a chunk of columns of one column panel are copied into the merged
+// panel of the next level, row segment by row segment.
+template <class real>
+struct CopyCol {
+    const real* A;    // first column of the chunk in the level's panel
+    int64_t lda;
+    real* D;          // the same column in the merged panel
+    int64_t ldd;
+    int ncols;
+    int seg_begin, nseg;
+    int pad;
+};
+struct RowSeg {
+    int64_t src, dst;   // first row in the panel / in the merged panel
+    int len;
+    int pad;
+};
+
 // Column segment of M_p = [A_{k p}^T ... | A_{p j} ...] (Section 2.5).
 template <class real>
 struct GatherSeg {
