@@ -514,6 +514,23 @@ int spaqr_stats(spaqr_kernel_stat* out, int cap, int* count, int64_t* total_laun
 #define SPAQR_PEAK_TF32 3
 int spaqr_peak(int which, int reps, double* flops, double* ms);
 
+/* Latency microbenchmark: clock cycles per operation of a dependent chain,
+ * in one CTA of `warps` warps (1..32) with the operation in lanes
+ * 0..lanes-1 (1..32) of every warp; *cycles = the slowest warp's cycles per
+ * operation.  op: SPAQR_OP_DFMA, SPAQR_OP_DADD, SPAQR_OP_DDIV,
+ * SPAQR_OP_DSQRT (with one FP64 add), SPAQR_OP_FFMA, SPAQR_OP_F2F
+ * (double -> float -> double and one FP64 add), SPAQR_OP_DSEL (FP64 compare,
+ * then a multiply or an add).  Synchronous on the current device.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+#define SPAQR_OP_DFMA 0
+#define SPAQR_OP_DADD 1
+#define SPAQR_OP_DDIV 2
+#define SPAQR_OP_DSQRT 3
+#define SPAQR_OP_FFMA 4
+#define SPAQR_OP_F2F 5
+#define SPAQR_OP_DSEL 6
+int spaqr_op_cycles(int op, int warps, int lanes, double* cycles);
+
 /* Self-check of the tcgen05 TF32 tile the mixed-precision factorisation
  * builds on: D (128 x N, row-major) = A (128 x K, row-major) B^T (B: N x K,
  * row-major), inputs rounded to TF32, FP32 accumulation.  Device pointers;

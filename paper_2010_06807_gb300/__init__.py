@@ -122,7 +122,7 @@ EXPORTS = [
     "spaqr_factor_info", "spaqr_factor_ranks", "spaqr_factor_sigmas", "spaqr_factor_level", "spaqr_factor_pivots",
     "spaqr_factor_destroy", "spaqr_stats_reset",
     "spaqr_profile", "spaqr_stats", "spaqr_use_graphs", "spaqr_autotune", "spaqr_factor_tuning",
-    "spaqr_test_fail_alloc", "spaqr_factor_nblocks", "spaqr_factor_block", "spaqr_peak", "spaqr_tc_tile_check",
+    "spaqr_test_fail_alloc", "spaqr_factor_nblocks", "spaqr_factor_block", "spaqr_peak", "spaqr_op_cycles", "spaqr_tc_tile_check",
     "spaqr_tc_gemm", "spaqr_use_tensor_cores",
 ]
 
@@ -185,6 +185,7 @@ def load_library(path=None):
                                     ctypes.POINTER(ctypes.c_int64)]
     if hasattr(lib, "spaqr_peak"):
         lib.spaqr_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.spaqr_op_cycles.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         lib.spaqr_tc_tile_check.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.spaqr_tc_gemm.argtypes = [i32, i32, i32, ctypes.c_float, vp, i64, i64, i32, vp, i64, i64,
                                       ctypes.c_float, vp, i64, i64, i32, vp]
@@ -711,6 +712,18 @@ def spaqr_stats():
 
 
 PEAKS = {"dfma": 0, "dmma": 1, "ffma": 2, "tf32": 3}
+
+
+OPS = {"dfma": 0, "dadd": 1, "ddiv": 2, "dsqrt": 3, "ffma": 4, "f2f": 5, "dsel": 6}
+
+
+def spaqr_op_cycles(op, warps=1, lanes=32):
+    """Clock cycles per operation of a dependent chain of `op` (a key of OPS)
+    in one CTA of `warps` warps, `lanes` active lanes each (slowest warp)."""
+    load_library()
+    c = ctypes.c_double(0.0)
+    _check(_lib.spaqr_op_cycles(OPS[op], int(warps), int(lanes), ctypes.byref(c)))
+    return c.value
 
 
 def spaqr_peak(which, reps=10):

@@ -1213,6 +1213,32 @@ const int kTcMinN = 48;    // reflectors of a front from which its application i
 const int kTcMinM = 256;   // and rows
 const int kPanelSmem = 112 * 1024;   // QR with a staged panel: two CTAs per SM
 
+// Heaviest first: independent tasks (or pieces) reordered by their work in
+// power-of-two classes, largest class first.  The block scheduler issues a
+// launch's CTAs roughly in index order, so the long ones start first and the
+// launch ends with short ones (the longest-processing-time rule); ncu showed
+// the SMs of a 2D application launch busy only 57% of its time, the rest a
+// tail of long CTAs.  Linear time, order kept within a class.
+template <class T, class W>
+void heaviest_first(std::vector<T>& v, W work) {
+    if (v.size() < 2) return;
+    constexpr int kClasses = 64;
+    std::vector<unsigned char> cls(v.size());
+    int cnt[kClasses + 1] = {0};
+    for (size_t i = 0; i < v.size(); i++) {
+        const double w = work(v[i]);
+        int e = 0;
+        if (w >= 1.0) std::frexp(w, &e);
+        e = std::min(std::max(e, 0), kClasses - 1);
+        cls[i] = (unsigned char)(kClasses - 1 - e);   // heavier -> smaller class index
+        cnt[cls[i] + 1]++;
+    }
+    for (int c = 0; c < kClasses; c++) cnt[c + 1] += cnt[c];
+    std::vector<T> out(v.size());
+    for (size_t i = 0; i < v.size(); i++) out[cnt[cls[i]]++] = v[i];
+    v.swap(out);
+}
+
 }  // namespace
 
 // Launch the QR tasks: small ones on one CTA each (k_qr), large ones on a
@@ -1231,6 +1257,12 @@ void launch_qr(Ctx& C, const std::vector<QRTask<real>>& all, size_t esz, int kin
             pr_s = std::max(pr_s, q1.m);
         }
     }
+    auto qr_work = [](const QRTask<real>& q1) {
+        const double t = q1.m < q1.n ? q1.m : q1.n;
+        return (double)q1.m * q1.n * t;
+    };
+    heaviest_first(small, qr_work);
+    heaviest_first(big, qr_work);
     if (qr_smem_bytes((int)esz, QC, pr_s) > kPanelSmem) pr_s = 0;
     if (qr_smem_bytes((int)esz, QC, pr_b) > kPanelSmem) pr_b = 0;
     cudaStream_t st = C.st;
@@ -1851,6 +1883,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
             }
         }
         if (!at.empty() && !tc_done) {
+            heaviest_first(at, [&](const ApplyTask<real>& T1) {
+                double w = 0.0;
+                for (int f = T1.fr_begin; f < T1.fr_begin + T1.nfr; f++) w += (double)af[f].m * af[f].n;
+                return w * T1.q;
+            });
             ApplyTask<real>* d1 = C.upload(at, false);
             ApplyFront<real>* d2 = C.upload(af, false);
             Seg* d3 = C.upload(asg, false);
@@ -2073,6 +2110,8 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                         for (int c0 = 0; c0 < sc[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sc[t].nj - c0)});
                         for (int r0 = 0; r0 < sc[t].mi; r0 += 64) pr.push_back({t, r0, std::min(64, sc[t].mi - r0)});
                     }
+                    heaviest_first(pl, [&](const ScalePiece& c) { return (double)sc[c.task].mi * sc[c.task].mi * c.len; });
+                    heaviest_first(pr, [&](const ScalePiece& c) { return (double)sc[c.task].nj * sc[c.task].nj * c.len; });
                     ScaleTask<real>* d = C.upload(sc, false);
                     ScalePiece* dl = C.upload(pl, false);
                     ScalePiece* dr = C.upload(pr, false);
@@ -2370,6 +2409,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 if (C.rc) return C.rc;
             }
             if (!cpb.empty()) {
+                heaviest_first(cpb, [](const CPQRTask<real>& t) { return (double)t.np * t.ncols * t.kmax; });
                 CPQRTask<real>* d1 = C.upload(cpb, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
@@ -2379,6 +2419,7 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 by_cp = 0.0;   // M_p's bytes are counted once per level
             }
             if (!cp.empty()) {
+                heaviest_first(cp, [](const CPQRTask<real>& t) { return (double)t.np * t.ncols * t.kmax; });
                 CPQRTask<real>* d1 = C.upload(cp, false);
                 if (C.rc) return C.rc;
                 SPAQR_LAUNCH(KK_CPQR, 0.0, by_cp, st,
@@ -2763,6 +2804,11 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     for (int c0 = 0; c0 < sk[t].nj; c0 += QC) pl.push_back({t, c0, std::min(QC, sk[t].nj - c0)});
                     for (int r0 = 0; r0 < sk[t].ri; r0 += 32) pr.push_back({t, r0, std::min(32, sk[t].ri - r0)});
                 }
+                heaviest_first(pl, [&](const ScalePiece& c) {
+                    const SparsifyTask<real>& t = sk[c.task];
+                    return t.mode == 0 ? (double)t.li * t.mi * c.len : (double)t.mi * t.nj / 16.0;
+                });
+                heaviest_first(pr, [&](const ScalePiece& c) { return (double)sk[c.task].rj * sk[c.task].nj * c.len; });
                 SparsifyTask<real>* d = C.upload(sk, false);
                 ScalePiece* dl = C.upload(pl, false);
                 ScalePiece* dr = C.upload(pr, false);

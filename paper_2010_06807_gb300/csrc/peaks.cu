@@ -179,10 +179,73 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
+// Latency of one kind of operation in a dependent chain, per warp: each
+// of the CTA's warps runs `iters` dependent operations in its lanes below
+// `lanes` and records its clock cycles.  The FP64 rows show what the FP64
+// kernels are designed around (an FP64 instruction costs the same pipe time
+// whatever its active lanes, and its latency is tens of cycles).
+__global__ void k_op_chain(int op, int iters, int lanes, double a, double b, double* out, long long* cyc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double x = 1.0 + threadIdx.x * 1e-3;
+    float xf = (float)x;
+    __syncwarp();
+    const long long t0 = clock64();
+    if (lane < lanes) {
+        switch (op) {
+            case 0: for (int i = 0; i < iters; i++) x = fma(x, a, b); break;
+            case 1: for (int i = 0; i < iters; i++) x = x + b; break;
+            case 2: for (int i = 0; i < iters; i++) x = a / x; break;
+            case 3: for (int i = 0; i < iters; i++) x = sqrt(x + a); break;
+            case 4: for (int i = 0; i < iters; i++) xf = fmaf(xf, (float)a, (float)b); break;
+            case 5: for (int i = 0; i < iters; i++) x = (double)(float)x + b; break;
+            default: for (int i = 0; i < iters; i++) x = x > b ? x * a : x + a; break;
+        }
+    }
+    __syncwarp();
+    const long long t1 = clock64();
+    if (lane == 0) cyc[w] = t1 - t0;
+    out[threadIdx.x] = x + xf;
+}
+
 }  // namespace
 }  // namespace spaqr
 
 using namespace spaqr;
+
+extern "C" int spaqr_op_cycles(int op, int warps, int lanes, double* cycles) {
+    if (op < 0 || op > 6 || warps < 1 || warps > 32 || lanes < 1 || lanes > 32 || !cycles) {
+        set_error("need 0 <= op <= 6, 1 <= warps <= 32, 1 <= lanes <= 32 and an output");
+        return SPAQR_ERR_INVALID_ARG;
+    }
+    double* out = nullptr;
+    long long* cyc = nullptr;
+    if (cudaMalloc(&out, 1024 * sizeof(double)) != cudaSuccess || cudaMalloc(&cyc, 32 * sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (out) cudaFree(out);
+        set_error("device allocation failed");
+        return SPAQR_ERR_OOM;
+    }
+    const int iters = 2048;
+    long long h[32] = {0};
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {   // the first run warms up
+        k_op_chain<<<1, 32 * warps>>>(op, iters, lanes, 0.999999, 1e-7, out, cyc);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, cyc, warps * sizeof(long long), cudaMemcpyDeviceToHost);
+    cudaFree(out);
+    cudaFree(cyc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("CUDA: ") + cudaGetErrorString(e));
+        return SPAQR_ERR_CUDA;
+    }
+    long long mx = 0;
+    for (int i = 0; i < warps; i++) mx = h[i] > mx ? h[i] : mx;
+    *cycles = (double)mx / iters;
+    return SPAQR_OK;
+}
 
 extern "C" int spaqr_peak(int which, int reps, double* flops, double* ms) {
     if (which < 0 || which > 3 || reps < 1 || !flops || !ms) { set_error("bad argument"); return SPAQR_ERR_INVALID_ARG; }

@@ -61,6 +61,24 @@ def test_peaks_plausible(dev):
     assert rates["tf32"] > rates["ffma"]
 
 
+def test_op_cycles_fp64_cost_model(dev):
+    """The FP64 cost model the kernels are designed around: a dependent FP64
+    operation takes several times an FP32 one, its cost does not depend on
+    how many lanes are active, and division and square root take several
+    FMAs' time."""
+    dfma1 = sq.spaqr_op_cycles("dfma", 1, 1)
+    dfma32 = sq.spaqr_op_cycles("dfma", 1, 32)
+    ffma = sq.spaqr_op_cycles("ffma", 1, 32)
+    assert 0 < ffma < dfma32 / 4
+    assert abs(dfma1 - dfma32) <= 0.1 * dfma32
+    assert sq.spaqr_op_cycles("ddiv", 1, 32) > 4 * dfma32
+    assert sq.spaqr_op_cycles("dsqrt", 1, 32) > 4 * dfma32
+    # eight warps share the SM's FP64 pipe: each waits longer per operation
+    assert sq.spaqr_op_cycles("dfma", 8, 32) > 1.5 * dfma32
+    with pytest.raises(sq.SpaqrError):
+        sq._check(sq._lib.spaqr_op_cycles(7, 1, 1, None))
+
+
 def _refl(P):
     """Unit lower trapezoidal reflector matrix of a stored panel."""
     V = np.tril(P, -1)
