@@ -1965,6 +1965,25 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 }
                 LV.colour_ptr.push_back((int)sfronts.size() - LV.front_begin);
                 LV.nfront = (int)sfronts.size() - LV.front_begin;
+                // within a colour (disjoint rows, any order), the heaviest
+                // fronts first: the application's launches issue them first
+                for (size_t c = 0; c + 1 < LV.colour_ptr.size(); c++) {
+                    const int a = LV.front_begin + LV.colour_ptr[c], b = LV.front_begin + LV.colour_ptr[c + 1];
+                    if (b - a < 2) continue;
+                    std::vector<int> idx(b - a);
+                    for (int u = 0; u < b - a; u++) idx[u] = a + u;
+                    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+                        return (int64_t)sfronts[x].m * sfronts[x].n > (int64_t)sfronts[y].m * sfronts[y].n;
+                    });
+                    std::vector<SolveFront<real>> sf2(b - a);
+                    std::vector<int> cl2(b - a);
+                    for (int u = 0; u < b - a; u++) {
+                        sf2[u] = sfronts[idx[u]];
+                        cl2[u] = front_cl[idx[u]];
+                    }
+                    std::copy(sf2.begin(), sf2.end(), sfronts.begin() + a);
+                    std::copy(cl2.begin(), cl2.end(), front_cl.begin() + a);
+                }
             }
             // tallest front of every colour (shared-memory size of the staged and
             // cluster forms of the forward step)
