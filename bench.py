@@ -362,6 +362,15 @@ def _profiled_kinds(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, passe
     return ks
 
 
+def _snapshot(torch, X, st):
+    """A host copy of X taken on the stream that wrote it (a device clone on
+    another stream could run after later work on `st` has overwritten X)."""
+    with torch.cuda.stream(st):
+        Xc = X.clone()
+    st.synchronize()
+    return Xc.cpu()
+
+
 def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, warmup, scaling=1):
     """Time `steps` factor + GMRES steps of one form (after `warmup` untimed ones)
     with CUDA events on `st`, L2 flushed between steps."""
@@ -394,7 +403,7 @@ def _timed_form(sq, torch, ordl, A, Bd, Xd, st, flush, eps, precision, steps, wa
             "gmres_ms_p50": _pct(gm, 50), "step_ms_p50": _pct(tot, 50), "gmres_iters_max": max(iters),
             "relres_max": float(rr.max()), "rank_sum": info["rank_sum"], "size_sum": info["size_sum"],
             "factor_mbytes": info["factor_bytes"] / 2 ** 20, "factor_gflop": info["factor_flops"] / 1e9,
-            "tensor_core_levels": info["tc_levels"]}, X.clone()
+            "tensor_core_levels": info["tc_levels"]}, _snapshot(torch, X, st)
 
 
 def _high_contrast(sq, torch, np, dev, st, flush):

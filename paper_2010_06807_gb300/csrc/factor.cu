@@ -2037,6 +2037,15 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     LV.rt_vec += 8.0 * snj * ((sf.n + kTileRows - 1) / kTileRows) + 8.0 * nkc * sf.n;
                 }
                 LV.ntile = (int)tiles.size() - LV.tile_begin;
+                // heaviest tiles first (rows x columns of their chunk)
+                std::stable_sort(tiles.begin() + LV.tile_begin, tiles.end(), [&](const RsjTile& x, const RsjTile& y) {
+                    auto w = [&](const RsjTile& t) {
+                        int64_t c = 0;
+                        for (int q = t.piece_begin; q < t.piece_begin + t.npiece; q++) c += pieces[q].nj;
+                        return (int64_t)t.nrows * c;
+                    };
+                    return w(x) > w(y);
+                });
                 zp_max = std::max(zp_max, zrows);
             }
         };
@@ -2899,6 +2908,23 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 LV.max_ss_r = std::max(LV.max_ss_r, s.r);
             }
             LV.nss = (int)sss.size() - LV.ss_begin;
+            {
+                // heaviest interfaces first (disjoint rows: any order)
+                const int a = LV.ss_begin, b = (int)sss.size();
+                std::vector<int> idx(b - a);
+                for (int u = 0; u < b - a; u++) idx[u] = a + u;
+                std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+                    return (int64_t)sss[x].np * sss[x].np > (int64_t)sss[y].np * sss[y].np;
+                });
+                std::vector<SolveSS<real>> s2(b - a);
+                std::vector<int> c2(b - a);
+                for (int u = 0; u < b - a; u++) {
+                    s2[u] = sss[idx[u]];
+                    c2[u] = ss_cl[idx[u]];
+                }
+                std::copy(s2.begin(), s2.end(), sss.begin() + a);
+                std::copy(c2.begin(), c2.end(), ss_cl.begin() + a);
+            }
             compact_level(k, arena, piece_begin);
             if (C.rc) return C.rc;
             DG.factor_bytes = F->bytes;
