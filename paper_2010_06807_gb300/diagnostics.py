@@ -133,8 +133,10 @@ def factor_problem(p, eps, scaling=1, precision="fp64", skip=2, device=None):
     return o, F, A, e0.elapsed_time(e1)
 
 
-def scaling_study(kind, sizes, eps, scaling=1, precision="fp64", gmres=True, device=None):
-    """Factor time, device memory, ranks and GMRES iterations per grid side."""
+def scaling_study(kind, sizes, eps, scaling=1, precision="fp64", gmres=True, device=None, apply_rhs=0):
+    """Factor time, device memory, ranks and GMRES iterations per grid side;
+    with apply_rhs > 0 also the time of one application of the factor to that
+    many right-hand sides (spaqr_solve; the first application warms up)."""
     import torch
     from synth.convdiff import config_problem, rhs
     dev = device or torch.device("cuda:0")
@@ -150,6 +152,16 @@ def scaling_study(kind, sizes, eps, scaling=1, precision="fp64", gmres=True, dev
                "factor_bytes": info["factor_bytes"], "bytes_per_unknown": info["factor_bytes"] / p.n,
                "top_separator": info["top_size"], "rank_sum": info["rank_sum"], "size_sum": info["size_sum"],
                "phase_ms": dict(zip(PHASES, info["phase_ms"])), "levels_detail": level_report(F)}
+        if apply_rhs > 0:
+            Bq = torch.from_numpy(np.ascontiguousarray(rhs(p, apply_rhs).T)).to(dev).T
+            sq.spaqr_solve(F, Bq)
+            st = torch.cuda.current_stream(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sq.spaqr_solve(F, Bq)
+            e1.record(st)
+            e1.synchronize()
+            row.update(apply_rhs=apply_rhs, apply_ms=e0.elapsed_time(e1))
         if gmres:
             b = torch.from_numpy(np.ascontiguousarray(rhs(p, 1).T)).to(dev).T
             t0 = time.perf_counter()
@@ -172,6 +184,10 @@ def markdown(study, title):
         lines.append(f"| {r['n_side']} | {r['N']} | {r['levels']} | {r['factor_ms']:.1f} | "
                      f"{r['factor_bytes'] / 2 ** 20:.0f} | {r['bytes_per_unknown']:.0f} | {r['top_separator']} | "
                      f"{r['rank_sum']} / {r['size_sum']} | {r.get('gmres_iters', '')} |")
+    for r in study:
+        if r.get("apply_ms") is not None:
+            lines.append(f"\nside {r['n_side']}: one application to {r['apply_rhs']} right-hand sides "
+                         f"{r['apply_ms']:.2f} ms")
     hist = [r for r in study if r.get("gmres_history")]
     if hist:
         lines += ["", "GMRES residual estimates ||b - A x_j|| / ||b|| (iterations 1, 2, ...):", ""]
@@ -200,6 +216,8 @@ def main(argv=None):
     ap.add_argument("--scaling", type=int, default=1)
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--apply-rhs", type=int, default=0, metavar="N",
+                    help="also time one application of the factor to N right-hand sides")
     ap.add_argument("--json")
     ap.add_argument("--plan-only", action="store_true",
                     help="host only: the symbolic plan of each size's ordering, no factorisation")
@@ -227,7 +245,8 @@ def main(argv=None):
             with open(a.json, "w") as f:
                 json.dump(reps, f, indent=1)
         return 0
-    study = scaling_study(a.kind, a.sizes, a.eps, a.scaling, a.precision, gmres=not a.no_gmres)
+    study = scaling_study(a.kind, a.sizes, a.eps, a.scaling, a.precision, gmres=not a.no_gmres,
+                          apply_rhs=a.apply_rhs)
     if a.json:
         with open(a.json, "w") as f:
             json.dump(study, f, indent=1)
