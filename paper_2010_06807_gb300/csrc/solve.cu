@@ -487,20 +487,38 @@ __global__ void __launch_bounds__(NT) k_rsj_tiles(const RsjTile* __restrict__ ti
                                                   const SolveFront<real>* __restrict__ fr, const real* __restrict__ Y,
                                                   int64_t ldy, real* __restrict__ Zp, int64_t ldz, int nrhs, int qs) {
     __shared__ real xs[kTileK * kTileQ];
+    __shared__ const real* colp[kTileK];   // R column of every column of the chunk (tile row 0)
+    __shared__ int64_t colx[kTileK];       // its rows in the level vector
+    __shared__ int pnj[kTileK];            // columns of every piece (npiece <= kTileK)
     constexpr int G = NT / kTileRows;
     constexpr int U = 8;
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const RsjTile t = tiles[blockIdx.x];
     const int n = fr[t.front].n;
-    int koff = 0;
-    for (int p = 0; p < t.npiece; p++) {
-        const SolveRsj<real> P = pieces[t.piece_begin + p];
-        for (int o = threadIdx.x; o < P.nj * qn; o += NT) {
-            const int u = o % P.nj, c = o / P.nj;
-            cp_async_elem(xs + koff + u + c * kTileK, Y + P.xoff + u + (int64_t)(c0 + c) * ldy);
+    // the pieces' descriptors are read in parallel (not one after the other
+    // by every thread), then every column of the chunk gets its R column and
+    // its rows of x in shared memory
+    SolveRsj<real> P{};
+    if ((int)threadIdx.x < t.npiece) {
+        P = pieces[t.piece_begin + threadIdx.x];
+        pnj[threadIdx.x] = P.nj;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < t.npiece) {
+        int koff = 0;
+        for (int q = 0; q < (int)threadIdx.x; q++) koff += pnj[q];
+        for (int u = 0; u < P.nj; u++) {
+            colp[koff + u] = P.R + (int64_t)u * P.ldr + t.row0;
+            colx[koff + u] = P.xoff + u;
         }
-        koff += P.nj;
+    }
+    __syncthreads();
+    int K = 0;
+    for (int q = 0; q < t.npiece; q++) K += pnj[q];
+    for (int o = threadIdx.x; o < K * qn; o += NT) {
+        const int u = o % K, c = o / K;
+        cp_async_elem(xs + u + c * kTileK, Y + colx[u] + (int64_t)(c0 + c) * ldy);
     }
     cp_async_commit();
     const int r = threadIdx.x % kTileRows, g = threadIdx.x / kTileRows;
@@ -510,31 +528,26 @@ __global__ void __launch_bounds__(NT) k_rsj_tiles(const RsjTile* __restrict__ ti
     cp_async_wait<0>();
     __syncthreads();
     if (r < t.nrows) {
-        koff = 0;
-        for (int p = 0; p < t.npiece; p++) {
-            const SolveRsj<real> P = pieces[t.piece_begin + p];
-            const real* Rr = P.R + (t.row0 + r);
-            int u = g;
-            for (; u + (U - 1) * G < P.nj; u += U * G) {
-                real v[U];
+        // the chunk's columns with stride G, eight loads of R in flight
+        int u = g;
+        for (; u + (U - 1) * G < K; u += U * G) {
+            real v[U];
 #pragma unroll
-                for (int k = 0; k < U; k++) v[k] = Rr[(int64_t)(u + k * G) * P.ldr];
+            for (int k = 0; k < U; k++) v[k] = colp[u + k * G][r];
 #pragma unroll
-                for (int k = 0; k < U; k++) {
-                    const real* xu = xs + koff + u + k * G;
-#pragma unroll
-                    for (int c = 0; c < Q; c++)
-                        if (c < qn) acc[c] += v[k] * xu[c * kTileK];
-                }
-            }
-            for (; u < P.nj; u += G) {
-                const real v = Rr[(int64_t)u * P.ldr];
-                const real* xu = xs + koff + u;
+            for (int k = 0; k < U; k++) {
+                const real* xu = xs + u + k * G;
 #pragma unroll
                 for (int c = 0; c < Q; c++)
-                    if (c < qn) acc[c] += v * xu[c * kTileK];
+                    if (c < qn) acc[c] += v[k] * xu[c * kTileK];
             }
-            koff += P.nj;
+        }
+        for (; u < K; u += G) {
+            const real v = colp[u][r];
+            const real* xu = xs + u;
+#pragma unroll
+            for (int c = 0; c < Q; c++)
+                if (c < qn) acc[c] += v * xu[c * kTileK];
         }
     }
     __syncthreads();
