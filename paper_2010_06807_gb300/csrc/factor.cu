@@ -325,11 +325,11 @@ __global__ void __launch_bounds__(NT) k_front_apply(const ApplyTask<real>* __res
     const ApplyTask<real> t = tasks[blockIdx.x];
     for (int f = 0; f < t.nfr; f++) {
         const ApplyFront<real> F = fronts[t.fr_begin + f];
-        int pos = 0;
-        for (int s = 0; s < F.nseg; s++) {
+        // a segment per thread: its descriptor is one load, not one of a
+        // chain of loads every thread would wait for in turn
+        for (int s = threadIdx.x; s < F.nseg; s += NT) {
             const Seg g = segs[F.seg_begin + s];
-            for (int r = threadIdx.x; r < g.len; r += NT) rmap[pos + r] = (int)(g.off + r);
-            pos += g.len;
+            for (int r = 0; r < g.len; r++) rmap[g.pos + r] = (int)(g.off + r);
         }
         __syncthreads();
         const Mat<real> B{t.B, 1, t.ldb, rmap};
@@ -370,11 +370,9 @@ __global__ void __launch_bounds__(NT) k_front_copy(const FrontCopy* __restrict__
     const int c0 = (int)blockIdx.y * kCopyCols;
     if (c0 >= c.ncol) return;
     const int c1 = min(c.ncol, c0 + kCopyCols);
-    int pos = 0;
-    for (int s = 0; s < c.nseg; s++) {
+    for (int s = threadIdx.x; s < c.nseg; s += NT) {   // a segment per thread
         const Seg g = segs[c.seg_begin + s];
-        for (int r = threadIdx.x; r < g.len; r += NT) rmap_sm[pos + r] = (int)(g.off + r);
-        pos += g.len;
+        for (int r = 0; r < g.len; r++) rmap_sm[g.pos + r] = (int)(g.off + r);
     }
     __syncthreads();
     for (int col = c0; col < c1; col++) {
@@ -1404,10 +1402,14 @@ int tc_front_apply(Ctx& C, const StepPlan& sp, const LevelLayout& lay, const std
                 c.ncol = (int)sz[j];
                 c.seg_begin = (int)segs.size();
                 const int* ep = sp.apply_e.data() + sp.fcol_ebase[sp.fcol_ptr[x.f] + t - 1];
+                int spos = 0;
                 for (size_t u = 0; u < sp.R[x.f].size(); u++) {
                     const int i = sp.R[x.f][u], e = ep[u];
                     if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
-                    if (sz[i] > 0) segs.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
+                    if (sz[i] > 0) {
+                        segs.push_back(Seg{lay.rowoff[e], (int)sz[i], spos});
+                        spos += (int)sz[i];
+                    }
                 }
                 c.nseg = (int)segs.size() - c.seg_begin;
                 cp.push_back(c);
@@ -1828,10 +1830,14 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                 A1.m = (int)lay.H[s];
                 A1.n = (int)sz[s];
                 A1.seg_begin = (int)asg.size();
+                int spos = 0;
                 for (size_t t = 0; t < sp.R[f].size(); t++) {
                     const int i = sp.R[f][t], e = ep[t];
                     if (e < 0) { set_error("missing fill block"); return SPAQR_ERR_INVALID_ARG; }
-                    if (sz[i] > 0) asg.push_back(Seg{lay.rowoff[e], (int)sz[i], 0});
+                    if (sz[i] > 0) {
+                        asg.push_back(Seg{lay.rowoff[e], (int)sz[i], spos});
+                        spos += (int)sz[i];
+                    }
                 }
                 A1.nseg = (int)asg.size() - A1.seg_begin;
                 af.push_back(A1);
@@ -1930,8 +1936,12 @@ int run_factor(const Ordering& o, const spaqr_csr* A, const spaqr_opts* opt, spa
                     sf.m = (int)lay.H[s];
                     sf.n = (int)sz[s];
                     sf.seg_begin = (int)ssegs.size();
+                    int spos = 0;
                     for (int i : sp.R[f])
-                        if (sz[i] > 0) ssegs.push_back(Seg{lay.voff[i], (int)sz[i], 0});
+                        if (sz[i] > 0) {
+                            ssegs.push_back(Seg{lay.voff[i], (int)sz[i], spos});
+                            spos += (int)sz[i];
+                        }
                     sf.nseg = (int)ssegs.size() - sf.seg_begin;
                     sf.rsj_begin = (int)srsj.size();
                     for (size_t t = 1; t < sp.C[f].size(); t++) {

@@ -75,11 +75,9 @@ __global__ void __launch_bounds__(NT) k_sfront_fwd(const SolveFront<real>* __res
     int c0, qn;
     if (!rhs_chunk(nrhs, qs, c0, qn)) return;
     const SolveFront<real> F = fr[blockIdx.x];
-    int pos = 0;
-    for (int s = 0; s < F.nseg; s++) {
+    for (int s = threadIdx.x; s < F.nseg; s += NT) {   // a segment per thread
         const Seg g = segs[F.seg_begin + s];
-        for (int r = threadIdx.x; r < g.len; r += NT) rmap[pos + r] = (int)(g.off + r);
-        pos += g.len;
+        for (int r = 0; r < g.len; r++) rmap[g.pos + r] = (int)(g.off + r);
     }
     __syncthreads();
     const Mat<real> B{Y + (int64_t)c0 * ldy, 1, ldy, rmap};
@@ -453,12 +451,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NT, 1)
     const int slab = wide_slab_rows(F.m, CS);
     const int lo = min(F.m, rank * slab), hi = min(F.m, lo + slab);
     const int rows = hi - lo;
-    int pos = 0;
-    for (int s = 0; s < F.nseg; s++) {
+    for (int s = threadIdx.x; s < F.nseg; s += NT) {   // a segment per thread: one load each
         const Seg g = segs[F.seg_begin + s];
-        const int a = max(pos, lo), b = min(pos + g.len, hi);
-        for (int r = a + threadIdx.x; r < b; r += NT) w.rmap[r - lo] = (int)(g.off + (r - pos));
-        pos += g.len;
+        const int a = max(g.pos, lo), b = min(g.pos + g.len, hi);
+        for (int r = a; r < b; r++) w.rmap[r - lo] = (int)(g.off + (r - g.pos));
     }
     __syncthreads();
     real* Yc = Y + (int64_t)c0 * ldy;

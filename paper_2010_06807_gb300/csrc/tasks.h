@@ -31,7 +31,7 @@ struct QRTask {
 struct Seg {
     int64_t off;   // first row
     int len;
-    int pad;
+    int pos;       // first row of the segment within the list's rows (sum of the earlier lengths)
 };
 
 // One front applied to one column panel (Section 2.4: H_s^T on the columns
