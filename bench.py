@@ -54,8 +54,8 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # factor_kernels_dram_convdiff2d_256x256_fp64.md for the factorisation); a
 # kind whose kernels changed since its capture, or whose kernel serves
 # several kinds (k_qr: front and scaling QR), has no entry.
-TRAFFIC = {"solve_front_fwd": 4.11e6, "front_apply": 40.95e6, "cpqr": 30.1e6, "scale_apply": 13.64e6,
-           "sparsify_merge": 18.49e6, "solve_rsj": 8.81e6, "solve_front_bwd": 4.24e6}
+TRAFFIC = {"solve_front_fwd": 4.10e6, "front_apply": 42.92e6, "cpqr": 56.52e6, "scale_apply": 13.69e6,
+           "sparsify_merge": 18.67e6, "solve_rsj": 8.82e6, "solve_front_bwd": 4.20e6}
 
 
 def _args():
